@@ -1,0 +1,92 @@
+"""Trace estimators for S(A) = tr f(A) (Section 3).
+
+* Hutchinson (eq. hutchinson-stochastic-trace-estimator):
+      tr_N(B) = (1/N) sum_j x_j^T B x_j.
+* Hutch++ (eq. Hutch++_formula):
+      tr(Q^T B Q) + tr_{N_H}((I - Q Q^T) B (I - Q Q^T)),
+  Q an orthonormal basis of range(B Omega), Omega with N_r columns; the cost is
+  N_r products B x and N_r + N_H quadratic forms.
+* Probing (eqs. probing_vectors, trace_probing):
+      T_d = sum_l v_l^T f(A) v_l,  v_l = sum_{i in V_l} e_i.
+
+B = f(A) is applied through Lanczos (module krylov).  Probes are Rademacher
+(module rng).  Hutch++ takes its sketch from probe columns 0..N_r-1 and its
+Hutchinson vectors from columns N_r..N_r+N_H-1.
+"""
+import numpy as np
+
+from .density import gershgorin_norm
+from .entropy import f_entropy
+from .krylov import lanczos_quadform, lanczos_fmatvec
+from .rng import rademacher
+
+
+def quadforms(A, X, m, reorth="full", desing=True, f=f_entropy):
+    """psi_m for every column of X (each column its own Krylov space)."""
+    nA = gershgorin_norm(A)
+    return np.array([lanczos_quadform(A, X[:, j], m, reorth=reorth, desing=desing, f=f, norm_A=nA)[0]
+                     for j in range(X.shape[1])])
+
+
+def hutchinson(A, num_vectors, m, seed, reorth="full", col_begin=0, rows=None):
+    """Returns (estimate, psi) for Rademacher probes of columns col_begin.."""
+    X = rademacher(seed, A.shape[0], col_begin, num_vectors, rows=rows)
+    psi = quadforms(A, X, m, reorth=reorth)
+    return float(np.mean(psi)) if num_vectors else 0.0, psi
+
+
+def orthonormal_range(Y, rtol=None):
+    """Orthonormal basis of range(Y): left singular vectors whose singular
+    value exceeds rtol * sigma_max (default: max(n, k) * eps)."""
+    if Y.shape[1] == 0:
+        return Y
+    U, s, _ = np.linalg.svd(Y, full_matrices=False)
+    if rtol is None:
+        rtol = max(Y.shape) * np.finfo(np.float64).eps
+    if s.size == 0 or s[0] == 0.0:
+        return U[:, :0]
+    return U[:, s > rtol * s[0]]
+
+
+def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_parts=False):
+    """Hutch++ estimate of tr f(A) (eq. Hutch++_formula)."""
+    n = A.shape[0]
+    nA = gershgorin_norm(A)
+    Omega = rademacher(seed, n, 0, n_sketch, rows=rows)
+    Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], m, reorth=reorth, norm_A=nA)
+                         for j in range(n_sketch)]) if n_sketch else np.zeros((n, 0))
+    Q = orthonormal_range(Y)
+    psi_q = np.array([lanczos_quadform(A, Q[:, i], m, reorth=reorth, norm_A=nA)[0]
+                      for i in range(Q.shape[1])])
+    G = rademacher(seed, n, n_sketch, n_hutch, rows=rows)
+    Gp = G - Q @ (Q.T @ G)
+    psi_g = np.array([lanczos_quadform(A, Gp[:, j], m, reorth=reorth, norm_A=nA)[0]
+                      for j in range(n_hutch)])
+    low_rank = float(np.sum(psi_q))
+    resid = float(np.mean(psi_g)) if n_hutch else 0.0
+    est = low_rank + resid
+    if return_parts:
+        return est, dict(Y=Y, Q=Q, psi_q=psi_q, psi_g=psi_g, low_rank=low_rank, resid=resid)
+    return est
+
+
+def probing_vectors(colors, n_colors=None):
+    """n x s 0/1 matrix with column l the indicator of colour class l (eq. probing_vectors)."""
+    colors = np.asarray(colors, dtype=np.int64)
+    s = int(colors.max()) + 1 if n_colors is None else int(n_colors)
+    V = np.zeros((colors.size, s))
+    V[np.arange(colors.size), colors] = 1.0
+    return V
+
+
+def probing(A, colors, m, reorth="full"):
+    """T_d = sum_l psi(v_l) (eq. trace_probing); returns (T_d, psi per colour)."""
+    V = probing_vectors(colors)
+    psi = quadforms(A, V, m, reorth=reorth)
+    return float(np.sum(psi)), psi
+
+
+def probing_exact(Fdense, colors):
+    """sum_l v_l^T F v_l for an explicit dense F = f(A) (no Krylov error)."""
+    V = probing_vectors(colors)
+    return float(np.sum(V * (Fdense @ V)))
