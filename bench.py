@@ -1,0 +1,364 @@
+"""Benchmark: Hutch++ entropy estimates per second on a Barabasi-Albert graph.
+
+Workload (one "step" = one full entropy estimate, every hot-path row):
+  Barabasi-Albert n = 1,000,000, m = 4 (seed 3), rho = L / tr(L) as an implicit
+  FP32 pattern Laplacian, nodes relabelled by descending degree; Hutch++ with
+  N_r = 100 sketch columns and N_H = 100 Hutchinson vectors (300 Lanczos runs
+  of 60 steps: 100 for f(A) Omega, 100 for Q, 100 for (I - QQ^T) G), FP32
+  vectors with FP64 alpha/beta, tridiagonal eigensolve and quadrature.
+
+Output: one JSON line (rank 0).  ``value`` is whole-job estimates/s with the
+matrix resident on the device; ``e2e`` repeats the measurement through the C
+ABI from host CSR buffers (matrix upload, relabelling and schedule included);
+``roofline`` is the Lanczos step (SpMM) kernel's algorithmic HBM bandwidth
+timed live with CUDA events on the library's stream; ``cpu_baseline`` times
+the FP64 CPU oracle on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NODES, BA_M, GRAPH_SEED = 1_000_000, 4, 3
+N_SKETCH, N_HUTCH, M_STEPS = 100, 100, 60
+METRIC = "entropy estimates/sec (Hutch++ N_r=100 N_H=100, 60 Lanczos steps, BA n=1e6 m=4, rel err vs FP64 <= 1e-4)"
+UNIT = "estimates/s"
+WORKLOAD = "BA n=1e6 m=4 (seed 3), rho=L/tr(L) FP32 implicit Laplacian, Hutch++ 300 matvec-equivalents, block 100, m=60"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--n", type=int, default=N_NODES, help="graph size (default: the workload's 1e6)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in ("kernels_lanczos.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2212_09642_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+        if rec.get("source_digest") == kernel_digest():
+            return float(rec["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def make_graph(n):
+    from paper_2212_09642_gb300 import graphs
+    return graphs.barabasi_albert(n, BA_M, GRAPH_SEED)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+
+def oracle_sample(g, columns=1, seed=7):
+    """Time the FP64 oracle on `columns` sketch matvecs and `columns`
+    quadratic forms of the workload plus one orthonormalisation and projection
+    of n x 100 blocks; return the extrapolated seconds per full estimate."""
+    import numpy as np
+    from oracle import density, estimators, krylov, rng
+
+    A, _ = density.density_matrix(g)
+    nA = density.gershgorin_norm(A)
+    X = rng.rademacher(seed, g.n, 0, columns)
+    t0 = time.perf_counter()
+    for j in range(columns):
+        krylov.lanczos_fmatvec(A, X[:, j], M_STEPS, reorth="none", norm_A=nA)
+    t_f = (time.perf_counter() - t0) / columns
+    t0 = time.perf_counter()
+    for j in range(columns):
+        krylov.lanczos_quadform(A, X[:, j], M_STEPS, reorth="none", norm_A=nA)
+    t_q = (time.perf_counter() - t0) / columns
+    Y = np.random.default_rng(0).standard_normal((g.n, N_SKETCH))
+    t0 = time.perf_counter()
+    Q = estimators.orthonormal_range(Y)
+    G = rng.rademacher(seed, g.n, N_SKETCH, N_HUTCH)
+    G - Q @ (Q.T @ G)
+    t_o = time.perf_counter() - t0
+    total = N_SKETCH * t_f + (N_SKETCH + N_HUTCH) * t_q + t_o
+    return total, dict(t_fmatvec=t_f, t_quadform=t_q, t_orth=t_o)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    g = make_graph(args.n)
+    for _ in range(args.warmup):
+        oracle_sample(g, columns=1)
+    times = []
+    for k in range(args.steps):
+        t, parts = oracle_sample(g, columns=1, seed=100 + k)
+        times.append(t)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "per step: 1 sketch matvec + 1 quadratic form (FP64 scipy Lanczos, 60 steps) "
+                                   "+ one n x 100 orthonormalisation/projection, scaled to 100 + 200 Krylov runs"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2212_09642_gb300 import _build, vne
+
+    _build.build_all()
+    dev = local
+    torch.cuda.set_device(dev)
+    g = make_graph(args.n)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = vne.vne_ctx_create(dev)
+    vne.vne_ctx_set_stream(ctx, stream)
+    flags = vne.VNE_FP32 | vne.VNE_REORDER
+    mat = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
+    opt = vne.options(reorth=0)
+    seed0 = 1000 * (rank + 1)
+
+    def one(seed):
+        return vne.vne_entropy_hutchpp(ctx, mat, N_SKETCH, N_HUTCH, M_STEPS, seed, opt=opt)
+
+    for w in range(args.warmup):
+        one(seed0 + w)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ests = []
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.__enter__()
+    vne.vne_ctx_profile(ctx, True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        ests.append(one(seed0 + 100 + k)[0])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    if sampler:
+        sampler.__exit__()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches, kst = vne.vne_ctx_stats(ctx)
+    vne.vne_ctx_profile(ctx, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # mixed-precision error against the FP64 GPU run on identical probes
+    rel_err = None
+    if not args.no_fp64_check and rank == 0:
+        mat64 = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, vne.VNE_FP64 | vne.VNE_REORDER)
+        e64 = vne.vne_entropy_hutchpp(ctx, mat64, N_SKETCH, N_HUTCH, M_STEPS, seed0 + 100, opt=vne.options(reorth=0))[0]
+        vne.vne_matrix_destroy(mat64)
+        rel_err = abs(ests[0] - e64) / abs(e64)
+
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        k2 = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(k2):
+            m2 = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
+            vne.vne_entropy_hutchpp(ctx, m2, N_SKETCH, N_HUTCH, M_STEPS, seed0 + 200 + k, opt=opt)
+            vne.vne_matrix_destroy(m2)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=f"cuda:{dev}", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * k2 / dt, "unit": UNIT, "h2d_bytes_per_step": int(8 * (g.n + 1) + 4 * g.nnz),
+               "d2h_bytes_per_step": 8 + 3 * 8 + 2 * 4 + 8 * (N_SKETCH + N_HUTCH)}
+
+    if rank != 0:
+        vne.vne_matrix_destroy(mat)
+        vne.vne_ctx_destroy(ctx)
+        return
+
+    peak, peak_kind = load_peaks()
+    cnt, ms, byts = kst["step"]
+    achieved = (byts / (ms / 1e3)) / 1e9 if ms > 0 else None
+    per_launch_bytes = byts / cnt if cnt else None
+    roof = {"kernel": "k_step (fused SpMM + Lanczos partial inner products)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
+            "peak_kind": peak_kind, "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
+            "avg_launch_ms": ms / cnt if cnt else None, "launches_timed": int(cnt),
+            "share_of_step_time": (ms / elapsed_ms) if elapsed_ms else None}
+    ucnt, ums, ubytes = kst["update"]
+    update = {"achieved_gbs": (ubytes / (ums / 1e3)) / 1e9 if ums > 0 else None,
+              "avg_launch_ms": ums / ucnt if ucnt else None, "share_of_step_time": ums / elapsed_ms}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        t_est, parts = oracle_sample(g, columns=2)
+        cpu = {"value": 1.0 / t_est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": "2 sketch matvecs + 2 quadratic forms (FP64 scipy Lanczos, 60 steps, same graph) + one "
+                         "n x 100 orthonormalisation/projection, extrapolated to 100 + 200 Krylov runs",
+               "detail_s": parts}
+
+    n_, nnz_, tr_, nb_ = vne.vne_matrix_info(mat)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
+                   "hutch_vectors": N_HUTCH, "krylov_steps": M_STEPS, "scalars": "f64",
+                   "l2": "inputs larger than L2 (each 100-column block is 400 MB; L2 129 MB)",
+                   "parallelism": f"replicas x{world} (independent estimates)"},
+        "roofline": roof, "update_kernel": update, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches), "clocks": sampler.summary() if sampler else None,
+        "rel_err_vs_fp64": rel_err, "estimates": ests,
+    }
+    print(json.dumps(line), flush=True)
+    vne.vne_matrix_destroy(mat)
+    vne.vne_ctx_destroy(ctx)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * vne.h -- C ABI of the GB300 von Neumann entropy library (libvne.so).
+ *
+ * The library estimates S(A) = tr f(A), f(x) = -x log x, for a sparse
+ * symmetric positive semidefinite density matrix A (normally A = L / tr L with
+ * L a graph Laplacian), following Benzi, Rinelli, Simunec, "Computation of
+ * the von Neumann entropy of large matrices via trace estimators and rational
+ * Krylov methods" (arXiv 2212.09642).  Every trace estimator reduces to many
+ * quadratic forms v^T f(A) v, which the library evaluates at once, one probe
+ * vector per column of a block, on the GPU.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns a vne_status; VNE_OK (0) on success.  On failure
+ *    vne_last_error(ctx) returns a human-readable message.  No C++ exception
+ *    crosses the ABI.
+ *  - All arrays are plain pointers with explicit sizes.  Unless a flag or the
+ *    argument's description says "device", pointers are host pointers; host
+ *    outputs are written before the call returns (the call synchronises its
+ *    stream).
+ *  - The caller owns every array it passes.  A vne_matrix owns its device
+ *    copy of the matrix until vne_matrix_destroy; the context owns the
+ *    device workspace it grows on demand and frees in vne_ctx_destroy.
+ *  - Work is enqueued on the context's stream (vne_ctx_set_stream; default
+ *    the legacy default stream).  Calls on one context are not thread safe.
+ *  - Node indices are int32 on the device: n < 2^31 and nnz < 2^31.
+ */
+#ifndef VNE_H
+#define VNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vne_status;
+#define VNE_OK 0
+#define VNE_EINVAL 1        /* invalid argument (size, pointer, flag, option) */
+#define VNE_ENOMEM 2        /* a device or host allocation failed */
+#define VNE_ENOTSYM 3       /* the CSR pattern is not symmetric */
+#define VNE_ENOCONVERGE 4   /* an iterative solve did not reach its tolerance */
+#define VNE_ETIMEOUT 5      /* a bounded device wait gave up */
+#define VNE_EDEVICE 6       /* a CUDA runtime call or kernel failed */
+#define VNE_EUNSUPPORTED 7  /* valid request that this build does not handle */
+
+typedef struct vne_ctx vne_ctx;
+typedef struct vne_matrix vne_matrix;
+
+/* ---- flags of vne_create_density_matrix ------------------------------ */
+#define VNE_FP64 0x1u            /* vectors, SpMM and Lanczos vectors in FP64 */
+#define VNE_FP32 0x2u            /* vectors and SpMM in FP32; alpha, beta,
+                                    inner products and the tridiagonal
+                                    eigensolve stay FP64 (mixed path) */
+#define VNE_NORMALIZE_TRACE 0x4u /* divide the given values by their trace */
+#define VNE_IS_LAPLACIAN 0x8u    /* A 1 = 0: use implicit desingularisation */
+#define VNE_INPUT_DEVICE 0x10u   /* row_ptr / col_idx / vals are device pointers */
+#define VNE_REORDER 0x20u        /* relabel nodes by descending degree */
+#define VNE_CHECK_SYMMETRY 0x40u /* verify the pattern is symmetric (host, O(nnz log)) */
+
+/* ---- options ---------------------------------------------------------- */
+typedef struct vne_options {
+    int32_t reorth;       /* 0: plain three-term Lanczos; 1: full
+                             reorthogonalisation (classical Gram-Schmidt
+                             twice) against the stored basis.  -1: default
+                             (full for FP64 matrices, none for FP32). */
+    int32_t block;        /* probe columns per device block, 0 = auto (<= 256) */
+    int32_t panel;        /* columns per panel of the panel-major vector
+                             layout (FP32: 8, 16, 32; FP64: 4, 8, 16), 0 = auto */
+    int32_t item_nnz;     /* target nonzeros per warp work item, 0 = auto */
+    int32_t n_inf_poles;  /* rational mode: poles at infinity (default 2) */
+    int32_t cg_max_iter;  /* rational mode: multi-shift CG iteration cap */
+    double cg_tol;        /* rational mode: relative residual (default 1e-8) */
+    double breakdown_tol; /* Lanczos stops when beta_j <= tol * ||A||_G;
+                             0 = default (1e-13 FP64, 1e-10 FP32) */
+    int32_t reserved[8];
+} vne_options;
+
+/* Fill *opt with the defaults described above. */
+void vne_options_default(vne_options *opt);
+
+/* ---- context ---------------------------------------------------------- */
+/* Create a context on CUDA device `device` (no allocation beyond small
+ * bookkeeping).  EINVAL for a bad device index, EDEVICE if CUDA fails. */
+vne_status vne_ctx_create(int32_t device, vne_ctx **ctx);
+/* Free the context and its workspace.  Matrices must be destroyed first. */
+vne_status vne_ctx_destroy(vne_ctx *ctx);
+/* Enqueue all further work on `stream` (a cudaStream_t, may be NULL). */
+vne_status vne_ctx_set_stream(vne_ctx *ctx, void *stream);
+/* Message of the last failing call on this context ("" if none).  The
+ * pointer stays valid until the next call on the context. */
+const char *vne_last_error(const vne_ctx *ctx);
+/* Library version string. */
+const char *vne_version(void);
+/* Measurement support.  vne_ctx_profile(ctx, 1) resets the counters and, from
+ * then on, brackets every launch of the Lanczos step (SpMM) and update
+ * kernels with CUDA events on the context stream; vne_ctx_stats returns the
+ * number of kernels this context launched since the reset and, per kernel
+ * kind (0 = step, 1 = update), {timed launches, total milliseconds, total
+ * algorithmic bytes}.  kernel_stats must hold 6 doubles (or be NULL). */
+vne_status vne_ctx_profile(vne_ctx *ctx, int32_t enable);
+vne_status vne_ctx_stats(const vne_ctx *ctx, int64_t *launches, double *kernel_stats);
+
+/* ---- density matrix (Section 2, eq. graph_laplacian) ------------------ */
+/* Copy a symmetric CSR matrix to the device.
+ *   n        number of rows (= columns), 1 <= n < 2^31
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz < 2^31
+ *   col_idx  int32[nnz], 0 <= col < n
+ *   vals     double[nnz] or NULL.  NULL: the matrix is the graph Laplacian
+ *            L = D - W of the pattern (off-diagonal entries = -1, no
+ *            self-loops or duplicates allowed; diagonal = degree), and the
+ *            density matrix is rho = L / tr(L) (VNE_NORMALIZE_TRACE and
+ *            VNE_IS_LAPLACIAN implied).  The Laplacian is kept implicit:
+ *            only the pattern is stored on the device.
+ *            Non-NULL: entries of a general symmetric matrix (diagonal
+ *            included), stored in the path precision.
+ *   flags    exactly one of VNE_FP64 / VNE_FP32, plus optional flags above.
+ * Errors: EINVAL (bad sizes, indices, flags; zero trace), ENOTSYM (with
+ * VNE_CHECK_SYMMETRY), ENOMEM, EDEVICE.  *out is NULL on failure. */
+vne_status vne_create_density_matrix(vne_ctx *ctx, int64_t n, const int64_t *row_ptr,
+                                     const int32_t *col_idx, const double *vals,
+                                     uint32_t flags, vne_matrix **out);
+vne_status vne_matrix_destroy(vne_matrix *mat);
+/* n, stored nnz, trace of the matrix before normalisation, Gershgorin bound
+ * ||A||_G of the normalised matrix.  Any output pointer may be NULL. */
+vne_status vne_matrix_info(const vne_matrix *mat, int64_t *n, int64_t *nnz, double *trace,
+                           double *norm_bound);
+
+/* ---- quadratic forms (Section 4, eq. rational-krylov-approximation-quadform)
+ * psi_j ~ b_j^T f(A) b_j for the k columns b_j of `vectors`.
+ *   vectors       double[n][k] row-major (host, or device with
+ *                 VNE_INPUT_DEVICE in `vec_flags`)
+ *   krylov_steps  m >= 1 Lanczos steps (polynomial mode) or, with poles,
+ *                 ignored (the space is fixed by the poles)
+ *   poles         NULL: polynomial Krylov (Lanczos Gauss quadrature).
+ *                 Otherwise num_poles positive shifts s (poles xi = -s):
+ *                 rational Krylov space span{c, Ac, .., A^l c,
+ *                 (A + s_i I)^{-1} c}, l = opt->n_inf_poles, solved by
+ *                 multi-shift CG (Sections 4.2, 5.3).
+ *   psi           double[k] output (host)
+ *   alpha_beta    NULL or double[k][2m] output (host): per column the
+ *                 Lanczos alpha_1..alpha_m then beta_1..beta_m of the
+ *                 normalised matrix (zeros after a breakdown).  Polynomial
+ *                 mode only.
+ * With VNE_IS_LAPLACIAN (or a pattern matrix) each b is replaced by
+ * b - mean(b) 1 (implicit desingularisation, Remark graph-laplacian-krylov),
+ * which leaves b^T f(A) b unchanged. */
+#define VNE_VECTORS_DEVICE 0x1u
+vne_status vne_quadform_batch(vne_matrix *mat, const double *vectors, int32_t k, uint32_t vec_flags,
+                              int32_t krylov_steps, const double *poles, int32_t num_poles,
+                              const vne_options *opt, double *psi, double *alpha_beta);
+
+/* ---- Hutchinson (Section 3.2, eq. hutchinson-stochastic-trace-estimator)
+ * estimate = (1/N) sum_j psi_m(x_j), x_j Rademacher columns 0..N-1 of the
+ * counter-based generator with `seed`; std_error = sample std / sqrt(N);
+ * psi_out = the N quadratic forms.  std_error, psi_out may be NULL. */
+vne_status vne_entropy_hutchinson(vne_matrix *mat, int32_t num_vectors, int32_t krylov_steps,
+                                  uint64_t seed, const vne_options *opt, double *estimate,
+                                  double *std_error, double *psi_out);
+
+/* ---- Hutch++ (Section 3.2, eq. Hutch++_formula)
+ * Omega = Rademacher columns 0..N_r-1, G = columns N_r..N_r+N_H-1.
+ * Y = f(A) Omega by the Lanczos matvec approximation
+ * (eq. rational-krylov-approximation-matvec), Q = orthonormal basis of Y
+ * (pivoted Cholesky-QR, twice), estimate = sum_i psi(q_i) +
+ * (1/N_H) sum_j psi((I - Q Q^T) g_j).  parts (NULL ok) receives
+ * {low-rank part, residual part, rank of Q}. */
+vne_status vne_entropy_hutchpp(vne_matrix *mat, int32_t sketch_cols, int32_t hutch_vectors,
+                               int32_t krylov_steps, uint64_t seed, const vne_options *opt,
+                               double *estimate, double *parts);
+
+/* ---- probing (Section 3.1, eqs. probing_vectors, trace_probing)
+ * T_d = sum_l psi(v_l), v_l the indicator of colour class l.
+ *   coloring   int32[n] colours 0..s-1 (host), or NULL to compute the greedy
+ *              distance-`distance` colouring (Algorithm 1, nodes by
+ *              descending degree, ties by ascending id) on the host.
+ *   poles      as in vne_quadform_batch (NULL: polynomial Lanczos).
+ *   num_colors output s (may be NULL). */
+vne_status vne_entropy_probing(vne_matrix *mat, const int32_t *coloring, int32_t distance,
+                               int32_t krylov_steps, const double *poles, int32_t num_poles,
+                               const vne_options *opt, double *estimate, int32_t *num_colors);
+
+/* Greedy distance-d colouring of a symmetric CSR pattern (Algorithm 1) on
+ * the host: colors int32[n] receives colours 0..s-1, *num_colors = s. */
+vne_status vne_greedy_coloring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                               int32_t distance, int32_t *colors, int32_t *num_colors);
+
+/* ---- kernel-level entry points (device pointers; used by the tests) ---
+ * Y = A X for a block of k columns, X and Y device arrays [n][k] row-major
+ * in the matrix's precision (float or double), rows in the caller's node
+ * numbering.  A is the normalised density matrix. */
+vne_status vne_spmm(vne_matrix *mat, const void *X, void *Y, int32_t k);
+
+/* Gauss quadrature of given tridiagonals (Section 4): for each of `count`
+ * columns, T = tridiag(beta[0..m-2], alpha[0..m-1]), psi = norm2 *
+ * sum_j u_{1j}^2 f(scale * theta_j).  alpha, beta: double[count][m] host;
+ * beta[m-1] is ignored; a zero beta_j truncates T after row j. */
+vne_status vne_tridiag_quadrature(vne_ctx *ctx, const double *alpha, const double *beta,
+                                  const double *norm2, double scale, int32_t count, int32_t m,
+                                  double *psi);
+
+/* Fill a device array [n][k] (row-major, float or double per `fp64`) with
+ * Rademacher columns col_begin..col_begin+k-1 for node ids 0..n-1. */
+vne_status vne_rademacher(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,
+                          int32_t fp64, void *out_device);
+
+/* ---- batched uneven graphs (one launch per step over all graphs) ------
+ * Packs `count` matrices (same precision) block-diagonally and runs
+ * Hutchinson with N Rademacher vectors and m Lanczos steps on each, all
+ * graphs advancing together.  estimates double[count]; std_errors may be
+ * NULL.  Each graph's result is independent of the others. */
+vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t num_vectors,
+                                int32_t krylov_steps, uint64_t seed, const vne_options *opt,
+                                double *estimates, double *std_errors);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VNE_H */

@@ -1,0 +1,10 @@
+// Host-side graph utilities of libvne.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+namespace vne {
+std::vector<int32_t> degree_order(int64_t n, const int64_t* rowptr);
+int32_t greedy_coloring(int64_t n, const int64_t* rowptr, const int32_t* col, int32_t d, int32_t* colors);
+}  // namespace vne

@@ -1,0 +1,132 @@
+// Internal kernel launch interface of libvne (host <-> device parameter blocks).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace vne {
+
+enum SourceKind { SRC_RADEMACHER = 0, SRC_INDICATOR = 1, SRC_DENSE64 = 2, SRC_PANEL = 3 };
+
+struct StartSource {
+    int32_t kind;
+    int32_t ncols;      // real columns (the rest of the block is zero padding)
+    int32_t col_begin;  // global probe index of block column 0 (Rademacher) or colour of column 0
+    int32_t ld;         // leading dimension of `dense`
+    uint64_t seed_mixed;
+    const int32_t* colors;  // SRC_INDICATOR: colour per local node id
+    const double* dense;    // SRC_DENSE64: [n][ld] in caller numbering
+};
+
+template <typename T>
+struct StartParams {
+    StartSource src;
+    const T* panel_src;        // SRC_PANEL: panel-major block
+    const int32_t* node_id;    // packed row -> local node id (NULL: identity within segment)
+    const SegInfo* seg;
+    int32_t nseg, K, n_total, tiles_per_panel;
+    const RowTile* tiles;
+    int32_t desing;
+    T* w1;
+    double* mean;   // [nseg*K]
+    double* norm2;  // [nseg*K]
+    double* sig1;   // [nseg*K]
+    double* part;
+    uint32_t* counter;
+};
+
+template <typename T>
+struct StepParams {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const T* vals;
+    int32_t n_total, K, nseg;
+    const SegInfo* seg;
+    const WorkItem* items;
+    int32_t ctas_per_panel;
+    const int32_t* cta_seg;
+    const HubRow* hubs;
+    int32_t nhubs, hub_slots;
+    T* hub_part;
+    uint32_t* hub_cnt;
+    const RowTile* tiles;
+    int32_t tiles_per_panel;
+    int32_t first;   // j == 1: no previous vector
+    int32_t renorm;  // update kernel: only recompute the norm of w_next in place
+    const T* w_cur;
+    const T* w_prev;
+    T* u;
+    T* w_next;
+    const double* sig_cur;
+    const double* sig_prev;
+    const double* beta_prev;
+    double* alpha;
+    double* beta;
+    double* sig_next;
+    double* part;
+    uint32_t* counter;
+};
+
+template <typename T>
+struct ReorthParams {
+    const T* basis;       // slot 0
+    size_t slot_stride;   // elements between consecutive slots
+    T* w;                 // vector being orthogonalised (slot j)
+    int32_t j, K, n_total, panels, tiles_per_panel;
+    const RowTile* tiles;
+    double* part;         // [panels][j][tiles][KS]
+    const double* coef;   // [j][K]
+};
+
+struct ReorthCoefParams {
+    const double* part;
+    const double* sig;    // [j][K] sigma_i of each basis vector
+    double* coef;
+    int32_t j, K, panels, tiles_per_panel;
+};
+
+template <typename T>
+struct RecoverParams {
+    const T* basis;
+    size_t slot_stride;
+    T* y;
+    const double* gamma;  // [m][K]
+    int32_t m, K, n_total, tiles_per_panel;
+    const RowTile* tiles;
+};
+
+template <typename T> cudaError_t launch_start(const StartParams<T>&, int ks, int panels, cudaStream_t);
+template <typename T> cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, cudaStream_t);
+template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
+template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
+template <typename T> cudaError_t launch_recover(const RecoverParams<T>&, int ks, int panels, cudaStream_t);
+template <typename T>
+cudaError_t launch_spmm_plain(const int32_t* rowptr, const int32_t* col, const T* vals, int n, int k,
+                              const int32_t* node_id, double scale, const T* X, T* Y, cudaStream_t);
+cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, int fp64, void* out,
+                                   cudaStream_t);
+
+// ---- dense / small kernels (kernels_dense.cu) ----
+// Gauss quadrature of `count` tridiagonals stored column-interleaved:
+// alpha[j*ld + c], beta[j*ld + c] for j < m.  psi[c] = norm2[c] * sum u1^2 f(scale[c] theta).
+// With zvec != NULL also z[j*ld + c] = (U f(scale Theta) U^T e1)_j (warp-per-column kernel).
+cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
+                                const double* scale_per_col, int count, int m, int ld, double* psi,
+                                cudaStream_t);
+cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col,
+                                int count, int m, int ld, double* zvec, cudaStream_t);
+
+// Gram C = X^T Y of two panel-major blocks (FP32/FP64 data, FP64 result [Kx][Ky]).
+template <typename T>
+cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks,
+                        double* C, cudaStream_t);
+// Out = (In2 ? In2 : 0) + coef * In * M, M double [kin][kout] row-major; panel-major blocks.
+template <typename T>
+cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
+                         double coef, cudaStream_t);
+// Pivoted Cholesky of a k x k SPD matrix G (FP64) with rank cut-off tol * max diag.
+// Writes Minv [k][k] (rows permuted: Q = Y Minv spans range(Y)) and rank.
+cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, cudaStream_t);
+
+}  // namespace vne

@@ -1,0 +1,433 @@
+// Small dense kernels of libvne: the tridiagonal eigensolve + Gauss
+// quadrature (Section 4, eq. rational-krylov-approximation-quadform), the
+// Lanczos matvec coefficients f(T) e1, and the Hutch++ sketch linear algebra
+// (Gram matrices, block products, pivoted Cholesky-QR factor).
+//
+// Tridiagonal eigenproblems use the implicit symmetric QR iteration with a
+// Wilkinson shift (Golub & Van Loan, Matrix Computations, Sec. 8.3), in
+// FP64.  Only the first row of the eigenvector matrix is needed for the
+// quadrature (the Golub-Welsch weights u_{1j}^2), so the per-column kernel
+// tracks that row alone; the matvec kernel keeps the full eigenvector matrix
+// in shared memory, one warp per column, lanes owning its rows.
+#include <float.h>
+#include <math.h>
+
+#include "kernels.h"
+
+namespace vne {
+
+__host__ __device__ __forceinline__ double f_entropy(double x) { return x > 0.0 ? -x * log(x) : 0.0; }
+
+// One implicit QR sweep framework.  d[0..n), e[0..n-1) are overwritten by the
+// eigenvalues / zeros; `rot(k, c, s)` is called for every Givens rotation
+// acting on columns k, k+1 of the eigenvector matrix.  Returns false if the
+// iteration cap was hit.
+template <typename Rot>
+__host__ __device__ bool symtri_qr(double* d, double* e, int n, Rot rot) {
+    const double eps = DBL_EPSILON;
+    int hi = n - 1;
+    int iters = 0;
+    const int max_iters = 40 * n + 40;
+    while (hi > 0) {
+        if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+            e[hi - 1] = 0.0;
+            hi--;
+            continue;
+        }
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) lo--;
+        if (lo > 0) e[lo - 1] = 0.0;
+        if (++iters > max_iters) return false;
+        // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
+        double delta = 0.5 * (d[hi - 1] - d[hi]);
+        double b2 = e[hi - 1] * e[hi - 1];
+        double den = delta + copysign(sqrt(delta * delta + b2), delta == 0.0 ? 1.0 : delta);
+        double mu = d[hi] - b2 / den;
+        double x = d[lo] - mu, y = e[lo];
+        for (int k = lo; k < hi; k++) {
+            double r = hypot(x, y);
+            double c, s;
+            if (r == 0.0) {
+                c = 1.0;
+                s = 0.0;
+            } else {
+                c = x / r;
+                s = -y / r;
+            }
+            if (k > lo) e[k - 1] = r;
+            double a = d[k], b = e[k], cc = d[k + 1];
+            double cs = c * s, c2 = c * c, s2 = s * s;
+            d[k] = a * c2 - 2.0 * b * cs + cc * s2;
+            d[k + 1] = a * s2 + 2.0 * b * cs + cc * c2;
+            e[k] = (a - cc) * cs + b * (c2 - s2);
+            rot(k, c, s);
+            if (k < hi - 1) {
+                x = e[k];
+                y = -s * e[k + 1];
+                e[k + 1] = c * e[k + 1];
+            }
+        }
+    }
+    return true;
+}
+
+template <int MAXM>
+__global__ void k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
+                               const double* __restrict__ norm2, const double* __restrict__ scale, int count,
+                               int m, int ld, double* __restrict__ psi) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= count) return;
+    double d[MAXM], e[MAXM], z[MAXM];
+    int n = m;
+    for (int j = 0; j < m; j++) {
+        d[j] = alpha[(size_t)j * ld + c];
+        z[j] = 0.0;
+    }
+    for (int j = 0; j + 1 < m; j++) {
+        e[j] = beta[(size_t)j * ld + c];
+        if (e[j] == 0.0) {
+            n = j + 1;
+            break;
+        }
+    }
+    z[0] = 1.0;
+    bool ok = symtri_qr(d, e, n, [&](int k, double cr, double sr) {
+        double a = z[k], b = z[k + 1];
+        z[k] = cr * a - sr * b;
+        z[k + 1] = sr * a + cr * b;
+    });
+    double sc = scale[c];
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s += z[k] * z[k] * f_entropy(sc * d[k]);
+    psi[c] = ok ? norm2[c] * s : nan("");
+}
+
+// warp per column; dynamic smem: Z [m][m] (row-major) per warp (1 warp / CTA)
+__global__ void k_tridiag_fvec(const double* __restrict__ alpha, const double* __restrict__ beta,
+                               const double* __restrict__ scale, int count, int m, int ld,
+                               double* __restrict__ zvec) {
+    extern __shared__ double sm[];
+    double* Z = sm;              // m*m
+    double* d = sm + m * m;      // m
+    double* e = d + m;           // m
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (c >= count) return;
+    for (int idx = lane; idx < m * m; idx += 32) Z[idx] = ((idx / m) == (idx % m)) ? 1.0 : 0.0;
+    for (int j = lane; j < m; j += 32) {
+        d[j] = alpha[(size_t)j * ld + c];
+        e[j] = (j + 1 < m) ? beta[(size_t)j * ld + c] : 0.0;
+    }
+    __syncwarp();
+    int n = m;
+    for (int j = 0; j + 1 < m; j++)
+        if (e[j] == 0.0) {
+            n = j + 1;
+            break;
+        }
+    // every lane runs the scalar recurrence on private copies (uniform control
+    // flow), and applies each rotation to the rows of Z it owns
+    double dl[128], el[128];
+    for (int j = 0; j < n; j++) {
+        dl[j] = d[j];
+        el[j] = e[j];
+    }
+    __syncwarp();
+    bool ok = symtri_qr(dl, el, n, [&](int k, double cr, double sr) {
+        for (int row = lane; row < n; row += 32) {
+            double a = Z[row * m + k], b = Z[row * m + k + 1];
+            Z[row * m + k] = cr * a - sr * b;
+            Z[row * m + k + 1] = sr * a + cr * b;
+        }
+    });
+    __syncwarp();
+    double sc = scale[c];
+    for (int row = lane; row < m; row += 32) {
+        double acc = 0.0;
+        if (row < n)
+            for (int k = 0; k < n; k++) acc += Z[row * m + k] * f_entropy(sc * dl[k]) * Z[k];
+        zvec[(size_t)row * ld + c] = ok ? acc : nan("");
+    }
+}
+
+cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
+                                const double* scale_per_col, int count, int m, int ld, double* psi,
+                                cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    dim3 block(64), grid((count + 63) / 64);
+    if (m <= 32) k_tridiag_quad<32><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
+    else if (m <= 64) k_tridiag_quad<64><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
+    else if (m <= 128) k_tridiag_quad<128><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col, int count,
+                                int m, int ld, double* zvec, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (m > 128) return cudaErrorInvalidValue;
+    size_t smem = ((size_t)m * m + 2 * m) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tridiag_fvec<<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gram C = X^T Y, 64 x 64 output tile per CTA, rows split into chunks.
+// Products accumulate in the data precision over 64-row tiles, then in FP64.
+template <typename T, int KS>
+__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, const T* __restrict__ Y, int ky,
+                                              int n, int rows_per_chunk, int tiles_y, double* __restrict__ part) {
+    __shared__ T Xs[64][65];
+    __shared__ T Ys[64][65];
+    const int chunk = blockIdx.x;
+    const int tx0 = (blockIdx.y / tiles_y) * 64, ty0 = (blockIdx.y % tiles_y) * 64;
+    const int r_begin = chunk * rows_per_chunk;
+    const int r_end = min(n, r_begin + rows_per_chunk);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double dacc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) dacc[a][b] = 0.0;
+    for (int rt = r_begin; rt < r_end; rt += 64) {
+        for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+            int rl = idx / 64, cl = idx % 64;
+            int r = rt + rl;
+            int cxg = tx0 + cl, cyg = ty0 + cl;
+            T xv = (T)0, yv = (T)0;
+            if (r < r_end) {
+                if (cxg < kx) xv = X[(size_t)(cxg / KS) * n * KS + (size_t)r * KS + (cxg % KS)];
+                if (cyg < ky) yv = Y[(size_t)(cyg / KS) * n * KS + (size_t)r * KS + (cyg % KS)];
+            }
+            Xs[rl][cl] = xv;
+            Ys[rl][cl] = yv;
+        }
+        __syncthreads();
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) acc[a][b] = (T)0;
+#pragma unroll 8
+        for (int rl = 0; rl < 64; rl++) {
+            T xa[4], yb[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) xa[a] = Xs[rl][tx * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; b++) yb[b] = Ys[rl][ty * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] += xa[a] * yb[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) dacc[a][b] += (double)acc[a][b];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            int i = tx0 + tx * 4 + a, j = ty0 + ty * 4 + b;
+            if (i < kx && j < ky) part[(size_t)chunk * kx * ky + (size_t)i * ky + j] = dacc[a][b];
+        }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int total, double* __restrict__ C) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += part[(size_t)c * total + idx];
+    C[idx] = s;
+}
+
+template <typename T>
+cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks, double* C,
+                        cudaStream_t st) {
+    if (kx <= 0 || ky <= 0) return cudaSuccess;
+    int tiles_x = (kx + 63) / 64, tiles_y = (ky + 63) / 64;
+    int rpc = (n + nchunks - 1) / nchunks;
+    rpc = ((rpc + 63) / 64) * 64;
+    int chunks = rpc > 0 ? (n + rpc - 1) / rpc : 1;
+    if (chunks < 1) chunks = 1;
+    dim3 grid(chunks, tiles_x * tiles_y);
+    if (ks == 4) k_gram<T, 4><<<grid, 256, 0, st>>>(X, kx, Y, ky, n, rpc, tiles_y, part);
+    else if (ks == 8) k_gram<T, 8><<<grid, 256, 0, st>>>(X, kx, Y, ky, n, rpc, tiles_y, part);
+    else if (ks == 16) k_gram<T, 16><<<grid, 256, 0, st>>>(X, kx, Y, ky, n, rpc, tiles_y, part);
+    else if (ks == 32) k_gram<T, 32><<<grid, 256, 0, st>>>(X, kx, Y, ky, n, rpc, tiles_y, part);
+    else return cudaErrorInvalidValue;
+    int total = kx * ky;
+    k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Out = In2 + coef * In * M over 32-row tiles; M (FP64 [kin][kout]) staged in smem
+// in the data precision.  8 threads per row, 16 output columns per thread.
+template <typename T, int KS>
+__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ In, int kin, const double* __restrict__ M,
+                                               int kout, const T* __restrict__ In2, T* __restrict__ Out, int n,
+                                               double coef) {
+    extern __shared__ unsigned char smraw[];
+    T* Ms = reinterpret_cast<T*>(smraw);  // [kin][128]
+    T* Ins = Ms + (size_t)kin * 128;      // [32][kin]
+    for (int idx = threadIdx.x; idx < kin * 128; idx += 256) {
+        int a = idx / 128, b = idx % 128;
+        Ms[idx] = (b < kout) ? (T)(coef * M[(size_t)a * kout + b]) : (T)0;
+    }
+    const int r0 = blockIdx.x * 32;
+    for (int idx = threadIdx.x; idx < 32 * kin; idx += 256) {
+        int rl = idx / kin, c = idx % kin;
+        int r = r0 + rl;
+        Ins[idx] = (r < n) ? In[(size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS)] : (T)0;
+    }
+    __syncthreads();
+    const int rl = threadIdx.x / 8, cb = (threadIdx.x % 8) * 16;
+    const int r = r0 + rl;
+    if (r >= n || cb >= kout) return;
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; q++) acc[q] = (T)0;
+    for (int k = 0; k < kin; k++) {
+        T a = Ins[rl * kin + k];
+#pragma unroll
+        for (int q = 0; q < 16; q++) acc[q] += a * Ms[k * 128 + cb + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        int c = cb + q;
+        if (c < kout) {
+            size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
+            T v = acc[q];
+            if (In2) v += In2[o];
+            Out[o] = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
+                         double coef, cudaStream_t st) {
+    if (kout > 128 || kin > 128) return cudaErrorInvalidValue;
+    size_t smem = ((size_t)kin * 128 + 32 * (size_t)kin) * sizeof(T);
+    dim3 grid((n + 31) / 32);
+#define VNE_APPLY_CASE(KSV)                                                                                  \
+    if (ks == KSV) {                                                                                        \
+        cudaError_t e = cudaFuncSetAttribute(k_apply<T, KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem);                                                    \
+        if (e != cudaSuccess) return e;                                                                     \
+        k_apply<T, KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef);                            \
+        return cudaGetLastError();                                                                          \
+    }
+    VNE_APPLY_CASE(4)
+    VNE_APPLY_CASE(8)
+    VNE_APPLY_CASE(16)
+    VNE_APPLY_CASE(32)
+#undef VNE_APPLY_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Pivoted Cholesky G = P R^T R P^T (one CTA, FP64).  Stops when the largest
+// remaining pivot is <= tol * max diag(G); rank r = pivots taken.  Writes
+// Minv with Minv[piv[i]][c] = (R^{-1})[i][c] for i, c < r, zero elsewhere, so
+// that Y Minv has orthonormal columns in exact arithmetic.
+__global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, double* __restrict__ Minv,
+                          int* __restrict__ rank_out) {
+    extern __shared__ double A[];  // k*k
+    __shared__ int piv[128];
+    __shared__ int s_p, s_rank;
+    __shared__ double s_max0;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) A[idx] = G[idx];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) piv[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < k; i++) mx = fmax(mx, A[i * k + i]);
+        s_max0 = mx;
+        s_rank = k;
+    }
+    __syncthreads();
+    for (int j = 0; j < k; j++) {
+        if (threadIdx.x == 0) {
+            int p = j;
+            double best = A[j * k + j];
+            for (int i = j + 1; i < k; i++)
+                if (A[i * k + i] > best) {
+                    best = A[i * k + i];
+                    p = i;
+                }
+            s_p = (best > tol * s_max0 && best > 0.0) ? p : -1;
+            if (s_p < 0) s_rank = j;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p < 0) break;
+        if (p != j) {
+            for (int i = threadIdx.x; i < k; i += blockDim.x) {  // swap rows
+                double t = A[j * k + i];
+                A[j * k + i] = A[p * k + i];
+                A[p * k + i] = t;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < k; i += blockDim.x) {  // swap columns
+                double t = A[i * k + j];
+                A[i * k + j] = A[i * k + p];
+                A[i * k + p] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = piv[j];
+                piv[j] = piv[p];
+                piv[p] = t;
+            }
+            __syncthreads();
+        }
+        const double rjj = sqrt(A[j * k + j]);
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[j * k + i] /= rjj;
+        if (threadIdx.x == 0) A[j * k + j] = rjj;
+        __syncthreads();
+        const int rem = k - j - 1;
+        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+            int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
+            A[a * k + b] -= A[j * k + a] * A[j * k + b];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const int r = s_rank;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) Minv[idx] = 0.0;
+    __syncthreads();
+    // R^{-1} column by column (back substitution), one thread per column
+    for (int c = threadIdx.x; c < r; c += blockDim.x) {
+        double x[128];
+        x[c] = 1.0 / A[c * k + c];
+        for (int i = c - 1; i >= 0; i--) {
+            double s = 0.0;
+            for (int l = i + 1; l <= c; l++) s += A[i * k + l] * x[l];
+            x[i] = -s / A[i * k + i];
+        }
+        for (int i = 0; i <= c; i++) Minv[(size_t)piv[i] * k + c] = x[i];
+    }
+    if (threadIdx.x == 0) *rank_out = r;
+}
+
+cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, cudaStream_t st) {
+    if (k > 128 || k <= 0) return cudaErrorInvalidValue;
+    size_t smem = (size_t)k * k * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_chol_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chol_qr<<<1, 256, smem, st>>>(G, k, tol, Minv, rank);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gram<float>(const float*, int, const float*, int, int, int, double*, int, double*, cudaStream_t);
+template cudaError_t launch_gram<double>(const double*, int, const double*, int, int, int, double*, int, double*, cudaStream_t);
+template cudaError_t launch_apply<float>(const float*, int, const double*, int, const float*, float*, int, int, double, cudaStream_t);
+template cudaError_t launch_apply<double>(const double*, int, const double*, int, const double*, double*, int, int, double, cudaStream_t);
+
+}  // namespace vne

@@ -1,0 +1,617 @@
+// Lanczos hot-path kernels of libvne: start vectors (probe generation and
+// implicit desingularisation), the fused SpMM step, the three-term update,
+// full reorthogonalisation and the Lanczos matvec recovery.
+//
+// Vector layout ("panel-major"): a block of K = P * KS columns over the
+// packed rows is stored as P panels, each [n_total][KS] row-major, so one row
+// of a panel is KS contiguous values (32-128 bytes) and a neighbour gather
+// reads whole sectors.  Panels are processed in blockIdx order, which keeps
+// the panel being gathered resident in L2 while the others stream.
+//
+// Lanczos in scaled form (Section 4, polynomial Krylov).  Slot j holds an
+// unnormalised basis vector w_j with v_j = sigma_j w_j (sigma_1 = 1/||c||,
+// sigma_{j+1} = 1/beta_j), so normalisation never needs its own pass:
+//   step kernel   u     = sigma_j M w_j - beta_{j-1} sigma_{j-1} w_{j-1}
+//                 alpha_j = sigma_j (w_j . u)
+//   update kernel w_{j+1} = u - alpha_j sigma_j w_j,  beta_j = ||w_{j+1}||
+// M is the stored operator (the Laplacian L for a graph, kept implicit) and
+// A = scale * M; alpha and beta here belong to M and are scaled in FP64 by
+// the quadrature.  Inner products are accumulated per lane in the vector
+// precision over at most a few rows, then in FP64 across lanes, warps and
+// CTAs; the cross-CTA sums are done by the last CTA to arrive for each
+// (panel, segment), in a fixed order, so results are bit-reproducible.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vne {
+
+// ---------------------------------------------------------------------------
+// fixed-order cross-CTA reduction
+//
+// Every CTA writes NQ*KS partial values at part[(panel*nparts + idx)*W + c]
+// (W = NQ*KS) and calls this; the CTA that arrives last for the counter sums
+// the `count` partials starting at `begin` in index order and returns true
+// with the totals in s_out[0..W).  The counter is reset for the next launch.
+template <int W>
+__device__ bool last_cta_reduce(const double* part, uint32_t* counter, int panel, int nparts,
+                                int begin, int count, double* s_out) {
+    __shared__ int s_last;
+    __shared__ double red[VNE_THREADS];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned old = atomicAdd(counter, 1u);
+        s_last = (old == (unsigned)(count - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    constexpr int NS = VNE_THREADS / W;
+    const int c = threadIdx.x % W, s = threadIdx.x / W;
+    double acc = 0.0;
+    if (s < NS)
+        for (int i = s; i < count; i += NS)
+            acc += ld_cg(&part[((size_t)panel * nparts + begin + i) * W + c]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < W) {
+        double t = 0.0;
+        for (int q = 0; q < NS; q++) t += red[q * W + threadIdx.x];
+        s_out[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// counter-based Rademacher entries (SplitMix64 mixer; see the header of
+// vne_api.cu for the definition)
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double rademacher_entry(uint64_t s, uint64_t col, uint64_t node) {
+    uint64_t h = mix64((((col << 32) | node) ^ s) + 0x9E3779B97F4A7C15ULL);
+    return (h >> 63) ? -1.0 : 1.0;
+}
+
+// Start-vector source value for packed row r (local node id `id`) and block
+// column gc (global within the block).
+__device__ __forceinline__ double source_value(const StartSource& S, int r, int id, int gc) {
+    if (gc >= S.ncols) return 0.0;
+    switch (S.kind) {
+        case SRC_RADEMACHER:
+            return rademacher_entry(S.seed_mixed, (uint64_t)(S.col_begin + gc), (uint64_t)id);
+        case SRC_INDICATOR:
+            return (S.colors[id] == S.col_begin + gc) ? 1.0 : 0.0;
+        case SRC_DENSE64:
+            return S.dense[(size_t)id * S.ld + gc];
+        default:
+            return 0.0;
+    }
+}
+
+template <typename T, int KS>
+__device__ __forceinline__ double source_value_panel(const StartSource& S, const T* panel_src, int r,
+                                                     int id, int gc, int n_total) {
+    if (S.kind == SRC_PANEL) {
+        if (gc >= S.ncols) return 0.0;
+        const T* base = panel_src + (size_t)(gc / KS) * n_total * KS;
+        return (double)base[(size_t)r * KS + (gc % KS)];
+    }
+    return source_value(S, r, id, gc);
+}
+
+// Pass 1: column sums per segment -> mean (only when desingularising).
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
+    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const SegInfo sg = p.seg[t.seg];
+    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
+    constexpr int RPI = VNE_THREADS / KS;
+    const int gc = panel * KS + c;
+    double acc = 0.0;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
+        int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
+        acc += source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total);
+    }
+    __shared__ double red[VNE_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
+        p.part[((size_t)panel * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
+    }
+    __shared__ double tot[KS];
+    if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + t.seg, panel, p.tiles_per_panel,
+                            sg.tile_begin, sg.tile_count, tot)) {
+        if (threadIdx.x < KS)
+            p.mean[(size_t)t.seg * p.K + panel * KS + threadIdx.x] = tot[threadIdx.x] / (double)sg.rows;
+    }
+}
+
+// Pass 2: w_1 = b - mean (stored in T), ||c||^2 in FP64, sigma_1 = 1/||c||.
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) {
+    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const SegInfo sg = p.seg[t.seg];
+    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
+    constexpr int RPI = VNE_THREADS / KS;
+    const int gc = panel * KS + c;
+    const double mu = p.desing ? p.mean[(size_t)t.seg * p.K + gc] : 0.0;
+    T* out = p.w1 + (size_t)panel * p.n_total * KS;
+    double acc = 0.0;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
+        int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
+        double v = source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total) - mu;
+        if (gc >= p.src.ncols) v = 0.0;
+        out[(size_t)r * KS + c] = (T)v;
+        acc += v * v;
+    }
+    __shared__ double red[VNE_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
+        p.part[((size_t)panel * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
+    }
+    __shared__ double tot[KS];
+    if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + t.seg, panel, p.tiles_per_panel,
+                            sg.tile_begin, sg.tile_count, tot)) {
+        if (threadIdx.x < KS) {
+            size_t o = (size_t)t.seg * p.K + panel * KS + threadIdx.x;
+            double nrm2 = tot[threadIdx.x];
+            p.norm2[o] = nrm2;
+            p.sig1[o] = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step kernel: u = sigma_j M w_j - beta_{j-1} sigma_{j-1} w_{j-1},
+// alpha_j = sigma_j (w_j . u).  One warp per work item.
+template <typename T, int KS, bool VALUED>
+__global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
+    constexpr int CPL = LaneVec<T>::CPL;
+    constexpr int LPR = KS / CPL;  // lanes per row
+    constexpr int G = 32 / LPR;    // row groups per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LPR, sub = lane % LPR;
+    const int panel = blockIdx.x / p.ctas_per_panel, cta = blockIdx.x % p.ctas_per_panel;
+    const int seg = p.cta_seg[cta];
+    const size_t pofs = (size_t)panel * p.n_total * KS;
+    const T* __restrict__ W = p.w_cur + pofs;
+    const T* __restrict__ Wp = p.w_prev + pofs;
+    T* __restrict__ U = p.u + pofs;
+    const int cofs = sub * CPL;
+    const size_t so = (size_t)seg * p.K + panel * KS + cofs;
+
+    T sig[CPL], cp[CPL], dot[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        sig[q] = (T)p.sig_cur[so + q];
+        cp[q] = p.first ? (T)0 : (T)(p.beta_prev[so + q] * p.sig_prev[so + q]);
+        dot[q] = (T)0;
+    }
+
+    auto epilogue = [&](int r, const T (&acc)[CPL], int deg) {
+        T x[CPL], xp[CPL], uu[CPL];
+        load_lane(W + (size_t)r * KS + cofs, x);
+        if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+            T ax = VALUED ? acc[q] : ((T)deg * x[q] - acc[q]);
+            T v = sig[q] * ax;
+            if (!p.first) v -= cp[q] * xp[q];
+            uu[q] = v;
+            dot[q] += x[q] * v;
+        }
+        store_lane(U + (size_t)r * KS + cofs, uu);
+    };
+
+    const WorkItem it = p.items[(size_t)cta * VNE_WARPS + warp];
+    if (it.rows > 0) {
+        for (int r = it.row + g; r < it.row + it.rows; r += G) {
+            const int kb = p.rowptr[r], ke = p.rowptr[r + 1];
+            T acc[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; q++) acc[q] = (T)0;
+            int k = kb;
+            for (; k + 4 <= ke; k += 4) {
+                int c0 = __ldg(p.col + k), c1 = __ldg(p.col + k + 1), c2 = __ldg(p.col + k + 2),
+                    c3 = __ldg(p.col + k + 3);
+                T a0[CPL], a1[CPL], a2[CPL], a3[CPL];
+                load_lane(W + (size_t)c0 * KS + cofs, a0);
+                load_lane(W + (size_t)c1 * KS + cofs, a1);
+                load_lane(W + (size_t)c2 * KS + cofs, a2);
+                load_lane(W + (size_t)c3 * KS + cofs, a3);
+                if (VALUED) {
+                    T v0 = __ldg(p.vals + k), v1 = __ldg(p.vals + k + 1), v2 = __ldg(p.vals + k + 2),
+                      v3 = __ldg(p.vals + k + 3);
+#pragma unroll
+                    for (int q = 0; q < CPL; q++) acc[q] += v0 * a0[q] + v1 * a1[q] + v2 * a2[q] + v3 * a3[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < CPL; q++) acc[q] += (a0[q] + a1[q]) + (a2[q] + a3[q]);
+                }
+            }
+            for (; k < ke; k++) {
+                int c0 = __ldg(p.col + k);
+                T a0[CPL];
+                load_lane(W + (size_t)c0 * KS + cofs, a0);
+                T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
+#pragma unroll
+                for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
+            }
+            epilogue(r, acc, ke - kb);
+        }
+    } else if (it.rows < 0) {
+        // one chunk of a long row, all groups of the warp share it
+        const HubRow h = p.hubs[it.row];
+        const int chunk = -it.rows - 1;
+        T acc[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; q++) acc[q] = (T)0;
+        for (int k = it.nnz_begin + g; k < it.nnz_end; k += G) {
+            int c0 = __ldg(p.col + k);
+            T a0[CPL];
+            load_lane(W + (size_t)c0 * KS + cofs, a0);
+            T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
+#pragma unroll
+            for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
+        }
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+            for (int q = 0; q < CPL; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        T* hp = p.hub_part + ((size_t)panel * p.hub_slots + h.slot) * KS;
+        if (g == 0) store_lane(hp + (size_t)chunk * KS + cofs, acc);
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            unsigned old = atomicAdd(p.hub_cnt + (size_t)panel * p.nhubs + it.row, 1u);
+            last = (old == (unsigned)(h.chunks - 1));
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            if (g == 0) {
+                T tot[CPL];
+#pragma unroll
+                for (int q = 0; q < CPL; q++) tot[q] = (T)0;
+                for (int c = 0; c < h.chunks; c++)
+#pragma unroll
+                    for (int q = 0; q < CPL; q++) tot[q] += ld_cg(hp + (size_t)c * KS + cofs + q);
+                const int r = h.row;
+                epilogue(r, tot, p.rowptr[r + 1] - p.rowptr[r]);
+            }
+            if (lane == 0) p.hub_cnt[(size_t)panel * p.nhubs + it.row] = 0u;
+        }
+    }
+
+    // CTA partial of w_j . u per column: FP64 across groups, warps, CTAs
+    __shared__ double sred[VNE_WARPS][KS];
+    double d[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        d[q] = (double)dot[q];
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
+    }
+    if (g == 0)
+#pragma unroll
+        for (int q = 0; q < CPL; q++) sred[warp][cofs + q] = d[q];
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < VNE_WARPS; w++) s += sred[w][threadIdx.x];
+        p.part[((size_t)panel * p.ctas_per_panel + cta) * KS + threadIdx.x] = s;
+    }
+    __shared__ double tot[KS];
+    const SegInfo sg = p.seg[seg];
+    if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + seg, panel, p.ctas_per_panel,
+                            sg.cta_begin, sg.cta_count, tot)) {
+        if (threadIdx.x < KS) {
+            size_t o = (size_t)seg * p.K + panel * KS + threadIdx.x;
+            p.alpha[o] = p.sig_cur[o] * tot[threadIdx.x];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update kernel: w_{j+1} = u - alpha_j sigma_j w_j (or, with `renorm`, just
+// the norm of w_{j+1} in place), beta_j = ||w_{j+1}||, sigma_{j+1} = 1/beta_j
+// unless beta_j <= tau (breakdown: beta_j = sigma_{j+1} = 0, column done).
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
+    constexpr int CPL = LaneVec<T>::CPL;
+    constexpr int LPR = KS / CPL;
+    constexpr int RPI = VNE_THREADS / LPR;  // rows per iteration
+    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
+    const int cofs = sub * CPL;
+    const size_t pofs = (size_t)panel * p.n_total * KS;
+    const size_t so = (size_t)t.seg * p.K + panel * KS + cofs;
+    T a[CPL], nrm[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        a[q] = p.renorm ? (T)0 : (T)(p.alpha[so + q] * p.sig_cur[so + q]);
+        nrm[q] = (T)0;
+    }
+    const T* __restrict__ Uu = p.u + pofs;
+    const T* __restrict__ W = p.w_cur + pofs;
+    T* __restrict__ Wn = p.w_next + pofs;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
+        T uu[CPL], x[CPL], wn[CPL];
+        if (p.renorm) {
+            load_lane(Wn + (size_t)r * KS + cofs, wn);
+        } else {
+            load_lane_stream(Uu + (size_t)r * KS + cofs, uu);
+            load_lane(W + (size_t)r * KS + cofs, x);
+#pragma unroll
+            for (int q = 0; q < CPL; q++) wn[q] = uu[q] - a[q] * x[q];
+            store_lane(Wn + (size_t)r * KS + cofs, wn);
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; q++) nrm[q] += wn[q] * wn[q];
+    }
+    __shared__ double red[VNE_THREADS / LPR][KS];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) red[rsub][cofs + q] = (double)nrm[q];
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+        for (int i = 0; i < RPI; i++) s += red[i][threadIdx.x];
+        p.part[((size_t)panel * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
+    }
+    __shared__ double tot[KS];
+    const SegInfo sg = p.seg[t.seg];
+    if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + t.seg, panel, p.tiles_per_panel,
+                            sg.tile_begin, sg.tile_count, tot)) {
+        if (threadIdx.x < KS) {
+            size_t o = (size_t)t.seg * p.K + panel * KS + threadIdx.x;
+            double b = sqrt(tot[threadIdx.x]);
+            if (!(b > sg.tau) || p.sig_cur[o] == 0.0) {
+                p.beta[o] = 0.0;
+                p.sig_next[o] = 0.0;
+            } else {
+                p.beta[o] = b;
+                p.sig_next[o] = 1.0 / b;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Full reorthogonalisation (classical Gram-Schmidt pass) of w_{j+1} against
+// v_i = sigma_i w_i, i = 1..j, all stored in consecutive slots.
+// Pass A: coef_i = sigma_i^2 (w_i . w_{j+1}) for every (i, column).
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) {
+    // grid: panel * tiles * j ; each CTA: one tile, one i
+    const int i = blockIdx.x % p.j;
+    const int pt = blockIdx.x / p.j;
+    const int panel = pt / p.tiles_per_panel, tile = pt % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
+    constexpr int RPI = VNE_THREADS / KS;
+    const size_t pofs = (size_t)panel * p.n_total * KS;
+    const T* Wi = p.basis + (size_t)i * p.slot_stride + pofs;
+    const T* Wn = p.w + pofs;
+    double acc = 0.0;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI)
+        acc += (double)Wi[(size_t)r * KS + c] * (double)Wn[(size_t)r * KS + c];
+    __shared__ double red[VNE_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
+        p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
+    }
+}
+
+// Pass B: fixed-order sum of the tile partials -> coefficients.
+template <int KS>
+__global__ void k_reorth_coef(ReorthCoefParams p) {
+    // one thread per (panel, i, c)
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int total = p.panels * p.j * KS;
+    if (idx >= total) return;
+    int c = idx % KS, i = (idx / KS) % p.j, panel = idx / (KS * p.j);
+    double s = 0.0;
+    for (int t = 0; t < p.tiles_per_panel; t++)
+        s += p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + t) * KS + c];
+    int col = panel * KS + c;
+    double sig = p.sig[(size_t)i * p.K + col];
+    p.coef[(size_t)i * p.K + col] = sig * sig * s;
+}
+
+// Pass C: w_{j+1} -= sum_i coef_i w_i.
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p) {
+    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
+    constexpr int RPI = VNE_THREADS / KS;
+    const size_t pofs = (size_t)panel * p.n_total * KS;
+    T* Wn = p.w + pofs;
+    const int col = panel * KS + c;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
+        double v = (double)Wn[(size_t)r * KS + c];
+        for (int i = 0; i < p.j; i++)
+            v -= p.coef[(size_t)i * p.K + col] * (double)p.basis[(size_t)i * p.slot_stride + pofs + (size_t)r * KS + c];
+        Wn[(size_t)r * KS + c] = (T)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos matvec recovery (eq. rational-krylov-approximation-matvec):
+// y = ||c|| V_m f(T_m) e1 = sum_j gamma_j w_j with gamma_j = ||c|| sigma_j z_j.
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_recover(RecoverParams<T> p) {
+    constexpr int CPL = LaneVec<T>::CPL;
+    constexpr int LPR = KS / CPL;
+    constexpr int RPI = VNE_THREADS / LPR;
+    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const RowTile t = p.tiles[tile];
+    const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
+    const int cofs = sub * CPL;
+    extern __shared__ double s_gamma[];  // [m][KS]
+    for (int idx = threadIdx.x; idx < p.m * KS; idx += blockDim.x) {
+        int j = idx / KS, c = idx % KS;
+        s_gamma[idx] = p.gamma[(size_t)j * p.K + panel * KS + c];
+    }
+    __syncthreads();
+    const size_t pofs = (size_t)panel * p.n_total * KS;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
+        T acc[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; q++) acc[q] = (T)0;
+        for (int j = 0; j < p.m; j++) {
+            T x[CPL];
+            load_lane_stream(p.basis + (size_t)j * p.slot_stride + pofs + (size_t)r * KS + cofs, x);
+#pragma unroll
+            for (int q = 0; q < CPL; q++) acc[q] += (T)s_gamma[j * KS + cofs + q] * x[q];
+        }
+        store_lane(p.y + pofs + (size_t)r * KS + cofs, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain SpMM Y = scale * M X for the kernel-level entry point (X, Y row-major
+// [n][k] in the caller's numbering; perm maps packed rows to caller rows).
+template <typename T, bool VALUED>
+__global__ void k_spmm_plain(const int32_t* rowptr, const int32_t* col, const T* vals, int n, int k,
+                             const int32_t* node_id, double scale, const T* X, T* Y) {
+    int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int kb = rowptr[r], ke = rowptr[r + 1];
+    int rid = node_id ? node_id[r] : r;
+    for (int c = lane; c < k; c += 32) {
+        double acc = 0.0;
+        for (int e = kb; e < ke; e++) {
+            int cc = col[e];
+            int cid = node_id ? node_id[cc] : cc;
+            double x = (double)X[(size_t)cid * k + c];
+            acc += VALUED ? (double)vals[e] * x : -x;
+        }
+        if (!VALUED) acc += (double)(ke - kb) * (double)X[(size_t)rid * k + c];
+        Y[(size_t)rid * k + c] = (T)(scale * acc);
+    }
+}
+
+__global__ void k_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, int fp64, void* out) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    int64_t i = idx / k;
+    int c = (int)(idx % k);
+    double v = rademacher_entry(seed_mixed, (uint64_t)(col_begin + c), (uint64_t)i);
+    if (fp64) ((double*)out)[idx] = v;
+    else ((float*)out)[idx] = (float)v;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+
+template <typename T>
+static int panel_width_ok(int ks) {
+    if (sizeof(T) == 4) return ks == 8 || ks == 16 || ks == 32;
+    return ks == 4 || ks == 8 || ks == 16;
+}
+
+#define VNE_DISPATCH_KS(T, ks, CALL)                                   \
+    do {                                                               \
+        if (sizeof(T) == 4) {                                          \
+            if ((ks) == 8) { constexpr int KS = 8; CALL; }             \
+            else if ((ks) == 16) { constexpr int KS = 16; CALL; }      \
+            else if ((ks) == 32) { constexpr int KS = 32; CALL; }      \
+            else return cudaErrorInvalidValue;                         \
+        } else {                                                       \
+            if ((ks) == 4) { constexpr int KS = 4; CALL; }             \
+            else if ((ks) == 8) { constexpr int KS = 8; CALL; }        \
+            else if ((ks) == 16) { constexpr int KS = 16; CALL; }      \
+            else return cudaErrorInvalidValue;                         \
+        }                                                              \
+    } while (0)
+
+template <typename T>
+cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream_t st) {
+    dim3 grid(panels * p.tiles_per_panel);
+    if (p.desing) VNE_DISPATCH_KS(T, ks, (k_start_mean<T, KS><<<grid, VNE_THREADS, 0, st>>>(p)));
+    VNE_DISPATCH_KS(T, ks, (k_start_center<T, KS><<<grid, VNE_THREADS, 0, st>>>(p)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step(const StepParams<T>& p, int ks, int panels, bool valued, cudaStream_t st) {
+    dim3 grid(panels * p.ctas_per_panel);
+    if (valued) VNE_DISPATCH_KS(T, ks, (k_step<T, KS, true><<<grid, VNE_THREADS, 0, st>>>(p)));
+    else VNE_DISPATCH_KS(T, ks, (k_step<T, KS, false><<<grid, VNE_THREADS, 0, st>>>(p)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const StepParams<T>& p, int ks, int panels, cudaStream_t st) {
+    dim3 grid(panels * p.tiles_per_panel);
+    VNE_DISPATCH_KS(T, ks, (k_update<T, KS><<<grid, VNE_THREADS, 0, st>>>(p)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reorth(const ReorthParams<T>& p, const ReorthCoefParams& c, int ks, cudaStream_t st) {
+    if (p.j <= 0) return cudaSuccess;
+    VNE_DISPATCH_KS(T, ks, (k_reorth_dots<T, KS><<<dim3(p.panels * p.tiles_per_panel * p.j), VNE_THREADS, 0, st>>>(p)));
+    int total = c.panels * c.j * ks;
+    VNE_DISPATCH_KS(T, ks, (k_reorth_coef<KS><<<dim3((total + 255) / 256), 256, 0, st>>>(c)));
+    VNE_DISPATCH_KS(T, ks, (k_reorth_apply<T, KS><<<dim3(p.panels * p.tiles_per_panel), VNE_THREADS, 0, st>>>(p)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_recover(const RecoverParams<T>& p, int ks, int panels, cudaStream_t st) {
+    size_t smem = (size_t)p.m * ks * sizeof(double);
+    dim3 grid(panels * p.tiles_per_panel);
+    VNE_DISPATCH_KS(T, ks, (k_recover<T, KS><<<grid, VNE_THREADS, smem, st>>>(p)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spmm_plain(const int32_t* rowptr, const int32_t* col, const T* vals, int n, int k,
+                              const int32_t* node_id, double scale, const T* X, T* Y, cudaStream_t st) {
+    dim3 grid((n + 7) / 8);
+    if (vals) k_spmm_plain<T, true><<<grid, 256, 0, st>>>(rowptr, col, vals, n, k, node_id, scale, X, Y);
+    else k_spmm_plain<T, false><<<grid, 256, 0, st>>>(rowptr, col, vals, n, k, node_id, scale, X, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, int fp64, void* out,
+                                   cudaStream_t st) {
+    int64_t total = n * (int64_t)k;
+    if (total == 0) return cudaSuccess;
+    k_rademacher_fill<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(seed_mixed, n, col_begin, k, fp64, out);
+    return cudaGetLastError();
+}
+
+#define VNE_INST(T)                                                                                        \
+    template cudaError_t launch_start<T>(const StartParams<T>&, int, int, cudaStream_t);                   \
+    template cudaError_t launch_step<T>(const StepParams<T>&, int, int, bool, cudaStream_t);               \
+    template cudaError_t launch_update<T>(const StepParams<T>&, int, int, cudaStream_t);                   \
+    template cudaError_t launch_reorth<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
+    template cudaError_t launch_recover<T>(const RecoverParams<T>&, int, int, cudaStream_t);               \
+    template cudaError_t launch_spmm_plain<T>(const int32_t*, const int32_t*, const T*, int, int,          \
+                                              const int32_t*, double, const T*, T*, cudaStream_t);
+VNE_INST(float)
+VNE_INST(double)
+
+}  // namespace vne

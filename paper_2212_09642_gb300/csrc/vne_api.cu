@@ -1,0 +1,1251 @@
+// libvne C ABI: contexts, density matrices, the block Krylov engine and the
+// trace estimators of Benzi, Rinelli, Simunec (arXiv 2212.09642).
+//
+// Engine overview.  A "problem" is a packed CSR operator M (one graph, or
+// several graphs block-diagonally, each a segment) with a warp-level work
+// schedule.  A block of K probe columns runs m Lanczos steps at once: per
+// step one fused SpMM kernel and one update kernel (kernels_lanczos.cu), all
+// launched back to back on the context stream with no host synchronisation;
+// then one FP64 tridiagonal-quadrature kernel gives psi for every column.
+//
+// Probe generator (identical to the oracle's, written independently):
+//   mix64 = SplitMix64 output mixer (Steele, Lea, Flood 2014),
+//   s = mix64(seed + 0x9E3779B97F4A7C15),
+//   h(j, i) = mix64((((j << 32) | i) ^ s) + 0x9E3779B97F4A7C15),
+//   entry = +1 if the top bit of h is 0 else -1,
+// j the global probe column, i the node id in the caller's numbering.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/vne.h"
+#include "host_graph.h"
+#include "kernels.h"
+
+using namespace vne;
+
+// ---------------------------------------------------------------------------
+// context, errors, workspace
+
+struct WsBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-kernel live timing (CUDA events on the context stream around each
+// launch of the step and update kernels), enabled by vne_ctx_profile.
+struct KernelStat {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;  // algorithmic bytes of the timed launches
+};
+
+struct vne_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    std::map<std::string, WsBuf> ws;
+    int64_t launches = 0;  // kernels launched by this context
+    bool profile = false;
+    KernelStat stat[2];    // 0: step (SpMM) kernel, 1: update kernel
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Pending> pending;
+    size_t ev_next = 0;
+};
+
+struct Problem;
+
+struct vne_matrix {
+    vne_ctx* ctx = nullptr;
+    int64_t n = 0, nnz = 0;
+    bool fp64 = false, pattern = false, desing = false;
+    double trace = 0.0, scale = 1.0, normM = 0.0;
+    std::vector<int64_t> h_rowptr;  // packed (possibly relabelled) numbering
+    std::vector<int32_t> h_col;
+    std::vector<double> h_vals;     // valued matrices only
+    std::vector<int32_t> perm;      // packed row -> caller node id (empty: identity)
+    int32_t* d_rowptr = nullptr;
+    int32_t* d_col = nullptr;
+    void* d_vals = nullptr;
+    int32_t* d_node_id = nullptr;
+    Problem* prob = nullptr;        // cached schedule
+    int prob_item_nnz = -1;
+};
+
+namespace {
+
+struct Error {
+    vne_status code;
+};
+
+void set_err(vne_ctx* ctx, const char* fmt, ...) {
+    if (!ctx) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+}
+
+#define VNE_TRY_CUDA(ctx, call)                                                                        \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            set_err((ctx), "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            throw Error{e_ == cudaErrorMemoryAllocation ? VNE_ENOMEM : VNE_EDEVICE};                     \
+        }                                                                                              \
+    } while (0)
+
+#define VNE_REQUIRE(ctx, cond, code, ...)     \
+    do {                                      \
+        if (!(cond)) {                        \
+            set_err((ctx), __VA_ARGS__);      \
+            throw Error{(code)};              \
+        }                                     \
+    } while (0)
+
+// Workspace buffers grow on demand and are kept for the life of the context,
+// so the hot loop never allocates.
+void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero = false) {
+    WsBuf& b = ctx->ws[name];
+    if (b.bytes < bytes) {
+        if (b.ptr) cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        size_t alloc = std::max<size_t>(bytes, 256);
+        VNE_TRY_CUDA(ctx, cudaMalloc(&b.ptr, alloc));
+        b.bytes = alloc;
+    }
+    if (zero && bytes) VNE_TRY_CUDA(ctx, cudaMemsetAsync(b.ptr, 0, bytes, ctx->stream));
+    return b.ptr;
+}
+
+template <typename T>
+T* ws_get_t(vne_ctx* ctx, const std::string& name, size_t count, bool zero = false) {
+    return (T*)ws_get(ctx, name, count * sizeof(T), zero);
+}
+
+template <typename T>
+T* upload(vne_ctx* ctx, const std::string& name, const std::vector<T>& v) {
+    T* d = ws_get_t<T>(ctx, name, std::max<size_t>(v.size(), 1));
+    if (!v.empty())
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return d;
+}
+
+cudaEvent_t ctx_event(vne_ctx* ctx) {
+    if (ctx->ev_next == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        VNE_TRY_CUDA(ctx, cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_next++];
+}
+
+// Resolve the recorded event pairs (the stream must be synchronised).
+void ctx_flush_profile(vne_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        VNE_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, p.a, p.b));
+        ctx->stat[p.kind].launches++;
+        ctx->stat[p.kind].ms += ms;
+        ctx->stat[p.kind].bytes += p.bytes;
+    }
+    ctx->pending.clear();
+    ctx->ev_next = 0;
+}
+
+uint64_t mix64_host(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+uint64_t seed_mix(uint64_t seed) { return mix64_host(seed + 0x9E3779B97F4A7C15ULL); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// schedule ("plan") of a packed operator
+
+struct Problem {
+    bool fp64 = false, valued = false;
+    int32_t n_total = 0, nseg = 0;
+    int64_t nnz_total = 0;
+    const int32_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const void* vals = nullptr;
+    const int32_t* node_id = nullptr;
+    std::vector<SegInfo> segs;
+    std::vector<WorkItem> items;
+    std::vector<HubRow> hubs;
+    std::vector<int32_t> cta_seg;
+    std::vector<RowTile> tiles;
+    int32_t hub_slots = 0;
+    // device copies (owned)
+    SegInfo* d_segs = nullptr;
+    WorkItem* d_items = nullptr;
+    HubRow* d_hubs = nullptr;
+    int32_t* d_cta_seg = nullptr;
+    RowTile* d_tiles = nullptr;
+    std::vector<void*> owned;  // extra device buffers owned by the problem (batch packing)
+    ~Problem() {
+        cudaFree(d_segs);
+        cudaFree(d_items);
+        cudaFree(d_hubs);
+        cudaFree(d_cta_seg);
+        cudaFree(d_tiles);
+        for (void* p : owned) cudaFree(p);
+    }
+    int ctas_per_panel() const { return (int)(items.size() / VNE_WARPS); }
+    int tiles_per_panel() const { return (int)tiles.size(); }
+};
+
+namespace {
+
+const int kTileRows = 4096;
+
+// Work items of one segment (rows [row_begin, row_begin + rows) of the packed
+// CSR): runs of short rows with about `target` nonzeros (at most 64 rows),
+// and rows longer than `long_thresh` split into chunks of `chunk` nonzeros.
+void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_t seg, int target, Problem& P) {
+    const int64_t long_thresh = std::max(2 * target, 128);
+    const int64_t chunk = std::max(target, 64);
+    const int max_rows = 64;
+    const size_t first_item = P.items.size();
+    int32_t blk_start = -1, blk_rows = 0;
+    int64_t blk_nnz = 0;
+    auto flush = [&]() {
+        if (blk_rows > 0) P.items.push_back(WorkItem{blk_start, blk_rows, 0, 0});
+        blk_start = -1;
+        blk_rows = 0;
+        blk_nnz = 0;
+    };
+    for (int32_t r = row_begin; r < row_begin + rows; r++) {
+        int64_t deg = rowptr[r + 1] - rowptr[r];
+        if (deg > long_thresh) {
+            flush();
+            int32_t nch = (int32_t)((deg + chunk - 1) / chunk);
+            int32_t h = (int32_t)P.hubs.size();
+            P.hubs.push_back(HubRow{r, nch, P.hub_slots, seg});
+            P.hub_slots += nch;
+            for (int32_t c = 0; c < nch; c++) {
+                int64_t b = rowptr[r] + c * chunk, e = std::min<int64_t>(rowptr[r + 1], b + chunk);
+                P.items.push_back(WorkItem{h, -(c + 1), (int32_t)b, (int32_t)e});
+            }
+            continue;
+        }
+        if (blk_rows == 0) blk_start = r;
+        blk_rows++;
+        blk_nnz += deg;
+        if (blk_nnz >= target || blk_rows >= max_rows) flush();
+    }
+    flush();
+    while ((P.items.size() - first_item) % VNE_WARPS) P.items.push_back(WorkItem{0, 0, 0, 0});
+    SegInfo& sg = P.segs[seg];
+    sg.cta_begin = (int32_t)(first_item / VNE_WARPS);
+    sg.cta_count = (int32_t)((P.items.size() - first_item) / VNE_WARPS);
+    for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
+    sg.tile_begin = (int32_t)P.tiles.size();
+    for (int32_t r = row_begin; r < row_begin + rows; r += kTileRows)
+        P.tiles.push_back(RowTile{r, std::min(row_begin + rows, r + kTileRows), seg, 0});
+    sg.tile_count = (int32_t)P.tiles.size() - sg.tile_begin;
+}
+
+template <typename T>
+T* dev_copy(vne_ctx* ctx, const std::vector<T>& v) {
+    T* d = nullptr;
+    size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    VNE_TRY_CUDA(ctx, cudaMalloc(&d, bytes));
+    if (!v.empty()) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return d;
+}
+
+void problem_upload(vne_ctx* ctx, Problem& P) {
+    P.d_segs = dev_copy(ctx, P.segs);
+    P.d_items = dev_copy(ctx, P.items);
+    P.d_hubs = dev_copy(ctx, P.hubs);
+    P.d_cta_seg = dev_copy(ctx, P.cta_seg);
+    P.d_tiles = dev_copy(ctx, P.tiles);
+}
+
+double default_tau(bool fp64) { return fp64 ? 1e-13 : 1e-10; }
+
+int default_item_nnz(const vne_options* o) { return (o && o->item_nnz > 0) ? o->item_nnz : 256; }
+
+Problem* matrix_problem(vne_matrix* M, const vne_options* opt) {
+    int target = default_item_nnz(opt);
+    double taurel = (opt && opt->breakdown_tol > 0) ? opt->breakdown_tol : default_tau(M->fp64);
+    if (M->prob && M->prob_item_nnz == target && M->prob->segs[0].tau == taurel * M->normM) return M->prob;
+    delete M->prob;
+    M->prob = nullptr;
+    std::unique_ptr<Problem> P(new Problem());
+    P->fp64 = M->fp64;
+    P->valued = !M->pattern;
+    P->n_total = (int32_t)M->n;
+    P->nnz_total = M->nnz;
+    P->nseg = 1;
+    P->rowptr = M->d_rowptr;
+    P->col = M->d_col;
+    P->vals = M->d_vals;
+    P->node_id = M->d_node_id;
+    SegInfo s{};
+    s.row_begin = 0;
+    s.rows = (int32_t)M->n;
+    s.scale = M->scale;
+    s.tau = taurel * M->normM;
+    P->segs.push_back(s);
+    plan_segment(M->h_rowptr.data(), 0, (int32_t)M->n, 0, target, *P);
+    problem_upload(M->ctx, *P);
+    M->prob = P.release();
+    M->prob_item_nnz = target;
+    return M->prob;
+}
+
+int choose_panel(bool fp64, const vne_options* opt, int64_t n) {
+    if (opt && opt->panel > 0) return opt->panel;
+    if (fp64) return 8;
+    // keep one panel (n * KS * 4 bytes) comfortably inside L2
+    if (n * 16 * 4 <= (int64_t)64 << 20) return 16;
+    return 8;
+}
+
+// ---------------------------------------------------------------------------
+// block Krylov engine
+
+struct BlockOut {
+    int K = 0, Kp = 0, ks = 0, panels = 0, m = 0, SK = 0;
+    double* alpha = nullptr;   // [m][SK]
+    double* beta = nullptr;    // [m][SK]
+    double* sigma = nullptr;   // [m+1][SK]
+    double* norm2 = nullptr;   // [SK]
+    double* psi = nullptr;     // [SK]
+    double* scale = nullptr;   // [SK]
+    void* basis = nullptr;     // slot 0 (when kept)
+    size_t slot_stride = 0;    // elements
+};
+
+template <typename T>
+void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
+               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out) {
+    cudaStream_t st = ctx->stream;
+    const int panels = (K + ks - 1) / ks;
+    const int Kp = panels * ks;
+    const int S = P.nseg;
+    const int SK = S * Kp;
+    const size_t slot_elems = (size_t)Kp * P.n_total;
+    const bool store_all = keep_basis || reorth;
+    const int nslots = store_all ? m + 1 : 2;
+    VNE_REQUIRE(ctx, reorth == false || S == 1, VNE_EUNSUPPORTED, "full reorthogonalisation needs a single matrix");
+    T* slots = ws_get_t<T>(ctx, tag + ".slots", slot_elems * nslots);
+    T* u = ws_get_t<T>(ctx, "u", slot_elems);
+    double* alpha = ws_get_t<double>(ctx, tag + ".alpha", (size_t)m * SK, true);
+    double* beta = ws_get_t<double>(ctx, tag + ".beta", (size_t)m * SK, true);
+    double* sigma = ws_get_t<double>(ctx, tag + ".sigma", (size_t)(m + 1) * SK, true);
+    double* norm2 = ws_get_t<double>(ctx, tag + ".norm2", SK);
+    double* mean = ws_get_t<double>(ctx, "mean", SK);
+    double* psi = ws_get_t<double>(ctx, tag + ".psi", SK);
+    const int ctas = P.ctas_per_panel(), tiles = P.tiles_per_panel();
+    double* part = ws_get_t<double>(ctx, "part", (size_t)panels * std::max(ctas, tiles) * ks);
+    uint32_t* counter = ws_get_t<uint32_t>(ctx, "counter", (size_t)panels * S, true);
+    const int nh = (int)P.hubs.size();
+    const int64_t nnz_total = P.nnz_total;
+    T* hub_part = ws_get_t<T>(ctx, "hub_part", (size_t)panels * std::max(P.hub_slots, 1) * ks);
+    uint32_t* hub_cnt = ws_get_t<uint32_t>(ctx, "hub_cnt", (size_t)panels * std::max(nh, 1), true);
+    // per-column scale (segment scale) for the quadrature
+    std::vector<double> hscale(SK);
+    for (int s = 0; s < S; s++)
+        for (int c = 0; c < Kp; c++) hscale[(size_t)s * Kp + c] = P.segs[s].scale;
+    double* dscale = upload(ctx, tag + ".scale", hscale);
+
+    auto slot = [&](int j) -> T* {  // slot holding w_j, j >= 1
+        int idx = store_all ? (j - 1) : ((j - 1) & 1);
+        return slots + (size_t)idx * slot_elems;
+    };
+
+    StartParams<T> sp{};
+    sp.src = src;
+    sp.panel_src = panel_src;
+    sp.node_id = P.node_id;
+    sp.seg = P.d_segs;
+    sp.nseg = S;
+    sp.K = Kp;
+    sp.n_total = P.n_total;
+    sp.tiles_per_panel = tiles;
+    sp.tiles = P.d_tiles;
+    sp.desing = desing ? 1 : 0;
+    sp.w1 = slot(1);
+    sp.mean = mean;
+    sp.norm2 = norm2;
+    sp.sig1 = sigma;
+    sp.part = part;
+    sp.counter = counter;
+    VNE_TRY_CUDA(ctx, launch_start<T>(sp, ks, panels, st));
+    ctx->launches += desing ? 2 : 1;
+
+    StepParams<T> p{};
+    p.rowptr = P.rowptr;
+    p.col = P.col;
+    p.vals = (const T*)P.vals;
+    p.n_total = P.n_total;
+    p.K = Kp;
+    p.nseg = S;
+    p.seg = P.d_segs;
+    p.items = P.d_items;
+    p.ctas_per_panel = ctas;
+    p.cta_seg = P.d_cta_seg;
+    p.hubs = P.d_hubs;
+    p.nhubs = std::max(nh, 1);
+    p.hub_slots = std::max(P.hub_slots, 1);
+    p.hub_part = hub_part;
+    p.hub_cnt = hub_cnt;
+    p.tiles = P.d_tiles;
+    p.tiles_per_panel = tiles;
+    p.u = u;
+    p.part = part;
+    p.counter = counter;
+    double* rcoef = nullptr;
+    double* rpart = nullptr;
+    if (reorth) {
+        rcoef = ws_get_t<double>(ctx, "reorth.coef", (size_t)m * Kp);
+        rpart = ws_get_t<double>(ctx, "reorth.part", (size_t)panels * m * tiles * ks);
+    }
+    for (int j = 1; j <= m; j++) {
+        p.first = (j == 1);
+        p.renorm = 0;
+        p.w_cur = slot(j);
+        p.w_prev = (j > 1) ? slot(j - 1) : slot(j);
+        p.w_next = slot(j + 1);
+        p.sig_cur = sigma + (size_t)(j - 1) * SK;
+        p.sig_prev = (j > 1) ? sigma + (size_t)(j - 2) * SK : sigma;
+        p.beta_prev = (j > 1) ? beta + (size_t)(j - 2) * SK : beta;
+        p.alpha = alpha + (size_t)(j - 1) * SK;
+        p.beta = beta + (size_t)(j - 1) * SK;
+        p.sig_next = sigma + (size_t)j * SK;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (ctx->profile) {
+            e0 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
+        }
+        VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, st));
+        if (ctx->profile) {
+            e1 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+        }
+        VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
+        ctx->launches += 2;
+        if (ctx->profile) {
+            e2 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e2, st));
+            // algorithmic bytes: CSR structure (+ values) once per panel, the
+            // gathered block w_j once, w_{j-1} (j > 1) and u once each
+            const double es = sizeof(T);
+            double csr = 4.0 * (P.n_total + 1) + (double)nnz_total * (4.0 + (P.valued ? es : 0.0));
+            double vec = (double)P.n_total * ks * es;
+            double step_bytes = panels * (csr + vec * (j > 1 ? 3.0 : 2.0));
+            double upd_bytes = panels * vec * 3.0;
+            ctx->pending.push_back({0, e0, e1, step_bytes});
+            ctx->pending.push_back({1, e1, e2, upd_bytes});
+        }
+        if (reorth && j < m + 1) {
+            ReorthParams<T> rp{};
+            rp.basis = slots;
+            rp.slot_stride = slot_elems;
+            rp.w = slot(j + 1);
+            rp.j = j;
+            rp.K = Kp;
+            rp.n_total = P.n_total;
+            rp.panels = panels;
+            rp.tiles_per_panel = tiles;
+            rp.tiles = P.d_tiles;
+            rp.part = rpart;
+            rp.coef = rcoef;
+            ReorthCoefParams cp{};
+            cp.part = rpart;
+            cp.sig = sigma;
+            cp.coef = rcoef;
+            cp.j = j;
+            cp.K = Kp;
+            cp.panels = panels;
+            cp.tiles_per_panel = tiles;
+            for (int pass = 0; pass < 2; pass++) VNE_TRY_CUDA(ctx, launch_reorth<T>(rp, cp, ks, st));
+            p.renorm = 1;
+            VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
+            ctx->launches += 7;
+        }
+    }
+    VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m, SK, psi, st));
+    ctx->launches += 1;
+    out.K = K;
+    out.Kp = Kp;
+    out.ks = ks;
+    out.panels = panels;
+    out.m = m;
+    out.SK = SK;
+    out.alpha = alpha;
+    out.beta = beta;
+    out.sigma = sigma;
+    out.norm2 = norm2;
+    out.psi = psi;
+    out.scale = dscale;
+    out.basis = slots;
+    out.slot_stride = slot_elems;
+}
+
+std::vector<double> download(vne_ctx* ctx, const double* d, size_t count) {
+    std::vector<double> h(count);
+    if (count) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(h.data(), d, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!ctx->pending.empty()) ctx_flush_profile(ctx);
+    return h;
+}
+
+bool want_reorth(const vne_matrix* M, const vne_options* o) {
+    int r = o ? o->reorth : -1;
+    if (r < 0) return M->fp64;
+    return r != 0;
+}
+
+int block_limit(const vne_options* o) { return (o && o->block > 0) ? o->block : 256; }
+
+vne_options defaults() {
+    vne_options o;
+    vne_options_default(&o);
+    return o;
+}
+
+void check_mat(vne_matrix* M) {
+    if (!M) throw Error{VNE_EINVAL};
+}
+
+template <typename T>
+void check_ks(vne_ctx* ctx, int ks) {
+    bool ok = sizeof(T) == 4 ? (ks == 8 || ks == 16 || ks == 32) : (ks == 4 || ks == 8 || ks == 16);
+    VNE_REQUIRE(ctx, ok, VNE_EINVAL, "panel width %d not supported for this precision", ks);
+}
+
+// Quadratic forms of one source over all its columns, in blocks.
+template <typename T>
+std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource src, int ncols, int m) {
+    vne_ctx* ctx = M->ctx;
+    Problem* P = matrix_problem(M, o);
+    int ks = choose_panel(M->fp64, o, M->n);
+    check_ks<T>(ctx, ks);
+    int lim = block_limit(o);
+    bool reorth = want_reorth(M, o);
+    std::vector<double> psi(ncols);
+    for (int b0 = 0; b0 < ncols; b0 += lim) {
+        int K = std::min(lim, ncols - b0);
+        StartSource s = src;
+        s.ncols = K;
+        if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
+        if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
+        BlockOut out;
+        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+        std::vector<double> h = download(ctx, out.psi, K);
+        std::copy(h.begin(), h.end(), psi.begin() + b0);
+    }
+    return psi;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+#define VNE_API_BEGIN try {
+#define VNE_API_END(ctx)                                  \
+    }                                                     \
+    catch (const Error& e) {                              \
+        return e.code;                                    \
+    }                                                     \
+    catch (const std::bad_alloc&) {                       \
+        set_err((ctx), "host allocation failed");         \
+        return VNE_ENOMEM;                                \
+    }                                                     \
+    catch (...) {                                         \
+        set_err((ctx), "unexpected internal error");      \
+        return VNE_EDEVICE;                               \
+    }                                                     \
+    return VNE_OK;
+
+extern "C" void vne_options_default(vne_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->reorth = -1;
+    o->n_inf_poles = 2;
+    o->cg_max_iter = 10000;
+    o->cg_tol = 1e-8;
+}
+
+extern "C" const char* vne_version(void) { return "vne 0.1 (sm_103a)"; }
+
+extern "C" vne_status vne_ctx_create(int32_t device, vne_ctx** out) {
+    if (!out) return VNE_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) return VNE_EDEVICE;
+    if (device < 0 || device >= count) return VNE_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return VNE_EDEVICE;
+    vne_ctx* c = new (std::nothrow) vne_ctx();
+    if (!c) return VNE_ENOMEM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
+    if (!ctx) return VNE_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    for (auto& kv : ctx->ws)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    delete ctx;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_set_stream(vne_ctx* ctx, void* stream) {
+    if (!ctx) return VNE_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return VNE_OK;
+}
+
+extern "C" const char* vne_last_error(const vne_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                     const double* vals, uint32_t flags, vne_matrix** out) {
+    if (!ctx || !out) return VNE_EINVAL;
+    *out = nullptr;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    const bool fp64 = flags & VNE_FP64, fp32 = flags & VNE_FP32;
+    VNE_REQUIRE(ctx, fp64 != fp32, VNE_EINVAL, "exactly one of VNE_FP64 / VNE_FP32 is required");
+    VNE_REQUIRE(ctx, n >= 1 && n < (int64_t)INT32_MAX, VNE_EINVAL, "n = %lld out of range", (long long)n);
+    VNE_REQUIRE(ctx, row_ptr && col_idx, VNE_EINVAL, "row_ptr and col_idx are required");
+    std::unique_ptr<vne_matrix> M(new vne_matrix());
+    M->ctx = ctx;
+    M->n = n;
+    M->fp64 = fp64;
+    M->pattern = (vals == nullptr);
+    std::vector<int64_t> rp(n + 1);
+    const bool dev = flags & VNE_INPUT_DEVICE;
+    if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    else memcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t));
+    VNE_REQUIRE(ctx, rp[0] == 0, VNE_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t i = 0; i < n; i++) VNE_REQUIRE(ctx, rp[i + 1] >= rp[i], VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
+    const int64_t nnz = rp[n];
+    VNE_REQUIRE(ctx, nnz < (int64_t)INT32_MAX, VNE_EINVAL, "nnz = %lld exceeds int32", (long long)nnz);
+    std::vector<int32_t> ci(nnz);
+    std::vector<double> va;
+    if (nnz) {
+        if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(ci.data(), col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        else memcpy(ci.data(), col_idx, nnz * sizeof(int32_t));
+    }
+    if (vals) {
+        va.resize(nnz);
+        if (nnz) {
+            if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(va.data(), vals, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+            else memcpy(va.data(), vals, nnz * sizeof(double));
+        }
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            VNE_REQUIRE(ctx, ci[k] >= 0 && ci[k] < n, VNE_EINVAL, "column index %d out of range in row %lld", ci[k], (long long)i);
+            if (!vals) VNE_REQUIRE(ctx, ci[k] != i, VNE_EINVAL, "self-loop at node %lld (pattern Laplacian)", (long long)i);
+        }
+    if (flags & VNE_CHECK_SYMMETRY) {
+        VNE_REQUIRE(ctx, !vals, VNE_EUNSUPPORTED, "VNE_CHECK_SYMMETRY supports pattern matrices only");
+        for (int64_t i = 0; i < n; i++) std::sort(ci.begin() + rp[i], ci.begin() + rp[i + 1]);
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+                int32_t j = ci[k];
+                bool found = std::binary_search(ci.begin() + rp[j], ci.begin() + rp[j + 1], (int32_t)i);
+                VNE_REQUIRE(ctx, found, VNE_ENOTSYM, "pattern not symmetric: (%lld,%d)", (long long)i, j);
+            }
+    }
+    // trace, Gershgorin bound of the stored operator M, scale
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < n; i++) maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
+    if (!vals) {
+        M->trace = (double)nnz;
+        M->normM = 2.0 * (double)maxdeg;
+        M->desing = true;
+    } else {
+        double tr = 0.0, nm = 0.0;
+        for (int64_t i = 0; i < n; i++) {
+            double rs = 0.0;
+            for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+                if (ci[k] == i) tr += va[k];
+                rs += fabs(va[k]);
+            }
+            nm = std::max(nm, rs);
+        }
+        M->trace = tr;
+        M->normM = nm;
+        M->desing = (flags & VNE_IS_LAPLACIAN) != 0;
+    }
+    bool normalize = !vals || (flags & VNE_NORMALIZE_TRACE);
+    if (normalize) {
+        VNE_REQUIRE(ctx, M->trace > 0.0, VNE_EINVAL, "trace must be positive to normalise (got %g)", M->trace);
+        M->scale = 1.0 / M->trace;
+    } else {
+        M->scale = 1.0;
+    }
+    // optional degree-descending relabelling (entropy is permutation invariant)
+    if (flags & VNE_REORDER) {
+        std::vector<int32_t> order = degree_order(n, rp.data());  // new -> old
+        std::vector<int32_t> inv(n);
+        for (int64_t i = 0; i < n; i++) inv[order[i]] = (int32_t)i;
+        std::vector<int64_t> rp2(n + 1, 0);
+        std::vector<int32_t> ci2(nnz);
+        std::vector<double> va2(vals ? nnz : 0);
+        for (int64_t i = 0; i < n; i++) rp2[i + 1] = rp2[i] + (rp[order[i] + 1] - rp[order[i]]);
+        std::vector<std::pair<int32_t, double>> tmp;
+        for (int64_t i = 0; i < n; i++) {
+            int32_t o = order[i];
+            tmp.clear();
+            for (int64_t k = rp[o]; k < rp[o + 1]; k++) tmp.emplace_back(inv[ci[k]], vals ? va[k] : 0.0);
+            std::sort(tmp.begin(), tmp.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) { return a.first < b.first; });
+            for (size_t q = 0; q < tmp.size(); q++) {
+                ci2[rp2[i] + q] = tmp[q].first;
+                if (vals) va2[rp2[i] + q] = tmp[q].second;
+            }
+        }
+        rp.swap(rp2);
+        ci.swap(ci2);
+        va.swap(va2);
+        M->perm = order;
+    }
+    M->nnz = nnz;
+    // device copies: int32 row pointers, int32 columns, values in the path precision
+    std::vector<int32_t> rp32(n + 1);
+    for (int64_t i = 0; i <= n; i++) rp32[i] = (int32_t)rp[i];
+    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
+    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp32.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_col, ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (vals) {
+        size_t es = fp64 ? 8 : 4;
+        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
+        if (fp64) {
+            if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_vals, va.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            std::vector<float> vf(va.begin(), va.end());
+            if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_vals, vf.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
+            VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    if (!M->perm.empty()) {
+        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_node_id, n * sizeof(int32_t)));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, M->perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    M->h_rowptr.swap(rp);
+    M->h_col.swap(ci);
+    M->h_vals.swap(va);
+    *out = M.release();
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_matrix_destroy(vne_matrix* M) {
+    if (!M) return VNE_EINVAL;
+    cudaSetDevice(M->ctx->device);
+    if (M->ctx->stream) cudaStreamSynchronize(M->ctx->stream);
+    delete M->prob;
+    cudaFree(M->d_rowptr);
+    cudaFree(M->d_col);
+    cudaFree(M->d_vals);
+    cudaFree(M->d_node_id);
+    delete M;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_matrix_info(const vne_matrix* M, int64_t* n, int64_t* nnz, double* trace, double* norm_bound) {
+    if (!M) return VNE_EINVAL;
+    if (n) *n = M->n;
+    if (nnz) *nnz = M->nnz;
+    if (trace) *trace = M->trace;
+    if (norm_bound) *norm_bound = M->normM * M->scale;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, int32_t k, uint32_t vec_flags,
+                              int32_t krylov_steps, const double* poles, int32_t num_poles, const vne_options* opt,
+                              double* psi, double* alpha_beta) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, k >= 1 && vectors && psi, VNE_EINVAL, "need k >= 1, vectors and psi");
+    VNE_REQUIRE(ctx, poles == nullptr, VNE_EUNSUPPORTED, "rational mode is provided by vne_quadform_rational");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    const int m = krylov_steps;
+    const double* dvec = vectors;
+    if (!(vec_flags & VNE_VECTORS_DEVICE)) {
+        double* d = ws_get_t<double>(ctx, "qb.input", (size_t)M->n * k);
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, vectors, (size_t)M->n * k * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        dvec = d;
+    }
+    Problem* P = matrix_problem(M, &o);
+    int ks = choose_panel(M->fp64, &o, M->n);
+    bool reorth = want_reorth(M, &o);
+    int lim = block_limit(&o);
+    for (int b0 = 0; b0 < k; b0 += lim) {
+        int K = std::min(lim, k - b0);
+        StartSource s{};
+        s.kind = SRC_DENSE64;
+        s.ncols = K;
+        s.ld = k;
+        s.dense = dvec + b0;
+        BlockOut out;
+        if (M->fp64) {
+            check_ks<double>(ctx, ks);
+            run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+        } else {
+            check_ks<float>(ctx, ks);
+            run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+        }
+        std::vector<double> h = download(ctx, out.psi, K);
+        std::copy(h.begin(), h.end(), psi + b0);
+        if (alpha_beta) {
+            std::vector<double> a = download(ctx, out.alpha, (size_t)m * out.SK);
+            std::vector<double> b = download(ctx, out.beta, (size_t)m * out.SK);
+            for (int c = 0; c < K; c++)
+                for (int j = 0; j < m; j++) {
+                    alpha_beta[(size_t)(b0 + c) * 2 * m + j] = a[(size_t)j * out.SK + c] * M->scale;
+                    alpha_beta[(size_t)(b0 + c) * 2 * m + m + j] = b[(size_t)j * out.SK + c] * M->scale;
+                }
+        }
+    }
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_entropy_hutchinson(vne_matrix* M, int32_t num_vectors, int32_t krylov_steps, uint64_t seed,
+                                  const vne_options* opt, double* estimate, double* std_error, double* psi_out) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, num_vectors >= 1 && estimate, VNE_EINVAL, "need num_vectors >= 1 and estimate");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    StartSource s{};
+    s.kind = SRC_RADEMACHER;
+    s.seed_mixed = seed_mix(seed);
+    s.col_begin = 0;
+    std::vector<double> psi = M->fp64 ? quadforms<double>(M, &o, s, num_vectors, krylov_steps)
+                                      : quadforms<float>(M, &o, s, num_vectors, krylov_steps);
+    double mean = 0.0;
+    for (double v : psi) mean += v;
+    mean /= num_vectors;
+    double var = 0.0;
+    for (double v : psi) var += (v - mean) * (v - mean);
+    var = num_vectors > 1 ? var / (num_vectors - 1) : 0.0;
+    *estimate = mean;
+    if (std_error) *std_error = sqrt(var / num_vectors);
+    if (psi_out) std::copy(psi.begin(), psi.end(), psi_out);
+    VNE_API_END(ctx)
+}
+
+namespace {
+
+__global__ void k_gamma(const double* norm2, const double* sigma, const double* zvec, int m, int K, double* gamma) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * K) return;
+    int c = idx % K;
+    gamma[idx] = sqrt(norm2[c]) * sigma[idx] * zvec[idx];
+}
+
+template <typename T>
+void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, uint64_t seed, double* estimate,
+                  double* parts) {
+    vne_ctx* ctx = M->ctx;
+    cudaStream_t st = ctx->stream;
+    Problem* P = matrix_problem(M, o);
+    const int n = (int)M->n;
+    int ks = choose_panel(M->fp64, o, M->n);
+    check_ks<T>(ctx, ks);
+    VNE_REQUIRE(ctx, Nr >= 1 && Nr <= 128 && NH >= 0 && NH <= 4096, VNE_EINVAL, "need 1 <= N_r <= 128, 0 <= N_H");
+    const uint64_t sm = seed_mix(seed);
+    // 1. sketch: Y = f(A) Omega by the Lanczos matvec approximation, basis kept
+    StartSource s{};
+    s.kind = SRC_RADEMACHER;
+    s.seed_mixed = sm;
+    s.col_begin = 0;
+    s.ncols = Nr;
+    BlockOut sk;
+    run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk);
+    const int Kp = sk.Kp;
+    double* zvec = ws_get_t<double>(ctx, "zvec", (size_t)m * Kp);
+    VNE_TRY_CUDA(ctx, launch_tridiag_fvec(sk.alpha, sk.beta, sk.scale, Kp, m, Kp, zvec, st));
+    double* gamma = ws_get_t<double>(ctx, "gamma", (size_t)m * Kp);
+    k_gamma<<<(m * Kp + 255) / 256, 256, 0, st>>>(sk.norm2, sk.sigma, zvec, m, Kp, gamma);
+    VNE_TRY_CUDA(ctx, cudaGetLastError());
+    const size_t blk = (size_t)Kp * n;
+    T* Y = ws_get_t<T>(ctx, "Y", blk);
+    RecoverParams<T> rp{};
+    rp.basis = (const T*)sk.basis;
+    rp.slot_stride = sk.slot_stride;
+    rp.y = Y;
+    rp.gamma = gamma;
+    rp.m = m;
+    rp.K = Kp;
+    rp.n_total = n;
+    rp.tiles_per_panel = P->tiles_per_panel();
+    rp.tiles = P->d_tiles;
+    VNE_TRY_CUDA(ctx, launch_recover<T>(rp, ks, sk.panels, st));
+    ctx->launches += 3;  // fvec, gamma, recover
+    // 2. Q = orthonormal basis of range(Y): pivoted Cholesky-QR, twice
+    const int nch = std::max(1, std::min(4 * ctx->sm_count, (n + 63) / 64));
+    double* gpart = ws_get_t<double>(ctx, "gram.part", (size_t)nch * Kp * std::max(Kp, 128));
+    double* G1 = ws_get_t<double>(ctx, "G1", (size_t)Kp * Kp);
+    double* Minv = ws_get_t<double>(ctx, "Minv", (size_t)Kp * Kp);
+    int* drank = ws_get_t<int>(ctx, "rank", 2);
+    T* Q1 = ws_get_t<T>(ctx, "Q1", blk);
+    T* Q = ws_get_t<T>(ctx, "Q", blk);
+    const double tol = M->fp64 ? 1e-13 : 1e-5;
+    VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, st));
+    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, st));
+    VNE_TRY_CUDA(ctx, launch_apply<T>(Y, Kp, Minv, Kp, nullptr, Q1, ks, n, 1.0, st));
+    VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, st));
+    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, st));
+    VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, st));
+    ctx->launches += 10;  // 2 x (gram + reduce + factor + apply)
+    int hr[2] = {0, 0};
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    const int r = std::min(hr[0], hr[1]);
+    // 3. tr(Q^T f(A) Q): Lanczos quadratures of the r columns of Q
+    double low = 0.0;
+    if (r > 0) {
+        StartSource sq{};
+        sq.kind = SRC_PANEL;
+        sq.ncols = r;
+        BlockOut qo;
+        run_block<T>(ctx, *P, sq, Q, r, ks, m, want_reorth(M, o), false, M->desing, "q", qo);
+        std::vector<double> h = download(ctx, qo.psi, r);
+        for (double v : h) low += v;
+    }
+    // 4. residual part: G' = (I - Q Q^T) G, Hutchinson on G'
+    double resid = 0.0;
+    if (NH > 0) {
+        const int Kg = ((NH + ks - 1) / ks) * ks;
+        const size_t gblk = (size_t)Kg * n;
+        T* Gr = ws_get_t<T>(ctx, "Graw", gblk);
+        T* Gp = ws_get_t<T>(ctx, "Gproj", gblk);
+        StartSource sg{};
+        sg.kind = SRC_RADEMACHER;
+        sg.seed_mixed = sm;
+        sg.col_begin = Nr;
+        sg.ncols = NH;
+        {
+            // materialise G with the start kernel (no centring)
+            StartParams<T> spp{};
+            spp.src = sg;
+            spp.node_id = P->node_id;
+            spp.seg = P->d_segs;
+            spp.nseg = 1;
+            spp.K = Kg;
+            spp.n_total = n;
+            spp.tiles_per_panel = P->tiles_per_panel();
+            spp.tiles = P->d_tiles;
+            spp.desing = 0;
+            spp.w1 = Gr;
+            spp.mean = ws_get_t<double>(ctx, "mean", Kg);
+            spp.norm2 = ws_get_t<double>(ctx, "g.norm2", Kg);
+            spp.sig1 = ws_get_t<double>(ctx, "g.sig", Kg);
+            spp.part = ws_get_t<double>(ctx, "part", (size_t)(Kg / ks) * P->tiles_per_panel() * ks);
+            spp.counter = ws_get_t<uint32_t>(ctx, "counter", (size_t)(Kg / ks), true);
+            VNE_TRY_CUDA(ctx, launch_start<T>(spp, ks, Kg / ks, st));
+            ctx->launches += 1;
+        }
+        double* C = ws_get_t<double>(ctx, "QtG", (size_t)Kp * Kg);
+        double* gpart2 = ws_get_t<double>(ctx, "gram.part2", (size_t)nch * Kp * Kg);
+        VNE_REQUIRE(ctx, Kg <= 128, VNE_EUNSUPPORTED, "N_H > 128 not supported in one projection block");
+        VNE_TRY_CUDA(ctx, launch_gram<T>(Q, Kp, Gr, Kg, ks, n, gpart2, nch, C, st));
+        VNE_TRY_CUDA(ctx, launch_apply<T>(Q, Kp, C, Kg, Gr, Gp, ks, n, -1.0, st));
+        ctx->launches += 3;
+        StartSource sp{};
+        sp.kind = SRC_PANEL;
+        sp.ncols = NH;
+        BlockOut go;
+        run_block<T>(ctx, *P, sp, Gp, NH, ks, m, want_reorth(M, o), false, M->desing, "q", go);
+        std::vector<double> h = download(ctx, go.psi, NH);
+        for (double v : h) resid += v;
+        resid /= NH;
+    }
+    *estimate = low + resid;
+    if (parts) {
+        parts[0] = low;
+        parts[1] = resid;
+        parts[2] = (double)r;
+    }
+}
+
+}  // namespace
+
+extern "C" vne_status vne_entropy_hutchpp(vne_matrix* M, int32_t sketch_cols, int32_t hutch_vectors,
+                                          int32_t krylov_steps, uint64_t seed, const vne_options* opt,
+                                          double* estimate, double* parts) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, estimate, VNE_EINVAL, "estimate is required");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    if (M->fp64) hutchpp_impl<double>(M, &o, sketch_cols, hutch_vectors, krylov_steps, seed, estimate, parts);
+    else hutchpp_impl<float>(M, &o, sketch_cols, hutch_vectors, krylov_steps, seed, estimate, parts);
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_greedy_coloring(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t distance,
+                                          int32_t* colors, int32_t* num_colors) {
+    if (n < 1 || !row_ptr || !col_idx || !colors || distance < 1) return VNE_EINVAL;
+    try {
+        int32_t s = greedy_coloring(n, row_ptr, col_idx, distance, colors);
+        if (num_colors) *num_colors = s;
+    } catch (...) {
+        return VNE_ENOMEM;
+    }
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring, int32_t distance,
+                                          int32_t krylov_steps, const double* poles, int32_t num_poles,
+                                          const vne_options* opt, double* estimate, int32_t* num_colors) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, estimate, VNE_EINVAL, "estimate is required");
+    VNE_REQUIRE(ctx, poles == nullptr, VNE_EUNSUPPORTED, "rational probing is provided by vne_entropy_probing_rational");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    const int64_t n = M->n;
+    // colours in the caller's node numbering
+    std::vector<int32_t> col(n);
+    int32_t s = 0;
+    if (coloring) {
+        for (int64_t i = 0; i < n; i++) {
+            VNE_REQUIRE(ctx, coloring[i] >= 0, VNE_EINVAL, "negative colour at node %lld", (long long)i);
+            col[i] = coloring[i];
+            s = std::max(s, coloring[i] + 1);
+        }
+    } else {
+        VNE_REQUIRE(ctx, distance >= 1, VNE_EINVAL, "distance must be >= 1");
+        // colour the caller's graph (undo the relabelling for the traversal)
+        std::vector<int32_t> c2(n);
+        s = greedy_coloring(n, M->h_rowptr.data(), M->h_col.data(), distance, c2.data());
+        if (M->perm.empty()) col.swap(c2);
+        else
+            for (int64_t i = 0; i < n; i++) col[M->perm[i]] = c2[i];
+        // Note: with a relabelled matrix the greedy order is computed on the
+        // relabelled graph, whose degree order is the same up to ties.
+    }
+    int32_t* dcol = upload(ctx, "colors", col);
+    StartSource src{};
+    src.kind = SRC_INDICATOR;
+    src.colors = dcol;
+    src.col_begin = 0;
+    std::vector<double> psi = M->fp64 ? quadforms<double>(M, &o, src, s, krylov_steps)
+                                      : quadforms<float>(M, &o, src, s, krylov_steps);
+    double tot = 0.0;
+    for (double v : psi) tot += v;
+    *estimate = tot;
+    if (num_colors) *num_colors = s;
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_spmm(vne_matrix* M, const void* X, void* Y, int32_t k) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, X && Y && k >= 1, VNE_EINVAL, "need X, Y and k >= 1");
+    if (M->fp64)
+        VNE_TRY_CUDA(ctx, launch_spmm_plain<double>(M->d_rowptr, M->d_col, (const double*)M->d_vals, (int)M->n, k,
+                                                    M->d_node_id, M->scale, (const double*)X, (double*)Y, ctx->stream));
+    else
+        VNE_TRY_CUDA(ctx, launch_spmm_plain<float>(M->d_rowptr, M->d_col, (const float*)M->d_vals, (int)M->n, k,
+                                                   M->d_node_id, M->scale, (const float*)X, (float*)Y, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_tridiag_quadrature(vne_ctx* ctx, const double* alpha, const double* beta, const double* norm2,
+                                             double scale, int32_t count, int32_t m, double* psi) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, alpha && beta && norm2 && psi && count >= 1 && m >= 1 && m <= 128, VNE_EINVAL,
+                "bad arguments to vne_tridiag_quadrature");
+    // host layout [count][m] -> device column-interleaved [m][count]
+    std::vector<double> a((size_t)m * count), b((size_t)m * count), sc(count, scale), nn(norm2, norm2 + count);
+    for (int c = 0; c < count; c++)
+        for (int j = 0; j < m; j++) {
+            a[(size_t)j * count + c] = alpha[(size_t)c * m + j];
+            b[(size_t)j * count + c] = (j + 1 < m) ? beta[(size_t)c * m + j] : 0.0;
+        }
+    double* da = upload(ctx, "tq.a", a);
+    double* db = upload(ctx, "tq.b", b);
+    double* ds = upload(ctx, "tq.s", sc);
+    double* dn = upload(ctx, "tq.n", nn);
+    double* dp = ws_get_t<double>(ctx, "tq.p", count);
+    VNE_TRY_CUDA(ctx, launch_tridiag_quad(da, db, dn, ds, count, m, count, dp, ctx->stream));
+    std::vector<double> h = download(ctx, dp, count);
+    std::copy(h.begin(), h.end(), psi);
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_rademacher(vne_ctx* ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k, int32_t fp64,
+                                     void* out_device) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, out_device && n >= 1 && k >= 1 && col_begin >= 0, VNE_EINVAL, "bad arguments to vne_rademacher");
+    VNE_TRY_CUDA(ctx, launch_rademacher_fill(seed_mix(seed), n, col_begin, k, fp64, out_device, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_API_END(ctx)
+}
+
+// ---------------------------------------------------------------------------
+// batched uneven graphs: block-diagonal packing, one schedule, one launch per
+// kernel per step for all graphs
+
+extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t count, int32_t num_vectors,
+                                           int32_t krylov_steps, uint64_t seed, const vne_options* opt,
+                                           double* estimates, double* std_errors) {
+    if (!mats || count < 1 || !mats[0]) return VNE_EINVAL;
+    vne_ctx* ctx = mats[0]->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, estimates && num_vectors >= 1, VNE_EINVAL, "need estimates and num_vectors >= 1");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    const bool fp64 = mats[0]->fp64;
+    int64_t ntot = 0, nnztot = 0;
+    bool any_perm = false, any_valued = false;
+    for (int i = 0; i < count; i++) {
+        VNE_REQUIRE(ctx, mats[i] && mats[i]->ctx == ctx && mats[i]->fp64 == fp64, VNE_EINVAL,
+                    "all matrices must share the context and precision");
+        ntot += mats[i]->n;
+        nnztot += mats[i]->nnz;
+        any_perm |= !mats[i]->perm.empty();
+        any_valued |= !mats[i]->pattern;
+    }
+    VNE_REQUIRE(ctx, !any_valued, VNE_EUNSUPPORTED, "batched mode packs pattern (graph) matrices");
+    VNE_REQUIRE(ctx, ntot < INT32_MAX && nnztot < INT32_MAX, VNE_EINVAL, "packed batch too large");
+    // packed CSR
+    std::vector<int64_t> rp(ntot + 1, 0);
+    std::vector<int32_t> ci(nnztot);
+    std::vector<int32_t> nid;
+    if (any_perm) nid.resize(ntot);
+    std::unique_ptr<Problem> P(new Problem());
+    P->fp64 = fp64;
+    P->valued = false;
+    P->n_total = (int32_t)ntot;
+    P->nnz_total = nnztot;
+    P->nseg = count;
+    double taurel = o.breakdown_tol > 0 ? o.breakdown_tol : default_tau(fp64);
+    int64_t r0 = 0, e0 = 0;
+    for (int i = 0; i < count; i++) {
+        const vne_matrix* M = mats[i];
+        for (int64_t r = 0; r < M->n; r++) {
+            rp[r0 + r + 1] = e0 + M->h_rowptr[r + 1];
+            if (any_perm) nid[r0 + r] = M->perm.empty() ? (int32_t)r : M->perm[r];
+        }
+        for (int64_t e = 0; e < M->nnz; e++) ci[e0 + e] = M->h_col[e] + (int32_t)r0;
+        SegInfo s{};
+        s.row_begin = (int32_t)r0;
+        s.rows = (int32_t)M->n;
+        s.scale = M->scale;
+        s.tau = taurel * M->normM;
+        P->segs.push_back(s);
+        r0 += M->n;
+        e0 += M->nnz;
+    }
+    const int target = default_item_nnz(&o);
+    for (int i = 0; i < count; i++) plan_segment(rp.data(), P->segs[i].row_begin, P->segs[i].rows, i, target, *P);
+    std::vector<int32_t> rp32(ntot + 1);
+    for (int64_t i = 0; i <= ntot; i++) rp32[i] = (int32_t)rp[i];
+    int32_t* drp = dev_copy(ctx, rp32);
+    int32_t* dci = dev_copy(ctx, ci);
+    P->owned.push_back(drp);
+    P->owned.push_back(dci);
+    P->rowptr = drp;
+    P->col = dci;
+    if (any_perm) {
+        int32_t* dn = dev_copy(ctx, nid);
+        P->owned.push_back(dn);
+        P->node_id = dn;
+    }
+    problem_upload(ctx, *P);
+    int ks = choose_panel(fp64, &o, ntot);
+    StartSource s{};
+    s.kind = SRC_RADEMACHER;
+    s.seed_mixed = seed_mix(seed);
+    s.col_begin = 0;
+    s.ncols = num_vectors;
+    BlockOut out;
+    if (fp64) {
+        check_ks<double>(ctx, ks);
+        run_block<double>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out);
+    } else {
+        check_ks<float>(ctx, ks);
+        run_block<float>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out);
+    }
+    std::vector<double> psi = download(ctx, out.psi, out.SK);
+    for (int i = 0; i < count; i++) {
+        double mean = 0.0;
+        for (int c = 0; c < num_vectors; c++) mean += psi[(size_t)i * out.Kp + c];
+        mean /= num_vectors;
+        double var = 0.0;
+        for (int c = 0; c < num_vectors; c++) {
+            double d = psi[(size_t)i * out.Kp + c] - mean;
+            var += d * d;
+        }
+        estimates[i] = mean;
+        if (std_errors) std_errors[i] = num_vectors > 1 ? sqrt(var / (num_vectors - 1) / num_vectors) : 0.0;
+    }
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_ctx_profile(vne_ctx* ctx, int32_t enable) {
+    if (!ctx) return VNE_EINVAL;
+    ctx->profile = enable != 0;
+    for (auto& k : ctx->stat) k = KernelStat();
+    ctx->launches = 0;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_stats(const vne_ctx* ctx, int64_t* launches, double* kernel_stats) {
+    if (!ctx) return VNE_EINVAL;
+    if (launches) *launches = ctx->launches;
+    if (kernel_stats)
+        for (int k = 0; k < 2; k++) {
+            kernel_stats[3 * k + 0] = (double)ctx->stat[k].launches;
+            kernel_stats[3 * k + 1] = ctx->stat[k].ms;
+            kernel_stats[3 * k + 2] = ctx->stat[k].bytes;
+        }
+    return VNE_OK;
+}

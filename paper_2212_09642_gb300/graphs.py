@@ -34,6 +34,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _GEN_SRC = os.path.join(_HERE, "gen", "graphgen.c")
 _GEN_LIB = os.path.join(_HERE, "gen", "libgraphgen.so")
+_GEN_STAMP = os.path.join(_HERE, "gen", "libgraphgen.stamp")
 _lock = threading.Lock()
 _lib = None
 
@@ -65,15 +66,21 @@ class Graph:
 
 def build_generator_library(force: bool = False) -> str:
     """Compile ``gen/graphgen.c`` into a shared library (idempotent)."""
+    import hashlib
+    import platform
+    with open(_GEN_SRC, "rb") as fh:
+        tag = f"{platform.machine()}:{hashlib.sha256(fh.read()).hexdigest()}"
     with _lock:
-        stale = (not os.path.exists(_GEN_LIB)) or (
-            os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC))
+        stale = (not os.path.exists(_GEN_LIB)) or (not os.path.exists(_GEN_STAMP)) or (
+            open(_GEN_STAMP).read() != tag)
         if force or stale:
             tmp = _GEN_LIB + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
                    _GEN_SRC, "-o", tmp, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _GEN_LIB)
+            with open(_GEN_STAMP, "w") as fh:
+                fh.write(tag)
     return _GEN_LIB
 
 

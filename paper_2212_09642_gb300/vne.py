@@ -1,0 +1,300 @@
+"""ctypes binding of the libvne C ABI (include/vne.h).
+
+Argument marshalling only: every step of the computation runs in libvne's
+CUDA kernels.  Function names follow the C ABI.  Host arrays are NumPy
+arrays; device arrays may be passed as CUDA tensors (their ``data_ptr``) or
+integer addresses.  The binding raises :class:`VneError` for every non-zero
+status, with the library's message.
+
+The shared library is built in-tree by ``__graft_entry__.build()`` (or
+``paper_2212_09642_gb300._build.build()``); importing this module without it
+raises immediately -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvne.so")
+
+VNE_OK = 0
+VNE_EINVAL = 1
+VNE_ENOMEM = 2
+VNE_ENOTSYM = 3
+VNE_ENOCONVERGE = 4
+VNE_ETIMEOUT = 5
+VNE_EDEVICE = 6
+VNE_EUNSUPPORTED = 7
+
+VNE_FP64 = 0x1
+VNE_FP32 = 0x2
+VNE_NORMALIZE_TRACE = 0x4
+VNE_IS_LAPLACIAN = 0x8
+VNE_INPUT_DEVICE = 0x10
+VNE_REORDER = 0x20
+VNE_CHECK_SYMMETRY = 0x40
+VNE_VECTORS_DEVICE = 0x1
+
+
+class VneError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libvne status {status}: {message}")
+        self.status = status
+
+
+class vne_options(ctypes.Structure):
+    _fields_ = [("reorth", ctypes.c_int32), ("block", ctypes.c_int32), ("panel", ctypes.c_int32),
+                ("item_nnz", ctypes.c_int32), ("n_inf_poles", ctypes.c_int32), ("cg_max_iter", ctypes.c_int32),
+                ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def _declare(lib):
+    st = ctypes.c_int32
+    sig = {
+        "vne_options_default": (None, [ctypes.POINTER(vne_options)]),
+        "vne_version": (ctypes.c_char_p, []),
+        "vne_ctx_create": (st, [ctypes.c_int32, ctypes.POINTER(_P)]),
+        "vne_ctx_destroy": (st, [_P]),
+        "vne_ctx_set_stream": (st, [_P, _P]),
+        "vne_last_error": (ctypes.c_char_p, [_P]),
+        "vne_create_density_matrix": (st, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_uint32, ctypes.POINTER(_P)]),
+        "vne_matrix_destroy": (st, [_P]),
+        "vne_matrix_info": (st, [_P, _PI64, _PI64, _PD, _PD]),
+        "vne_quadform_batch": (st, [_P, _P, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, _P, ctypes.c_int32,
+                                    ctypes.POINTER(vne_options), _PD, _PD]),
+        "vne_entropy_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.POINTER(vne_options), _PD, _PD, _PD]),
+        "vne_entropy_hutchpp": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                     ctypes.POINTER(vne_options), _PD, _PD]),
+        "vne_entropy_probing": (st, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                     ctypes.POINTER(vne_options), _PD, _PI32]),
+        "vne_greedy_coloring": (st, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _PI32]),
+        "vne_spmm": (st, [_P, _P, _P, ctypes.c_int32]),
+        "vne_tridiag_quadrature": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P]),
+        "vne_rademacher": (st, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
+        "vne_batch_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.POINTER(vne_options), _P, _P]),
+        "vne_ctx_profile": (st, [_P, ctypes.c_int32]),
+        "vne_ctx_stats": (st, [_P, _PI64, _P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return sig
+
+
+def load():
+    """Load libvne.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding declares."""
+    return list(_SIGNATURES)
+
+
+_SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
+               "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
+               "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
+               "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats"]
+
+
+def _check(status, ctx=None):
+    if status != VNE_OK:
+        msg = load().vne_last_error(ctx).decode() if ctx else ""
+        raise VneError(status, msg)
+
+
+def _ptr(a):
+    """Address of a NumPy array, a CUDA tensor, an int address or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def options(**kw) -> vne_options:
+    o = vne_options()
+    load().vne_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def vne_version() -> str:
+    return load().vne_version().decode()
+
+
+def vne_ctx_create(device: int = 0):
+    h = _P()
+    _check(load().vne_ctx_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def vne_ctx_destroy(ctx):
+    _check(load().vne_ctx_destroy(ctx))
+
+
+def vne_ctx_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+    s = getattr(stream, "cuda_stream", stream)
+    _check(load().vne_ctx_set_stream(ctx, s), ctx)
+
+
+def vne_create_density_matrix(ctx, n, row_ptr, col_idx, vals=None, flags=VNE_FP32):
+    if not (flags & VNE_INPUT_DEVICE):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if vals is not None:
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+    h = _P()
+    _check(load().vne_create_density_matrix(ctx, int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), int(flags),
+                                            ctypes.byref(h)), ctx)
+    return h
+
+
+def vne_matrix_destroy(mat):
+    _check(load().vne_matrix_destroy(mat))
+
+
+def vne_matrix_info(mat):
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    tr, nb = ctypes.c_double(), ctypes.c_double()
+    _check(load().vne_matrix_info(mat, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(tr), ctypes.byref(nb)))
+    return n.value, nnz.value, tr.value, nb.value
+
+
+def vne_quadform_batch(ctx, mat, vectors, krylov_steps, opt=None, want_alpha_beta=False, device=False, k=None):
+    """psi (and optionally alpha/beta, shape [k, 2m]) for the columns of ``vectors`` ([n, k])."""
+    if device:
+        kk = int(k if k is not None else vectors.shape[1])
+        vp = _ptr(vectors)
+        flags = VNE_VECTORS_DEVICE
+    else:
+        vectors = np.ascontiguousarray(vectors, dtype=np.float64)
+        kk = vectors.shape[1]
+        vp = _ptr(vectors)
+        flags = 0
+    psi = np.zeros(kk)
+    ab = np.zeros((kk, 2 * krylov_steps)) if want_alpha_beta else None
+    o = opt if opt is not None else options()
+    _check(load().vne_quadform_batch(mat, vp, kk, flags, int(krylov_steps), None, 0, ctypes.byref(o),
+                                     psi.ctypes.data_as(_PD), ab.ctypes.data_as(_PD) if ab is not None else None), ctx)
+    return (psi, ab) if want_alpha_beta else psi
+
+
+def vne_entropy_hutchinson(ctx, mat, num_vectors, krylov_steps, seed, opt=None, want_psi=False):
+    est, se = ctypes.c_double(), ctypes.c_double()
+    psi = np.zeros(num_vectors) if want_psi else None
+    o = opt if opt is not None else options()
+    _check(load().vne_entropy_hutchinson(mat, int(num_vectors), int(krylov_steps), int(seed) & (2**64 - 1),
+                                         ctypes.byref(o), ctypes.byref(est), ctypes.byref(se),
+                                         psi.ctypes.data_as(_PD) if psi is not None else None), ctx)
+    return (est.value, se.value, psi) if want_psi else (est.value, se.value)
+
+
+def vne_entropy_hutchpp(ctx, mat, sketch_cols, hutch_vectors, krylov_steps, seed, opt=None):
+    est = ctypes.c_double()
+    parts = np.zeros(3)
+    o = opt if opt is not None else options()
+    _check(load().vne_entropy_hutchpp(mat, int(sketch_cols), int(hutch_vectors), int(krylov_steps),
+                                      int(seed) & (2**64 - 1), ctypes.byref(o), ctypes.byref(est),
+                                      parts.ctypes.data_as(_PD)), ctx)
+    return est.value, parts
+
+
+def vne_entropy_probing(ctx, mat, coloring=None, distance=1, krylov_steps=30, opt=None):
+    est = ctypes.c_double()
+    s = ctypes.c_int32()
+    o = opt if opt is not None else options()
+    cp = None
+    if coloring is not None:
+        coloring = np.ascontiguousarray(coloring, dtype=np.int32)
+        cp = _ptr(coloring)
+    _check(load().vne_entropy_probing(mat, cp, int(distance), int(krylov_steps), None, 0, ctypes.byref(o),
+                                      ctypes.byref(est), ctypes.byref(s)), ctx)
+    return est.value, s.value
+
+
+def vne_greedy_coloring(n, row_ptr, col_idx, distance):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    colors = np.zeros(n, dtype=np.int32)
+    s = ctypes.c_int32()
+    _check(load().vne_greedy_coloring(int(n), _ptr(row_ptr), _ptr(col_idx), int(distance), _ptr(colors),
+                                      ctypes.byref(s)))
+    return colors, s.value
+
+
+def vne_spmm(ctx, mat, X, Y, k):
+    _check(load().vne_spmm(mat, _ptr(X), _ptr(Y), int(k)), ctx)
+
+
+def vne_tridiag_quadrature(ctx, alpha, beta, norm2, scale):
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    norm2 = np.ascontiguousarray(norm2, dtype=np.float64)
+    count, m = alpha.shape
+    psi = np.zeros(count)
+    _check(load().vne_tridiag_quadrature(ctx, _ptr(alpha), _ptr(beta), _ptr(norm2), float(scale), count, m,
+                                         _ptr(psi)), ctx)
+    return psi
+
+
+def vne_rademacher(ctx, seed, n, col_begin, k, out_device, fp64):
+    _check(load().vne_rademacher(ctx, int(seed) & (2**64 - 1), int(n), int(col_begin), int(k), int(bool(fp64)),
+                                 _ptr(out_device)), ctx)
+
+
+def vne_batch_hutchinson(ctx, mats, num_vectors, krylov_steps, seed, opt=None):
+    arr = (_P * len(mats))(*mats)
+    est = np.zeros(len(mats))
+    se = np.zeros(len(mats))
+    o = opt if opt is not None else options()
+    _check(load().vne_batch_hutchinson(arr, len(mats), int(num_vectors), int(krylov_steps), int(seed) & (2**64 - 1),
+                                       ctypes.byref(o), _ptr(est), _ptr(se)), ctx)
+    return est, se
+
+
+def vne_ctx_profile(ctx, enable=True):
+    _check(load().vne_ctx_profile(ctx, int(bool(enable))), ctx)
+
+
+def vne_ctx_stats(ctx):
+    """(launches, {"step": (count, ms, bytes), "update": (count, ms, bytes)})."""
+    n = ctypes.c_int64()
+    st = np.zeros(6)
+    _check(load().vne_ctx_stats(ctx, ctypes.byref(n), _ptr(st)), ctx)
+    return n.value, {"step": tuple(st[0:3]), "update": tuple(st[3:6])}
+
+
+# ---------------------------------------------------------------------------
+# small convenience layer (still marshalling only)
+
+def matrix_from_graph(ctx, graph, fp64=False, reorder=False, extra_flags=0):
+    """Density matrix rho = L / tr(L) of a graph pattern (implicit Laplacian)."""
+    flags = (VNE_FP64 if fp64 else VNE_FP32) | (VNE_REORDER if reorder else 0) | extra_flags
+    return vne_create_density_matrix(ctx, graph.n, graph.rowptr, graph.col, None, flags)

@@ -1,0 +1,69 @@
+"""GPU kernel parity through the C ABI: probe generator, SpMM, quadrature."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import density, krylov, rng
+from paper_2212_09642_gb300 import graphs, vne
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    iso = graphs.from_edges(300, np.array([1, 2, 3, 10]), np.array([2, 3, 1, 11]))  # mostly isolated nodes
+    star = graphs.star(5000)  # one row with 4999 nonzeros (split into chunks)
+    return [graphs.erdos_renyi(3000, 0.003, 2), graphs.barabasi_albert(20000, 4, 3), star, iso,
+            graphs.disjoint_union([graphs.star(700), graphs.watts_strogatz(900, 6, 0.2, 1)])]
+
+
+def test_rademacher_bit_exact(vctx):
+    import torch
+    n, k, c0 = 5003, 37, 11
+    out = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    vne.vne_rademacher(vctx, 1234, n, c0, k, out, fp64=True)
+    want = rng.rademacher(1234, n, c0, k)
+    assert np.array_equal(out.cpu().numpy(), want)
+    out32 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    vne.vne_rademacher(vctx, 99, n, 0, k, out32, fp64=False)
+    assert np.array_equal(out32.cpu().numpy().astype(np.float64), rng.rademacher(99, n, 0, k))
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("reorder", [False, True])
+def test_spmm_matches_scipy(vctx, fp64, reorder):
+    import torch
+    dt = torch.float64 if fp64 else torch.float32
+    for g in _graphs():
+        A, _ = density.density_matrix(g)
+        k = 5
+        X = np.random.default_rng(g.n).standard_normal((g.n, k))
+        mat = vne.matrix_from_graph(vctx, g, fp64=fp64, reorder=reorder)
+        try:
+            Xd = torch.tensor(X, dtype=dt, device="cuda")
+            Yd = torch.empty_like(Xd)
+            vne.vne_spmm(vctx, mat, Xd, Yd, k)
+            Y = Yd.cpu().numpy().astype(np.float64)
+        finally:
+            vne.vne_matrix_destroy(mat)
+        ref = A @ X
+        scale = np.abs(A) @ np.abs(X) + 1e-300
+        tol = 1e-13 if fp64 else 1e-5
+        assert np.max(np.abs(Y - ref) / scale) < tol
+
+
+def test_tridiag_quadrature_matches_oracle(vctx):
+    r = np.random.default_rng(3)
+    count, m = 200, 60
+    a = r.uniform(0, 1e-3, (count, m))
+    b = r.uniform(0, 5e-4, (count, m))
+    b[::7, 13] = 0.0           # truncation after row 14
+    a[::11, :] = 2e-4          # clustered Toeplitz spectra
+    b[::11, :] = 1e-4
+    norm2 = r.uniform(1, 100, count)
+    got = vne.vne_tridiag_quadrature(vctx, a, b, norm2, 3.0)
+    for c in range(count):
+        bb = b[c, :m - 1]
+        z = np.where(bb == 0)[0]
+        kk = m if len(z) == 0 else z[0] + 1
+        want = krylov.gauss_quadrature(3.0 * a[c, :kk], 3.0 * bb[:kk - 1], norm2[c])
+        assert abs(got[c] - want) <= 1e-12 * abs(want)
