@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--n", type=int, default=N_NODES, help="graph size (default: the workload's 1e6)")
+    ap.add_argument("--estimator", choices=["hutchpp", "hutchinson"], default="hutchpp",
+                    help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
+    ap.add_argument("--vectors", type=int, default=112)
     return ap.parse_args()
 
 
@@ -241,6 +244,8 @@ def run_native(args):
     seed0 = 1000 * (rank + 1)
 
     def one(seed):
+        if args.estimator == "hutchinson":
+            return vne.vne_entropy_hutchinson(ctx, mat, args.vectors, M_STEPS, seed, opt=opt)
         return vne.vne_entropy_hutchpp(ctx, mat, N_SKETCH, N_HUTCH, M_STEPS, seed, opt=opt)
 
     for w in range(args.warmup):
@@ -280,7 +285,7 @@ def run_native(args):
 
     # mixed-precision error against the FP64 GPU run on identical probes
     rel_err = None
-    if not args.no_fp64_check and rank == 0:
+    if not args.no_fp64_check and rank == 0 and args.estimator == "hutchpp":
         mat64 = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, vne.VNE_FP64 | vne.VNE_REORDER)
         e64 = vne.vne_entropy_hutchpp(ctx, mat64, N_SKETCH, N_HUTCH, M_STEPS, seed0 + 100, opt=vne.options(reorth=0))[0]
         vne.vne_matrix_destroy(mat64)
@@ -288,7 +293,7 @@ def run_native(args):
 
     # end to end through the C ABI from host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.estimator == "hutchpp":
         k2 = max(1, min(args.steps, 3))
         barrier()
         torch.cuda.synchronize(dev)
@@ -326,7 +331,7 @@ def run_native(args):
               "avg_launch_ms": ums / ucnt if ucnt else None, "share_of_step_time": ums / elapsed_ms}
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.estimator == "hutchpp":
         t_est, parts = oracle_sample(g, columns=2)
         cpu = {"value": 1.0 / t_est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": "2 sketch matvecs + 2 quadratic forms (FP64 scipy Lanczos, 60 steps, same graph) + one "
@@ -339,7 +344,9 @@ def run_native(args):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
+        "config": {"workload": WORKLOAD if args.estimator == "hutchpp" else
+                   f"Hutchinson {args.vectors} vectors x {M_STEPS} steps on BA n={args.n} m=4 (profiling case)",
+                   "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
                    "hutch_vectors": N_HUTCH, "krylov_steps": M_STEPS, "scalars": "f64",
                    "l2": "inputs larger than L2 (each 100-column block is 400 MB; L2 129 MB)",
                    "parallelism": f"replicas x{world} (independent estimates)"},
