@@ -213,6 +213,35 @@ vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t 
                                 int32_t krylov_steps, uint64_t seed, const vne_options *opt,
                                 double *estimates, double *std_errors);
 
+/* ---- allocation-free quadratic forms ---------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need the result (code bound
+ * to another framework's memory pool, allocator-free real-time loops,
+ * embedding hosts that hand over only the buffers they own).
+ *
+ * Same quantity as vne_quadform_batch in the FP64 path with a plain
+ * three-term recurrence (reorth = 0): psi[j] ~ b_j^T f(rho) b_j for the graph
+ * Laplacian density rho = L / tr(L) of a CSR pattern, with implicit
+ * desingularisation.  Everything is caller-owned device memory:
+ *   row_ptr  int32[n+1], col_idx int32[nnz] -- symmetric pattern, no self-loops
+ *   vectors  double[n][k] row-major
+ *   psi      double[k] output
+ * Work goes on `stream` (a cudaStream_t, NULL for the legacy stream) on the
+ * current device; the call returns without synchronising.
+ *
+ * Nothing is allocated: all intermediates live in one static device array of
+ * VNE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  It needs about 24 n ceil(k/8)*8 bytes plus small
+ * terms; larger problems fail with VNE_EINVAL.  All calls share the array,
+ * which keeps the previous call's contents (each call clears what must
+ * start at zero), so calls that overlap on a GPU race: serialise them.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Not thread safe. */
+#define VNE_NOALLOC_SCRATCH_BYTES (32u << 20)
+vne_status vne_quadform_noalloc(void *stream, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                const double *vectors, int32_t k, int32_t krylov_steps, double *psi);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ def _declare(lib):
         "vne_batch_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(vne_options), _P, _P]),
         "vne_ctx_profile": (st, [_P, ctypes.c_int32]),
+        "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
     }
     for name, (res, args) in sig.items():
@@ -116,7 +117,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
-               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats"]
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc"]
 
 
 def _check(status, ctx=None):
@@ -289,6 +290,16 @@ def vne_ctx_stats(ctx):
     st = np.zeros(6)
     _check(load().vne_ctx_stats(ctx, ctypes.byref(n), _ptr(st)), ctx)
     return n.value, {"step": tuple(st[0:3]), "update": tuple(st[3:6])}
+
+
+def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, krylov_steps, psi_dev):
+    """Allocation-free FP64 Lanczos quadrature; every array is caller-owned device memory
+    (see include/vne.h).  Returns without synchronising the stream."""
+    s = getattr(stream, "cuda_stream", stream)
+    st = load().vne_quadform_noalloc(s, int(n), _ptr(row_ptr_dev), _ptr(col_idx_dev), _ptr(vectors_dev), int(k),
+                                     int(krylov_steps), _ptr(psi_dev))
+    if st != VNE_OK:
+        raise VneError(st, "vne_quadform_noalloc rejected the call (sizes beyond the fixed scratch, or bad arguments)")
 
 
 # ---------------------------------------------------------------------------
