@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--estimator", choices=["hutchpp", "hutchinson"], default="hutchpp",
                     help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
     ap.add_argument("--vectors", type=int, default=112)
+    ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -242,6 +243,15 @@ def run_native(args):
     mat = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
     opt = vne.options(reorth=0)
     seed0 = 1000 * (rank + 1)
+    if args.schedule:
+        pnl, itm, var = (int(x) for x in args.schedule.split(","))
+        opt = vne.options(reorth=0, panel=pnl, item_nnz=itm, step_variant=var)
+        tuned_cfg = {"panel": pnl, "item_nnz": itm, "step_variant": var, "source": "--schedule"}
+    else:
+        # schedule autotuner (once per matrix shape; cached in the context)
+        tuned, tune_ms = vne.vne_autotune(ctx, mat, 112 if args.estimator == "hutchpp" else args.vectors, 8)
+        tuned_cfg = {"panel": tuned.panel, "item_nnz": tuned.item_nnz, "step_variant": tuned.step_variant,
+                     "ms_per_lanczos_step_112_cols": tune_ms, "source": "vne_autotune"}
 
     def one(seed):
         if args.estimator == "hutchinson":
@@ -352,6 +362,7 @@ def run_native(args):
                    "parallelism": f"replicas x{world} (independent estimates)"},
         "roofline": roof, "update_kernel": update, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": sampler.summary() if sampler else None,
+        "schedule": tuned_cfg,
         "rel_err_vs_fp64": rel_err, "estimates": ests,
     }
     print(json.dumps(line), flush=True)

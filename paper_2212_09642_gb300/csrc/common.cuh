@@ -92,6 +92,8 @@ struct SegInfo {
     int32_t cta_count;
     int32_t tile_begin;  // first row tile (within a panel)
     int32_t tile_count;
+    int32_t hub_begin;   // long rows of the segment: hubs [hub_begin, hub_begin + hub_count)
+    int32_t hub_count;
     double scale;        // A = scale * M for the stored operator M
     double tau;          // breakdown threshold on beta (for M)
 };

@@ -50,8 +50,10 @@ struct StepParams {
     int32_t nhubs, hub_slots;
     T* hub_part;
     uint32_t* hub_cnt;
+    double* hub_dot;   // [panels][nhubs][KS]: w_j . u of each long row (added in fixed order)
     const RowTile* tiles;
     int32_t tiles_per_panel;
+    int32_t stage_nnz;  // largest work item in nonzeros (staged variants)
     int32_t first;   // j == 1: no previous vector
     int32_t renorm;  // update kernel: only recompute the norm of w_next in place
     const T* w_cur;
@@ -97,7 +99,9 @@ struct RecoverParams {
 };
 
 template <typename T> cudaError_t launch_start(const StartParams<T>&, int ks, int panels, cudaStream_t);
-template <typename T> cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, cudaStream_t);
+template <typename T>
+cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, int variant, cudaStream_t);
+constexpr int kStepVariants = 6;
 template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
 template <typename T> cudaError_t launch_recover(const RecoverParams<T>&, int ks, int panels, cudaStream_t);

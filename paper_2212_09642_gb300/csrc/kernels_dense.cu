@@ -11,12 +11,17 @@
 // in shared memory, one warp per column, lanes owning its rows.
 #include <float.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "kernels.h"
 
 namespace vne {
 
 __host__ __device__ __forceinline__ double f_entropy(double x) { return x > 0.0 ? -x * log(x) : 0.0; }
+
+#ifndef __CUDA_ARCH__
+static inline double rsqrt(double v) { return 1.0 / sqrt(v); }
+#endif
 
 // One implicit QR sweep framework.  d[0..n), e[0..n-1) are overwritten by the
 // eigenvalues / zeros; `rot(k, c, s)` is called for every Givens rotation
@@ -45,14 +50,19 @@ __host__ __device__ bool symtri_qr(double* d, double* e, int n, Rot rot) {
         double mu = d[hi] - b2 / den;
         double x = d[lo] - mu, y = e[lo];
         for (int k = lo; k < hi; k++) {
-            double r = hypot(x, y);
-            double c, s;
-            if (r == 0.0) {
+            // Givens rotation from one reciprocal square root (cheaper than
+            // hypot and two divisions on an FP64-poor GPU)
+            double r2 = x * x + y * y;
+            double c, s, r;
+            if (r2 == 0.0) {
                 c = 1.0;
                 s = 0.0;
+                r = 0.0;
             } else {
-                c = x / r;
-                s = -y / r;
+                double inv = rsqrt(r2);
+                c = x * inv;
+                s = -y * inv;
+                r = r2 * inv;
             }
             if (k > lo) e[k - 1] = r;
             double a = d[k], b = e[k], cc = d[k + 1];
@@ -74,8 +84,9 @@ __host__ __device__ bool symtri_qr(double* d, double* e, int n, Rot rot) {
 template <int MAXM>
 __global__ void k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
                                const double* __restrict__ norm2, const double* __restrict__ scale, int count,
-                               int m, int ld, double* __restrict__ psi) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+                               int m, int ld, double* __restrict__ psi, int cols_per_cta) {
+    if ((int)threadIdx.x >= cols_per_cta) return;
+    int c = blockIdx.x * cols_per_cta + threadIdx.x;
     if (c >= count) return;
     double d[MAXM], e[MAXM], z[MAXM];
     int n = m;
@@ -154,10 +165,18 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    dim3 block(64), grid((count + 63) / 64);
-    if (m <= 32) k_tridiag_quad<32><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
-    else if (m <= 64) k_tridiag_quad<64><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
-    else if (m <= 128) k_tridiag_quad<128><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);
+    // columns per CTA (one warp per CTA): fewer columns per warp spread the
+    // FP64 work over more SMs when there are few columns
+    static int cpw = -1;
+    if (cpw < 0) {
+        const char* e = getenv("VNE_TRIDIAG_COLS_PER_WARP");
+        cpw = e ? atoi(e) : 32;
+        if (cpw < 1 || cpw > 32) cpw = 32;
+    }
+    dim3 block(32), grid((count + cpw - 1) / cpw);
+    if (m <= 32) k_tridiag_quad<32><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
+    else if (m <= 64) k_tridiag_quad<64><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
+    else if (m <= 128) k_tridiag_quad<128><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -175,12 +194,15 @@ cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const d
 
 // ---------------------------------------------------------------------------
 // Gram C = X^T Y, 64 x 64 output tile per CTA, rows split into chunks.
-// Products accumulate in the data precision over 64-row tiles, then in FP64.
+// Each thread owns a 4 x 4 block of the tile; the 64-row slabs of X and Y are
+// staged transposed-free in shared memory ([row][col], float4-aligned).
+// Products accumulate in the data precision over one 64-row slab, then in
+// FP64 across slabs.
 template <typename T, int KS>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, const T* __restrict__ Y, int ky,
                                               int n, int rows_per_chunk, int tiles_y, double* __restrict__ part) {
-    __shared__ T Xs[64][65];
-    __shared__ T Ys[64][65];
+    __shared__ __align__(16) T Xs[64][64];
+    __shared__ __align__(16) T Ys[64][64];
     const int chunk = blockIdx.x;
     const int tx0 = (blockIdx.y / tiles_y) * 64, ty0 = (blockIdx.y % tiles_y) * 64;
     const int r_begin = chunk * rows_per_chunk;
@@ -192,6 +214,7 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, c
 #pragma unroll
         for (int b = 0; b < 4; b++) dacc[a][b] = 0.0;
     for (int rt = r_begin; rt < r_end; rt += 64) {
+        // each panel row holds KS consecutive columns: copy whole KS-runs
         for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
             int rl = idx / 64, cl = idx % 64;
             int r = rt + rl;
@@ -210,7 +233,7 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, c
         for (int a = 0; a < 4; a++)
 #pragma unroll
             for (int b = 0; b < 4; b++) acc[a][b] = (T)0;
-#pragma unroll 8
+#pragma unroll 4
         for (int rl = 0; rl < 64; rl++) {
             T xa[4], yb[4];
 #pragma unroll
@@ -266,45 +289,63 @@ cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, d
 }
 
 // ---------------------------------------------------------------------------
-// Out = In2 + coef * In * M over 32-row tiles; M (FP64 [kin][kout]) staged in smem
-// in the data precision.  8 threads per row, 16 output columns per thread.
+// Out = In2 + coef * In * M.  Persistent CTAs: M (FP64 [kin][kout]) is staged
+// once per CTA in shared memory in the data precision, then 64-row tiles of
+// In are streamed through shared memory (stored transposed, [k][row]); each
+// thread owns 4 rows x 8 output columns.
 template <typename T, int KS>
 __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ In, int kin, const double* __restrict__ M,
                                                int kout, const T* __restrict__ In2, T* __restrict__ Out, int n,
                                                double coef) {
-    extern __shared__ unsigned char smraw[];
-    T* Ms = reinterpret_cast<T*>(smraw);  // [kin][128]
-    T* Ins = Ms + (size_t)kin * 128;      // [32][kin]
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Ms = reinterpret_cast<T*>(smraw);          // [kin][128]
+    T* Ist = Ms + (size_t)kin * 128;              // [kin][64]  (transposed tile)
     for (int idx = threadIdx.x; idx < kin * 128; idx += 256) {
         int a = idx / 128, b = idx % 128;
         Ms[idx] = (b < kout) ? (T)(coef * M[(size_t)a * kout + b]) : (T)0;
     }
-    const int r0 = blockIdx.x * 32;
-    for (int idx = threadIdx.x; idx < 32 * kin; idx += 256) {
-        int rl = idx / kin, c = idx % kin;
-        int r = r0 + rl;
-        Ins[idx] = (r < n) ? In[(size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS)] : (T)0;
-    }
-    __syncthreads();
-    const int rl = threadIdx.x / 8, cb = (threadIdx.x % 8) * 16;
-    const int r = r0 + rl;
-    if (r >= n || cb >= kout) return;
-    T acc[16];
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // rows ty*4.., cols tx*8..
+    const int ntiles = (n + 63) / 64;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * 64;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 64 * kin; idx += 256) {
+            int c = idx / 64, rl = idx % 64;
+            int r = r0 + rl;
+            Ist[idx] = (r < n) ? In[(size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS)] : (T)0;
+        }
+        __syncthreads();
+        if (tx * 8 >= kout) continue;
+        T acc[4][8];
 #pragma unroll
-    for (int q = 0; q < 16; q++) acc[q] = (T)0;
-    for (int k = 0; k < kin; k++) {
-        T a = Ins[rl * kin + k];
+        for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int q = 0; q < 16; q++) acc[q] += a * Ms[k * 128 + cb + q];
-    }
+            for (int b = 0; b < 8; b++) acc[a][b] = (T)0;
+        for (int k = 0; k < kin; k++) {
+            T av[4], bv[8];
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-        int c = cb + q;
-        if (c < kout) {
-            size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
-            T v = acc[q];
-            if (In2) v += In2[o];
-            Out[o] = v;
+            for (int a = 0; a < 4; a++) av[a] = Ist[k * 64 + ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 8; b++) bv[b] = Ms[k * 128 + tx * 8 + b];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 8; b++) acc[a][b] += av[a] * bv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const int r = r0 + ty * 4 + a;
+            if (r >= n) continue;
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int c = tx * 8 + b;
+                if (c < kout) {
+                    size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
+                    T v = acc[a][b];
+                    if (In2) v += In2[o];
+                    Out[o] = v;
+                }
+            }
         }
     }
 }
@@ -313,14 +354,19 @@ template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
                          double coef, cudaStream_t st) {
     if (kout > 128 || kin > 128) return cudaErrorInvalidValue;
-    size_t smem = ((size_t)kin * 128 + 32 * (size_t)kin) * sizeof(T);
-    dim3 grid((n + 31) / 32);
+    size_t smem = ((size_t)kin * 128 + 64 * (size_t)kin) * sizeof(T);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int ntiles = (n + 63) / 64;
+    int per_sm = sizeof(T) == 4 ? 2 : 1;
+    dim3 grid(ntiles < sms * per_sm ? ntiles : sms * per_sm);
 #define VNE_APPLY_CASE(KSV)                                                                                  \
     if (ks == KSV) {                                                                                        \
         cudaError_t e = cudaFuncSetAttribute(k_apply<T, KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smem);                                                    \
         if (e != cudaSuccess) return e;                                                                     \
-        k_apply<T, KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef);                            \
+        k_apply<T, KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef);                      \
         return cudaGetLastError();                                                                          \
     }
     VNE_APPLY_CASE(4)

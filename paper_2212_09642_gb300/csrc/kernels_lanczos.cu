@@ -176,8 +176,15 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
 // ---------------------------------------------------------------------------
 // Step kernel: u = sigma_j M w_j - beta_{j-1} sigma_{j-1} w_{j-1},
 // alpha_j = sigma_j (w_j . u).  One warp per work item.
-template <typename T, int KS, bool VALUED>
-__global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
+// Variants (selected by the schedule autotuner): MINB = CTAs per SM the
+// register allocation must allow, UNR = independent neighbour gathers in
+// flight per row group, STREAM = write u with an evict-first hint, STAGE =
+// copy the work item's column indices and row offsets into shared memory
+// with coalesced loads first, so each gather waits on a shared-memory read
+// instead of a dependent global index load (dynamic smem: item_nnz ints per
+// warp + 65 row offsets per warp).
+template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE>
+__global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;  // lanes per row
     constexpr int G = 32 / LPR;    // row groups per warp
@@ -190,66 +197,87 @@ __global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
     const T* __restrict__ Wp = p.w_prev + pofs;
     T* __restrict__ U = p.u + pofs;
     const int cofs = sub * CPL;
-    const size_t so = (size_t)seg * p.K + panel * KS + cofs;
 
-    T sig[CPL], cp[CPL], dot[CPL];
-#pragma unroll
-    for (int q = 0; q < CPL; q++) {
-        sig[q] = (T)p.sig_cur[so + q];
-        cp[q] = p.first ? (T)0 : (T)(p.beta_prev[so + q] * p.sig_prev[so + q]);
-        dot[q] = (T)0;
+    // per-column coefficients staged in shared memory (keeps registers for gathers)
+    __shared__ T s_sig[KS], s_cp[KS];
+    if (threadIdx.x < KS) {
+        const size_t o = (size_t)seg * p.K + panel * KS + threadIdx.x;
+        s_sig[threadIdx.x] = (T)p.sig_cur[o];
+        s_cp[threadIdx.x] = p.first ? (T)0 : (T)(p.beta_prev[o] * p.sig_prev[o]);
     }
+    __syncthreads();
+    T dot[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) dot[q] = (T)0;
 
-    auto epilogue = [&](int r, const T (&acc)[CPL], int deg) {
+    auto epilogue = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL]) {
         T x[CPL], xp[CPL], uu[CPL];
         load_lane(W + (size_t)r * KS + cofs, x);
         if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
 #pragma unroll
         for (int q = 0; q < CPL; q++) {
             T ax = VALUED ? acc[q] : ((T)deg * x[q] - acc[q]);
-            T v = sig[q] * ax;
-            if (!p.first) v -= cp[q] * xp[q];
+            T v = s_sig[cofs + q] * ax;
+            if (!p.first) v -= s_cp[cofs + q] * xp[q];
             uu[q] = v;
-            dot[q] += x[q] * v;
+            dt[q] += x[q] * v;
         }
-        store_lane(U + (size_t)r * KS + cofs, uu);
+        if (STREAM) store_lane_stream(U + (size_t)r * KS + cofs, uu);
+        else store_lane(U + (size_t)r * KS + cofs, uu);
     };
 
     const WorkItem it = p.items[(size_t)cta * VNE_WARPS + warp];
+    extern __shared__ int32_t s_stage[];
+    int32_t* s_col = s_stage + warp * (p.stage_nnz + 68);
+    int32_t* s_rp = s_col + p.stage_nnz;
+    int nb_item = it.nnz_begin;
+    if (STAGE && it.rows != 0) {
+        const int cnt = it.nnz_end - it.nnz_begin;
+        for (int i = lane; i < cnt; i += 32) s_col[i] = __ldcs(p.col + nb_item + i);
+        if (it.rows > 0)
+            for (int i = lane; i <= it.rows; i += 32) s_rp[i] = p.rowptr[it.row + i];
+        __syncwarp();
+    }
+    auto colidx = [&](int k) -> int { return STAGE ? s_col[k - nb_item] : __ldg(p.col + k); };
     if (it.rows > 0) {
         for (int r = it.row + g; r < it.row + it.rows; r += G) {
-            const int kb = p.rowptr[r], ke = p.rowptr[r + 1];
+            const int kb = STAGE ? s_rp[r - it.row] : p.rowptr[r];
+            const int ke = STAGE ? s_rp[r - it.row + 1] : p.rowptr[r + 1];
             T acc[CPL];
 #pragma unroll
             for (int q = 0; q < CPL; q++) acc[q] = (T)0;
             int k = kb;
-            for (; k + 4 <= ke; k += 4) {
-                int c0 = __ldg(p.col + k), c1 = __ldg(p.col + k + 1), c2 = __ldg(p.col + k + 2),
-                    c3 = __ldg(p.col + k + 3);
-                T a0[CPL], a1[CPL], a2[CPL], a3[CPL];
-                load_lane(W + (size_t)c0 * KS + cofs, a0);
-                load_lane(W + (size_t)c1 * KS + cofs, a1);
-                load_lane(W + (size_t)c2 * KS + cofs, a2);
-                load_lane(W + (size_t)c3 * KS + cofs, a3);
-                if (VALUED) {
-                    T v0 = __ldg(p.vals + k), v1 = __ldg(p.vals + k + 1), v2 = __ldg(p.vals + k + 2),
-                      v3 = __ldg(p.vals + k + 3);
+            for (; k + UNR <= ke; k += UNR) {
+                int cc[UNR];
 #pragma unroll
-                    for (int q = 0; q < CPL; q++) acc[q] += v0 * a0[q] + v1 * a1[q] + v2 * a2[q] + v3 * a3[q];
+                for (int u = 0; u < UNR; u++) cc[u] = colidx(k + u);
+                T a[UNR][CPL];
+#pragma unroll
+                for (int u = 0; u < UNR; u++) load_lane(W + (size_t)cc[u] * KS + cofs, a[u]);
+                if (VALUED) {
+                    T v[UNR];
+#pragma unroll
+                    for (int u = 0; u < UNR; u++) v[u] = __ldg(p.vals + k + u);
+#pragma unroll
+                    for (int u = 0; u < UNR; u++)
+#pragma unroll
+                        for (int q = 0; q < CPL; q++) acc[q] += v[u] * a[u][q];
                 } else {
 #pragma unroll
-                    for (int q = 0; q < CPL; q++) acc[q] += (a0[q] + a1[q]) + (a2[q] + a3[q]);
+                    for (int u = 0; u < UNR; u += 2)
+#pragma unroll
+                        for (int q = 0; q < CPL; q++) acc[q] += a[u][q] + a[u + 1][q];
                 }
             }
             for (; k < ke; k++) {
-                int c0 = __ldg(p.col + k);
+                int c0 = colidx(k);
                 T a0[CPL];
                 load_lane(W + (size_t)c0 * KS + cofs, a0);
                 T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
 #pragma unroll
                 for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
             }
-            epilogue(r, acc, ke - kb);
+            epilogue(r, acc, ke - kb, dot);
         }
     } else if (it.rows < 0) {
         // one chunk of a long row, all groups of the warp share it
@@ -259,7 +287,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
 #pragma unroll
         for (int q = 0; q < CPL; q++) acc[q] = (T)0;
         for (int k = it.nnz_begin + g; k < it.nnz_end; k += G) {
-            int c0 = __ldg(p.col + k);
+            int c0 = colidx(k);
             T a0[CPL];
             load_lane(W + (size_t)c0 * KS + cofs, a0);
             T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
@@ -283,14 +311,23 @@ __global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
         if (last) {
             __threadfence();
             if (g == 0) {
-                T tot[CPL];
+                T tot[CPL], hd[CPL];
 #pragma unroll
-                for (int q = 0; q < CPL; q++) tot[q] = (T)0;
+                for (int q = 0; q < CPL; q++) {
+                    tot[q] = (T)0;
+                    hd[q] = (T)0;
+                }
                 for (int c = 0; c < h.chunks; c++)
 #pragma unroll
                     for (int q = 0; q < CPL; q++) tot[q] += ld_cg(hp + (size_t)c * KS + cofs + q);
                 const int r = h.row;
-                epilogue(r, tot, p.rowptr[r + 1] - p.rowptr[r]);
+                epilogue(r, tot, p.rowptr[r + 1] - p.rowptr[r], hd);
+                // the long row's share of w_j . u goes to its own slot, summed
+                // in hub order by the reducing CTA (independent of which CTA
+                // finished the row)
+#pragma unroll
+                for (int q = 0; q < CPL; q++)
+                    p.hub_dot[((size_t)panel * p.nhubs + it.row) * KS + cofs + q] = (double)hd[q];
             }
             if (lane == 0) p.hub_cnt[(size_t)panel * p.nhubs + it.row] = 0u;
         }
@@ -319,9 +356,20 @@ __global__ void __launch_bounds__(VNE_THREADS) k_step(StepParams<T> p) {
     const SegInfo sg = p.seg[seg];
     if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + seg, panel, p.ctas_per_panel,
                             sg.cta_begin, sg.cta_count, tot)) {
+        // add the long rows' shares in a fixed order (strided over the CTA)
+        __shared__ double hred[VNE_THREADS];
+        constexpr int NS = VNE_THREADS / KS;
+        const int c = threadIdx.x % KS, s = threadIdx.x / KS;
+        double hacc = 0.0;
+        for (int h = s; h < sg.hub_count; h += NS)
+            hacc += ld_cg(&p.hub_dot[((size_t)panel * p.nhubs + sg.hub_begin + h) * KS + c]);
+        hred[threadIdx.x] = hacc;
+        __syncthreads();
         if (threadIdx.x < KS) {
+            double t = tot[threadIdx.x];
+            for (int q = 0; q < NS; q++) t += hred[q * KS + threadIdx.x];
             size_t o = (size_t)seg * p.K + panel * KS + threadIdx.x;
-            p.alpha[o] = p.sig_cur[o] * tot[threadIdx.x];
+            p.alpha[o] = p.sig_cur[o] * t;
         }
     }
 }
@@ -466,10 +514,11 @@ __global__ void __launch_bounds__(VNE_THREADS) k_recover(RecoverParams<T> p) {
     const RowTile t = p.tiles[tile];
     const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
     const int cofs = sub * CPL;
-    extern __shared__ double s_gamma[];  // [m][KS]
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T* s_gamma = reinterpret_cast<T*>(s_raw);  // [m][KS], converted once to the data precision
     for (int idx = threadIdx.x; idx < p.m * KS; idx += blockDim.x) {
         int j = idx / KS, c = idx % KS;
-        s_gamma[idx] = p.gamma[(size_t)j * p.K + panel * KS + c];
+        s_gamma[idx] = (T)p.gamma[(size_t)j * p.K + panel * KS + c];
     }
     __syncthreads();
     const size_t pofs = (size_t)panel * p.n_total * KS;
@@ -477,11 +526,23 @@ __global__ void __launch_bounds__(VNE_THREADS) k_recover(RecoverParams<T> p) {
         T acc[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; q++) acc[q] = (T)0;
-        for (int j = 0; j < p.m; j++) {
-            T x[CPL];
-            load_lane_stream(p.basis + (size_t)j * p.slot_stride + pofs + (size_t)r * KS + cofs, x);
+        const T* b = p.basis + pofs + (size_t)r * KS + cofs;
+        int j = 0;
+        // eight independent streaming loads in flight per thread
+        for (; j + 8 <= p.m; j += 8) {
+            T x[8][CPL];
 #pragma unroll
-            for (int q = 0; q < CPL; q++) acc[q] += (T)s_gamma[j * KS + cofs + q] * x[q];
+            for (int u = 0; u < 8; u++) load_lane_stream(b + (size_t)(j + u) * p.slot_stride, x[u]);
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+#pragma unroll
+                for (int q = 0; q < CPL; q++) acc[q] += s_gamma[(j + u) * KS + cofs + q] * x[u][q];
+        }
+        for (; j < p.m; j++) {
+            T x[CPL];
+            load_lane_stream(b + (size_t)j * p.slot_stride, x);
+#pragma unroll
+            for (int q = 0; q < CPL; q++) acc[q] += s_gamma[j * KS + cofs + q] * x[q];
         }
         store_lane(p.y + pofs + (size_t)r * KS + cofs, acc);
     }
@@ -553,11 +614,23 @@ cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream
     return cudaGetLastError();
 }
 
+// Step-kernel variants: {MINB, UNR, STREAM, STAGE}.  FP64 uses variant 0 only.
+#define VNE_STEP_VARIANTS(T, KS, VALUED, v, st, grid, p, smem)                                                   \
+    switch (sizeof(T) == 8 ? 0 : (v)) {                                                                          \
+        case 1: k_step<T, KS, VALUED, 6, 4, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
+        case 2: k_step<T, KS, VALUED, 6, 8, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
+        case 3: k_step<T, KS, VALUED, 8, 4, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
+        case 4: k_step<T, KS, VALUED, 6, 4, true, true><<<grid, VNE_THREADS, smem, st>>>(p); break;             \
+        case 5: k_step<T, KS, VALUED, 4, 8, true, true><<<grid, VNE_THREADS, smem, st>>>(p); break;             \
+        default: k_step<T, KS, VALUED, 4, 4, false, false><<<grid, VNE_THREADS, 0, st>>>(p); break;             \
+    }
+
 template <typename T>
-cudaError_t launch_step(const StepParams<T>& p, int ks, int panels, bool valued, cudaStream_t st) {
+cudaError_t launch_step(const StepParams<T>& p, int ks, int panels, bool valued, int variant, cudaStream_t st) {
     dim3 grid(panels * p.ctas_per_panel);
-    if (valued) VNE_DISPATCH_KS(T, ks, (k_step<T, KS, true><<<grid, VNE_THREADS, 0, st>>>(p)));
-    else VNE_DISPATCH_KS(T, ks, (k_step<T, KS, false><<<grid, VNE_THREADS, 0, st>>>(p)));
+    const size_t smem = (size_t)VNE_WARPS * (p.stage_nnz + 68) * sizeof(int32_t);
+    if (valued) VNE_DISPATCH_KS(T, ks, VNE_STEP_VARIANTS(T, KS, true, variant, st, grid, p, smem));
+    else VNE_DISPATCH_KS(T, ks, VNE_STEP_VARIANTS(T, KS, false, variant, st, grid, p, smem));
     return cudaGetLastError();
 }
 
@@ -580,7 +653,7 @@ cudaError_t launch_reorth(const ReorthParams<T>& p, const ReorthCoefParams& c, i
 
 template <typename T>
 cudaError_t launch_recover(const RecoverParams<T>& p, int ks, int panels, cudaStream_t st) {
-    size_t smem = (size_t)p.m * ks * sizeof(double);
+    size_t smem = (size_t)p.m * ks * sizeof(T);
     dim3 grid(panels * p.tiles_per_panel);
     VNE_DISPATCH_KS(T, ks, (k_recover<T, KS><<<grid, VNE_THREADS, smem, st>>>(p)));
     return cudaGetLastError();
@@ -605,7 +678,7 @@ cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin
 
 #define VNE_INST(T)                                                                                        \
     template cudaError_t launch_start<T>(const StartParams<T>&, int, int, cudaStream_t);                   \
-    template cudaError_t launch_step<T>(const StepParams<T>&, int, int, bool, cudaStream_t);               \
+    template cudaError_t launch_step<T>(const StepParams<T>&, int, int, bool, int, cudaStream_t);          \
     template cudaError_t launch_update<T>(const StepParams<T>&, int, int, cudaStream_t);                   \
     template cudaError_t launch_reorth<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
     template cudaError_t launch_recover<T>(const RecoverParams<T>&, int, int, cudaStream_t);               \

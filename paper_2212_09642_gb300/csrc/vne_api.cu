@@ -21,6 +21,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <tuple>
 #include <map>
 #include <memory>
 #include <new>
@@ -67,6 +69,17 @@ struct vne_ctx {
     };
     std::vector<Pending> pending;
     size_t ev_next = 0;
+    bool time_steps = false;          // autotuner: time the whole step loop
+    cudaEvent_t loop_ev[2] = {nullptr, nullptr};
+    // autotuned schedules, shared by matrices of the same shape
+    struct TuneKey {
+        int64_t n, nnz, maxdeg;
+        int fp64, pattern;
+        bool operator<(const TuneKey& o) const {
+            return std::tie(n, nnz, maxdeg, fp64, pattern) < std::tie(o.n, o.nnz, o.maxdeg, o.fp64, o.pattern);
+        }
+    };
+    std::map<TuneKey, std::array<int, 3>> tune_cache;
 };
 
 struct Problem;
@@ -86,6 +99,9 @@ struct vne_matrix {
     int32_t* d_node_id = nullptr;
     Problem* prob = nullptr;        // cached schedule
     int prob_item_nnz = -1;
+    bool tuned = false;             // autotuned schedule (vne_autotune)
+    int tuned_panel = 0, tuned_item_nnz = 0, tuned_variant = 0;
+    int64_t maxdeg = 0;
 };
 
 namespace {
@@ -198,6 +214,7 @@ struct Problem {
     std::vector<int32_t> cta_seg;
     std::vector<RowTile> tiles;
     int32_t hub_slots = 0;
+    int32_t stage_nnz = 0;   // largest item (nonzeros)
     // device copies (owned)
     SegInfo* d_segs = nullptr;
     WorkItem* d_items = nullptr;
@@ -225,21 +242,26 @@ const int kTileRows = 4096;
 // CSR): runs of short rows with about `target` nonzeros (at most 64 rows),
 // and rows longer than `long_thresh` split into chunks of `chunk` nonzeros.
 void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_t seg, int target, Problem& P) {
-    const int64_t long_thresh = std::max(2 * target, 128);
-    const int64_t chunk = std::max(target, 64);
+    // every item holds at most `target` nonzeros: short rows are packed into
+    // runs (at most 64 rows), rows longer than `target` are split into chunks
+    const int64_t chunk = std::max(target, 32);
     const int max_rows = 64;
     const size_t first_item = P.items.size();
+    SegInfo& sg0 = P.segs[seg];
+    sg0.hub_begin = (int32_t)P.hubs.size();
     int32_t blk_start = -1, blk_rows = 0;
     int64_t blk_nnz = 0;
     auto flush = [&]() {
-        if (blk_rows > 0) P.items.push_back(WorkItem{blk_start, blk_rows, 0, 0});
+        if (blk_rows > 0)
+            P.items.push_back(WorkItem{blk_start, blk_rows, (int32_t)rowptr[blk_start],
+                                       (int32_t)rowptr[blk_start + blk_rows]});
         blk_start = -1;
         blk_rows = 0;
         blk_nnz = 0;
     };
     for (int32_t r = row_begin; r < row_begin + rows; r++) {
         int64_t deg = rowptr[r + 1] - rowptr[r];
-        if (deg > long_thresh) {
+        if (deg > chunk) {
             flush();
             int32_t nch = (int32_t)((deg + chunk - 1) / chunk);
             int32_t h = (int32_t)P.hubs.size();
@@ -251,14 +273,17 @@ void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_
             }
             continue;
         }
+        if (blk_rows > 0 && (blk_nnz + deg > chunk || blk_rows >= max_rows)) flush();
         if (blk_rows == 0) blk_start = r;
         blk_rows++;
         blk_nnz += deg;
-        if (blk_nnz >= target || blk_rows >= max_rows) flush();
     }
     flush();
     while ((P.items.size() - first_item) % VNE_WARPS) P.items.push_back(WorkItem{0, 0, 0, 0});
+    for (size_t i = first_item; i < P.items.size(); i++)
+        P.stage_nnz = std::max<int32_t>(P.stage_nnz, P.items[i].nnz_end - P.items[i].nnz_begin);
     SegInfo& sg = P.segs[seg];
+    sg.hub_count = (int32_t)P.hubs.size() - sg.hub_begin;
     sg.cta_begin = (int32_t)(first_item / VNE_WARPS);
     sg.cta_count = (int32_t)((P.items.size() - first_item) / VNE_WARPS);
     for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
@@ -289,8 +314,25 @@ double default_tau(bool fp64) { return fp64 ? 1e-13 : 1e-10; }
 
 int default_item_nnz(const vne_options* o) { return (o && o->item_nnz > 0) ? o->item_nnz : 256; }
 
+struct Sched {
+    int ks, item_nnz, variant;
+};
+
+int choose_panel(bool fp64, const vne_options* opt, int64_t n);
+
+// Schedule for a call: explicit options win, then the matrix's autotuned
+// choice, then the built-in defaults.
+Sched resolve_sched(const vne_matrix* M, const vne_options* o) {
+    Sched s;
+    s.ks = (o && o->panel > 0) ? o->panel : (M->tuned ? M->tuned_panel : choose_panel(M->fp64, o, M->n));
+    s.item_nnz = (o && o->item_nnz > 0) ? o->item_nnz : (M->tuned ? M->tuned_item_nnz : 256);
+    s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 0);
+    if (M->fp64) s.variant = 0;
+    return s;
+}
+
 Problem* matrix_problem(vne_matrix* M, const vne_options* opt) {
-    int target = default_item_nnz(opt);
+    int target = resolve_sched(M, opt).item_nnz;
     double taurel = (opt && opt->breakdown_tol > 0) ? opt->breakdown_tol : default_tau(M->fp64);
     if (M->prob && M->prob_item_nnz == target && M->prob->segs[0].tau == taurel * M->normM) return M->prob;
     delete M->prob;
@@ -343,7 +385,7 @@ struct BlockOut {
 
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
-               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out) {
+               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
     const int Kp = panels * ks;
@@ -368,6 +410,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     const int64_t nnz_total = P.nnz_total;
     T* hub_part = ws_get_t<T>(ctx, "hub_part", (size_t)panels * std::max(P.hub_slots, 1) * ks);
     uint32_t* hub_cnt = ws_get_t<uint32_t>(ctx, "hub_cnt", (size_t)panels * std::max(nh, 1), true);
+    double* hub_dot = ws_get_t<double>(ctx, "hub_dot", (size_t)panels * std::max(nh, 1) * ks);
     // per-column scale (segment scale) for the quadrature
     std::vector<double> hscale(SK);
     for (int s = 0; s < S; s++)
@@ -415,6 +458,8 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     p.hub_slots = std::max(P.hub_slots, 1);
     p.hub_part = hub_part;
     p.hub_cnt = hub_cnt;
+    p.hub_dot = hub_dot;
+    p.stage_nnz = std::max(P.stage_nnz, 1);
     p.tiles = P.d_tiles;
     p.tiles_per_panel = tiles;
     p.u = u;
@@ -426,6 +471,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
         rcoef = ws_get_t<double>(ctx, "reorth.coef", (size_t)m * Kp);
         rpart = ws_get_t<double>(ctx, "reorth.part", (size_t)panels * m * tiles * ks);
     }
+    if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[0], st));
     for (int j = 1; j <= m; j++) {
         p.first = (j == 1);
         p.renorm = 0;
@@ -443,7 +489,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             e0 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
         }
-        VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, st));
+        VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
         if (ctx->profile) {
             e1 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
@@ -490,6 +536,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             ctx->launches += 7;
         }
     }
+    if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[1], st));
     VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m, SK, psi, st));
     ctx->launches += 1;
     out.K = K;
@@ -545,7 +592,8 @@ template <typename T>
 std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource src, int ncols, int m) {
     vne_ctx* ctx = M->ctx;
     Problem* P = matrix_problem(M, o);
-    int ks = choose_panel(M->fp64, o, M->n);
+    Sched sc = resolve_sched(M, o);
+    int ks = sc.ks;
     check_ks<T>(ctx, ks);
     int lim = block_limit(o);
     bool reorth = want_reorth(M, o);
@@ -557,7 +605,7 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
         if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
         if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
         BlockOut out;
-        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi.begin() + b0);
     }
@@ -592,6 +640,7 @@ extern "C" void vne_options_default(vne_options* o) {
     o->n_inf_poles = 2;
     o->cg_max_iter = 10000;
     o->cg_tol = 1e-8;
+    o->step_variant = -1;
 }
 
 extern "C" const char* vne_version(void) { return "vne 0.1 (sm_103a)"; }
@@ -618,6 +667,9 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
     else cudaDeviceSynchronize();
     for (auto& kv : ctx->ws)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->loop_ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return VNE_OK;
 }
@@ -761,6 +813,16 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     M->h_rowptr.swap(rp);
     M->h_col.swap(ci);
     M->h_vals.swap(va);
+    M->maxdeg = maxdeg;
+    {
+        auto it = ctx->tune_cache.find(vne_ctx::TuneKey{M->n, M->nnz, maxdeg, (int)M->fp64, (int)M->pattern});
+        if (it != ctx->tune_cache.end()) {
+            M->tuned = true;
+            M->tuned_panel = it->second[0];
+            M->tuned_item_nnz = it->second[1];
+            M->tuned_variant = it->second[2];
+        }
+    }
     *out = M.release();
     VNE_API_END(ctx)
 }
@@ -806,7 +868,8 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
         dvec = d;
     }
     Problem* P = matrix_problem(M, &o);
-    int ks = choose_panel(M->fp64, &o, M->n);
+    Sched sc = resolve_sched(M, &o);
+    int ks = sc.ks;
     bool reorth = want_reorth(M, &o);
     int lim = block_limit(&o);
     for (int b0 = 0; b0 < k; b0 += lim) {
@@ -819,10 +882,10 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
         BlockOut out;
         if (M->fp64) {
             check_ks<double>(ctx, ks);
-            run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+            run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
         } else {
             check_ks<float>(ctx, ks);
-            run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out);
+            run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
         }
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi + b0);
@@ -882,7 +945,8 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     cudaStream_t st = ctx->stream;
     Problem* P = matrix_problem(M, o);
     const int n = (int)M->n;
-    int ks = choose_panel(M->fp64, o, M->n);
+    Sched sc = resolve_sched(M, o);
+    int ks = sc.ks;
     check_ks<T>(ctx, ks);
     VNE_REQUIRE(ctx, Nr >= 1 && Nr <= 128 && NH >= 0 && NH <= 4096, VNE_EINVAL, "need 1 <= N_r <= 128, 0 <= N_H");
     const uint64_t sm = seed_mix(seed);
@@ -893,7 +957,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     s.col_begin = 0;
     s.ncols = Nr;
     BlockOut sk;
-    run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk);
+    run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant);
     const int Kp = sk.Kp;
     double* zvec = ws_get_t<double>(ctx, "zvec", (size_t)m * Kp);
     VNE_TRY_CUDA(ctx, launch_tridiag_fvec(sk.alpha, sk.beta, sk.scale, Kp, m, Kp, zvec, st));
@@ -921,7 +985,13 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     double* Minv = ws_get_t<double>(ctx, "Minv", (size_t)Kp * Kp);
     int* drank = ws_get_t<int>(ctx, "rank", 2);
     T* Q1 = ws_get_t<T>(ctx, "Q1", blk);
-    T* Q = ws_get_t<T>(ctx, "Q", blk);
+    // Q and (I - Q Q^T) G share one buffer: Q in block columns [0, Kp), the
+    // projected Hutchinson vectors in [Kp, Kp + Kg), so one Lanczos block
+    // evaluates all N_r + N_H quadratic forms.
+    const int Kg = NH > 0 ? ((NH + ks - 1) / ks) * ks : 0;
+    VNE_REQUIRE(ctx, Kg <= 128, VNE_EUNSUPPORTED, "N_H > 128 not supported in one projection block");
+    T* QG = ws_get_t<T>(ctx, "QG", (size_t)(Kp + Kg) * n);
+    T* Q = QG;
     const double tol = M->fp64 ? 1e-13 : 1e-5;
     VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, st));
@@ -930,68 +1000,55 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, st));
     ctx->launches += 10;  // 2 x (gram + reduce + factor + apply)
-    int hr[2] = {0, 0};
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
-    const int r = std::min(hr[0], hr[1]);
-    // 3. tr(Q^T f(A) Q): Lanczos quadratures of the r columns of Q
-    double low = 0.0;
-    if (r > 0) {
-        StartSource sq{};
-        sq.kind = SRC_PANEL;
-        sq.ncols = r;
-        BlockOut qo;
-        run_block<T>(ctx, *P, sq, Q, r, ks, m, want_reorth(M, o), false, M->desing, "q", qo);
-        std::vector<double> h = download(ctx, qo.psi, r);
-        for (double v : h) low += v;
-    }
-    // 4. residual part: G' = (I - Q Q^T) G, Hutchinson on G'
-    double resid = 0.0;
-    if (NH > 0) {
-        const int Kg = ((NH + ks - 1) / ks) * ks;
+    if (Kg > 0) {
+        // G (Rademacher columns N_r..N_r+N_H-1), then G' = G - Q (Q^T G)
         const size_t gblk = (size_t)Kg * n;
         T* Gr = ws_get_t<T>(ctx, "Graw", gblk);
-        T* Gp = ws_get_t<T>(ctx, "Gproj", gblk);
+        T* Gp = QG + (size_t)Kp * n;
         StartSource sg{};
         sg.kind = SRC_RADEMACHER;
         sg.seed_mixed = sm;
         sg.col_begin = Nr;
         sg.ncols = NH;
-        {
-            // materialise G with the start kernel (no centring)
-            StartParams<T> spp{};
-            spp.src = sg;
-            spp.node_id = P->node_id;
-            spp.seg = P->d_segs;
-            spp.nseg = 1;
-            spp.K = Kg;
-            spp.n_total = n;
-            spp.tiles_per_panel = P->tiles_per_panel();
-            spp.tiles = P->d_tiles;
-            spp.desing = 0;
-            spp.w1 = Gr;
-            spp.mean = ws_get_t<double>(ctx, "mean", Kg);
-            spp.norm2 = ws_get_t<double>(ctx, "g.norm2", Kg);
-            spp.sig1 = ws_get_t<double>(ctx, "g.sig", Kg);
-            spp.part = ws_get_t<double>(ctx, "part", (size_t)(Kg / ks) * P->tiles_per_panel() * ks);
-            spp.counter = ws_get_t<uint32_t>(ctx, "counter", (size_t)(Kg / ks), true);
-            VNE_TRY_CUDA(ctx, launch_start<T>(spp, ks, Kg / ks, st));
-            ctx->launches += 1;
-        }
+        StartParams<T> spp{};
+        spp.src = sg;
+        spp.node_id = P->node_id;
+        spp.seg = P->d_segs;
+        spp.nseg = 1;
+        spp.K = Kg;
+        spp.n_total = n;
+        spp.tiles_per_panel = P->tiles_per_panel();
+        spp.tiles = P->d_tiles;
+        spp.desing = 0;
+        spp.w1 = Gr;
+        spp.mean = ws_get_t<double>(ctx, "mean", Kg);
+        spp.norm2 = ws_get_t<double>(ctx, "g.norm2", Kg);
+        spp.sig1 = ws_get_t<double>(ctx, "g.sig", Kg);
+        spp.part = ws_get_t<double>(ctx, "part", (size_t)(Kg / ks) * P->tiles_per_panel() * ks);
+        spp.counter = ws_get_t<uint32_t>(ctx, "counter", (size_t)(Kg / ks), true);
+        VNE_TRY_CUDA(ctx, launch_start<T>(spp, ks, Kg / ks, st));
         double* C = ws_get_t<double>(ctx, "QtG", (size_t)Kp * Kg);
         double* gpart2 = ws_get_t<double>(ctx, "gram.part2", (size_t)nch * Kp * Kg);
-        VNE_REQUIRE(ctx, Kg <= 128, VNE_EUNSUPPORTED, "N_H > 128 not supported in one projection block");
         VNE_TRY_CUDA(ctx, launch_gram<T>(Q, Kp, Gr, Kg, ks, n, gpart2, nch, C, st));
         VNE_TRY_CUDA(ctx, launch_apply<T>(Q, Kp, C, Kg, Gr, Gp, ks, n, -1.0, st));
-        ctx->launches += 3;
-        StartSource sp{};
-        sp.kind = SRC_PANEL;
-        sp.ncols = NH;
-        BlockOut go;
-        run_block<T>(ctx, *P, sp, Gp, NH, ks, m, want_reorth(M, o), false, M->desing, "q", go);
-        std::vector<double> h = download(ctx, go.psi, NH);
-        for (double v : h) resid += v;
-        resid /= NH;
+        ctx->launches += 4;
+    }
+    int hr[2] = {0, 0};
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    const int r = std::min(hr[0], hr[1]);
+    // 3. all N_r + N_H quadratic forms in one Lanczos block
+    double low = 0.0, resid = 0.0;
+    {
+        StartSource sq{};
+        sq.kind = SRC_PANEL;
+        sq.ncols = Kp + Kg;
+        BlockOut qo;
+        run_block<T>(ctx, *P, sq, QG, Kp + Kg, ks, m, want_reorth(M, o), false, M->desing, "q", qo, sc.variant);
+        std::vector<double> h = download(ctx, qo.psi, Kp + Kg);
+        for (int c = 0; c < r; c++) low += h[c];
+        for (int c = 0; c < NH; c++) resid += h[Kp + c];
+        if (NH > 0) resid /= NH;
     }
     *estimate = low + resid;
     if (parts) {
@@ -1201,6 +1258,7 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     }
     problem_upload(ctx, *P);
     int ks = choose_panel(fp64, &o, ntot);
+    const int variant = (!fp64 && o.step_variant >= 0) ? o.step_variant : 0;
     StartSource s{};
     s.kind = SRC_RADEMACHER;
     s.seed_mixed = seed_mix(seed);
@@ -1212,7 +1270,8 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
         run_block<double>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out);
     } else {
         check_ks<float>(ctx, ks);
-        run_block<float>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out);
+        run_block<float>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out,
+                         variant);
     }
     std::vector<double> psi = download(ctx, out.psi, out.SK);
     for (int i = 0; i < count; i++) {
@@ -1248,4 +1307,82 @@ extern "C" vne_status vne_ctx_stats(const vne_ctx* ctx, int64_t* launches, doubl
             kernel_stats[3 * k + 2] = ctx->stat[k].bytes;
         }
     return VNE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// schedule autotuner
+
+extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_options* chosen,
+                                   double* ms_per_step) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, k >= 1 && k <= 256 && steps >= 2 && steps <= 128, VNE_EINVAL,
+                "autotune needs 1 <= k <= 256 and 2 <= steps <= 128");
+    for (int i = 0; i < 2; i++)
+        if (!ctx->loop_ev[i]) VNE_TRY_CUDA(ctx, cudaEventCreate(&ctx->loop_ev[i]));
+    const int panels_f[3] = {8, 16, 32}, panels_d[3] = {4, 8, 16};
+    const int items[4] = {128, 256, 512, 1024};
+    const int nvar = M->fp64 ? 1 : kStepVariants;
+    double best = 1e300;
+    int bk = 0, bi = 0, bv = 0;
+    const bool was_tuned = M->tuned;
+    M->tuned = false;
+    for (int pi = 0; pi < 3; pi++)
+        for (int ii = 0; ii < 4; ii++)
+            for (int v = 0; v < nvar; v++) {
+                vne_options o;
+                vne_options_default(&o);
+                o.panel = M->fp64 ? panels_d[pi] : panels_f[pi];
+                o.item_nnz = items[ii];
+                o.step_variant = v;
+                o.reorth = 0;
+                Problem* P = matrix_problem(M, &o);
+                StartSource s{};
+                s.kind = SRC_RADEMACHER;
+                s.seed_mixed = seed_mix(12345);
+                s.ncols = k;
+                double ms_min = 1e300;
+                for (int rep = 0; rep < 2; rep++) {
+                    BlockOut out;
+                    ctx->time_steps = true;
+                    if (M->fp64) run_block<double>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v);
+                    else run_block<float>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v);
+                    ctx->time_steps = false;
+                    download(ctx, out.psi, 1);
+                    float ms = 0.f;
+                    VNE_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->loop_ev[0], ctx->loop_ev[1]));
+                    ms_min = std::min(ms_min, (double)ms);
+                }
+                if (ms_min < best) {
+                    best = ms_min;
+                    bk = o.panel;
+                    bi = items[ii];
+                    bv = v;
+                }
+            }
+    // release the tuning block's workspace
+    for (auto it = ctx->ws.begin(); it != ctx->ws.end();) {
+        if (it->first.compare(0, 5, "tune.") == 0) {
+            cudaFree(it->second.ptr);
+            it = ctx->ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    (void)was_tuned;
+    M->tuned = true;
+    M->tuned_panel = bk;
+    M->tuned_item_nnz = bi;
+    M->tuned_variant = bv;
+    ctx->tune_cache[vne_ctx::TuneKey{M->n, M->nnz, M->maxdeg, (int)M->fp64, (int)M->pattern}] = {bk, bi, bv};
+    if (chosen) {
+        vne_options_default(chosen);
+        chosen->panel = bk;
+        chosen->item_nnz = bi;
+        chosen->step_variant = bv;
+    }
+    if (ms_per_step) *ms_per_step = best / steps;
+    VNE_API_END(ctx)
 }

@@ -49,7 +49,7 @@ class vne_options(ctypes.Structure):
     _fields_ = [("reorth", ctypes.c_int32), ("block", ctypes.c_int32), ("panel", ctypes.c_int32),
                 ("item_nnz", ctypes.c_int32), ("n_inf_poles", ctypes.c_int32), ("cg_max_iter", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("step_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 _lib = None
@@ -86,6 +86,7 @@ def _declare(lib):
         "vne_batch_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(vne_options), _P, _P]),
         "vne_ctx_profile": (st, [_P, ctypes.c_int32]),
+        "vne_autotune": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vne_options), _PD]),
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
     }
@@ -117,7 +118,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
-               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc"]
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune"]
 
 
 def _check(status, ctx=None):
@@ -278,6 +279,14 @@ def vne_batch_hutchinson(ctx, mats, num_vectors, krylov_steps, seed, opt=None):
     _check(load().vne_batch_hutchinson(arr, len(mats), int(num_vectors), int(krylov_steps), int(seed) & (2**64 - 1),
                                        ctypes.byref(o), _ptr(est), _ptr(se)), ctx)
     return est, se
+
+
+def vne_autotune(ctx, mat, k, steps=8):
+    """Pick the fastest schedule for `mat` (kept as its default); returns (options, ms_per_step)."""
+    o = vne_options()
+    ms = ctypes.c_double()
+    _check(load().vne_autotune(mat, int(k), int(steps), ctypes.byref(o), ctypes.byref(ms)), ctx)
+    return o, ms.value
 
 
 def vne_ctx_profile(ctx, enable=True):
