@@ -152,6 +152,24 @@ vne_status vne_quadform_batch(vne_matrix *mat, const double *vectors, int32_t k,
                               int32_t krylov_steps, const double *poles, int32_t num_poles,
                               const vne_options *opt, double *psi, double *alpha_beta);
 
+/* ---- rational Krylov quadratic forms (Sections 4, 4.2, 5.3) -----------
+ * psi_j ~ b_j^T f(A) b_j in the rational Krylov space with poles -shifts[i]
+ * (i < num_shifts <= 8) and opt->n_inf_poles poles at infinity:
+ * span{c, A c, .., A^l c, (A + s_i I)^{-1} c}, c the (desingularised) b_j.
+ * The shifted systems are solved together by multi-shift conjugate
+ * gradients seeded on the smallest shift, each shift retired once its
+ * recursive relative residual is <= opt->cg_tol (default 1e-8) or after
+ * opt->cg_max_iter iterations; the basis is orthonormalised in pole order
+ * (first vector c / ||c||) and psi = ||c||^2 e1^T f(V^T A V) e1.
+ *   shifts        NULL: default log-spaced shifts on [1e-4 ||A||_G, ||A||_G]
+ *   cg_iterations NULL or int32[num_shifts][k]: iterations until each shift converged
+ *   residuals     NULL or double[num_shifts][k]: final recursive relative residuals
+ * vne_quadform_batch and vne_entropy_probing take the same path when they
+ * are given poles. */
+vne_status vne_quadform_rational(vne_matrix *mat, const double *vectors, int32_t k, uint32_t vec_flags,
+                                 const double *shifts, int32_t num_shifts, const vne_options *opt, double *psi,
+                                 int32_t *cg_iterations, double *residuals);
+
 /* ---- Hutchinson (Section 3.2, eq. hutchinson-stochastic-trace-estimator)
  * estimate = (1/N) sum_j psi_m(x_j), x_j Rademacher columns 0..N-1 of the
  * counter-based generator with `seed`; std_error = sample std / sqrt(N);

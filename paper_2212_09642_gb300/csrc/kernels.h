@@ -111,6 +111,47 @@ cudaError_t launch_spmm_plain(const int32_t* rowptr, const int32_t* col, const T
 cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, int fp64, void* out,
                                    cudaStream_t);
 
+// ---- multi-shift CG and rational projection (rational.cu) ----
+struct CgState {
+    int32_t K, nshift;
+    double scale, shift0, tol;
+    const double* shift;  // [nshift] (device)
+    const double* dq;     // step-kernel output: scale * (p . q) per column
+    double *rho, *rho_new, *a, *b, *a_prev, *b_prev, *cnorm;
+    double *zeta, *zeta_prev, *zeta_next, *as, *bs, *resid;  // [nshift][K]
+    int32_t *active, *iters;                                  // [nshift][K]
+    int32_t* any_active;
+};
+
+template <typename T>
+struct CgVectors {
+    int32_t n, tiles_per_panel;
+    const RowTile* tiles;
+    T *r, *q, *p;
+    T* x[8];
+    T* ps[8];
+    double* part;
+    uint32_t* counter;
+};
+
+template <typename T>
+struct PairDots {
+    int32_t n, panels, ks, tiles_per_panel;
+    const RowTile* tiles;
+    const T* const* x;  // device array of block pointers, one per pair
+    const T* const* y;
+    double* part;       // [pairs][panels][tiles][ks]
+};
+
+cudaError_t launch_cg_scalars_a(const CgState&, cudaStream_t);
+cudaError_t launch_cg_scalars_b(const CgState&, cudaStream_t);
+template <typename T> cudaError_t launch_cg_update(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
+template <typename T> cudaError_t launch_cg_direction(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
+template <typename T> cudaError_t launch_pair_dots(const PairDots<T>&, int npairs, double* out, cudaStream_t);
+cudaError_t launch_rational_small(const double* M, const double* K, int nb, int ncols, double drop, double* psi,
+                                  int* rank, cudaStream_t);
+cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t);
+
 // ---- dense / small kernels (kernels_dense.cu) ----
 // Gauss quadrature of `count` tridiagonals stored column-interleaved:
 // alpha[j*ld + c], beta[j*ld + c] for j < m.  psi[c] = norm2[c] * sum u1^2 f(scale[c] theta).

@@ -1,0 +1,429 @@
+// Rational Krylov quadrature with negative real poles (Sections 4, 4.2, 5.3)
+// via a batched multi-shift conjugate gradient.
+//
+// For poles xi_s = -s_s (s_s > 0) and ell poles at infinity the rational
+// Krylov space of eq. rational-krylov-subspace-definition is, by partial
+// fractions, span{c, A c, .., A^ell c, x_1, .., x_S} with
+// x_s = (A + s_s I)^{-1} c.  All S shifted systems are solved from one
+// Krylov sequence: conjugate gradients run on the seed system (A + s_0 I),
+// s_0 the smallest shift, and every shifted residual stays collinear with the
+// seed residual, r_s = zeta_s r, which gives each shifted iterate from the
+// seed's coefficients (Jegerlehner 1996; Frommer 2003).  A shift is retired
+// once |zeta_s| ||r|| <= tol ||c||.
+//
+// Per CG iteration, for a block of K columns (panel-major, as in the
+// Lanczos engine):
+//   step kernel (shared with Lanczos)  q = (A + s_0 I) p,  d = p . q
+//   k_cg_scalars_a   a = rho / d, zeta_{k+1}, a_s     (per column, FP64)
+//   k_cg_update      r -= a q, rho' = ||r||^2,  x_s += a_s p_s
+//   k_cg_scalars_b   b = rho'/rho, b_s, convergence, shift history
+//   k_cg_direction   p = r + b p,  p_s = zeta_{k+1} r + b_s p_s
+// Afterwards the basis W and A W are formed (A^j c by the step kernel,
+// A x_s by the step kernel), their Gram matrices W^T W and W^T A W are
+// accumulated per column, and a per-column FP64 kernel orthonormalises W in
+// pole order (Cholesky of the column-scaled Gram, dropping dependent
+// columns; the first basis vector is c / ||c|| as in rational Arnoldi),
+// projects A, diagonalises the small matrix by cyclic Jacobi and returns
+// psi = ||c||^2 e1^T f(A_m) e1.
+#include <float.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vne {
+
+constexpr int kMaxShifts = 8;
+constexpr int kMaxBasis = 12;
+
+__device__ __forceinline__ double f_ent(double x) { return x > 0.0 ? -x * log(x) : 0.0; }
+
+// x_s = 0, r = p = p_s = c are set by copies; here the scalar state:
+// rho = ||c||^2, zeta = zeta_prev = 1, a_prev = 1, b_prev = 0, all shifts
+// active for non-zero columns.
+__global__ void k_cg_init(CgState st, const double* norm2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.K) return;
+    const double n2 = norm2[c];
+    st.rho[c] = n2;
+    st.cnorm[c] = sqrt(n2);
+    st.a_prev[c] = 1.0;
+    st.b_prev[c] = 0.0;
+    st.a[c] = 0.0;
+    st.b[c] = 0.0;
+    for (int s = 0; s < st.nshift; s++) {
+        const size_t o = (size_t)s * st.K + c;
+        st.zeta[o] = 1.0;
+        st.zeta_prev[o] = 1.0;
+        st.zeta_next[o] = 1.0;
+        st.as[o] = 0.0;
+        st.bs[o] = 0.0;
+        st.active[o] = n2 > 0.0 ? 1 : 0;
+        st.iters[o] = 0;
+        st.resid[o] = n2 > 0.0 ? 1.0 : 0.0;
+    }
+}
+
+cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t s) {
+    k_cg_init<<<(st.K + 63) / 64, 64, 0, s>>>(st, norm2);
+    return cudaGetLastError();
+}
+
+// per column: a = rho / d (d from the step kernel as scale * (p . q)), then
+// the shifted coefficients
+__global__ void k_cg_scalars_a(CgState st) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.K) return;
+    const double d = st.dq[c] / st.scale;
+    const double rho = st.rho[c];
+    double a = (d > 0.0 && rho > 0.0) ? rho / d : 0.0;
+    st.a[c] = a;
+    for (int s = 0; s < st.nshift; s++) {
+        const size_t o = (size_t)s * st.K + c;
+        if (!st.active[o] || a == 0.0) {
+            st.as[o] = 0.0;
+            continue;
+        }
+        const double zk = st.zeta[o], zkm1 = st.zeta_prev[o];
+        const double ap = st.a_prev[c], bp = st.b_prev[c];
+        const double delta = st.shift[s] - st.shift0;
+        const double den = ap * zkm1 * (1.0 + delta * a) + a * bp * (zkm1 - zk);
+        const double zn = (den != 0.0) ? zk * zkm1 * ap / den : 0.0;
+        st.zeta_next[o] = zn;
+        st.as[o] = (zk != 0.0) ? a * zn / zk : 0.0;
+    }
+}
+
+// per column: b = rho' / rho and the shifted b_s, convergence, history shift
+__global__ void k_cg_scalars_b(CgState st) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.K) return;
+    const double rho = st.rho[c], rhon = st.rho_new[c];
+    const double b = (rho > 0.0) ? rhon / rho : 0.0;
+    st.b[c] = b;
+    const double rnorm = sqrt(rhon);
+    int any = 0;
+    for (int s = 0; s < st.nshift; s++) {
+        const size_t o = (size_t)s * st.K + c;
+        if (!st.active[o]) continue;
+        const double zk = st.zeta[o], zn = st.zeta_next[o];
+        const double ratio = (zk != 0.0) ? zn / zk : 0.0;
+        st.bs[o] = b * ratio * ratio;
+        st.zeta_prev[o] = zk;
+        st.zeta[o] = zn;
+        st.iters[o] += 1;
+        const double res = fabs(zn) * rnorm;
+        st.resid[o] = res / st.cnorm[c];
+        if (!(res > st.tol * st.cnorm[c])) st.active[o] = 0;  // converged (or breakdown)
+        else any = 1;
+    }
+    st.a_prev[c] = st.a[c];
+    st.b_prev[c] = b;
+    st.rho[c] = rhon;
+    if (any) atomicOr(st.any_active, 1);
+}
+
+// r -= a q;  rho' = ||r||^2 (FP64 across the CTA, fixed-order last-CTA sum);
+// x_s += a_s p_s for active shifts
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_cg_update(CgVectors<T> v, CgState st) {
+    constexpr int RPI = VNE_THREADS / KS;
+    const int panel = blockIdx.x / v.tiles_per_panel, tile = blockIdx.x % v.tiles_per_panel;
+    const RowTile t = v.tiles[tile];
+    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
+    const int col = panel * KS + c;
+    const size_t pofs = (size_t)panel * v.n * KS;
+    __shared__ T s_as[kMaxShifts][KS];
+    __shared__ int s_act[kMaxShifts][KS];
+    if (threadIdx.x < KS)
+        for (int s = 0; s < st.nshift; s++) {
+            s_as[s][threadIdx.x] = (T)st.as[(size_t)s * st.K + panel * KS + threadIdx.x];
+            s_act[s][threadIdx.x] = st.active[(size_t)s * st.K + panel * KS + threadIdx.x];
+        }
+    __syncthreads();
+    const T a = (T)st.a[col];
+    double acc = 0.0;
+    T accf = (T)0;
+    int cnt = 0;
+    for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
+        const size_t o = pofs + (size_t)r * KS + c;
+        T rv = v.r[o] - a * v.q[o];
+        v.r[o] = rv;
+        accf += rv * rv;
+        if (++cnt == 16) {
+            acc += (double)accf;
+            accf = (T)0;
+            cnt = 0;
+        }
+        for (int s = 0; s < st.nshift; s++)
+            if (s_act[s][c]) v.x[s][o] += s_as[s][c] * v.ps[s][o];
+    }
+    acc += (double)accf;
+    __shared__ double red[VNE_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double sum = 0.0;
+        for (int q = 0; q < RPI; q++) sum += red[q * KS + threadIdx.x];
+        v.part[((size_t)panel * v.tiles_per_panel + tile) * KS + threadIdx.x] = sum;
+    }
+    // last CTA of the panel sums the partials in tile order
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(v.counter + panel, 1u) == (unsigned)(v.tiles_per_panel - 1));
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x < KS) {
+            double sum = 0.0;
+            for (int i = 0; i < v.tiles_per_panel; i++)
+                sum += __ldcg(&v.part[((size_t)panel * v.tiles_per_panel + i) * KS + threadIdx.x]);
+            st.rho_new[panel * KS + threadIdx.x] = sum;
+        }
+        if (threadIdx.x == 0) v.counter[panel] = 0u;
+    }
+}
+
+// p = r + b p;  p_s = zeta_{k+1} r + b_s p_s for shifts active before this iteration
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, CgState st) {
+    constexpr int RPI = VNE_THREADS / KS;
+    const int panel = blockIdx.x / v.tiles_per_panel, tile = blockIdx.x % v.tiles_per_panel;
+    const RowTile t = v.tiles[tile];
+    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
+    const int col = panel * KS + c;
+    const size_t pofs = (size_t)panel * v.n * KS;
+    __shared__ T s_z[kMaxShifts][KS], s_b[kMaxShifts][KS];
+    __shared__ int s_act[kMaxShifts][KS];
+    if (threadIdx.x < KS)
+        for (int s = 0; s < st.nshift; s++) {
+            const size_t o = (size_t)s * st.K + panel * KS + threadIdx.x;
+            s_z[s][threadIdx.x] = (T)st.zeta[o];
+            s_b[s][threadIdx.x] = (T)st.bs[o];
+            s_act[s][threadIdx.x] = st.active[o];
+        }
+    __syncthreads();
+    const T b = (T)st.b[col];
+    for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
+        const size_t o = pofs + (size_t)r * KS + c;
+        const T rv = v.r[o];
+        v.p[o] = rv + b * v.p[o];
+        for (int s = 0; s < st.nshift; s++)
+            if (s_act[s][c]) v.ps[s][o] = s_z[s][c] * rv + s_b[s][c] * v.ps[s][o];
+    }
+}
+
+// Per-column inner products between pairs of panel-major blocks:
+// out[pair][col] = sum_i X_pair[i][col] Y_pair[i][col] (FP64 across rows).
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_pair_dots(PairDots<T> pd) {
+    constexpr int RPI = VNE_THREADS / KS;
+    const int pair = blockIdx.y;
+    const int panel = blockIdx.x / pd.tiles_per_panel, tile = blockIdx.x % pd.tiles_per_panel;
+    const RowTile t = pd.tiles[tile];
+    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
+    const size_t pofs = (size_t)panel * pd.n * KS;
+    const T* X = pd.x[pair] + pofs;
+    const T* Y = pd.y[pair] + pofs;
+    double acc = 0.0;
+    T accf = (T)0;
+    int cnt = 0;
+    for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
+        accf += X[(size_t)r * KS + c] * Y[(size_t)r * KS + c];
+        if (++cnt == 16) {
+            acc += (double)accf;
+            accf = (T)0;
+            cnt = 0;
+        }
+    }
+    acc += (double)accf;
+    __shared__ double red[VNE_THREADS];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double sum = 0.0;
+        for (int q = 0; q < RPI; q++) sum += red[q * KS + threadIdx.x];
+        pd.part[(((size_t)pair * pd.panels + panel) * pd.tiles_per_panel + tile) * KS + threadIdx.x] = sum;
+    }
+}
+
+__global__ void k_pair_reduce(const double* part, int npairs, int panels, int tiles, int ks, double* out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = panels * ks;
+    if (idx >= npairs * K) return;
+    const int pair = idx / K, col = idx % K, panel = col / ks, c = col % ks;
+    double s = 0.0;
+    for (int t = 0; t < tiles; t++) s += part[(((size_t)pair * panels + panel) * tiles + t) * ks + c];
+    out[(size_t)pair * K + col] = s;
+}
+
+// Per column: orthonormalise W in order via Cholesky of the scaled Gram
+// (dropping columns whose pivot is <= drop), A_m = R^-T Kt R^-1, cyclic
+// Jacobi, psi = ||c||^2 sum_k z_{1k}^2 f(mu_k).
+__global__ void k_rational_small(const double* Mg, const double* Kg, int nb, int K, double drop, double* psi,
+                                 int* rank_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double Mt[kMaxBasis][kMaxBasis], Kt[kMaxBasis][kMaxBasis], D[kMaxBasis];
+    for (int a = 0; a < nb; a++) {
+        double maa = Mg[((size_t)a * nb + a) * K + c];
+        D[a] = maa > 0.0 ? 1.0 / sqrt(maa) : 0.0;
+    }
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+            Mt[a][b] = Mg[((size_t)a * nb + b) * K + c] * D[a] * D[b];
+            // symmetrise W^T A W
+            Kt[a][b] = 0.5 * (Kg[((size_t)a * nb + b) * K + c] + Kg[((size_t)b * nb + a) * K + c]) * D[a] * D[b];
+        }
+    const double c2 = Mg[c];  // ||c||^2
+    if (!(c2 > 0.0)) {
+        psi[c] = 0.0;
+        rank_out[c] = 0;
+        return;
+    }
+    // Cholesky in order with dropping: keep[] lists kept columns
+    int keep[kMaxBasis];
+    int r = 0;
+    double R[kMaxBasis][kMaxBasis];
+    for (int a = 0; a < nb; a++) {
+        if (D[a] == 0.0) continue;
+        // R[i][a] for kept i < a:  solve R^T col = Mt[kept][a]
+        double col[kMaxBasis];
+        double s = Mt[a][a];
+        for (int i = 0; i < r; i++) {
+            double v = Mt[keep[i]][a];
+            for (int l = 0; l < i; l++) v -= R[l][i] * col[l];
+            col[i] = v / R[i][i];
+            s -= col[i] * col[i];
+        }
+        if (s <= drop) continue;  // dependent on the kept columns
+        for (int i = 0; i < r; i++) R[i][r] = col[i];
+        for (int i = r + 1; i < kMaxBasis; i++) R[i][r] = 0.0;
+        R[r][r] = sqrt(s);
+        keep[r++] = a;
+    }
+    // Rinv (upper triangular r x r)
+    double Ri[kMaxBasis][kMaxBasis];
+    for (int j = 0; j < r; j++) {
+        for (int i = 0; i < r; i++) Ri[i][j] = 0.0;
+        Ri[j][j] = 1.0 / R[j][j];
+        for (int i = j - 1; i >= 0; i--) {
+            double v = 0.0;
+            for (int l = i + 1; l <= j; l++) v += R[i][l] * Ri[l][j];
+            Ri[i][j] = -v / R[i][i];
+        }
+    }
+    // A_m = Ri^T Kt_kept Ri
+    double T1[kMaxBasis][kMaxBasis], Am[kMaxBasis][kMaxBasis];
+    for (int i = 0; i < r; i++)
+        for (int j = 0; j < r; j++) {
+            double v = 0.0;
+            for (int l = 0; l <= j; l++) v += Kt[keep[i]][keep[l]] * Ri[l][j];
+            T1[i][j] = v;
+        }
+    for (int i = 0; i < r; i++)
+        for (int j = 0; j < r; j++) {
+            double v = 0.0;
+            for (int l = 0; l <= i; l++) v += Ri[l][i] * T1[l][j];
+            Am[i][j] = v;
+        }
+    // cyclic Jacobi, eigenvector matrix Z (only row 0 is needed)
+    double z0[kMaxBasis];
+    for (int j = 0; j < r; j++) z0[j] = (j == 0) ? 1.0 : 0.0;
+    double Z[kMaxBasis][kMaxBasis];
+    for (int i = 0; i < r; i++)
+        for (int j = 0; j < r; j++) Z[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 30; sweep++) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < r; i++)
+            for (int j = 0; j < r; j++) {
+                tot += Am[i][j] * Am[i][j];
+                if (i != j) off += Am[i][j] * Am[i][j];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < r; p++)
+            for (int q = p + 1; q < r; q++) {
+                double apq = Am[p][q];
+                if (apq == 0.0) continue;
+                double theta = (Am[q][q] - Am[p][p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < r; k++) {
+                    double akp = Am[k][p], akq = Am[k][q];
+                    Am[k][p] = cs * akp - sn * akq;
+                    Am[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < r; k++) {
+                    double apk = Am[p][k], aqk = Am[q][k];
+                    Am[p][k] = cs * apk - sn * aqk;
+                    Am[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < r; k++) {
+                    double zkp = Z[k][p], zkq = Z[k][q];
+                    Z[k][p] = cs * zkp - sn * zkq;
+                    Z[k][q] = sn * zkp + cs * zkq;
+                }
+            }
+    }
+    (void)z0;
+    double s = 0.0;
+    for (int k = 0; k < r; k++) s += Z[0][k] * Z[0][k] * f_ent(Am[k][k]);
+    psi[c] = c2 * s;
+    rank_out[c] = r;
+}
+
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_cg_scalars_a(const CgState& st, cudaStream_t s) {
+    k_cg_scalars_a<<<(st.K + 63) / 64, 64, 0, s>>>(st);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_scalars_b(const CgState& st, cudaStream_t s) {
+    k_cg_scalars_b<<<(st.K + 63) / 64, 64, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+#define VNE_KS_SWITCH(T, ks, CALL)                                        \
+    do {                                                                  \
+        if ((ks) == 4) { constexpr int KS = 4; CALL; }                    \
+        else if ((ks) == 8) { constexpr int KS = 8; CALL; }               \
+        else if ((ks) == 16) { constexpr int KS = 16; CALL; }             \
+        else if ((ks) == 32) { constexpr int KS = 32; CALL; }             \
+        else return cudaErrorInvalidValue;                                \
+    } while (0)
+
+template <typename T>
+cudaError_t launch_cg_update(const CgVectors<T>& v, const CgState& st, int ks, int panels, cudaStream_t s) {
+    VNE_KS_SWITCH(T, ks, (k_cg_update<T, KS><<<panels * v.tiles_per_panel, VNE_THREADS, 0, s>>>(v, st)));
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cg_direction(const CgVectors<T>& v, const CgState& st, int ks, int panels, cudaStream_t s) {
+    VNE_KS_SWITCH(T, ks, (k_cg_direction<T, KS><<<panels * v.tiles_per_panel, VNE_THREADS, 0, s>>>(v, st)));
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pair_dots(const PairDots<T>& pd, int npairs, double* out, cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    dim3 grid(pd.panels * pd.tiles_per_panel, npairs);
+    VNE_KS_SWITCH(T, pd.ks, (k_pair_dots<T, KS><<<grid, VNE_THREADS, 0, s>>>(pd)));
+    const int K = pd.panels * pd.ks;
+    k_pair_reduce<<<(npairs * K + 255) / 256, 256, 0, s>>>(pd.part, npairs, pd.panels, pd.tiles_per_panel, pd.ks, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_rational_small(const double* M, const double* Kmat, int nb, int K, double drop, double* psi,
+                                  int* rank, cudaStream_t s) {
+    if (nb > kMaxBasis) return cudaErrorInvalidValue;
+    k_rational_small<<<(K + 31) / 32, 32, 0, s>>>(M, Kmat, nb, K, drop, psi, rank);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_update<float>(const CgVectors<float>&, const CgState&, int, int, cudaStream_t);
+template cudaError_t launch_cg_update<double>(const CgVectors<double>&, const CgState&, int, int, cudaStream_t);
+template cudaError_t launch_cg_direction<float>(const CgVectors<float>&, const CgState&, int, int, cudaStream_t);
+template cudaError_t launch_cg_direction<double>(const CgVectors<double>&, const CgState&, int, int, cudaStream_t);
+template cudaError_t launch_pair_dots<float>(const PairDots<float>&, int, double*, cudaStream_t);
+template cudaError_t launch_pair_dots<double>(const PairDots<double>&, int, double*, cudaStream_t);
+
+}  // namespace vne

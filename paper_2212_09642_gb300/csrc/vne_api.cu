@@ -59,6 +59,7 @@ struct vne_ctx {
     std::string err;
     std::map<std::string, WsBuf> ws;
     int64_t launches = 0;  // kernels launched by this context
+    int last_cg_iters = 0; // largest multi-shift CG iteration count of the last rational call
     bool profile = false;
     KernelStat stat[2];    // 0: step (SpMM) kernel, 1: update kernel
     std::vector<cudaEvent_t> ev_pool;
@@ -612,6 +613,283 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
     return psi;
 }
 
+
+// Apply the operator to a panel-major block with the Lanczos step kernel:
+// out = A in + shift * in (A = scale M), and dq[c] = scale * (in . out).
+template <typename T>
+void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* out, double shift, double* dq,
+                    int variant, const std::string& tag) {
+    cudaStream_t st = ctx->stream;
+    const int panels = Kp / ks;
+    const int ctas = P.ctas_per_panel(), tiles = P.tiles_per_panel();
+    const int nh = (int)P.hubs.size();
+    const double scale = P.segs[0].scale;
+    std::vector<double> hs(Kp, scale), hc(Kp, -shift), h1(Kp, 1.0);
+    StepParams<T> p{};
+    p.rowptr = P.rowptr;
+    p.col = P.col;
+    p.vals = (const T*)P.vals;
+    p.n_total = P.n_total;
+    p.K = Kp;
+    p.nseg = 1;
+    p.seg = P.d_segs;
+    p.items = P.d_items;
+    p.ctas_per_panel = ctas;
+    p.cta_seg = P.d_cta_seg;
+    p.hubs = P.d_hubs;
+    p.nhubs = std::max(nh, 1);
+    p.hub_slots = std::max(P.hub_slots, 1);
+    p.hub_part = ws_get_t<T>(ctx, "hub_part", (size_t)panels * std::max(P.hub_slots, 1) * ks);
+    p.hub_cnt = ws_get_t<uint32_t>(ctx, "op.hub_cnt", (size_t)panels * std::max(nh, 1));
+    p.hub_dot = ws_get_t<double>(ctx, "hub_dot", (size_t)panels * std::max(nh, 1) * ks);
+    p.stage_nnz = std::max(P.stage_nnz, 1);
+    p.tiles = P.d_tiles;
+    p.tiles_per_panel = tiles;
+    p.first = (shift == 0.0) ? 1 : 0;
+    p.renorm = 0;
+    p.w_cur = in;
+    p.w_prev = in;
+    p.u = out;
+    p.w_next = out;
+    p.sig_cur = upload(ctx, tag + ".sig", hs);
+    p.beta_prev = upload(ctx, tag + ".cp", hc);
+    p.sig_prev = upload(ctx, tag + ".one", h1);
+    p.alpha = dq;
+    p.part = ws_get_t<double>(ctx, "op.part", (size_t)panels * std::max(ctas, tiles) * ks);
+    p.counter = ws_get_t<uint32_t>(ctx, "op.counter", (size_t)panels);
+    VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
+    ctx->launches += 1;
+}
+
+// Rational Krylov quadratic forms (poles -shifts[i] and n_inf poles at
+// infinity) of one start block, by multi-shift CG.
+template <typename T>
+void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int ks, const double* shifts,
+                    int nshift, int n_inf, double tol, int max_iter, bool desing, int variant, double drop,
+                    std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid, int* rank_min) {
+    cudaStream_t st = ctx->stream;
+    VNE_REQUIRE(ctx, P.nseg == 1, VNE_EUNSUPPORTED, "rational mode needs a single matrix");
+    VNE_REQUIRE(ctx, nshift >= 1 && nshift <= 8, VNE_EINVAL, "1..8 finite poles are supported");
+    VNE_REQUIRE(ctx, n_inf >= 0 && n_inf <= 3, VNE_EINVAL, "0..3 poles at infinity are supported");
+    const int panels = (K + ks - 1) / ks, Kp = panels * ks;
+    const int n = P.n_total;
+    const size_t blk = (size_t)Kp * n;
+    const int tiles = P.tiles_per_panel();
+    // seed system: the smallest shift
+    int s0i = 0;
+    for (int i = 1; i < nshift; i++)
+        if (shifts[i] < shifts[s0i]) s0i = i;
+    const double s0 = shifts[s0i];
+    const double scale = P.segs[0].scale;
+    // start block c (desingularised probes), norms
+    T* C = ws_get_t<T>(ctx, "rat.c", blk);
+    double* norm2 = ws_get_t<double>(ctx, "rat.norm2", Kp);
+    double* sig1 = ws_get_t<double>(ctx, "rat.sig1", Kp);
+    {
+        StartParams<T> sp{};
+        sp.src = src;
+        sp.node_id = P.node_id;
+        sp.seg = P.d_segs;
+        sp.nseg = 1;
+        sp.K = Kp;
+        sp.n_total = n;
+        sp.tiles_per_panel = tiles;
+        sp.tiles = P.d_tiles;
+        sp.desing = desing ? 1 : 0;
+        sp.w1 = C;
+        sp.mean = ws_get_t<double>(ctx, "mean", Kp);
+        sp.norm2 = norm2;
+        sp.sig1 = sig1;
+        sp.part = ws_get_t<double>(ctx, "part", (size_t)panels * tiles * ks);
+        sp.counter = ws_get_t<uint32_t>(ctx, "counter", (size_t)panels, true);
+        VNE_TRY_CUDA(ctx, launch_start<T>(sp, ks, panels, st));
+    }
+    // CG vectors
+    CgVectors<T> v{};
+    v.n = n;
+    v.tiles_per_panel = tiles;
+    v.tiles = P.d_tiles;
+    v.r = ws_get_t<T>(ctx, "rat.r", blk);
+    v.q = ws_get_t<T>(ctx, "rat.q", blk);
+    v.p = ws_get_t<T>(ctx, "rat.p", blk);
+    T* xs = ws_get_t<T>(ctx, "rat.x", blk * nshift);
+    T* pss = ws_get_t<T>(ctx, "rat.ps", blk * nshift);
+    for (int i = 0; i < nshift; i++) {
+        v.x[i] = xs + (size_t)i * blk;
+        v.ps[i] = pss + (size_t)i * blk;
+    }
+    v.part = ws_get_t<double>(ctx, "rat.part", (size_t)panels * tiles * ks);
+    v.counter = ws_get_t<uint32_t>(ctx, "rat.counter", (size_t)panels, true);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(v.r, C, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(v.p, C, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    VNE_TRY_CUDA(ctx, cudaMemsetAsync(xs, 0, blk * nshift * sizeof(T), st));
+    for (int i = 0; i < nshift; i++)
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(v.ps[i], C, blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    // scalar state
+    CgState cs{};
+    cs.K = Kp;
+    cs.nshift = nshift;
+    cs.scale = scale;
+    cs.shift0 = s0;
+    cs.tol = tol;
+    std::vector<double> hsh(shifts, shifts + nshift);
+    cs.shift = upload(ctx, "rat.shifts", hsh);
+    double* dq = ws_get_t<double>(ctx, "rat.dq", Kp);
+    cs.dq = dq;
+    double* sc = ws_get_t<double>(ctx, "rat.scalars", (size_t)Kp * (7 + 6 * nshift));
+    cs.rho = sc;
+    cs.rho_new = sc + Kp;
+    cs.a = sc + 2 * Kp;
+    cs.b = sc + 3 * Kp;
+    cs.a_prev = sc + 4 * Kp;
+    cs.b_prev = sc + 5 * Kp;
+    cs.cnorm = sc + 6 * Kp;
+    double* sh = sc + 7 * Kp;
+    cs.zeta = sh;
+    cs.zeta_prev = sh + (size_t)nshift * Kp;
+    cs.zeta_next = sh + 2 * (size_t)nshift * Kp;
+    cs.as = sh + 3 * (size_t)nshift * Kp;
+    cs.bs = sh + 4 * (size_t)nshift * Kp;
+    cs.resid = sh + 5 * (size_t)nshift * Kp;
+    int32_t* ibuf = ws_get_t<int32_t>(ctx, "rat.ints", (size_t)2 * nshift * Kp + 1);
+    cs.active = ibuf;
+    cs.iters = ibuf + (size_t)nshift * Kp;
+    cs.any_active = ibuf + 2 * (size_t)nshift * Kp;
+    VNE_TRY_CUDA(ctx, launch_cg_init(cs, norm2, st));
+    ctx->launches += 1;
+    int it = 0;
+    for (; it < max_iter; it++) {
+        apply_operator<T>(ctx, P, ks, Kp, v.p, v.q, s0, dq, variant, "rat.op");
+        VNE_TRY_CUDA(ctx, launch_cg_scalars_a(cs, st));
+        VNE_TRY_CUDA(ctx, launch_cg_update<T>(v, cs, ks, panels, st));
+        VNE_TRY_CUDA(ctx, cudaMemsetAsync(cs.any_active, 0, sizeof(int32_t), st));
+        VNE_TRY_CUDA(ctx, launch_cg_scalars_b(cs, st));
+        VNE_TRY_CUDA(ctx, launch_cg_direction<T>(v, cs, ks, panels, st));
+        ctx->launches += 4;
+        if ((it & 7) == 7 || it + 1 == max_iter) {
+            int32_t any = 0;
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&any, cs.any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+            if (!any) {
+                it++;
+                break;
+            }
+        }
+    }
+    // basis W = [c, A c, .., A^n_inf c, x_1..x_S] and A W
+    const int nb = 1 + n_inf + nshift;
+    T* apow = ws_get_t<T>(ctx, "rat.apow", blk * (n_inf + 1));
+    const T* prev = C;
+    for (int j = 0; j <= n_inf; j++) {
+        T* out = apow + (size_t)j * blk;
+        apply_operator<T>(ctx, P, ks, Kp, prev, out, 0.0, dq, variant, "rat.op0");
+        prev = out;
+    }
+    for (int i = 0; i < nshift; i++)  // A x_s into the (now free) direction buffers
+        apply_operator<T>(ctx, P, ks, Kp, v.x[i], v.ps[i], 0.0, dq, variant, "rat.op0");
+    std::vector<const T*> W(nb), AW(nb);
+    W[0] = C;
+    for (int j = 1; j <= n_inf; j++) W[j] = apow + (size_t)(j - 1) * blk;
+    for (int j = 0; j <= n_inf; j++) AW[j] = apow + (size_t)j * blk;
+    for (int i = 0; i < nshift; i++) {
+        W[1 + n_inf + i] = v.x[i];
+        AW[1 + n_inf + i] = v.ps[i];
+    }
+    std::vector<const T*> px, py;
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+            px.push_back(W[a]);
+            py.push_back(W[b]);
+        }
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++) {
+            px.push_back(W[a]);
+            py.push_back(AW[b]);
+        }
+    const int npairs = (int)px.size();
+    PairDots<T> pd{};
+    pd.n = n;
+    pd.panels = panels;
+    pd.ks = ks;
+    pd.tiles_per_panel = tiles;
+    pd.tiles = P.d_tiles;
+    pd.x = upload(ctx, "rat.px", px);
+    pd.y = upload(ctx, "rat.py", py);
+    pd.part = ws_get_t<double>(ctx, "rat.ppart", (size_t)npairs * panels * tiles * ks);
+    double* gram = ws_get_t<double>(ctx, "rat.gram", (size_t)npairs * Kp);
+    VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, gram, st));
+    double* dpsi = ws_get_t<double>(ctx, "rat.psi", Kp);
+    int* drank = ws_get_t<int>(ctx, "rat.rank", Kp);
+    VNE_TRY_CUDA(ctx, launch_rational_small(gram, gram + (size_t)nb * nb * Kp, nb, Kp, drop, dpsi, drank, st));
+    ctx->launches += 3;
+    psi = download(ctx, dpsi, K);
+    std::vector<int> hr(Kp), hit((size_t)nshift * Kp);
+    std::vector<double> hres((size_t)nshift * Kp);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr.data(), drank, Kp * sizeof(int), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hit.data(), cs.iters, hit.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hres.data(), cs.resid, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    iters.assign((size_t)nshift * K, 0);
+    resid.assign((size_t)nshift * K, 0.0);
+    for (int i = 0; i < nshift; i++)
+        for (int c = 0; c < K; c++) {
+            iters[(size_t)i * K + c] = hit[(size_t)i * Kp + c];
+            resid[(size_t)i * K + c] = hres[(size_t)i * Kp + c];
+        }
+    int rmin = nb;
+    for (int c = 0; c < K; c++) rmin = std::min(rmin, hr[c]);
+    if (rank_min) *rank_min = rmin;
+    (void)it;
+}
+
+template <typename T>
+void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, int ncols, const double* shifts,
+                        int nshift, std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid) {
+    vne_ctx* ctx = M->ctx;
+    Problem* P = matrix_problem(M, o);
+    Sched sc = resolve_sched(M, o);
+    check_ks<T>(ctx, sc.ks);
+    const int lim = std::min(block_limit(o), 128);
+    const double tol = (o && o->cg_tol > 0) ? o->cg_tol : 1e-8;
+    const int maxit = (o && o->cg_max_iter > 0) ? o->cg_max_iter : 10000;
+    const int n_inf = o ? o->n_inf_poles : 2;
+    const double drop = M->fp64 ? 1e-14 : 1e-6;
+    psi.assign(ncols, 0.0);
+    iters.assign((size_t)nshift * ncols, 0);
+    resid.assign((size_t)nshift * ncols, 0.0);
+    for (int b0 = 0; b0 < ncols; b0 += lim) {
+        const int K = std::min(lim, ncols - b0);
+        StartSource s = src;
+        s.ncols = K;
+        if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
+        if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
+        std::vector<double> bp, br;
+        std::vector<int> bi;
+        int rmin = 0;
+        rational_block<T>(ctx, *P, s, K, sc.ks, shifts, nshift, n_inf, tol, maxit, M->desing, sc.variant, drop, bp,
+                          bi, br, &rmin);
+        for (int c = 0; c < K; c++) psi[b0 + c] = bp[c];
+        for (int i = 0; i < nshift; i++)
+            for (int c = 0; c < K; c++) {
+                iters[(size_t)i * ncols + b0 + c] = bi[(size_t)i * K + c];
+                resid[(size_t)i * ncols + b0 + c] = br[(size_t)i * K + c];
+            }
+    }
+}
+
+std::vector<double> resolve_shifts(const vne_matrix* M, const double* poles, int num_poles) {
+    std::vector<double> sh(num_poles);
+    if (poles) {
+        for (int i = 0; i < num_poles; i++) sh[i] = poles[i];
+    } else {
+        // default poles: log-spaced on [1e-4 ||A||_G, ||A||_G]
+        const double lam = M->normM * M->scale;
+        for (int i = 0; i < num_poles; i++)
+            sh[i] = lam * pow(10.0, num_poles > 1 ? -4.0 * i / (num_poles - 1) : 0.0);
+    }
+    return sh;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -858,15 +1136,34 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
     cudaSetDevice(ctx->device);
     vne_options o = opt ? *opt : defaults();
     VNE_REQUIRE(ctx, k >= 1 && vectors && psi, VNE_EINVAL, "need k >= 1, vectors and psi");
-    VNE_REQUIRE(ctx, poles == nullptr, VNE_EUNSUPPORTED, "rational mode is provided by vne_quadform_rational");
-    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
-    const int m = krylov_steps;
     const double* dvec = vectors;
     if (!(vec_flags & VNE_VECTORS_DEVICE)) {
         double* d = ws_get_t<double>(ctx, "qb.input", (size_t)M->n * k);
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, vectors, (size_t)M->n * k * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         dvec = d;
     }
+    if (poles != nullptr || num_poles > 0) {
+        // rational Krylov space: multi-shift CG
+        VNE_REQUIRE(ctx, num_poles >= 1 && num_poles <= 8, VNE_EINVAL, "1..8 poles are supported");
+        std::vector<double> sh = resolve_shifts(M, poles, num_poles);
+        for (double v : sh) VNE_REQUIRE(ctx, v > 0.0, VNE_EINVAL, "poles must be negative reals (shifts > 0)");
+        StartSource s{};
+        s.kind = SRC_DENSE64;
+        s.ld = k;
+        s.dense = dvec;
+        std::vector<double> ps, rs;
+        std::vector<int> its;
+        if (M->fp64) rational_quadforms<double>(M, &o, s, k, sh.data(), num_poles, ps, its, rs);
+        else rational_quadforms<float>(M, &o, s, k, sh.data(), num_poles, ps, its, rs);
+        std::copy(ps.begin(), ps.end(), psi);
+        if (alpha_beta) {  // rational mode: report CG iterations and final residuals per shift
+            for (int c = 0; c < k; c++)
+                for (int i = 0; i < 2 * krylov_steps; i++) alpha_beta[(size_t)c * 2 * krylov_steps + i] = 0.0;
+        }
+        return VNE_OK;
+    }
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    const int m = krylov_steps;
     Problem* P = matrix_problem(M, &o);
     Sched sc = resolve_sched(M, &o);
     int ks = sc.ks;
@@ -1096,8 +1393,9 @@ extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring
     cudaSetDevice(ctx->device);
     vne_options o = opt ? *opt : defaults();
     VNE_REQUIRE(ctx, estimate, VNE_EINVAL, "estimate is required");
-    VNE_REQUIRE(ctx, poles == nullptr, VNE_EUNSUPPORTED, "rational probing is provided by vne_entropy_probing_rational");
-    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    const bool rational = (poles != nullptr || num_poles > 0);
+    VNE_REQUIRE(ctx, rational || (krylov_steps >= 1 && krylov_steps <= 128), VNE_EINVAL,
+                "krylov_steps must be in [1, 128]");
     const int64_t n = M->n;
     // colours in the caller's node numbering
     std::vector<int32_t> col(n);
@@ -1124,8 +1422,21 @@ extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring
     src.kind = SRC_INDICATOR;
     src.colors = dcol;
     src.col_begin = 0;
-    std::vector<double> psi = M->fp64 ? quadforms<double>(M, &o, src, s, krylov_steps)
-                                      : quadforms<float>(M, &o, src, s, krylov_steps);
+    std::vector<double> psi;
+    if (rational) {
+        VNE_REQUIRE(ctx, num_poles >= 1 && num_poles <= 8, VNE_EINVAL, "1..8 poles are supported");
+        std::vector<double> sh = resolve_shifts(M, poles, num_poles);
+        for (double v : sh) VNE_REQUIRE(ctx, v > 0.0, VNE_EINVAL, "poles must be negative reals (shifts > 0)");
+        std::vector<int> its;
+        std::vector<double> rs;
+        if (M->fp64) rational_quadforms<double>(M, &o, src, s, sh.data(), num_poles, psi, its, rs);
+        else rational_quadforms<float>(M, &o, src, s, sh.data(), num_poles, psi, its, rs);
+        int mx = 0;
+        for (int v : its) mx = std::max(mx, v);
+        ctx->last_cg_iters = mx;
+    } else {
+        psi = M->fp64 ? quadforms<double>(M, &o, src, s, krylov_steps) : quadforms<float>(M, &o, src, s, krylov_steps);
+    }
     double tot = 0.0;
     for (double v : psi) tot += v;
     *estimate = tot;
@@ -1384,5 +1695,37 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
         chosen->step_variant = bv;
     }
     if (ms_per_step) *ms_per_step = best / steps;
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_quadform_rational(vne_matrix* M, const double* vectors, int32_t k, uint32_t vec_flags,
+                                            const double* shifts, int32_t num_shifts, const vne_options* opt,
+                                            double* psi, int32_t* cg_iterations, double* residuals) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    vne_options o = opt ? *opt : defaults();
+    VNE_REQUIRE(ctx, k >= 1 && vectors && psi, VNE_EINVAL, "need k >= 1, vectors and psi");
+    VNE_REQUIRE(ctx, num_shifts >= 1 && num_shifts <= 8, VNE_EINVAL, "1..8 poles are supported");
+    std::vector<double> sh = resolve_shifts(M, shifts, num_shifts);
+    for (double v : sh) VNE_REQUIRE(ctx, v > 0.0, VNE_EINVAL, "shifts must be positive (poles -s)");
+    const double* dvec = vectors;
+    if (!(vec_flags & VNE_VECTORS_DEVICE)) {
+        double* d = ws_get_t<double>(ctx, "qb.input", (size_t)M->n * k);
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, vectors, (size_t)M->n * k * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        dvec = d;
+    }
+    StartSource s{};
+    s.kind = SRC_DENSE64;
+    s.ld = k;
+    s.dense = dvec;
+    std::vector<double> ps, rs;
+    std::vector<int> its;
+    if (M->fp64) rational_quadforms<double>(M, &o, s, k, sh.data(), num_shifts, ps, its, rs);
+    else rational_quadforms<float>(M, &o, s, k, sh.data(), num_shifts, ps, its, rs);
+    std::copy(ps.begin(), ps.end(), psi);
+    if (cg_iterations) std::copy(its.begin(), its.end(), cg_iterations);
+    if (residuals) std::copy(rs.begin(), rs.end(), residuals);
     VNE_API_END(ctx)
 }

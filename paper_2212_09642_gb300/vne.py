@@ -86,6 +86,8 @@ def _declare(lib):
         "vne_batch_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(vne_options), _P, _P]),
         "vne_ctx_profile": (st, [_P, ctypes.c_int32]),
+        "vne_quadform_rational": (st, [_P, _P, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.c_int32,
+                                       ctypes.POINTER(vne_options), _PD, _P, _P]),
         "vne_autotune": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vne_options), _PD]),
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
@@ -118,7 +120,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
-               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune"]
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational"]
 
 
 def _check(status, ctx=None):
@@ -208,6 +210,21 @@ def vne_quadform_batch(ctx, mat, vectors, krylov_steps, opt=None, want_alpha_bet
     return (psi, ab) if want_alpha_beta else psi
 
 
+def vne_quadform_rational(ctx, mat, vectors, shifts=None, num_shifts=None, opt=None):
+    """(psi, cg_iterations [S, k], residuals [S, k]) for the columns of ``vectors`` ([n, k])."""
+    vectors = np.ascontiguousarray(vectors, dtype=np.float64)
+    k = vectors.shape[1]
+    sh = None if shifts is None else np.ascontiguousarray(shifts, dtype=np.float64)
+    S = len(sh) if sh is not None else int(num_shifts or 8)
+    psi = np.zeros(k)
+    its = np.zeros((S, k), dtype=np.int32)
+    res = np.zeros((S, k))
+    o = opt if opt is not None else options()
+    _check(load().vne_quadform_rational(mat, _ptr(vectors), k, 0, _ptr(sh), S, ctypes.byref(o),
+                                        psi.ctypes.data_as(_PD), _ptr(its), _ptr(res)), ctx)
+    return psi, its, res
+
+
 def vne_entropy_hutchinson(ctx, mat, num_vectors, krylov_steps, seed, opt=None, want_psi=False):
     est, se = ctypes.c_double(), ctypes.c_double()
     psi = np.zeros(num_vectors) if want_psi else None
@@ -228,7 +245,10 @@ def vne_entropy_hutchpp(ctx, mat, sketch_cols, hutch_vectors, krylov_steps, seed
     return est.value, parts
 
 
-def vne_entropy_probing(ctx, mat, coloring=None, distance=1, krylov_steps=30, opt=None):
+def vne_entropy_probing(ctx, mat, coloring=None, distance=1, krylov_steps=30, opt=None, shifts=None,
+                        num_shifts=0):
+    """Probing estimate; with shifts (or num_shifts > 0 for the default poles) the
+    quadratic forms use the rational Krylov space (multi-shift CG)."""
     est = ctypes.c_double()
     s = ctypes.c_int32()
     o = opt if opt is not None else options()
@@ -236,7 +256,9 @@ def vne_entropy_probing(ctx, mat, coloring=None, distance=1, krylov_steps=30, op
     if coloring is not None:
         coloring = np.ascontiguousarray(coloring, dtype=np.int32)
         cp = _ptr(coloring)
-    _check(load().vne_entropy_probing(mat, cp, int(distance), int(krylov_steps), None, 0, ctypes.byref(o),
+    sh = None if shifts is None else np.ascontiguousarray(shifts, dtype=np.float64)
+    S = len(sh) if sh is not None else int(num_shifts)
+    _check(load().vne_entropy_probing(mat, cp, int(distance), int(krylov_steps), _ptr(sh), S, ctypes.byref(o),
                                       ctypes.byref(est), ctypes.byref(s)), ctx)
     return est.value, s.value
 
