@@ -53,6 +53,10 @@ def parse():
                     help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
     ap.add_argument("--vectors", type=int, default=112)
     ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant (skips the autotuner)")
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                    help="c2 = the headline workload; c1/c3/c4/c5 print measurement lines of the other configs")
+    ap.add_argument("--requests", type=int, default=400, help="c5: number of queries")
+    ap.add_argument("--rate", type=float, default=200.0, help="c5: Poisson arrival rate (queries/s)")
     return ap.parse_args()
 
 
@@ -370,10 +374,197 @@ def run_native(args):
     vne.vne_ctx_destroy(ctx)
 
 
+# ---------------------------------------------------------------------------
+# measurement lines of the other configurations (not the headline)
+
+def _timed(ctx, stream, fn, steps, warmup):
+    import torch
+    from paper_2212_09642_gb300 import vne
+    for w in range(warmup):
+        fn(w)
+    torch.cuda.synchronize()
+    vne.vne_ctx_profile(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.__enter__()
+    e0.record(stream)
+    outs = [fn(100 + k) for k in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.__exit__()
+    ms = e0.elapsed_time(e1)
+    launches, kst = vne.vne_ctx_stats(ctx)
+    vne.vne_ctx_profile(ctx, False)
+    return outs, ms, launches, kst, sampler.summary()
+
+
+def _roof(kst, kind, ms_total, label):
+    peak, kind_p = load_peaks()
+    cnt, ms, byts = kst[kind]
+    if not cnt or ms <= 0:
+        return None
+    ach = byts / (ms / 1e3) / 1e9
+    return {"kernel": label, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": kind_p, "traffic": None, "algorithmic_bytes_per_launch": byts / cnt,
+            "avg_launch_ms": ms / cnt, "launches_timed": int(cnt), "share_of_step_time": ms / ms_total}
+
+
+def run_other(args):
+    import numpy as np
+    import torch
+    from paper_2212_09642_gb300 import _build, graphs, vne
+    _build.build_all()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = vne.vne_ctx_create(0)
+    vne.vne_ctx_set_stream(ctx, stream)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "unit": UNIT}
+    if args.workload == "c1":
+        from oracle import density, entropy
+        g = graphs.erdos_renyi(2000, 0.005, 1)
+        mat = vne.matrix_from_graph(ctx, g, fp64=True)
+        outs, ms, launches, kst, clk = _timed(ctx, stream, lambda s: vne.vne_entropy_hutchinson(
+            ctx, mat, 100, 50, s), args.steps, args.warmup)
+        A, _ = density.density_matrix(g)
+        S = entropy.dense_entropy(A)
+        line.update(metric="entropy estimates/sec (Hutchinson 100 x 50, ER n=2000 p=0.005, FP64)",
+                    value=args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f64",
+                    config={"workload": "C1: ER G(2000,0.005) seed 1, FP64, Hutchinson 100 Rademacher x 50 Lanczos "
+                                        "steps, full reorthogonalisation", "l2": "working set L2-resident (latency-bound)"},
+                    roofline=_roof(kst, "step", ms, "k_step FP64"), gpu_launches=int(launches), clocks=clk,
+                    estimate=outs[0][0], std_error=outs[0][1], dense_entropy=S,
+                    abs_err_vs_dense=abs(outs[0][0] - S))
+        vne.vne_matrix_destroy(mat)
+    elif args.workload == "c3":
+        n = args.n if args.n != N_NODES else 4_000_000
+        g = graphs.random_geometric(n, graphs.rgg_radius_for_degree(n, 6.0), 4)
+        t0 = time.perf_counter()
+        colors, s = vne.vne_greedy_coloring(g.n, g.rowptr, g.col, 2)
+        t_col = time.perf_counter() - t0
+        mat = vne.matrix_from_graph(ctx, g, fp64=False)
+        opt = vne.options(cg_tol=1e-8, n_inf_poles=2)
+        outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
+            ctx, mat, colors, 2, 0, opt=opt, num_shifts=8), args.steps, args.warmup)
+        line.update(metric="entropy estimates/sec (probing d=2, rational Krylov 8 poles + 2 at infinity, RGG n=4e6)",
+                    value=args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
+                    config={"workload": f"C3: RGG n={g.n} avg degree 6 (seed 4), generation order, greedy distance-2 "
+                                        f"colouring ({s} colours, host {t_col:.1f} s, untimed), 8 log-spaced poles on "
+                                        "[1e-4, 1] ||A||_G, multi-shift CG to recursive rel. residual 1e-8",
+                            "nnz": g.nnz, "colors": s, "l2": "inputs larger than L2"},
+                    roofline=_roof(kst, "step", ms, "k_step (SpMM inside CG)"),
+                    cg_update=_roof(kst, "cg_update", ms, "k_cg_update"),
+                    cg_direction=_roof(kst, "cg_direction", ms, "k_cg_direction"),
+                    gpu_launches=int(launches), clocks=clk, estimate=outs[0][0])
+        vne.vne_matrix_destroy(mat)
+    elif args.workload == "c4":
+        gs = graphs.batched_uneven_family(512, 1000, 200000, 1000)
+        mats = [vne.matrix_from_graph(ctx, gg, fp64=False) for gg in gs]
+        outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_batch_hutchinson(
+            ctx, mats, 64, 40, sd, opt=vne.options(reorth=0)), args.steps, args.warmup)
+        line.update(metric="entropy estimates/sec (512 uneven graphs batched, Hutchinson 64 x 40)",
+                    value=512 * args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
+                    config={"workload": "C4: 512 graphs, n log-uniform [1e3, 2e5], ER deg 8 / BA m=3 / WS k=6 b=0.1, "
+                                        "64 Rademacher x 40 Lanczos steps each, one packed launch sequence",
+                            "sum_n": int(sum(gg.n for gg in gs)), "sum_nnz": int(sum(gg.nnz for gg in gs)),
+                            "l2": "inputs larger than L2"},
+                    roofline=_roof(kst, "step", ms, "k_step (packed segments)"),
+                    update_kernel=_roof(kst, "update", ms, "k_update"), gpu_launches=int(launches), clocks=clk)
+        for m in mats:
+            vne.vne_matrix_destroy(m)
+    else:
+        line.update(run_serving(args, ctx, stream))
+    vne.vne_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, ctx, stream):
+    """C5: Poisson arrivals of entropy queries (rel. accuracy 1e-3), continuous batching."""
+    import numpy as np
+    import torch
+    from paper_2212_09642_gb300 import graphs, vne
+    rng = np.random.default_rng(5)
+    pool_n = np.rint(np.exp(rng.uniform(math.log(1e3), math.log(1e6), size=24))).astype(int)
+    pool = []
+    for i, nn in enumerate(pool_n):
+        kind = i % 3
+        if kind == 0:
+            pool.append(graphs.erdos_renyi(int(nn), 8.0 / (nn - 1), 500 + i))
+        elif kind == 1:
+            pool.append(graphs.barabasi_albert(int(nn), 3, 500 + i))
+        else:
+            pool.append(graphs.watts_strogatz(int(nn), 6, 0.1, 500 + i))
+    mats = [vne.matrix_from_graph(ctx, g, fp64=False, reorder=True) for g in pool]
+    R = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=R))
+    which = rng.integers(0, len(pool), size=R)
+    eps, cap = 1e-3, 8192
+    srv = vne.vne_server_create(ctx, 200 << 30, max_active=256, krylov_steps=40, block_vectors=64,
+                                opt=vne.options(reorth=0))
+    sampler = ClockSampler(0)
+    sampler.__enter__()
+    t0 = time.perf_counter()
+    nxt, done_t, tickets = 0, {}, {}
+    vne.vne_ctx_profile(ctx, True)
+    while len(done_t) < R:
+        now = time.perf_counter() - t0
+        while nxt < R and arrivals[nxt] <= now:
+            tickets[nxt] = vne.vne_server_submit(ctx, srv, mats[which[nxt]], eps, 9000 + nxt, cap)
+            nxt += 1
+        q, a, _ = vne.vne_server_info(srv)
+        if q == 0 and a == 0:
+            if nxt < R:
+                time.sleep(max(0.0, arrivals[nxt] - now))
+            continue
+        vne.vne_server_step(ctx, srv)
+        t_now = time.perf_counter() - t0
+        for i, t in tickets.items():
+            if i not in done_t and vne.vne_server_result(srv, t)["state"] == 2:
+                done_t[i] = t_now
+    total = time.perf_counter() - t0
+    sampler.__exit__()
+    launches, kst = vne.vne_ctx_stats(ctx)
+    vne.vne_ctx_profile(ctx, False)
+    lat = np.array([done_t[i] - arrivals[i] for i in range(R)])
+    vecs = np.array([vne.vne_server_result(srv, tickets[i])["vectors"] for i in range(R)])
+    vne.vne_server_destroy(srv)
+    # FP64 one-query-at-a-time on the first 50 queries: same stopping rule, queueing on the same arrivals
+    m64 = {}
+    free_at, lat64 = 0.0, []
+    R64 = min(50, R)
+    for i in range(R64):
+        g = pool[which[i]]
+        if which[i] not in m64:
+            m64[which[i]] = vne.matrix_from_graph(ctx, g, fp64=True, reorder=True)
+        ts = time.perf_counter()
+        vne.vne_entropy_hutchinson(ctx, m64[which[i]], 64, 40, 9000 + i, opt=vne.options(reorth=0, block=64))
+        # one FP64 block of 64 probes, scaled by the blocks the query needed when served
+        service = (time.perf_counter() - ts) * max(1, int(vecs[i]) // 64)
+        start = max(free_at, arrivals[i])
+        free_at = start + service
+        lat64.append(free_at - arrivals[i])
+    for m in list(m64.values()) + mats:
+        vne.vne_matrix_destroy(m)
+    lat64 = np.array(lat64)
+    return {"metric": "served entropy estimates/sec at rel. accuracy 1e-3 (continuous batching), p50/p99 latency",
+            "value": R / total, "ms_per_step": 1e3 * total / R, "dtype": "f32",
+            "config": {"workload": f"C5: {R} queries, Poisson {args.rate}/s (seed 5), graphs from a pool of 24 "
+                                   "(n log-uniform [1e3, 1e6], ER/BA/WS), eps 1e-3, blocks of 64 probes x 40 steps, "
+                                   "cap 8192 probes", "pool_n": [int(x) for x in pool_n]},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean())},
+            "fp64_one_at_a_time_first50": {"p50": float(np.percentile(lat64, 50)),
+                                            "p99": float(np.percentile(lat64, 99))},
+            "mean_vectors_per_query": float(vecs.mean()), "roofline": _roof(kst, "step", 1e3 * total, "k_step"),
+            "gpu_launches": int(launches), "clocks": sampler.summary()}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        run_other(args)
     else:
         run_native(args)
 

@@ -98,8 +98,9 @@ const char *vne_version(void);
  * then on, brackets every launch of the Lanczos step (SpMM) and update
  * kernels with CUDA events on the context stream; vne_ctx_stats returns the
  * number of kernels this context launched since the reset and, per kernel
- * kind (0 = step, 1 = update), {timed launches, total milliseconds, total
- * algorithmic bytes}.  kernel_stats must hold 6 doubles (or be NULL). */
+ * kind (0 = step / SpMM, 1 = Lanczos update, 2 = CG update, 3 = CG
+ * direction), {timed launches, total milliseconds, total algorithmic bytes}.
+ * kernel_stats must hold 12 doubles (or be NULL). */
 vne_status vne_ctx_profile(vne_ctx *ctx, int32_t enable);
 vne_status vne_ctx_stats(const vne_ctx *ctx, int64_t *launches, double *kernel_stats);
 
@@ -243,6 +244,37 @@ vne_status vne_autotune(vne_matrix *mat, int32_t k, int32_t steps, vne_options *
 vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t num_vectors,
                                 int32_t krylov_steps, uint64_t seed, const vne_options *opt,
                                 double *estimates, double *std_errors);
+
+/* ---- serving: continuous batching of entropy queries -------------------
+ * A server admits queued queries (FIFO) while the active set fits
+ * `hbm_budget_bytes` (each query counts its resident CSR plus one block of
+ * Lanczos vectors) and `max_active` slots.  Each vne_server_step is one
+ * tick: it packs the active graphs block-diagonally on the device and runs
+ * one Lanczos block (`block_vectors` Rademacher probes x `krylov_steps`
+ * steps) for all of them in one batched launch sequence, then updates every
+ * query's running mean and standard error and retires those with
+ * 2.576 * stderr <= (eps / 2) * |estimate| (after at least two blocks) or
+ * with max_vectors probes.  A query's probes in its t-th block are columns
+ * t*block .. (t+1)*block-1 of its own seed, so its result is bit-identical
+ * alone and in any mix.  This is the stated proxy for the adaptive
+ * stopping of Section 5.2 (Hutchinson part only; no low-rank sketch).
+ * Matrices must be FP32 graph patterns of the server's context and stay
+ * alive until their queries are done. */
+typedef struct vne_server vne_server;
+vne_status vne_server_create(vne_ctx *ctx, uint64_t hbm_budget_bytes, int32_t max_active, int32_t krylov_steps,
+                             int32_t block_vectors, const vne_options *opt, vne_server **out);
+vne_status vne_server_destroy(vne_server *srv);
+/* Queue a query: relative accuracy rel_eps, probe seed, cap on probe vectors.
+ * ENOMEM if the query alone exceeds the budget. */
+vne_status vne_server_submit(vne_server *srv, vne_matrix *mat, double rel_eps, uint64_t seed, int32_t max_vectors,
+                             int32_t *ticket);
+/* One tick (admission + one batched block); completed = queries retired in it,
+ * active = queries that ran in it. */
+vne_status vne_server_step(vne_server *srv, int32_t *completed, int32_t *active);
+/* state 0 queued / 1 active / 2 done; ticks[3] = {submit, admit, done} tick. */
+vne_status vne_server_result(const vne_server *srv, int32_t ticket, int32_t *state, double *estimate,
+                             double *std_error, int64_t *vectors_used, int64_t *ticks);
+vne_status vne_server_info(const vne_server *srv, int32_t *queued, int32_t *active, uint64_t *used_bytes);
 
 /* ---- allocation-free quadratic forms ---------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -17,6 +17,8 @@ struct StartSource {
     uint64_t seed_mixed;
     const int32_t* colors;  // SRC_INDICATOR: colour per local node id
     const double* dense;    // SRC_DENSE64: [n][ld] in caller numbering
+    const uint64_t* seg_seed;  // SRC_RADEMACHER, optional: per-segment mixed seed
+    const int32_t* seg_col0;   //   and per-segment first probe column
 };
 
 template <typename T>

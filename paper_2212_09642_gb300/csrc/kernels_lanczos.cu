@@ -77,12 +77,14 @@ __device__ __forceinline__ double rademacher_entry(uint64_t s, uint64_t col, uin
     return (h >> 63) ? -1.0 : 1.0;
 }
 
-// Start-vector source value for packed row r (local node id `id`) and block
-// column gc (global within the block).
-__device__ __forceinline__ double source_value(const StartSource& S, int r, int id, int gc) {
+// Start-vector source value for packed row r (local node id `id`, segment
+// seg) and block column gc (global within the block).
+__device__ __forceinline__ double source_value(const StartSource& S, int r, int id, int gc, int seg) {
     if (gc >= S.ncols) return 0.0;
     switch (S.kind) {
         case SRC_RADEMACHER:
+            if (S.seg_seed)
+                return rademacher_entry(S.seg_seed[seg], (uint64_t)(S.seg_col0[seg] + gc), (uint64_t)id);
             return rademacher_entry(S.seed_mixed, (uint64_t)(S.col_begin + gc), (uint64_t)id);
         case SRC_INDICATOR:
             return (S.colors[id] == S.col_begin + gc) ? 1.0 : 0.0;
@@ -95,13 +97,13 @@ __device__ __forceinline__ double source_value(const StartSource& S, int r, int 
 
 template <typename T, int KS>
 __device__ __forceinline__ double source_value_panel(const StartSource& S, const T* panel_src, int r,
-                                                     int id, int gc, int n_total) {
+                                                     int id, int gc, int n_total, int seg) {
     if (S.kind == SRC_PANEL) {
         if (gc >= S.ncols) return 0.0;
         const T* base = panel_src + (size_t)(gc / KS) * n_total * KS;
         return (double)base[(size_t)r * KS + (gc % KS)];
     }
-    return source_value(S, r, id, gc);
+    return source_value(S, r, id, gc, seg);
 }
 
 // Pass 1: column sums per segment -> mean (only when desingularising).
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     double acc = 0.0;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        acc += source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total);
+        acc += source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg);
     }
     __shared__ double red[VNE_THREADS];
     red[threadIdx.x] = acc;
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
     double acc = 0.0;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        double v = source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total) - mu;
+        double v = source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg) - mu;
         if (gc >= p.src.ncols) v = 0.0;
         out[(size_t)r * KS + c] = (T)v;
         acc += v * v;

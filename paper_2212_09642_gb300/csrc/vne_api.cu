@@ -61,7 +61,7 @@ struct vne_ctx {
     int64_t launches = 0;  // kernels launched by this context
     int last_cg_iters = 0; // largest multi-shift CG iteration count of the last rational call
     bool profile = false;
-    KernelStat stat[2];    // 0: step (SpMM) kernel, 1: update kernel
+    KernelStat stat[4];    // 0: step (SpMM) kernel, 1: update kernel, 2: CG update, 3: CG direction
     std::vector<cudaEvent_t> ev_pool;
     struct Pending {
         int kind;
@@ -139,7 +139,9 @@ void set_err(vne_ctx* ctx, const char* fmt, ...) {
     } while (0)
 
 // Workspace buffers grow on demand and are kept for the life of the context,
-// so the hot loop never allocates.
+// so the hot loop never allocates.  New allocations are zero-filled (the
+// cross-CTA counters rely on starting at zero; the kernels reset them after
+// use).  zero = true clears the requested bytes on every call.
 void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero = false) {
     WsBuf& b = ctx->ws[name];
     if (b.bytes < bytes) {
@@ -148,6 +150,7 @@ void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero = fa
         b.bytes = 0;
         size_t alloc = std::max<size_t>(bytes, 256);
         VNE_TRY_CUDA(ctx, cudaMalloc(&b.ptr, alloc));
+        VNE_TRY_CUDA(ctx, cudaMemsetAsync(b.ptr, 0, alloc, ctx->stream));
         b.bytes = alloc;
     }
     if (zero && bytes) VNE_TRY_CUDA(ctx, cudaMemsetAsync(b.ptr, 0, bytes, ctx->stream));
@@ -223,12 +226,15 @@ struct Problem {
     int32_t* d_cta_seg = nullptr;
     RowTile* d_tiles = nullptr;
     std::vector<void*> owned;  // extra device buffers owned by the problem (batch packing)
+    bool owns_tables = true;   // false: the tables live in context workspace
     ~Problem() {
-        cudaFree(d_segs);
-        cudaFree(d_items);
-        cudaFree(d_hubs);
-        cudaFree(d_cta_seg);
-        cudaFree(d_tiles);
+        if (owns_tables) {
+            cudaFree(d_segs);
+            cudaFree(d_items);
+            cudaFree(d_hubs);
+            cudaFree(d_cta_seg);
+            cudaFree(d_tiles);
+        }
         for (void* p : owned) cudaFree(p);
     }
     int ctas_per_panel() const { return (int)(items.size() / VNE_WARPS); }
@@ -657,8 +663,21 @@ void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* ou
     p.alpha = dq;
     p.part = ws_get_t<double>(ctx, "op.part", (size_t)panels * std::max(ctas, tiles) * ks);
     p.counter = ws_get_t<uint32_t>(ctx, "op.counter", (size_t)panels);
+    cudaEvent_t e0 = nullptr;
+    if (ctx->profile) {
+        e0 = ctx_event(ctx);
+        VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
+    }
     VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
     ctx->launches += 1;
+    if (ctx->profile) {
+        cudaEvent_t e1 = ctx_event(ctx);
+        VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+        const double es = sizeof(T);
+        double csr = 4.0 * (P.n_total + 1) + (double)P.nnz_total * (4.0 + (P.valued ? es : 0.0));
+        double vec = (double)P.n_total * ks * es;
+        ctx->pending.push_back({0, e0, e1, panels * (csr + vec * (shift != 0.0 ? 3.0 : 2.0))});
+    }
 }
 
 // Rational Krylov quadratic forms (poles -shifts[i] and n_inf poles at
@@ -761,11 +780,34 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
     for (; it < max_iter; it++) {
         apply_operator<T>(ctx, P, ks, Kp, v.p, v.q, s0, dq, variant, "rat.op");
         VNE_TRY_CUDA(ctx, launch_cg_scalars_a(cs, st));
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+        if (ctx->profile) {
+            e0 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
+        }
         VNE_TRY_CUDA(ctx, launch_cg_update<T>(v, cs, ks, panels, st));
+        if (ctx->profile) {
+            e1 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+        }
         VNE_TRY_CUDA(ctx, cudaMemsetAsync(cs.any_active, 0, sizeof(int32_t), st));
         VNE_TRY_CUDA(ctx, launch_cg_scalars_b(cs, st));
+        if (ctx->profile) {
+            e2 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e2, st));
+        }
         VNE_TRY_CUDA(ctx, launch_cg_direction<T>(v, cs, ks, panels, st));
         ctx->launches += 4;
+        if (ctx->profile) {
+            e3 = ctx_event(ctx);
+            VNE_TRY_CUDA(ctx, cudaEventRecord(e3, st));
+            // algorithmic bytes with every shift counted active (an upper bound
+            // once shifts retire): update reads r, q and (x_s, p_s) per shift and
+            // writes r, x_s; direction reads r, p, p_s and writes p, p_s
+            const double vec = (double)n * Kp * sizeof(T);
+            ctx->pending.push_back({2, e0, e1, vec * (3.0 + 3.0 * nshift)});
+            ctx->pending.push_back({3, e2, e3, vec * (3.0 + 2.0 * nshift)});
+        }
         if ((it & 7) == 7 || it + 1 == max_iter) {
             int32_t any = 0;
             VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&any, cs.any_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1612,7 +1654,7 @@ extern "C" vne_status vne_ctx_stats(const vne_ctx* ctx, int64_t* launches, doubl
     if (!ctx) return VNE_EINVAL;
     if (launches) *launches = ctx->launches;
     if (kernel_stats)
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < 4; k++) {
             kernel_stats[3 * k + 0] = (double)ctx->stat[k].launches;
             kernel_stats[3 * k + 1] = ctx->stat[k].ms;
             kernel_stats[3 * k + 2] = ctx->stat[k].bytes;
@@ -1728,4 +1770,279 @@ extern "C" vne_status vne_quadform_rational(vne_matrix* M, const double* vectors
     if (cg_iterations) std::copy(its.begin(), its.end(), cg_iterations);
     if (residuals) std::copy(rs.begin(), rs.end(), residuals);
     VNE_API_END(ctx)
+}
+
+// ---------------------------------------------------------------------------
+// serving: continuous batching of entropy queries
+//
+// Each tick admits queued requests (FIFO) while the active set fits the HBM
+// budget and the slot limit, packs the active graphs block-diagonally on the
+// device (their CSR stays resident from vne_create_density_matrix), and runs
+// one Lanczos block of `block` Rademacher probes per request in one batched
+// launch sequence.  A request's probes for tick t are its columns
+// t*block .. (t+1)*block-1, so its numbers do not depend on its neighbours.
+// After the block each request updates its running mean and variance and
+// retires once 2.576 * stderr <= (eps / 2) * |mean| (at least two blocks) or
+// its vector cap is reached.
+
+namespace {
+
+__global__ void k_pack_rowptr(const int32_t* src, int n, int32_t e0, int32_t* dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] + e0;
+}
+__global__ void k_pack_col(const int32_t* src, int64_t nnz, int32_t r0, int32_t* dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) dst[i] = src[i] + r0;
+}
+__global__ void k_pack_ids(const int32_t* perm, int n, int32_t* dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = perm ? perm[i] : i;
+}
+
+}  // namespace
+
+struct vne_server {
+    vne_ctx* ctx = nullptr;
+    size_t budget = 0, used = 0;
+    int max_active = 64, m = 40, block = 64, max_vectors = 8192;
+    vne_options opt;
+    struct Req {
+        vne_matrix* M;
+        double eps;
+        uint64_t seed_mixed;
+        int max_vectors;
+        int state;  // 0 queued, 1 active, 2 done
+        int64_t nvec;
+        double mean, m2, est, se;
+        size_t footprint;
+        int64_t submit_tick, admit_tick, done_tick;
+        int blocks;
+    };
+    std::vector<Req> reqs;
+    std::vector<int> pending;  // FIFO (front = index pend_head)
+    size_t pend_head = 0;
+    std::vector<int> active;
+    int64_t tick = 0;
+};
+
+extern "C" vne_status vne_server_create(vne_ctx* ctx, uint64_t hbm_budget_bytes, int32_t max_active,
+                                        int32_t krylov_steps, int32_t block_vectors, const vne_options* opt,
+                                        vne_server** out) {
+    if (!ctx || !out) return VNE_EINVAL;
+    *out = nullptr;
+    if (max_active < 1 || krylov_steps < 1 || krylov_steps > 128 || block_vectors < 2 || block_vectors > 256)
+        return VNE_EINVAL;
+    vne_server* S = new (std::nothrow) vne_server();
+    if (!S) return VNE_ENOMEM;
+    S->ctx = ctx;
+    S->budget = hbm_budget_bytes;
+    S->max_active = max_active;
+    S->m = krylov_steps;
+    S->block = block_vectors;
+    if (opt) S->opt = *opt;
+    else vne_options_default(&S->opt);
+    *out = S;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_server_destroy(vne_server* S) {
+    if (!S) return VNE_EINVAL;
+    delete S;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_server_submit(vne_server* S, vne_matrix* M, double rel_eps, uint64_t seed,
+                                        int32_t max_vectors, int32_t* ticket) {
+    if (!S || !M || !ticket || !(rel_eps > 0.0) || max_vectors < 2) return VNE_EINVAL;
+    vne_ctx* ctx = S->ctx;
+    if (M->ctx != ctx || M->fp64 || !M->pattern) {
+        set_err(ctx, "serving takes FP32 graph (pattern) matrices of the server's context");
+        return VNE_EINVAL;
+    }
+    vne_server::Req r{};
+    r.M = M;
+    r.eps = rel_eps;
+    r.seed_mixed = seed_mix(seed);
+    r.max_vectors = max_vectors;
+    const int ks = resolve_sched(M, &S->opt).ks;
+    const int Kp = ((S->block + ks - 1) / ks) * ks;
+    // resident CSR + the block's Lanczos vectors (2 slots + u) + scalars
+    r.footprint = (size_t)4 * (M->n + 1 + M->nnz) + (size_t)3 * M->n * Kp * 4 + (size_t)(3 * S->m + 8) * Kp * 8;
+    if (r.footprint > S->budget) {
+        set_err(ctx, "request footprint %zu exceeds the HBM budget %zu", r.footprint, S->budget);
+        return VNE_ENOMEM;
+    }
+    r.submit_tick = S->tick;
+    *ticket = (int32_t)S->reqs.size();
+    S->reqs.push_back(r);
+    S->pending.push_back(*ticket);
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t* active_count) {
+    if (!S) return VNE_EINVAL;
+    vne_ctx* ctx = S->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    if (completed) *completed = 0;
+    // admission
+    while (S->pend_head < S->pending.size() && (int)S->active.size() < S->max_active) {
+        vne_server::Req& r = S->reqs[S->pending[S->pend_head]];
+        if (S->used + r.footprint > S->budget) break;
+        S->used += r.footprint;
+        r.state = 1;
+        r.admit_tick = S->tick;
+        S->active.push_back(S->pending[S->pend_head]);
+        S->pend_head++;
+    }
+    if (active_count) *active_count = (int32_t)S->active.size();
+    S->tick++;
+    if (S->active.empty()) return VNE_OK;
+    const vne_options& o = S->opt;
+    // all active matrices share the schedule knobs of the server options
+    const int target = default_item_nnz(&o);
+    int ks = 0, variant = 0;
+    Problem P;
+    P.owns_tables = false;
+    P.fp64 = false;
+    P.valued = false;
+    int64_t ntot = 0, nnztot = 0;
+    for (int idx : S->active) {
+        ntot += S->reqs[idx].M->n;
+        nnztot += S->reqs[idx].M->nnz;
+    }
+    VNE_REQUIRE(ctx, ntot < INT32_MAX && nnztot < INT32_MAX, VNE_EINVAL, "active set too large");
+    int32_t* prp = ws_get_t<int32_t>(ctx, "srv.rowptr", ntot + 1);
+    int32_t* pci = ws_get_t<int32_t>(ctx, "srv.col", std::max<int64_t>(nnztot, 1));
+    int32_t* pid = ws_get_t<int32_t>(ctx, "srv.ids", ntot);
+    std::vector<uint64_t> seeds;
+    std::vector<int32_t> col0;
+    int64_t r0 = 0, e0 = 0;
+    cudaStream_t st = ctx->stream;
+    for (size_t sidx = 0; sidx < S->active.size(); sidx++) {
+        vne_server::Req& rq = S->reqs[S->active[sidx]];
+        vne_matrix* M = rq.M;
+        Sched sc = resolve_sched(M, &o);
+        if (sidx == 0) {
+            ks = sc.ks;
+            variant = sc.variant;
+        }
+        Problem* MP = matrix_problem(M, &o);  // the matrix's own (cached) schedule
+        const int n = (int)M->n;
+        k_pack_rowptr<<<(n + 255) / 256, 256, 0, st>>>(M->d_rowptr, n, (int32_t)e0, prp + r0);
+        if (M->nnz) k_pack_col<<<(unsigned)((M->nnz + 255) / 256), 256, 0, st>>>(M->d_col, M->nnz, (int32_t)r0, pci + e0);
+        k_pack_ids<<<(n + 255) / 256, 256, 0, st>>>(M->d_node_id, n, pid + r0);
+        ctx->launches += 3;
+        SegInfo sg = MP->segs[0];
+        const int32_t seg = (int32_t)sidx;
+        const int32_t hub_base = (int32_t)P.hubs.size(), slot_base = P.hub_slots;
+        sg.row_begin = (int32_t)r0;
+        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);
+        sg.tile_begin = (int32_t)P.tiles.size();
+        sg.hub_begin = hub_base;
+        for (WorkItem it : MP->items) {
+            if (it.rows > 0) it.row += (int32_t)r0;
+            else if (it.rows < 0) it.row += hub_base;
+            if (it.rows != 0) {
+                it.nnz_begin += (int32_t)e0;
+                it.nnz_end += (int32_t)e0;
+            }
+            P.items.push_back(it);
+        }
+        for (HubRow h : MP->hubs) {
+            h.row += (int32_t)r0;
+            h.slot += slot_base;
+            h.seg = seg;
+            P.hubs.push_back(h);
+        }
+        P.hub_slots += MP->hub_slots;
+        for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
+        for (RowTile t : MP->tiles) {
+            t.row_begin += (int32_t)r0;
+            t.row_end += (int32_t)r0;
+            t.seg = seg;
+            P.tiles.push_back(t);
+        }
+        P.stage_nnz = std::max(P.stage_nnz, MP->stage_nnz);
+        P.segs.push_back(sg);
+        seeds.push_back(rq.seed_mixed);
+        col0.push_back(rq.blocks * S->block);
+        r0 += M->n;
+        e0 += M->nnz;
+    }
+    const int32_t last = (int32_t)nnztot;
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(prp + ntot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    VNE_TRY_CUDA(ctx, cudaGetLastError());
+    P.n_total = (int32_t)ntot;
+    P.nnz_total = nnztot;
+    P.nseg = (int32_t)S->active.size();
+    P.rowptr = prp;
+    P.col = pci;
+    P.node_id = pid;
+    P.d_segs = upload(ctx, "srv.segs", P.segs);
+    P.d_items = upload(ctx, "srv.items", P.items);
+    P.d_hubs = upload(ctx, "srv.hubs", P.hubs);
+    P.d_cta_seg = upload(ctx, "srv.ctaseg", P.cta_seg);
+    P.d_tiles = upload(ctx, "srv.tiles", P.tiles);
+    StartSource src{};
+    src.kind = SRC_RADEMACHER;
+    src.ncols = S->block;
+    src.seg_seed = upload(ctx, "srv.seeds", seeds);
+    src.seg_col0 = upload(ctx, "srv.col0", col0);
+    BlockOut out;
+    check_ks<float>(ctx, ks);
+    run_block<float>(ctx, P, src, nullptr, S->block, ks, S->m, false, false, true, "srv", out, variant);
+    std::vector<double> psi = download(ctx, out.psi, out.SK);
+    // statistics and retirement
+    std::vector<int> still;
+    for (size_t sidx = 0; sidx < S->active.size(); sidx++) {
+        const int idx = S->active[sidx];
+        vne_server::Req& rq = S->reqs[idx];
+        for (int c = 0; c < S->block; c++) {  // Welford update
+            const double x = psi[sidx * out.Kp + c];
+            rq.nvec++;
+            const double d = x - rq.mean;
+            rq.mean += d / (double)rq.nvec;
+            rq.m2 += d * (x - rq.mean);
+        }
+        rq.blocks++;
+        rq.est = rq.mean;
+        rq.se = rq.nvec > 1 ? sqrt(rq.m2 / (double)(rq.nvec - 1) / (double)rq.nvec) : 0.0;
+        const bool converged = rq.blocks >= 2 && 2.576 * rq.se <= 0.5 * rq.eps * fabs(rq.mean);
+        if (converged || rq.nvec >= rq.max_vectors) {
+            rq.state = 2;
+            rq.done_tick = S->tick;
+            S->used -= rq.footprint;
+            if (completed) (*completed)++;
+        } else {
+            still.push_back(idx);
+        }
+    }
+    S->active.swap(still);
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_server_result(const vne_server* S, int32_t ticket, int32_t* state, double* estimate,
+                                        double* std_error, int64_t* vectors_used, int64_t* ticks) {
+    if (!S || ticket < 0 || ticket >= (int32_t)S->reqs.size()) return VNE_EINVAL;
+    const vne_server::Req& r = S->reqs[ticket];
+    if (state) *state = r.state;
+    if (estimate) *estimate = r.est;
+    if (std_error) *std_error = r.se;
+    if (vectors_used) *vectors_used = r.nvec;
+    if (ticks) {
+        ticks[0] = r.submit_tick;
+        ticks[1] = r.admit_tick;
+        ticks[2] = r.done_tick;
+    }
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_server_info(const vne_server* S, int32_t* queued, int32_t* active, uint64_t* used_bytes) {
+    if (!S) return VNE_EINVAL;
+    if (queued) *queued = (int32_t)(S->pending.size() - S->pend_head);
+    if (active) *active = (int32_t)S->active.size();
+    if (used_bytes) *used_bytes = S->used;
+    return VNE_OK;
 }

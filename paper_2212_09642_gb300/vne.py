@@ -86,6 +86,13 @@ def _declare(lib):
         "vne_batch_hutchinson": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.POINTER(vne_options), _P, _P]),
         "vne_ctx_profile": (st, [_P, ctypes.c_int32]),
+        "vne_server_create": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(vne_options), ctypes.POINTER(_P)]),
+        "vne_server_destroy": (st, [_P]),
+        "vne_server_submit": (st, [_P, _P, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32, _PI32]),
+        "vne_server_step": (st, [_P, _PI32, _PI32]),
+        "vne_server_result": (st, [_P, ctypes.c_int32, _PI32, _PD, _PD, _PI64, _P]),
+        "vne_server_info": (st, [_P, _PI32, _PI32, ctypes.POINTER(ctypes.c_uint64)]),
         "vne_quadform_rational": (st, [_P, _P, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.c_int32,
                                        ctypes.POINTER(vne_options), _PD, _P, _P]),
         "vne_autotune": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vne_options), _PD]),
@@ -120,7 +127,9 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
-               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational"]
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
+               "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
+               "vne_server_result", "vne_server_info"]
 
 
 def _check(status, ctx=None):
@@ -316,11 +325,12 @@ def vne_ctx_profile(ctx, enable=True):
 
 
 def vne_ctx_stats(ctx):
-    """(launches, {"step": (count, ms, bytes), "update": (count, ms, bytes)})."""
+    """(launches, {kind: (count, ms, algorithmic bytes)}) for kinds step, update, cg_update, cg_direction."""
     n = ctypes.c_int64()
-    st = np.zeros(6)
+    st = np.zeros(12)
     _check(load().vne_ctx_stats(ctx, ctypes.byref(n), _ptr(st)), ctx)
-    return n.value, {"step": tuple(st[0:3]), "update": tuple(st[3:6])}
+    names = ["step", "update", "cg_update", "cg_direction"]
+    return n.value, {nm: tuple(st[3 * i:3 * i + 3]) for i, nm in enumerate(names)}
 
 
 def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, krylov_steps, psi_dev):
@@ -331,6 +341,50 @@ def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, kr
                                      int(krylov_steps), _ptr(psi_dev))
     if st != VNE_OK:
         raise VneError(st, "vne_quadform_noalloc rejected the call (sizes beyond the fixed scratch, or bad arguments)")
+
+
+def vne_server_create(ctx, hbm_budget_bytes, max_active=64, krylov_steps=40, block_vectors=64, opt=None):
+    h = _P()
+    o = opt if opt is not None else options()
+    _check(load().vne_server_create(ctx, int(hbm_budget_bytes), int(max_active), int(krylov_steps),
+                                    int(block_vectors), ctypes.byref(o), ctypes.byref(h)), ctx)
+    return h
+
+
+def vne_server_destroy(srv):
+    _check(load().vne_server_destroy(srv))
+
+
+def vne_server_submit(ctx, srv, mat, rel_eps, seed, max_vectors=8192):
+    t = ctypes.c_int32()
+    _check(load().vne_server_submit(srv, mat, float(rel_eps), int(seed) & (2**64 - 1), int(max_vectors),
+                                    ctypes.byref(t)), ctx)
+    return t.value
+
+
+def vne_server_step(ctx, srv):
+    done, act = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().vne_server_step(srv, ctypes.byref(done), ctypes.byref(act)), ctx)
+    return done.value, act.value
+
+
+def vne_server_result(srv, ticket):
+    """dict(state, estimate, std_error, vectors, submit_tick, admit_tick, done_tick)."""
+    state = ctypes.c_int32()
+    est, se = ctypes.c_double(), ctypes.c_double()
+    nv = ctypes.c_int64()
+    ticks = np.zeros(3, dtype=np.int64)
+    _check(load().vne_server_result(srv, int(ticket), ctypes.byref(state), ctypes.byref(est), ctypes.byref(se),
+                                    ctypes.byref(nv), _ptr(ticks)))
+    return dict(state=state.value, estimate=est.value, std_error=se.value, vectors=nv.value,
+                submit_tick=int(ticks[0]), admit_tick=int(ticks[1]), done_tick=int(ticks[2]))
+
+
+def vne_server_info(srv):
+    q, a = ctypes.c_int32(), ctypes.c_int32()
+    u = ctypes.c_uint64()
+    _check(load().vne_server_info(srv, ctypes.byref(q), ctypes.byref(a), ctypes.byref(u)))
+    return q.value, a.value, u.value
 
 
 # ---------------------------------------------------------------------------

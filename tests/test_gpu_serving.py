@@ -1,0 +1,94 @@
+"""Serving (continuous batching): queries admitted by HBM budget and slots,
+batched per tick; each result is bit-identical alone and in the mix, and
+matches the oracle's Hutchinson estimate on the same probes (mixed path,
+1e-5 relative)."""
+import numpy as np
+import pytest
+
+from oracle import density, estimators
+from paper_2212_09642_gb300 import graphs, vne
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs():
+    return [graphs.erdos_renyi(3000, 8 / 2999, 31), graphs.barabasi_albert(5000, 3, 32),
+            graphs.watts_strogatz(2000, 6, 0.1, 33), graphs.barabasi_albert(1500, 3, 34),
+            graphs.erdos_renyi(7000, 8 / 6999, 35)]
+
+
+def _run(vctx, mats, schedule, budget, max_active, eps=2e-3, cap=1024):
+    """schedule: list of (tick, matrix index, seed); returns per-request results and
+    the largest number of queries active in one tick.  Checks that the bytes
+    held by admitted queries never exceed the budget."""
+    srv = vne.vne_server_create(vctx, budget, max_active=max_active, krylov_steps=30, block_vectors=64,
+                                opt=vne.options(reorth=0, panel=8))
+    tickets = {}
+    most = 0
+    try:
+        tick = 0
+        pending = list(schedule)
+        while True:
+            while pending and pending[0][0] <= tick:
+                _, mi, seed = pending.pop(0)
+                tickets[(mi, seed)] = vne.vne_server_submit(vctx, srv, mats[mi], eps, seed, cap)
+            done, active = vne.vne_server_step(vctx, srv)
+            most = max(most, active)
+            q, a, used = vne.vne_server_info(srv)
+            assert used <= budget
+            tick += 1
+            if not pending and q == 0 and a == 0:
+                break
+            assert tick < 10000
+        res = {k: vne.vne_server_result(srv, t) for k, t in tickets.items()}
+    finally:
+        vne.vne_server_destroy(srv)
+    return res, most
+
+
+def test_serving_same_alone_and_in_mix(vctx):
+    gs = _graphs()
+    mats = [vne.matrix_from_graph(vctx, g, fp64=False) for g in gs]
+    try:
+        mix = [(0, 0, 11), (0, 1, 12), (1, 2, 13), (3, 3, 14), (3, 0, 15), (5, 4, 16), (9, 1, 17)]
+        mixed, most = _run(vctx, mats, mix, budget=1 << 36, max_active=8)
+        assert most >= 3  # queries really overlapped
+        for (mi, seed), r in mixed.items():
+            assert r["state"] == 2
+            alone, _ = _run(vctx, mats, [(0, mi, seed)], budget=1 << 36, max_active=8)
+            ra = alone[(mi, seed)]
+            assert ra["estimate"] == r["estimate"] and ra["vectors"] == r["vectors"]
+            A, _ = density.density_matrix(gs[mi])
+            ref, _ = estimators.hutchinson(A, r["vectors"], 30, seed=seed, reorth="none")
+            assert abs(r["estimate"] - ref) <= 1e-5 * ref
+            conv = 2.576 * r["std_error"] <= 0.5 * 2e-3 * r["estimate"]
+            assert conv or r["vectors"] >= 1024
+    finally:
+        for m in mats:
+            vne.vne_matrix_destroy(m)
+
+
+def test_serving_admission_respects_budget_and_slots(vctx):
+    gs = _graphs()
+    mats = [vne.matrix_from_graph(vctx, g, fp64=False) for g in gs]
+    try:
+        sched = [(0, i % 5, 100 + i) for i in range(8)]
+        # slots: at most 2 queries per tick
+        res, most = _run(vctx, mats, sched, budget=1 << 36, max_active=2)
+        assert most <= 2 and all(r["state"] == 2 for r in res.values())
+        # budget: room for about two of the larger queries only
+        biggest = max(g.n for g in gs)
+        budget = int(2.2 * (3 * biggest * 64 * 4 + 4 * 80000))
+        res2, most2 = _run(vctx, mats, sched, budget=budget, max_active=8)
+        assert most2 < 8 and all(r["state"] == 2 for r in res2.values())
+        for k in res:
+            assert res[k]["estimate"] == res2[k]["estimate"]
+        with pytest.raises(vne.VneError):  # a query larger than the whole budget
+            srv = vne.vne_server_create(vctx, 1000, max_active=2, krylov_steps=30, block_vectors=64)
+            try:
+                vne.vne_server_submit(vctx, srv, mats[0], 1e-3, 1)
+            finally:
+                vne.vne_server_destroy(srv)
+    finally:
+        for m in mats:
+            vne.vne_matrix_destroy(m)
