@@ -150,8 +150,18 @@ cudaError_t launch_cg_scalars_b(const CgState&, cudaStream_t);
 template <typename T> cudaError_t launch_cg_update(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_cg_direction(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_pair_dots(const PairDots<T>&, int npairs, double* out, cudaStream_t);
-cudaError_t launch_rational_small(const double* M, const double* K, int nb, int ncols, double drop, double* psi,
-                                  int* rank, cudaStream_t);
+template <typename T>
+struct BlockTransform {
+    int32_t n, K, nb, tiles_per_panel;
+    const RowTile* tiles;
+    const T* in[12];
+    T* out[12];
+    const double* X;  // [nb][nb][K]
+};
+cudaError_t launch_rational_pass1(const double* M, int nb, int ncols, double drop, double* X, cudaStream_t);
+cudaError_t launch_rational_pass2(const double* M, const double* K, const double* c2, int nb, int ncols, double drop,
+                                  double* psi, int* rank, cudaStream_t);
+template <typename T> cudaError_t launch_block_transform(const BlockTransform<T>&, int ks, int panels, cudaStream_t);
 cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t);
 
 // ---- dense / small kernels (kernels_dense.cu) ----

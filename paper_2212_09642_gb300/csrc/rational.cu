@@ -23,8 +23,11 @@
 // accumulated per column, and a per-column FP64 kernel orthonormalises W in
 // pole order (Cholesky of the column-scaled Gram, dropping dependent
 // columns; the first basis vector is c / ||c|| as in rational Arnoldi),
-// projects A, diagonalises the small matrix by cyclic Jacobi and returns
-// psi = ||c||^2 e1^T f(A_m) e1.
+// applies that basis change to the vectors W and A W and repeats the
+// orthonormalisation from the new Gram matrices (Cholesky-QR2, so the
+// rounding error no longer grows with the square of the basis condition
+// number), projects A, diagonalises the small matrix by cyclic Jacobi and
+// returns psi = ||c||^2 e1^T f(A_m) e1.
 #include <float.h>
 #include <math.h>
 
@@ -258,52 +261,73 @@ __global__ void k_pair_reduce(const double* part, int npairs, int panels, int ti
     out[(size_t)pair * K + col] = s;
 }
 
-// Per column: orthonormalise W in order via Cholesky of the scaled Gram
-// (dropping columns whose pivot is <= drop), A_m = R^-T Kt R^-1, cyclic
-// Jacobi, psi = ||c||^2 sum_k z_{1k}^2 f(mu_k).
-__global__ void k_rational_small(const double* Mg, const double* Kg, int nb, int K, double drop, double* psi,
-                                 int* rank_out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= K) return;
-    double Mt[kMaxBasis][kMaxBasis], Kt[kMaxBasis][kMaxBasis], D[kMaxBasis];
+// Per-column Cholesky of the column-scaled Gram matrix in pole order.  A
+// column whose pivot (squared relative remainder) is <= drop is dependent on
+// the kept ones and is dropped.  Returns the kept count; R (upper, kept
+// columns) and D (column scales) are outputs.
+__device__ int gram_cholesky(const double* Mg, int nb, int K, int c, double drop, double (&R)[kMaxBasis][kMaxBasis],
+                             double (&D)[kMaxBasis], int (&keep)[kMaxBasis]) {
     for (int a = 0; a < nb; a++) {
         double maa = Mg[((size_t)a * nb + a) * K + c];
         D[a] = maa > 0.0 ? 1.0 / sqrt(maa) : 0.0;
     }
-    for (int a = 0; a < nb; a++)
-        for (int b = 0; b < nb; b++) {
-            Mt[a][b] = Mg[((size_t)a * nb + b) * K + c] * D[a] * D[b];
-            // symmetrise W^T A W
-            Kt[a][b] = 0.5 * (Kg[((size_t)a * nb + b) * K + c] + Kg[((size_t)b * nb + a) * K + c]) * D[a] * D[b];
+    int r = 0;
+    for (int a = 0; a < nb; a++) {
+        if (D[a] == 0.0) continue;
+        double col[kMaxBasis];
+        double s = 1.0;
+        for (int i = 0; i < r; i++) {
+            double v = Mg[((size_t)keep[i] * nb + a) * K + c] * D[keep[i]] * D[a];
+            for (int l = 0; l < i; l++) v -= R[l][i] * col[l];
+            col[i] = v / R[i][i];
+            s -= col[i] * col[i];
         }
-    const double c2 = Mg[c];  // ||c||^2
+        if (s <= drop) continue;
+        for (int i = 0; i < r; i++) R[i][r] = col[i];
+        R[r][r] = sqrt(s);
+        keep[r++] = a;
+    }
+    return r;
+}
+
+// Pass 1: X[c] = P D R^{-1} (nb x nb, rows by original column, zero for
+// dropped ones) so that W X has orthonormal columns up to rounding; the
+// second pass re-orthonormalises W X from its own Gram matrix (Cholesky-QR2).
+__global__ void k_rational_pass1(const double* Mg, int nb, int K, double drop, double* X) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double R[kMaxBasis][kMaxBasis], D[kMaxBasis];
+    int keep[kMaxBasis];
+    const int r = gram_cholesky(Mg, nb, K, c, drop, R, D, keep);
+    for (int i = 0; i < nb * nb; i++) X[(size_t)i * K + c] = 0.0;
+    for (int j = 0; j < r; j++) {
+        // column j of R^{-1} (back substitution)
+        double x[kMaxBasis];
+        x[j] = 1.0 / R[j][j];
+        for (int i = j - 1; i >= 0; i--) {
+            double v = 0.0;
+            for (int l = i + 1; l <= j; l++) v += R[i][l] * x[l];
+            x[i] = -v / R[i][i];
+        }
+        for (int i = 0; i <= j; i++) X[((size_t)keep[i] * nb + j) * K + c] = D[keep[i]] * x[i];
+    }
+}
+
+// Pass 2: orthonormalise the transformed basis, project A, diagonalise by
+// cyclic Jacobi, psi = ||c||^2 sum_k z_{1k}^2 f(mu_k).  c2 = ||c||^2.
+__global__ void k_rational_pass2(const double* Mg, const double* Kg, const double* c2v, int nb, int K, double drop,
+                                 double* psi, int* rank_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    const double c2 = c2v[(size_t)0 * K + c];
+    double R[kMaxBasis][kMaxBasis], D[kMaxBasis];
+    int keep[kMaxBasis];
     if (!(c2 > 0.0)) {
         psi[c] = 0.0;
         rank_out[c] = 0;
         return;
     }
-    // Cholesky in order with dropping: keep[] lists kept columns
-    int keep[kMaxBasis];
-    int r = 0;
-    double R[kMaxBasis][kMaxBasis];
-    for (int a = 0; a < nb; a++) {
-        if (D[a] == 0.0) continue;
-        // R[i][a] for kept i < a:  solve R^T col = Mt[kept][a]
-        double col[kMaxBasis];
-        double s = Mt[a][a];
-        for (int i = 0; i < r; i++) {
-            double v = Mt[keep[i]][a];
-            for (int l = 0; l < i; l++) v -= R[l][i] * col[l];
-            col[i] = v / R[i][i];
-            s -= col[i] * col[i];
-        }
-        if (s <= drop) continue;  // dependent on the kept columns
-        for (int i = 0; i < r; i++) R[i][r] = col[i];
-        for (int i = r + 1; i < kMaxBasis; i++) R[i][r] = 0.0;
-        R[r][r] = sqrt(s);
-        keep[r++] = a;
-    }
-    // Rinv (upper triangular r x r)
+    const int r = gram_cholesky(Mg, nb, K, c, drop, R, D, keep);
     double Ri[kMaxBasis][kMaxBasis];
     for (int j = 0; j < r; j++) {
         for (int i = 0; i < r; i++) Ri[i][j] = 0.0;
@@ -314,12 +338,16 @@ __global__ void k_rational_small(const double* Mg, const double* Kg, int nb, int
             Ri[i][j] = -v / R[i][i];
         }
     }
-    // A_m = Ri^T Kt_kept Ri
+    // A_m = Ri^T Kt Ri with Kt the scaled, symmetrised W^T A W on kept columns
     double T1[kMaxBasis][kMaxBasis], Am[kMaxBasis][kMaxBasis];
     for (int i = 0; i < r; i++)
         for (int j = 0; j < r; j++) {
             double v = 0.0;
-            for (int l = 0; l <= j; l++) v += Kt[keep[i]][keep[l]] * Ri[l][j];
+            for (int l = 0; l <= j; l++) {
+                const int a = keep[i], b = keep[l];
+                const double kab = 0.5 * (Kg[((size_t)a * nb + b) * K + c] + Kg[((size_t)b * nb + a) * K + c]);
+                v += kab * D[a] * D[b] * Ri[l][j];
+            }
             T1[i][j] = v;
         }
     for (int i = 0; i < r; i++)
@@ -328,9 +356,6 @@ __global__ void k_rational_small(const double* Mg, const double* Kg, int nb, int
             for (int l = 0; l <= i; l++) v += Ri[l][i] * T1[l][j];
             Am[i][j] = v;
         }
-    // cyclic Jacobi, eigenvector matrix Z (only row 0 is needed)
-    double z0[kMaxBasis];
-    for (int j = 0; j < r; j++) z0[j] = (j == 0) ? 1.0 : 0.0;
     double Z[kMaxBasis][kMaxBasis];
     for (int i = 0; i < r; i++)
         for (int j = 0; j < r; j++) Z[i][j] = (i == j) ? 1.0 : 0.0;
@@ -366,11 +391,39 @@ __global__ void k_rational_small(const double* Mg, const double* Kg, int nb, int
                 }
             }
     }
-    (void)z0;
     double s = 0.0;
     for (int k = 0; k < r; k++) s += Z[0][k] * Z[0][k] * f_ent(Am[k][k]);
     psi[c] = c2 * s;
     rank_out[c] = r;
+}
+
+// Per-column basis change: out_j = sum_i in_i X[i][j] (X per column, FP64,
+// staged in shared memory in the data precision).
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_block_transform(BlockTransform<T> bt) {
+    constexpr int RPI = VNE_THREADS / KS;
+    const int panel = blockIdx.x / bt.tiles_per_panel, tile = blockIdx.x % bt.tiles_per_panel;
+    const RowTile t = bt.tiles[tile];
+    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
+    const int col = panel * KS + c;
+    __shared__ T sx[kMaxBasis * kMaxBasis][KS];
+    for (int idx = threadIdx.x; idx < bt.nb * bt.nb * KS; idx += VNE_THREADS) {
+        const int e = idx / KS, cc = idx % KS;
+        sx[e][cc] = (T)bt.X[(size_t)e * bt.K + panel * KS + cc];
+    }
+    __syncthreads();
+    const size_t pofs = (size_t)panel * bt.n * KS;
+    for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
+        const size_t o = pofs + (size_t)r * KS + c;
+        T v[kMaxBasis];
+        for (int i = 0; i < bt.nb; i++) v[i] = bt.in[i][o];
+        for (int j = 0; j < bt.nb; j++) {
+            T acc = (T)0;
+            for (int i = 0; i < bt.nb; i++) acc += v[i] * sx[i * bt.nb + j][c];
+            bt.out[j][o] = acc;
+        }
+    }
+    (void)col;
 }
 
 // ---------------------------------------------------------------------------
@@ -412,10 +465,21 @@ cudaError_t launch_pair_dots(const PairDots<T>& pd, int npairs, double* out, cud
     k_pair_reduce<<<(npairs * K + 255) / 256, 256, 0, s>>>(pd.part, npairs, pd.panels, pd.tiles_per_panel, pd.ks, out);
     return cudaGetLastError();
 }
-cudaError_t launch_rational_small(const double* M, const double* Kmat, int nb, int K, double drop, double* psi,
-                                  int* rank, cudaStream_t s) {
+cudaError_t launch_rational_pass1(const double* M, int nb, int K, double drop, double* X, cudaStream_t s) {
     if (nb > kMaxBasis) return cudaErrorInvalidValue;
-    k_rational_small<<<(K + 31) / 32, 32, 0, s>>>(M, Kmat, nb, K, drop, psi, rank);
+    k_rational_pass1<<<(K + 31) / 32, 32, 0, s>>>(M, nb, K, drop, X);
+    return cudaGetLastError();
+}
+cudaError_t launch_rational_pass2(const double* M, const double* Kmat, const double* c2, int nb, int K, double drop,
+                                  double* psi, int* rank, cudaStream_t s) {
+    if (nb > kMaxBasis) return cudaErrorInvalidValue;
+    k_rational_pass2<<<(K + 31) / 32, 32, 0, s>>>(M, Kmat, c2, nb, K, drop, psi, rank);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_block_transform(const BlockTransform<T>& bt, int ks, int panels, cudaStream_t s) {
+    if (bt.nb > kMaxBasis) return cudaErrorInvalidValue;
+    VNE_KS_SWITCH(T, ks, (k_block_transform<T, KS><<<panels * bt.tiles_per_panel, VNE_THREADS, 0, s>>>(bt)));
     return cudaGetLastError();
 }
 
@@ -425,5 +489,7 @@ template cudaError_t launch_cg_direction<float>(const CgVectors<float>&, const C
 template cudaError_t launch_cg_direction<double>(const CgVectors<double>&, const CgState&, int, int, cudaStream_t);
 template cudaError_t launch_pair_dots<float>(const PairDots<float>&, int, double*, cudaStream_t);
 template cudaError_t launch_pair_dots<double>(const PairDots<double>&, int, double*, cudaStream_t);
+template cudaError_t launch_block_transform<float>(const BlockTransform<float>&, int, int, cudaStream_t);
+template cudaError_t launch_block_transform<double>(const BlockTransform<double>&, int, int, cudaStream_t);
 
 }  // namespace vne

@@ -182,6 +182,10 @@ cudaEvent_t ctx_event(vne_ctx* ctx) {
 // Resolve the recorded event pairs (the stream must be synchronised).
 void ctx_flush_profile(vne_ctx* ctx) {
     for (auto& p : ctx->pending) {
+        if (!p.a) {  // bytes-only record (work measured after the launches ran)
+            ctx->stat[p.kind].bytes += p.bytes;
+            continue;
+        }
         float ms = 0.f;
         VNE_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, p.a, p.b));
         ctx->stat[p.kind].launches++;
@@ -333,7 +337,7 @@ Sched resolve_sched(const vne_matrix* M, const vne_options* o) {
     Sched s;
     s.ks = (o && o->panel > 0) ? o->panel : (M->tuned ? M->tuned_panel : choose_panel(M->fp64, o, M->n));
     s.item_nnz = (o && o->item_nnz > 0) ? o->item_nnz : (M->tuned ? M->tuned_item_nnz : 256);
-    s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 0);
+    s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 4);
     if (M->fp64) s.variant = 0;
     return s;
 }
@@ -685,7 +689,8 @@ void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* ou
 template <typename T>
 void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int ks, const double* shifts,
                     int nshift, int n_inf, double tol, int max_iter, bool desing, int variant, double drop,
-                    std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid, int* rank_min) {
+                    double drop2, std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid,
+                    int* rank_min) {
     cudaStream_t st = ctx->stream;
     VNE_REQUIRE(ctx, P.nseg == 1, VNE_EUNSUPPORTED, "rational mode needs a single matrix");
     VNE_REQUIRE(ctx, nshift >= 1 && nshift <= 8, VNE_EINVAL, "1..8 finite poles are supported");
@@ -801,12 +806,13 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         if (ctx->profile) {
             e3 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e3, st));
-            // algorithmic bytes with every shift counted active (an upper bound
-            // once shifts retire): update reads r, q and (x_s, p_s) per shift and
-            // writes r, x_s; direction reads r, p, p_s and writes p, p_s
-            const double vec = (double)n * Kp * sizeof(T);
-            ctx->pending.push_back({2, e0, e1, vec * (3.0 + 3.0 * nshift)});
-            ctx->pending.push_back({3, e2, e3, vec * (3.0 + 2.0 * nshift)});
+            // algorithmic bytes of the seed part: update reads r, q, writes r;
+            // direction reads r, p, writes p.  The per-shift part (update:
+            // x_s read + write, p_s read; direction: p_s read + write) is added
+            // after the loop from the iterations each shift stayed active.
+            const double vec = (double)n * K * sizeof(T);
+            ctx->pending.push_back({2, e0, e1, vec * 3.0});
+            ctx->pending.push_back({3, e2, e3, vec * 3.0});
         }
         if ((it & 7) == 7 || it + 1 == max_iter) {
             int32_t any = 0;
@@ -837,33 +843,64 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         W[1 + n_inf + i] = v.x[i];
         AW[1 + n_inf + i] = v.ps[i];
     }
-    std::vector<const T*> px, py;
-    for (int a = 0; a < nb; a++)
-        for (int b = 0; b < nb; b++) {
-            px.push_back(W[a]);
-            py.push_back(W[b]);
+    // Gram matrices of (W, A W), Cholesky-QR2: pass 1 basis change X1, then
+    // the Gram matrices of (W X1, A W X1) for the final orthonormalisation
+    auto gram_pairs = [&](const std::vector<const T*>& Wv, const std::vector<const T*>& AWv, double* out) {
+        std::vector<const T*> px, py;
+        for (int a = 0; a < nb; a++)
+            for (int b = 0; b < nb; b++) {
+                px.push_back(Wv[a]);
+                py.push_back(Wv[b]);
+            }
+        for (int a = 0; a < nb; a++)
+            for (int b = 0; b < nb; b++) {
+                px.push_back(Wv[a]);
+                py.push_back(AWv[b]);
+            }
+        const int npairs = (int)px.size();
+        PairDots<T> pd{};
+        pd.n = n;
+        pd.panels = panels;
+        pd.ks = ks;
+        pd.tiles_per_panel = tiles;
+        pd.tiles = P.d_tiles;
+        pd.x = upload(ctx, "rat.px", px);
+        pd.y = upload(ctx, "rat.py", py);
+        pd.part = ws_get_t<double>(ctx, "rat.ppart", (size_t)npairs * panels * tiles * ks);
+        VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, out, st));
+        ctx->launches += 2;
+    };
+    const size_t gsz = (size_t)2 * nb * nb * Kp;
+    double* gram = ws_get_t<double>(ctx, "rat.gram", gsz);
+    double* gram2 = ws_get_t<double>(ctx, "rat.gram2", gsz);
+    double* X1 = ws_get_t<double>(ctx, "rat.X1", (size_t)nb * nb * Kp);
+    gram_pairs(W, AW, gram);
+    VNE_TRY_CUDA(ctx, launch_rational_pass1(gram, nb, Kp, drop, X1, st));
+    T* tw = ws_get_t<T>(ctx, "rat.tw", blk * nb);
+    T* taw = ws_get_t<T>(ctx, "rat.taw", blk * nb);
+    std::vector<const T*> W1(nb), AW1(nb);
+    for (int dir = 0; dir < 2; dir++) {
+        BlockTransform<T> bt{};
+        bt.n = n;
+        bt.K = Kp;
+        bt.nb = nb;
+        bt.tiles_per_panel = tiles;
+        bt.tiles = P.d_tiles;
+        bt.X = X1;
+        T* base = dir == 0 ? tw : taw;
+        for (int i = 0; i < nb; i++) {
+            bt.in[i] = dir == 0 ? W[i] : AW[i];
+            bt.out[i] = base + (size_t)i * blk;
+            (dir == 0 ? W1 : AW1)[i] = bt.out[i];
         }
-    for (int a = 0; a < nb; a++)
-        for (int b = 0; b < nb; b++) {
-            px.push_back(W[a]);
-            py.push_back(AW[b]);
-        }
-    const int npairs = (int)px.size();
-    PairDots<T> pd{};
-    pd.n = n;
-    pd.panels = panels;
-    pd.ks = ks;
-    pd.tiles_per_panel = tiles;
-    pd.tiles = P.d_tiles;
-    pd.x = upload(ctx, "rat.px", px);
-    pd.y = upload(ctx, "rat.py", py);
-    pd.part = ws_get_t<double>(ctx, "rat.ppart", (size_t)npairs * panels * tiles * ks);
-    double* gram = ws_get_t<double>(ctx, "rat.gram", (size_t)npairs * Kp);
-    VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, gram, st));
+        VNE_TRY_CUDA(ctx, launch_block_transform<T>(bt, ks, panels, st));
+    }
+    gram_pairs(W1, AW1, gram2);
     double* dpsi = ws_get_t<double>(ctx, "rat.psi", Kp);
     int* drank = ws_get_t<int>(ctx, "rat.rank", Kp);
-    VNE_TRY_CUDA(ctx, launch_rational_small(gram, gram + (size_t)nb * nb * Kp, nb, Kp, drop, dpsi, drank, st));
-    ctx->launches += 3;
+    // ||c||^2 is the (0,0) entry of the first Gram matrix
+    VNE_TRY_CUDA(ctx, launch_rational_pass2(gram2, gram2 + (size_t)nb * nb * Kp, gram, nb, Kp, drop2, dpsi, drank, st));
+    ctx->launches += 4;
     psi = download(ctx, dpsi, K);
     std::vector<int> hr(Kp), hit((size_t)nshift * Kp);
     std::vector<double> hres((size_t)nshift * Kp);
@@ -871,6 +908,15 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hit.data(), cs.iters, hit.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hres.data(), cs.resid, hres.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ctx->profile) {
+        double shift_iters = 0.0;
+        for (int i = 0; i < nshift; i++)
+            for (int c = 0; c < K; c++) shift_iters += hit[(size_t)i * Kp + c];
+        const double per = (double)n * sizeof(T);
+        ctx->pending.push_back({2, nullptr, nullptr, shift_iters * per * 3.0});
+        ctx->pending.push_back({3, nullptr, nullptr, shift_iters * per * 2.0});
+        ctx_flush_profile(ctx);
+    }
     iters.assign((size_t)nshift * K, 0);
     resid.assign((size_t)nshift * K, 0.0);
     for (int i = 0; i < nshift; i++)
@@ -895,7 +941,10 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
     const double tol = (o && o->cg_tol > 0) ? o->cg_tol : 1e-8;
     const int maxit = (o && o->cg_max_iter > 0) ? o->cg_max_iter : 10000;
     const int n_inf = o ? o->n_inf_poles : 2;
-    const double drop = M->fp64 ? 1e-14 : 1e-6;
+    // pass 1 drops only columns lost to rounding in the Gram matrix; pass 2
+    // (near-orthonormal columns) drops what is dependent at working precision
+    const double drop = M->fp64 ? 1e-15 : 1e-7;
+    const double drop2 = M->fp64 ? 1e-14 : 1e-6;
     psi.assign(ncols, 0.0);
     iters.assign((size_t)nshift * ncols, 0);
     resid.assign((size_t)nshift * ncols, 0.0);
@@ -908,8 +957,8 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
         std::vector<double> bp, br;
         std::vector<int> bi;
         int rmin = 0;
-        rational_block<T>(ctx, *P, s, K, sc.ks, shifts, nshift, n_inf, tol, maxit, M->desing, sc.variant, drop, bp,
-                          bi, br, &rmin);
+        rational_block<T>(ctx, *P, s, K, sc.ks, shifts, nshift, n_inf, tol, maxit, M->desing, sc.variant, drop, drop2,
+                          bp, bi, br, &rmin);
         for (int c = 0; c < K; c++) psi[b0 + c] = bp[c];
         for (int i = 0; i < nshift; i++)
             for (int c = 0; c < K; c++) {
@@ -1610,8 +1659,12 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
         P->node_id = dn;
     }
     problem_upload(ctx, *P);
-    int ks = choose_panel(fp64, &o, ntot);
-    const int variant = (!fp64 && o.step_variant >= 0) ? o.step_variant : 0;
+    // the packed launch walks the segments in order, so the panel that has to
+    // stay L2-resident is one segment's slice: size it by the largest graph
+    int64_t nmax = 0;
+    for (int i = 0; i < count; i++) nmax = std::max<int64_t>(nmax, mats[i]->n);
+    int ks = choose_panel(fp64, &o, nmax);
+    const int variant = fp64 ? 0 : (o.step_variant >= 0 ? o.step_variant : 4);
     StartSource s{};
     s.kind = SRC_RADEMACHER;
     s.seed_mixed = seed_mix(seed);
