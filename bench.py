@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--estimator", choices=["hutchpp", "hutchinson"], default="hutchpp",
                     help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
     ap.add_argument("--vectors", type=int, default=112)
-    ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant (skips the autotuner)")
+    ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant[,interleave] (skips the autotuner)")
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
                     help="c2 = the headline workload; c1/c3/c4/c5 print measurement lines of the other configs")
     ap.add_argument("--requests", type=int, default=400, help="c5: number of queries")
@@ -248,14 +248,16 @@ def run_native(args):
     opt = vne.options(reorth=0)
     seed0 = 1000 * (rank + 1)
     if args.schedule:
-        pnl, itm, var = (int(x) for x in args.schedule.split(","))
-        opt = vne.options(reorth=0, panel=pnl, item_nnz=itm, step_variant=var)
-        tuned_cfg = {"panel": pnl, "item_nnz": itm, "step_variant": var, "source": "--schedule"}
+        vals = [int(x) for x in args.schedule.split(",")] + [0]
+        pnl, itm, var, il = vals[:4]
+        opt = vne.options(reorth=0, panel=pnl, item_nnz=itm, step_variant=var, interleave=il)
+        tuned_cfg = {"panel": pnl, "item_nnz": itm, "step_variant": var, "interleave": il, "source": "--schedule"}
     else:
         # schedule autotuner (once per matrix shape; cached in the context)
         tuned, tune_ms = vne.vne_autotune(ctx, mat, 112 if args.estimator == "hutchpp" else args.vectors, 8)
         tuned_cfg = {"panel": tuned.panel, "item_nnz": tuned.item_nnz, "step_variant": tuned.step_variant,
-                     "ms_per_lanczos_step_112_cols": tune_ms, "source": "vne_autotune"}
+                     "interleave": tuned.interleave, "ms_per_lanczos_step_112_cols": tune_ms,
+                     "source": "vne_autotune"}
 
     def one(seed):
         if args.estimator == "hutchinson":

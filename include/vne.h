@@ -73,9 +73,12 @@ typedef struct vne_options {
     double cg_tol;        /* rational mode: relative residual (default 1e-8) */
     double breakdown_tol; /* Lanczos stops when beta_j <= tol * ||A||_G;
                              0 = default (1e-13 FP64, 1e-10 FP32) */
-    int32_t step_variant; /* SpMM step-kernel variant 0..3 (occupancy /
-                             gathers in flight), -1 = auto */
-    int32_t reserved[7];
+    int32_t step_variant; /* SpMM step-kernel variant 0..5 (occupancy,
+                             gathers in flight, shared-memory staging), -1 = auto */
+    int32_t interleave;   /* 1: launch step and update panel by panel so the
+                             update reads the panel while it is in L2; 0: one
+                             launch each over all panels; -1 = auto */
+    int32_t reserved[6];
 } vne_options;
 
 /* Fill *opt with the defaults described above. */
@@ -228,10 +231,10 @@ vne_status vne_rademacher(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_be
 /* ---- schedule autotuner --------------------------------------------------
  * Time the Lanczos step and update kernels of `mat` on one block of k
  * Rademacher columns for `steps` Lanczos steps under every candidate schedule
- * (panel width, nonzeros per warp work item, step-kernel variant); keep the
- * fastest as the matrix's default for options left at "auto" (panel = 0,
- * item_nnz = 0, step_variant = -1) and report it in *chosen (panel,
- * item_nnz, step_variant) and its time per Lanczos step in *ms_per_step.
+ * (panel width, nonzeros per warp work item, step-kernel variant, per-panel
+ * interleaving); keep the fastest as the matrix's default for options left at
+ * "auto" (panel = 0, item_nnz = 0, step_variant = -1, interleave = -1) and
+ * report it in *chosen and its time per Lanczos step in *ms_per_step.
  * The choice is also cached in the context for matrices created later with
  * the same n, nnz, maximum degree, precision and kind. */
 vne_status vne_autotune(vne_matrix *mat, int32_t k, int32_t steps, vne_options *chosen, double *ms_per_step);

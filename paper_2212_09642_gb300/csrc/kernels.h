@@ -56,6 +56,7 @@ struct StepParams {
     const RowTile* tiles;
     int32_t tiles_per_panel;
     int32_t stage_nnz;  // largest work item in nonzeros (staged variants)
+    int32_t panel_base; // first panel of this launch (per-panel launches)
     int32_t first;   // j == 1: no previous vector
     int32_t renorm;  // update kernel: only recompute the norm of w_next in place
     const T* w_cur;

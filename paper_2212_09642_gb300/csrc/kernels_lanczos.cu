@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     constexpr int G = 32 / LPR;    // row groups per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / LPR, sub = lane % LPR;
-    const int panel = blockIdx.x / p.ctas_per_panel, cta = blockIdx.x % p.ctas_per_panel;
+    const int panel = p.panel_base + blockIdx.x / p.ctas_per_panel, cta = blockIdx.x % p.ctas_per_panel;
     const int seg = p.cta_seg[cta];
     const size_t pofs = (size_t)panel * p.n_total * KS;
     const T* __restrict__ W = p.w_cur + pofs;
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;
     constexpr int RPI = VNE_THREADS / LPR;  // rows per iteration
-    const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    const int panel = p.panel_base + blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
     const int cofs = sub * CPL;

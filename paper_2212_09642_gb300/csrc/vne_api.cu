@@ -80,7 +80,7 @@ struct vne_ctx {
             return std::tie(n, nnz, maxdeg, fp64, pattern) < std::tie(o.n, o.nnz, o.maxdeg, o.fp64, o.pattern);
         }
     };
-    std::map<TuneKey, std::array<int, 3>> tune_cache;
+    std::map<TuneKey, std::array<int, 4>> tune_cache;
 };
 
 struct Problem;
@@ -102,6 +102,7 @@ struct vne_matrix {
     int prob_item_nnz = -1;
     bool tuned = false;             // autotuned schedule (vne_autotune)
     int tuned_panel = 0, tuned_item_nnz = 0, tuned_variant = 0;
+    bool tuned_interleave = false;
     int64_t maxdeg = 0;
 };
 
@@ -327,6 +328,7 @@ int default_item_nnz(const vne_options* o) { return (o && o->item_nnz > 0) ? o->
 
 struct Sched {
     int ks, item_nnz, variant;
+    bool interleave;
 };
 
 int choose_panel(bool fp64, const vne_options* opt, int64_t n);
@@ -339,6 +341,7 @@ Sched resolve_sched(const vne_matrix* M, const vne_options* o) {
     s.item_nnz = (o && o->item_nnz > 0) ? o->item_nnz : (M->tuned ? M->tuned_item_nnz : 256);
     s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 4);
     if (M->fp64) s.variant = 0;
+    s.interleave = (o && o->interleave >= 0) ? (o->interleave != 0) : (M->tuned ? M->tuned_interleave : false);
     return s;
 }
 
@@ -396,7 +399,8 @@ struct BlockOut {
 
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
-               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0) {
+               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
+               bool interleave = false) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
     const int Kp = panels * ks;
@@ -500,13 +504,30 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             e0 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
         }
-        VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
-        if (ctx->profile) {
-            e1 = ctx_event(ctx);
-            VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+        if (interleave && !reorth) {
+            // per-panel launches, step then update of the same panel: the
+            // update finds u and w_j of that panel still in L2
+            for (int pn = 0; pn < panels; pn++) {
+                p.panel_base = pn;
+                VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, 1, P.valued, variant, st));
+                VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, 1, st));
+            }
+            p.panel_base = 0;
+            ctx->launches += 2 * panels;
+            if (ctx->profile) {
+                e1 = ctx_event(ctx);
+                VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+            }
+        } else {
+            p.panel_base = 0;
+            VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
+            if (ctx->profile) {
+                e1 = ctx_event(ctx);
+                VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+            }
+            VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
+            ctx->launches += 2;
         }
-        VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
-        ctx->launches += 2;
         if (ctx->profile) {
             e2 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e2, st));
@@ -517,8 +538,13 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             double vec = (double)P.n_total * ks * es;
             double step_bytes = panels * (csr + vec * (j > 1 ? 3.0 : 2.0));
             double upd_bytes = panels * vec * 3.0;
-            ctx->pending.push_back({0, e0, e1, step_bytes});
-            ctx->pending.push_back({1, e1, e2, upd_bytes});
+            if (interleave && !reorth) {
+                // one timed span covers the interleaved step and update launches
+                ctx->pending.push_back({0, e0, e1, step_bytes + upd_bytes});
+            } else {
+                ctx->pending.push_back({0, e0, e1, step_bytes});
+                ctx->pending.push_back({1, e1, e2, upd_bytes});
+            }
         }
         if (reorth && j < m + 1) {
             ReorthParams<T> rp{};
@@ -616,7 +642,7 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
         if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
         if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
         BlockOut out;
-        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
+        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant, sc.interleave);
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi.begin() + b0);
     }
@@ -941,10 +967,12 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
     const double tol = (o && o->cg_tol > 0) ? o->cg_tol : 1e-8;
     const int maxit = (o && o->cg_max_iter > 0) ? o->cg_max_iter : 10000;
     const int n_inf = o ? o->n_inf_poles : 2;
-    // pass 1 drops only columns lost to rounding in the Gram matrix; pass 2
-    // (near-orthonormal columns) drops what is dependent at working precision
-    const double drop = M->fp64 ? 1e-15 : 1e-7;
-    const double drop2 = M->fp64 ? 1e-14 : 1e-6;
+    // a pole direction whose squared relative remainder after orthogonalising
+    // against the earlier ones is below the threshold is dependent (the oracle
+    // uses the same rule, remainder 1e-6 of the norm); both Cholesky-QR passes
+    // apply it, the first also keeps rounding noise of the Gram matrix out
+    const double drop = M->fp64 ? 1e-12 : 1e-10;
+    const double drop2 = drop;
     psi.assign(ncols, 0.0);
     iters.assign((size_t)nshift * ncols, 0);
     resid.assign((size_t)nshift * ncols, 0.0);
@@ -1010,6 +1038,7 @@ extern "C" void vne_options_default(vne_options* o) {
     o->cg_max_iter = 10000;
     o->cg_tol = 1e-8;
     o->step_variant = -1;
+    o->interleave = -1;
 }
 
 extern "C" const char* vne_version(void) { return "vne 0.1 (sm_103a)"; }
@@ -1190,6 +1219,7 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
             M->tuned_panel = it->second[0];
             M->tuned_item_nnz = it->second[1];
             M->tuned_variant = it->second[2];
+            M->tuned_interleave = it->second[3] != 0;
         }
     }
     *out = M.release();
@@ -1270,10 +1300,12 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
         BlockOut out;
         if (M->fp64) {
             check_ks<double>(ctx, ks);
-            run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
+            run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant,
+                              sc.interleave);
         } else {
             check_ks<float>(ctx, ks);
-            run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant);
+            run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant,
+                             sc.interleave);
         }
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi + b0);
@@ -1345,7 +1377,8 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     s.col_begin = 0;
     s.ncols = Nr;
     BlockOut sk;
-    run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant);
+    run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant,
+                 sc.interleave);
     const int Kp = sk.Kp;
     double* zvec = ws_get_t<double>(ctx, "zvec", (size_t)m * Kp);
     VNE_TRY_CUDA(ctx, launch_tridiag_fvec(sk.alpha, sk.beta, sk.scale, Kp, m, Kp, zvec, st));
@@ -1432,7 +1465,8 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
         sq.kind = SRC_PANEL;
         sq.ncols = Kp + Kg;
         BlockOut qo;
-        run_block<T>(ctx, *P, sq, QG, Kp + Kg, ks, m, want_reorth(M, o), false, M->desing, "q", qo, sc.variant);
+        run_block<T>(ctx, *P, sq, QG, Kp + Kg, ks, m, want_reorth(M, o), false, M->desing, "q", qo, sc.variant,
+                     sc.interleave);
         std::vector<double> h = download(ctx, qo.psi, Kp + Kg);
         for (int c = 0; c < r; c++) low += h[c];
         for (int c = 0; c < NH; c++) resid += h[Kp + c];
@@ -1732,17 +1766,19 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
     const int items[4] = {128, 256, 512, 1024};
     const int nvar = M->fp64 ? 1 : kStepVariants;
     double best = 1e300;
-    int bk = 0, bi = 0, bv = 0;
+    int bk = 0, bi = 0, bv = 0, bil = 0;
     const bool was_tuned = M->tuned;
     M->tuned = false;
     for (int pi = 0; pi < 3; pi++)
         for (int ii = 0; ii < 4; ii++)
-            for (int v = 0; v < nvar; v++) {
+            for (int v = 0; v < nvar; v++)
+            for (int il = 0; il < 2; il++) {
                 vne_options o;
                 vne_options_default(&o);
                 o.panel = M->fp64 ? panels_d[pi] : panels_f[pi];
                 o.item_nnz = items[ii];
                 o.step_variant = v;
+                o.interleave = il;
                 o.reorth = 0;
                 Problem* P = matrix_problem(M, &o);
                 StartSource s{};
@@ -1753,8 +1789,8 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
                 for (int rep = 0; rep < 2; rep++) {
                     BlockOut out;
                     ctx->time_steps = true;
-                    if (M->fp64) run_block<double>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v);
-                    else run_block<float>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v);
+                    if (M->fp64) run_block<double>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il);
+                    else run_block<float>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il);
                     ctx->time_steps = false;
                     download(ctx, out.psi, 1);
                     float ms = 0.f;
@@ -1766,6 +1802,7 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
                     bk = o.panel;
                     bi = items[ii];
                     bv = v;
+                    bil = il;
                 }
             }
     // release the tuning block's workspace
@@ -1782,12 +1819,14 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
     M->tuned_panel = bk;
     M->tuned_item_nnz = bi;
     M->tuned_variant = bv;
-    ctx->tune_cache[vne_ctx::TuneKey{M->n, M->nnz, M->maxdeg, (int)M->fp64, (int)M->pattern}] = {bk, bi, bv};
+    M->tuned_interleave = bil != 0;
+    ctx->tune_cache[vne_ctx::TuneKey{M->n, M->nnz, M->maxdeg, (int)M->fp64, (int)M->pattern}] = {bk, bi, bv, bil};
     if (chosen) {
         vne_options_default(chosen);
         chosen->panel = bk;
         chosen->item_nnz = bi;
         chosen->step_variant = bv;
+        chosen->interleave = bil;
     }
     if (ms_per_step) *ms_per_step = best / steps;
     VNE_API_END(ctx)

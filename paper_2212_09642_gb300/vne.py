@@ -49,7 +49,7 @@ class vne_options(ctypes.Structure):
     _fields_ = [("reorth", ctypes.c_int32), ("block", ctypes.c_int32), ("panel", ctypes.c_int32),
                 ("item_nnz", ctypes.c_int32), ("n_inf_poles", ctypes.c_int32), ("cg_max_iter", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
-                ("step_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
