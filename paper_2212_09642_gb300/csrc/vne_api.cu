@@ -968,10 +968,12 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
     const int maxit = (o && o->cg_max_iter > 0) ? o->cg_max_iter : 10000;
     const int n_inf = o ? o->n_inf_poles : 2;
     // a pole direction whose squared relative remainder after orthogonalising
-    // against the earlier ones is below the threshold is dependent (the oracle
-    // uses the same rule, remainder 1e-6 of the norm); both Cholesky-QR passes
-    // apply it, the first also keeps rounding noise of the Gram matrix out
-    const double drop = M->fp64 ? 1e-12 : 1e-10;
+    // against the earlier ones is below the threshold is dependent: FP64 uses
+    // the oracle's rule (remainder 1e-6 of the norm); FP32 vectors stop at a
+    // remainder of 1e-3, because a kept direction's A-image carries the
+    // vectors' rounding amplified by 1 / remainder.  Both Cholesky-QR passes
+    // apply the rule.
+    const double drop = M->fp64 ? 1e-12 : 1e-6;
     const double drop2 = drop;
     psi.assign(ncols, 0.0);
     iters.assign((size_t)nshift * ncols, 0);
