@@ -73,8 +73,9 @@ typedef struct vne_options {
     double cg_tol;        /* rational mode: relative residual (default 1e-8) */
     double breakdown_tol; /* Lanczos stops when beta_j <= tol * ||A||_G;
                              0 = default (1e-13 FP64, 1e-10 FP32) */
-    int32_t step_variant; /* SpMM step-kernel variant 0..5 (occupancy,
-                             gathers in flight, shared-memory staging), -1 = auto */
+    int32_t step_variant; /* SpMM step-kernel variant 0..7 (occupancy,
+                             gathers in flight, shared-memory staging, L2
+                             cache policy of the gathers), -1 = auto */
     int32_t interleave;   /* 1: launch step and update panel by panel so the
                              update reads the panel while it is in L2; 0: one
                              launch each over all panels; -1 = auto */

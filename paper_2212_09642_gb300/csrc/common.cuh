@@ -52,6 +52,47 @@ __device__ __forceinline__ void store_lane_stream(T* p, const T (&v)[LaneVec<T>:
     __stcs(reinterpret_cast<V*>(p), x);
 }
 
+// Gathered loads with an L2 evict_last cache policy (HINT 1) and, for
+// HINT 2, without allocating in L1: the gathered panel is reused by every
+// row that has a neighbour in it, the streams around it are read once.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+template <int HINT>
+__device__ __forceinline__ void load_lane_hint(const float* p, float (&v)[4], uint64_t pol) {
+    if (HINT == 0) {
+        float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if (HINT == 1) {
+        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                     : "l"(p), "l"(pol));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                     : "l"(p), "l"(pol));
+    }
+}
+
+template <int HINT>
+__device__ __forceinline__ void load_lane_hint(const double* p, double (&v)[2], uint64_t pol) {
+    if (HINT == 0) {
+        double2 x = *reinterpret_cast<const double2*>(p);
+        v[0] = x.x; v[1] = x.y;
+    } else if (HINT == 1) {
+        asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                     : "=d"(v[0]), "=d"(v[1])
+                     : "l"(p), "l"(pol));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                     : "=d"(v[0]), "=d"(v[1])
+                     : "l"(p), "l"(pol));
+    }
+}
+
 // L2-coherent load of a value another CTA wrote in this kernel (bypasses L1).
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }

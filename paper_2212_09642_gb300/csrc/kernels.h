@@ -104,7 +104,7 @@ struct RecoverParams {
 template <typename T> cudaError_t launch_start(const StartParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T>
 cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, int variant, cudaStream_t);
-constexpr int kStepVariants = 6;
+constexpr int kStepVariants = 8;
 template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
 template <typename T> cudaError_t launch_recover(const RecoverParams<T>&, int ks, int panels, cudaStream_t);

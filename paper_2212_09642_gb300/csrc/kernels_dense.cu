@@ -81,6 +81,88 @@ __host__ __device__ bool symtri_qr(double* d, double* e, int n, Rot rot) {
     return true;
 }
 
+// Implicit QR with `nr` rows of the eigenvector matrix tracked alongside (the
+// quadrature needs the first row only; f(T) e1 needs all rows, spread over
+// the lanes of a warp).  The sweep's running values (d_k, e_k and each
+// tracked row's entry k) are carried in registers, so the dependent chain of
+// one rotation touches no memory; old values of the next position are loaded
+// ahead of their use.
+template <int R>
+__host__ __device__ inline bool symtri_qr_rows(double* d, double* e, int n, double* const* zr, int nr) {
+    const double eps = DBL_EPSILON;
+    int hi = n - 1;
+    int iters = 0;
+    const int max_iters = 40 * n + 40;
+    while (hi > 0) {
+        if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+            e[hi - 1] = 0.0;
+            hi--;
+            continue;
+        }
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) lo--;
+        if (lo > 0) e[lo - 1] = 0.0;
+        if (++iters > max_iters) return false;
+        const double delta = 0.5 * (d[hi - 1] - d[hi]);
+        const double b2 = e[hi - 1] * e[hi - 1];
+        const double den = delta + copysign(sqrt(delta * delta + b2), delta == 0.0 ? 1.0 : delta);
+        const double mu = d[hi] - b2 / den;
+        double dk = d[lo], ek = e[lo];
+        double zk[R];
+#pragma unroll
+        for (int q = 0; q < R; q++) zk[q] = (q < nr) ? zr[q][lo] : 0.0;
+        double x = dk - mu, y = ek;
+        for (int k = lo; k < hi; k++) {
+            const double dk1 = d[k + 1];
+            const double ek1 = (k + 1 < hi) ? e[k + 1] : 0.0;
+            double zk1[R];
+#pragma unroll
+            for (int q = 0; q < R; q++) zk1[q] = (q < nr) ? zr[q][k + 1] : 0.0;
+            const double r2 = x * x + y * y;
+            double c, s, r;
+            if (r2 == 0.0) {
+                c = 1.0;
+                s = 0.0;
+                r = 0.0;
+            } else {
+                const double inv = rsqrt(r2);
+                c = x * inv;
+                s = -y * inv;
+                r = r2 * inv;
+            }
+            if (k > lo) e[k - 1] = r;
+            const double cs = c * s, c2 = c * c, s2 = s * s;
+            const double a = dk, b = ek;
+            d[k] = a * c2 - 2.0 * b * cs + dk1 * s2;
+            const double ndk1 = a * s2 + 2.0 * b * cs + dk1 * c2;
+            const double nek = (a - dk1) * cs + b * (c2 - s2);
+#pragma unroll
+            for (int q = 0; q < R; q++) {
+                if (q < nr) zr[q][k] = c * zk[q] - s * zk1[q];
+                zk[q] = s * zk[q] + c * zk1[q];
+            }
+            dk = ndk1;
+            if (k < hi - 1) {
+                x = nek;
+                y = -s * ek1;
+                ek = c * ek1;
+            } else {
+                e[k] = nek;
+            }
+        }
+        d[hi] = dk;
+#pragma unroll
+        for (int q = 0; q < R; q++)
+            if (q < nr) zr[q][hi] = zk[q];
+    }
+    return true;
+}
+
+__host__ __device__ inline bool symtri_qr_first_row(double* d, double* e, double* z, int n) {
+    double* rows[1] = {z};
+    return symtri_qr_rows<1>(d, e, n, rows, 1);
+}
+
 template <int MAXM>
 __global__ void k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
                                const double* __restrict__ norm2, const double* __restrict__ scale, int count,
@@ -102,18 +184,17 @@ __global__ void k_tridiag_quad(const double* __restrict__ alpha, const double* _
         }
     }
     z[0] = 1.0;
-    bool ok = symtri_qr(d, e, n, [&](int k, double cr, double sr) {
-        double a = z[k], b = z[k + 1];
-        z[k] = cr * a - sr * b;
-        z[k + 1] = sr * a + cr * b;
-    });
+    bool ok = symtri_qr_first_row(d, e, z, n);
     double sc = scale[c];
     double s = 0.0;
     for (int k = 0; k < n; k++) s += z[k] * z[k] * f_entropy(sc * d[k]);
     psi[c] = ok ? norm2[c] * s : nan("");
 }
 
-// warp per column; dynamic smem: Z [m][m] (row-major) per warp (1 warp / CTA)
+// warp per column; dynamic smem: Z [m][m] (row-major) per warp (1 warp / CTA).
+// Every lane runs the scalar recurrence on its own copies (uniform control
+// flow) and rotates the rows of Z it owns (rows lane, lane + 32, ...).
+template <int R>
 __global__ void k_tridiag_fvec(const double* __restrict__ alpha, const double* __restrict__ beta,
                                const double* __restrict__ scale, int count, int m, int ld,
                                double* __restrict__ zvec) {
@@ -136,21 +217,20 @@ __global__ void k_tridiag_fvec(const double* __restrict__ alpha, const double* _
             n = j + 1;
             break;
         }
-    // every lane runs the scalar recurrence on private copies (uniform control
-    // flow), and applies each rotation to the rows of Z it owns
     double dl[128], el[128];
     for (int j = 0; j < n; j++) {
         dl[j] = d[j];
         el[j] = e[j];
     }
+    double* rows[R];
+    int nr = 0;
+    for (int q = 0; q < R; q++) {
+        const int row = lane + 32 * q;
+        rows[q] = Z + (size_t)(row < n ? row : 0) * m;
+        if (row < n) nr = q + 1;
+    }
     __syncwarp();
-    bool ok = symtri_qr(dl, el, n, [&](int k, double cr, double sr) {
-        for (int row = lane; row < n; row += 32) {
-            double a = Z[row * m + k], b = Z[row * m + k + 1];
-            Z[row * m + k] = cr * a - sr * b;
-            Z[row * m + k + 1] = sr * a + cr * b;
-        }
-    });
+    bool ok = symtri_qr_rows<R>(dl, el, n, rows, nr);
     __syncwarp();
     double sc = scale[c];
     for (int row = lane; row < m; row += 32) {
@@ -186,9 +266,15 @@ cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const d
     if (count <= 0) return cudaSuccess;
     if (m > 128) return cudaErrorInvalidValue;
     size_t smem = ((size_t)m * m + 2 * m) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tridiag_fvec<<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
+    if (m <= 64) {
+        cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tridiag_fvec<2><<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tridiag_fvec<4><<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
+    }
     return cudaGetLastError();
 }
 

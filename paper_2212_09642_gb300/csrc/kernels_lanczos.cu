@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
 // with coalesced loads first, so each gather waits on a shared-memory read
 // instead of a dependent global index load (dynamic smem: item_nnz ints per
 // warp + 65 row offsets per warp).
-template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE>
+template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE, int HINT = 0>
 __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;  // lanes per row
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     T dot[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; q++) dot[q] = (T)0;
+    const uint64_t pol = HINT ? policy_evict_last() : 0ull;
 
     auto epilogue = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL]) {
         T x[CPL], xp[CPL], uu[CPL];
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
                 for (int u = 0; u < UNR; u++) cc[u] = colidx(k + u);
                 T a[UNR][CPL];
 #pragma unroll
-                for (int u = 0; u < UNR; u++) load_lane(W + (size_t)cc[u] * KS + cofs, a[u]);
+                for (int u = 0; u < UNR; u++) load_lane_hint<HINT>(W + (size_t)cc[u] * KS + cofs, a[u], pol);
                 if (VALUED) {
                     T v[UNR];
 #pragma unroll
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
             for (; k < ke; k++) {
                 int c0 = colidx(k);
                 T a0[CPL];
-                load_lane(W + (size_t)c0 * KS + cofs, a0);
+                load_lane_hint<HINT>(W + (size_t)c0 * KS + cofs, a0, pol);
                 T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
 #pragma unroll
                 for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
         for (int k = it.nnz_begin + g; k < it.nnz_end; k += G) {
             int c0 = colidx(k);
             T a0[CPL];
-            load_lane(W + (size_t)c0 * KS + cofs, a0);
+            load_lane_hint<HINT>(W + (size_t)c0 * KS + cofs, a0, pol);
             T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
 #pragma unroll
             for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
@@ -616,7 +617,7 @@ cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream
     return cudaGetLastError();
 }
 
-// Step-kernel variants: {MINB, UNR, STREAM, STAGE}.  FP64 uses variant 0 only.
+// Step-kernel variants: {MINB, UNR, STREAM, STAGE, HINT}.  FP64 uses variant 0 only.
 #define VNE_STEP_VARIANTS(T, KS, VALUED, v, st, grid, p, smem)                                                   \
     switch (sizeof(T) == 8 ? 0 : (v)) {                                                                          \
         case 1: k_step<T, KS, VALUED, 6, 4, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
@@ -624,6 +625,8 @@ cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream
         case 3: k_step<T, KS, VALUED, 8, 4, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
         case 4: k_step<T, KS, VALUED, 6, 4, true, true><<<grid, VNE_THREADS, smem, st>>>(p); break;             \
         case 5: k_step<T, KS, VALUED, 4, 8, true, true><<<grid, VNE_THREADS, smem, st>>>(p); break;             \
+        case 6: k_step<T, KS, VALUED, 6, 4, true, true, 1><<<grid, VNE_THREADS, smem, st>>>(p); break;          \
+        case 7: k_step<T, KS, VALUED, 6, 4, true, true, 2><<<grid, VNE_THREADS, smem, st>>>(p); break;          \
         default: k_step<T, KS, VALUED, 4, 4, false, false><<<grid, VNE_THREADS, 0, st>>>(p); break;             \
     }
 
