@@ -79,7 +79,17 @@ typedef struct vne_options {
     int32_t interleave;   /* 1: launch step and update panel by panel so the
                              update reads the panel while it is in L2; 0: one
                              launch each over all panels; -1 = auto */
-    int32_t reserved[6];
+    int32_t graphs;       /* 1: replay the Lanczos step loop of a block as a
+                             CUDA graph, captured on the second call with the
+                             same shape and buffers and cached in the context;
+                             0: launch every kernel directly; -1 = auto (1).
+                             Calls with profiling on launch directly. */
+    int32_t probe_offset; /* Hutchinson: index of the first probe column of
+                             the seeded Rademacher stream (probes
+                             probe_offset .. probe_offset + N - 1), so that
+                             ranks splitting [0, N) into ranges evaluate
+                             exactly the probes of one single run; 0 default */
+    int32_t reserved[4];
 } vne_options;
 
 /* Fill *opt with the defaults described above. */
@@ -107,6 +117,11 @@ const char *vne_version(void);
  * kernel_stats must hold 12 doubles (or be NULL). */
 vne_status vne_ctx_profile(vne_ctx *ctx, int32_t enable);
 vne_status vne_ctx_stats(const vne_ctx *ctx, int64_t *launches, double *kernel_stats);
+/* CUDA-graph use of the context since its creation: step loops captured into
+ * a new graph (*captured) and step loops replayed from a cached graph
+ * (*replayed, including the replay right after a capture).  Either pointer
+ * may be NULL.  EINVAL for a null context. */
+vne_status vne_ctx_graph_stats(const vne_ctx *ctx, int64_t *captured, int64_t *replayed);
 
 /* ---- density matrix (Section 2, eq. graph_laplacian) ------------------ */
 /* Copy a symmetric CSR matrix to the device.

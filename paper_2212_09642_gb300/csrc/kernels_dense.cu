@@ -245,14 +245,14 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    // columns per CTA (one warp per CTA): fewer columns per warp spread the
-    // FP64 work over more SMs when there are few columns
-    static int cpw = -1;
-    if (cpw < 0) {
-        const char* e = getenv("VNE_TRIDIAG_COLS_PER_WARP");
-        cpw = e ? atoi(e) : 32;
-        if (cpw < 1 || cpw > 32) cpw = 32;
-    }
+    // columns per CTA (one warp per CTA).  The FP64 pipe of an SM retires a
+    // 32-lane FP64 instruction over many cycles, so the columns are spread
+    // over all SMs first: ceil(count / SMs) columns per warp, at most 32.
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    int cpw = (count + sms - 1) / sms;
+    if (cpw > 32) cpw = 32;
     dim3 block(32), grid((count + cpw - 1) / cpw);
     if (m <= 32) k_tridiag_quad<32><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
     else if (m <= 64) k_tridiag_quad<64><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
@@ -346,6 +346,122 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, c
         }
 }
 
+// Tensor-core Gram C = X^T Y for FP32 blocks (kx, ky <= 128): warp-level
+// MMA m16n8k8 on TF32 operands with a three-product split (x = x_hi + x_lo,
+// both TF32; x^T y ~ hi.hi + hi.lo + lo.hi), which keeps the products at
+// FP32 accuracy.  The contraction reads each row of X and Y once (about 50
+// flops per byte for 112 columns), so it is bound by HBM, not by the tensor
+// pipe.  CTA: 8 warps in a 4 x 2 grid, each owning a 32 x 64 block of the
+// 128 x 128 output; rows are streamed in 32-row slabs through padded shared
+// memory; accumulation in FP32 over the CTA's rows, FP64 across CTAs.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int KS>
+__global__ void __launch_bounds__(256, 2) k_gram_tc(const float* __restrict__ X, int kx, const float* __restrict__ Y,
+                                                    int ky, int n, int rows_per_chunk, double* __restrict__ part) {
+    constexpr int LD = 136;  // padded row (128 + 8 floats): conflict-free fragment loads
+    constexpr int SLAB = 32;
+    constexpr int V_PER_ROW = KS / 4;  // float4 per row of one panel
+    __shared__ __align__(16) float Xs[SLAB][LD];
+    __shared__ __align__(16) float Ys[SLAB][LD];
+    const int chunk = blockIdx.x;
+    const int r_begin = chunk * rows_per_chunk;
+    const int r_end = min(n, r_begin + rows_per_chunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp >> 1, wn = warp & 1;  // warp block: rows wm*32.., cols wn*64..
+    const int g = lane >> 2, tq = lane & 3;
+    const int px = kx / KS, py = ky / KS;     // panels of X and Y
+    float acc[2][8][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+    // zero the columns no panel covers (they stay zero for the whole kernel)
+    for (int idx = threadIdx.x; idx < SLAB * 128; idx += 256) {
+        const int rl = idx >> 7, cl = idx & 127;
+        if (cl >= kx) Xs[rl][cl] = 0.f;
+        if (cl >= ky) Ys[rl][cl] = 0.f;
+    }
+    for (int rt = r_begin; rt < r_end; rt += SLAB) {
+        // slab of SLAB rows: panel p of a block holds these rows contiguously
+        // (SLAB * KS floats), so consecutive threads read consecutive float4s
+        const int nx = px * SLAB * V_PER_ROW, ny = py * SLAB * V_PER_ROW;
+        for (int idx = threadIdx.x; idx < nx + ny; idx += 256) {
+            const bool isx = idx < nx;
+            const int e = isx ? idx : idx - nx;
+            const int p = e / (SLAB * V_PER_ROW), rem = e % (SLAB * V_PER_ROW);
+            const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
+            const int r = rt + rl;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < r_end) {
+                const float* src = (isx ? X : Y) + (size_t)p * n * KS + (size_t)r * KS + c;
+                v = __ldcs(reinterpret_cast<const float4*>(src));
+            }
+            float* dst = isx ? &Xs[rl][p * KS + c] : &Ys[rl][p * KS + c];
+            *reinterpret_cast<float4*>(dst) = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k0 = 0; k0 < SLAB; k0 += 8) {
+            // A = X^T (M = output rows, K = slab rows), two 16-row tiles per warp
+            uint32_t ahi[2][4], alo[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int m0 = wm * 32 + i * 16;
+                const float vv[4] = {Xs[k0 + tq][m0 + g], Xs[k0 + tq][m0 + g + 8], Xs[k0 + tq + 4][m0 + g],
+                                     Xs[k0 + tq + 4][m0 + g + 8]};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    ahi[i][q] = to_tf32(vv[q]);
+                    alo[i][q] = to_tf32(vv[q] - __uint_as_float(ahi[i][q]));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int n0 = wn * 64 + j * 8;
+                const float w0 = Ys[k0 + tq][n0 + g], w1 = Ys[k0 + tq + 4][n0 + g];
+                uint32_t bhi[2], blo[2];
+                bhi[0] = to_tf32(w0);
+                bhi[1] = to_tf32(w1);
+                blo[0] = to_tf32(w0 - __uint_as_float(bhi[0]));
+                blo[1] = to_tf32(w1 - __uint_as_float(bhi[1]));
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    mma_tf32(acc[i][j], alo[i], bhi);
+                    mma_tf32(acc[i][j], ahi[i], blo);
+                    mma_tf32(acc[i][j], ahi[i], bhi);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // fragment (row g / g+8, col 2tq / 2tq+1) -> partial Gram of this chunk
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int row = wm * 32 + i * 16 + g + ((q & 2) ? 8 : 0);
+                const int col = wn * 64 + j * 8 + 2 * tq + (q & 1);
+                if (row < kx && col < ky) part[(size_t)chunk * kx * ky + (size_t)row * ky + col] = (double)acc[i][j][q];
+            }
+}
+
 __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int total, double* __restrict__ C) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -358,6 +474,22 @@ template <typename T>
 cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks, double* C,
                         cudaStream_t st) {
     if (kx <= 0 || ky <= 0) return cudaSuccess;
+    if (sizeof(T) == 4 && kx <= 128 && ky <= 128) {
+        // tensor-core path (FP32 data)
+        int rpc = (n + nchunks - 1) / nchunks;
+        rpc = ((rpc + 31) / 32) * 32;
+        int chunks = rpc > 0 ? (n + rpc - 1) / rpc : 1;
+        if (chunks < 1) chunks = 1;
+        const float* Xf = reinterpret_cast<const float*>(X);
+        const float* Yf = reinterpret_cast<const float*>(Y);
+        if (ks == 8) k_gram_tc<8><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
+        else if (ks == 16) k_gram_tc<16><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
+        else if (ks == 32) k_gram_tc<32><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
+        else return cudaErrorInvalidValue;
+        int total = kx * ky;
+        k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
+        return cudaGetLastError();
+    }
     int tiles_x = (kx + 63) / 64, tiles_y = (ky + 63) / 64;
     int rpc = (n + nchunks - 1) / nchunks;
     rpc = ((rpc + 63) / 64) * 64;

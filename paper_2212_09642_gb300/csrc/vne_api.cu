@@ -81,6 +81,16 @@ struct vne_ctx {
         }
     };
     std::map<TuneKey, std::array<int, 4>> tune_cache;
+    // CUDA graphs of step loops, keyed by the launch parameters of the loop;
+    // a loop is captured the second time its key is seen
+    struct LoopGraph {
+        cudaGraphExec_t exec;
+        int64_t kernels;  // kernel launches the graph holds
+    };
+    std::map<std::string, LoopGraph> graphs;
+    std::map<std::string, int> graph_seen;
+    cudaStream_t cap_stream = nullptr;  // private stream the captures run on
+    int64_t graphs_captured = 0, graphs_replayed = 0;
 };
 
 struct Problem;
@@ -329,6 +339,7 @@ int default_item_nnz(const vne_options* o) { return (o && o->item_nnz > 0) ? o->
 struct Sched {
     int ks, item_nnz, variant;
     bool interleave;
+    bool graph;
 };
 
 int choose_panel(bool fp64, const vne_options* opt, int64_t n);
@@ -342,6 +353,7 @@ Sched resolve_sched(const vne_matrix* M, const vne_options* o) {
     s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 4);
     if (M->fp64) s.variant = 0;
     s.interleave = (o && o->interleave >= 0) ? (o->interleave != 0) : (M->tuned ? M->tuned_interleave : false);
+    s.graph = !(o && o->graphs == 0);
     return s;
 }
 
@@ -400,7 +412,7 @@ struct BlockOut {
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
                bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
-               bool interleave = false) {
+               bool interleave = false, bool graph = true) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
     const int Kp = panels * ks;
@@ -457,7 +469,8 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     VNE_TRY_CUDA(ctx, launch_start<T>(sp, ks, panels, st));
     ctx->launches += desing ? 2 : 1;
 
-    StepParams<T> p{};
+    StepParams<T> p;
+    memset(&p, 0, sizeof(p));  // the bytes of p are part of the graph key
     p.rowptr = P.rowptr;
     p.col = P.col;
     p.vals = (const T*)P.vals;
@@ -486,91 +499,149 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
         rcoef = ws_get_t<double>(ctx, "reorth.coef", (size_t)m * Kp);
         rpart = ws_get_t<double>(ctx, "reorth.part", (size_t)panels * m * tiles * ks);
     }
-    if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[0], st));
-    for (int j = 1; j <= m; j++) {
-        p.first = (j == 1);
-        p.renorm = 0;
-        p.w_cur = slot(j);
-        p.w_prev = (j > 1) ? slot(j - 1) : slot(j);
-        p.w_next = slot(j + 1);
-        p.sig_cur = sigma + (size_t)(j - 1) * SK;
-        p.sig_prev = (j > 1) ? sigma + (size_t)(j - 2) * SK : sigma;
-        p.beta_prev = (j > 1) ? beta + (size_t)(j - 2) * SK : beta;
-        p.alpha = alpha + (size_t)(j - 1) * SK;
-        p.beta = beta + (size_t)(j - 1) * SK;
-        p.sig_next = sigma + (size_t)j * SK;
-        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-        if (ctx->profile) {
-            e0 = ctx_event(ctx);
-            VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
-        }
-        if (interleave && !reorth) {
-            // per-panel launches, step then update of the same panel: the
-            // update finds u and w_j of that panel still in L2
-            for (int pn = 0; pn < panels; pn++) {
-                p.panel_base = pn;
-                VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, 1, P.valued, variant, st));
-                VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, 1, st));
+    // The step loop, enqueued on stream `s`; `prof` brackets the launches
+    // with events (never while capturing).
+    auto enqueue_loop = [&](cudaStream_t s, bool prof) {
+        for (int j = 1; j <= m; j++) {
+            p.first = (j == 1);
+            p.renorm = 0;
+            p.w_cur = slot(j);
+            p.w_prev = (j > 1) ? slot(j - 1) : slot(j);
+            p.w_next = slot(j + 1);
+            p.sig_cur = sigma + (size_t)(j - 1) * SK;
+            p.sig_prev = (j > 1) ? sigma + (size_t)(j - 2) * SK : sigma;
+            p.beta_prev = (j > 1) ? beta + (size_t)(j - 2) * SK : beta;
+            p.alpha = alpha + (size_t)(j - 1) * SK;
+            p.beta = beta + (size_t)(j - 1) * SK;
+            p.sig_next = sigma + (size_t)j * SK;
+            cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+            if (prof) {
+                e0 = ctx_event(ctx);
+                VNE_TRY_CUDA(ctx, cudaEventRecord(e0, s));
             }
-            p.panel_base = 0;
-            ctx->launches += 2 * panels;
-            if (ctx->profile) {
-                e1 = ctx_event(ctx);
-                VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
-            }
-        } else {
-            p.panel_base = 0;
-            VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, st));
-            if (ctx->profile) {
-                e1 = ctx_event(ctx);
-                VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
-            }
-            VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
-            ctx->launches += 2;
-        }
-        if (ctx->profile) {
-            e2 = ctx_event(ctx);
-            VNE_TRY_CUDA(ctx, cudaEventRecord(e2, st));
-            // algorithmic bytes: CSR structure (+ values) once per panel, the
-            // gathered block w_j once, w_{j-1} (j > 1) and u once each
-            const double es = sizeof(T);
-            double csr = 4.0 * (P.n_total + 1) + (double)nnz_total * (4.0 + (P.valued ? es : 0.0));
-            double vec = (double)P.n_total * ks * es;
-            double step_bytes = panels * (csr + vec * (j > 1 ? 3.0 : 2.0));
-            double upd_bytes = panels * vec * 3.0;
             if (interleave && !reorth) {
-                // one timed span covers the interleaved step and update launches
-                ctx->pending.push_back({0, e0, e1, step_bytes + upd_bytes});
+                // per-panel launches, step then update of the same panel: the
+                // update finds u and w_j of that panel still in L2
+                for (int pn = 0; pn < panels; pn++) {
+                    p.panel_base = pn;
+                    VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, 1, P.valued, variant, s));
+                    VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, 1, s));
+                }
+                p.panel_base = 0;
+                ctx->launches += 2 * panels;
+                if (prof) {
+                    e1 = ctx_event(ctx);
+                    VNE_TRY_CUDA(ctx, cudaEventRecord(e1, s));
+                }
             } else {
-                ctx->pending.push_back({0, e0, e1, step_bytes});
-                ctx->pending.push_back({1, e1, e2, upd_bytes});
+                p.panel_base = 0;
+                VNE_TRY_CUDA(ctx, launch_step<T>(p, ks, panels, P.valued, variant, s));
+                if (prof) {
+                    e1 = ctx_event(ctx);
+                    VNE_TRY_CUDA(ctx, cudaEventRecord(e1, s));
+                }
+                VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, s));
+                ctx->launches += 2;
+            }
+            if (prof) {
+                e2 = ctx_event(ctx);
+                VNE_TRY_CUDA(ctx, cudaEventRecord(e2, s));
+                // algorithmic bytes: CSR structure (+ values) once per panel, the
+                // gathered block w_j once, w_{j-1} (j > 1) and u once each
+                const double es = sizeof(T);
+                double csr = 4.0 * (P.n_total + 1) + (double)nnz_total * (4.0 + (P.valued ? es : 0.0));
+                double vec = (double)P.n_total * ks * es;
+                double step_bytes = panels * (csr + vec * (j > 1 ? 3.0 : 2.0));
+                double upd_bytes = panels * vec * 3.0;
+                if (interleave && !reorth) {
+                    // one timed span covers the interleaved step and update launches
+                    ctx->pending.push_back({0, e0, e1, step_bytes + upd_bytes});
+                } else {
+                    ctx->pending.push_back({0, e0, e1, step_bytes});
+                    ctx->pending.push_back({1, e1, e2, upd_bytes});
+                }
+            }
+            if (reorth && j < m + 1) {
+                ReorthParams<T> rp{};
+                rp.basis = slots;
+                rp.slot_stride = slot_elems;
+                rp.w = slot(j + 1);
+                rp.j = j;
+                rp.K = Kp;
+                rp.n_total = P.n_total;
+                rp.panels = panels;
+                rp.tiles_per_panel = tiles;
+                rp.tiles = P.d_tiles;
+                rp.part = rpart;
+                rp.coef = rcoef;
+                ReorthCoefParams cp{};
+                cp.part = rpart;
+                cp.sig = sigma;
+                cp.coef = rcoef;
+                cp.j = j;
+                cp.K = Kp;
+                cp.panels = panels;
+                cp.tiles_per_panel = tiles;
+                for (int pass = 0; pass < 2; pass++) VNE_TRY_CUDA(ctx, launch_reorth<T>(rp, cp, ks, s));
+                p.renorm = 1;
+                VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, s));
+                ctx->launches += 7;
             }
         }
-        if (reorth && j < m + 1) {
-            ReorthParams<T> rp{};
-            rp.basis = slots;
-            rp.slot_stride = slot_elems;
-            rp.w = slot(j + 1);
-            rp.j = j;
-            rp.K = Kp;
-            rp.n_total = P.n_total;
-            rp.panels = panels;
-            rp.tiles_per_panel = tiles;
-            rp.tiles = P.d_tiles;
-            rp.part = rpart;
-            rp.coef = rcoef;
-            ReorthCoefParams cp{};
-            cp.part = rpart;
-            cp.sig = sigma;
-            cp.coef = rcoef;
-            cp.j = j;
-            cp.K = Kp;
-            cp.panels = panels;
-            cp.tiles_per_panel = tiles;
-            for (int pass = 0; pass < 2; pass++) VNE_TRY_CUDA(ctx, launch_reorth<T>(rp, cp, ks, st));
-            p.renorm = 1;
-            VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, st));
-            ctx->launches += 7;
+    };
+    if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[0], st));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    if (!graph || ctx->profile || cap != cudaStreamCaptureStatusNone) {
+        enqueue_loop(st, ctx->profile);
+    } else {
+        // Graph key: every value the loop's launches depend on.
+        std::string key;
+        auto put = [&key](const void* v, size_t b) { key.append(reinterpret_cast<const char*>(v), b); };
+        const int ints[] = {(int)sizeof(T), ks, panels, m, variant, (int)interleave, (int)reorth, (int)store_all,
+                            (int)P.valued, SK};
+        put(ints, sizeof(ints));
+        const void* ptrs[] = {slots, alpha, beta, sigma, rcoef, rpart};
+        put(ptrs, sizeof(ptrs));
+        put(&slot_elems, sizeof(slot_elems));
+        put(&p, sizeof(p));
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end()) {
+            if (ctx->graph_seen.size() > 4096) ctx->graph_seen.clear();
+            if (++ctx->graph_seen[key] >= 2) {
+                if (ctx->graphs.size() >= 64) {
+                    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+                    ctx->graphs.clear();
+                }
+                if (!ctx->cap_stream)
+                    VNE_TRY_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+                const int64_t l0 = ctx->launches;
+                cudaGraph_t g = nullptr;
+                VNE_TRY_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+                try {
+                    enqueue_loop(ctx->cap_stream, false);
+                } catch (...) {
+                    cudaStreamEndCapture(ctx->cap_stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    ctx->launches = l0;
+                    throw;
+                }
+                VNE_TRY_CUDA(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
+                cudaGraphExec_t ex = nullptr;
+                cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+                cudaGraphDestroy(g);
+                VNE_TRY_CUDA(ctx, e);
+                it = ctx->graphs.emplace(key, vne_ctx::LoopGraph{ex, ctx->launches - l0}).first;
+                ctx->launches = l0;
+                ctx->graphs_captured++;
+            }
+        }
+        if (it != ctx->graphs.end()) {
+            VNE_TRY_CUDA(ctx, cudaGraphLaunch(it->second.exec, st));
+            ctx->launches += it->second.kernels;
+            ctx->graphs_replayed++;
+        } else {
+            enqueue_loop(st, false);
         }
     }
     if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[1], st));
@@ -642,7 +713,8 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
         if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
         if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
         BlockOut out;
-        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant, sc.interleave);
+        run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant, sc.interleave,
+                     sc.graph);
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi.begin() + b0);
     }
@@ -1041,6 +1113,7 @@ extern "C" void vne_options_default(vne_options* o) {
     o->cg_tol = 1e-8;
     o->step_variant = -1;
     o->interleave = -1;
+    o->graphs = -1;
 }
 
 extern "C" const char* vne_version(void) { return "vne 0.1 (sm_103a)"; }
@@ -1070,6 +1143,8 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->loop_ev)
         if (e) cudaEventDestroy(e);
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return VNE_OK;
 }
@@ -1303,11 +1378,11 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
         if (M->fp64) {
             check_ks<double>(ctx, ks);
             run_block<double>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant,
-                              sc.interleave);
+                              sc.interleave, sc.graph);
         } else {
             check_ks<float>(ctx, ks);
             run_block<float>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant,
-                             sc.interleave);
+                             sc.interleave, sc.graph);
         }
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi + b0);
@@ -1336,7 +1411,8 @@ extern "C" vne_status vne_entropy_hutchinson(vne_matrix* M, int32_t num_vectors,
     StartSource s{};
     s.kind = SRC_RADEMACHER;
     s.seed_mixed = seed_mix(seed);
-    s.col_begin = 0;
+    VNE_REQUIRE(ctx, o.probe_offset >= 0, VNE_EINVAL, "probe_offset must be >= 0");
+    s.col_begin = o.probe_offset;
     std::vector<double> psi = M->fp64 ? quadforms<double>(M, &o, s, num_vectors, krylov_steps)
                                       : quadforms<float>(M, &o, s, num_vectors, krylov_steps);
     double mean = 0.0;
@@ -1380,7 +1456,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     s.ncols = Nr;
     BlockOut sk;
     run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant,
-                 sc.interleave);
+                 sc.interleave, sc.graph);
     const int Kp = sk.Kp;
     double* zvec = ws_get_t<double>(ctx, "zvec", (size_t)m * Kp);
     VNE_TRY_CUDA(ctx, launch_tridiag_fvec(sk.alpha, sk.beta, sk.scale, Kp, m, Kp, zvec, st));
@@ -1468,7 +1544,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
         sq.ncols = Kp + Kg;
         BlockOut qo;
         run_block<T>(ctx, *P, sq, QG, Kp + Kg, ks, m, want_reorth(M, o), false, M->desing, "q", qo, sc.variant,
-                     sc.interleave);
+                     sc.interleave, sc.graph);
         std::vector<double> h = download(ctx, qo.psi, Kp + Kg);
         for (int c = 0; c < r; c++) low += h[c];
         for (int c = 0; c < NH; c++) resid += h[Kp + c];
@@ -1709,11 +1785,12 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     BlockOut out;
     if (fp64) {
         check_ks<double>(ctx, ks);
-        run_block<double>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out);
+        run_block<double>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out, 0,
+                          false, o.graphs != 0);
     } else {
         check_ks<float>(ctx, ks);
         run_block<float>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out,
-                         variant);
+                         variant, false, o.graphs != 0);
     }
     std::vector<double> psi = download(ctx, out.psi, out.SK);
     for (int i = 0; i < count; i++) {
@@ -1736,6 +1813,13 @@ extern "C" vne_status vne_ctx_profile(vne_ctx* ctx, int32_t enable) {
     ctx->profile = enable != 0;
     for (auto& k : ctx->stat) k = KernelStat();
     ctx->launches = 0;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_graph_stats(const vne_ctx* ctx, int64_t* captured, int64_t* replayed) {
+    if (!ctx) return VNE_EINVAL;
+    if (captured) *captured = ctx->graphs_captured;
+    if (replayed) *replayed = ctx->graphs_replayed;
     return VNE_OK;
 }
 
@@ -1791,8 +1875,8 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
                 for (int rep = 0; rep < 2; rep++) {
                     BlockOut out;
                     ctx->time_steps = true;
-                    if (M->fp64) run_block<double>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il);
-                    else run_block<float>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il);
+                    if (M->fp64) run_block<double>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il, false);
+                    else run_block<float>(ctx, *P, s, nullptr, k, o.panel, steps, false, false, M->desing, "tune", out, v, il, false);
                     ctx->time_steps = false;
                     download(ctx, out.psi, 1);
                     float ms = 0.f;
@@ -2086,7 +2170,8 @@ extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t
     src.seg_col0 = upload(ctx, "srv.col0", col0);
     BlockOut out;
     check_ks<float>(ctx, ks);
-    run_block<float>(ctx, P, src, nullptr, S->block, ks, S->m, false, false, true, "srv", out, variant);
+    run_block<float>(ctx, P, src, nullptr, S->block, ks, S->m, false, false, true, "srv", out, variant, false,
+                     S->opt.graphs != 0);
     std::vector<double> psi = download(ctx, out.psi, out.SK);
     // statistics and retirement
     std::vector<int> still;

@@ -49,7 +49,8 @@ class vne_options(ctypes.Structure):
     _fields_ = [("reorth", ctypes.c_int32), ("block", ctypes.c_int32), ("panel", ctypes.c_int32),
                 ("item_nnz", ctypes.c_int32), ("n_inf_poles", ctypes.c_int32), ("cg_max_iter", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
-                ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("probe_offset", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -98,6 +99,7 @@ def _declare(lib):
         "vne_autotune": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vne_options), _PD]),
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
+        "vne_ctx_graph_stats": (st, [_P, _PI64, _PI64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -127,7 +129,8 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
-               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
+               "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
+               "vne_ctx_graph_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
                "vne_server_result", "vne_server_info"]
 
@@ -331,6 +334,13 @@ def vne_ctx_stats(ctx):
     _check(load().vne_ctx_stats(ctx, ctypes.byref(n), _ptr(st)), ctx)
     names = ["step", "update", "cg_update", "cg_direction"]
     return n.value, {nm: tuple(st[3 * i:3 * i + 3]) for i, nm in enumerate(names)}
+
+
+def vne_ctx_graph_stats(ctx):
+    """(captured, replayed): step loops captured into CUDA graphs / replayed from them."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().vne_ctx_graph_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
 
 
 def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, krylov_steps, psi_dev):
