@@ -101,8 +101,7 @@ struct vne_matrix {
     bool fp64 = false, pattern = false, desing = false;
     double trace = 0.0, scale = 1.0, normM = 0.0;
     std::vector<int64_t> h_rowptr;  // packed (possibly relabelled) numbering
-    std::vector<int32_t> h_col;
-    std::vector<double> h_vals;     // valued matrices only
+    std::vector<int32_t> h_col;     // host copy of d_col, made on first use (host_cols)
     std::vector<int32_t> perm;      // packed row -> caller node id (empty: identity)
     int32_t* d_rowptr = nullptr;
     int32_t* d_col = nullptr;
@@ -179,6 +178,19 @@ T* upload(vne_ctx* ctx, const std::string& name, const std::vector<T>& v) {
     if (!v.empty())
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     return d;
+}
+
+// Host copy of the stored column indices (device order), made on first use.
+const std::vector<int32_t>& host_cols(vne_matrix* M) {
+    if ((int64_t)M->h_col.size() != M->nnz) {
+        M->h_col.resize(M->nnz);
+        if (M->nnz) {
+            VNE_TRY_CUDA(M->ctx, cudaMemcpyAsync(M->h_col.data(), M->d_col, M->nnz * sizeof(int32_t),
+                                                 cudaMemcpyDeviceToHost, M->ctx->stream));
+            VNE_TRY_CUDA(M->ctx, cudaStreamSynchronize(M->ctx->stream));
+        }
+    }
+    return M->h_col;
 }
 
 cudaEvent_t ctx_event(vne_ctx* ctx) {
@@ -1163,54 +1175,90 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     *out = nullptr;
     VNE_API_BEGIN
     cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
     const bool fp64 = flags & VNE_FP64, fp32 = flags & VNE_FP32;
     VNE_REQUIRE(ctx, fp64 != fp32, VNE_EINVAL, "exactly one of VNE_FP64 / VNE_FP32 is required");
     VNE_REQUIRE(ctx, n >= 1 && n < (int64_t)INT32_MAX, VNE_EINVAL, "n = %lld out of range", (long long)n);
     VNE_REQUIRE(ctx, row_ptr && col_idx, VNE_EINVAL, "row_ptr and col_idx are required");
+    VNE_REQUIRE(ctx, !(vals && (flags & VNE_CHECK_SYMMETRY)), VNE_EUNSUPPORTED,
+                "VNE_CHECK_SYMMETRY supports pattern matrices only");
     std::unique_ptr<vne_matrix> M(new vne_matrix());
     M->ctx = ctx;
     M->n = n;
     M->fp64 = fp64;
     M->pattern = (vals == nullptr);
-    std::vector<int64_t> rp(n + 1);
     const bool dev = flags & VNE_INPUT_DEVICE;
+    // Row pointers on the host (O(n)): monotonicity, degrees, the relabelling
+    // and the work plan need them there.
+    std::vector<int64_t> rp(n + 1);
     if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     else memcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t));
     VNE_REQUIRE(ctx, rp[0] == 0, VNE_EINVAL, "row_ptr[0] must be 0");
-    for (int64_t i = 0; i < n; i++) VNE_REQUIRE(ctx, rp[i + 1] >= rp[i], VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < n; i++) {
+        VNE_REQUIRE(ctx, rp[i + 1] >= rp[i], VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
+        maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
+    }
     const int64_t nnz = rp[n];
     VNE_REQUIRE(ctx, nnz < (int64_t)INT32_MAX, VNE_EINVAL, "nnz = %lld exceeds int32", (long long)nnz);
-    std::vector<int32_t> ci(nnz);
-    std::vector<double> va;
-    if (nnz) {
-        if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(ci.data(), col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        else memcpy(ci.data(), col_idx, nnz * sizeof(int32_t));
+    M->nnz = nnz;
+    std::vector<int32_t> rp32(n + 1);
+    for (int64_t i = 0; i <= n; i++) rp32[i] = (int32_t)rp[i];
+    // Columns (and values) on the device: the caller's device arrays, or one
+    // copy of the host arrays into staging buffers.
+    const int32_t* d_ci = col_idx;
+    if (!dev) {
+        int32_t* stage = ws_get_t<int32_t>(ctx, "asm.col", std::max<int64_t>(nnz, 1));
+        if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(stage, col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        d_ci = stage;
     }
-    if (vals) {
-        va.resize(nnz);
-        if (nnz) {
-            if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(va.data(), vals, nnz * sizeof(double), cudaMemcpyDeviceToHost));
-            else memcpy(va.data(), vals, nnz * sizeof(double));
+    const double* d_va = vals;
+    if (vals && !dev) {
+        double* stage = ws_get_t<double>(ctx, "asm.vals", std::max<int64_t>(nnz, 1));
+        if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(stage, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+        d_va = stage;
+    }
+    int32_t* d_rp_in = upload(ctx, "asm.rowptr", rp32);
+    // column range and (pattern) self-loops, checked on the device
+    unsigned long long* d_bad = ws_get_t<unsigned long long>(ctx, "asm.bad", 2);
+    VNE_TRY_CUDA(ctx, launch_validate(d_rp_in, d_ci, n, vals ? 0 : 1, d_bad, st));
+    unsigned long long bad[2];
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    ctx->launches += 1;
+    if (bad[0] != ~0ull || bad[1] != ~0ull) {
+        const unsigned long long k = std::min(bad[0], bad[1]);
+        const int64_t row = (int64_t)(std::upper_bound(rp.begin(), rp.end(), (int64_t)k) - rp.begin()) - 1;
+        int32_t c = 0;
+        VNE_TRY_CUDA(ctx, cudaMemcpy(&c, d_ci + k, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (k == bad[0]) VNE_REQUIRE(ctx, false, VNE_EINVAL, "column index %d out of range in row %lld", c, (long long)row);
+        VNE_REQUIRE(ctx, false, VNE_EINVAL, "self-loop at node %lld (pattern Laplacian)", (long long)row);
+    }
+    // Host copies of columns / values only where a host pass needs them
+    // (symmetry check; trace and Gershgorin bound of a valued matrix).
+    std::vector<int32_t> hci;
+    std::vector<double> hva;
+    const bool need_host = vals || (flags & VNE_CHECK_SYMMETRY);
+    if (need_host && nnz) {
+        hci.resize(nnz);
+        if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(hci.data(), col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        else memcpy(hci.data(), col_idx, nnz * sizeof(int32_t));
+        if (vals) {
+            hva.resize(nnz);
+            if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(hva.data(), vals, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+            else memcpy(hva.data(), vals, nnz * sizeof(double));
         }
     }
-    for (int64_t i = 0; i < n; i++)
-        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-            VNE_REQUIRE(ctx, ci[k] >= 0 && ci[k] < n, VNE_EINVAL, "column index %d out of range in row %lld", ci[k], (long long)i);
-            if (!vals) VNE_REQUIRE(ctx, ci[k] != i, VNE_EINVAL, "self-loop at node %lld (pattern Laplacian)", (long long)i);
-        }
     if (flags & VNE_CHECK_SYMMETRY) {
-        VNE_REQUIRE(ctx, !vals, VNE_EUNSUPPORTED, "VNE_CHECK_SYMMETRY supports pattern matrices only");
-        for (int64_t i = 0; i < n; i++) std::sort(ci.begin() + rp[i], ci.begin() + rp[i + 1]);
+        for (int64_t i = 0; i < n; i++) std::sort(hci.begin() + rp[i], hci.begin() + rp[i + 1]);
         for (int64_t i = 0; i < n; i++)
             for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-                int32_t j = ci[k];
-                bool found = std::binary_search(ci.begin() + rp[j], ci.begin() + rp[j + 1], (int32_t)i);
+                int32_t j = hci[k];
+                bool found = std::binary_search(hci.begin() + rp[j], hci.begin() + rp[j + 1], (int32_t)i);
                 VNE_REQUIRE(ctx, found, VNE_ENOTSYM, "pattern not symmetric: (%lld,%d)", (long long)i, j);
             }
     }
     // trace, Gershgorin bound of the stored operator M, scale
-    int64_t maxdeg = 0;
-    for (int64_t i = 0; i < n; i++) maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
     if (!vals) {
         M->trace = (double)nnz;
         M->normM = 2.0 * (double)maxdeg;
@@ -1220,8 +1268,8 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         for (int64_t i = 0; i < n; i++) {
             double rs = 0.0;
             for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-                if (ci[k] == i) tr += va[k];
-                rs += fabs(va[k]);
+                if (hci[k] == i) tr += hva[k];
+                rs += fabs(hva[k]);
             }
             nm = std::max(nm, rs);
         }
@@ -1236,58 +1284,41 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     } else {
         M->scale = 1.0;
     }
-    // optional degree-descending relabelling (entropy is permutation invariant)
+    const size_t es = fp64 ? 8 : 4;
+    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
+    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    if (vals) VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
     if (flags & VNE_REORDER) {
+        // degree-descending relabelling, stable in the node id (host, O(n));
+        // the nonzeros are moved on the device
         std::vector<int32_t> order = degree_order(n, rp.data());  // new -> old
         std::vector<int32_t> inv(n);
         for (int64_t i = 0; i < n; i++) inv[order[i]] = (int32_t)i;
         std::vector<int64_t> rp2(n + 1, 0);
-        std::vector<int32_t> ci2(nnz);
-        std::vector<double> va2(vals ? nnz : 0);
         for (int64_t i = 0; i < n; i++) rp2[i + 1] = rp2[i] + (rp[order[i] + 1] - rp[order[i]]);
-        std::vector<std::pair<int32_t, double>> tmp;
-        for (int64_t i = 0; i < n; i++) {
-            int32_t o = order[i];
-            tmp.clear();
-            for (int64_t k = rp[o]; k < rp[o + 1]; k++) tmp.emplace_back(inv[ci[k]], vals ? va[k] : 0.0);
-            std::sort(tmp.begin(), tmp.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) { return a.first < b.first; });
-            for (size_t q = 0; q < tmp.size(); q++) {
-                ci2[rp2[i] + q] = tmp[q].first;
-                if (vals) va2[rp2[i] + q] = tmp[q].second;
-            }
-        }
-        rp.swap(rp2);
-        ci.swap(ci2);
-        va.swap(va2);
-        M->perm = order;
-    }
-    M->nnz = nnz;
-    // device copies: int32 row pointers, int32 columns, values in the path precision
-    std::vector<int32_t> rp32(n + 1);
-    for (int64_t i = 0; i <= n; i++) rp32[i] = (int32_t)rp[i];
-    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
-    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp32.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_col, ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-    if (vals) {
-        size_t es = fp64 ? 8 : 4;
-        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
-        if (fp64) {
-            if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_vals, va.data(), nnz * 8, cudaMemcpyHostToDevice, ctx->stream));
-        } else {
-            std::vector<float> vf(va.begin(), va.end());
-            if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_vals, vf.data(), nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
-            VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        }
-    }
-    if (!M->perm.empty()) {
+        std::vector<int32_t> rp2_32(n + 1);
+        for (int64_t i = 0; i <= n; i++) rp2_32[i] = (int32_t)rp2[i];
+        int32_t* d_inv = upload(ctx, "asm.inv", inv);
         VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_node_id, n * sizeof(int32_t)));
-        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, M->perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp2_32.data(), (n + 1) * sizeof(int32_t),
+                                          cudaMemcpyHostToDevice, st));
+        VNE_TRY_CUDA(ctx, launch_relabel(d_rp_in, d_ci, d_va, M->d_rowptr, M->d_node_id, d_inv, n, M->d_col,
+                                         M->d_vals, fp64 ? 1 : 0, st));
+        ctx->launches += 1;
+        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));  // host vectors above are sources of async copies
+        rp.swap(rp2);
+        M->perm = std::move(order);
+    } else {
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, d_rp_in, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_col, d_ci, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        if (vals) {
+            VNE_TRY_CUDA(ctx, launch_convert_values(d_va, nnz, M->d_vals, fp64 ? 1 : 0, st));
+            ctx->launches += 1;
+        }
+        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
     }
-    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     M->h_rowptr.swap(rp);
-    M->h_col.swap(ci);
-    M->h_vals.swap(va);
     M->maxdeg = maxdeg;
     {
         auto it = ctx->tune_cache.find(vne_ctx::TuneKey{M->n, M->nnz, maxdeg, (int)M->fp64, (int)M->pattern});
@@ -1613,7 +1644,7 @@ extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring
         VNE_REQUIRE(ctx, distance >= 1, VNE_EINVAL, "distance must be >= 1");
         // colour the caller's graph (undo the relabelling for the traversal)
         std::vector<int32_t> c2(n);
-        s = greedy_coloring(n, M->h_rowptr.data(), M->h_col.data(), distance, c2.data());
+        s = greedy_coloring(n, M->h_rowptr.data(), host_cols(M).data(), distance, c2.data());
         if (M->perm.empty()) col.swap(c2);
         else
             for (int64_t i = 0; i < n; i++) col[M->perm[i]] = c2[i];
@@ -1740,12 +1771,13 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     double taurel = o.breakdown_tol > 0 ? o.breakdown_tol : default_tau(fp64);
     int64_t r0 = 0, e0 = 0;
     for (int i = 0; i < count; i++) {
-        const vne_matrix* M = mats[i];
+        vne_matrix* M = mats[i];
+        const std::vector<int32_t>& hc = host_cols(M);
         for (int64_t r = 0; r < M->n; r++) {
             rp[r0 + r + 1] = e0 + M->h_rowptr[r + 1];
             if (any_perm) nid[r0 + r] = M->perm.empty() ? (int32_t)r : M->perm[r];
         }
-        for (int64_t e = 0; e < M->nnz; e++) ci[e0 + e] = M->h_col[e] + (int32_t)r0;
+        for (int64_t e = 0; e < M->nnz; e++) ci[e0 + e] = hc[e] + (int32_t)r0;
         SegInfo s{};
         s.row_begin = (int32_t)r0;
         s.rows = (int32_t)M->n;

@@ -179,6 +179,32 @@ def test_invalid_inputs_raise(vctx):
         vne.vne_matrix_destroy(mat)
 
 
+def test_device_validation_reports_first_offender(vctx):
+    """Column range and self-loops are checked on the device over many rows;
+    the error names the first offending entry and the context stays usable."""
+    g = graphs.erdos_renyi(200000, 4e-5, 9)
+    k_late, k_early = g.nnz - 3, g.nnz // 2
+    bad = g.col.copy()
+    bad[k_late] = -1
+    bad[k_early] = g.n
+    with pytest.raises(vne.VneError, match="out of range") as ei:
+        vne.vne_create_density_matrix(vctx, g.n, g.rowptr, bad, None, vne.VNE_FP32 | vne.VNE_REORDER)
+    row = int(np.searchsorted(g.rowptr, k_early, side="right") - 1)
+    assert f"row {row}" in str(ei.value)
+    loop = g.col.copy()
+    r = int(np.searchsorted(g.rowptr, k_late, side="right") - 1)
+    loop[k_late] = r
+    with pytest.raises(vne.VneError, match="self-loop"):
+        vne.vne_create_density_matrix(vctx, g.n, g.rowptr, loop, None, vne.VNE_FP32)
+    # the context is still usable
+    mat = vne.matrix_from_graph(vctx, g, reorder=True)
+    try:
+        est, _ = vne.vne_entropy_hutchinson(vctx, mat, 8, 5, 1)
+        assert np.isfinite(est)
+    finally:
+        vne.vne_matrix_destroy(mat)
+
+
 def test_autotuned_schedule_keeps_parity(vctx):
     g = graphs.barabasi_albert(30000, 4, 21)
     A, _ = density.density_matrix(g)
