@@ -163,32 +163,565 @@ __host__ __device__ inline bool symtri_qr_first_row(double* d, double* e, double
     return symtri_qr_rows<1>(d, e, n, rows, 1);
 }
 
-template <int MAXM>
-__global__ void k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
-                               const double* __restrict__ norm2, const double* __restrict__ scale, int count,
-                               int m, int ld, double* __restrict__ psi, int cols_per_cta) {
-    if ((int)threadIdx.x >= cols_per_cta) return;
-    int c = blockIdx.x * cols_per_cta + threadIdx.x;
-    if (c >= count) return;
-    double d[MAXM], e[MAXM], z[MAXM];
-    int n = m;
-    for (int j = 0; j < m; j++) {
-        d[j] = alpha[(size_t)j * ld + c];
-        z[j] = 0.0;
+// ---------------------------------------------------------------------------
+// Gauss quadrature psi = ||c||^2 sum_j u_{1j}^2 f(sigma theta_j) of the
+// leading unreduced block of T (Golub & Meurant, Matrices, Moments and
+// Quadrature, Ch. 6), one warp per tridiagonal with the eigenvalues spread
+// over the lanes.  GB300 retires FP64 instructions slowly and with long
+// latency, so one long sequential QR chain per column is the slowest possible
+// schedule; here every lane runs short independent chains:
+//  * theta_j by bisection on the Sturm count #{theta < z} (number of k with
+//    sign p_k(z) = sign p_{k-1}(z), p_k = det(z I - T_k) by the three-term
+//    recurrence, rescaled by powers of two every four steps; Wilkinson, The
+//    Algebraic Eigenvalue Problem, Ch. 5): FP32 halvings first narrow the
+//    Gershgorin interval, FP64 counts check the bracket, then FP64
+//    quadrisection with all of a lane's points evaluated as interleaved
+//    independent recurrences, a warp-uniform number of passes;
+//  * u_{1j}^2 from the eigenvector of the twisted factorisation
+//    T - theta I = N_r Delta_r N_r^T at the twist index r of smallest
+//    |gamma_r| (Parlett & Dhillon, Lin. Alg. Appl. 309, 2000): z_r = 1,
+//    components above r from the top-down pivots, below r from the bottom-up
+//    pivots, u_{1j}^2 = z_1^2 / ||z||^2;
+//  * eigenvalues closer than kClusterGap * span to a neighbour (or closer
+//    than 16 x the half-width of the group being formed) form a cluster,
+//    whose individual weights are ill-conditioned; its summed weight W and
+//    first and second moments come from the resolvent e1^T (z I - T)^{-1} e1
+//    (continued fraction) integrated by the trapezoid rule on a circle
+//    around it, and it contributes W f(tbar) + f''(tbar) W var / 2 (weighted
+//    mean tbar, variance var).  A cluster closer than 16 x its half-width to
+//    the previous group sends the column to the sequential implicit QR
+//    (lane 0), which keeps the kernel correct for any input.
+constexpr double kClusterGap = 1e-5;
+constexpr int kContourPoints = 32;
+
+// Power of two that brings |x| (the largest of the values passed) to [1, 2):
+// multiplying the recurrence state by it keeps signs and ratios.
+__device__ __forceinline__ double pow2_rescale(long long maxbits) {
+    int se = 2046 - (int)(maxbits >> 52);
+    se = se < 1 ? 1 : (se > 2046 ? 2046 : se);
+    return __longlong_as_double((long long)se << 52);
+}
+
+__device__ __forceinline__ long long absbits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+
+// #{eigenvalues of the leading n x n block < z[q]} for NC points at once
+// (independent recurrences, interleaved for instruction-level parallelism):
+// the number of k with sign p_k = sign p_{k-1}, p_0 = 1.  b2[k] =
+// beta_{k-1}^2, b2[0] = 0.  A p_k that is exactly +0 counts as positive (a
+// perturbation of z by one ulp).
+template <int NC>
+__device__ __forceinline__ void sturm_counts(const double* a, const double* b2, int n, const double (&z)[NC],
+                                             int (&cnt)[NC]) {
+    double p2[NC], p1[NC];  // p_{k-2}, p_{k-1}
+    int hprev[NC], changes[NC];
+#pragma unroll
+    for (int q = 0; q < NC; q++) {
+        p2[q] = 0.0;
+        p1[q] = 1.0;
+        hprev[q] = 0;
+        changes[q] = 0;
     }
-    for (int j = 0; j + 1 < m; j++) {
-        e[j] = beta[(size_t)j * ld + c];
-        if (e[j] == 0.0) {
-            n = j + 1;
+    for (int k = 0; k < n; k++) {
+        const double ak = a[k], bk = b2[k];
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+            const double p = fma(z[q] - ak, p1[q], -(bk * p2[q]));
+            const int h = __double2hiint(p);
+            changes[q] += (int)((unsigned)(h ^ hprev[q]) >> 31);
+            hprev[q] = h;
+            p2[q] = p1[q];
+            p1[q] = p;
+        }
+        if ((k & 7) == 7) {
+#pragma unroll
+            for (int q = 0; q < NC; q++) {
+                const long long m1 = absbits(p1[q]), m2 = absbits(p2[q]);
+                const double fsc = pow2_rescale(m1 > m2 ? m1 : m2);
+                p1[q] *= fsc;
+                p2[q] *= fsc;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; q++) cnt[q] = n - changes[q];
+}
+
+// p_n(z) / p_n'(z) for the characteristic polynomial p_n(z) = det(z I - T)
+// and the Sturm count at z, from one recurrence (p_k' = p_{k-1} +
+// (z - a_k) p_{k-1}' - b2_k p_{k-2}'), for NC points.
+template <int NC>
+__device__ __forceinline__ void newton_counts(const double* a, const double* b2, int n, const double (&z)[NC],
+                                              double (&ratio)[NC], int (&cnt)[NC]) {
+    double p2[NC], p1[NC], d2[NC], d1[NC];
+    int hprev[NC], changes[NC];
+#pragma unroll
+    for (int q = 0; q < NC; q++) {
+        p2[q] = 0.0;
+        p1[q] = 1.0;
+        d2[q] = 0.0;
+        d1[q] = 0.0;
+        hprev[q] = 0;
+        changes[q] = 0;
+    }
+    for (int k = 0; k < n; k++) {
+        const double ak = a[k], bk = b2[k];
+#pragma unroll
+        for (int q = 0; q < NC; q++) {
+            const double zk = z[q] - ak;
+            const double p = fma(zk, p1[q], -(bk * p2[q]));
+            const double d = fma(zk, d1[q], p1[q]) - bk * d2[q];
+            const int h = __double2hiint(p);
+            changes[q] += (int)((unsigned)(h ^ hprev[q]) >> 31);
+            hprev[q] = h;
+            p2[q] = p1[q];
+            p1[q] = p;
+            d2[q] = d1[q];
+            d1[q] = d;
+        }
+        if ((k & 7) == 7) {
+#pragma unroll
+            for (int q = 0; q < NC; q++) {
+                long long m = absbits(p1[q]);
+                m = max(m, absbits(p2[q]));
+                m = max(m, absbits(d1[q]));
+                m = max(m, absbits(d2[q]));
+                const double fsc = pow2_rescale(m);
+                p1[q] *= fsc;
+                p2[q] *= fsc;
+                d1[q] *= fsc;
+                d2[q] *= fsc;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; q++) {
+        ratio[q] = p1[q] / d1[q];
+        cnt[q] = n - changes[q];
+    }
+}
+
+// FP32 Sturm count on the FP32-rounded block (pivots d_k of T - zI,
+// #{d_k < 0}), used only to narrow the FP64 search interval; the interval is
+// checked with FP64 counts before it is trusted.
+__device__ __forceinline__ int sturm_count_f32(const float* a, const float* b2, int n, float z, float pivmin) {
+    int cnt = 0;
+    float d = 1.f;
+    for (int k = 0; k < n; k++) {
+        d = (a[k] - z) - __fdividef(b2[k], d);
+        if (fabsf(d) < pivmin) d = -pivmin;
+        cnt += d < 0.f;
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ double guard_pivot(double x, double pivmin) {
+    return fabs(x) < pivmin ? (x < 0.0 ? -pivmin : pivmin) : x;
+}
+
+// u_{1j}^2 by the twisted factorisation at an isolated eigenvalue th.
+// Dp / Rp: this lane's columns of the pivot scratch ([k][32] doubles).
+__device__ double twisted_weight(const double* a, const double* b, int n, double th, double pivmin, double* Dp,
+                                 double* Rp) {
+    double d = 0.0;
+    for (int k = 0; k < n; k++) {
+        d = guard_pivot((a[k] - th) - (k > 0 ? b[k - 1] * b[k - 1] / d : 0.0), pivmin);
+        Dp[k * 32] = d;
+    }
+    double r = 0.0, best = INFINITY;
+    int tw = n - 1;
+    for (int k = n - 1; k >= 0; k--) {
+        r = guard_pivot((a[k] - th) - (k + 1 < n ? b[k] * b[k] / r : 0.0), pivmin);
+        Rp[k * 32] = r;
+        const double gam = fabs(Dp[k * 32] + r - (a[k] - th));
+        if (gam < best) {
+            best = gam;
+            tw = k;
+        }
+    }
+    double s = 1.0, z = 1.0;
+    for (int k = tw - 1; k >= 0; k--) {
+        z = -b[k] * z / Dp[k * 32];
+        s = fma(z, z, s);
+    }
+    const double z1 = tw > 0 ? z : 1.0;
+    z = 1.0;
+    for (int k = tw + 1; k < n; k++) {
+        z = -b[k - 1] * z / Rp[k * 32];
+        s = fma(z, z, s);
+    }
+    return z1 * z1 / s;
+}
+
+// Point q of the K-point trapezoid rule on the circle z = c + rho e^{i phi}:
+// Re F(z) dz^p, p = 1, 2, 3, with dz = z - c and F(z) = e1^T (z I - T)^{-1} e1
+// by the bottom-up continued fraction.  (1/K) times their sums over q are the
+// summed weight and the first and second moments about c of the eigenvalues
+// inside the circle.
+__device__ void resolvent_point(const double* a, const double* b, int n, double c, double rho, int q, double& re1,
+                                double& re2, double& re3) {
+    double sph, cph;
+    sincospi((2.0 * q + 1.0) / kContourPoints, &sph, &cph);
+    const double dzr = rho * cph, dzi = rho * sph;
+    const double zr = c + dzr, zi = dzi;
+    double gr = zr - a[n - 1], gi = zi;
+    for (int k = n - 2; k >= 0; k--) {
+        // g <- (z - a_k) - b_k^2 / g
+        const double t = b[k] * b[k] / (gr * gr + gi * gi);
+        gr = (zr - a[k]) - t * gr;
+        gi = zi + t * gi;
+    }
+    const double den = gr * gr + gi * gi;
+    const double fr = gr / den, fi = -gi / den;                        // F = 1 / g
+    const double pr = fr * dzr - fi * dzi, pim = fr * dzi + fi * dzr;  // F dz
+    re1 = pr;
+    const double p2r = pr * dzr - pim * dzi, p2i = pr * dzi + pim * dzr;  // F dz^2
+    re2 = p2r;
+    re3 = p2r * dzr - p2i * dzi;  // Re(F dz^3)
+}
+
+// Fallback: the quadrature by the sequential implicit QR of the whole
+// (scaled) block, run by lane 0 of the warp.
+template <int MAXM>
+__device__ void quad_by_qr(const double* sa, const double* sb, int n, double sc, double norm2, int lane,
+                           double* out) {
+    if (lane != 0) return;
+    double d[MAXM], ee[MAXM], z[MAXM];
+    for (int k = 0; k < n; k++) {
+        d[k] = sa[k];
+        ee[k] = sb[k];
+        z[k] = 0.0;
+    }
+    z[0] = 1.0;
+    const bool ok = symtri_qr_first_row(d, ee, z, n);
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s += z[k] * z[k] * f_entropy(sc * d[k]);
+    *out = ok ? norm2 * s : nan("");
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                                     const double* __restrict__ norm2, const double* __restrict__ scale,
+                                                     int count, int m, int ld, double* __restrict__ psi) {
+    __shared__ double sa[MAXM], sb[MAXM], sb2[MAXM + 1], sth[MAXM];
+    __shared__ float sa32[MAXM], sb2_32[MAXM + 1];
+    extern __shared__ double piv[];  // [2][MAXM][32]: twisted pivots, transposed per lane
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= count) return;
+    // leading unreduced block: n = 1 + first j with beta_j == 0
+    int n = m;
+    for (int j0 = 0; j0 < m - 1; j0 += 32) {
+        const int j = j0 + lane;
+        const bool zero = j < m - 1 && beta[(size_t)j * ld + c] == 0.0;
+        const unsigned zb = __ballot_sync(0xffffffffu, zero);
+        if (zb) {
+            n = j0 + __ffs(zb);
             break;
         }
     }
-    z[0] = 1.0;
-    bool ok = symtri_qr_first_row(d, e, z, n);
-    double sc = scale[c];
-    double s = 0.0;
-    for (int k = 0; k < n; k++) s += z[k] * z[k] * f_entropy(sc * d[k]);
-    psi[c] = ok ? norm2[c] * s : nan("");
+    bool finite = true;
+    double glo = INFINITY, ghi = -INFINITY, bmax = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const double aj = alpha[(size_t)j * ld + c];
+        const double bj = (j + 1 < n) ? beta[(size_t)j * ld + c] : 0.0;
+        const double bp = (j > 0) ? beta[(size_t)(j - 1) * ld + c] : 0.0;
+        sa[j] = aj;
+        sb[j] = bj;
+        sb2[j + 1] = bj * bj;
+        finite = finite && isfinite(aj) && isfinite(bj);
+        const double r = fabs(bj) + fabs(bp);
+        glo = fmin(glo, aj - r);
+        ghi = fmax(ghi, aj + r);
+        bmax = fmax(bmax, bj * bj);
+    }
+    if (lane == 0) {
+        sb2[0] = 0.0;
+        sb2_32[0] = 0.f;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+        ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    __syncwarp();
+    if (!finite) {
+        if (lane == 0) psi[c] = nan("");
+        return;
+    }
+    // scale the block by the power of two s2 that brings its Gershgorin
+    // radius to [1, 2) (exact: eigenvalues scale by s2, weights do not), so
+    // the unnormalised Sturm recurrences stay far from overflow
+    const double s2 = pow2_rescale(absbits(fmax(fmax(fabs(glo), fabs(ghi)), DBL_MIN)));
+    for (int j = lane; j < n; j += 32) {
+        sa[j] *= s2;
+        sb[j] *= s2;
+        sb2[j + 1] *= s2 * s2;
+        sa32[j] = (float)sa[j];
+        sb2_32[j + 1] = (float)sb2[j + 1];
+    }
+    __syncwarp();
+    glo *= s2;
+    ghi *= s2;
+    bmax *= s2 * s2;
+    const double span = fmax(fmax(fabs(glo), fabs(ghi)), DBL_MIN);
+    glo -= 4.0 * DBL_EPSILON * span + DBL_MIN;
+    ghi += 4.0 * DBL_EPSILON * span + DBL_MIN;
+    const double pivmin = DBL_MIN * fmax(1.0, bmax);
+    // 1. eigenvalues, ascending: theta_j is the j-th smallest.  Lane l owns
+    //    j = l + 32 r, r < R (the last lanes carry a dummy root when n < 32 R,
+    //    so the warp stays converged).
+    constexpr int R = MAXM / 32;
+    __shared__ double sbw[MAXM];  // final bracket width of each root
+    double lo[R], hi[R];
+    int clo[R], chi[R];  // Sturm counts at lo and hi
+    {
+        // (a) FP32 bisection narrows each bracket to a few ulps of FP32
+        const float pivmin32 = FLT_MIN * fmaxf(1.f, (float)bmax);
+        const float glo32 = (float)glo, ghi32 = (float)ghi;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int j = lane + 32 * r;
+            float l32 = glo32, h32 = ghi32;
+            if (j < n)
+                for (int it = 0; it < 26; it++) {
+                    const float z = 0.5f * (l32 + h32);
+                    if (sturm_count_f32(sa32, sb2_32, n, z, pivmin32) > j) h32 = z;
+                    else l32 = z;
+                }
+            const double w = 4e-6 * span + 8.0 * (double)FLT_EPSILON * fabs((double)h32);
+            lo[r] = fmax(glo, (double)l32 - w);
+            hi[r] = fmin(ghi, (double)h32 + w);
+        }
+        // (b) FP64 check of the brackets: count(lo) <= j < count(hi)
+        double zc[2 * R];
+        int cc[2 * R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            zc[2 * r] = lo[r];
+            zc[2 * r + 1] = hi[r];
+        }
+        sturm_counts<2 * R>(sa, sb2, n, zc, cc);
+        bool widened = false;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int j = lane + 32 * r;
+            clo[r] = cc[2 * r];
+            chi[r] = cc[2 * r + 1];
+            if (j < n && !(clo[r] <= j && chi[r] > j)) {
+                lo[r] = glo;
+                hi[r] = ghi;
+                clo[r] = 0;
+                chi[r] = n;
+                widened = true;
+            }
+        }
+        // (c) FP64 quadrisection (three interior points per root and pass)
+        //     down to ~3e-8 span: 4 passes from the FP32 bracket, 13 from the
+        //     Gershgorin interval
+        const int passes = __any_sync(0xffffffffu, widened) ? 13 : 4;
+        for (int it = 0; it < passes; it++) {
+            double zq[3 * R];
+            int cq[3 * R];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const double w = hi[r] - lo[r];
+#pragma unroll
+                for (int q = 0; q < 3; q++) zq[3 * r + q] = lo[r] + 0.25 * (q + 1) * w;
+            }
+            sturm_counts<3 * R>(sa, sb2, n, zq, cq);
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int j = lane + 32 * r;
+                const double z1 = zq[3 * r], z2 = zq[3 * r + 1], z3 = zq[3 * r + 2];
+                if (cq[3 * r] > j) {
+                    hi[r] = z1;
+                    chi[r] = cq[3 * r];
+                } else if (cq[3 * r + 1] > j) {
+                    lo[r] = z1;
+                    clo[r] = cq[3 * r];
+                    hi[r] = z2;
+                    chi[r] = cq[3 * r + 1];
+                } else if (cq[3 * r + 2] > j) {
+                    lo[r] = z2;
+                    clo[r] = cq[3 * r + 1];
+                    hi[r] = z3;
+                    chi[r] = cq[3 * r + 2];
+                } else {
+                    lo[r] = z3;
+                    clo[r] = cq[3 * r + 2];
+                }
+            }
+        }
+        // (d) safeguarded Newton on p_n (each step also counts, so the bracket
+        //     keeps shrinking): a root alone in its bracket converges
+        //     quadratically; roots sharing a bracket (tight clusters) keep
+        //     the bracket midpoint and are handled as a cluster below
+        double zn[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) zn[r] = 0.5 * (lo[r] + hi[r]);
+        for (int it = 0; it < 4; it++) {
+            double ratio[R];
+            int cn[R];
+            newton_counts<R>(sa, sb2, n, zn, ratio, cn);
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int j = lane + 32 * r;
+                if (cn[r] > j) {
+                    hi[r] = zn[r];
+                    chi[r] = cn[r];
+                } else {
+                    lo[r] = zn[r];
+                    clo[r] = cn[r];
+                }
+                const double zt = zn[r] - ratio[r];
+                const bool alone = (chi[r] - clo[r]) == 1;
+                zn[r] = (alone && zt >= lo[r] && zt <= hi[r]) ? zt : 0.5 * (lo[r] + hi[r]);  // converged: stays
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int j = lane + 32 * r;
+            if (j < n) {
+                sth[j] = zn[r];
+                sbw[j] = hi[r] - lo[r];
+            }
+        }
+    }
+    __syncwarp();
+    // 2. groups of eigenvalues (lane 0, one pass with merging): a group grows
+    //    while the next gap is below kClusterGap * span or below 16 x its
+    //    half-width, and absorbs the previous group while the gap to it is
+    //    below 17 x its half-width; one-member groups are isolated
+    //    eigenvalues, the others clusters.  A cluster closer than 16 x its
+    //    half-width to a neighbouring group sends the column to the
+    //    sequential QR.
+    const double sc = scale[c] / s2;  // f is applied to the unscaled eigenvalues
+    const double tau = kClusterGap * span;
+    constexpr int MAXC = MAXM / 2;
+    __shared__ double s_cc[MAXC], s_rho[MAXC], s_half[MAXC];
+    __shared__ int s_gfirst[MAXM + 1], s_glast[MAXM], s_cl_of_group[MAXM];
+    __shared__ int s_ngroups, s_ncl, s_fallback;
+    if (lane == 0) {
+        auto halfw = [&](int f, int l) {
+            double h = 0.5 * (sth[l] - sth[f]);
+            for (int q = f; q <= l; q++) h = fmax(h, 0.5 * sbw[q]);
+            return h;
+        };
+        int ng = 0;
+        for (int j = 0; j < n;) {
+            int f = j, e = j;
+            for (;;) {
+                while (e + 1 < n) {
+                    const double gap = sth[e + 1] - sth[e];
+                    if (!(gap < tau || gap < 16.0 * halfw(f, e))) break;
+                    e++;
+                }
+                if (ng > 0 && e > f && sth[f] - sth[s_glast[ng - 1]] < 17.0 * halfw(f, e)) {
+                    f = s_gfirst[--ng];  // absorb the previous group
+                    continue;
+                }
+                break;
+            }
+            s_gfirst[ng] = f;
+            s_glast[ng] = e;
+            ng++;
+            j = e + 1;
+        }
+        int ncl = 0, fb = 0;
+        for (int g = 0; g < ng; g++) {
+            const int f = s_gfirst[g], e = s_glast[g];
+            s_cl_of_group[g] = -1;
+            if (e == f) continue;
+            const double half = fmax(halfw(f, e), 4.0 * DBL_EPSILON * span);
+            const double dl = g > 0 ? sth[f] - sth[s_glast[g - 1]] : INFINITY;
+            const double dr = g + 1 < ng ? sth[s_gfirst[g + 1]] - sth[e] : INFINITY;
+            const double D = fmin(dl, dr) - half;
+            if (!(D >= 16.0 * half)) fb = 1;
+            // circle radius: D / 8 for a tight cluster, else the geometric mean
+            // of half-width and distance (both error terms (half / D)^(K/2))
+            s_cc[ncl] = 0.5 * (sth[f] + sth[e]);
+            s_rho[ncl] = !isfinite(D) ? 0.25 * span : (D >= 64.0 * half ? D / 8.0 : sqrt(half * D));
+            s_half[ncl] = half;
+            s_cl_of_group[g] = ncl++;
+        }
+        s_gfirst[ng] = n;
+        s_ngroups = ng;
+        s_ncl = ncl;
+        s_fallback = fb;
+    }
+    __syncwarp();
+    const int ngroups = s_ngroups, ncl = s_ncl;
+    if (s_fallback) {
+        quad_by_qr<MAXM>(sa, sb, n, sc, norm2[c], lane, psi + c);
+        return;
+    }
+    // 3. isolated eigenvalues: twisted-factorisation weights, groups spread
+    //    over the lanes
+    double acc = 0.0, wsum = 0.0, errb = 0.0;
+    for (int g = lane; g < ngroups; g += 32) {
+        if (s_cl_of_group[g] >= 0) continue;
+        const int j = s_gfirst[g];
+        const double w = twisted_weight(sa, sb, n, sth[j], pivmin, piv + lane, piv + MAXM * 32 + lane);
+        acc += w * f_entropy(sc * sth[j]);
+        wsum += w;
+    }
+    // 4. clusters: the K contour points of all clusters spread over the lanes
+    //    (their values reuse the pivot scratch), then lane (cluster mod 32)
+    //    sums each cluster's points in order
+    __syncwarp();
+    double* pts = piv;  // [cluster][K][3]
+    for (int item = lane; item < ncl * kContourPoints; item += 32) {
+        const int cl = item / kContourPoints, q = item % kContourPoints;
+        resolvent_point(sa, sb, n, s_cc[cl], s_rho[cl], q, pts[3 * item], pts[3 * item + 1], pts[3 * item + 2]);
+    }
+    __syncwarp();
+    for (int cl = lane; cl < ncl; cl += 32) {
+        double W = 0.0, M1 = 0.0, M2 = 0.0;
+        for (int q = 0; q < kContourPoints; q++) {
+            W += pts[3 * (cl * kContourPoints + q)];
+            M1 += pts[3 * (cl * kContourPoints + q) + 1];
+            M2 += pts[3 * (cl * kContourPoints + q) + 2];
+        }
+        W /= kContourPoints;
+        M1 /= kContourPoints;
+        M2 /= kContourPoints;
+        // sum_j w_j f(theta_j) over the cluster ~ W f(tbar) + f''(tbar) W var / 2
+        // with the weighted mean tbar and variance var; a cluster whose weight
+        // is at rounding level (eigenvectors that vanish at row 1) keeps its
+        // centre and no correction
+        const double cc = s_cc[cl], half = s_half[cl];
+        double contrib = W * f_entropy(sc * cc);
+        if (W > 0.0 && fabs(M1) <= 2.0 * half * W) {
+            const double mu = M1 / W, tbar = cc + mu;
+            const double var = fmax(M2 / W - mu * mu, 0.0);
+            contrib = W * f_entropy(sc * tbar);
+            if (tbar > 0.0) contrib -= 0.5 * (sc / tbar) * W * var;  // d2/dt2 f(sc t) = -sc / t
+        }
+        if (half > 1e-3 * fabs(cc)) {
+            // a cluster at the origin: the expansion does not hold, but its
+            // members lie in [cc - half, cc + half] and f >= 0 increases from
+            // 0, so the error is below W f(cc + half)
+            errb += fmax(W, 0.0) * f_entropy(fmin(sc * fmax(cc + half, 0.0), 0.36787944117144233));
+        }
+        acc += contrib;
+        wsum += W;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, off);
+        errb += __shfl_xor_sync(0xffffffffu, errb, off);
+    }
+    if (!(errb <= 1e-10 * fabs(acc))) {
+        if (lane == 0) s_fallback = 1;
+    } else if (lane == 0) {
+        // the weights sum to one; dividing by the computed sum removes their
+        // common rounding
+        psi[c] = norm2[c] * (acc / wsum);
+    }
+    __syncwarp();
+    if (s_fallback) quad_by_qr<MAXM>(sa, sb, n, sc, norm2[c], lane, psi + c);
 }
 
 // warp per column; dynamic smem: Z [m][m] (row-major) per warp (1 warp / CTA).
@@ -245,20 +778,22 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    // columns per CTA (one warp per CTA).  The FP64 pipe of an SM retires a
-    // 32-lane FP64 instruction over many cycles, so the columns are spread
-    // over all SMs first: ceil(count / SMs) columns per warp, at most 32.
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-    int cpw = (count + sms - 1) / sms;
-    if (cpw > 32) cpw = 32;
-    dim3 block(32), grid((count + cpw - 1) / cpw);
-    if (m <= 32) k_tridiag_quad<32><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
-    else if (m <= 64) k_tridiag_quad<64><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
-    else if (m <= 128) k_tridiag_quad<128><<<grid, block, 0, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi, cpw);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    // one warp (CTA) per tridiagonal; dynamic shared memory holds the
+    // twisted-factorisation pivots of the 32 lanes
+#define VNE_QUAD_CASE(MM)                                                                                    \
+    if (m <= MM) {                                                                                          \
+        const int smem = 2 * MM * 32 * (int)sizeof(double);                                                 \
+        cudaError_t e = cudaFuncSetAttribute(k_tridiag_quad<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             smem);                                                         \
+        if (e != cudaSuccess) return e;                                                                     \
+        k_tridiag_quad<MM><<<count, 32, smem, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);   \
+        return cudaGetLastError();                                                                          \
+    }
+    VNE_QUAD_CASE(32)
+    VNE_QUAD_CASE(64)
+    VNE_QUAD_CASE(128)
+#undef VNE_QUAD_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col, int count,
@@ -568,15 +1103,135 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ In, int kin
     }
 }
 
+// Tensor-core block product Out = coef * In M (+ In2) for FP32 blocks
+// (kin, kout <= 128), same TF32 three-product split as k_gram_tc.  M (FP64,
+// kin x kout) is converted once per CTA into hi/lo TF32 halves in shared
+// memory; each CTA then streams 64-row tiles of In through shared memory
+// (persistent grid).  Warps: 4 x 2, each owning 16 rows x 64 output columns.
+template <int KS>
+__global__ void __launch_bounds__(256) k_apply_tc(const float* __restrict__ In, int kin, const double* __restrict__ M,
+                                                  int kout, const float* __restrict__ In2, float* __restrict__ Out,
+                                                  int n, double coef) {
+    constexpr int LDB = 136;  // 136 = 8 (mod 32): conflict-free B fragments
+    constexpr int V_PER_ROW = KS / 4;
+    extern __shared__ __align__(16) uint32_t smu[];
+    const int kp = (kin + 7) & ~7;
+    const int lda = kp + 4;  // = 4 (mod 8): conflict-free A fragments
+    uint32_t* Bh = smu;
+    uint32_t* Bl = Bh + (size_t)kp * LDB;
+    float* As = reinterpret_cast<float*>(Bl + (size_t)kp * LDB);  // [64][lda]
+    for (int idx = threadIdx.x; idx < kp * 128; idx += 256) {
+        const int k = idx >> 7, c = idx & 127;
+        const float x = (k < kin && c < kout) ? (float)(coef * M[(size_t)k * kout + c]) : 0.f;
+        const uint32_t hi = to_tf32(x);
+        Bh[k * LDB + c] = hi;
+        Bl[k * LDB + c] = to_tf32(x - __uint_as_float(hi));
+    }
+    // columns kin..kp of the row tile stay zero
+    for (int idx = threadIdx.x; idx < 64 * (kp - kin); idx += 256) {
+        const int rl = idx / (kp - kin), c = kin + idx % (kp - kin);
+        As[rl * lda + c] = 0.f;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, tq = lane & 3;
+    const int pin = kin / KS;
+    const int ntiles = (n + 63) / 64;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * 64;
+        __syncthreads();
+        // panel p holds rows r0.. contiguously: consecutive threads read
+        // consecutive float4s
+        for (int idx = threadIdx.x; idx < pin * 64 * V_PER_ROW; idx += 256) {
+            const int p = idx / (64 * V_PER_ROW), rem = idx % (64 * V_PER_ROW);
+            const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
+            const int r = r0 + rl;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < n) v = __ldcs(reinterpret_cast<const float4*>(In + (size_t)p * n * KS + (size_t)r * KS + c));
+            float* d = As + rl * lda + p * KS + c;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+        }
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
+        const int c0w = wn * 64;
+        if (c0w < kout) {
+            for (int k0 = 0; k0 < kp; k0 += 8) {
+                const float* ar = As + (wm * 16 + g) * lda + k0 + tq;
+                const float vv[4] = {ar[0], ar[8 * lda], ar[4], ar[8 * lda + 4]};
+                uint32_t ahi[4], alo[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    ahi[q] = to_tf32(vv[q]);
+                    alo[q] = to_tf32(vv[q] - __uint_as_float(ahi[q]));
+                }
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int cb = c0w + j * 8;
+                    if (cb < kout) {
+                        const int bi = (k0 + tq) * LDB + cb + g;
+                        const uint32_t bhi[2] = {Bh[bi], Bh[bi + 4 * LDB]};
+                        const uint32_t blo[2] = {Bl[bi], Bl[bi + 4 * LDB]};
+                        mma_tf32(acc[j], alo, bhi);
+                        mma_tf32(acc[j], ahi, blo);
+                        mma_tf32(acc[j], ahi, bhi);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int r = r0 + wm * 16 + g + ((q & 2) ? 8 : 0);
+                const int c = c0w + j * 8 + 2 * tq + (q & 1);
+                if (r < n && c < kout) {
+                    const size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
+                    float v = acc[j][q];
+                    if (In2) v += In2[o];
+                    Out[o] = v;
+                }
+            }
+    }
+}
+
 template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
                          double coef, cudaStream_t st) {
     if (kout > 128 || kin > 128) return cudaErrorInvalidValue;
-    size_t smem = ((size_t)kin * 128 + 64 * (size_t)kin) * sizeof(T);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int ntiles = (n + 63) / 64;
+    if (sizeof(T) == 4 && kin > 0 && kout > 0 && kin % ks == 0) {
+        // tensor-core path (FP32 data)
+        const int kp = (kin + 7) & ~7;
+        const size_t smem_tc = (2 * (size_t)kp * 136 + 64 * (size_t)(kp + 4)) * 4;
+        dim3 g1(ntiles < sms ? ntiles : sms);
+        const float* Inf = reinterpret_cast<const float*>(In);
+        const float* In2f = reinterpret_cast<const float*>(In2);
+        float* Outf = reinterpret_cast<float*>(Out);
+#define VNE_APPLY_TC(KSV)                                                                                      \
+        if (ks == KSV) {                                                                                      \
+            cudaError_t e = cudaFuncSetAttribute(k_apply_tc<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)smem_tc);                                               \
+            if (e != cudaSuccess) return e;                                                                   \
+            k_apply_tc<KSV><<<g1, 256, smem_tc, st>>>(Inf, kin, M, kout, In2f, Outf, n, coef);                 \
+            return cudaGetLastError();                                                                        \
+        }
+        VNE_APPLY_TC(8)
+        VNE_APPLY_TC(16)
+        VNE_APPLY_TC(32)
+#undef VNE_APPLY_TC
+        return cudaErrorInvalidValue;
+    }
+    size_t smem = ((size_t)kin * 128 + 64 * (size_t)kin) * sizeof(T);
     int per_sm = sizeof(T) == 4 ? 2 : 1;
     dim3 grid(ntiles < sms * per_sm ? ntiles : sms * per_sm);
 #define VNE_APPLY_CASE(KSV)                                                                                  \

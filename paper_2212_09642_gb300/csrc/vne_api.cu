@@ -424,7 +424,7 @@ struct BlockOut {
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
                bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
-               bool interleave = false, bool graph = true) {
+               bool interleave = false, bool graph = true, bool want_psi = true) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
     const int Kp = panels * ks;
@@ -657,8 +657,10 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
         }
     }
     if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[1], st));
-    VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m, SK, psi, st));
-    ctx->launches += 1;
+    if (want_psi) {
+        VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m, SK, psi, st));
+        ctx->launches += 1;
+    }
     out.K = K;
     out.Kp = Kp;
     out.ks = ks;
@@ -1486,8 +1488,9 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     s.col_begin = 0;
     s.ncols = Nr;
     BlockOut sk;
+    // the sketch block only feeds f(A) Omega: its quadratures are not needed
     run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant,
-                 sc.interleave, sc.graph);
+                 sc.interleave, sc.graph, false);
     const int Kp = sk.Kp;
     double* zvec = ws_get_t<double>(ctx, "zvec", (size_t)m * Kp);
     VNE_TRY_CUDA(ctx, launch_tridiag_fvec(sk.alpha, sk.beta, sk.scale, Kp, m, Kp, zvec, st));

@@ -67,3 +67,54 @@ def test_tridiag_quadrature_matches_oracle(vctx):
         kk = m if len(z) == 0 else z[0] + 1
         want = krylov.gauss_quadrature(3.0 * a[c, :kk], 3.0 * bb[:kk - 1], norm2[c])
         assert abs(got[c] - want) <= 1e-12 * abs(want)
+
+
+def _wilkinson_plus(k):
+    n = 2 * k + 1
+    return np.abs(np.arange(n) - k).astype(float) + 1.0, np.ones(n - 1)
+
+
+def _ghost_tridiagonal(g, m, seed):
+    """Lanczos tridiagonal without reorthogonalisation: converged Ritz values
+    reappear as near-identical copies (clusters down to rounding level)."""
+    A, _ = density.density_matrix(g)
+    x = rng.rademacher(seed, g.n, 0, 1)[:, 0]
+    _, al, be = krylov.lanczos_quadform(A, x, m, reorth="none")
+    return np.asarray(al), np.asarray(be[:len(al) - 1])
+
+
+def test_tridiag_quadrature_clusters_and_grading(vctx):
+    """Tight eigenvalue pairs (Wilkinson W+), Lanczos ghost clusters, graded
+    and nearly decoupled tridiagonals, a 1 x 1 block: the quadrature matches
+    the oracle's eigendecomposition to 1e-12 relative."""
+    cases = []
+    for k in (10, 20, 30, 63):
+        a, b = _wilkinson_plus(k)
+        cases.append((a / (a.max() + 2.5), b / (a.max() + 2.5)))
+    g = graphs.barabasi_albert(3000, 3, 1)
+    for m, seed in ((60, 1), (100, 2), (128, 3)):
+        cases.append(_ghost_tridiagonal(g, m, seed))
+    r = np.random.default_rng(11)
+    for _ in range(6):
+        n = int(r.integers(20, 120))
+        cases.append((10.0 ** r.uniform(-8, 0, n), 10.0 ** r.uniform(-10, -1, n - 1)))   # graded
+        cases.append((r.random(n), r.random(n - 1) * 1e-9 + 1e-14))                      # nearly decoupled
+    cases.append((np.array([0.25]), np.zeros(0)))
+    m = max(len(a) for a, _ in cases)
+    count = len(cases)
+    A = np.zeros((count, m))
+    B = np.zeros((count, m))
+    for c, (a, b) in enumerate(cases):
+        A[c, :len(a)] = a
+        B[c, :len(b)] = b
+        # rows past the block stay decoupled: beta = 0 ends it
+    norm2 = np.ones(count)
+    got = vne.vne_tridiag_quadrature(vctx, A, B, norm2, 1.0)
+    again = vne.vne_tridiag_quadrature(vctx, A, B, norm2, 1.0)
+    assert np.array_equal(got, again)
+    for c, (a, b) in enumerate(cases):
+        want = krylov.gauss_quadrature(a, b, 1.0)
+        # eigenvalues are backward stable: an absolute floor of a few ulps of
+        # ||T|| covers graded blocks whose quadrature is tiny
+        tnorm = np.max(np.abs(a) + np.r_[np.abs(b), 0.0] + np.r_[0.0, np.abs(b)])
+        assert abs(got[c] - want) <= 1e-12 * abs(want) + 64 * np.finfo(float).eps * tnorm, (c, len(a), got[c], want)
