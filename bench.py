@@ -133,10 +133,17 @@ def load_peaks():
 
 
 def kernel_digest():
+    """Digest of the step kernel's source: its translation unit, the shared
+    device header and the StepParams layout it is launched with."""
+    csrc = os.path.join(ROOT, "paper_2212_09642_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("kernels_lanczos.cu", "common.cuh", "kernels.h"):
-        with open(os.path.join(ROOT, "paper_2212_09642_gb300", "csrc", f), "rb") as fh:
+    for f in ("kernels_lanczos.cu", "common.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "kernels.h")) as fh:
+        hdr = fh.read()
+    i = hdr.index("struct StepParams")
+    h.update(hdr[i:hdr.index("};", i) + 2].encode())
     return h.hexdigest()[:16]
 
 

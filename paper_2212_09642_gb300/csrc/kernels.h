@@ -166,9 +166,6 @@ template <typename T> cudaError_t launch_block_transform(const BlockTransform<T>
 cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t);
 
 // ---- dense / small kernels (kernels_dense.cu) ----
-// Gauss quadrature of `count` tridiagonals stored column-interleaved:
-// alpha[j*ld + c], beta[j*ld + c] for j < m.  psi[c] = norm2[c] * sum u1^2 f(scale[c] theta).
-// With zvec != NULL also z[j*ld + c] = (U f(scale Theta) U^T e1)_j (warp-per-column kernel).
 // Matrix assembly (assemble.cu).  bad[0] / bad[1]: smallest nonzero index
 // with an out-of-range column / a self-loop (pattern matrices), ~0 if none.
 cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int64_t n, int pattern,
@@ -180,6 +177,9 @@ cudaError_t launch_relabel(const int32_t* rp_old, const int32_t* col_old, const 
                            int32_t* col_new, void* val_new, int fp64, cudaStream_t st);
 cudaError_t launch_convert_values(const double* in, int64_t count, void* out, int fp64, cudaStream_t st);
 
+// Gauss quadrature of `count` tridiagonals stored column-interleaved:
+// alpha[j*ld + c], beta[j*ld + c] for j < m.  psi[c] = norm2[c] * sum u1^2 f(scale[c] theta).
+// With zvec != NULL also z[j*ld + c] = (U f(scale Theta) U^T e1)_j (warp-per-column kernel).
 cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t);

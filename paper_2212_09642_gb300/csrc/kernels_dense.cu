@@ -398,15 +398,31 @@ __device__ void quad_by_qr(const double* sa, const double* sb, int n, double sc,
     *out = ok ? norm2 * s : nan("");
 }
 
+// Shared state of the spectral kernels for one tridiagonal (one warp).
 template <int MAXM>
-__global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
-                                                     const double* __restrict__ norm2, const double* __restrict__ scale,
-                                                     int count, int m, int ld, double* __restrict__ psi) {
-    __shared__ double sa[MAXM], sb[MAXM], sb2[MAXM + 1], sth[MAXM];
-    __shared__ float sa32[MAXM], sb2_32[MAXM + 1];
-    extern __shared__ double piv[];  // [2][MAXM][32]: twisted pivots, transposed per lane
-    const int c = blockIdx.x, lane = threadIdx.x;
-    if (c >= count) return;
+struct TqShared {
+    double a[MAXM], b[MAXM], b2[MAXM + 1];  // scaled block, b2[k] = beta_{k-1}^2
+    double th[MAXM], bw[MAXM];              // eigenvalues (ascending), bracket widths
+    float a32[MAXM], b2_32[MAXM + 1];
+    double cc[MAXM / 2], rho[MAXM / 2], half[MAXM / 2];  // clusters: centre, circle radius, half-width
+    int gfirst[MAXM + 1], glast[MAXM], cl_of_group[MAXM];
+    int ngroups, ncl, fallback, n;
+    double span, s2, pivmin;
+};
+
+// Eigenvalues and their grouping for the leading unreduced block of
+// tridiagonal c (all 32 lanes call it).  Returns false if the block has a
+// non-finite entry.
+template <int MAXM>
+__device__ bool tq_spectrum(const double* __restrict__ alpha, const double* __restrict__ beta, int c, int m, int ld,
+                            int lane, TqShared<MAXM>& S) {
+    double* sa = S.a;
+    double* sb = S.b;
+    double* sb2 = S.b2;
+    double* sth = S.th;
+    double* sbw = S.bw;
+    float* sa32 = S.a32;
+    float* sb2_32 = S.b2_32;
     // leading unreduced block: n = 1 + first j with beta_j == 0
     int n = m;
     for (int j0 = 0; j0 < m - 1; j0 += 32) {
@@ -445,10 +461,7 @@ __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ 
     }
     finite = __all_sync(0xffffffffu, finite);
     __syncwarp();
-    if (!finite) {
-        if (lane == 0) psi[c] = nan("");
-        return;
-    }
+    if (!finite) return false;
     // scale the block by the power of two s2 that brings its Gershgorin
     // radius to [1, 2) (exact: eigenvalues scale by s2, weights do not), so
     // the unnormalised Sturm recurrences stay far from overflow
@@ -472,7 +485,6 @@ __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ 
     //    j = l + 32 r, r < R (the last lanes carry a dummy root when n < 32 R,
     //    so the warp stays converged).
     constexpr int R = MAXM / 32;
-    __shared__ double sbw[MAXM];  // final bracket width of each root
     double lo[R], hi[R];
     int clo[R], chi[R];  // Sturm counts at lo and hi
     {
@@ -596,12 +608,13 @@ __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ 
     //    eigenvalues, the others clusters.  A cluster closer than 16 x its
     //    half-width to a neighbouring group sends the column to the
     //    sequential QR.
-    const double sc = scale[c] / s2;  // f is applied to the unscaled eigenvalues
     const double tau = kClusterGap * span;
-    constexpr int MAXC = MAXM / 2;
-    __shared__ double s_cc[MAXC], s_rho[MAXC], s_half[MAXC];
-    __shared__ int s_gfirst[MAXM + 1], s_glast[MAXM], s_cl_of_group[MAXM];
-    __shared__ int s_ngroups, s_ncl, s_fallback;
+    double* s_cc = S.cc;
+    double* s_rho = S.rho;
+    double* s_half = S.half;
+    int* s_gfirst = S.gfirst;
+    int* s_glast = S.glast;
+    int* s_cl_of_group = S.cl_of_group;
     if (lane == 0) {
         auto halfw = [&](int f, int l) {
             double h = 0.5 * (sth[l] - sth[f]);
@@ -646,13 +659,43 @@ __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ 
             s_cl_of_group[g] = ncl++;
         }
         s_gfirst[ng] = n;
-        s_ngroups = ng;
-        s_ncl = ncl;
-        s_fallback = fb;
+        S.ngroups = ng;
+        S.ncl = ncl;
+        S.fallback = fb;
+        S.n = n;
+        S.span = span;
+        S.s2 = s2;
+        S.pivmin = pivmin;
     }
     __syncwarp();
-    const int ngroups = s_ngroups, ncl = s_ncl;
-    if (s_fallback) {
+    return true;
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                                     const double* __restrict__ norm2, const double* __restrict__ scale,
+                                                     int count, int m, int ld, double* __restrict__ psi) {
+    __shared__ TqShared<MAXM> S;
+    extern __shared__ double piv[];  // [2][MAXM][32]: twisted pivots, transposed per lane
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= count) return;
+    if (!tq_spectrum<MAXM>(alpha, beta, c, m, ld, lane, S)) {
+        if (lane == 0) psi[c] = nan("");
+        return;
+    }
+    const int n = S.n;
+    const double span = S.span, pivmin = S.pivmin;
+    const double* sa = S.a;
+    const double* sb = S.b;
+    const double* sth = S.th;
+    const double* s_cc = S.cc;
+    const double* s_rho = S.rho;
+    const double* s_half = S.half;
+    const int* s_gfirst = S.gfirst;
+    const int* s_cl_of_group = S.cl_of_group;
+    const double sc = scale[c] / S.s2;  // f is applied to the unscaled eigenvalues
+    const int ngroups = S.ngroups, ncl = S.ncl;
+    if (S.fallback) {
         quad_by_qr<MAXM>(sa, sb, n, sc, norm2[c], lane, psi + c);
         return;
     }
@@ -714,63 +757,188 @@ __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ 
         errb += __shfl_xor_sync(0xffffffffu, errb, off);
     }
     if (!(errb <= 1e-10 * fabs(acc))) {
-        if (lane == 0) s_fallback = 1;
+        if (lane == 0) S.fallback = 1;
     } else if (lane == 0) {
         // the weights sum to one; dividing by the computed sum removes their
         // common rounding
         psi[c] = norm2[c] * (acc / wsum);
     }
     __syncwarp();
-    if (s_fallback) quad_by_qr<MAXM>(sa, sb, n, sc, norm2[c], lane, psi + c);
+    if (S.fallback) quad_by_qr<MAXM>(sa, sb, n, sc, norm2[c], lane, psi + c);
 }
 
-// warp per column; dynamic smem: Z [m][m] (row-major) per warp (1 warp / CTA).
-// Every lane runs the scalar recurrence on its own copies (uniform control
-// flow) and rotates the rows of Z it owns (rows lane, lane + 32, ...).
-template <int R>
-__global__ void k_tridiag_fvec(const double* __restrict__ alpha, const double* __restrict__ beta,
-                               const double* __restrict__ scale, int count, int m, int ld,
-                               double* __restrict__ zvec) {
-    extern __shared__ double sm[];
-    double* Z = sm;              // m*m
-    double* d = sm + m * m;      // m
-    double* e = d + m;           // m
-    const int c = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (c >= count) return;
-    for (int idx = lane; idx < m * m; idx += 32) Z[idx] = ((idx / m) == (idx % m)) ? 1.0 : 0.0;
-    for (int j = lane; j < m; j += 32) {
-        d[j] = alpha[(size_t)j * ld + c];
-        e[j] = (j + 1 < m) ? beta[(size_t)j * ld + c] : 0.0;
-    }
-    __syncwarp();
-    int n = m;
-    for (int j = 0; j + 1 < m; j++)
-        if (e[j] == 0.0) {
-            n = j + 1;
-            break;
-        }
-    double dl[128], el[128];
+// f(T) e1 by the sequential implicit QR with the full eigenvector matrix Z
+// (n x n, row-major, in shared memory): every lane runs the scalar
+// recurrence on its own copies (uniform control flow) and rotates the rows of
+// Z it owns (rows lane, lane + 32, ...).  Fallback of k_tridiag_fvec.
+template <int MAXM>
+__device__ void fvec_by_qr(const double* sa, const double* sb, int n, int m, double sc, int lane, double* Z,
+                           double* __restrict__ zvec, int ld, int c) {
+    constexpr int R = MAXM / 32;
+    for (int idx = lane; idx < n * n; idx += 32) Z[idx] = ((idx / n) == (idx % n)) ? 1.0 : 0.0;
+    double dl[MAXM], el[MAXM];
     for (int j = 0; j < n; j++) {
-        dl[j] = d[j];
-        el[j] = e[j];
+        dl[j] = sa[j];
+        el[j] = sb[j];
     }
     double* rows[R];
     int nr = 0;
     for (int q = 0; q < R; q++) {
         const int row = lane + 32 * q;
-        rows[q] = Z + (size_t)(row < n ? row : 0) * m;
+        rows[q] = Z + (size_t)(row < n ? row : 0) * n;
         if (row < n) nr = q + 1;
     }
     __syncwarp();
-    bool ok = symtri_qr_rows<R>(dl, el, n, rows, nr);
+    const bool ok = symtri_qr_rows<R>(dl, el, n, rows, nr);
     __syncwarp();
-    double sc = scale[c];
     for (int row = lane; row < m; row += 32) {
         double acc = 0.0;
         if (row < n)
-            for (int k = 0; k < n; k++) acc += Z[row * m + k] * f_entropy(sc * dl[k]) * Z[k];
+            for (int k = 0; k < n; k++) acc += Z[row * n + k] * f_entropy(sc * dl[k]) * Z[k];
         zvec[(size_t)row * ld + c] = ok ? acc : nan("");
+    }
+}
+
+// f(T) e1 = sum_j u_j u_{1j} f(sigma theta_j) for the matrix-function
+// recovery of the Hutch++ sketch (eq. rational-krylov-approximation-matvec),
+// with the spectrum of k_tridiag_quad: an isolated eigenvalue adds its
+// twisted-factorisation eigenvector z scaled by z_1 f / ||z||^2; a cluster
+// adds (1/2 pi i) \oint (f(c) + f'(c)(z - c) + f''(c)(z - c)^2 / 2)
+// (z I - T)^{-1} e1 dz by the 32-point trapezoid rule (one point per lane;
+// the resolvent vector from the bottom-up continued fraction, then the
+// forward ratios x_k = x_{k-1} beta_{k-1} / g_k).  Each lane accumulates its
+// own column of a [n][32] buffer, summed in lane order at the end.
+template <int MAXM>
+__global__ void __launch_bounds__(32) k_tridiag_fvec(const double* __restrict__ alpha,
+                                                     const double* __restrict__ beta,
+                                                     const double* __restrict__ scale, int count, int m, int ld,
+                                                     double* __restrict__ zvec) {
+    __shared__ TqShared<MAXM> S;
+    extern __shared__ double piv[];  // [2][MAXM][32] pivots / resolvent, [MAXM][32] partial sums
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= count) return;
+    if (!tq_spectrum<MAXM>(alpha, beta, c, m, ld, lane, S)) {
+        for (int row = lane; row < m; row += 32) zvec[(size_t)row * ld + c] = nan("");
+        return;
+    }
+    const int n = S.n;
+    const double span = S.span, pivmin = S.pivmin;
+    const double* sa = S.a;
+    const double* sb = S.b;
+    const double* sth = S.th;
+    const double sc = scale[c] / S.s2;  // f is applied to the unscaled eigenvalues
+    if (S.fallback) {
+        fvec_by_qr<MAXM>(sa, sb, n, m, sc, lane, piv, zvec, ld, c);
+        return;
+    }
+    double* Dp = piv + lane;                // this lane's pivots / real parts
+    double* Rp = piv + MAXM * 32 + lane;    // this lane's pivots / imaginary parts
+    double* ys = piv + 2 * MAXM * 32 + lane;  // this lane's partial sum of y
+    for (int k = 0; k < n; k++) ys[k * 32] = 0.0;
+    // isolated eigenvalues
+    for (int g = lane; g < S.ngroups; g += 32) {
+        if (S.cl_of_group[g] >= 0) continue;
+        const double th = sth[S.gfirst[g]];
+        double d = 0.0;
+        for (int k = 0; k < n; k++) {
+            d = guard_pivot((sa[k] - th) - (k > 0 ? sb[k - 1] * sb[k - 1] / d : 0.0), pivmin);
+            Dp[k * 32] = d;
+        }
+        double r = 0.0, best = INFINITY;
+        int tw = n - 1;
+        for (int k = n - 1; k >= 0; k--) {
+            r = guard_pivot((sa[k] - th) - (k + 1 < n ? sb[k] * sb[k] / r : 0.0), pivmin);
+            Rp[k * 32] = r;
+            const double gam = fabs(Dp[k * 32] + r - (sa[k] - th));
+            if (gam < best) {
+                best = gam;
+                tw = k;
+            }
+        }
+        // eigenvector components overwrite the pivots they were made from
+        double nrm = 1.0, z = 1.0;
+        for (int k = tw - 1; k >= 0; k--) {
+            z = -sb[k] * z / Dp[k * 32];
+            Dp[k * 32] = z;
+            nrm = fma(z, z, nrm);
+        }
+        const double z1 = tw > 0 ? z : 1.0;
+        z = 1.0;
+        for (int k = tw + 1; k < n; k++) {
+            z = -sb[k - 1] * z / Rp[k * 32];
+            Rp[k * 32] = z;
+            nrm = fma(z, z, nrm);
+        }
+        const double coef = z1 * f_entropy(sc * th) / nrm;
+        for (int k = 0; k < n; k++) {
+            const double zk = k < tw ? Dp[k * 32] : (k == tw ? 1.0 : Rp[k * 32]);
+            ys[k * 32] += coef * zk;
+        }
+    }
+    // clusters: one round per cluster, contour point q on lane q
+    double errb = 0.0;
+    for (int cl = 0; cl < S.ncl; cl++) {
+        const double cc = S.cc[cl], rho = S.rho[cl], half = S.half[cl];
+        double sph, cph;
+        sincospi((2.0 * lane + 1.0) / kContourPoints, &sph, &cph);
+        const double dzr = rho * cph, dzi = rho * sph;
+        const double zr = cc + dzr, zi = dzi;
+        // bottom-up continued fraction g_k, stored
+        double gr = zr - sa[n - 1], gi = zi;
+        Dp[(n - 1) * 32] = gr;
+        Rp[(n - 1) * 32] = gi;
+        for (int k = n - 2; k >= 0; k--) {
+            const double t = sb[k] * sb[k] / (gr * gr + gi * gi);
+            gr = (zr - sa[k]) - t * gr;
+            gi = zi + t * gi;
+            Dp[k * 32] = gr;
+            Rp[k * 32] = gi;
+        }
+        // Taylor weight h = dz (f0 + f1 dz + f2 dz^2 / 2) of the cluster centre
+        const double x0 = sc * cc;
+        const double f0 = f_entropy(x0);
+        const double f1 = x0 > 0.0 ? sc * (-log(x0) - 1.0) : 0.0;
+        const double f2 = cc > 0.0 ? -sc / cc : 0.0;
+        const double d2r = dzr * dzr - dzi * dzi, d2i = 2.0 * dzr * dzi;
+        const double pr = f0 + f1 * dzr + 0.5 * f2 * d2r, pi = f1 * dzi + 0.5 * f2 * d2i;
+        const double hr = (dzr * pr - dzi * pi) / kContourPoints, hi = (dzr * pi + dzi * pr) / kContourPoints;
+        // forward ratios: x_0 = 1 / g_0, x_k = x_{k-1} beta_{k-1} / g_k
+        double xr, xi;
+        {
+            const double den = gr * gr + gi * gi;
+            xr = gr / den;
+            xi = -gi / den;
+        }
+        double wq = (xr * dzr - xi * dzi) / kContourPoints;  // Re x_0 dz / K
+        ys[0] += xr * hr - xi * hi;
+        for (int k = 1; k < n; k++) {
+            const double g_r = Dp[k * 32], g_i = Rp[k * 32];
+            const double den = g_r * g_r + g_i * g_i;
+            const double ur = sb[k - 1] * g_r / den, ui = -sb[k - 1] * g_i / den;  // beta / g
+            const double nxr = xr * ur - xi * ui, nxi = xr * ui + xi * ur;
+            xr = nxr;
+            xi = nxi;
+            ys[k * 32] += xr * hr - xi * hi;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) wq += __shfl_xor_sync(0xffffffffu, wq, off);
+        if (half > 1e-3 * fabs(cc))  // cluster at the origin: error below W f(c + half)
+            errb += fmax(wq, 0.0) * f_entropy(fmin(sc * fmax(cc + half, 0.0), 0.36787944117144233));
+    }
+    __syncwarp();
+    // y_k = sum over lanes of the partial sums, in lane order
+    double y0 = 0.0;
+    for (int k = lane; k < m; k += 32) {
+        double y = 0.0;
+        if (k < n)
+            for (int l = 0; l < 32; l++) y += piv[2 * MAXM * 32 + k * 32 + l];
+        if (k == 0) y0 = y;
+        zvec[(size_t)k * ld + c] = y;
+    }
+    y0 = __shfl_sync(0xffffffffu, y0, 0);
+    if (!(errb <= 1e-10 * fabs(y0))) {
+        __syncwarp();
+        fvec_by_qr<MAXM>(sa, sb, n, m, sc, lane, piv, zvec, ld, c);
     }
 }
 
@@ -799,18 +967,24 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
 cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col, int count,
                                 int m, int ld, double* zvec, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    if (m > 128) return cudaErrorInvalidValue;
-    size_t smem = ((size_t)m * m + 2 * m) * sizeof(double);
-    if (m <= 64) {
-        cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tridiag_fvec<2><<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tridiag_fvec<4><<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);
+    // one warp (CTA) per tridiagonal; dynamic shared memory: pivots /
+    // resolvent and the lanes' partial sums (3 x MM x 32 doubles), or Z for
+    // the QR fallback (MM x MM)
+#define VNE_FVEC_CASE(MM)                                                                                    \
+    if (m <= MM) {                                                                                          \
+        const int words = 3 * MM * 32 > MM * MM ? 3 * MM * 32 : MM * MM;                                    \
+        const int smem = words * (int)sizeof(double);                                                       \
+        cudaError_t e = cudaFuncSetAttribute(k_tridiag_fvec<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             smem);                                                         \
+        if (e != cudaSuccess) return e;                                                                     \
+        k_tridiag_fvec<MM><<<count, 32, smem, st>>>(alpha, beta, scale_per_col, count, m, ld, zvec);         \
+        return cudaGetLastError();                                                                          \
     }
-    return cudaGetLastError();
+    VNE_FVEC_CASE(32)
+    VNE_FVEC_CASE(64)
+    VNE_FVEC_CASE(128)
+#undef VNE_FVEC_CASE
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
