@@ -274,6 +274,10 @@ def run_native(args):
     for w in range(args.warmup):
         one(seed0 + w)
     torch.cuda.synchronize(dev)
+    # ceiling of the step kernel's access pattern: random row gathers from a
+    # table of one panel (n x panel FP32), untimed
+    ks = int(tuned_cfg["panel"]) or 16
+    probe_gbs = vne.vne_measure_gather(ctx, g.n * ks * 4, ks * 4, 32 << 20, 0, 3)
 
     def barrier():
         if world > 1:
@@ -340,6 +344,7 @@ def run_native(args):
         vne.vne_ctx_destroy(ctx)
         return
 
+    n_, nnz_, tr_, nb_ = vne.vne_matrix_info(mat)
     peak, peak_kind = load_peaks()
     cnt, ms, byts = kst["step"]
     achieved = (byts / (ms / 1e3)) / 1e9 if ms > 0 else None
@@ -349,6 +354,18 @@ def run_native(args):
             "peak_kind": peak_kind, "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
             "avg_launch_ms": ms / cnt if cnt else None, "launches_timed": int(cnt),
             "share_of_step_time": (ms / elapsed_ms) if elapsed_ms else None}
+    # the same launches counted by what they move through L2: every nonzero
+    # gathers one row of KS columns per panel, besides the streams
+    kp_s = -(-N_SKETCH // ks) * ks
+    kp_avg = (kp_s + kp_s + -(-N_HUTCH // ks) * ks) / 2 if args.estimator == "hutchpp" else -(-args.vectors // ks) * ks
+    gathered = float(nnz_) * kp_avg * 4
+    l2_bytes = gathered + (per_launch_bytes - g.n * kp_avg * 4 if per_launch_bytes else 0.0)
+    roof["l2_gather"] = {"gathered_bytes_per_launch": gathered, "l2_bytes_per_launch": l2_bytes,
+                         "achieved_gbs": l2_bytes / (ms / cnt / 1e3) / 1e9 if cnt and ms > 0 else None,
+                         "probe_gbs": probe_gbs,
+                         "frac": (l2_bytes / (ms / cnt / 1e3) / 1e9) / probe_gbs if cnt and ms > 0 else None,
+                         "probe": f"random {ks * 4}-byte row gathers from a {g.n * ks * 4 / 2**20:.0f} MiB table "
+                                  f"(vne_measure_gather)"}
     ucnt, ums, ubytes = kst["update"]
     update = {"achieved_gbs": (ubytes / (ums / 1e3)) / 1e9 if ums > 0 else None,
               "avg_launch_ms": ums / ucnt if ucnt else None, "share_of_step_time": ums / elapsed_ms}
@@ -361,7 +378,6 @@ def run_native(args):
                          "n x 100 orthonormalisation/projection, extrapolated to 100 + 200 Krylov runs",
                "detail_s": parts}
 
-    n_, nnz_, tr_, nb_ = vne.vne_matrix_info(mat)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,

@@ -122,6 +122,14 @@ vne_status vne_ctx_stats(const vne_ctx *ctx, int64_t *launches, double *kernel_s
  * (*replayed, including the replay right after a capture).  Either pointer
  * may be NULL.  EINVAL for a null context. */
 vne_status vne_ctx_graph_stats(const vne_ctx *ctx, int64_t *captured, int64_t *replayed);
+/* Throughput ceiling of the SpMM step's access pattern (a measurement aid, not
+ * part of the method): `gathers` reads of random row_bytes-byte rows (32, 64
+ * or 128) from a device table of table_bytes, plus one streaming read of
+ * stream_bytes, on the context's stream; *gather_gbs = gathered bytes per
+ * second (GB/s), best of `reps` >= 1 launches after one warm-up.  The buffers
+ * are context workspace (kept until vne_ctx_destroy).  EINVAL for bad sizes. */
+vne_status vne_measure_gather(vne_ctx *ctx, uint64_t table_bytes, int32_t row_bytes, uint64_t gathers,
+                              uint64_t stream_bytes, int32_t reps, double *gather_gbs);
 
 /* ---- density matrix (Section 2, eq. graph_laplacian) ------------------ */
 /* Copy a symmetric CSR matrix to the device.

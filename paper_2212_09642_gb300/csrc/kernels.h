@@ -166,6 +166,12 @@ template <typename T> cudaError_t launch_block_transform(const BlockTransform<T>
 cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t);
 
 // ---- dense / small kernels (kernels_dense.cu) ----
+// Measurement (measure.cu): `count` random gathers of row_bytes-byte rows
+// (32, 64 or 128) from the first table_bytes of `table`, plus one streaming
+// read of stream_bytes from `stream`; both buffers must be zero-filled.
+cudaError_t launch_gather_probe(const void* table, uint64_t table_bytes, int row_bytes, uint64_t count, uint32_t seed,
+                                const void* stream, uint64_t stream_bytes, float* sink, cudaStream_t st);
+
 // Matrix assembly (assemble.cu).  bad[0] / bad[1]: smallest nonzero index
 // with an out-of-range column / a self-loop (pattern matrices), ~0 if none.
 cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int64_t n, int pattern,

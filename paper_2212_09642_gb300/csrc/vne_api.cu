@@ -1858,6 +1858,38 @@ extern "C" vne_status vne_ctx_graph_stats(const vne_ctx* ctx, int64_t* captured,
     return VNE_OK;
 }
 
+extern "C" vne_status vne_measure_gather(vne_ctx* ctx, uint64_t table_bytes, int32_t row_bytes, uint64_t gathers,
+                                         uint64_t stream_bytes, int32_t reps, double* gather_gbs) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, gather_gbs && reps >= 1 && gathers >= 1, VNE_EINVAL, "need gather_gbs, reps >= 1, gathers >= 1");
+    VNE_REQUIRE(ctx, row_bytes == 32 || row_bytes == 64 || row_bytes == 128, VNE_EINVAL, "row_bytes must be 32, 64 or 128");
+    VNE_REQUIRE(ctx, table_bytes >= (uint64_t)row_bytes && table_bytes / row_bytes <= 0xffffffffull, VNE_EINVAL,
+                "table size out of range");
+    cudaStream_t st = ctx->stream;
+    void* table = ws_get(ctx, "probe.table", table_bytes);
+    void* stream = ws_get(ctx, "probe.stream", std::max<uint64_t>(stream_bytes, 16));
+    float* sink = ws_get_t<float>(ctx, "probe.sink", 1);
+    for (int i = 0; i < 2; i++)
+        if (!ctx->loop_ev[i]) VNE_TRY_CUDA(ctx, cudaEventCreate(&ctx->loop_ev[i]));
+    cudaEvent_t e0 = ctx->loop_ev[0], e1 = ctx->loop_ev[1];
+    double best = 1e300;
+    for (int r = 0; r <= reps; r++) {
+        VNE_TRY_CUDA(ctx, cudaEventRecord(e0, st));
+        VNE_TRY_CUDA(ctx, launch_gather_probe(table, table_bytes, row_bytes, gathers, 977u * r + 1u, stream,
+                                              stream_bytes, sink, st));
+        VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
+        VNE_TRY_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VNE_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) best = std::min(best, (double)ms);
+    }
+    ctx->launches += reps + 1;
+    *gather_gbs = (double)gathers * row_bytes / (best * 1e-3) / 1e9;
+    VNE_API_END(ctx)
+}
+
 extern "C" vne_status vne_ctx_stats(const vne_ctx* ctx, int64_t* launches, double* kernel_stats) {
     if (!ctx) return VNE_EINVAL;
     if (launches) *launches = ctx->launches;

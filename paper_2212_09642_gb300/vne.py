@@ -100,6 +100,8 @@ def _declare(lib):
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
         "vne_ctx_graph_stats": (st, [_P, _PI64, _PI64]),
+        "vne_measure_gather": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_int32, _PD]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -130,7 +132,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
-               "vne_ctx_graph_stats", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
+               "vne_ctx_graph_stats", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
                "vne_server_result", "vne_server_info"]
 
@@ -341,6 +343,14 @@ def vne_ctx_graph_stats(ctx):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().vne_ctx_graph_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
     return a.value, b.value
+
+
+def vne_measure_gather(ctx, table_bytes, row_bytes, gathers, stream_bytes=0, reps=3):
+    """GB/s of random row gathers from a table of table_bytes (plus a concurrent stream)."""
+    g = ctypes.c_double()
+    _check(load().vne_measure_gather(ctx, int(table_bytes), int(row_bytes), int(gathers), int(stream_bytes),
+                                     int(reps), ctypes.byref(g)), ctx)
+    return g.value
 
 
 def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, krylov_steps, psi_dev):

@@ -118,3 +118,10 @@ def test_tridiag_quadrature_clusters_and_grading(vctx):
         # ||T|| covers graded blocks whose quadrature is tiny
         tnorm = np.max(np.abs(a) + np.r_[np.abs(b), 0.0] + np.r_[0.0, np.abs(b)])
         assert abs(got[c] - want) <= 1e-12 * abs(want) + 64 * np.finfo(float).eps * tnorm, (c, len(a), got[c], want)
+
+
+def test_measure_gather_probe(vctx):
+    gbs = vne.vne_measure_gather(vctx, 16 << 20, 64, 1 << 20, 0, 1)
+    assert gbs > 0
+    with pytest.raises(vne.VneError):
+        vne.vne_measure_gather(vctx, 16 << 20, 48, 1 << 20, 0, 1)
