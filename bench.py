@@ -133,13 +133,19 @@ def load_peaks():
 
 
 def kernel_digest():
-    """Digest of the step kernel's source: its translation unit, the shared
-    device header and the StepParams layout it is launched with."""
+    """Digest of the step kernel's source: the k_step template and its
+    launcher, the shared device header and the StepParams layout."""
     csrc = os.path.join(ROOT, "paper_2212_09642_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels_lanczos.cu")) as fh:
+        src = fh.read()
+    i = src.index("template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE")
+    j = src.index("// ------------", i)
+    k = src.index("cudaError_t launch_step(")
     h = hashlib.sha256()
-    for f in ("kernels_lanczos.cu", "common.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+    h.update(src[i:j].encode())
+    h.update(src[k:src.index("\n}\n", k)].encode())
+    with open(os.path.join(csrc, "common.cuh"), "rb") as fh:
+        h.update(fh.read())
     with open(os.path.join(csrc, "kernels.h")) as fh:
         hdr = fh.read()
     i = hdr.index("struct StepParams")
@@ -359,7 +365,9 @@ def run_native(args):
     kp_s = -(-N_SKETCH // ks) * ks
     kp_avg = (kp_s + kp_s + -(-N_HUTCH // ks) * ks) / 2 if args.estimator == "hutchpp" else -(-args.vectors // ks) * ks
     gathered = float(nnz_) * kp_avg * 4
-    l2_bytes = gathered + (per_launch_bytes - g.n * kp_avg * 4 if per_launch_bytes else 0.0)
+    csr_bytes = 4.0 * (g.n + 1) + 4.0 * float(nnz_)
+    # gathers + the CSR once per panel + own rows of w_j, w_{j-1} and u
+    l2_bytes = gathered + (kp_avg / ks) * csr_bytes + 3.0 * g.n * kp_avg * 4
     roof["l2_gather"] = {"gathered_bytes_per_launch": gathered, "l2_bytes_per_launch": l2_bytes,
                          "achieved_gbs": l2_bytes / (ms / cnt / 1e3) / 1e9 if cnt and ms > 0 else None,
                          "probe_gbs": probe_gbs,

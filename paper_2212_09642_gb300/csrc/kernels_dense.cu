@@ -1431,46 +1431,64 @@ cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const 
 // that Y Minv has orthonormal columns in exact arithmetic.
 __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, double* __restrict__ Minv,
                           int* __restrict__ rank_out) {
-    extern __shared__ double A[];  // k*k
+    extern __shared__ double A[];  // k x (k + 1): odd row stride against bank conflicts
+    const int ld = k + 1;
     __shared__ int piv[128];
     __shared__ int s_p, s_rank;
     __shared__ double s_max0;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) A[idx] = G[idx];
+    // symmetric part of G (the Gram partial sums of (a, b) and (b, a) may
+    // round differently)
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int a = idx / k, b = idx % k;
+        A[a * ld + b] = 0.5 * (G[idx] + G[b * k + a]);
+    }
     for (int i = threadIdx.x; i < k; i += blockDim.x) piv[i] = i;
     __syncthreads();
     if (threadIdx.x == 0) {
         double mx = 0.0;
-        for (int i = 0; i < k; i++) mx = fmax(mx, A[i * k + i]);
+        for (int i = 0; i < k; i++) mx = fmax(mx, A[i * ld + i]);
         s_max0 = mx;
         s_rank = k;
     }
     __syncthreads();
     for (int j = 0; j < k; j++) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // largest remaining diagonal entry (warp argmax, ties to the lower index)
+            double best = -INFINITY;
             int p = j;
-            double best = A[j * k + j];
-            for (int i = j + 1; i < k; i++)
-                if (A[i * k + i] > best) {
-                    best = A[i * k + i];
+            for (int i = j + (int)threadIdx.x; i < k; i += 32)
+                if (A[i * ld + i] > best) {
+                    best = A[i * ld + i];
                     p = i;
                 }
-            s_p = (best > tol * s_max0 && best > 0.0) ? p : -1;
-            if (s_p < 0) s_rank = j;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int op = __shfl_xor_sync(0xffffffffu, p, off);
+                if (ob > best || (ob == best && op < p)) {
+                    best = ob;
+                    p = op;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_p = (best > tol * s_max0 && best > 0.0) ? p : -1;
+                if (s_p < 0) s_rank = j;
+            }
         }
         __syncthreads();
         const int p = s_p;
         if (p < 0) break;
         if (p != j) {
             for (int i = threadIdx.x; i < k; i += blockDim.x) {  // swap rows
-                double t = A[j * k + i];
-                A[j * k + i] = A[p * k + i];
-                A[p * k + i] = t;
+                double t = A[j * ld + i];
+                A[j * ld + i] = A[p * ld + i];
+                A[p * ld + i] = t;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < k; i += blockDim.x) {  // swap columns
-                double t = A[i * k + j];
-                A[i * k + j] = A[i * k + p];
-                A[i * k + p] = t;
+                double t = A[i * ld + j];
+                A[i * ld + j] = A[i * ld + p];
+                A[i * ld + p] = t;
             }
             if (threadIdx.x == 0) {
                 int t = piv[j];
@@ -1479,15 +1497,23 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
             }
             __syncthreads();
         }
-        const double rjj = sqrt(A[j * k + j]);
+        const double rjj = sqrt(A[j * ld + j]);
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[j * k + i] /= rjj;
-        if (threadIdx.x == 0) A[j * k + j] = rjj;
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[j * ld + i] /= rjj;
+        if (threadIdx.x == 0) A[j * ld + j] = rjj;
         __syncthreads();
+        // rank-1 update of the trailing block: the upper triangle (a warp per
+        // row), mirrored into the lower one for later pivot swaps
         const int rem = k - j - 1;
-        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-            int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
-            A[a * k + b] -= A[j * k + a] * A[j * k + b];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+        for (int a = warp; a < rem; a += nwarp) {
+            const int ga = j + 1 + a;
+            const double la = A[j * ld + ga];
+            for (int gb = ga + lane; gb < k; gb += 32) {
+                const double v = A[ga * ld + gb] - la * A[j * ld + gb];
+                A[ga * ld + gb] = v;
+                A[gb * ld + ga] = v;
+            }
         }
         __syncthreads();
     }
@@ -1495,14 +1521,22 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
     const int r = s_rank;
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) Minv[idx] = 0.0;
     __syncthreads();
-    // R^{-1} column by column (back substitution), one thread per column
+    // R^{-1} column by column (back substitution), one thread per column; the
+    // inner products use four partial sums to shorten the dependent chain
     for (int c = threadIdx.x; c < r; c += blockDim.x) {
         double x[128];
-        x[c] = 1.0 / A[c * k + c];
+        x[c] = 1.0 / A[c * ld + c];
         for (int i = c - 1; i >= 0; i--) {
-            double s = 0.0;
-            for (int l = i + 1; l <= c; l++) s += A[i * k + l] * x[l];
-            x[i] = -s / A[i * k + i];
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int l = i + 1;
+            for (; l + 3 <= c; l += 4) {
+                s0 = fma(A[i * ld + l], x[l], s0);
+                s1 = fma(A[i * ld + l + 1], x[l + 1], s1);
+                s2 = fma(A[i * ld + l + 2], x[l + 2], s2);
+                s3 = fma(A[i * ld + l + 3], x[l + 3], s3);
+            }
+            for (; l <= c; l++) s0 = fma(A[i * ld + l], x[l], s0);
+            x[i] = -((s0 + s1) + (s2 + s3)) / A[i * ld + i];
         }
         for (int i = 0; i <= c; i++) Minv[(size_t)piv[i] * k + c] = x[i];
     }
@@ -1511,7 +1545,7 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
 
 cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, cudaStream_t st) {
     if (k > 128 || k <= 0) return cudaErrorInvalidValue;
-    size_t smem = (size_t)k * k * sizeof(double);
+    size_t smem = (size_t)k * (k + 1) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_chol_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_chol_qr<<<1, 256, smem, st>>>(G, k, tol, Minv, rank);

@@ -106,6 +106,55 @@ __device__ __forceinline__ double source_value_panel(const StartSource& S, const
     return source_value(S, r, id, gc, seg);
 }
 
+// Source value in the vector precision: FP32 blocks take the value in FP32
+// (exact for Rademacher and indicator entries), so the start passes do no
+// FP64 arithmetic per entry.
+template <typename T, int KS>
+__device__ __forceinline__ T source_value_t(const StartSource& S, const T* panel_src, int r, int id, int gc,
+                                            int n_total, int seg) {
+    if (sizeof(T) == 8) return (T)source_value_panel<T, KS>(S, panel_src, r, id, gc, n_total, seg);
+    if (gc >= S.ncols) return (T)0;
+    switch (S.kind) {
+        case SRC_RADEMACHER: {
+            const uint64_t s = S.seg_seed ? S.seg_seed[seg] : S.seed_mixed;
+            const uint64_t col = S.seg_seed ? (uint64_t)(S.seg_col0[seg] + gc) : (uint64_t)(S.col_begin + gc);
+            const uint64_t h = mix64((((col << 32) | (uint64_t)id) ^ s) + 0x9E3779B97F4A7C15ULL);
+            return (h >> 63) ? (T)-1 : (T)1;
+        }
+        case SRC_INDICATOR:
+            return (S.colors[id] == S.col_begin + gc) ? (T)1 : (T)0;
+        case SRC_DENSE64:
+            return (T)S.dense[(size_t)id * S.ld + gc];
+        case SRC_PANEL:
+            return panel_src[(size_t)(gc / KS) * n_total * KS + (size_t)r * KS + (gc % KS)];
+        default:
+            return (T)0;
+    }
+}
+
+// Per-thread sum over its rows: FP64 throughout for FP64 blocks; for FP32
+// blocks FP32 partial sums of 16 rows, added in FP64 (a Rademacher column's
+// partial sums are exact).
+template <typename T>
+struct RowSum {
+    double acc = 0.0;
+    T part = (T)0;
+    int cnt = 0;
+    __device__ __forceinline__ void add(T v) {
+        if (sizeof(T) == 8) {
+            acc += (double)v;
+            return;
+        }
+        part += v;
+        if (++cnt == 16) {
+            acc += (double)part;
+            part = (T)0;
+            cnt = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return acc + (double)part; }
+};
+
 // Pass 1: column sums per segment -> mean (only when desingularising).
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
@@ -115,13 +164,13 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
     constexpr int RPI = VNE_THREADS / KS;
     const int gc = panel * KS + c;
-    double acc = 0.0;
+    RowSum<T> rs;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        acc += source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg);
+        rs.add(source_value_t<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg));
     }
     __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = rs.total();
     __syncthreads();
     if (threadIdx.x < KS) {
         double s = 0.0;
@@ -136,7 +185,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     }
 }
 
-// Pass 2: w_1 = b - mean (stored in T), ||c||^2 in FP64, sigma_1 = 1/||c||.
+// Pass 2: w_1 = b - mean (stored in T), ||w_1||^2 (FP64 across partial sums),
+// sigma_1 = 1/||w_1||.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
@@ -145,18 +195,18 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
     const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
     constexpr int RPI = VNE_THREADS / KS;
     const int gc = panel * KS + c;
-    const double mu = p.desing ? p.mean[(size_t)t.seg * p.K + gc] : 0.0;
+    const T mu = p.desing ? (T)p.mean[(size_t)t.seg * p.K + gc] : (T)0;
+    const bool live = gc < p.src.ncols;
     T* out = p.w1 + (size_t)panel * p.n_total * KS;
-    double acc = 0.0;
+    RowSum<T> rs;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        double v = source_value_panel<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg) - mu;
-        if (gc >= p.src.ncols) v = 0.0;
-        out[(size_t)r * KS + c] = (T)v;
-        acc += v * v;
+        const T v = live ? source_value_t<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg) - mu : (T)0;
+        out[(size_t)r * KS + c] = v;
+        rs.add(v * v);
     }
     __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = rs.total();
     __syncthreads();
     if (threadIdx.x < KS) {
         double s = 0.0;

@@ -558,12 +558,14 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             if (prof) {
                 e2 = ctx_event(ctx);
                 VNE_TRY_CUDA(ctx, cudaEventRecord(e2, s));
-                // algorithmic bytes: CSR structure (+ values) once per panel, the
-                // gathered block w_j once, w_{j-1} (j > 1) and u once each
+                // algorithmic (compulsory) bytes: the CSR structure (+ values)
+                // once per launch, the gathered block w_j once, w_{j-1} (j > 1)
+                // and u once each; the re-reads of the CSR for every further
+                // panel are the design's own traffic, not counted here
                 const double es = sizeof(T);
                 double csr = 4.0 * (P.n_total + 1) + (double)nnz_total * (4.0 + (P.valued ? es : 0.0));
                 double vec = (double)P.n_total * ks * es;
-                double step_bytes = panels * (csr + vec * (j > 1 ? 3.0 : 2.0));
+                double step_bytes = (interleave && !reorth ? panels : 1) * csr + panels * vec * (j > 1 ? 3.0 : 2.0);
                 double upd_bytes = panels * vec * 3.0;
                 if (interleave && !reorth) {
                     // one timed span covers the interleaved step and update launches
@@ -792,7 +794,7 @@ void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* ou
         const double es = sizeof(T);
         double csr = 4.0 * (P.n_total + 1) + (double)P.nnz_total * (4.0 + (P.valued ? es : 0.0));
         double vec = (double)P.n_total * ks * es;
-        ctx->pending.push_back({0, e0, e1, panels * (csr + vec * (shift != 0.0 ? 3.0 : 2.0))});
+        ctx->pending.push_back({0, e0, e1, csr + panels * vec * (shift != 0.0 ? 3.0 : 2.0)});
     }
 }
 
