@@ -247,6 +247,22 @@ vne_status vne_tridiag_quadrature(vne_ctx *ctx, const double *alpha, const doubl
                                   const double *norm2, double scale, int32_t count, int32_t m,
                                   double *psi);
 
+/* A-posteriori bounds of Theorem 4.4 (polynomial Krylov case) for the
+ * quadratures above after m Lanczos steps: beta[m-1] holds beta_m of the
+ * decomposition A V_m = V_m T_m + beta_m v_{m+1} e_m^T (T, beta_m in the
+ * units of A / scale).  With g_m the function of eq. error-bound--gm-definition
+ * and f(x) = -x log x, lower = norm2 * min |g_m|, upper = norm2 * max |g_m|
+ * over [lam_min, lam_max] (0 < lam_min < lam_max, a spectral interval of A),
+ * estimate = norm2 * sqrt(min max) (eq. error-bound-a-posteriori--estimate).
+ * The extrema are taken over `grid` geometrically and `grid` linearly spaced
+ * points plus the Ritz values inside the interval.  A block that broke down
+ * (a zero beta_j, j < m) or beta_m = 0 gives 0.  Host arrays as for
+ * vne_tridiag_quadrature; outputs double[count].  EINVAL for a bad interval,
+ * grid < 1 or m outside [1, 128]. */
+vne_status vne_quadrature_bounds(vne_ctx *ctx, const double *alpha, const double *beta, const double *norm2,
+                                 double scale, int32_t count, int32_t m, double lam_min, double lam_max,
+                                 int32_t grid, double *lower, double *upper, double *estimate);
+
 /* Fill a device array [n][k] (row-major, float or double per `fp64`) with
  * Rademacher columns col_begin..col_begin+k-1 for node ids 0..n-1. */
 vne_status vne_rademacher(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,

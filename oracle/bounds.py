@@ -75,19 +75,42 @@ def gm_coefficients(alpha, beta):
     return theta, a, bb, gam
 
 
+def _dd1_dd2(z, t):
+    """Divided differences of f(x) = -x log x: f[t, z] and f[t, t, z].
+
+    With z = t (1 + u) they are -log t - h(u) and (1 - h(u)) / (t u), where
+    h(u) = (1 + u) log(1 + u) / u; near u = 0 the power series
+    1 - h(u) = sum_{k>=1} (-1)^k u^k / (k (k + 1)) replaces the quotient, so
+    the values stay accurate however close z is to t (the plain quotients of
+    eq. error-bound--gm-definition cancel catastrophically there).  At u = 0
+    they are f'(t) and f''(t) / 2, the limits the definition states."""
+    z = np.asarray(z, float)
+    u = (z - t) / t
+    small = np.abs(u) < 0.1
+    us = np.where(small, u, 0.0)
+    ser = np.zeros_like(u)          # (1 - h(u)) / u, series
+    p = np.ones_like(u)
+    for k in range(1, 40):
+        ser += ((-1.0) ** k) * p / (k * (k + 1))
+        p = p * us
+    ul = np.where(small, 1.0, u)
+    h_large = (1.0 + ul) * np.log1p(ul) / ul
+    one_minus_h = np.where(small, ser * us, 1.0 - h_large)
+    dd1 = -np.log(t) - (1.0 - one_minus_h)
+    dd2 = np.where(small, ser, (1.0 - h_large) / ul) / t
+    return dd1, dd2
+
+
 def gm_eval(z, theta, a, bb, gam):
+    """g_m(z) of eq. error-bound--gm-definition: the sum over j of
+    a_j^2 b_j^2 f[theta_j, theta_j, z] + 2 a_j b_j gamma_j f[theta_j, z]
+    (divided differences of f, evaluated stably by _dd1_dd2)."""
     z = np.atleast_1d(np.asarray(z, float))
     out = np.zeros_like(z)
     for j in range(len(theta)):
-        t = theta[j]
         ab = a[j] * bb[j]
-        diff = z - t
-        at = np.abs(diff) <= 1e-14 * max(abs(t), 1e-300)
-        dz = np.where(at, 1.0, diff)
-        fz = _f(z)
-        gen = ab * ab * ((fz - _f(t)) / dz ** 2 - _df(t) / dz) + 2.0 * ab * gam[j] * (fz - _f(t)) / dz
-        lim = 0.5 * ab * ab * _d2f(t) + 2.0 * ab * gam[j] * _df(t)
-        out += np.where(at, lim, gen)
+        dd1, dd2 = _dd1_dd2(z, theta[j])
+        out += ab * ab * dd2 + 2.0 * ab * gam[j] * dd1
     return out
 
 

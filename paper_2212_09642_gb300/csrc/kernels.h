@@ -189,6 +189,11 @@ cudaError_t launch_convert_values(const double* in, int64_t count, void* out, in
 cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t);
+// Theorem 4.4 bounds (lower, upper) and the geometric-mean estimate of the
+// quadrature error after m steps; beta row m-1 holds beta_m.  A = scale * T.
+cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const double* norm2, const double* scale,
+                                  int count, int m, int ld, double lam_min, double lam_max, int grid, double* lower,
+                                  double* upper, double* estimate, cudaStream_t st);
 cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col,
                                 int count, int m, int ld, double* zvec, cudaStream_t);
 

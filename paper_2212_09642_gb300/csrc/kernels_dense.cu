@@ -942,6 +942,169 @@ __global__ void __launch_bounds__(32) k_tridiag_fvec(const double* __restrict__ 
     }
 }
 
+// A-posteriori bounds of Theorem 4.4 for the polynomial Lanczos quadrature
+// after m steps (A V_m = V_m T_m + beta_m v_{m+1} e_m^T): with Ritz values
+// theta_j, a_j = beta_m U_{mj}, b_j = U_{1j} and
+// gamma_j = sum_{l != j} a_l b_l / (theta_j - theta_l),
+//   g_m(z) = sum_j a_j^2 b_j^2 f[theta_j, theta_j, z] + 2 a_j b_j gamma_j f[theta_j, z]
+// (divided differences of f, the limits at z = theta_j included; evaluated
+// stably, see dd_entropy), and ||c||^2 min / max of |g_m| over the
+// spectral interval bound the quadrature error from below / above; their
+// geometric mean is the paper's error estimate.  The minimum and maximum are
+// taken over `grid` geometrically and `grid` linearly spaced points of
+// [lam_min, lam_max] plus the Ritz values inside it, spread over the lanes.
+// U_{1j}, U_{mj} come from the twisted-factorisation eigenvectors of the
+// shared spectrum (for a tight cluster the individual products are as
+// ill-conditioned as the formula itself).  f(x) = -x log x; the interval must
+// be positive.
+// Divided differences of f(x) = -x log x at (t, z), z = t (1 + u), given
+// log z and log t: f[t, z] = -log t - h(u) and f[t, t, z] = (1 - h(u)) / (t u)
+// with h(u) = (1 + u) log(1 + u) / u = z (log z - log t) / (t u).  For
+// |u| < 0.1 the power series 1 - h(u) = sum_{k>=1} (-1)^k u^k / (k (k + 1))
+// avoids the cancellation of the plain quotients.
+__device__ __forceinline__ void dd_entropy(double z, double lz, double t, double lt, double& dd1, double& dd2) {
+    const double u = (z - t) / t;
+    if (fabs(u) < 0.1) {
+        // (1 - h(u)) / u by Horner, 18 terms (|u|^18 / 342 < 1e-20)
+        double ser = 0.0;
+        for (int k = 18; k >= 1; k--) ser = fma(ser, u, ((k & 1) ? -1.0 : 1.0) / (double)(k * (k + 1)));
+        dd1 = -lt - (1.0 - ser * u);
+        dd2 = ser / t;
+    } else {
+        const double h = (z / t) * (lz - lt) / u;
+        dd1 = -lt - h;
+        dd2 = (1.0 - h) / (t * u);
+    }
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(32) k_tridiag_bounds(const double* __restrict__ alpha,
+                                                       const double* __restrict__ beta,
+                                                       const double* __restrict__ norm2,
+                                                       const double* __restrict__ scale, int count, int m, int ld,
+                                                       double lam_min, double lam_max, int grid,
+                                                       double* __restrict__ lower, double* __restrict__ upper,
+                                                       double* __restrict__ estimate) {
+    __shared__ TqShared<MAXM> S;
+    __shared__ double s_th[MAXM], s_ab[MAXM], s_gam[MAXM], s_lt[MAXM];
+    extern __shared__ double piv[];  // [2][MAXM][32] twisted pivots
+    const int c = blockIdx.x, lane = threadIdx.x;
+    if (c >= count) return;
+    if (!tq_spectrum<MAXM>(alpha, beta, c, m, ld, lane, S)) {
+        if (lane == 0) lower[c] = upper[c] = estimate[c] = nan("");
+        return;
+    }
+    const int n = S.n;
+    const double bm = beta[(size_t)(m - 1) * ld + c] * scale[c];  // beta_m of A
+    if (n < m || bm == 0.0) {
+        // the Krylov space is invariant: the quadrature is exact
+        if (lane == 0) lower[c] = upper[c] = estimate[c] = 0.0;
+        return;
+    }
+    const double sc = scale[c] / S.s2;
+    double* Dp = piv + lane;
+    double* Rp = piv + MAXM * 32 + lane;
+    // first and last eigenvector components
+    for (int j = lane; j < n; j += 32) {
+        const double th = S.th[j];
+        double d = 0.0;
+        for (int k = 0; k < n; k++) {
+            d = guard_pivot((S.a[k] - th) - (k > 0 ? S.b[k - 1] * S.b[k - 1] / d : 0.0), S.pivmin);
+            Dp[k * 32] = d;
+        }
+        double r = 0.0, best = INFINITY;
+        int tw = n - 1;
+        for (int k = n - 1; k >= 0; k--) {
+            r = guard_pivot((S.a[k] - th) - (k + 1 < n ? S.b[k] * S.b[k] / r : 0.0), S.pivmin);
+            Rp[k * 32] = r;
+            const double gam = fabs(Dp[k * 32] + r - (S.a[k] - th));
+            if (gam < best) {
+                best = gam;
+                tw = k;
+            }
+        }
+        double nrm = 1.0, z = 1.0;
+        for (int k = tw - 1; k >= 0; k--) {
+            z = -S.b[k] * z / Dp[k * 32];
+            nrm = fma(z, z, nrm);
+        }
+        const double z1 = tw > 0 ? z : 1.0;
+        z = 1.0;
+        for (int k = tw + 1; k < n; k++) {
+            z = -S.b[k - 1] * z / Rp[k * 32];
+            nrm = fma(z, z, nrm);
+        }
+        const double zn = tw < n - 1 ? z : 1.0;
+        s_th[j] = sc * th;
+        s_ab[j] = bm * (zn * z1) / nrm;
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+        const double t = s_th[j];
+        double gsum = 0.0;
+        for (int l = 0; l < n; l++)
+            if (l != j) gsum += s_ab[l] / (t - s_th[l]);
+        s_gam[j] = gsum;
+        s_lt[j] = log(t);
+    }
+    __syncwarp();
+    const int npts = 2 * grid + n;
+    const double lratio = log(lam_max / lam_min);
+    double gmin = INFINITY, gmax = 0.0;
+    for (int q = lane; q < npts; q += 32) {
+        double z;
+        if (q < grid) z = grid > 1 ? lam_min * exp(lratio * q / (grid - 1)) : lam_min;
+        else if (q < 2 * grid) z = grid > 1 ? lam_min + (lam_max - lam_min) * (q - grid) / (grid - 1) : lam_min;
+        else {
+            z = s_th[q - 2 * grid];
+            if (!(z >= lam_min && z <= lam_max)) continue;
+        }
+        const double lz = log(z);
+        double g = 0.0;
+        for (int j = 0; j < n; j++) {
+            const double ab = s_ab[j];
+            double dd1, dd2;
+            dd_entropy(z, lz, s_th[j], s_lt[j], dd1, dd2);
+            g += ab * ab * dd2 + 2.0 * ab * s_gam[j] * dd1;
+        }
+        gmin = fmin(gmin, fabs(g));
+        gmax = fmax(gmax, fabs(g));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, off));
+        gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+    }
+    if (lane == 0) {
+        const double nb = norm2[c];
+        lower[c] = nb * gmin;
+        upper[c] = nb * gmax;
+        estimate[c] = nb * sqrt(gmin * gmax);
+    }
+}
+
+cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const double* norm2, const double* scale,
+                                  int count, int m, int ld, double lam_min, double lam_max, int grid, double* lower,
+                                  double* upper, double* estimate, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (!(lam_min > 0.0 && lam_max > lam_min) || grid < 1) return cudaErrorInvalidValue;
+#define VNE_BOUND_CASE(MM)                                                                                   \
+    if (m <= MM) {                                                                                          \
+        const int smem = 2 * MM * 32 * (int)sizeof(double);                                                 \
+        cudaError_t e = cudaFuncSetAttribute(k_tridiag_bounds<MM>,                                          \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);            \
+        if (e != cudaSuccess) return e;                                                                     \
+        k_tridiag_bounds<MM><<<count, 32, smem, st>>>(alpha, beta, norm2, scale, count, m, ld, lam_min, lam_max, \
+                                                       grid, lower, upper, estimate);                       \
+        return cudaGetLastError();                                                                          \
+    }
+    VNE_BOUND_CASE(32)
+    VNE_BOUND_CASE(64)
+    VNE_BOUND_CASE(128)
+#undef VNE_BOUND_CASE
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t st) {

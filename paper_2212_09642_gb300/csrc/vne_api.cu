@@ -1724,6 +1724,39 @@ extern "C" vne_status vne_tridiag_quadrature(vne_ctx* ctx, const double* alpha, 
     VNE_API_END(ctx)
 }
 
+extern "C" vne_status vne_quadrature_bounds(vne_ctx* ctx, const double* alpha, const double* beta,
+                                            const double* norm2, double scale, int32_t count, int32_t m,
+                                            double lam_min, double lam_max, int32_t grid, double* lower,
+                                            double* upper, double* estimate) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, alpha && beta && norm2 && lower && upper && estimate && count >= 1 && m >= 1 && m <= 128,
+                VNE_EINVAL, "bad arguments to vne_quadrature_bounds");
+    VNE_REQUIRE(ctx, lam_min > 0.0 && lam_max > lam_min && grid >= 1, VNE_EINVAL,
+                "need 0 < lam_min < lam_max and grid >= 1");
+    // host layout [count][m] -> device column-interleaved [m][count]
+    std::vector<double> a((size_t)m * count), b((size_t)m * count), sc(count, scale), nn(norm2, norm2 + count);
+    for (int c = 0; c < count; c++)
+        for (int j = 0; j < m; j++) {
+            a[(size_t)j * count + c] = alpha[(size_t)c * m + j];
+            b[(size_t)j * count + c] = beta[(size_t)c * m + j];
+        }
+    double* da = upload(ctx, "tb.a", a);
+    double* db = upload(ctx, "tb.b", b);
+    double* ds = upload(ctx, "tb.s", sc);
+    double* dn = upload(ctx, "tb.n", nn);
+    double* dout = ws_get_t<double>(ctx, "tb.out", 3 * (size_t)count);
+    VNE_TRY_CUDA(ctx, launch_tridiag_bounds(da, db, dn, ds, count, m, count, lam_min, lam_max, grid, dout,
+                                            dout + count, dout + 2 * count, ctx->stream));
+    ctx->launches += 1;
+    std::vector<double> h = download(ctx, dout, 3 * (size_t)count);
+    std::copy(h.begin(), h.begin() + count, lower);
+    std::copy(h.begin() + count, h.begin() + 2 * count, upper);
+    std::copy(h.begin() + 2 * count, h.end(), estimate);
+    VNE_API_END(ctx)
+}
+
 extern "C" vne_status vne_rademacher(vne_ctx* ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k, int32_t fp64,
                                      void* out_device) {
     if (!ctx) return VNE_EINVAL;

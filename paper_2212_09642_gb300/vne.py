@@ -100,6 +100,8 @@ def _declare(lib):
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
         "vne_ctx_graph_stats": (st, [_P, _PI64, _PI64]),
+        "vne_quadrature_bounds": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
         "vne_measure_gather": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_int32, _PD]),
     }
@@ -130,7 +132,7 @@ def exported_symbols():
 _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
-               "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_rademacher",
+               "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
@@ -300,6 +302,18 @@ def vne_tridiag_quadrature(ctx, alpha, beta, norm2, scale):
     _check(load().vne_tridiag_quadrature(ctx, _ptr(alpha), _ptr(beta), _ptr(norm2), float(scale), count, m,
                                          _ptr(psi)), ctx)
     return psi
+
+
+def vne_quadrature_bounds(ctx, alpha, beta, norm2, scale, lam_min, lam_max, grid=4000):
+    """(lower, upper, estimate) of Theorem 4.4 for tridiagonals alpha/beta [count, m] (beta[:, m-1] = beta_m)."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    norm2 = np.ascontiguousarray(norm2, dtype=np.float64)
+    count, m = alpha.shape
+    lo, hi, est = np.zeros(count), np.zeros(count), np.zeros(count)
+    _check(load().vne_quadrature_bounds(ctx, _ptr(alpha), _ptr(beta), _ptr(norm2), float(scale), count, m,
+                                        float(lam_min), float(lam_max), int(grid), _ptr(lo), _ptr(hi), _ptr(est)), ctx)
+    return lo, hi, est
 
 
 def vne_rademacher(ctx, seed, n, col_begin, k, out_device, fp64):

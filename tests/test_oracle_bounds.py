@@ -77,3 +77,25 @@ def test_probing_heuristic_recovers_model():
     d = bounds.probing_heuristic_d(T1, T2, T3, 1e-4)
     d_want = min(dd for dd in range(1, 64) if e(dd) <= 1e-4)
     assert d >= d_want  # the max over k in {2,3} is at least the k = 2 choice
+
+
+def test_gm_divided_differences_against_high_precision():
+    """The stable divided differences of f(x) = -x log x used by g_m agree
+    with 50-digit evaluations of the plain quotients of eq.
+    error-bound--gm-definition, including points next to the node where the
+    double-precision quotients cancel."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    from oracle import bounds
+    for t in (1.3e-3, 0.25, 7.0):
+        for rel in (0.0, 1e-13, -3e-9, 2e-5, 0.05, -0.07, 0.1, 0.5, 2.0, -0.8):
+            z = t * (1.0 + rel)
+            d1, d2 = bounds._dd1_dd2(np.array([z]), t)
+            T, Z = mp.mpf(t), mp.mpf(z)
+            if Z == T:
+                r1, r2 = -mp.log(T) - 1, -1 / (2 * T)
+            else:
+                r1 = (-Z * mp.log(Z) + T * mp.log(T)) / (Z - T)
+                r2 = (r1 + mp.log(T) + 1) / (Z - T)
+            assert abs(d1[0] - float(r1)) <= 1e-14 * abs(float(r1)) + 1e-300
+            assert abs(d2[0] - float(r2)) <= 1e-13 * abs(float(r2))
