@@ -89,7 +89,18 @@ typedef struct vne_options {
                              probe_offset .. probe_offset + N - 1), so that
                              ranks splitting [0, N) into ranges evaluate
                              exactly the probes of one single run; 0 default */
-    int32_t reserved[4];
+    int32_t check_every;  /* adaptive Lanczos (quad_tol > 0): steps between
+                             checks of the error estimate, 0 = 5 */
+    double quad_tol;      /* > 0: Lanczos quadratures stop once every column
+                             of a block has the error estimate of Theorem 4.4
+                             (geometric mean of its bounds) below quad_tol x
+                             |psi|, or at krylov_steps; checks after at least
+                             check_every steps.  0 = fixed krylov_steps. */
+    double spectrum_min;  /* adaptive mode: lower end of the spectral interval
+                             of A for the bounds; 0 = half the smallest
+                             positive Ritz value of each column (the upper end
+                             is the Gershgorin bound of A) */
+    int32_t reserved[2];
 } vne_options;
 
 /* Fill *opt with the defaults described above. */
@@ -122,6 +133,9 @@ vne_status vne_ctx_stats(const vne_ctx *ctx, int64_t *launches, double *kernel_s
  * (*replayed, including the replay right after a capture).  Either pointer
  * may be NULL.  EINVAL for a null context. */
 vne_status vne_ctx_graph_stats(const vne_ctx *ctx, int64_t *captured, int64_t *replayed);
+/* Lanczos steps taken by the last quadrature call on the context (the
+ * largest over its blocks; krylov_steps unless quad_tol stopped earlier). */
+vne_status vne_ctx_last_steps(const vne_ctx *ctx, int32_t *steps);
 /* Throughput ceiling of the SpMM step's access pattern (a measurement aid, not
  * part of the method): `gathers` reads of random row_bytes-byte rows (32, 64
  * or 128) from a device table of table_bytes, plus one streaming read of

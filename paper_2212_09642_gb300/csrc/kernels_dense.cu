@@ -1048,6 +1048,19 @@ __global__ void __launch_bounds__(32) k_tridiag_bounds(const double* __restrict_
         s_lt[j] = log(t);
     }
     __syncwarp();
+    if (!(lam_min > 0.0)) {
+        // half the smallest positive Ritz value of this column
+        double tmin = INFINITY;
+        for (int j = lane; j < n; j += 32)
+            if (s_th[j] > 0.0) tmin = fmin(tmin, s_th[j]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
+        lam_min = 0.5 * tmin;
+    }
+    if (!(lam_min > 0.0 && lam_max > lam_min)) {
+        if (lane == 0) lower[c] = upper[c] = estimate[c] = INFINITY;  // no usable interval: not converged
+        return;
+    }
     const int npts = 2 * grid + n;
     const double lratio = log(lam_max / lam_min);
     double gmin = INFINITY, gmax = 0.0;
@@ -1087,7 +1100,8 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const
                                   int count, int m, int ld, double lam_min, double lam_max, int grid, double* lower,
                                   double* upper, double* estimate, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    if (!(lam_min > 0.0 && lam_max > lam_min) || grid < 1) return cudaErrorInvalidValue;
+    // lam_min <= 0: half the smallest positive Ritz value of each column
+    if (!(lam_max > 0.0 && lam_max > lam_min) || grid < 1) return cudaErrorInvalidValue;
 #define VNE_BOUND_CASE(MM)                                                                                   \
     if (m <= MM) {                                                                                          \
         const int smem = 2 * MM * 32 * (int)sizeof(double);                                                 \

@@ -91,6 +91,7 @@ struct vne_ctx {
     std::map<std::string, int> graph_seen;
     cudaStream_t cap_stream = nullptr;  // private stream the captures run on
     int64_t graphs_captured = 0, graphs_replayed = 0;
+    int last_steps = 0;  // Lanczos steps of the last quadrature call (largest over its blocks)
 };
 
 struct Problem;
@@ -421,10 +422,23 @@ struct BlockOut {
     size_t slot_stride = 0;    // elements
 };
 
+std::vector<double> download(vne_ctx* ctx, const double* d, size_t count);
+
+// Adaptive stopping of a block (Theorem 4.4): after every `check` steps the
+// quadratures and the error estimates of all columns are computed; the block
+// stops once every estimate is at most tol x |psi|.
+struct Adaptive {
+    double tol = 0.0;
+    int check = 5;
+    double lam_min = 0.0;  // <= 0: half the smallest positive Ritz value per column
+    double lam_max = 0.0;
+    int grid = 1000;
+};
+
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
                bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
-               bool interleave = false, bool graph = true, bool want_psi = true) {
+               bool interleave = false, bool graph = true, bool want_psi = true, const Adaptive* ad = nullptr) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
     const int Kp = panels * ks;
@@ -513,8 +527,8 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     }
     // The step loop, enqueued on stream `s`; `prof` brackets the launches
     // with events (never while capturing).
-    auto enqueue_loop = [&](cudaStream_t s, bool prof) {
-        for (int j = 1; j <= m; j++) {
+    auto enqueue_loop = [&](cudaStream_t s, bool prof, int j_begin, int j_end) {
+        for (int j = j_begin; j <= j_end; j++) {
             p.first = (j == 1);
             p.renorm = 0;
             p.w_cur = slot(j);
@@ -606,8 +620,30 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[0], st));
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
-    if (!graph || ctx->profile || cap != cudaStreamCaptureStatusNone) {
-        enqueue_loop(st, ctx->profile);
+    int m_run = m;  // steps actually taken
+    if (ad && ad->tol > 0.0 && want_psi) {
+        // adaptive: chunks of `check` steps launched directly, each followed
+        // by the quadratures and error estimates of all columns
+        double* est = ws_get_t<double>(ctx, tag + ".est", 3 * (size_t)SK);
+        int j = 0;
+        m_run = 0;
+        while (j < m) {
+            const int j1 = std::min(m, j + std::max(1, ad->check));
+            enqueue_loop(st, ctx->profile, j + 1, j1);
+            j = j1;
+            m_run = j;
+            if (j >= m) break;
+            VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, j, SK, psi, st));
+            VNE_TRY_CUDA(ctx, launch_tridiag_bounds(alpha, beta, norm2, dscale, SK, j, SK, ad->lam_min, ad->lam_max,
+                                                    ad->grid, est, est + SK, est + 2 * SK, st));
+            ctx->launches += 2;
+            std::vector<double> hp = download(ctx, psi, SK), he = download(ctx, est + 2 * SK, SK);
+            bool done = true;
+            for (int c = 0; c < SK && done; c++) done = he[c] <= ad->tol * fabs(hp[c]);
+            if (done) break;
+        }
+    } else if (!graph || ctx->profile || cap != cudaStreamCaptureStatusNone) {
+        enqueue_loop(st, ctx->profile, 1, m);
     } else {
         // Graph key: every value the loop's launches depend on.
         std::string key;
@@ -633,7 +669,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
                 cudaGraph_t g = nullptr;
                 VNE_TRY_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
                 try {
-                    enqueue_loop(ctx->cap_stream, false);
+                    enqueue_loop(ctx->cap_stream, false, 1, m);
                 } catch (...) {
                     cudaStreamEndCapture(ctx->cap_stream, &g);
                     if (g) cudaGraphDestroy(g);
@@ -655,19 +691,20 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             ctx->launches += it->second.kernels;
             ctx->graphs_replayed++;
         } else {
-            enqueue_loop(st, false);
+            enqueue_loop(st, false, 1, m);
         }
     }
     if (ctx->time_steps) VNE_TRY_CUDA(ctx, cudaEventRecord(ctx->loop_ev[1], st));
     if (want_psi) {
-        VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m, SK, psi, st));
+        VNE_TRY_CUDA(ctx, launch_tridiag_quad(alpha, beta, norm2, dscale, SK, m_run, SK, psi, st));
         ctx->launches += 1;
     }
+    ctx->last_steps = std::max(ctx->last_steps, m_run);
     out.K = K;
     out.Kp = Kp;
     out.ks = ks;
     out.panels = panels;
-    out.m = m;
+    out.m = m_run;
     out.SK = SK;
     out.alpha = alpha;
     out.beta = beta;
@@ -722,6 +759,14 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
     int lim = block_limit(o);
     bool reorth = want_reorth(M, o);
     std::vector<double> psi(ncols);
+    ctx->last_steps = 0;
+    Adaptive ad;
+    if (o && o->quad_tol > 0.0) {
+        ad.tol = o->quad_tol;
+        ad.check = o->check_every > 0 ? o->check_every : 5;
+        ad.lam_min = o->spectrum_min;
+        ad.lam_max = M->normM * M->scale;
+    }
     for (int b0 = 0; b0 < ncols; b0 += lim) {
         int K = std::min(lim, ncols - b0);
         StartSource s = src;
@@ -730,7 +775,7 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
         if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
         BlockOut out;
         run_block<T>(ctx, *P, s, nullptr, K, ks, m, reorth, false, M->desing, "q", out, sc.variant, sc.interleave,
-                     sc.graph);
+                     sc.graph, true, ad.tol > 0.0 ? &ad : nullptr);
         std::vector<double> h = download(ctx, out.psi, K);
         std::copy(h.begin(), h.end(), psi.begin() + b0);
     }
@@ -1490,6 +1535,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     s.col_begin = 0;
     s.ncols = Nr;
     BlockOut sk;
+    ctx->last_steps = 0;
     // the sketch block only feeds f(A) Omega: its quadratures are not needed
     run_block<T>(ctx, *P, s, nullptr, Nr, ks, m, want_reorth(M, o), true, M->desing, "sketch", sk, sc.variant,
                  sc.interleave, sc.graph, false);
@@ -1853,6 +1899,7 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     s.col_begin = 0;
     s.ncols = num_vectors;
     BlockOut out;
+    ctx->last_steps = 0;
     if (fp64) {
         check_ks<double>(ctx, ks);
         run_block<double>(ctx, *P, s, nullptr, num_vectors, ks, krylov_steps, false, false, true, "batch", out, 0,
@@ -1883,6 +1930,12 @@ extern "C" vne_status vne_ctx_profile(vne_ctx* ctx, int32_t enable) {
     ctx->profile = enable != 0;
     for (auto& k : ctx->stat) k = KernelStat();
     ctx->launches = 0;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_last_steps(const vne_ctx* ctx, int32_t* steps) {
+    if (!ctx || !steps) return VNE_EINVAL;
+    *steps = ctx->last_steps;
     return VNE_OK;
 }
 
@@ -2272,6 +2325,7 @@ extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t
     src.seg_col0 = upload(ctx, "srv.col0", col0);
     BlockOut out;
     check_ks<float>(ctx, ks);
+    ctx->last_steps = 0;
     run_block<float>(ctx, P, src, nullptr, S->block, ks, S->m, false, false, true, "srv", out, variant, false,
                      S->opt.graphs != 0);
     std::vector<double> psi = download(ctx, out.psi, out.SK);

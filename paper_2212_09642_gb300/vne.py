@@ -50,7 +50,8 @@ class vne_options(ctypes.Structure):
                 ("item_nnz", ctypes.c_int32), ("n_inf_poles", ctypes.c_int32), ("cg_max_iter", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
                 ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("probe_offset", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("probe_offset", ctypes.c_int32), ("check_every", ctypes.c_int32), ("quad_tol", ctypes.c_double),
+                ("spectrum_min", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None
@@ -100,6 +101,7 @@ def _declare(lib):
         "vne_quadform_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
         "vne_ctx_graph_stats": (st, [_P, _PI64, _PI64]),
+        "vne_ctx_last_steps": (st, [_P, _PI32]),
         "vne_quadrature_bounds": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
         "vne_measure_gather": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
@@ -134,7 +136,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
-               "vne_ctx_graph_stats", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
+               "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
                "vne_server_result", "vne_server_info"]
 
@@ -357,6 +359,13 @@ def vne_ctx_graph_stats(ctx):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().vne_ctx_graph_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
     return a.value, b.value
+
+
+def vne_ctx_last_steps(ctx):
+    """Lanczos steps taken by the last quadrature call (adaptive mode may stop early)."""
+    v = ctypes.c_int32()
+    _check(load().vne_ctx_last_steps(ctx, ctypes.byref(v)), ctx)
+    return v.value
 
 
 def vne_measure_gather(ctx, table_bytes, row_bytes, gathers, stream_bytes=0, reps=3):

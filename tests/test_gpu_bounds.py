@@ -69,3 +69,27 @@ def test_bounds_zero_after_breakdown(vctx):
     assert lo[0] == 0.0 and hi[0] == 0.0 and est[0] == 0.0
     with pytest.raises(vne.VneError):
         vne.vne_quadrature_bounds(vctx, a, bb, np.array([1.0]), 1.0, 0.0, 0.1, 100)
+
+
+def test_adaptive_lanczos_stops_early_with_parity(vctx):
+    """quad_tol > 0: the block stops at the first check where every column's
+    Theorem 4.4 estimate is below quad_tol |psi|; the quadratures are then the
+    oracle's at that step count, and close to the converged ones."""
+    g = graphs.barabasi_albert(3000, 3, 5)
+    A, _ = density.density_matrix(g)
+    mat = vne.matrix_from_graph(vctx, g, fp64=True)
+    try:
+        opt = vne.options(quad_tol=1e-8, check_every=4)
+        est, se, psi = vne.vne_entropy_hutchinson(vctx, mat, 24, 120, 17, opt=opt, want_psi=True)
+        steps = vne.vne_ctx_last_steps(vctx)
+        full, _, psi_full = vne.vne_entropy_hutchinson(vctx, mat, 24, 120, 17, want_psi=True)
+        assert vne.vne_ctx_last_steps(vctx) == 120
+    finally:
+        vne.vne_matrix_destroy(mat)
+    assert 4 <= steps < 120 and steps % 4 == 0, steps
+    X = rng.rademacher(17, g.n, 0, 24)
+    nA = density.gershgorin_norm(A)
+    for j in range(24):
+        ref = krylov.lanczos_quadform(A, X[:, j], steps, reorth="full", norm_A=nA)[0]
+        assert abs(psi[j] - ref) <= 1e-10 * abs(ref)
+        assert abs(psi[j] - psi_full[j]) <= 1e-6 * abs(psi_full[j])
