@@ -468,6 +468,15 @@ def run_other(args):
                     roofline=_roof(kst, "step", ms, "k_step FP64"), gpu_launches=int(launches), clocks=clk,
                     estimate=outs[0][0], std_error=outs[0][1], dense_entropy=S,
                     abs_err_vs_dense=abs(outs[0][0] - S))
+        # the same estimates with adaptive stopping by the Theorem 4.4
+        # estimate (relative quadrature error 1e-8, checks every 5 steps)
+        aopt = vne.options(quad_tol=1e-8, check_every=5)
+        outs2, ms2, _, _, _ = _timed(ctx, stream, lambda s: vne.vne_entropy_hutchinson(
+            ctx, mat, 100, 50, s, opt=aopt), args.steps, args.warmup)
+        line["adaptive_quad_tol_1e-8"] = {"value": args.steps / (ms2 / 1e3), "unit": UNIT,
+                                          "krylov_steps_taken": vne.vne_ctx_last_steps(ctx),
+                                          "estimate": outs2[0][0],
+                                          "rel_diff_vs_fixed_steps": abs(outs2[0][0] - outs[0][0]) / abs(outs[0][0])}
         vne.vne_matrix_destroy(mat)
     elif args.workload == "c3":
         n = args.n if args.n != N_NODES else 4_000_000
@@ -475,15 +484,19 @@ def run_other(args):
         t0 = time.perf_counter()
         colors, s = vne.vne_greedy_coloring(g.n, g.rowptr, g.col, 2)
         t_col = time.perf_counter() - t0
-        mat = vne.matrix_from_graph(ctx, g, fp64=False)
+        t1 = time.perf_counter()
+        mat = vne.matrix_from_graph(ctx, g, fp64=False, reorder="rcm")
+        t_asm = time.perf_counter() - t1
         opt = vne.options(cg_tol=1e-8, n_inf_poles=2)
         outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
             ctx, mat, colors, 2, 0, opt=opt, num_shifts=8), args.steps, args.warmup)
         line.update(metric="entropy estimates/sec (probing d=2, rational Krylov 8 poles + 2 at infinity, RGG n=4e6)",
                     value=args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
                     config={"workload": f"C3: RGG n={g.n} avg degree 6 (seed 4), generation order, greedy distance-2 "
-                                        f"colouring ({s} colours, host {t_col:.1f} s, untimed), 8 log-spaced poles on "
-                                        "[1e-4, 1] ||A||_G, multi-shift CG to recursive rel. residual 1e-8",
+                                        f"colouring ({s} colours, host {t_col:.1f} s, untimed), matrix relabelled by "
+                                        f"reverse Cuthill-McKee in vne_create_density_matrix ({t_asm:.1f} s, untimed), "
+                                        "8 log-spaced poles on [1e-4, 1] ||A||_G, multi-shift CG to recursive rel. "
+                                        "residual 1e-8",
                             "nnz": g.nnz, "colors": s, "l2": "inputs larger than L2"},
                     roofline=_roof(kst, "step", ms, "k_step (SpMM inside CG)"),
                     cg_update=_roof(kst, "cg_update", ms, "k_cg_update"),

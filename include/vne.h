@@ -57,6 +57,9 @@ typedef struct vne_matrix vne_matrix;
 #define VNE_INPUT_DEVICE 0x10u   /* row_ptr / col_idx / vals are device pointers */
 #define VNE_REORDER 0x20u        /* relabel nodes by descending degree */
 #define VNE_CHECK_SYMMETRY 0x40u /* verify the pattern is symmetric (host, O(nnz log)) */
+#define VNE_REORDER_RCM 0x80u    /* relabel nodes by reverse Cuthill-McKee (host BFS, O(nnz log)):
+                                    neighbours get nearby labels, so the SpMM's gathers stay local
+                                    on graphs with geometric structure; wins over VNE_REORDER */
 
 /* ---- options ---------------------------------------------------------- */
 typedef struct vne_options {

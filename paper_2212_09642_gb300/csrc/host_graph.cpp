@@ -1,5 +1,6 @@
 // Host-side graph utilities of libvne: greedy distance-d colouring
-// (Algorithm 1 of Section 3.1) and the degree-descending relabelling.
+// (Algorithm 1 of Section 3.1) and the degree-descending and reverse
+// Cuthill-McKee relabellings.
 #include <stdint.h>
 
 #include <algorithm>
@@ -19,6 +20,40 @@ std::vector<int32_t> degree_order(int64_t n, const int64_t* rowptr) {
     for (int64_t i = 0; i < n; i++) cnt[maxdeg - (rowptr[i + 1] - rowptr[i]) + 1]++;
     for (int64_t d = 0; d <= maxdeg; d++) cnt[d + 1] += cnt[d];
     for (int64_t i = 0; i < n; i++) order[cnt[maxdeg - (rowptr[i + 1] - rowptr[i])]++] = (int32_t)i;
+    return order;
+}
+
+std::vector<int32_t> rcm_order(int64_t n, const int64_t* rowptr, const int32_t* col) {
+    std::vector<int32_t> order;
+    order.reserve(n);
+    std::vector<char> seen(n, 0);
+    // component seeds in ascending degree, ties by id
+    std::vector<int32_t> by_degree = degree_order(n, rowptr);  // descending degree
+    std::vector<int32_t> nbr;
+    for (int64_t s = n - 1; s >= 0; s--) {
+        const int32_t seed = by_degree[s];
+        if (seen[seed]) continue;
+        seen[seed] = 1;
+        size_t head = order.size();
+        order.push_back(seed);
+        while (head < order.size()) {
+            const int32_t u = order[head++];
+            nbr.clear();
+            for (int64_t k = rowptr[u]; k < rowptr[u + 1]; k++) {
+                const int32_t w = col[k];
+                if (!seen[w]) {
+                    seen[w] = 1;
+                    nbr.push_back(w);
+                }
+            }
+            std::sort(nbr.begin(), nbr.end(), [&](int32_t a, int32_t b) {
+                const int64_t da = rowptr[a + 1] - rowptr[a], db = rowptr[b + 1] - rowptr[b];
+                return da != db ? da < db : a < b;
+            });
+            order.insert(order.end(), nbr.begin(), nbr.end());
+        }
+    }
+    std::reverse(order.begin(), order.end());
     return order;
 }
 

@@ -1287,7 +1287,7 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     // (symmetry check; trace and Gershgorin bound of a valued matrix).
     std::vector<int32_t> hci;
     std::vector<double> hva;
-    const bool need_host = vals || (flags & VNE_CHECK_SYMMETRY);
+    const bool need_host = vals || (flags & VNE_CHECK_SYMMETRY) || (flags & VNE_REORDER_RCM);
     if (need_host && nnz) {
         hci.resize(nnz);
         if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(hci.data(), col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1337,10 +1337,11 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
     VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
     if (vals) VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
-    if (flags & VNE_REORDER) {
-        // degree-descending relabelling, stable in the node id (host, O(n));
-        // the nonzeros are moved on the device
-        std::vector<int32_t> order = degree_order(n, rp.data());  // new -> old
+    if (flags & (VNE_REORDER | VNE_REORDER_RCM)) {
+        // relabelling (host): reverse Cuthill-McKee, else degree-descending
+        // stable in the node id; the nonzeros are moved on the device
+        std::vector<int32_t> order = (flags & VNE_REORDER_RCM) ? rcm_order(n, rp.data(), hci.data())
+                                                               : degree_order(n, rp.data());  // new -> old
         std::vector<int32_t> inv(n);
         for (int64_t i = 0; i < n; i++) inv[order[i]] = (int32_t)i;
         std::vector<int64_t> rp2(n + 1, 0);

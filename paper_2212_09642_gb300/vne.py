@@ -35,6 +35,7 @@ VNE_NORMALIZE_TRACE = 0x4
 VNE_IS_LAPLACIAN = 0x8
 VNE_INPUT_DEVICE = 0x10
 VNE_REORDER = 0x20
+VNE_REORDER_RCM = 0x80
 VNE_CHECK_SYMMETRY = 0x40
 VNE_VECTORS_DEVICE = 0x1
 
@@ -434,6 +435,8 @@ def vne_server_info(srv):
 # small convenience layer (still marshalling only)
 
 def matrix_from_graph(ctx, graph, fp64=False, reorder=False, extra_flags=0):
-    """Density matrix rho = L / tr(L) of a graph pattern (implicit Laplacian)."""
-    flags = (VNE_FP64 if fp64 else VNE_FP32) | (VNE_REORDER if reorder else 0) | extra_flags
+    """Density matrix rho = L / tr(L) of a graph pattern (implicit Laplacian).
+    reorder: False, True (degree order) or "rcm" (reverse Cuthill-McKee)."""
+    ro = VNE_REORDER_RCM if reorder == "rcm" else (VNE_REORDER if reorder else 0)
+    flags = (VNE_FP64 if fp64 else VNE_FP32) | ro | extra_flags
     return vne_create_density_matrix(ctx, graph.n, graph.rowptr, graph.col, None, flags)

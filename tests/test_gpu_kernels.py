@@ -29,7 +29,7 @@ def test_rademacher_bit_exact(vctx):
 
 
 @pytest.mark.parametrize("fp64", [True, False])
-@pytest.mark.parametrize("reorder", [False, True])
+@pytest.mark.parametrize("reorder", [False, True, "rcm"])
 def test_spmm_matches_scipy(vctx, fp64, reorder):
     import torch
     dt = torch.float64 if fp64 else torch.float32

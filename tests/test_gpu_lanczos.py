@@ -70,11 +70,15 @@ def test_fp32_mixed_parity(vctx, name, g, panel):
     assert rel.max() <= TOL32, rel.max()
 
 
-def test_reordering_leaves_quadforms_unchanged(vctx):
-    g = graphs.barabasi_albert(5000, 3, 7)
+@pytest.mark.parametrize("reorder,g", [
+    (True, graphs.barabasi_albert(5000, 3, 7)),
+    ("rcm", graphs.random_geometric(4000, graphs.rgg_radius_for_degree(4000, 6.0), 2)),
+    ("rcm", graphs.disjoint_union([graphs.barabasi_albert(1500, 2, 1), graphs.grid2d(30, 40), graphs.star(50)])),
+])
+def test_reordering_leaves_quadforms_unchanged(vctx, reorder, g):
     A, _ = density.density_matrix(g)
     X = rng.rademacher(2, g.n, 0, 8)
-    mat = vne.matrix_from_graph(vctx, g, fp64=True, reorder=True)
+    mat = vne.matrix_from_graph(vctx, g, fp64=True, reorder=reorder)
     try:
         psi = vne.vne_quadform_batch(vctx, mat, X, 20, opt=vne.options(reorth=1))
     finally:
