@@ -127,47 +127,94 @@ __global__ void k_cg_scalars_b(CgState st) {
 }
 
 // r -= a q;  rho' = ||r||^2 (FP64 across the CTA, fixed-order last-CTA sum);
-// x_s += a_s p_s for active shifts
+// x_s += a_s p_s for active shifts.  Each lane owns CPL consecutive columns
+// of a row (16-byte vector accesses); a shift's x_s and p_s are touched only
+// by lanes that have an active column for it.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_cg_update(CgVectors<T> v, CgState st) {
-    constexpr int RPI = VNE_THREADS / KS;
+    constexpr int CPL = LaneVec<T>::CPL;
+    constexpr int LPR = KS / CPL;            // lanes per row
+    constexpr int RPI = VNE_THREADS / LPR;   // rows per iteration
     const int panel = blockIdx.x / v.tiles_per_panel, tile = blockIdx.x % v.tiles_per_panel;
     const RowTile t = v.tiles[tile];
-    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
-    const int col = panel * KS + c;
+    const int sub = threadIdx.x % LPR, rs = threadIdx.x / LPR;
+    const int cofs = sub * CPL;
     const size_t pofs = (size_t)panel * v.n * KS;
-    __shared__ T s_as[kMaxShifts][KS];
-    __shared__ int s_act[kMaxShifts][KS];
-    if (threadIdx.x < KS)
-        for (int s = 0; s < st.nshift; s++) {
-            s_as[s][threadIdx.x] = (T)st.as[(size_t)s * st.K + panel * KS + threadIdx.x];
-            s_act[s][threadIdx.x] = st.active[(size_t)s * st.K + panel * KS + threadIdx.x];
-        }
+    // per-column coefficients in shared memory; this lane's active columns
+    // as a bit mask (bit s * CPL + q)
+    __shared__ __align__(16) T s_as[kMaxShifts][KS];
+    for (int i = threadIdx.x; i < kMaxShifts * KS; i += VNE_THREADS) {
+        const int sh = i / KS, cc = i % KS;
+        const size_t o = (size_t)sh * st.K + panel * KS + cc;
+        s_as[sh][cc] = (sh < st.nshift && st.active[o]) ? (T)st.as[o] : (T)0;
+    }
+    uint32_t amask = 0;
+#pragma unroll
+    for (int sh = 0; sh < kMaxShifts; sh++)
+#pragma unroll
+        for (int q = 0; q < CPL; q++)
+            if (sh < st.nshift && st.active[(size_t)sh * st.K + panel * KS + cofs + q]) amask |= 1u << (sh * CPL + q);
     __syncthreads();
-    const T a = (T)st.a[col];
-    double acc = 0.0;
-    T accf = (T)0;
+    T a[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) a[q] = (T)st.a[panel * KS + cofs + q];
+    T* R = v.r + pofs;
+    const T* Q = v.q + pofs;
+    double acc[CPL];
+    T accf[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) {
+        acc[q] = 0.0;
+        accf[q] = (T)0;
+    }
     int cnt = 0;
     for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
-        const size_t o = pofs + (size_t)r * KS + c;
-        T rv = v.r[o] - a * v.q[o];
-        v.r[o] = rv;
-        accf += rv * rv;
+        const size_t o = (size_t)r * KS + cofs;
+        // every load of the row first (the pointers may alias as far as the
+        // compiler knows, so a store between them would serialise them)
+        T rv[CPL], qv[CPL];
+        load_lane(R + o, rv);
+        load_lane_stream(Q + o, qv);
+        T xv[kMaxShifts][CPL], pv[kMaxShifts][CPL];
+#pragma unroll
+        for (int sh = 0; sh < kMaxShifts; sh++)
+            if ((amask >> (sh * CPL)) & ((1u << CPL) - 1u)) {
+                load_lane(v.x[sh] + pofs + o, xv[sh]);
+                load_lane_stream(v.ps[sh] + pofs + o, pv[sh]);
+            }
+#pragma unroll
+        for (int q = 0; q < CPL; q++) {
+            rv[q] -= a[q] * qv[q];
+            accf[q] += rv[q] * rv[q];
+        }
+        store_lane(R + o, rv);
         if (++cnt == 16) {
-            acc += (double)accf;
-            accf = (T)0;
+#pragma unroll
+            for (int q = 0; q < CPL; q++) {
+                acc[q] += (double)accf[q];
+                accf[q] = (T)0;
+            }
             cnt = 0;
         }
-        for (int s = 0; s < st.nshift; s++)
-            if (s_act[s][c]) v.x[s][o] += s_as[s][c] * v.ps[s][o];
+#pragma unroll
+        for (int sh = 0; sh < kMaxShifts; sh++) {
+            const uint32_t m = (amask >> (sh * CPL)) & ((1u << CPL) - 1u);
+            if (!m) continue;
+            T cv[CPL];
+            load_lane(&s_as[sh][cofs], cv);
+#pragma unroll
+            for (int q = 0; q < CPL; q++)
+                if (m & (1u << q)) xv[sh][q] += cv[q] * pv[sh][q];
+            store_lane(v.x[sh] + pofs + o, xv[sh]);
+        }
     }
-    acc += (double)accf;
-    __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = acc;
+    __shared__ double red[RPI][KS];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) red[rs][cofs + q] = acc[q] + (double)accf[q];
     __syncthreads();
     if (threadIdx.x < KS) {
         double sum = 0.0;
-        for (int q = 0; q < RPI; q++) sum += red[q * KS + threadIdx.x];
+        for (int q = 0; q < RPI; q++) sum += red[q][threadIdx.x];
         v.part[((size_t)panel * v.tiles_per_panel + tile) * KS + threadIdx.x] = sum;
     }
     // last CTA of the panel sums the partials in tile order
@@ -188,32 +235,62 @@ __global__ void __launch_bounds__(VNE_THREADS) k_cg_update(CgVectors<T> v, CgSta
     }
 }
 
-// p = r + b p;  p_s = zeta_{k+1} r + b_s p_s for shifts active before this iteration
+// p = r + b p;  p_s = zeta_{k+1} r + b_s p_s for shifts active before this
+// iteration (vector lanes as in k_cg_update)
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, CgState st) {
-    constexpr int RPI = VNE_THREADS / KS;
+    constexpr int CPL = LaneVec<T>::CPL;
+    constexpr int LPR = KS / CPL;
+    constexpr int RPI = VNE_THREADS / LPR;
     const int panel = blockIdx.x / v.tiles_per_panel, tile = blockIdx.x % v.tiles_per_panel;
     const RowTile t = v.tiles[tile];
-    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
-    const int col = panel * KS + c;
+    const int sub = threadIdx.x % LPR, rs = threadIdx.x / LPR;
+    const int cofs = sub * CPL;
     const size_t pofs = (size_t)panel * v.n * KS;
-    __shared__ T s_z[kMaxShifts][KS], s_b[kMaxShifts][KS];
-    __shared__ int s_act[kMaxShifts][KS];
-    if (threadIdx.x < KS)
-        for (int s = 0; s < st.nshift; s++) {
-            const size_t o = (size_t)s * st.K + panel * KS + threadIdx.x;
-            s_z[s][threadIdx.x] = (T)st.zeta[o];
-            s_b[s][threadIdx.x] = (T)st.bs[o];
-            s_act[s][threadIdx.x] = st.active[o];
-        }
+    __shared__ __align__(16) T s_z[kMaxShifts][KS], s_b[kMaxShifts][KS];
+    for (int i = threadIdx.x; i < kMaxShifts * KS; i += VNE_THREADS) {
+        const int sh = i / KS, cc = i % KS;
+        const size_t o = (size_t)sh * st.K + panel * KS + cc;
+        const bool on = sh < st.nshift && st.active[o];
+        s_z[sh][cc] = on ? (T)st.zeta[o] : (T)0;
+        s_b[sh][cc] = on ? (T)st.bs[o] : (T)0;
+    }
+    uint32_t amask = 0;
+#pragma unroll
+    for (int sh = 0; sh < kMaxShifts; sh++)
+#pragma unroll
+        for (int q = 0; q < CPL; q++)
+            if (sh < st.nshift && st.active[(size_t)sh * st.K + panel * KS + cofs + q]) amask |= 1u << (sh * CPL + q);
     __syncthreads();
-    const T b = (T)st.b[col];
+    T b[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; q++) b[q] = (T)st.b[panel * KS + cofs + q];
+    const T* R = v.r + pofs;
+    T* Pp = v.p + pofs;
     for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
-        const size_t o = pofs + (size_t)r * KS + c;
-        const T rv = v.r[o];
-        v.p[o] = rv + b * v.p[o];
-        for (int s = 0; s < st.nshift; s++)
-            if (s_act[s][c]) v.ps[s][o] = s_z[s][c] * rv + s_b[s][c] * v.ps[s][o];
+        const size_t o = (size_t)r * KS + cofs;
+        T rv[CPL], pv[CPL];
+        load_lane(R + o, rv);
+        load_lane(Pp + o, pv);
+        T sv[kMaxShifts][CPL];
+#pragma unroll
+        for (int sh = 0; sh < kMaxShifts; sh++)
+            if ((amask >> (sh * CPL)) & ((1u << CPL) - 1u)) load_lane(v.ps[sh] + pofs + o, sv[sh]);
+#pragma unroll
+        for (int sh = 0; sh < kMaxShifts; sh++) {
+            const uint32_t m = (amask >> (sh * CPL)) & ((1u << CPL) - 1u);
+            if (!m) continue;
+            T zv[CPL], bv[CPL];
+            load_lane(&s_z[sh][cofs], zv);
+            load_lane(&s_b[sh][cofs], bv);
+#pragma unroll
+            for (int q = 0; q < CPL; q++)
+                if (m & (1u << q)) sv[sh][q] = zv[q] * rv[q] + bv[q] * sv[sh][q];
+            store_lane(v.ps[sh] + pofs + o, sv[sh]);
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; q++) pv[q] = rv[q] + b[q] * pv[q];
+        store_lane(Pp + o, pv);
     }
 }
 
