@@ -487,6 +487,8 @@ def run_other(args):
         t1 = time.perf_counter()
         mat = vne.matrix_from_graph(ctx, g, fp64=False, reorder="rcm")
         t_asm = time.perf_counter() - t1
+        # SpMM schedule tuned on a block of one column per colour (cached in the context)
+        tuned, _ = vne.vne_autotune(ctx, mat, s, 8)
         opt = vne.options(cg_tol=1e-8, n_inf_poles=2)
         outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
             ctx, mat, colors, 2, 0, opt=opt, num_shifts=8), args.steps, args.warmup)
@@ -497,7 +499,9 @@ def run_other(args):
                                         f"reverse Cuthill-McKee in vne_create_density_matrix ({t_asm:.1f} s, untimed), "
                                         "8 log-spaced poles on [1e-4, 1] ||A||_G, multi-shift CG to recursive rel. "
                                         "residual 1e-8",
-                            "nnz": g.nnz, "colors": s, "l2": "inputs larger than L2"},
+                            "nnz": g.nnz, "colors": s, "l2": "inputs larger than L2",
+                            "schedule": {"panel": tuned.panel, "item_nnz": tuned.item_nnz,
+                                         "step_variant": tuned.step_variant, "interleave": tuned.interleave}},
                     roofline=_roof(kst, "step", ms, "k_step (SpMM inside CG)"),
                     cg_update=_roof(kst, "cg_update", ms, "k_cg_update"),
                     cg_direction=_roof(kst, "cg_direction", ms, "k_cg_direction"),
