@@ -131,7 +131,7 @@ __global__ void k_cg_scalars_b(CgState st) {
 // of a row (16-byte vector accesses); a shift's x_s and p_s are touched only
 // by lanes that have an active column for it.
 template <typename T, int KS>
-__global__ void __launch_bounds__(VNE_THREADS) k_cg_update(CgVectors<T> v, CgState st) {
+__global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, CgState st) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;            // lanes per row
     constexpr int RPI = VNE_THREADS / LPR;   // rows per iteration
