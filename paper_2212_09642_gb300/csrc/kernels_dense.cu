@@ -1260,8 +1260,12 @@ __global__ void __launch_bounds__(256, 2) k_gram_tc(const float* __restrict__ X,
     constexpr int LD = 136;  // padded row (128 + 8 floats): conflict-free fragment loads
     constexpr int SLAB = 32;
     constexpr int V_PER_ROW = KS / 4;  // float4 per row of one panel
-    __shared__ __align__(16) float Xs[SLAB][LD];
-    __shared__ __align__(16) float Ys[SLAB][LD];
+    // dynamic shared memory: [2 buffers][X, Y][SLAB][LD]; a Gram of a block
+    // with itself (X == Y) loads one slab per buffer
+    extern __shared__ __align__(16) float gsm[];
+    const bool same = (X == Y) && (kx == ky);
+    float* xbuf[2] = {gsm, gsm + 2 * SLAB * LD};
+    float* ybuf[2] = {same ? xbuf[0] : gsm + SLAB * LD, same ? xbuf[1] : gsm + 3 * SLAB * LD};
     const int chunk = blockIdx.x;
     const int r_begin = chunk * rows_per_chunk;
     const int r_end = min(n, r_begin + rows_per_chunk);
@@ -1279,28 +1283,45 @@ __global__ void __launch_bounds__(256, 2) k_gram_tc(const float* __restrict__ X,
     // zero the columns no panel covers (they stay zero for the whole kernel)
     for (int idx = threadIdx.x; idx < SLAB * 128; idx += 256) {
         const int rl = idx >> 7, cl = idx & 127;
-        if (cl >= kx) Xs[rl][cl] = 0.f;
-        if (cl >= ky) Ys[rl][cl] = 0.f;
+        for (int bb = 0; bb < 2; bb++) {
+            if (cl >= kx) xbuf[bb][rl * LD + cl] = 0.f;
+            if (cl >= ky) ybuf[bb][rl * LD + cl] = 0.f;
+        }
     }
-    for (int rt = r_begin; rt < r_end; rt += SLAB) {
-        // slab of SLAB rows: panel p of a block holds these rows contiguously
-        // (SLAB * KS floats), so consecutive threads read consecutive float4s
-        const int nx = px * SLAB * V_PER_ROW, ny = py * SLAB * V_PER_ROW;
+    // slab of SLAB rows into buffer bb by asynchronous 16-byte copies (rows
+    // past the chunk zero-filled): panel p of a block holds these rows
+    // contiguously, so consecutive threads copy consecutive pieces; the copy
+    // of the next slab runs while the current one is multiplied
+    const int nx = px * SLAB * V_PER_ROW, ny = same ? 0 : py * SLAB * V_PER_ROW;
+    auto issue_slab = [&](int rt, int bb) {
         for (int idx = threadIdx.x; idx < nx + ny; idx += 256) {
             const bool isx = idx < nx;
             const int e = isx ? idx : idx - nx;
             const int p = e / (SLAB * V_PER_ROW), rem = e % (SLAB * V_PER_ROW);
             const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
             const int r = rt + rl;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < r_end) {
-                const float* src = (isx ? X : Y) + (size_t)p * n * KS + (size_t)r * KS + c;
-                v = __ldcs(reinterpret_cast<const float4*>(src));
-            }
-            float* dst = isx ? &Xs[rl][p * KS + c] : &Ys[rl][p * KS + c];
-            *reinterpret_cast<float4*>(dst) = v;
+            const float* src = (isx ? X : Y) + (size_t)p * n * KS + (size_t)(r < r_end ? r : r_begin) * KS + c;
+            float* dst = (isx ? xbuf[bb] : ybuf[bb]) + rl * LD + p * KS + c;
+            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                         "r"(r < r_end ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    __syncthreads();
+    if (r_begin < r_end) issue_slab(r_begin, 0);
+    for (int rt = r_begin, it = 0; rt < r_end; rt += SLAB, it++) {
+        const int bb = it & 1;
+        if (rt + SLAB < r_end) {
+            issue_slab(rt + SLAB, bb ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
+        const float(*Xs)[LD] = reinterpret_cast<const float(*)[LD]>(xbuf[bb]);
+        const float(*Ys)[LD] = reinterpret_cast<const float(*)[LD]>(ybuf[bb]);
 #pragma unroll 1
         for (int k0 = 0; k0 < SLAB; k0 += 8) {
             // A = X^T (M = output rows, K = slab rows), two 16-row tiles per warp
@@ -1368,10 +1389,18 @@ cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, d
         if (chunks < 1) chunks = 1;
         const float* Xf = reinterpret_cast<const float*>(X);
         const float* Yf = reinterpret_cast<const float*>(Y);
-        if (ks == 8) k_gram_tc<8><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
-        else if (ks == 16) k_gram_tc<16><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
-        else if (ks == 32) k_gram_tc<32><<<chunks, 256, 0, st>>>(Xf, kx, Yf, ky, n, rpc, part);
+        const int smem = 4 * 32 * 136 * (int)sizeof(float);  // [2][X, Y][32][136]
+#define VNE_GRAM_TC(KSV)                                                                                     \
+        if (ks == KSV) {                                                                                     \
+            cudaError_t e = cudaFuncSetAttribute(k_gram_tc<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+            if (e != cudaSuccess) return e;                                                                  \
+            k_gram_tc<KSV><<<chunks, 256, smem, st>>>(Xf, kx, Yf, ky, n, rpc, part);                        \
+        }
+        VNE_GRAM_TC(8)
+        else VNE_GRAM_TC(16)
+        else VNE_GRAM_TC(32)
         else return cudaErrorInvalidValue;
+#undef VNE_GRAM_TC
         int total = kx * ky;
         k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
         return cudaGetLastError();
@@ -1470,7 +1499,7 @@ __global__ void __launch_bounds__(256) k_apply_tc(const float* __restrict__ In, 
     const int lda = kp + 4;  // = 4 (mod 8): conflict-free A fragments
     uint32_t* Bh = smu;
     uint32_t* Bl = Bh + (size_t)kp * LDB;
-    float* As = reinterpret_cast<float*>(Bl + (size_t)kp * LDB);  // [64][lda]
+    float* As0 = reinterpret_cast<float*>(Bl + (size_t)kp * LDB);  // [2][64][lda]: double-buffered row tiles
     for (int idx = threadIdx.x; idx < kp * 128; idx += 256) {
         const int k = idx >> 7, c = idx & 127;
         const float x = (k < kin && c < kout) ? (float)(coef * M[(size_t)k * kout + c]) : 0.f;
@@ -1478,32 +1507,43 @@ __global__ void __launch_bounds__(256) k_apply_tc(const float* __restrict__ In, 
         Bh[k * LDB + c] = hi;
         Bl[k * LDB + c] = to_tf32(x - __uint_as_float(hi));
     }
-    // columns kin..kp of the row tile stay zero
-    for (int idx = threadIdx.x; idx < 64 * (kp - kin); idx += 256) {
+    // columns kin..kp of both row-tile buffers stay zero
+    for (int idx = threadIdx.x; idx < 2 * 64 * (kp - kin); idx += 256) {
         const int rl = idx / (kp - kin), c = kin + idx % (kp - kin);
-        As[rl * lda + c] = 0.f;
+        As0[rl * lda + c] = 0.f;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp >> 1, wn = warp & 1;
     const int g = lane >> 2, tq = lane & 3;
     const int pin = kin / KS;
     const int ntiles = (n + 63) / 64;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // Row tile `tile` into buffer `buf` by asynchronous 16-byte copies (rows
+    // past n are zero-filled): panel p holds rows r0.. contiguously, so
+    // consecutive threads copy consecutive 16-byte pieces.  The copy of the
+    // next tile runs while the current one is multiplied.
+    auto issue_tile = [&](int tile, int buf) {
         const int r0 = tile * 64;
-        __syncthreads();
-        // panel p holds rows r0.. contiguously: consecutive threads read
-        // consecutive float4s
+        float* As = As0 + (size_t)buf * 64 * lda;
         for (int idx = threadIdx.x; idx < pin * 64 * V_PER_ROW; idx += 256) {
             const int p = idx / (64 * V_PER_ROW), rem = idx % (64 * V_PER_ROW);
             const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
             const int r = r0 + rl;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < n) v = __ldcs(reinterpret_cast<const float4*>(In + (size_t)p * n * KS + (size_t)r * KS + c));
-            float* d = As + rl * lda + p * KS + c;
-            d[0] = v.x;
-            d[1] = v.y;
-            d[2] = v.z;
-            d[3] = v.w;
+            const float* src = In + (size_t)p * n * KS + (size_t)(r < n ? r : 0) * KS + c;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(As + rl * lda + p * KS + c);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(r < n ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (blockIdx.x < ntiles) issue_tile(blockIdx.x, 0);
+    for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, it++) {
+        const int r0 = tile * 64;
+        const float* As = As0 + (size_t)(it & 1) * 64 * lda;
+        if (tile + (int)gridDim.x < ntiles) {
+            issue_tile(tile + gridDim.x, (it + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
         float acc[8][4];
@@ -1549,6 +1589,7 @@ __global__ void __launch_bounds__(256) k_apply_tc(const float* __restrict__ In, 
                     Out[o] = v;
                 }
             }
+        __syncthreads();  // the buffer just read is the target of the next copy but one
     }
 }
 
@@ -1563,7 +1604,7 @@ cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const 
     if (sizeof(T) == 4 && kin > 0 && kout > 0 && kin % ks == 0) {
         // tensor-core path (FP32 data)
         const int kp = (kin + 7) & ~7;
-        const size_t smem_tc = (2 * (size_t)kp * 136 + 64 * (size_t)(kp + 4)) * 4;
+        const size_t smem_tc = (2 * (size_t)kp * 136 + 2 * 64 * (size_t)(kp + 4)) * 4;
         dim3 g1(ntiles < sms ? ntiles : sms);
         const float* Inf = reinterpret_cast<const float*>(In);
         const float* In2f = reinterpret_cast<const float*>(In2);

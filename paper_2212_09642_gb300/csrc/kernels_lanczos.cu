@@ -165,9 +165,20 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     constexpr int RPI = VNE_THREADS / KS;
     const int gc = panel * KS + c;
     RowSum<T> rs;
-    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
-        int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        rs.add(source_value_t<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg));
+    // four rows per pass, their node ids loaded first (same row order as a
+    // plain loop, so the sums are unchanged)
+    for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPI) {
+        int ids[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPI;
+            ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPI;
+            if (r < t.row_end) rs.add(source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg));
+        }
     }
     __shared__ double red[VNE_THREADS];
     red[threadIdx.x] = rs.total();
@@ -199,11 +210,29 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
     const bool live = gc < p.src.ncols;
     T* out = p.w1 + (size_t)panel * p.n_total * KS;
     RowSum<T> rs;
-    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
-        int id = p.node_id ? p.node_id[r] : r - sg.row_begin;
-        const T v = live ? source_value_t<T, KS>(p.src, p.panel_src, r, id, gc, p.n_total, t.seg) - mu : (T)0;
-        out[(size_t)r * KS + c] = v;
-        rs.add(v * v);
+    for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPI) {
+        int ids[4];
+        T vals[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPI;
+            ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPI;
+            vals[u] = (live && r < t.row_end)
+                          ? source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg) - mu
+                          : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPI;
+            if (r < t.row_end) {
+                out[(size_t)r * KS + c] = vals[u];
+                rs.add(vals[u] * vals[u]);
+            }
+        }
     }
     __shared__ double red[VNE_THREADS];
     red[threadIdx.x] = rs.total();
