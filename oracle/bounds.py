@@ -132,10 +132,13 @@ def probing_heuristic_d(T1, T2, T3, eps_abs, d_max=64):
     """d* = max over k in {2, 3} of min{d : C q^d / d^k <= eps_abs}, with C, q
     fitted from |T_{d+1} - T_d| = C q^d / d^k at d = 1, 2.  A k whose fitted q
     is >= 1 does not describe a decaying error and is skipped; None when
-    neither k fits."""
+    neither k fits.  Degenerate data: e1 = 0 means C = 0 (d = 1); e2 = 0 means
+    q = 0, a modelled error of e1 at d = 1 and 0 from d = 2 on."""
     e1, e2 = abs(T2 - T1), abs(T3 - T2)
     if e1 == 0.0:
         return 1
+    if e2 == 0.0:
+        return 1 if e1 <= eps_abs else 2
     best = None
     for k in (2, 3):
         q = (2.0 ** k) * e2 / e1
