@@ -238,17 +238,73 @@ vne_status vne_entropy_hutchpp(vne_matrix *mat, int32_t sketch_cols, int32_t hut
  * T_d = sum_l psi(v_l), v_l the indicator of colour class l.
  *   coloring   int32[n] colours 0..s-1 (host), or NULL to compute the greedy
  *              distance-`distance` colouring (Algorithm 1, nodes by
- *              descending degree, ties by ascending id) on the host.
+ *              descending degree, ties by ascending id) with
+ *              vne_matrix_coloring.
  *   poles      as in vne_quadform_batch (NULL: polynomial Lanczos).
  *   num_colors output s (may be NULL). */
 vne_status vne_entropy_probing(vne_matrix *mat, const int32_t *coloring, int32_t distance,
                                int32_t krylov_steps, const double *poles, int32_t num_poles,
                                const vne_options *opt, double *estimate, int32_t *num_colors);
 
+/* ---- probing method with the choice of d (Section 5.1, Algorithm 2)
+ * Target: |estimate - S| <~ eps S (a heuristic, not a guarantee).
+ *   1. T_1, T_2, T_3: probing at d = 1, 2, 3 (colourings by
+ *      vne_matrix_coloring).  T_1's quadratic forms stop when the Theorem
+ *      4.4 estimate of each is <= eps/2 x psi_l; then eps_abs = eps/2 x T_1
+ *      (T_1 <= S for a graph Laplacian) and every later quadratic form stops
+ *      at <= eps_abs |V_l| / n (eq. algorithm-probing-quadform-error-
+ *      requirement-abs), so the sum is within eps_abs of T_d.
+ *   2. d from the fit of |S - T_d| ~ C q^d / d^k to |T_2 - T_1|, |T_3 - T_2|
+ *      for k = 2 and 3, the larger of the two smallest d with a modelled
+ *      error <= eps_abs (eq. probing-heuristic-convergence).  Without a
+ *      decaying fit: the smallest d with |T_{d+1} - T_d| <= eps_abs.  d is
+ *      capped at d_max.
+ *   3. estimate = T_d (reused when d <= 3).
+ * The Lanczos quadratures use krylov_steps as the step limit and the
+ * options' check_every / spectrum_min (quad_tol is ignored).  Polynomial
+ * Lanczos only.  report may be NULL.  EINVAL: eps outside (0, 1),
+ * krylov_steps outside [1, 128], d_max outside [1, 1024]. */
+#define VNE_PROBING_RULE_FIT 0          /* d from the fitted error model */
+#define VNE_PROBING_RULE_DIFFERENCES 1  /* d from consecutive differences */
+#define VNE_PROBING_RULE_CAPPED 2       /* d = d_max before the target was met */
+typedef struct vne_probing_report {
+    double t[3];           /* T_1, T_2, T_3 */
+    double eps_abs;        /* eps/2 x T_1 */
+    int32_t distance;      /* d of the estimate */
+    int32_t num_colors;    /* colours of the distance-d colouring */
+    int32_t colors_d[3];   /* colours at d = 1, 2, 3 */
+    int32_t steps_d[3];    /* Lanczos steps at d = 1, 2, 3 (largest over blocks) */
+    int32_t steps_chosen;  /* Lanczos steps at the chosen d */
+    int32_t rule;          /* VNE_PROBING_RULE_* */
+    int32_t evaluated;     /* T_1..T_evaluated were computed in sequence */
+    int32_t reserved;
+} vne_probing_report;
+vne_status vne_entropy_probing_auto(vne_matrix *mat, double eps, int32_t krylov_steps, int32_t d_max,
+                                    const vne_options *opt, double *estimate, vne_probing_report *report);
+
 /* Greedy distance-d colouring of a symmetric CSR pattern (Algorithm 1) on
  * the host: colors int32[n] receives colours 0..s-1, *num_colors = s. */
 vne_status vne_greedy_coloring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                                int32_t distance, int32_t *colors, int32_t *num_colors);
+
+/* Greedy distance-d colouring (Algorithm 1, Section 3.1) of the matrix's
+ * graph on the device: the colouring Algorithm 1 computes (nodes by
+ * descending degree, ties by ascending caller id, each node the smallest
+ * colour not used by an earlier node within distance `distance`), node for
+ * node.  Nodes are coloured in rounds, each node as soon as every node of
+ * higher priority in its distance-d ball has its colour.  For distance >= 3
+ * a ball is de-duplicated in shared memory; when one does not fit (more than
+ * about 1500 nodes within distance d - 1) the sweep runs on the host instead
+ * and gives the same colours.
+ *   colors         host int32[n] (may be NULL): colours in the caller's
+ *                  numbering (the numbering of vne_create_density_matrix's
+ *                  input, whatever the relabelling).
+ *   num_colors     s (may be NULL).
+ *   device_rounds  rounds run on the device, 0 when the host sweep ran (may
+ *                  be NULL).
+ * EINVAL for distance < 1. */
+vne_status vne_matrix_coloring(vne_matrix *mat, int32_t distance, int32_t *colors, int32_t *num_colors,
+                               int32_t *device_rounds);
 
 /* ---- kernel-level entry points (device pointers; used by the tests) ---
  * Y = A X for a block of k columns, X and Y device arrays [n][k] row-major

@@ -1,0 +1,326 @@
+// Greedy distance-d colouring (Algorithm 1, Section 3.1) on the device.
+//
+// Algorithm 1 visits the nodes in a fixed priority order (descending degree,
+// ties by ascending caller node id) and gives each node the smallest colour
+// not used by an earlier node within geodesic distance d.  The colour of a
+// node therefore depends only on the colours of the higher-priority nodes of
+// its d-ball.  The device version colours, in rounds, every node all of whose
+// higher-priority d-ball neighbours are already coloured (Jones-Plassmann
+// with the greedy order as priority): such a node sees exactly the colours
+// the sequential sweep would have shown it, so the result is Algorithm 1's
+// colouring node for node, whatever the order in which the rounds run.
+//
+// A node stays uncoloured while some uncoloured node of higher priority lies
+// in its d-ball; that node is remembered (the "blocker") and the ball is
+// searched again only once the blocker has its colour.  Colours are written
+// once and never change, so a node may read colours written during the same
+// round: a stale "uncoloured" only postpones it to the next round, and no
+// node of lower priority in its ball can be coloured before it.
+//
+// The d-ball is walked level by level.  For d <= 2 the levels are the CSR
+// slices themselves (repeats are harmless: the test and the colour mark are
+// idempotent).  For d >= 3 the nodes of levels 1..d-1 are de-duplicated in a
+// per-warp open-addressing table in shared memory; a ball that does not fit
+// sets the overflow flag and the caller uses the host sweep instead.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace vne {
+
+namespace {
+
+constexpr int kCWarps = 4;          // warps per CTA
+constexpr int kWin = 1024;          // colours per mex window (32 words of 32 bits)
+constexpr int kHashSlots = 2048;    // d >= 3: de-duplication table per warp
+constexpr int kBallCap = 1024;      // d >= 3: nodes of levels 2..d-1 kept as frontiers
+
+__device__ __forceinline__ int ld_color(const int32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ void st_color(int32_t* p, int v) { __stcg(p, v); }
+
+__device__ __forceinline__ uint32_t hash_node(int32_t w) {
+    uint32_t x = (uint32_t)w * 0x9E3779B1u;
+    return x >> 21;  // 11 bits: kHashSlots = 2048
+}
+
+// Priority key: smaller = earlier in Algorithm 1's order.
+__global__ void k_color_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ node_id, int64_t n,
+                             uint64_t* __restrict__ key, int32_t* __restrict__ color, int32_t* __restrict__ blk,
+                             int32_t* __restrict__ list) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t deg = (uint32_t)(rowptr[v + 1] - rowptr[v]);
+        const uint32_t id = node_id ? (uint32_t)node_id[v] : (uint32_t)v;
+        key[v] = ((uint64_t)(0x7fffffffu - deg) << 32) | id;
+        color[v] = -1;
+        blk[v] = -1;
+        list[v] = (int32_t)v;
+    }
+}
+
+// Per-warp scratch in shared memory.
+struct WarpScratch {
+    uint32_t win[32];      // mex window bitmap
+    int32_t excl[32];      // flattened enumeration: exclusive degree prefix per frontier slot
+    int32_t start[32];     //   and the CSR start of each frontier node
+};
+
+struct BallCtx {
+    int32_t v;
+    uint64_t kv;
+    int base;               // first colour of the mex window
+    int32_t blocker;        // per lane: an uncoloured higher-priority node seen, else -1
+};
+
+__device__ __forceinline__ void visit(int32_t w, const uint64_t* __restrict__ key, const int32_t* color,
+                                      BallCtx& b, WarpScratch& ws) {
+    const int c = ld_color(color + w);
+    if (c < 0) {
+        if (w != b.v && __ldg(key + w) < b.kv) b.blocker = w;
+    } else if (c >= b.base && c < b.base + kWin) {
+        const int o = c - b.base;
+        atomicOr(&ws.win[o >> 5], 1u << (o & 31));
+    }
+}
+
+// Insert w into the warp's table: 1 = new, 0 = present, -1 = table full.
+__device__ __forceinline__ int table_insert(int32_t* table, int32_t w) {
+    uint32_t h = hash_node(w);
+    for (int probe = 0; probe < kHashSlots; probe++) {
+        const int32_t old = atomicCAS(&table[h], -1, w);
+        if (old == -1) return 1;
+        if (old == w) return 0;
+        h = (h + 1) & (kHashSlots - 1);
+    }
+    return -1;
+}
+
+// Visit every neighbour of the `cnt` frontier nodes fr[0..cnt) with the warp
+// (a flattened, load-balanced enumeration of their adjacency lists).  With a
+// table, new nodes are inserted and, if `append`, stored in ball[] as the
+// next frontier.  Returns true (warp-uniform) once a lane has seen a blocker
+// or the table overflowed.
+__device__ __forceinline__ bool expand(const int32_t* fr, int cnt, const int32_t* __restrict__ rowptr,
+                       const int32_t* __restrict__ col, const uint64_t* __restrict__ key, const int32_t* color,
+                       BallCtx& b, WarpScratch& ws, int32_t* table, bool append, int32_t* ball, int* nball,
+                       int* nins, bool& overflow) {
+    const int lane = threadIdx.x & 31;
+    for (int f0 = 0; f0 < cnt; f0 += 32) {
+        const int i = f0 + lane;
+        const int32_t u = i < cnt ? fr[i] : -1;
+        int s = 0, deg = 0;
+        if (u >= 0) {
+            s = rowptr[u];
+            deg = rowptr[u + 1] - s;
+        }
+        int inc = deg;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, inc, 31);
+        ws.excl[lane] = inc - deg;
+        ws.start[lane] = s;
+        __syncwarp();
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+            const int t = t0 + lane;
+            if (t < tot) {
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (ws.excl[j + step] <= t) j += step;
+                const int32_t w = col[ws.start[j] + t - ws.excl[j]];
+                visit(w, key, color, b, ws);
+                if (table) {
+                    const int r = table_insert(table, w);
+                    if (r < 0) {
+                        overflow = true;
+                    } else if (r == 1) {
+                        const int q = atomicAdd(nins, 1);
+                        if (q >= kHashSlots * 3 / 4) overflow = true;
+                        if (append) {
+                            const int pos = atomicAdd(nball, 1);
+                            if (pos < kBallCap) ball[pos] = w;
+                            else overflow = true;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (__any_sync(0xffffffffu, b.blocker >= 0 || overflow)) return true;
+    }
+    return false;
+}
+
+// One search of v's d-ball with mex window [base, base + kWin).  Returns the
+// colour (>= 0), -1 when a blocker was found (*blocker set), -2 when the ball
+// did not fit the per-warp table, -3 when every colour of the window is used.
+__device__ __forceinline__ int search_ball(int32_t v, int d, int base, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ col, const uint64_t* __restrict__ key, const int32_t* color,
+                           WarpScratch& ws, int32_t* table, int32_t* ball, int* nball, int* nins, int32_t* self,
+                           int32_t* blocker_out) {
+    const int lane = threadIdx.x & 31;
+    BallCtx b{v, __ldg(key + v), base, -1};
+    ws.win[lane] = 0u;
+    const bool dedup = d >= 3;
+    if (dedup) {
+        for (int i = lane; i < kHashSlots; i += 32) table[i] = -1;
+        if (lane == 0) {
+            *nball = 0;
+            *nins = 0;
+            *self = v;
+        }
+        __syncwarp();
+        if (lane == 0) table_insert(table, v);
+    } else if (lane == 0) {
+        *self = v;
+    }
+    __syncwarp();
+    bool overflow = false;
+    bool stop = expand(self, 1, rowptr, col, key, color, b, ws, dedup ? table : nullptr, false, ball, nball, nins,
+                       overflow);
+    if (!stop && d >= 2) {
+        const int32_t rb = rowptr[v];
+        stop = expand(col + rb, rowptr[v + 1] - rb, rowptr, col, key, color, b, ws, dedup ? table : nullptr, d > 2,
+                      ball, nball, nins, overflow);
+    }
+    int lb = 0;
+    for (int lev = 3; lev <= d && !stop; lev++) {
+        __syncwarp();
+        const int le = min(*nball, kBallCap);
+        if (le == lb) break;  // the ball is exhausted
+        // level lev - 1 lives in ball[lb, le); the new level is appended after it
+        stop = expand(ball + lb, le - lb, rowptr, col, key, color, b, ws, table, lev < d, ball, nball, nins, overflow);
+        lb = le;
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, overflow)) return -2;
+    const unsigned hasb = __ballot_sync(0xffffffffu, b.blocker >= 0);
+    if (hasb) {
+        *blocker_out = __shfl_sync(0xffffffffu, b.blocker, __ffs(hasb) - 1);
+        return -1;
+    }
+    const uint32_t word = ws.win[lane];
+    const unsigned free_lanes = __ballot_sync(0xffffffffu, word != 0xffffffffu);
+    if (!free_lanes) return -3;
+    const int L = __ffs(free_lanes) - 1;
+    const uint32_t wl = __shfl_sync(0xffffffffu, word, L);
+    return base + L * 32 + (__ffs(~wl) - 1);
+}
+
+// One round over the list of uncoloured nodes.  Counters rotate over three
+// slots: round r reads cnt[r % 3], appends the nodes that stay uncoloured to
+// cnt[(r + 1) % 3] and clears cnt[(r + 2) % 3] (the input of round r - 1 and
+// the output of round r + 1).
+__global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
+    extern __shared__ int32_t dyn[];  // d >= 3: per warp kHashSlots table + kBallCap ball
+    __shared__ WarpScratch ws_all[kCWarps];
+    __shared__ int nball_all[kCWarps], nins_all[kCWarps];
+    __shared__ int32_t self_all[kCWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = p.round;
+    int* cnt = p.cnt;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
+    const int total = cnt[r % 3];
+    int* cout = cnt + (r + 1) % 3;
+    if (__ldcg(p.overflow) != 0) return;
+    const int32_t* in = (r & 1) ? p.list[1] : p.list[0];
+    int32_t* out = (r & 1) ? p.list[0] : p.list[1];
+    WarpScratch& ws = ws_all[warp];
+    int32_t* table = p.d >= 3 ? dyn + warp * (kHashSlots + kBallCap) : nullptr;
+    int32_t* ball = p.d >= 3 ? table + kHashSlots : nullptr;
+    const int nw = gridDim.x * kCWarps;
+    for (int i = blockIdx.x * kCWarps + warp; i < total; i += nw) {
+        const int32_t v = in[i];
+        const int32_t b = p.blk[v];
+        if (b >= 0 && ld_color(p.color + b) < 0) {
+            if (lane == 0) out[atomicAdd(cout, 1)] = v;
+            continue;
+        }
+        int base = 0, res;
+        int32_t blocker = -1;
+        for (;;) {
+            res = search_ball(v, p.d, base, p.rowptr, p.col, p.key, p.color, ws, table, ball, &nball_all[warp],
+                              &nins_all[warp], &self_all[warp], &blocker);
+            // every colour of the window is taken: the next window (the
+            // ball has at most n nodes, so this ends)
+            if (res != -3 || base > (1 << 30)) break;
+            base += kWin;
+        }
+        if (lane == 0) {
+            if (res >= 0) {
+                st_color(p.color + v, res);
+                atomicMax(p.ncolors, res + 1);
+            } else {
+                if (res == -1) p.blk[v] = blocker;
+                else atomicExch(p.overflow, 1);
+                out[atomicAdd(cout, 1)] = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_color_scatter(const int32_t* __restrict__ color, const int32_t* __restrict__ node_id, int64_t n,
+                                int32_t* __restrict__ out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[node_id ? node_id[v] : v] = color[v];
+}
+
+__global__ void k_color_hist(const int32_t* __restrict__ color, int64_t n, int32_t* __restrict__ counts) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(counts + color[v], 1);
+}
+
+int sm_count() {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    return sms;
+}
+
+int flat_grid(int64_t n) {
+    const int64_t want = (n + 255) / 256, cap = (int64_t)sm_count() * 8;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_color_init(const int32_t* rowptr, const int32_t* node_id, int64_t n, uint64_t* key,
+                              int32_t* color, int32_t* blk, int32_t* list, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_color_init<<<flat_grid(n), 256, 0, st>>>(rowptr, node_id, n, key, color, blk, list);
+    return cudaGetLastError();
+}
+
+size_t color_round_smem(int d) { return d >= 3 ? (size_t)kCWarps * (kHashSlots + kBallCap) * sizeof(int32_t) : 0; }
+
+cudaError_t launch_color_round(const ColorRound& p, cudaStream_t st) {
+    const size_t smem = color_round_smem(p.d);
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_color_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = sm_count() * (p.d >= 3 ? 4 : 8);
+    k_color_round<<<grid, kCWarps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_color_scatter(const int32_t* color, const int32_t* node_id, int64_t n, int32_t* out,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_color_scatter<<<flat_grid(n), 256, 0, st>>>(color, node_id, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_color_hist(const int32_t* color, int64_t n, int32_t* counts, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_color_hist<<<flat_grid(n), 256, 0, st>>>(color, n, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace vne

@@ -172,6 +172,29 @@ cudaError_t launch_cg_init(CgState st, const double* norm2, cudaStream_t);
 cudaError_t launch_gather_probe(const void* table, uint64_t table_bytes, int row_bytes, uint64_t count, uint32_t seed,
                                 const void* stream, uint64_t stream_bytes, float* sink, cudaStream_t st);
 
+// Greedy distance-d colouring on the device (coloring.cu).  key[v] orders the
+// nodes as Algorithm 1 does (descending degree, then ascending caller id);
+// color[v] = -1 until coloured; blk[v] = last blocker seen.
+struct ColorRound {
+    const int32_t* rowptr;
+    const int32_t* col;
+    const uint64_t* key;
+    int32_t* color;
+    int32_t* blk;
+    int32_t* list[2];   // uncoloured nodes: read list[r & 1], append to list[(r + 1) & 1]
+    int32_t* cnt;       // [3] rotating list lengths
+    int32_t* ncolors;   // max colour + 1
+    int32_t* overflow;  // set when a d-ball (d >= 3) does not fit the per-warp table
+    int32_t d, round;
+};
+cudaError_t launch_color_init(const int32_t* rowptr, const int32_t* node_id, int64_t n, uint64_t* key,
+                              int32_t* color, int32_t* blk, int32_t* list, cudaStream_t st);
+cudaError_t launch_color_round(const ColorRound& p, cudaStream_t st);
+// out[node_id[v]] = color[v] (caller numbering); counts[c] += |{v : color[v] = c}|
+cudaError_t launch_color_scatter(const int32_t* color, const int32_t* node_id, int64_t n, int32_t* out,
+                                 cudaStream_t st);
+cudaError_t launch_color_hist(const int32_t* color, int64_t n, int32_t* counts, cudaStream_t st);
+
 // Matrix assembly (assemble.cu).  bad[0] / bad[1]: smallest nonzero index
 // with an out-of-range column / a self-loop (pattern matrices), ~0 if none.
 cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int64_t n, int pattern,

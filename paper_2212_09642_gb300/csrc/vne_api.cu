@@ -16,6 +16,7 @@
 // j the global probe column, i the node id in the caller's numbering.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -426,13 +427,16 @@ std::vector<double> download(vne_ctx* ctx, const double* d, size_t count);
 
 // Adaptive stopping of a block (Theorem 4.4): after every `check` steps the
 // quadratures and the error estimates of all columns are computed; the block
-// stops once every estimate is at most tol x |psi|.
+// stops once every estimate is at most tol x |psi|, or, with `abs`, at most
+// abs[c] for each real column c of the block.
 struct Adaptive {
     double tol = 0.0;
     int check = 5;
     double lam_min = 0.0;  // <= 0: half the smallest positive Ritz value per column
     double lam_max = 0.0;
     int grid = 1000;
+    const double* abs = nullptr;  // per-column absolute tolerances of this block
+    int ncols = 0;                // real columns covered by `abs`
 };
 
 template <typename T>
@@ -639,7 +643,10 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
             ctx->launches += 2;
             std::vector<double> hp = download(ctx, psi, SK), he = download(ctx, est + 2 * SK, SK);
             bool done = true;
-            for (int c = 0; c < SK && done; c++) done = he[c] <= ad->tol * fabs(hp[c]);
+            if (ad->abs)
+                for (int c = 0; c < ad->ncols && done; c++) done = he[c] <= ad->abs[c];
+            else
+                for (int c = 0; c < SK && done; c++) done = he[c] <= ad->tol * fabs(hp[c]);
             if (done) break;
         }
     } else if (!graph || ctx->profile || cap != cudaStreamCaptureStatusNone) {
@@ -750,7 +757,8 @@ void check_ks(vne_ctx* ctx, int ks) {
 
 // Quadratic forms of one source over all its columns, in blocks.
 template <typename T>
-std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource src, int ncols, int m) {
+std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource src, int ncols, int m,
+                              const double* abs_tol = nullptr) {
     vne_ctx* ctx = M->ctx;
     Problem* P = matrix_problem(M, o);
     Sched sc = resolve_sched(M, o);
@@ -767,8 +775,18 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
         ad.lam_min = o->spectrum_min;
         ad.lam_max = M->normM * M->scale;
     }
+    if (abs_tol) {
+        ad.tol = 1.0;  // enables the adaptive loop; the per-column tolerances decide
+        ad.check = o && o->check_every > 0 ? o->check_every : 5;
+        ad.lam_min = o ? o->spectrum_min : 0.0;
+        ad.lam_max = M->normM * M->scale;
+    }
     for (int b0 = 0; b0 < ncols; b0 += lim) {
         int K = std::min(lim, ncols - b0);
+        if (abs_tol) {
+            ad.abs = abs_tol + b0;
+            ad.ncols = K;
+        }
         StartSource s = src;
         s.ncols = K;
         if (s.kind == SRC_RADEMACHER || s.kind == SRC_INDICATOR) s.col_begin = src.col_begin + b0;
@@ -1658,6 +1676,104 @@ extern "C" vne_status vne_entropy_hutchpp(vne_matrix* M, int32_t sketch_cols, in
     VNE_API_END(ctx)
 }
 
+namespace {
+
+// Greedy distance-d colouring (Algorithm 1) of M's graph on the device, in
+// rounds of k_color_round; the colours land in workspace `name` in the
+// caller's node numbering.  Returns the number of rounds, or 0 when a d-ball
+// (d >= 3) did not fit the per-warp table; then nothing is written and the
+// caller colours on the host.
+int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out, int32_t* s) {
+    vne_ctx* ctx = M->ctx;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = M->n;
+    uint64_t* key = ws_get_t<uint64_t>(ctx, "col.key", n);
+    int32_t* color = ws_get_t<int32_t>(ctx, "col.color", n);
+    int32_t* blk = ws_get_t<int32_t>(ctx, "col.blk", n);
+    int32_t* l0 = ws_get_t<int32_t>(ctx, "col.l0", n);
+    int32_t* l1 = ws_get_t<int32_t>(ctx, "col.l1", n);
+    int32_t* ctr = ws_get_t<int32_t>(ctx, "col.ctr", 8, true);  // cnt[3], ncolors, overflow
+    VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, color, blk, l0, st));
+    const int32_t n32 = (int32_t)n;
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(ctr, &n32, sizeof(n32), cudaMemcpyHostToDevice, st));
+    ColorRound p{};
+    p.rowptr = M->d_rowptr;
+    p.col = M->d_col;
+    p.key = key;
+    p.color = color;
+    p.blk = blk;
+    p.list[0] = l0;
+    p.list[1] = l1;
+    p.cnt = ctr;
+    p.ncolors = ctr + 3;
+    p.overflow = ctr + 4;
+    p.d = d;
+    int r = 0;
+    int64_t prev = n;
+    int32_t h[8];
+    for (;;) {
+        // every round colours at least the first uncoloured node in the
+        // greedy order, so a batch of rounds always makes progress
+        const int batch = prev > 4096 ? 4 : 16;
+        for (int b = 0; b < batch; b++, r++) {
+            p.round = r;
+            VNE_TRY_CUDA(ctx, launch_color_round(p, st));
+            ctx->launches++;
+        }
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+        if (h[4]) return 0;
+        const int64_t left = h[r % 3];
+        if (left == 0) break;
+        VNE_REQUIRE(ctx, left < prev, VNE_EDEVICE, "device colouring made no progress (%lld nodes left)",
+                    (long long)left);
+        prev = left;
+    }
+    int32_t* dout = ws_get_t<int32_t>(ctx, name, n);
+    VNE_TRY_CUDA(ctx, launch_color_scatter(color, M->d_node_id, n, dout, st));
+    ctx->launches++;
+    *out = dout;
+    *s = h[3];
+    return r;
+}
+
+// Colours of M's graph in the caller's numbering, on the device (host sweep
+// when the device search does not fit); *rounds = device rounds, 0 = host.
+int32_t* matrix_coloring(vne_matrix* M, int d, const std::string& name, int32_t* s, int* rounds) {
+    vne_ctx* ctx = M->ctx;
+    int32_t* dcol = nullptr;
+    int r = device_coloring(M, d, name, &dcol, s);
+    if (rounds) *rounds = r;
+    if (r > 0) return dcol;
+    const int64_t n = M->n;
+    std::vector<int32_t> c2(n), col(n);
+    *s = greedy_coloring(n, M->h_rowptr.data(), host_cols(M).data(), d, c2.data());
+    if (M->perm.empty()) col.swap(c2);
+    else
+        for (int64_t i = 0; i < n; i++) col[M->perm[i]] = c2[i];
+    return upload(ctx, name, col);
+}
+
+}  // namespace
+
+extern "C" vne_status vne_matrix_coloring(vne_matrix* M, int32_t distance, int32_t* colors, int32_t* num_colors,
+                                          int32_t* device_rounds) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, distance >= 1, VNE_EINVAL, "distance must be >= 1");
+    int32_t s = 0;
+    int rounds = 0;
+    int32_t* d = matrix_coloring(M, distance, "colors", &s, &rounds);
+    if (colors && M->n)
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(colors, d, M->n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (num_colors) *num_colors = s;
+    if (device_rounds) *device_rounds = rounds;
+    VNE_API_END(ctx)
+}
+
 extern "C" vne_status vne_greedy_coloring(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t distance,
                                           int32_t* colors, int32_t* num_colors) {
     if (n < 1 || !row_ptr || !col_idx || !colors || distance < 1) return VNE_EINVAL;
@@ -1684,26 +1800,20 @@ extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring
                 "krylov_steps must be in [1, 128]");
     const int64_t n = M->n;
     // colours in the caller's node numbering
-    std::vector<int32_t> col(n);
     int32_t s = 0;
+    int32_t* dcol = nullptr;
     if (coloring) {
+        std::vector<int32_t> col(n);
         for (int64_t i = 0; i < n; i++) {
             VNE_REQUIRE(ctx, coloring[i] >= 0, VNE_EINVAL, "negative colour at node %lld", (long long)i);
             col[i] = coloring[i];
             s = std::max(s, coloring[i] + 1);
         }
+        dcol = upload(ctx, "colors", col);
     } else {
         VNE_REQUIRE(ctx, distance >= 1, VNE_EINVAL, "distance must be >= 1");
-        // colour the caller's graph (undo the relabelling for the traversal)
-        std::vector<int32_t> c2(n);
-        s = greedy_coloring(n, M->h_rowptr.data(), host_cols(M).data(), distance, c2.data());
-        if (M->perm.empty()) col.swap(c2);
-        else
-            for (int64_t i = 0; i < n; i++) col[M->perm[i]] = c2[i];
-        // Note: with a relabelled matrix the greedy order is computed on the
-        // relabelled graph, whose degree order is the same up to ties.
+        dcol = matrix_coloring(M, distance, "colors", &s, nullptr);
     }
-    int32_t* dcol = upload(ctx, "colors", col);
     StartSource src{};
     src.kind = SRC_INDICATOR;
     src.colors = dcol;
@@ -1727,6 +1837,143 @@ extern "C" vne_status vne_entropy_probing(vne_matrix* M, const int32_t* coloring
     for (double v : psi) tot += v;
     *estimate = tot;
     if (num_colors) *num_colors = s;
+    VNE_API_END(ctx)
+}
+
+namespace {
+
+// Section 5.1: d from T_1, T_2, T_3.  The model |S - T_d| ~ C q^d / d^k is
+// fitted to |T_{d+1} - T_d| at d = 1, 2 for k = 2 and k = 3 (q = 2^k e2 / e1,
+// C = e1 / q); each decaying fit (q < 1) gives the smallest d with a
+// modelled error <= eps_abs, and the larger of the two is taken.  Returns
+// -1 when neither k gives a decaying fit.  e1 = 0: d = 1; e2 = 0 (q = 0):
+// d = 1 if e1 <= eps_abs, else 2.  The result may exceed d_max by one.
+int probing_heuristic_d(double t1, double t2, double t3, double eps_abs, int d_max) {
+    const double e1 = fabs(t2 - t1), e2 = fabs(t3 - t2);
+    if (e1 == 0.0) return 1;
+    if (e2 == 0.0) return e1 <= eps_abs ? 1 : 2;
+    int best = -1;
+    for (int k = 2; k <= 3; k++) {
+        const double q = std::ldexp(1.0, k) * e2 / e1;
+        if (!(q < 1.0)) continue;
+        const double C = e1 / q;
+        int d = 1;
+        while (d <= d_max && C * std::pow(q, d) / std::pow((double)d, k) > eps_abs) d++;
+        best = std::max(best, d);
+    }
+    return best;
+}
+
+// T_d of Algorithm 2 at one distance: colour on the device, then Lanczos on
+// the colour indicators with the adaptive stop of Theorem 4.4, either
+// relative (tol_rel x psi) or per colour eps_abs |V_l| / n.
+template <typename T>
+double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_rel, double eps_abs, int* colors,
+                  int* steps) {
+    vne_ctx* ctx = M->ctx;
+    int32_t s = 0;
+    int32_t* dcol = matrix_coloring(M, d, "colors", &s, nullptr);
+    StartSource src{};
+    src.kind = SRC_INDICATOR;
+    src.colors = dcol;
+    src.col_begin = 0;
+    vne_options oo = *o;
+    std::vector<double> psi;
+    if (eps_abs > 0.0) {
+        int32_t* cnt = ws_get_t<int32_t>(ctx, "colors.count", (size_t)s, true);
+        VNE_TRY_CUDA(ctx, launch_color_hist(dcol, M->n, cnt, ctx->stream));
+        ctx->launches++;
+        std::vector<int32_t> sizes(s);
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(sizes.data(), cnt, s * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        std::vector<double> tol(s);
+        for (int l = 0; l < s; l++) tol[l] = eps_abs * (double)sizes[l] / (double)M->n;
+        oo.quad_tol = 0.0;
+        psi = quadforms<T>(M, &oo, src, s, m, tol.data());
+    } else {
+        oo.quad_tol = tol_rel;
+        psi = quadforms<T>(M, &oo, src, s, m);
+    }
+    *colors = s;
+    *steps = ctx->last_steps;
+    double tot = 0.0;
+    for (double v : psi) tot += v;
+    return tot;
+}
+
+}  // namespace
+
+extern "C" vne_status vne_entropy_probing_auto(vne_matrix* M, double eps, int32_t krylov_steps, int32_t d_max,
+                                               const vne_options* opt, double* estimate, vne_probing_report* rep) {
+    if (!M) return VNE_EINVAL;
+    vne_ctx* ctx = M->ctx;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, estimate, VNE_EINVAL, "estimate is required");
+    VNE_REQUIRE(ctx, eps > 0.0 && eps < 1.0, VNE_EINVAL, "eps must be in (0, 1)");
+    VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
+    VNE_REQUIRE(ctx, d_max >= 1 && d_max <= 1024, VNE_EINVAL, "d_max must be in [1, 1024]");
+    vne_options o = opt ? *opt : defaults();
+    vne_probing_report r{};
+    std::vector<double> T;
+    std::vector<int> cols, steps;
+    auto run = [&](int d, double tol_rel, double eps_abs) {
+        int c = 0, st = 0;
+        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, tol_rel, eps_abs, &c, &st)
+                           : probing_at<float>(M, &o, d, krylov_steps, tol_rel, eps_abs, &c, &st);
+        T.push_back(t);
+        cols.push_back(c);
+        steps.push_back(st);
+    };
+    // T_1 with the relative rule: its sum is within eps/2 of T_1 <= S
+    run(1, 0.5 * eps, 0.0);
+    const double eps_abs = 0.5 * eps * T[0];
+    run(2, 0.0, eps_abs);
+    run(3, 0.0, eps_abs);
+    int d = probing_heuristic_d(T[0], T[1], T[2], eps_abs, d_max);
+    int rule = VNE_PROBING_RULE_FIT;
+    if (d > d_max) {
+        d = d_max;
+        rule = VNE_PROBING_RULE_CAPPED;
+    } else if (d < 0) {
+        // no decaying fit: the smallest d with |T_{d+1} - T_d| <= eps_abs
+        rule = VNE_PROBING_RULE_DIFFERENCES;
+        d = 1;
+        for (;;) {
+            if (d >= d_max) {
+                d = d_max;
+                rule = VNE_PROBING_RULE_CAPPED;
+                break;
+            }
+            if ((int)T.size() < d + 1) run(d + 1, 0.0, eps_abs);
+            if (fabs(T[d] - T[d - 1]) <= eps_abs) break;
+            d++;
+        }
+    }
+    if ((int)T.size() < d) {
+        // T_d at a distance not evaluated yet (the distances in between are not needed)
+        int c = 0, st = 0;
+        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, 0.0, eps_abs, &c, &st)
+                           : probing_at<float>(M, &o, d, krylov_steps, 0.0, eps_abs, &c, &st);
+        r.num_colors = c;
+        r.steps_chosen = st;
+        *estimate = t;
+    } else {
+        r.num_colors = cols[d - 1];
+        r.steps_chosen = steps[d - 1];
+        *estimate = T[d - 1];
+    }
+    for (int i = 0; i < 3; i++) {
+        r.t[i] = T[i];
+        r.colors_d[i] = cols[i];
+        r.steps_d[i] = steps[i];
+    }
+    r.eps_abs = eps_abs;
+    r.distance = d;
+    r.rule = rule;
+    r.evaluated = (int32_t)T.size();
+    if (rep) *rep = r;
     VNE_API_END(ctx)
 }
 

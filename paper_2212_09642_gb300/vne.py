@@ -83,6 +83,9 @@ def _declare(lib):
         "vne_entropy_probing": (st, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                      ctypes.POINTER(vne_options), _PD, _PI32]),
         "vne_greedy_coloring": (st, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _PI32]),
+        "vne_matrix_coloring": (st, [_P, ctypes.c_int32, _P, _PI32, _PI32]),
+        "vne_entropy_probing_auto": (st, [_P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(vne_options), _PD, ctypes.POINTER(vne_probing_report)]),
         "vne_spmm": (st, [_P, _P, _P, ctypes.c_int32]),
         "vne_tridiag_quadrature": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_rademacher": (st, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
@@ -135,7 +138,7 @@ def exported_symbols():
 _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
-               "vne_greedy_coloring", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
+               "vne_greedy_coloring", "vne_matrix_coloring", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
@@ -290,6 +293,34 @@ def vne_greedy_coloring(n, row_ptr, col_idx, distance):
     _check(load().vne_greedy_coloring(int(n), _ptr(row_ptr), _ptr(col_idx), int(distance), _ptr(colors),
                                       ctypes.byref(s)))
     return colors, s.value
+
+
+class vne_probing_report(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double * 3), ("eps_abs", ctypes.c_double), ("distance", ctypes.c_int32),
+                ("num_colors", ctypes.c_int32), ("colors_d", ctypes.c_int32 * 3), ("steps_d", ctypes.c_int32 * 3),
+                ("steps_chosen", ctypes.c_int32), ("rule", ctypes.c_int32), ("evaluated", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def vne_entropy_probing_auto(ctx, mat, eps, krylov_steps=60, d_max=64, opt=None):
+    """Probing with the heuristic choice of d: (estimate, report dict)."""
+    est = ctypes.c_double()
+    rep = vne_probing_report()
+    o = opt if opt is not None else options()
+    _check(load().vne_entropy_probing_auto(mat, float(eps), int(krylov_steps), int(d_max), ctypes.byref(o),
+                                           ctypes.byref(est), ctypes.byref(rep)), ctx)
+    return est.value, dict(T=list(rep.t), eps_abs=rep.eps_abs, d=rep.distance, colors=rep.num_colors,
+                           colors_d=list(rep.colors_d), steps_d=list(rep.steps_d), steps=rep.steps_chosen,
+                           rule=rep.rule, evaluated=rep.evaluated)
+
+
+def vne_matrix_coloring(ctx, mat, n, distance):
+    """Greedy distance-d colouring of the matrix's graph on the device, in the
+    caller's numbering: (colours, s, device rounds; 0 rounds = host sweep)."""
+    colors = np.zeros(n, dtype=np.int32)
+    s, rounds = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().vne_matrix_coloring(mat, int(distance), _ptr(colors), ctypes.byref(s), ctypes.byref(rounds)), ctx)
+    return colors, s.value, rounds.value
 
 
 def vne_spmm(ctx, mat, X, Y, k):
