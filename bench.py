@@ -53,8 +53,8 @@ def parse():
                     help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
     ap.add_argument("--vectors", type=int, default=112)
     ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant[,interleave] (skips the autotuner)")
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
-                    help="c2 = the headline workload; c1/c3/c4/c5 print measurement lines of the other configs")
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c6"], default="c2",
+                    help="c2 = the headline workload; c1/c3/c4/c5/c6 print measurement lines of the other configs")
     ap.add_argument("--requests", type=int, default=400, help="c5: number of queries")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: Poisson arrival rate (queries/s)")
     return ap.parse_args()
@@ -487,25 +487,59 @@ def run_other(args):
         t1 = time.perf_counter()
         mat = vne.matrix_from_graph(ctx, g, fp64=False, reorder="rcm")
         t_asm = time.perf_counter() - t1
+        # the device colouring alone (Algorithm 1 in rounds), checked against the host sweep
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vne.vne_matrix_coloring(ctx, mat, g.n, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dcolors, ds, rounds = vne.vne_matrix_coloring(ctx, mat, g.n, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dev_col = {"ms": e0.elapsed_time(e1), "rounds": rounds, "colors": ds,
+                   "equal_to_host_sweep": bool(np.array_equal(dcolors, colors)), "host_sweep_s": t_col}
         # SpMM schedule tuned on a block of one column per colour (cached in the context)
         tuned, _ = vne.vne_autotune(ctx, mat, s, 8)
         opt = vne.options(cg_tol=1e-8, n_inf_poles=2)
+        # one step = Algorithm 1's colouring on the device + the probing estimate
         outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
-            ctx, mat, colors, 2, 0, opt=opt, num_shifts=8), args.steps, args.warmup)
+            ctx, mat, None, 2, 0, opt=opt, num_shifts=8), args.steps, args.warmup)
         line.update(metric="entropy estimates/sec (probing d=2, rational Krylov 8 poles + 2 at infinity, RGG n=4e6)",
                     value=args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
                     config={"workload": f"C3: RGG n={g.n} avg degree 6 (seed 4), generation order, greedy distance-2 "
-                                        f"colouring ({s} colours, host {t_col:.1f} s, untimed), matrix relabelled by "
-                                        f"reverse Cuthill-McKee in vne_create_density_matrix ({t_asm:.1f} s, untimed), "
-                                        "8 log-spaced poles on [1e-4, 1] ||A||_G, multi-shift CG to recursive rel. "
-                                        "residual 1e-8",
+                                        f"colouring on the device inside each step ({s} colours), matrix relabelled "
+                                        f"by reverse Cuthill-McKee in vne_create_density_matrix ({t_asm:.1f} s, "
+                                        "untimed), 8 log-spaced poles on [1e-4, 1] ||A||_G, multi-shift CG to "
+                                        "recursive rel. residual 1e-8",
                             "nnz": g.nnz, "colors": s, "l2": "inputs larger than L2",
                             "schedule": {"panel": tuned.panel, "item_nnz": tuned.item_nnz,
                                          "step_variant": tuned.step_variant, "interleave": tuned.interleave}},
                     roofline=_roof(kst, "step", ms, "k_step (SpMM inside CG)"),
                     cg_update=_roof(kst, "cg_update", ms, "k_cg_update"),
                     cg_direction=_roof(kst, "cg_direction", ms, "k_cg_direction"),
-                    gpu_launches=int(launches), clocks=clk, estimate=outs[0][0])
+                    gpu_launches=int(launches), clocks=clk, estimate=outs[0][0], device_coloring=dev_col)
+        vne.vne_matrix_destroy(mat)
+    elif args.workload == "c6":
+        # Algorithm 2: T_1..T_3 (device colourings at d = 1, 2, 3), the fitted
+        # error model for d, T_d with per-colour tolerances (Lanczos with the
+        # Theorem 4.4 stop, checks every 2 steps)
+        n = args.n if args.n != N_NODES else 4_000_000
+        g = graphs.random_geometric(n, graphs.rgg_radius_for_degree(n, 6.0), 4)
+        mat = vne.matrix_from_graph(ctx, g, fp64=False, reorder="rcm")
+        tuned, _ = vne.vne_autotune(ctx, mat, 32, 8)
+        eps = 1e-3
+        aopt = vne.options(check_every=2)
+        outs, ms, launches, kst, clk = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing_auto(
+            ctx, mat, eps, 128, 32, opt=aopt), args.steps, args.warmup)
+        est, rep = outs[0]
+        line.update(metric="entropy estimates/sec (probing with the heuristic choice of d, eps=1e-3, RGG n=4e6)",
+                    value=args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
+                    config={"workload": f"C6: RGG n={g.n} avg degree 6 (seed 4), relabelled by reverse Cuthill-McKee; "
+                                        "probing with d from the fitted error model (T_1..T_3), device colourings "
+                                        "inside each step, Lanczos stopped by the Theorem 4.4 estimate at "
+                                        "eps/2 T_1 |V_l| / n (at most 128 steps, checks every 2)",
+                            "nnz": g.nnz, "eps": eps, "l2": "inputs larger than L2"},
+                    roofline=_roof(kst, "step", ms, "k_step"), update_kernel=_roof(kst, "update", ms, "k_update"),
+                    gpu_launches=int(launches), clocks=clk, estimate=est, report=rep)
         vne.vne_matrix_destroy(mat)
     elif args.workload == "c4":
         gs = graphs.batched_uneven_family(512, 1000, 200000, 1000)
