@@ -293,15 +293,15 @@ vne_status vne_greedy_coloring(int64_t n, const int64_t *row_ptr, const int32_t 
  * colour not used by an earlier node within distance `distance`), node for
  * node.  Nodes are coloured in rounds, each node as soon as every node of
  * higher priority in its distance-d ball has its colour.  For distance >= 3
- * a ball is de-duplicated in shared memory; when one does not fit (more than
- * about 1500 nodes within distance d - 1) the sweep runs on the host instead
- * and gives the same colours.
+ * the nodes within distance d - 1 are de-duplicated in a warp's shared
+ * memory (about 1,500 nodes) or, for larger balls, by a whole CTA in global
+ * memory (about 196,000 nodes); a larger ball gives EUNSUPPORTED (the
+ * sequential sweep would need n x 196,000 steps or more).
  *   colors         host int32[n] (may be NULL): colours in the caller's
  *                  numbering (the numbering of vne_create_density_matrix's
  *                  input, whatever the relabelling).
  *   num_colors     s (may be NULL).
- *   device_rounds  rounds run on the device, 0 when the host sweep ran (may
- *                  be NULL).
+ *   device_rounds  rounds run on the device (may be NULL).
  * EINVAL for distance < 1. */
 vne_status vne_matrix_coloring(vne_matrix *mat, int32_t distance, int32_t *colors, int32_t *num_colors,
                                int32_t *device_rounds);

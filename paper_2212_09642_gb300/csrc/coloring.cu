@@ -20,8 +20,10 @@
 // The d-ball is walked level by level.  For d <= 2 the levels are the CSR
 // slices themselves (repeats are harmless: the test and the colour mark are
 // idempotent).  For d >= 3 the nodes of levels 1..d-1 are de-duplicated in a
-// per-warp open-addressing table in shared memory; a ball that does not fit
-// sets the overflow flag and the caller uses the host sweep instead.
+// per-warp open-addressing table in shared memory; a node whose ball does
+// not fit is searched again in the same round by a whole CTA with a table in
+// global memory (k_color_big), and one that does not fit there either sets
+// the overflow flag (the caller reports the colouring as unsupported).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -194,7 +196,10 @@ __device__ __forceinline__ int search_ball(int32_t v, int d, int base, const int
         const int le = min(*nball, kBallCap);
         if (le == lb) break;  // the ball is exhausted
         // level lev - 1 lives in ball[lb, le); the new level is appended after it
-        stop = expand(ball + lb, le - lb, rowptr, col, key, color, b, ws, table, lev < d, ball, nball, nins, overflow);
+        // the last level is only visited: no insertion, so the table holds
+        // the nodes within distance d - 1
+        stop = expand(ball + lb, le - lb, rowptr, col, key, color, b, ws, lev < d ? table : nullptr, lev < d, ball,
+                      nball, nins, overflow);
         lb = le;
     }
     __syncwarp();
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
     int32_t* ball = p.d >= 3 ? table + kHashSlots : nullptr;
     const int nw = gridDim.x * kCWarps;
     for (int i = blockIdx.x * kCWarps + warp; i < total; i += nw) {
+        if (__shfl_sync(0xffffffffu, lane == 0 ? __ldcg(p.overflow) : 0, 0) != 0) break;
         const int32_t v = in[i];
         const int32_t b = p.blk[v];
         if (b >= 0 && ld_color(p.color + b) < 0) {
@@ -255,9 +261,15 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
             if (res >= 0) {
                 st_color(p.color + v, res);
                 atomicMax(p.ncolors, res + 1);
+            } else if (res == -1) {
+                p.blk[v] = blocker;
+                out[atomicAdd(cout, 1)] = v;
+            } else if (p.biglist) {
+                // the ball does not fit the warp's table: the CTA-wide search
+                // of k_color_big takes the node in this round
+                p.biglist[atomicAdd(p.bigcnt + (r & 1), 1)] = v;
             } else {
-                if (res == -1) p.blk[v] = blocker;
-                else atomicExch(p.overflow, 1);
+                atomicExch(p.overflow, 1);
                 out[atomicAdd(cout, 1)] = v;
             }
         }
@@ -274,6 +286,204 @@ __global__ void k_color_scatter(const int32_t* __restrict__ color, const int32_t
 __global__ void k_color_hist(const int32_t* __restrict__ color, int64_t n, int32_t* __restrict__ counts) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(counts + color[v], 1);
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide search for balls that do not fit a warp's table (d >= 3): the same
+// level-by-level walk with 256 threads, de-duplicated in a per-CTA table in
+// global memory.  Entries carry the search's epoch, so a table never needs
+// clearing: an entry of an older epoch counts as empty.
+
+constexpr int kBigThreads = 256;
+constexpr int kBigTableBits = 18;
+constexpr int kBigTable = 1 << kBigTableBits;  // entries per CTA
+constexpr int kBigBall = 1 << 18;              // frontier nodes per CTA
+constexpr int kBigWin = kBigThreads * 32;      // colours per mex window
+
+struct BigShared {
+    uint32_t win[kBigThreads];
+    int32_t excl[kBigThreads];
+    int32_t start[kBigThreads];
+    int32_t wpre[kBigThreads / 32];
+    int32_t tot, stop, blocker, overflow, nball, nins, mex, self;
+    uint32_t epoch;
+};
+
+__device__ __forceinline__ int big_insert(uint64_t* tab, uint32_t epoch, int32_t w) {
+    uint32_t h = ((uint32_t)w * 0x9E3779B1u) >> (32 - kBigTableBits);
+    const uint64_t mine = ((uint64_t)epoch << 32) | (uint32_t)w;
+    for (int probe = 0; probe < kBigTable; probe++) {
+        uint64_t cur = __ldcg(reinterpret_cast<const unsigned long long*>(tab + h));
+        if ((uint32_t)(cur >> 32) != epoch) {
+            const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(tab + h), (unsigned long long)cur,
+                                           (unsigned long long)mine);
+            if (old == cur) return 1;
+            cur = old;  // taken in this epoch by another thread of the CTA
+        }
+        if ((int32_t)(uint32_t)cur == w) return 0;
+        h = (h + 1) & (kBigTable - 1);
+    }
+    return -1;
+}
+
+// Visit the neighbours of fr[0..cnt) with the whole CTA.  Returns true (CTA
+// uniform) once a blocker or an overflow has been seen.
+__device__ __forceinline__ bool big_expand(const int32_t* fr, int cnt, const ColorRound& p, BigShared& sh, uint64_t* tab,
+                           int32_t* ball, bool insert, bool append, int32_t v, uint64_t kv, int base) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t epoch = sh.epoch;
+    for (int f0 = 0; f0 < cnt; f0 += kBigThreads) {
+        const int i = f0 + tid;
+        const int32_t u = i < cnt ? fr[i] : -1;
+        int s = 0, deg = 0;
+        if (u >= 0) {
+            s = p.rowptr[u];
+            deg = p.rowptr[u + 1] - s;
+        }
+        int inc = deg;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += t;
+        }
+        if (lane == 31) sh.wpre[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const int x0 = lane < kBigThreads / 32 ? sh.wpre[lane] : 0;
+            int x = x0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += t;
+            }
+            if (lane < kBigThreads / 32) sh.wpre[lane] = x - x0;
+            if (lane == kBigThreads / 32 - 1) sh.tot = x;
+        }
+        __syncthreads();
+        sh.excl[tid] = inc - deg + sh.wpre[warp];
+        sh.start[tid] = s;
+        __syncthreads();
+        const int tot = sh.tot;
+        for (int t = tid; t < tot; t += kBigThreads) {
+            int j = 0;
+#pragma unroll
+            for (int step = kBigThreads / 2; step > 0; step >>= 1)
+                if (sh.excl[j + step] <= t) j += step;
+            const int32_t w = p.col[sh.start[j] + t - sh.excl[j]];
+            const int c = ld_color(p.color + w);
+            if (c < 0) {
+                if (w != v && __ldg(p.key + w) < kv) {
+                    atomicCAS(&sh.blocker, -1, w);
+                    sh.stop = 1;
+                }
+            } else if (c >= base && c < base + kBigWin) {
+                const int o = c - base;
+                atomicOr(&sh.win[o >> 5], 1u << (o & 31));
+            }
+            if (insert) {
+                const int r = big_insert(tab, epoch, w);
+                if (r < 0) {
+                    sh.overflow = 1;
+                    sh.stop = 1;
+                } else if (r == 1) {
+                    if (atomicAdd(&sh.nins, 1) >= kBigTable / 4 * 3) {
+                        sh.overflow = 1;
+                        sh.stop = 1;
+                    }
+                    if (append) {
+                        const int pos = atomicAdd(&sh.nball, 1);
+                        if (pos < kBigBall) {
+                            ball[pos] = w;
+                        } else {
+                            sh.overflow = 1;
+                            sh.stop = 1;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (sh.stop) return true;
+    }
+    return false;
+}
+
+// Same results as search_ball: colour, -1 blocker (sh.blocker), -2 overflow,
+// -3 window full.
+__device__ __forceinline__ int big_search(int32_t v, int base, const ColorRound& p, BigShared& sh, uint64_t* tab, int32_t* ball) {
+    const int tid = threadIdx.x;
+    const uint64_t kv = __ldg(p.key + v);
+    if (tid == 0) {
+        sh.stop = 0;
+        sh.blocker = -1;
+        sh.overflow = 0;
+        sh.nball = 0;
+        sh.nins = 0;
+        sh.mex = 0x7fffffff;
+        sh.self = v;
+        sh.epoch = ++p.epoch[blockIdx.x];
+        big_insert(tab, sh.epoch, v);
+    }
+    sh.win[tid] = 0u;
+    __syncthreads();
+    bool stop = big_expand(&sh.self, 1, p, sh, tab, ball, true, false, v, kv, base);
+    if (!stop) {
+        const int32_t rb = p.rowptr[v];
+        stop = big_expand(p.col + rb, p.rowptr[v + 1] - rb, p, sh, tab, ball, p.d > 2, p.d > 2, v, kv, base);
+    }
+    int lb = 0;
+    for (int lev = 3; lev <= p.d && !stop; lev++) {
+        const int le = min(sh.nball, kBigBall);
+        if (le == lb) break;
+        stop = big_expand(ball + lb, le - lb, p, sh, tab, ball, lev < p.d, lev < p.d, v, kv, base);
+        lb = le;
+    }
+    __syncthreads();
+    if (sh.overflow) return -2;
+    if (sh.blocker >= 0) return -1;
+    const uint32_t word = sh.win[tid];
+    if (word != 0xffffffffu) atomicMin(&sh.mex, tid * 32 + (__ffs(~word) - 1));
+    __syncthreads();
+    const int m = sh.mex;
+    return m == 0x7fffffff ? -3 : base + m;
+}
+
+__global__ void __launch_bounds__(kBigThreads) k_color_big(ColorRound p) {
+    __shared__ BigShared sh;
+    const int r = p.round;
+    int* bc = p.bigcnt;
+    const int total = bc[r & 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) bc[(r + 1) & 1] = 0;
+    if (total == 0 || __ldcg(p.overflow) != 0) return;
+    int* cout = p.cnt + (r + 1) % 3;
+    int32_t* out = (r & 1) ? p.list[0] : p.list[1];
+    uint64_t* tab = p.bigtab + (size_t)blockIdx.x * kBigTable;
+    int32_t* ball = p.bigball + (size_t)blockIdx.x * kBigBall;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        if (threadIdx.x == 0) sh.stop = __ldcg(p.overflow);
+        __syncthreads();
+        if (sh.stop) break;
+        __syncthreads();
+        const int32_t v = p.biglist[i];
+        int base = 0, res;
+        for (;;) {
+            res = big_search(v, base, p, sh, tab, ball);
+            if (res != -3 || base > (1 << 30)) break;
+            base += kBigWin;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (res >= 0) {
+                st_color(p.color + v, res);
+                atomicMax(p.ncolors, res + 1);
+            } else {
+                if (res == -1) p.blk[v] = sh.blocker;
+                else atomicExch(p.overflow, 1);
+                out[atomicAdd(cout, 1)] = v;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 int sm_count() {
@@ -307,6 +517,15 @@ cudaError_t launch_color_round(const ColorRound& p, cudaStream_t st) {
     }
     const int grid = sm_count() * (p.d >= 3 ? 4 : 8);
     k_color_round<<<grid, kCWarps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+int color_big_ctas() { return sm_count(); }
+size_t color_big_table_entries() { return (size_t)kBigTable; }
+size_t color_big_ball_entries() { return (size_t)kBigBall; }
+
+cudaError_t launch_color_big(const ColorRound& p, cudaStream_t st) {
+    k_color_big<<<color_big_ctas(), kBigThreads, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -184,12 +184,22 @@ struct ColorRound {
     int32_t* list[2];   // uncoloured nodes: read list[r & 1], append to list[(r + 1) & 1]
     int32_t* cnt;       // [3] rotating list lengths
     int32_t* ncolors;   // max colour + 1
-    int32_t* overflow;  // set when a d-ball (d >= 3) does not fit the per-warp table
+    int32_t* overflow;  // set when a d-ball (d >= 3) does not fit even the per-CTA table
+    int32_t* biglist;   // d >= 3: nodes whose ball does not fit a warp's table (NULL: set overflow instead)
+    int32_t* bigcnt;    // [2] rotating lengths of biglist
+    uint64_t* bigtab;   // per CTA of k_color_big: open-addressing table (epoch << 32 | node)
+    int32_t* bigball;   // per CTA: frontier storage
+    uint32_t* epoch;    // per CTA: search counter (table entries of older searches count as empty)
     int32_t d, round;
 };
 cudaError_t launch_color_init(const int32_t* rowptr, const int32_t* node_id, int64_t n, uint64_t* key,
                               int32_t* color, int32_t* blk, int32_t* list, cudaStream_t st);
 cudaError_t launch_color_round(const ColorRound& p, cudaStream_t st);
+// d >= 3: the nodes of biglist, one CTA each, with a table in global memory.
+cudaError_t launch_color_big(const ColorRound& p, cudaStream_t st);
+int color_big_ctas();
+size_t color_big_table_entries();
+size_t color_big_ball_entries();
 // out[node_id[v]] = color[v] (caller numbering); counts[c] += |{v : color[v] = c}|
 cudaError_t launch_color_scatter(const int32_t* color, const int32_t* node_id, int64_t n, int32_t* out,
                                  cudaStream_t st);

@@ -1679,10 +1679,10 @@ extern "C" vne_status vne_entropy_hutchpp(vne_matrix* M, int32_t sketch_cols, in
 namespace {
 
 // Greedy distance-d colouring (Algorithm 1) of M's graph on the device, in
-// rounds of k_color_round; the colours land in workspace `name` in the
-// caller's node numbering.  Returns the number of rounds, or 0 when a d-ball
-// (d >= 3) did not fit the per-warp table; then nothing is written and the
-// caller colours on the host.
+// rounds of k_color_round (and k_color_big for balls too large for a warp);
+// the colours land in workspace `name` in the caller's node numbering.
+// Returns the number of rounds, or 0 when a ball (d >= 3) did not fit even a
+// CTA's table; then nothing is written.
 int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out, int32_t* s) {
     vne_ctx* ctx = M->ctx;
     cudaStream_t st = ctx->stream;
@@ -1692,7 +1692,7 @@ int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out
     int32_t* blk = ws_get_t<int32_t>(ctx, "col.blk", n);
     int32_t* l0 = ws_get_t<int32_t>(ctx, "col.l0", n);
     int32_t* l1 = ws_get_t<int32_t>(ctx, "col.l1", n);
-    int32_t* ctr = ws_get_t<int32_t>(ctx, "col.ctr", 8, true);  // cnt[3], ncolors, overflow
+    int32_t* ctr = ws_get_t<int32_t>(ctx, "col.ctr", 8, true);  // cnt[3], ncolors, overflow, bigcnt[2]
     VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, color, blk, l0, st));
     const int32_t n32 = (int32_t)n;
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(ctr, &n32, sizeof(n32), cudaMemcpyHostToDevice, st));
@@ -1708,6 +1708,16 @@ int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out
     p.ncolors = ctr + 3;
     p.overflow = ctr + 4;
     p.d = d;
+    if (d >= 3) {
+        // balls too large for a warp's shared-memory table go to one CTA
+        // each (k_color_big); the tables start empty (epoch 0 everywhere)
+        const size_t ctas = (size_t)color_big_ctas();
+        p.biglist = ws_get_t<int32_t>(ctx, "col.big", n);
+        p.bigcnt = ctr + 5;
+        p.bigtab = ws_get_t<uint64_t>(ctx, "col.bigtab", ctas * color_big_table_entries(), true);
+        p.bigball = ws_get_t<int32_t>(ctx, "col.bigball", ctas * color_big_ball_entries());
+        p.epoch = ws_get_t<uint32_t>(ctx, "col.epoch", ctas, true);
+    }
     int r = 0;
     int64_t prev = n;
     int32_t h[8];
@@ -1719,6 +1729,10 @@ int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out
             p.round = r;
             VNE_TRY_CUDA(ctx, launch_color_round(p, st));
             ctx->launches++;
+            if (p.biglist) {
+                VNE_TRY_CUDA(ctx, launch_color_big(p, st));
+                ctx->launches++;
+            }
         }
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
         VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
@@ -1737,21 +1751,19 @@ int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out
     return r;
 }
 
-// Colours of M's graph in the caller's numbering, on the device (host sweep
-// when the device search does not fit); *rounds = device rounds, 0 = host.
+// Colours of M's graph in the caller's numbering, on the device; *rounds =
+// device rounds.  A distance-(d - 1) ball beyond the CTA table (about 196,000
+// nodes) is refused: the sequential sweep over such balls would take
+// n x 196,000 steps or more.
 int32_t* matrix_coloring(vne_matrix* M, int d, const std::string& name, int32_t* s, int* rounds) {
     vne_ctx* ctx = M->ctx;
     int32_t* dcol = nullptr;
     int r = device_coloring(M, d, name, &dcol, s);
+    VNE_REQUIRE(ctx, r > 0, VNE_EUNSUPPORTED,
+                "distance-%d colouring: a ball of radius %d holds more than %zu nodes; pass a colouring", d, d - 1,
+                color_big_table_entries() / 4 * 3);
     if (rounds) *rounds = r;
-    if (r > 0) return dcol;
-    const int64_t n = M->n;
-    std::vector<int32_t> c2(n), col(n);
-    *s = greedy_coloring(n, M->h_rowptr.data(), host_cols(M).data(), d, c2.data());
-    if (M->perm.empty()) col.swap(c2);
-    else
-        for (int64_t i = 0; i < n; i++) col[M->perm[i]] = c2[i];
-    return upload(ctx, name, col);
+    return dcol;
 }
 
 }  // namespace

@@ -56,19 +56,42 @@ def test_device_coloring_large_rgg_and_ba(vctx):
         assert np.array_equal(got, want), (g.n, d, int(np.sum(got != want)))
 
 
-def test_ball_overflow_uses_host_sweep(vctx):
-    """A star with 1700 leaves at d = 3: the hub's neighbourhood does not fit
-    the per-warp table, the host sweep runs and gives Algorithm 1's colours
-    (all distinct: every pair of nodes is within distance 2)."""
-    g = graphs.star(1701)
+def test_large_balls_searched_by_a_cta(vctx):
+    """Balls too large for a warp's table (d >= 3) are searched by a whole CTA
+    with a table in global memory: a star with 1700 leaves (every pair within
+    distance 2, so all colours distinct) and a hub joined to 1600 nodes of a
+    1800-node cycle, whose neighbours each have 1600 nodes within distance 2."""
+    ring = np.arange(1, 1801)
+    hub_ring = graphs.from_edges(1801, np.concatenate([np.zeros(1600, dtype=np.int64), ring]),
+                                 np.concatenate([np.arange(1, 1601), np.roll(ring, 1)]))
+    for g, d in [(graphs.star(1701), 3), (hub_ring, 3), (hub_ring, 4)]:
+        mat = vne.matrix_from_graph(vctx, g, reorder=True)
+        try:
+            got, s, rounds = vne.vne_matrix_coloring(vctx, mat, g.n, d)
+        finally:
+            vne.vne_matrix_destroy(mat)
+        want = coloring.greedy_distance_coloring(g, d)
+        assert rounds > 0
+        assert np.array_equal(got, want), (g.n, d, int(np.sum(got != want)))
+    assert s == int(want.max()) + 1
+
+
+def test_ball_beyond_the_cta_table_is_refused(vctx):
+    """A hub with 200,000 neighbours at d = 3: the radius-2 ball of every leaf
+    holds the whole graph, more than a CTA's table; the call reports
+    EUNSUPPORTED instead of colouring (the context stays usable)."""
+    g = graphs.star(200001)
     mat = vne.matrix_from_graph(vctx, g)
     try:
-        got, s, rounds = vne.vne_matrix_coloring(vctx, mat, g.n, 3)
+        with pytest.raises(vne.VneError) as e:
+            vne.vne_matrix_coloring(vctx, mat, g.n, 3)
+        assert e.value.status == vne.VNE_EUNSUPPORTED
+        got, s, rounds = vne.vne_matrix_coloring(vctx, mat, g.n, 1)
     finally:
         vne.vne_matrix_destroy(mat)
-    assert rounds == 0
-    assert np.array_equal(got, coloring.greedy_distance_coloring(g, 3))
-    assert s == g.n
+    want = np.ones(g.n, dtype=np.int32)
+    want[0] = 0  # the hub first (highest degree), then every leaf next to it
+    assert s == 2 and np.array_equal(got, want)
 
 
 def test_probing_without_colouring_uses_algorithm_1(vctx):
