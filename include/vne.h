@@ -279,7 +279,14 @@ typedef struct vne_probing_report {
     int32_t evaluated;     /* T_1..T_evaluated were computed in sequence */
     int32_t reserved;
 } vne_probing_report;
+/* Caller-supplied colouring for vne_entropy_probing_auto (for instance an
+ * optimal colouring of a structured graph): fill colors (host int32[n],
+ * caller numbering) with a distance-`distance` colouring and return the
+ * number of colours s (colours in [0, s)), or a value < 1 on failure (the
+ * call then returns EINVAL).  Called from the calling thread. */
+typedef int32_t (*vne_coloring_fn)(void *user, int32_t distance, int64_t n, int32_t *colors);
 vne_status vne_entropy_probing_auto(vne_matrix *mat, double eps, int32_t krylov_steps, int32_t d_max,
+                                    vne_coloring_fn coloring_fn /* NULL: vne_matrix_coloring */, void *user,
                                     const vne_options *opt, double *estimate, vne_probing_report *report);
 
 /* Greedy distance-d colouring of a symmetric CSR pattern (Algorithm 1) on

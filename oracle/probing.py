@@ -111,15 +111,17 @@ def choose_distance(T, eps_abs, d_max, more):
         d += 1
 
 
-def probing_auto(A, graph, eps, m_max, check=5, d_max=64, lam_min=0.0, grid=1000, reorth="full"):
+def probing_auto(A, graph, eps, m_max, check=5, d_max=64, lam_min=0.0, grid=1000, reorth="full",
+                 coloring=None):
     """Algorithm 2 for S(A), A the density matrix of `graph`, relative target
-    eps.  Returns (estimate, report) with report keys T (T_1, T_2, T_3, ...),
+    eps.  `coloring(d)` supplies the distance-d colouring (default: Algorithm
+    1).  Returns (estimate, report) with report keys T (T_1, T_2, T_3, ...),
     eps_abs, d, rule, colors (colour count per d), steps (Lanczos steps per d)."""
     n = A.shape[0]
     rep = dict(T=[], colors={}, steps={}, psi={})
 
     def run(d, eps_abs):
-        col = greedy_distance_coloring(graph, d)
+        col = greedy_distance_coloring(graph, d) if coloring is None else np.asarray(coloring(d))
         s = int(col.max()) + 1
         V = np.zeros((n, s))
         V[np.arange(n), col] = 1.0

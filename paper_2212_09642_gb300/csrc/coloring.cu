@@ -11,8 +11,13 @@
 // colouring node for node, whatever the order in which the rounds run.
 //
 // A node stays uncoloured while some uncoloured node of higher priority lies
-// in its d-ball; that node is remembered (the "blocker") and the ball is
-// searched again only once the blocker has its colour.  Colours are written
+// in its d-ball; such a node is remembered (the "blocker") and the ball is
+// searched again only once the blocker has its colour.  The first two
+// searches of a node stop at the first blocker they meet (cheap when balls
+// are small); later ones walk the whole ball and keep the blocker latest in
+// the greedy order, whose colouring mostly comes after the others', so that
+// nodes with large balls are searched a few times rather than once per
+// higher-priority neighbour.  Colours are written
 // once and never change, so a node may read colours written during the same
 // round: a stale "uncoloured" only postpones it to the next round, and no
 // node of lower priority in its ball can be coloured before it.
@@ -48,14 +53,23 @@ __device__ __forceinline__ uint32_t hash_node(int32_t w) {
     return x >> 21;  // 11 bits: kHashSlots = 2048
 }
 
+// The stored node of a key: its low half is the caller's id, mapped back to
+// the stored numbering by inv (NULL: the numberings agree).
+__device__ __forceinline__ int32_t key_node(uint64_t k, const int32_t* __restrict__ inv) {
+    const int32_t id = (int32_t)(uint32_t)k;
+    return inv ? __ldg(inv + id) : id;
+}
+
 // Priority key: smaller = earlier in Algorithm 1's order.
 __global__ void k_color_init(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ node_id, int64_t n,
-                             uint64_t* __restrict__ key, int32_t* __restrict__ color, int32_t* __restrict__ blk,
-                             int32_t* __restrict__ list) {
+                             uint64_t* __restrict__ key, int32_t* __restrict__ inv, int32_t* __restrict__ tries,
+                             int32_t* __restrict__ color, int32_t* __restrict__ blk, int32_t* __restrict__ list) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t deg = (uint32_t)(rowptr[v + 1] - rowptr[v]);
         const uint32_t id = node_id ? (uint32_t)node_id[v] : (uint32_t)v;
         key[v] = ((uint64_t)(0x7fffffffu - deg) << 32) | id;
+        if (inv) inv[id] = (int32_t)v;
+        tries[v] = 0;
         color[v] = -1;
         blk[v] = -1;
         list[v] = (int32_t)v;
@@ -73,14 +87,15 @@ struct BallCtx {
     int32_t v;
     uint64_t kv;
     int base;               // first colour of the mex window
-    int32_t blocker;        // per lane: an uncoloured higher-priority node seen, else -1
+    uint64_t bkey;          // per lane: largest key of an uncoloured higher-priority node seen, else 0
 };
 
 __device__ __forceinline__ void visit(int32_t w, const uint64_t* __restrict__ key, const int32_t* color,
                                       BallCtx& b, WarpScratch& ws) {
     const int c = ld_color(color + w);
     if (c < 0) {
-        if (w != b.v && __ldg(key + w) < b.kv) b.blocker = w;
+        const uint64_t kw = __ldg(key + w);
+        if (w != b.v && kw < b.kv && kw > b.bkey) b.bkey = kw;
     } else if (c >= b.base && c < b.base + kWin) {
         const int o = c - b.base;
         atomicOr(&ws.win[o >> 5], 1u << (o & 31));
@@ -102,12 +117,12 @@ __device__ __forceinline__ int table_insert(int32_t* table, int32_t w) {
 // Visit every neighbour of the `cnt` frontier nodes fr[0..cnt) with the warp
 // (a flattened, load-balanced enumeration of their adjacency lists).  With a
 // table, new nodes are inserted and, if `append`, stored in ball[] as the
-// next frontier.  Returns true (warp-uniform) once a lane has seen a blocker
-// or the table overflowed.
+// next frontier.  Returns true (warp-uniform) once the table overflowed or,
+// with `early`, once a blocker has been seen.
 __device__ __forceinline__ bool expand(const int32_t* fr, int cnt, const int32_t* __restrict__ rowptr,
                        const int32_t* __restrict__ col, const uint64_t* __restrict__ key, const int32_t* color,
                        BallCtx& b, WarpScratch& ws, int32_t* table, bool append, int32_t* ball, int* nball,
-                       int* nins, bool& overflow) {
+                       int* nins, bool& overflow, bool early) {
     const int lane = threadIdx.x & 31;
     for (int f0 = 0; f0 < cnt; f0 += 32) {
         const int i = f0 + lane;
@@ -153,7 +168,7 @@ __device__ __forceinline__ bool expand(const int32_t* fr, int cnt, const int32_t
             }
         }
         __syncwarp();
-        if (__any_sync(0xffffffffu, b.blocker >= 0 || overflow)) return true;
+        if (__any_sync(0xffffffffu, overflow || (early && b.bkey != 0ull))) return true;
     }
     return false;
 }
@@ -164,9 +179,9 @@ __device__ __forceinline__ bool expand(const int32_t* fr, int cnt, const int32_t
 __device__ __forceinline__ int search_ball(int32_t v, int d, int base, const int32_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const uint64_t* __restrict__ key, const int32_t* color,
                            WarpScratch& ws, int32_t* table, int32_t* ball, int* nball, int* nins, int32_t* self,
-                           int32_t* blocker_out) {
+                           const int32_t* __restrict__ inv, bool early, int32_t* blocker_out) {
     const int lane = threadIdx.x & 31;
-    BallCtx b{v, __ldg(key + v), base, -1};
+    BallCtx b{v, __ldg(key + v), base, 0ull};
     ws.win[lane] = 0u;
     const bool dedup = d >= 3;
     if (dedup) {
@@ -184,11 +199,11 @@ __device__ __forceinline__ int search_ball(int32_t v, int d, int base, const int
     __syncwarp();
     bool overflow = false;
     bool stop = expand(self, 1, rowptr, col, key, color, b, ws, dedup ? table : nullptr, false, ball, nball, nins,
-                       overflow);
+                       overflow, early);
     if (!stop && d >= 2) {
         const int32_t rb = rowptr[v];
         stop = expand(col + rb, rowptr[v + 1] - rb, rowptr, col, key, color, b, ws, dedup ? table : nullptr, d > 2,
-                      ball, nball, nins, overflow);
+                      ball, nball, nins, overflow, early);
     }
     int lb = 0;
     for (int lev = 3; lev <= d && !stop; lev++) {
@@ -199,14 +214,19 @@ __device__ __forceinline__ int search_ball(int32_t v, int d, int base, const int
         // the last level is only visited: no insertion, so the table holds
         // the nodes within distance d - 1
         stop = expand(ball + lb, le - lb, rowptr, col, key, color, b, ws, lev < d ? table : nullptr, lev < d, ball,
-                      nball, nins, overflow);
+                      nball, nins, overflow, early);
         lb = le;
     }
     __syncwarp();
     if (__any_sync(0xffffffffu, overflow)) return -2;
-    const unsigned hasb = __ballot_sync(0xffffffffu, b.blocker >= 0);
-    if (hasb) {
-        *blocker_out = __shfl_sync(0xffffffffu, b.blocker, __ffs(hasb) - 1);
+    uint64_t bk = b.bkey;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(0xffffffffu, bk, off);
+        bk = o > bk ? o : bk;
+    }
+    if (bk != 0ull) {
+        *blocker_out = key_node(bk, inv);
         return -1;
     }
     const uint32_t word = ws.win[lane];
@@ -229,18 +249,31 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = p.round;
     int* cnt = p.cnt;
-    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
-    const int total = cnt[r % 3];
+    // one thread per CTA reads the shared words (all threads reading one
+    // address queue on a single L2 slice)
+    __shared__ int s_total, s_over;
+    if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) cnt[(r + 2) % 3] = 0;
+        s_total = cnt[r % 3];
+        s_over = p.d >= 3 ? __ldcg(p.overflow) : 0;
+    }
+    __syncthreads();
+    const int total = s_total;
     int* cout = cnt + (r + 1) % 3;
-    if (__ldcg(p.overflow) != 0) return;
+    if (s_over != 0) return;
     const int32_t* in = (r & 1) ? p.list[1] : p.list[0];
     int32_t* out = (r & 1) ? p.list[0] : p.list[1];
     WarpScratch& ws = ws_all[warp];
     int32_t* table = p.d >= 3 ? dyn + warp * (kHashSlots + kBallCap) : nullptr;
     int32_t* ball = p.d >= 3 ? table + kHashSlots : nullptr;
     const int nw = gridDim.x * kCWarps;
+    int it = 0;
     for (int i = blockIdx.x * kCWarps + warp; i < total; i += nw) {
-        if (__shfl_sync(0xffffffffu, lane == 0 ? __ldcg(p.overflow) : 0, 0) != 0) break;
+        // an overflow (d >= 3 only) ends the round early; the flag is read
+        // every 32 nodes, not per node: every warp reading one word per node
+        // queues on a single L2 slice
+        if (p.d >= 3 && (++it & 31) == 0 && __shfl_sync(0xffffffffu, lane == 0 ? __ldcg(p.overflow) : 0, 0) != 0)
+            break;
         const int32_t v = in[i];
         const int32_t b = p.blk[v];
         if (b >= 0 && ld_color(p.color + b) < 0) {
@@ -249,9 +282,10 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
         }
         int base = 0, res;
         int32_t blocker = -1;
+        const int tries = p.tries[v];
         for (;;) {
             res = search_ball(v, p.d, base, p.rowptr, p.col, p.key, p.color, ws, table, ball, &nball_all[warp],
-                              &nins_all[warp], &self_all[warp], &blocker);
+                              &nins_all[warp], &self_all[warp], p.inv, tries < 2, &blocker);
             // every colour of the window is taken: the next window (the
             // ball has at most n nodes, so this ends)
             if (res != -3 || base > (1 << 30)) break;
@@ -263,6 +297,7 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
                 atomicMax(p.ncolors, res + 1);
             } else if (res == -1) {
                 p.blk[v] = blocker;
+                p.tries[v] = tries + 1;
                 out[atomicAdd(cout, 1)] = v;
             } else if (p.biglist) {
                 // the ball does not fit the warp's table: the CTA-wide search
@@ -305,7 +340,8 @@ struct BigShared {
     int32_t excl[kBigThreads];
     int32_t start[kBigThreads];
     int32_t wpre[kBigThreads / 32];
-    int32_t tot, stop, blocker, overflow, nball, nins, mex, self;
+    unsigned long long bkey;
+    int32_t tot, stop, overflow, nball, nins, mex, self;
     uint32_t epoch;
 };
 
@@ -327,7 +363,7 @@ __device__ __forceinline__ int big_insert(uint64_t* tab, uint32_t epoch, int32_t
 }
 
 // Visit the neighbours of fr[0..cnt) with the whole CTA.  Returns true (CTA
-// uniform) once a blocker or an overflow has been seen.
+// uniform) once the table overflowed.
 __device__ __forceinline__ bool big_expand(const int32_t* fr, int cnt, const ColorRound& p, BigShared& sh, uint64_t* tab,
                            int32_t* ball, bool insert, bool append, int32_t v, uint64_t kv, int base) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -372,10 +408,8 @@ __device__ __forceinline__ bool big_expand(const int32_t* fr, int cnt, const Col
             const int32_t w = p.col[sh.start[j] + t - sh.excl[j]];
             const int c = ld_color(p.color + w);
             if (c < 0) {
-                if (w != v && __ldg(p.key + w) < kv) {
-                    atomicCAS(&sh.blocker, -1, w);
-                    sh.stop = 1;
-                }
+                const uint64_t kw = __ldg(p.key + w);
+                if (w != v && kw < kv) atomicMax(&sh.bkey, (unsigned long long)kw);
             } else if (c >= base && c < base + kBigWin) {
                 const int o = c - base;
                 atomicOr(&sh.win[o >> 5], 1u << (o & 31));
@@ -408,14 +442,15 @@ __device__ __forceinline__ bool big_expand(const int32_t* fr, int cnt, const Col
     return false;
 }
 
-// Same results as search_ball: colour, -1 blocker (sh.blocker), -2 overflow,
+// Same results as search_ball: colour, -1 blocker (*blocker), -2 overflow,
 // -3 window full.
-__device__ __forceinline__ int big_search(int32_t v, int base, const ColorRound& p, BigShared& sh, uint64_t* tab, int32_t* ball) {
+__device__ __forceinline__ int big_search(int32_t v, int base, const ColorRound& p, BigShared& sh, uint64_t* tab,
+                                          int32_t* ball, int32_t* blocker) {
     const int tid = threadIdx.x;
     const uint64_t kv = __ldg(p.key + v);
     if (tid == 0) {
         sh.stop = 0;
-        sh.blocker = -1;
+        sh.bkey = 0ull;
         sh.overflow = 0;
         sh.nball = 0;
         sh.nins = 0;
@@ -440,7 +475,10 @@ __device__ __forceinline__ int big_search(int32_t v, int base, const ColorRound&
     }
     __syncthreads();
     if (sh.overflow) return -2;
-    if (sh.blocker >= 0) return -1;
+    if (sh.bkey != 0ull) {
+        *blocker = key_node(sh.bkey, p.inv);
+        return -1;
+    }
     const uint32_t word = sh.win[tid];
     if (word != 0xffffffffu) atomicMin(&sh.mex, tid * 32 + (__ffs(~word) - 1));
     __syncthreads();
@@ -452,9 +490,15 @@ __global__ void __launch_bounds__(kBigThreads) k_color_big(ColorRound p) {
     __shared__ BigShared sh;
     const int r = p.round;
     int* bc = p.bigcnt;
-    const int total = bc[r & 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) bc[(r + 1) & 1] = 0;
-    if (total == 0 || __ldcg(p.overflow) != 0) return;
+    if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) bc[(r + 1) & 1] = 0;
+        sh.tot = bc[r & 1];
+        sh.stop = __ldcg(p.overflow);
+    }
+    __syncthreads();
+    const int total = sh.tot;
+    if (total == 0 || sh.stop != 0) return;
+    __syncthreads();  // sh.tot and sh.stop are reused by the searches
     int* cout = p.cnt + (r + 1) % 3;
     int32_t* out = (r & 1) ? p.list[0] : p.list[1];
     uint64_t* tab = p.bigtab + (size_t)blockIdx.x * kBigTable;
@@ -466,8 +510,9 @@ __global__ void __launch_bounds__(kBigThreads) k_color_big(ColorRound p) {
         __syncthreads();
         const int32_t v = p.biglist[i];
         int base = 0, res;
+        int32_t blocker = -1;
         for (;;) {
-            res = big_search(v, base, p, sh, tab, ball);
+            res = big_search(v, base, p, sh, tab, ball, &blocker);
             if (res != -3 || base > (1 << 30)) break;
             base += kBigWin;
             __syncthreads();
@@ -477,7 +522,7 @@ __global__ void __launch_bounds__(kBigThreads) k_color_big(ColorRound p) {
                 st_color(p.color + v, res);
                 atomicMax(p.ncolors, res + 1);
             } else {
-                if (res == -1) p.blk[v] = sh.blocker;
+                if (res == -1) p.blk[v] = blocker;
                 else atomicExch(p.overflow, 1);
                 out[atomicAdd(cout, 1)] = v;
             }
@@ -501,9 +546,10 @@ int flat_grid(int64_t n) {
 }  // namespace
 
 cudaError_t launch_color_init(const int32_t* rowptr, const int32_t* node_id, int64_t n, uint64_t* key,
-                              int32_t* color, int32_t* blk, int32_t* list, cudaStream_t st) {
+                              int32_t* inv, int32_t* tries, int32_t* color, int32_t* blk, int32_t* list,
+                              cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_color_init<<<flat_grid(n), 256, 0, st>>>(rowptr, node_id, n, key, color, blk, list);
+    k_color_init<<<flat_grid(n), 256, 0, st>>>(rowptr, node_id, n, key, inv, tries, color, blk, list);
     return cudaGetLastError();
 }
 

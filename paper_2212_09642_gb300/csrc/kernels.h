@@ -179,8 +179,10 @@ struct ColorRound {
     const int32_t* rowptr;
     const int32_t* col;
     const uint64_t* key;
+    const int32_t* inv;  // caller id -> stored node (NULL: identity)
     int32_t* color;
     int32_t* blk;
+    int32_t* tries;     // searches that ended at a blocker, per node
     int32_t* list[2];   // uncoloured nodes: read list[r & 1], append to list[(r + 1) & 1]
     int32_t* cnt;       // [3] rotating list lengths
     int32_t* ncolors;   // max colour + 1
@@ -193,7 +195,8 @@ struct ColorRound {
     int32_t d, round;
 };
 cudaError_t launch_color_init(const int32_t* rowptr, const int32_t* node_id, int64_t n, uint64_t* key,
-                              int32_t* color, int32_t* blk, int32_t* list, cudaStream_t st);
+                              int32_t* inv, int32_t* tries, int32_t* color, int32_t* blk, int32_t* list,
+                              cudaStream_t st);
 cudaError_t launch_color_round(const ColorRound& p, cudaStream_t st);
 // d >= 3: the nodes of biglist, one CTA each, with a table in global memory.
 cudaError_t launch_color_big(const ColorRound& p, cudaStream_t st);

@@ -1693,15 +1693,19 @@ int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out
     int32_t* l0 = ws_get_t<int32_t>(ctx, "col.l0", n);
     int32_t* l1 = ws_get_t<int32_t>(ctx, "col.l1", n);
     int32_t* ctr = ws_get_t<int32_t>(ctx, "col.ctr", 8, true);  // cnt[3], ncolors, overflow, bigcnt[2]
-    VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, color, blk, l0, st));
+    int32_t* inv = M->d_node_id ? ws_get_t<int32_t>(ctx, "col.inv", n) : nullptr;
+    int32_t* tries = ws_get_t<int32_t>(ctx, "col.tries", n);
+    VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, inv, tries, color, blk, l0, st));
     const int32_t n32 = (int32_t)n;
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(ctr, &n32, sizeof(n32), cudaMemcpyHostToDevice, st));
     ColorRound p{};
     p.rowptr = M->d_rowptr;
     p.col = M->d_col;
     p.key = key;
+    p.inv = inv;
     p.color = color;
     p.blk = blk;
+    p.tries = tries;
     p.list[0] = l0;
     p.list[1] = l1;
     p.cnt = ctr;
@@ -1880,11 +1884,27 @@ int probing_heuristic_d(double t1, double t2, double t3, double eps_abs, int d_m
 // the colour indicators with the adaptive stop of Theorem 4.4, either
 // relative (tol_rel x psi) or per colour eps_abs |V_l| / n.
 template <typename T>
-double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_rel, double eps_abs, int* colors,
-                  int* steps) {
+double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_rel, double eps_abs,
+                  vne_coloring_fn fn, void* user, int* colors, int* steps) {
     vne_ctx* ctx = M->ctx;
     int32_t s = 0;
-    int32_t* dcol = matrix_coloring(M, d, "colors", &s, nullptr);
+    int32_t* dcol = nullptr;
+    std::vector<int32_t> host_sizes;
+    if (fn) {
+        // the caller's colouring (e.g. an optimal one for a structured graph)
+        std::vector<int32_t> col(M->n);
+        s = fn(user, d, M->n, col.data());
+        VNE_REQUIRE(ctx, s >= 1, VNE_EINVAL, "colouring callback failed at distance %d (returned %d)", d, s);
+        host_sizes.assign(s, 0);
+        for (int64_t i = 0; i < M->n; i++) {
+            VNE_REQUIRE(ctx, col[i] >= 0 && col[i] < s, VNE_EINVAL, "colour %d of node %lld outside [0, %d)", col[i],
+                        (long long)i, s);
+            host_sizes[col[i]]++;
+        }
+        dcol = upload(ctx, "colors", col);
+    } else {
+        dcol = matrix_coloring(M, d, "colors", &s, nullptr);
+    }
     StartSource src{};
     src.kind = SRC_INDICATOR;
     src.colors = dcol;
@@ -1892,13 +1912,17 @@ double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_
     vne_options oo = *o;
     std::vector<double> psi;
     if (eps_abs > 0.0) {
-        int32_t* cnt = ws_get_t<int32_t>(ctx, "colors.count", (size_t)s, true);
-        VNE_TRY_CUDA(ctx, launch_color_hist(dcol, M->n, cnt, ctx->stream));
-        ctx->launches++;
         std::vector<int32_t> sizes(s);
-        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(sizes.data(), cnt, s * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                          ctx->stream));
-        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (fn) {
+            sizes = host_sizes;
+        } else {
+            int32_t* cnt = ws_get_t<int32_t>(ctx, "colors.count", (size_t)s, true);
+            VNE_TRY_CUDA(ctx, launch_color_hist(dcol, M->n, cnt, ctx->stream));
+            ctx->launches++;
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(sizes.data(), cnt, s * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                              ctx->stream));
+            VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
         std::vector<double> tol(s);
         for (int l = 0; l < s; l++) tol[l] = eps_abs * (double)sizes[l] / (double)M->n;
         oo.quad_tol = 0.0;
@@ -1917,7 +1941,8 @@ double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_
 }  // namespace
 
 extern "C" vne_status vne_entropy_probing_auto(vne_matrix* M, double eps, int32_t krylov_steps, int32_t d_max,
-                                               const vne_options* opt, double* estimate, vne_probing_report* rep) {
+                                               vne_coloring_fn coloring_fn, void* user, const vne_options* opt,
+                                               double* estimate, vne_probing_report* rep) {
     if (!M) return VNE_EINVAL;
     vne_ctx* ctx = M->ctx;
     VNE_API_BEGIN
@@ -1932,8 +1957,8 @@ extern "C" vne_status vne_entropy_probing_auto(vne_matrix* M, double eps, int32_
     std::vector<int> cols, steps;
     auto run = [&](int d, double tol_rel, double eps_abs) {
         int c = 0, st = 0;
-        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, tol_rel, eps_abs, &c, &st)
-                           : probing_at<float>(M, &o, d, krylov_steps, tol_rel, eps_abs, &c, &st);
+        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st)
+                           : probing_at<float>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st);
         T.push_back(t);
         cols.push_back(c);
         steps.push_back(st);
@@ -1966,8 +1991,8 @@ extern "C" vne_status vne_entropy_probing_auto(vne_matrix* M, double eps, int32_
     if ((int)T.size() < d) {
         // T_d at a distance not evaluated yet (the distances in between are not needed)
         int c = 0, st = 0;
-        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, 0.0, eps_abs, &c, &st)
-                           : probing_at<float>(M, &o, d, krylov_steps, 0.0, eps_abs, &c, &st);
+        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, 0.0, eps_abs, coloring_fn, user, &c, &st)
+                           : probing_at<float>(M, &o, d, krylov_steps, 0.0, eps_abs, coloring_fn, user, &c, &st);
         r.num_colors = c;
         r.steps_chosen = st;
         *estimate = t;

@@ -62,6 +62,10 @@ _PI32 = ctypes.POINTER(ctypes.c_int32)
 _PI64 = ctypes.POINTER(ctypes.c_int64)
 
 
+_COLORING_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                ctypes.POINTER(ctypes.c_int32))
+
+
 def _declare(lib):
     st = ctypes.c_int32
     sig = {
@@ -84,7 +88,7 @@ def _declare(lib):
                                      ctypes.POINTER(vne_options), _PD, _PI32]),
         "vne_greedy_coloring": (st, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _PI32]),
         "vne_matrix_coloring": (st, [_P, ctypes.c_int32, _P, _PI32, _PI32]),
-        "vne_entropy_probing_auto": (st, [_P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+        "vne_entropy_probing_auto": (st, [_P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _COLORING_FN, _P,
                                           ctypes.POINTER(vne_options), _PD, ctypes.POINTER(vne_probing_report)]),
         "vne_spmm": (st, [_P, _P, _P, ctypes.c_int32]),
         "vne_tridiag_quadrature": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P]),
@@ -302,13 +306,27 @@ class vne_probing_report(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-def vne_entropy_probing_auto(ctx, mat, eps, krylov_steps=60, d_max=64, opt=None):
-    """Probing with the heuristic choice of d: (estimate, report dict)."""
+def vne_entropy_probing_auto(ctx, mat, eps, krylov_steps=60, d_max=64, opt=None, coloring=None):
+    """Probing with the heuristic choice of d: (estimate, report dict).
+    coloring: optional callable d -> int array of n colours (caller numbering)
+    used instead of the device's greedy colouring."""
     est = ctypes.c_double()
     rep = vne_probing_report()
     o = opt if opt is not None else options()
-    _check(load().vne_entropy_probing_auto(mat, float(eps), int(krylov_steps), int(d_max), ctypes.byref(o),
-                                           ctypes.byref(est), ctypes.byref(rep)), ctx)
+    cb = _COLORING_FN()
+    if coloring is not None:
+        def _fill(user, d, n, out):
+            try:
+                c = np.ascontiguousarray(coloring(int(d)), dtype=np.int32)
+                if c.shape != (n,) or c.min() < 0:
+                    return 0
+                ctypes.memmove(out, c.ctypes.data, c.nbytes)
+                return int(c.max()) + 1
+            except Exception:
+                return 0
+        cb = _COLORING_FN(_fill)
+    _check(load().vne_entropy_probing_auto(mat, float(eps), int(krylov_steps), int(d_max), cb, None,
+                                           ctypes.byref(o), ctypes.byref(est), ctypes.byref(rep)), ctx)
     return est.value, dict(T=list(rep.t), eps_abs=rep.eps_abs, d=rep.distance, colors=rep.num_colors,
                            colors_d=list(rep.colors_d), steps_d=list(rep.steps_d), steps=rep.steps_chosen,
                            rule=rep.rule, evaluated=rep.evaluated)
