@@ -96,3 +96,69 @@ def rational_quadform(A, b, shifts, n_inf=2, desing=True, f=f_entropy, method="a
         return 0.0
     V = orthonormalize(rational_basis(A, c, shifts, n_inf=n_inf, method=method))
     return projected_quadform(A, V, c, f=f)
+
+
+# ---- mixed polynomial / rational Krylov (Section 5.3) ----
+#
+# The method first runs polynomial Krylov iterations (poles at infinity) and
+# switches to the finite poles once the polynomial error estimate stalls: after
+# iteration k it switches if err_est_k / err_est_{k-ell-1} >= c^ell (ell = 3,
+# c = 0.75 in the paper).  Readings: err_est_k is the Theorem 4.4 estimate
+# (geometric mean of the bounds, polynomial case) of the k-step Lanczos
+# quadrature, whose space is K_k(A, c); the rule applies from k = ell + 2 on
+# (the first k with an err_est_{k-ell-1}); an estimate of 0 (invariant Krylov
+# space) ends the polynomial phase at that k; without a switch the phase ends
+# at k_max.  The polynomial part of the space is K_k(A, c) (k - 1 poles at
+# infinity), spanned here by the Lanczos vectors, which span the same space as
+# the powers c, A c, .. and stay well conditioned for large k.
+
+def switch_index(est, ell=3, cfac=0.75):
+    """The k at which the polynomial phase ends; est[k-1] = err_est_k."""
+    est = list(est)
+    for k in range(1, len(est) + 1):
+        e = est[k - 1]
+        if e == 0.0:
+            return k
+        if k >= ell + 2 and e / est[k - ell - 2] >= cfac ** ell:
+            return k
+    return len(est)
+
+
+def polynomial_estimates(A, c, k_max, lam_min=0.0, grid=1000):
+    """err_est_k, k = 1..k_max (fewer on breakdown), and the Lanczos vectors
+    (columns) of the k_max-step run with full reorthogonalisation."""
+    from .bounds import posterior_bounds
+    from .krylov import lanczos, tridiagonal_eig
+    nA = gershgorin_norm(A)
+    alpha, beta, V = lanczos(A, c, k_max, reorth="full", norm_A=nA, keep_basis=True)
+    nb2 = float(c @ c)
+    est = []
+    for k in range(1, len(alpha) + 1):
+        if beta[k - 1] == 0.0:
+            est.append(0.0)
+            break
+        lo = lam_min
+        if not lo > 0.0:
+            theta, _ = tridiagonal_eig(alpha[:k], beta[:k - 1])
+            pos = theta[theta > 0.0]
+            lo = 0.5 * float(pos.min()) if pos.size else 0.0
+        est.append(posterior_bounds(alpha[:k], beta[:k], nb2, lo, nA, grid=grid)[2] if lo > 0.0 else np.inf)
+    return np.array(est), V
+
+
+def mixed_quadform(A, b, shifts, ell=3, cfac=0.75, k_max=12, k_poly=None, desing=True, f=f_entropy,
+                   method="auto", lam_min=0.0, grid=1000):
+    """psi on K_k(A, c) + span{(A + s I)^{-1} c}, k from the switching rule
+    (or k_poly when given).  Returns (psi, k from the rule)."""
+    c = desingularize(b) if desing else np.asarray(b, float)
+    if np.linalg.norm(c) == 0.0:
+        return 0.0, 0
+    est, V = polynomial_estimates(A, c, k_max, lam_min=lam_min, grid=grid)
+    k_rule = switch_index(est, ell, cfac)
+    k = k_rule if k_poly is None else k_poly
+    cols = [V[:, j] for j in range(min(k, V.shape[1]))]
+    if len(shifts):
+        X = shifted_solves(A, c, shifts, method=method)
+        cols += [X[:, s] for s in range(X.shape[1])]
+    Q = orthonormalize(np.column_stack(cols))
+    return projected_quadform(A, Q, c, f=f), k_rule

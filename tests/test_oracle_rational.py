@@ -63,3 +63,53 @@ def test_cg_solves_match_dense():
     Xd = rational.shifted_solves(A, c, s, method="dense")
     Xc = rational.shifted_solves(A, c, s, method="cg", rtol=1e-12)
     assert np.allclose(Xd, Xc, rtol=1e-8, atol=1e-10 * np.abs(Xd).max())
+
+
+# ---- mixed polynomial / rational Krylov (Section 5.3 switching rule) ----
+
+def test_switch_index_rule():
+    """Switch after iteration k when err_k / err_{k-ell-1} >= c^ell (ell = 3,
+    c = 0.75: 0.421875), first possible at k = ell + 2 = 5."""
+    assert rational.switch_index([0.5 ** k for k in range(1, 13)]) == 12  # ratio 0.0625: never
+    assert rational.switch_index([0.9 ** k for k in range(1, 13)]) == 5   # ratio 0.656 at once
+    est = [1.0, 0.1, 0.01, 1e-3, 1e-4, 9e-5, 8e-5, 7e-5, 6e-5, 5e-5]
+    # k = 9: 6e-5 / 1e-4 = 0.6 is the first ratio >= 0.421875 (k = 8: 7e-5 / 1e-3)
+    assert rational.switch_index(est) == 9
+    assert rational.switch_index([1.0, 0.2, 0.0, 0.1]) == 3  # invariant Krylov space
+    ratio_at_threshold = 0.75 ** 3
+    assert rational.switch_index([1.0, 1.0, 1.0, 1.0, ratio_at_threshold]) == 5
+
+
+def test_mixed_without_poles_is_lanczos_quadrature():
+    """With no finite poles the space is K_k(A, c): the projection equals the
+    k-step Lanczos (Gauss) quadrature."""
+    g = G.barabasi_albert(400, 3, 6)
+    A, _ = density.density_matrix(g)
+    b = rng.rademacher(3, g.n, 0, 1)[:, 0]
+    for k in (3, 7, 11):
+        psi, _ = rational.mixed_quadform(A, b, [], k_poly=k, k_max=12)
+        ref = krylov.lanczos_quadform(A, b, k)[0]
+        assert abs(psi - ref) <= 1e-12 * abs(ref), (k, psi, ref)
+
+
+def test_mixed_complete_graph_exact():
+    g = G.complete(30)
+    A, _ = density.density_matrix(g)
+    b = rng.rademacher(5, 30, 0, 1)[:, 0]
+    c = krylov.desingularize(b)
+    lam = 1.0 / 29
+    psi, k = rational.mixed_quadform(A, b, rational.default_shifts(A))
+    assert k == 1  # the Krylov space of c is invariant after one step
+    assert abs(psi - float(c @ c) * (-lam * math.log(lam))) <= 1e-12
+
+
+def test_mixed_matches_dense_on_small_graph():
+    """K_k(A, c) + the eight pole directions: on a 300-node graph the
+    quadrature agrees with c^T f(A) c from the dense spectrum to 1e-9."""
+    g = G.watts_strogatz(300, 6, 0.2, 9)
+    A, _ = density.density_matrix(g)
+    F = entropy.dense_matrix_function(A)
+    b = rng.rademacher(7, g.n, 0, 1)[:, 0]
+    c = krylov.desingularize(b)
+    psi, k = rational.mixed_quadform(A, b, rational.default_shifts(A))
+    assert abs(psi - float(c @ F @ c)) <= 1e-9 * float(c @ F @ c)
