@@ -514,6 +514,14 @@ def run_other(args):
                     cg_update=_roof(kst, "cg_update", ms, "k_cg_update"),
                     cg_direction=_roof(kst, "cg_direction", ms, "k_cg_direction"),
                     gpu_launches=int(launches), clocks=clk, estimate=outs[0][0], device_coloring=dev_col)
+        # the same estimate with the polynomial part chosen by the switching
+        # rule of Section 5.3 (n_inf_poles = -1) instead of two poles at infinity
+        mopt = vne.options(cg_tol=1e-8, n_inf_poles=-1)
+        outs_m, ms_m, _, _, _ = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
+            ctx, mat, None, 2, 0, opt=mopt, num_shifts=8), max(1, args.steps // 2), 1)
+        line["switching_rule"] = {"value": max(1, args.steps // 2) / (ms_m / 1e3), "unit": UNIT,
+                                  "polynomial_dim": vne.vne_ctx_last_poly_dim(ctx), "estimate": outs_m[0][0],
+                                  "diff_vs_two_poles_at_infinity": outs_m[0][0] - outs[0][0]}
         vne.vne_matrix_destroy(mat)
     elif args.workload == "c6":
         # Algorithm 2: T_1..T_3 (device colourings at d = 1, 2, 3), the fitted

@@ -71,7 +71,13 @@ typedef struct vne_options {
     int32_t panel;        /* columns per panel of the panel-major vector
                              layout (FP32: 8, 16, 32; FP64: 4, 8, 16), 0 = auto */
     int32_t item_nnz;     /* target nonzeros per warp work item, 0 = auto */
-    int32_t n_inf_poles;  /* rational mode: poles at infinity (default 2) */
+    int32_t n_inf_poles;  /* rational mode: poles at infinity, 0..3 (default
+                             2); -1: chosen per block by the switching rule of
+                             Section 5.3 (polynomial iterations until
+                             err_k / err_{k-4} >= 0.75^3 for the Theorem 4.4
+                             estimate, at most 16; the largest k over the
+                             block's columns), the polynomial part K_k(A, c)
+                             spanned by the seed CG residuals */
     int32_t cg_max_iter;  /* rational mode: multi-shift CG iteration cap */
     double cg_tol;        /* rational mode: relative residual (default 1e-8) */
     double breakdown_tol; /* Lanczos stops when beta_j <= tol * ||A||_G;
@@ -139,6 +145,10 @@ vne_status vne_ctx_graph_stats(const vne_ctx *ctx, int64_t *captured, int64_t *r
 /* Lanczos steps taken by the last quadrature call on the context (the
  * largest over its blocks; krylov_steps unless quad_tol stopped earlier). */
 vne_status vne_ctx_last_steps(const vne_ctx *ctx, int32_t *steps);
+/* Dimension k of the polynomial part K_k(A, c) the switching rule chose in the
+ * last rational call with n_inf_poles = -1 (largest over its blocks); 0 after
+ * a call with a fixed number of poles at infinity. */
+vne_status vne_ctx_last_poly_dim(const vne_ctx *ctx, int32_t *k);
 /* Throughput ceiling of the SpMM step's access pattern (a measurement aid, not
  * part of the method): `gathers` reads of random row_bytes-byte rows (32, 64
  * or 128) from a device table of table_bytes, plus one streaming read of

@@ -144,6 +144,7 @@ struct PairDots {
     const T* const* x;  // device array of block pointers, one per pair
     const T* const* y;
     double* part;       // [pairs][panels][tiles][ks]
+    int32_t tile_in_y;  // set by the launcher: grid (pairs, tiles) instead of (tiles, pairs)
 };
 
 cudaError_t launch_cg_scalars_a(const CgState&, cudaStream_t);
@@ -155,10 +156,15 @@ template <typename T>
 struct BlockTransform {
     int32_t n, K, nb, tiles_per_panel;
     const RowTile* tiles;
-    const T* in[12];
-    T* out[12];
+    const T* in[24];
+    T* out[24];
     const double* X;  // [nb][nb][K]
 };
+// Seed-CG scalars -> Lanczos tridiagonal of A (k rows, column-interleaved).
+cudaError_t launch_cg_tridiag(const double* a_hist, const double* b_hist, int K, int k, double s0, double tau,
+                              double* diag, double* off, cudaStream_t);
+// Full [nb][nb][K] Gram matrices from their upper triangles (pairs a <= b).
+cudaError_t launch_gram_mirror(const double* uniq, int nb, int K, double* full, cudaStream_t);
 cudaError_t launch_rational_pass1(const double* M, int nb, int ncols, double drop, double* X, cudaStream_t);
 cudaError_t launch_rational_pass2(const double* M, const double* K, const double* c2, int nb, int ncols, double drop,
                                   double* psi, int* rank, cudaStream_t);

@@ -37,7 +37,7 @@
 namespace vne {
 
 constexpr int kMaxShifts = 8;
-constexpr int kMaxBasis = 12;
+constexpr int kMaxBasis = 24;  // 1 + up to 15 polynomial directions + 8 poles
 
 __device__ __forceinline__ double f_ent(double x) { return x > 0.0 ? -x * log(x) : 0.0; }
 
@@ -299,8 +299,12 @@ __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, Cg
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_pair_dots(PairDots<T> pd) {
     constexpr int RPI = VNE_THREADS / KS;
-    const int pair = blockIdx.y;
-    const int panel = blockIdx.x / pd.tiles_per_panel, tile = blockIdx.x % pd.tiles_per_panel;
+    // consecutive CTAs take different pairs of the same row tile, so the
+    // tile's vectors are read from HBM once and then hit in L2 (tiles along y
+    // while they fit its 65535 limit)
+    const int pair = pd.tile_in_y ? blockIdx.x : blockIdx.y;
+    const int pt = pd.tile_in_y ? blockIdx.y : blockIdx.x;
+    const int panel = pt / pd.tiles_per_panel, tile = pt % pd.tiles_per_panel;
     const RowTile t = pd.tiles[tile];
     const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
     const size_t pofs = (size_t)panel * pd.n * KS;
@@ -483,7 +487,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_block_transform(BlockTransform<
     const RowTile t = bt.tiles[tile];
     const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
     const int col = panel * KS + c;
-    __shared__ T sx[kMaxBasis * kMaxBasis][KS];
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    T(*sx)[KS] = reinterpret_cast<T(*)[KS]>(bt_smem);  // [nb * nb][KS]
     for (int idx = threadIdx.x; idx < bt.nb * bt.nb * KS; idx += VNE_THREADS) {
         const int e = idx / KS, cc = idx % KS;
         sx[e][cc] = (T)bt.X[(size_t)e * bt.K + panel * KS + cc];
@@ -501,6 +506,38 @@ __global__ void __launch_bounds__(VNE_THREADS) k_block_transform(BlockTransform<
         }
     }
     (void)col;
+}
+
+// Lanczos tridiagonal of A from the seed CG's scalars (the CG-Lanczos
+// relation): with step lengths a_i and direction coefficients b_i of CG on
+// A + s0 I, T_{i+1,i+1} = 1/a_i + b_{i-1}/a_{i-1} - s0 (no second term at
+// i = 0) and T_{i+1,i+2} = sqrt(b_i)/a_i.  An off-diagonal at or below tau
+// (the Lanczos breakdown threshold) is set to 0: the Krylov space is
+// invariant there, and the rows after it are not used.  History rows
+// [i][K], i < k.
+__global__ void k_cg_tridiag(const double* ah, const double* bh, int K, int k, double s0, double tau,
+                             double* diag, double* off) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double prev = 0.0;  // b_{i-1} / a_{i-1}
+    for (int i = 0; i < k; i++) {
+        const double a = ah[(size_t)i * K + c], b = bh[(size_t)i * K + c];
+        const double t = sqrt(b) / a;
+        diag[(size_t)i * K + c] = 1.0 / a + prev - s0;
+        off[(size_t)i * K + c] = t > tau ? t : 0.0;
+        prev = b / a;
+    }
+}
+
+// Full [nb][nb][K] Gram layout from its upper triangle, pairs (a <= b)
+// numbered row by row.
+__global__ void k_gram_mirror(const double* uniq, int nb, int K, double* full) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nb * nb * K) return;
+    const int c = (int)(idx % K), b = (int)((idx / K) % nb), a = (int)(idx / ((size_t)K * nb));
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const size_t pr = (size_t)lo * nb - (size_t)lo * (lo - 1) / 2 + (hi - lo);
+    full[idx] = uniq[pr * K + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -536,10 +573,25 @@ cudaError_t launch_cg_direction(const CgVectors<T>& v, const CgState& st, int ks
 template <typename T>
 cudaError_t launch_pair_dots(const PairDots<T>& pd, int npairs, double* out, cudaStream_t s) {
     if (npairs <= 0) return cudaSuccess;
-    dim3 grid(pd.panels * pd.tiles_per_panel, npairs);
-    VNE_KS_SWITCH(T, pd.ks, (k_pair_dots<T, KS><<<grid, VNE_THREADS, 0, s>>>(pd)));
+    PairDots<T> q = pd;
+    const int ntile = pd.panels * pd.tiles_per_panel;
+    q.tile_in_y = ntile <= 65535 ? 1 : 0;
+    const dim3 grid = q.tile_in_y ? dim3(npairs, ntile) : dim3(ntile, npairs);
+    VNE_KS_SWITCH(T, pd.ks, (k_pair_dots<T, KS><<<grid, VNE_THREADS, 0, s>>>(q)));
     const int K = pd.panels * pd.ks;
     k_pair_reduce<<<(npairs * K + 255) / 256, 256, 0, s>>>(pd.part, npairs, pd.panels, pd.tiles_per_panel, pd.ks, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_tridiag(const double* ah, const double* bh, int K, int k, double s0, double tau, double* diag,
+                              double* off, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_cg_tridiag<<<(K + 63) / 64, 64, 0, s>>>(ah, bh, K, k, s0, tau, diag, off);
+    return cudaGetLastError();
+}
+cudaError_t launch_gram_mirror(const double* uniq, int nb, int K, double* full, cudaStream_t s) {
+    const size_t total = (size_t)nb * nb * K;
+    if (total == 0) return cudaSuccess;
+    k_gram_mirror<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(uniq, nb, K, full);
     return cudaGetLastError();
 }
 cudaError_t launch_rational_pass1(const double* M, int nb, int K, double drop, double* X, cudaStream_t s) {
@@ -553,11 +605,26 @@ cudaError_t launch_rational_pass2(const double* M, const double* Kmat, const dou
     k_rational_pass2<<<(K + 31) / 32, 32, 0, s>>>(M, Kmat, c2, nb, K, drop, psi, rank);
     return cudaGetLastError();
 }
+// the basis-change matrix (nb^2 x KS values) lives in dynamic shared memory,
+// beyond 48 KB for the largest bases
+template <typename T, int KS>
+cudaError_t block_transform_ks(const BlockTransform<T>& bt, int panels, size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_block_transform<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_block_transform<T, KS><<<panels * bt.tiles_per_panel, VNE_THREADS, smem, s>>>(bt);
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_block_transform(const BlockTransform<T>& bt, int ks, int panels, cudaStream_t s) {
     if (bt.nb > kMaxBasis) return cudaErrorInvalidValue;
-    VNE_KS_SWITCH(T, ks, (k_block_transform<T, KS><<<panels * bt.tiles_per_panel, VNE_THREADS, 0, s>>>(bt)));
-    return cudaGetLastError();
+    const size_t smem = (size_t)bt.nb * bt.nb * ks * sizeof(T);
+    cudaError_t e = cudaSuccess;
+    VNE_KS_SWITCH(T, ks, (e = block_transform_ks<T, KS>(bt, panels, smem, s)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template cudaError_t launch_cg_update<float>(const CgVectors<float>&, const CgState&, int, int, cudaStream_t);

@@ -93,6 +93,7 @@ struct vne_ctx {
     cudaStream_t cap_stream = nullptr;  // private stream the captures run on
     int64_t graphs_captured = 0, graphs_replayed = 0;
     int last_steps = 0;  // Lanczos steps of the last quadrature call (largest over its blocks)
+    int last_poly_dim = 0;  // polynomial dimension chosen by the switching rule (last rational call)
 };
 
 struct Problem;
@@ -867,11 +868,18 @@ template <typename T>
 void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int ks, const double* shifts,
                     int nshift, int n_inf, double tol, int max_iter, bool desing, int variant, double drop,
                     double drop2, std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid,
-                    int* rank_min) {
+                    int* rank_min, double lam_min = 0.0, double lam_max = 0.0, int* kpoly_out = nullptr) {
     cudaStream_t st = ctx->stream;
     VNE_REQUIRE(ctx, P.nseg == 1, VNE_EUNSUPPORTED, "rational mode needs a single matrix");
     VNE_REQUIRE(ctx, nshift >= 1 && nshift <= 8, VNE_EINVAL, "1..8 finite poles are supported");
-    VNE_REQUIRE(ctx, n_inf >= 0 && n_inf <= 3, VNE_EINVAL, "0..3 poles at infinity are supported");
+    VNE_REQUIRE(ctx, n_inf >= -1 && n_inf <= 3, VNE_EINVAL, "0..3 poles at infinity (or -1: switching rule)");
+    // n_inf = -1: the polynomial part K_k(A, c) is chosen by the switching
+    // rule of Section 5.3 (ell = 3, c = 0.75) from the polynomial error
+    // estimates of the first kMixMax CG iterations, and spanned by the seed
+    // CG residuals r_0..r_{k-1} (orthogonal, the Lanczos directions of A)
+    constexpr int kMixMax = 16, kMixEll = 3;
+    constexpr double kMixC = 0.75;
+    const bool mixed = n_inf < 0;
     const int panels = (K + ks - 1) / ks, Kp = panels * ks;
     const int n = P.n_total;
     const size_t blk = (size_t)Kp * n;
@@ -958,10 +966,16 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
     cs.any_active = ibuf + 2 * (size_t)nshift * Kp;
     VNE_TRY_CUDA(ctx, launch_cg_init(cs, norm2, st));
     ctx->launches += 1;
+    double* ah = mixed ? ws_get_t<double>(ctx, "rat.ahist", (size_t)kMixMax * Kp) : nullptr;
+    double* bh = mixed ? ws_get_t<double>(ctx, "rat.bhist", (size_t)kMixMax * Kp) : nullptr;
+    T* rh = mixed ? ws_get_t<T>(ctx, "rat.rhist", blk * (kMixMax - 1)) : nullptr;  // r_1 .. r_{kMixMax-1}
     int it = 0;
     for (; it < max_iter; it++) {
         apply_operator<T>(ctx, P, ks, Kp, v.p, v.q, s0, dq, variant, "rat.op");
         VNE_TRY_CUDA(ctx, launch_cg_scalars_a(cs, st));
+        if (mixed && it < kMixMax)
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(ah + (size_t)it * Kp, cs.a, Kp * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, st));
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
         if (ctx->profile) {
             e0 = ctx_event(ctx);
@@ -972,8 +986,14 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
             e1 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e1, st));
         }
+        if (mixed && it + 1 < kMixMax)
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(rh + (size_t)it * blk, v.r, blk * sizeof(T), cudaMemcpyDeviceToDevice,
+                                              st));
         VNE_TRY_CUDA(ctx, cudaMemsetAsync(cs.any_active, 0, sizeof(int32_t), st));
         VNE_TRY_CUDA(ctx, launch_cg_scalars_b(cs, st));
+        if (mixed && it < kMixMax)
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(bh + (size_t)it * Kp, cs.b, Kp * sizeof(double),
+                                              cudaMemcpyDeviceToDevice, st));
         if (ctx->profile) {
             e2 = ctx_event(ctx);
             VNE_TRY_CUDA(ctx, cudaEventRecord(e2, st));
@@ -1001,40 +1021,83 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
             }
         }
     }
-    // basis W = [c, A c, .., A^n_inf c, x_1..x_S] and A W
-    const int nb = 1 + n_inf + nshift;
-    T* apow = ws_get_t<T>(ctx, "rat.apow", blk * (n_inf + 1));
-    const T* prev = C;
-    for (int j = 0; j <= n_inf; j++) {
-        T* out = apow + (size_t)j * blk;
-        apply_operator<T>(ctx, P, ks, Kp, prev, out, 0.0, dq, variant, "rat.op0");
-        prev = out;
+    // polynomial part: K_{n_inf+1}(A, c) by powers of A, or, with the
+    // switching rule, K_k(A, c) by the seed residuals
+    int kpoly = n_inf + 1;
+    if (mixed) {
+        const int kk = std::min(kMixMax, it);  // CG iterations recorded
+        double* tdiag = ws_get_t<double>(ctx, "rat.tdiag", (size_t)kMixMax * Kp);
+        double* toff = ws_get_t<double>(ctx, "rat.toff", (size_t)kMixMax * Kp);
+        double* est = ws_get_t<double>(ctx, "rat.est", (size_t)kMixMax * Kp);
+        double* blo = ws_get_t<double>(ctx, "rat.blo", (size_t)2 * Kp);
+        double* ones = upload(ctx, "rat.ones", std::vector<double>(Kp, 1.0));
+        // breakdown threshold of the Lanczos engine, in units of A
+        const double tau_a = P.segs[0].tau * P.segs[0].scale;
+        VNE_TRY_CUDA(ctx, launch_cg_tridiag(ah, bh, Kp, kk, s0, tau_a, tdiag, toff, st));
+        for (int k = 1; k <= kk; k++)
+            VNE_TRY_CUDA(ctx, launch_tridiag_bounds(tdiag, toff, norm2, ones, Kp, k, Kp, lam_min, lam_max, 1000, blo,
+                                                    blo + Kp, est + (size_t)(k - 1) * Kp, st));
+        ctx->launches += 1 + kk;
+        std::vector<double> he = download(ctx, est, (size_t)std::max(kk, 1) * Kp);
+        // per column: the first k with err_k / err_{k-ell-1} >= c^ell (an
+        // estimate of 0: the Krylov space is invariant); the block takes
+        // the largest k
+        kpoly = 1;
+        for (int c = 0; c < K; c++) {
+            int kc = kk;
+            for (int k = 1; k <= kk; k++) {
+                const double e = he[(size_t)(k - 1) * Kp + c];
+                if (e == 0.0 || (k >= kMixEll + 2 && e / he[(size_t)(k - kMixEll - 2) * Kp + c] >=
+                                                       std::pow(kMixC, kMixEll))) {
+                    kc = k;
+                    break;
+                }
+            }
+            kpoly = std::max(kpoly, kc);
+        }
+        kpoly = std::max(1, std::min(kpoly, kk > 0 ? kk : 1));
+    }
+    if (kpoly_out) *kpoly_out = mixed ? kpoly : 0;
+    // basis W = [polynomial part, x_1..x_S] and A W
+    const int nb = kpoly + nshift;
+    T* apow = ws_get_t<T>(ctx, "rat.apow", blk * kpoly);
+    std::vector<const T*> W(nb), AW(nb);
+    W[0] = C;
+    if (mixed) {
+        for (int j = 1; j < kpoly; j++) W[j] = rh + (size_t)(j - 1) * blk;
+        for (int j = 0; j < kpoly; j++) {
+            apply_operator<T>(ctx, P, ks, Kp, W[j], apow + (size_t)j * blk, 0.0, dq, variant, "rat.op0");
+            AW[j] = apow + (size_t)j * blk;
+        }
+    } else {
+        const T* prev = C;
+        for (int j = 0; j < kpoly; j++) {
+            T* out = apow + (size_t)j * blk;
+            apply_operator<T>(ctx, P, ks, Kp, prev, out, 0.0, dq, variant, "rat.op0");
+            prev = out;
+        }
+        for (int j = 1; j < kpoly; j++) W[j] = apow + (size_t)(j - 1) * blk;
+        for (int j = 0; j < kpoly; j++) AW[j] = apow + (size_t)j * blk;
     }
     for (int i = 0; i < nshift; i++)  // A x_s into the (now free) direction buffers
         apply_operator<T>(ctx, P, ks, Kp, v.x[i], v.ps[i], 0.0, dq, variant, "rat.op0");
-    std::vector<const T*> W(nb), AW(nb);
-    W[0] = C;
-    for (int j = 1; j <= n_inf; j++) W[j] = apow + (size_t)(j - 1) * blk;
-    for (int j = 0; j <= n_inf; j++) AW[j] = apow + (size_t)j * blk;
     for (int i = 0; i < nshift; i++) {
-        W[1 + n_inf + i] = v.x[i];
-        AW[1 + n_inf + i] = v.ps[i];
+        W[kpoly + i] = v.x[i];
+        AW[kpoly + i] = v.ps[i];
     }
     // Gram matrices of (W, A W), Cholesky-QR2: pass 1 basis change X1, then
-    // the Gram matrices of (W X1, A W X1) for the final orthonormalisation
+    // the Gram matrices of (W X1, A W X1) for the final orthonormalisation.
+    // Both are symmetric (W^T A W since A is): the pairs a <= b are formed
+    // and mirrored.
     auto gram_pairs = [&](const std::vector<const T*>& Wv, const std::vector<const T*>& AWv, double* out) {
         std::vector<const T*> px, py;
-        for (int a = 0; a < nb; a++)
-            for (int b = 0; b < nb; b++) {
-                px.push_back(Wv[a]);
-                py.push_back(Wv[b]);
-            }
-        for (int a = 0; a < nb; a++)
-            for (int b = 0; b < nb; b++) {
-                px.push_back(Wv[a]);
-                py.push_back(AWv[b]);
-            }
-        const int npairs = (int)px.size();
+        for (int half = 0; half < 2; half++)
+            for (int a = 0; a < nb; a++)
+                for (int b = a; b < nb; b++) {
+                    px.push_back(Wv[a]);
+                    py.push_back(half == 0 ? Wv[b] : AWv[b]);
+                }
+        const int npairs = (int)px.size(), nu = nb * (nb + 1) / 2;
         PairDots<T> pd{};
         pd.n = n;
         pd.panels = panels;
@@ -1044,8 +1107,11 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         pd.x = upload(ctx, "rat.px", px);
         pd.y = upload(ctx, "rat.py", py);
         pd.part = ws_get_t<double>(ctx, "rat.ppart", (size_t)npairs * panels * tiles * ks);
-        VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, out, st));
-        ctx->launches += 2;
+        double* uniq = ws_get_t<double>(ctx, "rat.uniq", (size_t)npairs * Kp);
+        VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, uniq, st));
+        VNE_TRY_CUDA(ctx, launch_gram_mirror(uniq, nb, Kp, out, st));
+        VNE_TRY_CUDA(ctx, launch_gram_mirror(uniq + (size_t)nu * Kp, nb, Kp, out + (size_t)nb * nb * Kp, st));
+        ctx->launches += 4;
     };
     const size_t gsz = (size_t)2 * nb * nb * Kp;
     double* gram = ws_get_t<double>(ctx, "rat.gram", gsz);
@@ -1129,6 +1195,8 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
     psi.assign(ncols, 0.0);
     iters.assign((size_t)nshift * ncols, 0);
     resid.assign((size_t)nshift * ncols, 0.0);
+    const double lam_min = o ? o->spectrum_min : 0.0, lam_max = M->normM * M->scale;
+    ctx->last_poly_dim = 0;
     for (int b0 = 0; b0 < ncols; b0 += lim) {
         const int K = std::min(lim, ncols - b0);
         StartSource s = src;
@@ -1137,9 +1205,10 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
         if (s.kind == SRC_DENSE64) s.dense = src.dense + b0;
         std::vector<double> bp, br;
         std::vector<int> bi;
-        int rmin = 0;
+        int rmin = 0, kpoly = 0;
         rational_block<T>(ctx, *P, s, K, sc.ks, shifts, nshift, n_inf, tol, maxit, M->desing, sc.variant, drop, drop2,
-                          bp, bi, br, &rmin);
+                          bp, bi, br, &rmin, lam_min, lam_max, &kpoly);
+        ctx->last_poly_dim = std::max(ctx->last_poly_dim, kpoly);
         for (int c = 0; c < K; c++) psi[b0 + c] = bp[c];
         for (int i = 0; i < nshift; i++)
             for (int c = 0; c < K; c++) {
@@ -2221,6 +2290,12 @@ extern "C" vne_status vne_ctx_profile(vne_ctx* ctx, int32_t enable) {
 extern "C" vne_status vne_ctx_last_steps(const vne_ctx* ctx, int32_t* steps) {
     if (!ctx || !steps) return VNE_EINVAL;
     *steps = ctx->last_steps;
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_ctx_last_poly_dim(const vne_ctx* ctx, int32_t* k) {
+    if (!ctx || !k) return VNE_EINVAL;
+    *k = ctx->last_poly_dim;
     return VNE_OK;
 }
 

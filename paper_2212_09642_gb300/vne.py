@@ -110,6 +110,7 @@ def _declare(lib):
         "vne_ctx_stats": (st, [_P, _PI64, _P]),
         "vne_ctx_graph_stats": (st, [_P, _PI64, _PI64]),
         "vne_ctx_last_steps": (st, [_P, _PI32]),
+        "vne_ctx_last_poly_dim": (st, [_P, _PI32]),
         "vne_quadrature_bounds": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
         "vne_measure_gather": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
@@ -144,7 +145,7 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_matrix_coloring", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
-               "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
+               "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_ctx_last_poly_dim", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
                "vne_server_result", "vne_server_info"]
 
@@ -416,6 +417,11 @@ def vne_ctx_last_steps(ctx):
     v = ctypes.c_int32()
     _check(load().vne_ctx_last_steps(ctx, ctypes.byref(v)), ctx)
     return v.value
+
+def vne_ctx_last_poly_dim(ctx):
+    k = ctypes.c_int32()
+    _check(load().vne_ctx_last_poly_dim(ctx, ctypes.byref(k)), ctx)
+    return k.value
 
 
 def vne_measure_gather(ctx, table_bytes, row_bytes, gathers, stream_bytes=0, reps=3):

@@ -79,3 +79,61 @@ def test_rational_probing(vctx, fp64):
     assert s == V.shape[1]
     assert abs(est - ref) <= (1e-9 if fp64 else 2e-5) * ref
     assert est <= entropy.dense_entropy(A) * (1 + 1e-7)
+
+
+# ---- switching rule (Section 5.3): polynomial part chosen per block ----
+
+def _oracle_rule_k(A, X, k_max=16):
+    ks = []
+    for j in range(X.shape[1]):
+        c = krylov.desingularize(X[:, j])
+        est, _ = rational.polynomial_estimates(A, c, k_max)
+        ks.append(rational.switch_index(est))
+    return max(ks)
+
+
+@pytest.mark.parametrize("name,g", _cases())
+@pytest.mark.parametrize("fp64", [True, False])
+def test_mixed_switching_parity(vctx, name, g, fp64):
+    """n_inf_poles = -1: the device takes the polynomial dimension k from the
+    seed CG's coefficients (CG-Lanczos relation) and its Theorem 4.4
+    estimates, spans K_k(A, c) by the CG residuals and adds the pole
+    directions.  FP64: k equals the oracle's (Lanczos in FP64, same rule, the
+    block's largest k); both paths: psi equals the oracle's mixed quadrature
+    with the device's k."""
+    A, _ = density.density_matrix(g)
+    sh = rational.default_shifts(A)
+    X = rng.rademacher(6, g.n, 0, 7)
+    mat = vne.matrix_from_graph(vctx, g, fp64=fp64)
+    tol_cg = 1e-13 if fp64 else 1e-8
+    try:
+        psi, its, res = vne.vne_quadform_rational(vctx, mat, X, sh, opt=vne.options(cg_tol=tol_cg, n_inf_poles=-1))
+        k = vne.vne_ctx_last_poly_dim(vctx)
+    finally:
+        vne.vne_matrix_destroy(mat)
+    assert 1 <= k <= 16
+    if fp64:
+        assert k == _oracle_rule_k(A, X), (name, k)
+    ref = np.array([rational.mixed_quadform(A, X[:, j], sh, k_poly=k, k_max=16)[0] for j in range(X.shape[1])])
+    rel = np.abs(psi - ref) / np.abs(ref)
+    assert rel.max() <= (1e-9 if fp64 else 2e-5), (k, rel.max())
+    assert np.all(res <= tol_cg * 1.0000001)
+
+
+def test_mixed_complete_graph_one_step(vctx):
+    """K_n: the polynomial estimate is 0 after one step (invariant Krylov
+    space), so the polynomial part is K_1 = span{c} and psi is exact."""
+    g = graphs.complete(40)
+    A, _ = density.density_matrix(g)
+    X = rng.rademacher(3, 40, 0, 3)
+    mat = vne.matrix_from_graph(vctx, g, fp64=True)
+    try:
+        psi, _, _ = vne.vne_quadform_rational(vctx, mat, X, None, num_shifts=8, opt=vne.options(n_inf_poles=-1))
+        k = vne.vne_ctx_last_poly_dim(vctx)
+    finally:
+        vne.vne_matrix_destroy(mat)
+    lam = 1.0 / 39
+    c = krylov.desingularize(X)
+    want = np.sum(c * c, axis=0) * (-lam * math.log(lam))
+    assert k == 1
+    assert np.allclose(psi, want, rtol=1e-10, atol=0)
