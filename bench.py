@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--estimator", choices=["hutchpp", "hutchinson"], default="hutchpp",
                     help="hutchinson: one block of --vectors probes (small-memory case for profiling)")
     ap.add_argument("--vectors", type=int, default=112)
+    ap.add_argument("--reorder", choices=["degree", "rcm", "none"], default="degree",
+                    help="node relabelling of the headline matrix (default: descending degree)")
     ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant[,interleave] (skips the autotuner)")
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c6", "c7"], default="c2",
                     help="c2 = the headline workload; c1/c3/c4/c5/c6/c7 print measurement lines of the other configs")
@@ -257,7 +259,7 @@ def run_native(args):
     stream = torch.cuda.Stream(device=dev)
     ctx = vne.vne_ctx_create(dev)
     vne.vne_ctx_set_stream(ctx, stream)
-    flags = vne.VNE_FP32 | vne.VNE_REORDER
+    flags = vne.VNE_FP32 | {"degree": vne.VNE_REORDER, "rcm": vne.VNE_REORDER_RCM, "none": 0}[args.reorder]
     mat = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
     opt = vne.options(reorth=0)
     seed0 = 1000 * (rank + 1)
@@ -397,7 +399,7 @@ def run_native(args):
                    "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
                    "hutch_vectors": N_HUTCH, "krylov_steps": M_STEPS, "scalars": "f64",
                    "l2": "inputs larger than L2 (each 100-column block is 400 MB; L2 129 MB)",
-                   "parallelism": f"replicas x{world} (independent estimates)"},
+                   "parallelism": f"replicas x{world} (independent estimates)", "reorder": args.reorder},
         "roofline": roof, "update_kernel": update, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": sampler.summary() if sampler else None,
         "schedule": tuned_cfg,
