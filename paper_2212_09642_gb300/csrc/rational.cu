@@ -15,9 +15,10 @@
 // Lanczos engine):
 //   step kernel (shared with Lanczos)  q = (A + s_0 I) p,  d = p . q
 //   k_cg_scalars_a   a = rho / d, zeta_{k+1}, a_s     (per column, FP64)
-//   k_cg_update      r -= a q, rho' = ||r||^2,  x_s += a_s p_s
+//   k_cg_update      p_s = zeta_k r + b_s p_s, x_s += a_s p_s, r -= a q,
+//                    rho' = ||r||^2
 //   k_cg_scalars_b   b = rho'/rho, b_s, convergence, shift history
-//   k_cg_direction   p = r + b p,  p_s = zeta_{k+1} r + b_s p_s
+//   k_cg_direction   p = r + b p
 // Afterwards the basis W and A W are formed (A^j c by the step kernel,
 // A x_s by the step kernel), their Gram matrices W^T W and W^T A W are
 // accumulated per column, and a per-column FP64 kernel orthonormalises W in
@@ -127,9 +128,12 @@ __global__ void k_cg_scalars_b(CgState st) {
 }
 
 // r -= a q;  rho' = ||r||^2 (FP64 across the CTA, fixed-order last-CTA sum);
-// x_s += a_s p_s for active shifts.  Each lane owns CPL consecutive columns
-// of a row (16-byte vector accesses); a shift's x_s and p_s are touched only
-// by lanes that have an active column for it.
+// for active shifts first the shifted direction of this iteration,
+// p_s = zeta_k r + b_s p_s (r before its update: the direction kernel of the
+// previous iteration left it to this pass, which reads r anyway), then
+// x_s += a_s p_s.  Each lane owns CPL consecutive columns of a row (16-byte
+// vector accesses); a shift's x_s and p_s are touched only by lanes that
+// have an active column for it.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, CgState st) {
     constexpr int CPL = LaneVec<T>::CPL;
@@ -142,11 +146,14 @@ __global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, Cg
     const size_t pofs = (size_t)panel * v.n * KS;
     // per-column coefficients in shared memory; this lane's active columns
     // as a bit mask (bit s * CPL + q)
-    __shared__ __align__(16) T s_as[kMaxShifts][KS];
+    __shared__ __align__(16) T s_as[kMaxShifts][KS], s_z[kMaxShifts][KS], s_b[kMaxShifts][KS];
     for (int i = threadIdx.x; i < kMaxShifts * KS; i += VNE_THREADS) {
         const int sh = i / KS, cc = i % KS;
         const size_t o = (size_t)sh * st.K + panel * KS + cc;
-        s_as[sh][cc] = (sh < st.nshift && st.active[o]) ? (T)st.as[o] : (T)0;
+        const bool on = sh < st.nshift && st.active[o];
+        s_as[sh][cc] = on ? (T)st.as[o] : (T)0;
+        s_z[sh][cc] = on ? (T)st.zeta[o] : (T)0;  // zeta_k
+        s_b[sh][cc] = on ? (T)st.bs[o] : (T)0;    // b_s of the previous iteration
     }
     uint32_t amask = 0;
 #pragma unroll
@@ -182,8 +189,10 @@ __global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, Cg
                 load_lane(v.x[sh] + pofs + o, xv[sh]);
                 load_lane_stream(v.ps[sh] + pofs + o, pv[sh]);
             }
+        T r0[CPL];  // r_k, for the shifted directions
 #pragma unroll
         for (int q = 0; q < CPL; q++) {
+            r0[q] = rv[q];
             rv[q] -= a[q] * qv[q];
             accf[q] += rv[q] * rv[q];
         }
@@ -200,11 +209,17 @@ __global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, Cg
         for (int sh = 0; sh < kMaxShifts; sh++) {
             const uint32_t m = (amask >> (sh * CPL)) & ((1u << CPL) - 1u);
             if (!m) continue;
-            T cv[CPL];
+            T cv[CPL], zv[CPL], bv[CPL];
             load_lane(&s_as[sh][cofs], cv);
+            load_lane(&s_z[sh][cofs], zv);
+            load_lane(&s_b[sh][cofs], bv);
 #pragma unroll
             for (int q = 0; q < CPL; q++)
-                if (m & (1u << q)) xv[sh][q] += cv[q] * pv[sh][q];
+                if (m & (1u << q)) {
+                    pv[sh][q] = zv[q] * r0[q] + bv[q] * pv[sh][q];
+                    xv[sh][q] += cv[q] * pv[sh][q];
+                }
+            store_lane(v.ps[sh] + pofs + o, pv[sh]);
             store_lane(v.x[sh] + pofs + o, xv[sh]);
         }
     }
@@ -235,8 +250,7 @@ __global__ void __launch_bounds__(VNE_THREADS, 2) k_cg_update(CgVectors<T> v, Cg
     }
 }
 
-// p = r + b p;  p_s = zeta_{k+1} r + b_s p_s for shifts active before this
-// iteration (vector lanes as in k_cg_update)
+// p = r + b p (the shifted directions are formed by the next k_cg_update)
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, CgState st) {
     constexpr int CPL = LaneVec<T>::CPL;
@@ -247,21 +261,6 @@ __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, Cg
     const int sub = threadIdx.x % LPR, rs = threadIdx.x / LPR;
     const int cofs = sub * CPL;
     const size_t pofs = (size_t)panel * v.n * KS;
-    __shared__ __align__(16) T s_z[kMaxShifts][KS], s_b[kMaxShifts][KS];
-    for (int i = threadIdx.x; i < kMaxShifts * KS; i += VNE_THREADS) {
-        const int sh = i / KS, cc = i % KS;
-        const size_t o = (size_t)sh * st.K + panel * KS + cc;
-        const bool on = sh < st.nshift && st.active[o];
-        s_z[sh][cc] = on ? (T)st.zeta[o] : (T)0;
-        s_b[sh][cc] = on ? (T)st.bs[o] : (T)0;
-    }
-    uint32_t amask = 0;
-#pragma unroll
-    for (int sh = 0; sh < kMaxShifts; sh++)
-#pragma unroll
-        for (int q = 0; q < CPL; q++)
-            if (sh < st.nshift && st.active[(size_t)sh * st.K + panel * KS + cofs + q]) amask |= 1u << (sh * CPL + q);
-    __syncthreads();
     T b[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; q++) b[q] = (T)st.b[panel * KS + cofs + q];
@@ -270,24 +269,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, Cg
     for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
         const size_t o = (size_t)r * KS + cofs;
         T rv[CPL], pv[CPL];
-        load_lane(R + o, rv);
+        load_lane_stream(R + o, rv);
         load_lane(Pp + o, pv);
-        T sv[kMaxShifts][CPL];
-#pragma unroll
-        for (int sh = 0; sh < kMaxShifts; sh++)
-            if ((amask >> (sh * CPL)) & ((1u << CPL) - 1u)) load_lane(v.ps[sh] + pofs + o, sv[sh]);
-#pragma unroll
-        for (int sh = 0; sh < kMaxShifts; sh++) {
-            const uint32_t m = (amask >> (sh * CPL)) & ((1u << CPL) - 1u);
-            if (!m) continue;
-            T zv[CPL], bv[CPL];
-            load_lane(&s_z[sh][cofs], zv);
-            load_lane(&s_b[sh][cofs], bv);
-#pragma unroll
-            for (int q = 0; q < CPL; q++)
-                if (m & (1u << q)) sv[sh][q] = zv[q] * rv[q] + bv[q] * sv[sh][q];
-            store_lane(v.ps[sh] + pofs + o, sv[sh]);
-        }
 #pragma unroll
         for (int q = 0; q < CPL; q++) pv[q] = rv[q] + b[q] * pv[q];
         store_lane(Pp + o, pv);

@@ -1005,8 +1005,8 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
             VNE_TRY_CUDA(ctx, cudaEventRecord(e3, st));
             // algorithmic bytes of the seed part: update reads r, q, writes r;
             // direction reads r, p, writes p.  The per-shift part (update:
-            // x_s read + write, p_s read; direction: p_s read + write) is added
-            // after the loop from the iterations each shift stayed active.
+            // p_s and x_s read and written) is added after the loop from the
+            // iterations each shift stayed active.
             const double vec = (double)n * K * sizeof(T);
             ctx->pending.push_back({2, e0, e1, vec * 3.0});
             ctx->pending.push_back({3, e2, e3, vec * 3.0});
@@ -1156,8 +1156,7 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         for (int i = 0; i < nshift; i++)
             for (int c = 0; c < K; c++) shift_iters += hit[(size_t)i * Kp + c];
         const double per = (double)n * sizeof(T);
-        ctx->pending.push_back({2, nullptr, nullptr, shift_iters * per * 3.0});
-        ctx->pending.push_back({3, nullptr, nullptr, shift_iters * per * 2.0});
+        ctx->pending.push_back({2, nullptr, nullptr, shift_iters * per * 4.0});
         ctx_flush_profile(ctx);
     }
     iters.assign((size_t)nshift * K, 0);
