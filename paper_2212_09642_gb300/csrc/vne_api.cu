@@ -325,8 +325,12 @@ void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_
     sg.cta_count = (int32_t)((P.items.size() - first_item) / VNE_WARPS);
     for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
     sg.tile_begin = (int32_t)P.tiles.size();
-    for (int32_t r = row_begin; r < row_begin + rows; r += kTileRows)
-        P.tiles.push_back(RowTile{r, std::min(row_begin + rows, r + kTileRows), seg, 0});
+    // row tiles of the streaming kernels: 4096 rows, fewer for small
+    // segments (at least 16 tiles down to 256 rows) so that their update and
+    // reorthogonalisation passes still spread over several SMs
+    const int32_t trows = std::max<int32_t>(256, std::min<int32_t>(kTileRows, ((rows / 16) + 31) & ~31));
+    for (int32_t r = row_begin; r < row_begin + rows; r += trows)
+        P.tiles.push_back(RowTile{r, std::min(row_begin + rows, r + trows), seg, 0});
     sg.tile_count = (int32_t)P.tiles.size() - sg.tile_begin;
 }
 
