@@ -558,7 +558,8 @@ def run_other(args):
         line.update(metric="entropy estimates/sec (512 uneven graphs batched, Hutchinson 64 x 40)",
                     value=512 * args.steps / (ms / 1e3), ms_per_step=ms / args.steps, dtype="f32",
                     config={"workload": "C4: 512 graphs, n log-uniform [1e3, 2e5], ER deg 8 / BA m=3 / WS k=6 b=0.1, "
-                                        "64 Rademacher x 40 Lanczos steps each, one packed launch sequence",
+                                        "64 Rademacher x 40 Lanczos steps each, one packed launch sequence (the packed layout of the "
+                                        "batch is built by the first call and kept in the context)",
                             "sum_n": int(sum(gg.n for gg in gs)), "sum_nnz": int(sum(gg.nnz for gg in gs)),
                             "l2": "inputs larger than L2"},
                     roofline=_roof(kst, "step", ms, "k_step (packed segments)"),

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <tuple>
 #include <map>
 #include <memory>
@@ -52,6 +53,8 @@ struct KernelStat {
     double ms = 0.0;
     double bytes = 0.0;  // algorithmic bytes of the timed launches
 };
+
+struct Problem;
 
 struct vne_ctx {
     int device = 0;
@@ -94,12 +97,17 @@ struct vne_ctx {
     int64_t graphs_captured = 0, graphs_replayed = 0;
     int last_steps = 0;  // Lanczos steps of the last quadrature call (largest over its blocks)
     int last_poly_dim = 0;  // polynomial dimension chosen by the switching rule (last rational call)
+    // packed layout of the last batch of matrices (vne_batch_hutchinson),
+    // kept for repeated estimates over the same batch; key = the matrices'
+    // creation ids and the plan parameters
+    Problem* batch_prob = nullptr;
+    std::vector<uint64_t> batch_key;
+    int batch_ks = 0;
 };
-
-struct Problem;
 
 struct vne_matrix {
     vne_ctx* ctx = nullptr;
+    uint64_t uid = 0;               // creation id, unique within the process
     int64_t n = 0, nnz = 0;
     bool fp64 = false, pattern = false, desing = false;
     double trace = 0.0, scale = 1.0, normM = 0.0;
@@ -1296,6 +1304,7 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx->batch_prob;
     delete ctx;
     return VNE_OK;
 }
@@ -1323,6 +1332,8 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
                 "VNE_CHECK_SYMMETRY supports pattern matrices only");
     std::unique_ptr<vne_matrix> M(new vne_matrix());
     M->ctx = ctx;
+    static std::atomic<uint64_t> next_uid{1};
+    M->uid = next_uid.fetch_add(1);
     M->n = n;
     M->fp64 = fp64;
     M->pattern = (vals == nullptr);
@@ -2198,57 +2209,74 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     }
     VNE_REQUIRE(ctx, !any_valued, VNE_EUNSUPPORTED, "batched mode packs pattern (graph) matrices");
     VNE_REQUIRE(ctx, ntot < INT32_MAX && nnztot < INT32_MAX, VNE_EINVAL, "packed batch too large");
-    // packed CSR
-    std::vector<int64_t> rp(ntot + 1, 0);
-    std::vector<int32_t> ci(nnztot);
-    std::vector<int32_t> nid;
-    if (any_perm) nid.resize(ntot);
-    std::unique_ptr<Problem> P(new Problem());
-    P->fp64 = fp64;
-    P->valued = false;
-    P->n_total = (int32_t)ntot;
-    P->nnz_total = nnztot;
-    P->nseg = count;
     double taurel = o.breakdown_tol > 0 ? o.breakdown_tol : default_tau(fp64);
-    int64_t r0 = 0, e0 = 0;
-    for (int i = 0; i < count; i++) {
-        vne_matrix* M = mats[i];
-        const std::vector<int32_t>& hc = host_cols(M);
-        for (int64_t r = 0; r < M->n; r++) {
-            rp[r0 + r + 1] = e0 + M->h_rowptr[r + 1];
-            if (any_perm) nid[r0 + r] = M->perm.empty() ? (int32_t)r : M->perm[r];
-        }
-        for (int64_t e = 0; e < M->nnz; e++) ci[e0 + e] = hc[e] + (int32_t)r0;
-        SegInfo s{};
-        s.row_begin = (int32_t)r0;
-        s.rows = (int32_t)M->n;
-        s.scale = M->scale;
-        s.tau = taurel * M->normM;
-        P->segs.push_back(s);
-        r0 += M->n;
-        e0 += M->nnz;
-    }
     const int target = default_item_nnz(&o);
-    for (int i = 0; i < count; i++) plan_segment(rp.data(), P->segs[i].row_begin, P->segs[i].rows, i, target, *P);
-    std::vector<int32_t> rp32(ntot + 1);
-    for (int64_t i = 0; i <= ntot; i++) rp32[i] = (int32_t)rp[i];
-    int32_t* drp = dev_copy(ctx, rp32);
-    int32_t* dci = dev_copy(ctx, ci);
-    P->owned.push_back(drp);
-    P->owned.push_back(dci);
-    P->rowptr = drp;
-    P->col = dci;
-    if (any_perm) {
-        int32_t* dn = dev_copy(ctx, nid);
-        P->owned.push_back(dn);
-        P->node_id = dn;
+    std::vector<uint64_t> key;
+    key.push_back((uint64_t)target);
+    uint64_t tbits = 0;
+    memcpy(&tbits, &taurel, sizeof(tbits));
+    key.push_back(tbits);
+    key.push_back((uint64_t)fp64);
+    key.push_back((uint64_t)o.panel);
+    for (int i = 0; i < count; i++) key.push_back(mats[i]->uid);
+    if (!ctx->batch_prob || ctx->batch_key != key) {
+        delete ctx->batch_prob;
+        ctx->batch_prob = nullptr;
+        ctx->batch_key.clear();
+        // packed CSR
+        std::vector<int64_t> rp(ntot + 1, 0);
+        std::vector<int32_t> ci(nnztot);
+        std::vector<int32_t> nid;
+        if (any_perm) nid.resize(ntot);
+        std::unique_ptr<Problem> P(new Problem());
+        P->fp64 = fp64;
+        P->valued = false;
+        P->n_total = (int32_t)ntot;
+        P->nnz_total = nnztot;
+        P->nseg = count;
+        int64_t r0 = 0, e0 = 0;
+        for (int i = 0; i < count; i++) {
+            vne_matrix* M = mats[i];
+            const std::vector<int32_t>& hc = host_cols(M);
+            for (int64_t r = 0; r < M->n; r++) {
+                rp[r0 + r + 1] = e0 + M->h_rowptr[r + 1];
+                if (any_perm) nid[r0 + r] = M->perm.empty() ? (int32_t)r : M->perm[r];
+            }
+            for (int64_t e = 0; e < M->nnz; e++) ci[e0 + e] = hc[e] + (int32_t)r0;
+            SegInfo s{};
+            s.row_begin = (int32_t)r0;
+            s.rows = (int32_t)M->n;
+            s.scale = M->scale;
+            s.tau = taurel * M->normM;
+            P->segs.push_back(s);
+            r0 += M->n;
+            e0 += M->nnz;
+        }
+        for (int i = 0; i < count; i++) plan_segment(rp.data(), P->segs[i].row_begin, P->segs[i].rows, i, target, *P);
+        std::vector<int32_t> rp32(ntot + 1);
+        for (int64_t i = 0; i <= ntot; i++) rp32[i] = (int32_t)rp[i];
+        int32_t* drp = dev_copy(ctx, rp32);
+        int32_t* dci = dev_copy(ctx, ci);
+        P->owned.push_back(drp);
+        P->owned.push_back(dci);
+        P->rowptr = drp;
+        P->col = dci;
+        if (any_perm) {
+            int32_t* dn = dev_copy(ctx, nid);
+            P->owned.push_back(dn);
+            P->node_id = dn;
+        }
+        problem_upload(ctx, *P);
+        // the packed launch walks the segments in order, so the panel that has to
+        // stay L2-resident is one segment's slice: size it by the largest graph
+        int64_t nmax = 0;
+        for (int i = 0; i < count; i++) nmax = std::max<int64_t>(nmax, mats[i]->n);
+        ctx->batch_ks = choose_panel(fp64, &o, nmax);
+        ctx->batch_prob = P.release();
+        ctx->batch_key = key;
     }
-    problem_upload(ctx, *P);
-    // the packed launch walks the segments in order, so the panel that has to
-    // stay L2-resident is one segment's slice: size it by the largest graph
-    int64_t nmax = 0;
-    for (int i = 0; i < count; i++) nmax = std::max<int64_t>(nmax, mats[i]->n);
-    int ks = choose_panel(fp64, &o, nmax);
+    Problem* P = ctx->batch_prob;
+    const int ks = ctx->batch_ks;
     const int variant = fp64 ? 0 : (o.step_variant >= 0 ? o.step_variant : 4);
     StartSource s{};
     s.kind = SRC_RADEMACHER;
