@@ -267,49 +267,67 @@ __global__ void __launch_bounds__(kCWarps * 32) k_color_round(ColorRound p) {
     int32_t* table = p.d >= 3 ? dyn + warp * (kHashSlots + kBallCap) : nullptr;
     int32_t* ball = p.d >= 3 ? table + kHashSlots : nullptr;
     const int nw = gridDim.x * kCWarps;
-    int it = 0;
-    for (int i = blockIdx.x * kCWarps + warp; i < total; i += nw) {
-        // an overflow (d >= 3 only) ends the round early; the flag is read
-        // every 32 nodes, not per node: every warp reading one word per node
-        // queues on a single L2 slice
-        if (p.d >= 3 && (++it & 31) == 0 && __shfl_sync(0xffffffffu, lane == 0 ? __ldcg(p.overflow) : 0, 0) != 0)
-            break;
-        const int32_t v = in[i];
-        const int32_t b = p.blk[v];
-        if (b >= 0 && ld_color(p.color + b) < 0) {
-            if (lane == 0) out[atomicAdd(cout, 1)] = v;
-            continue;
+    // 32 list entries per warp step: each lane re-checks its node's blocker
+    // (the common case, one load each; survivors appended with one atomic per
+    // warp), then the warp searches the balls of the nodes whose blocker is
+    // coloured, one after another
+    const unsigned lt = (1u << lane) - 1u;
+    int wmax = 0;  // colours used by this warp (max + 1), one atomicMax at the end
+    for (int i0 = (blockIdx.x * kCWarps + warp) * 32; i0 < total; i0 += nw * 32) {
+        // an overflow (d >= 3 only) ends the round early
+        if (p.d >= 3 && __shfl_sync(0xffffffffu, lane == 0 ? __ldcg(p.overflow) : 0, 0) != 0) break;
+        const int i = i0 + lane;
+        int32_t v = -1;
+        bool need = false;
+        if (i < total) {
+            v = in[i];
+            const int32_t b = p.blk[v];
+            need = !(b >= 0 && ld_color(p.color + b) < 0);
         }
-        int base = 0, res;
-        int32_t blocker = -1;
-        const int tries = p.tries[v];
-        for (;;) {
-            res = search_ball(v, p.d, base, p.rowptr, p.col, p.key, p.color, ws, table, ball, &nball_all[warp],
-                              &nins_all[warp], &self_all[warp], p.inv, tries < 2, &blocker);
-            // every colour of the window is taken: the next window (the
-            // ball has at most n nodes, so this ends)
-            if (res != -3 || base > (1 << 30)) break;
-            base += kWin;
+        const unsigned stay = __ballot_sync(0xffffffffu, i < total && !need);
+        if (stay) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(cout, __popc(stay));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((stay >> lane) & 1u) out[base + __popc(stay & lt)] = v;
         }
-        if (lane == 0) {
-            if (res >= 0) {
-                st_color(p.color + v, res);
-                atomicMax(p.ncolors, res + 1);
-            } else if (res == -1) {
-                p.blk[v] = blocker;
-                p.tries[v] = tries + 1;
-                out[atomicAdd(cout, 1)] = v;
-            } else if (p.biglist) {
-                // the ball does not fit the warp's table: the CTA-wide search
-                // of k_color_big takes the node in this round
-                p.biglist[atomicAdd(p.bigcnt + (r & 1), 1)] = v;
-            } else {
-                atomicExch(p.overflow, 1);
-                out[atomicAdd(cout, 1)] = v;
+        unsigned todo = __ballot_sync(0xffffffffu, need);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int32_t u = __shfl_sync(0xffffffffu, v, src);
+            int base = 0, res;
+            int32_t blocker = -1;
+            const int tries = p.tries[u];
+            for (;;) {
+                res = search_ball(u, p.d, base, p.rowptr, p.col, p.key, p.color, ws, table, ball, &nball_all[warp],
+                                  &nins_all[warp], &self_all[warp], p.inv, tries < 2, &blocker);
+                // every colour of the window is taken: the next window (the
+                // ball has at most n nodes, so this ends)
+                if (res != -3 || base > (1 << 30)) break;
+                base += kWin;
             }
+            if (lane == 0) {
+                if (res >= 0) {
+                    st_color(p.color + u, res);
+                    wmax = max(wmax, res + 1);
+                } else if (res == -1) {
+                    p.blk[u] = blocker;
+                    p.tries[u] = tries + 1;
+                    out[atomicAdd(cout, 1)] = u;
+                } else if (p.biglist) {
+                    // the ball does not fit the warp's table: the CTA-wide
+                    // search of k_color_big takes the node in this round
+                    p.biglist[atomicAdd(p.bigcnt + (r & 1), 1)] = u;
+                } else {
+                    atomicExch(p.overflow, 1);
+                    out[atomicAdd(cout, 1)] = u;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
+    if (lane == 0 && wmax > 0) atomicMax(p.ncolors, wmax);
 }
 
 __global__ void k_color_scatter(const int32_t* __restrict__ color, const int32_t* __restrict__ node_id, int64_t n,
