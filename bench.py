@@ -301,11 +301,13 @@ def run_native(args):
     barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvtx_push("timed_steps")
     e0.record(stream)
     for k in range(args.steps):
         ests.append(one(seed0 + 100 + k)[0])
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    nvtx_pop()
     barrier()
     if sampler:
         sampler.__exit__()
@@ -413,7 +415,25 @@ def run_native(args):
 # ---------------------------------------------------------------------------
 # measurement lines of the other configurations (not the headline)
 
-def _timed(ctx, stream, fn, steps, warmup):
+def nvtx_push(name):
+    """Mark a timed region (an ncu run can restrict its capture to it with
+    --nvtx --nvtx-include name/)."""
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+def _timed(ctx, stream, fn, steps, warmup, label="timed_steps"):
     import torch
     from paper_2212_09642_gb300 import vne
     for w in range(warmup):
@@ -423,10 +443,12 @@ def _timed(ctx, stream, fn, steps, warmup):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(0)
     sampler.__enter__()
+    nvtx_push(label)
     e0.record(stream)
     outs = [fn(100 + k) for k in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
+    nvtx_pop()
     sampler.__exit__()
     ms = e0.elapsed_time(e1)
     launches, kst = vne.vne_ctx_stats(ctx)
@@ -520,7 +542,7 @@ def run_other(args):
         # rule of Section 5.3 (n_inf_poles = -1) instead of two poles at infinity
         mopt = vne.options(cg_tol=1e-8, n_inf_poles=-1)
         outs_m, ms_m, _, _, _ = _timed(ctx, stream, lambda sd: vne.vne_entropy_probing(
-            ctx, mat, None, 2, 0, opt=mopt, num_shifts=8), max(1, args.steps // 2), 1)
+            ctx, mat, None, 2, 0, opt=mopt, num_shifts=8), max(1, args.steps // 2), 1, label="timed_sub")
         line["switching_rule"] = {"value": max(1, args.steps // 2) / (ms_m / 1e3), "unit": UNIT,
                                   "polynomial_dim": vne.vne_ctx_last_poly_dim(ctx), "estimate": outs_m[0][0],
                                   "diff_vs_two_poles_at_infinity": outs_m[0][0] - outs[0][0]}

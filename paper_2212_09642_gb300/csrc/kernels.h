@@ -137,21 +137,25 @@ struct CgVectors {
     uint32_t* counter;
 };
 
+// Both Gram matrices of a basis W and its image A W in one pass over the
+// vectors: for every column, W_a . W_b and W_a . (A W)_b for a <= b, pairs
+// numbered row by row (W.W first, then W.AW), written to out[pair][col].
 template <typename T>
-struct PairDots {
-    int32_t n, panels, ks, tiles_per_panel;
-    const RowTile* tiles;
-    const T* const* x;  // device array of block pointers, one per pair
-    const T* const* y;
-    double* part;       // [pairs][panels][tiles][ks]
-    int32_t tile_in_y;  // set by the launcher: grid (pairs, tiles) instead of (tiles, pairs)
+struct MultiGram {
+    int32_t n, panels, ks, nb;
+    const T* w[24];
+    const T* aw[24];
+    int32_t chunks;   // row ranges per panel (grid x)
+    int32_t groups;   // output groups per chunk (grid y)
+    double* part;     // [panels][groups][chunks][outputs of a group]
 };
+template <typename T> cudaError_t launch_multi_gram(MultiGram<T> g, double* out, cudaStream_t);
+
 
 cudaError_t launch_cg_scalars_a(const CgState&, cudaStream_t);
 cudaError_t launch_cg_scalars_b(const CgState&, cudaStream_t);
 template <typename T> cudaError_t launch_cg_update(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_cg_direction(const CgVectors<T>&, const CgState&, int ks, int panels, cudaStream_t);
-template <typename T> cudaError_t launch_pair_dots(const PairDots<T>&, int npairs, double* out, cudaStream_t);
 template <typename T>
 struct BlockTransform {
     int32_t n, K, nb, tiles_per_panel;

@@ -21,7 +21,7 @@
 //   k_cg_direction   p = r + b p
 // Afterwards the basis W and A W are formed (A^j c by the step kernel,
 // A x_s by the step kernel), their Gram matrices W^T W and W^T A W are
-// accumulated per column, and a per-column FP64 kernel orthonormalises W in
+// accumulated per column in one pass over the vectors (k_multi_gram), and a per-column FP64 kernel orthonormalises W in
 // pole order (Cholesky of the column-scaled Gram, dropping dependent
 // columns; the first basis vector is c / ||c|| as in rational Arnoldi),
 // applies that basis change to the vectors W and A W and repeats the
@@ -277,54 +277,6 @@ __global__ void __launch_bounds__(VNE_THREADS) k_cg_direction(CgVectors<T> v, Cg
     }
 }
 
-// Per-column inner products between pairs of panel-major blocks:
-// out[pair][col] = sum_i X_pair[i][col] Y_pair[i][col] (FP64 across rows).
-template <typename T, int KS>
-__global__ void __launch_bounds__(VNE_THREADS) k_pair_dots(PairDots<T> pd) {
-    constexpr int RPI = VNE_THREADS / KS;
-    // consecutive CTAs take different pairs of the same row tile, so the
-    // tile's vectors are read from HBM once and then hit in L2 (tiles along y
-    // while they fit its 65535 limit)
-    const int pair = pd.tile_in_y ? blockIdx.x : blockIdx.y;
-    const int pt = pd.tile_in_y ? blockIdx.y : blockIdx.x;
-    const int panel = pt / pd.tiles_per_panel, tile = pt % pd.tiles_per_panel;
-    const RowTile t = pd.tiles[tile];
-    const int c = threadIdx.x % KS, rs = threadIdx.x / KS;
-    const size_t pofs = (size_t)panel * pd.n * KS;
-    const T* X = pd.x[pair] + pofs;
-    const T* Y = pd.y[pair] + pofs;
-    double acc = 0.0;
-    T accf = (T)0;
-    int cnt = 0;
-    for (int r = t.row_begin + rs; r < t.row_end; r += RPI) {
-        accf += X[(size_t)r * KS + c] * Y[(size_t)r * KS + c];
-        if (++cnt == 16) {
-            acc += (double)accf;
-            accf = (T)0;
-            cnt = 0;
-        }
-    }
-    acc += (double)accf;
-    __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < KS) {
-        double sum = 0.0;
-        for (int q = 0; q < RPI; q++) sum += red[q * KS + threadIdx.x];
-        pd.part[(((size_t)pair * pd.panels + panel) * pd.tiles_per_panel + tile) * KS + threadIdx.x] = sum;
-    }
-}
-
-__global__ void k_pair_reduce(const double* part, int npairs, int panels, int tiles, int ks, double* out) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int K = panels * ks;
-    if (idx >= npairs * K) return;
-    const int pair = idx / K, col = idx % K, panel = col / ks, c = col % ks;
-    double s = 0.0;
-    for (int t = 0; t < tiles; t++) s += part[(((size_t)pair * panels + panel) * tiles + t) * ks + c];
-    out[(size_t)pair * K + col] = s;
-}
-
 // Per-column Cholesky of the column-scaled Gram matrix in pole order.  A
 // column whose pivot (squared relative remainder) is <= drop is dependent on
 // the kept ones and is dropped.  Returns the kept count; R (upper, kept
@@ -491,6 +443,89 @@ __global__ void __launch_bounds__(VNE_THREADS) k_block_transform(BlockTransform<
     (void)col;
 }
 
+// ---------------------------------------------------------------------------
+// Gram matrices W^T W and W^T (A W) per column in one pass over the vectors
+// (a kernel per pair of vectors would read every vector about nb times).  A
+// CTA takes a range of rows of one panel in tiles of kGramRows rows: all 2 nb
+// vectors' tile rows go to shared memory, and each thread accumulates a
+// fixed set of (pair, column) outputs; the outputs are split into groups of
+// kGramOut so that a thread holds at most kGramPer of them.  Sums per tile in
+// the data precision (16 rows, as the pairwise kernel), FP64 across tiles,
+// FP64 fixed-order sum over the row ranges.
+constexpr int kGramRows = 16;
+constexpr int kGramPer = 16;
+constexpr int kGramOut = VNE_THREADS * kGramPer;
+
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_multi_gram(MultiGram<T> g) {
+    extern __shared__ __align__(16) unsigned char mg_smem[];
+    T* sv = reinterpret_cast<T*>(mg_smem);  // [2 nb][kGramRows][KS]
+    __shared__ unsigned char s_x[kGramOut / KS + 1], s_y[kGramOut / KS + 1];
+    const int chunk = blockIdx.x, grp = blockIdx.y, panel = blockIdx.z;
+    const int nb = g.nb, nu = nb * (nb + 1) / 2, npair = 2 * nu;
+    const int o_begin = grp * kGramOut, o_end = min(npair * KS, o_begin + kGramOut);
+    // pair -> (x vector, y vector) for this group's pairs; y >= nb is AW
+    const int p_begin = o_begin / KS, p_end = (o_end + KS - 1) / KS;
+    for (int pr = p_begin + threadIdx.x; pr < p_end; pr += VNE_THREADS) {
+        const int half = pr >= nu, q = half ? pr - nu : pr;
+        int a = 0, rem = q;
+        while (rem >= nb - a) {
+            rem -= nb - a;
+            a++;
+        }
+        s_x[pr - p_begin] = (unsigned char)a;
+        s_y[pr - p_begin] = (unsigned char)(a + rem + (half ? nb : 0));
+    }
+    const int rows_per = (g.n + g.chunks - 1) / g.chunks;
+    const int r_begin = chunk * rows_per, r_end = min(g.n, r_begin + rows_per);
+    const size_t pofs = (size_t)panel * g.n * KS;
+    double acc[kGramPer];
+#pragma unroll
+    for (int j = 0; j < kGramPer; j++) acc[j] = 0.0;
+    const int nvec = 2 * nb;
+    for (int r0 = r_begin; r0 < r_end; r0 += kGramRows) {
+        const int rows = min(kGramRows, r_end - r0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nvec * kGramRows * KS; idx += VNE_THREADS) {
+            const int v = idx / (kGramRows * KS), e = idx % (kGramRows * KS), rr = e / KS;
+            const T* src = v < nb ? g.w[v] : g.aw[v - nb];
+            sv[idx] = rr < rows ? src[pofs + (size_t)(r0 + rr) * KS + (e % KS)] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kGramPer; j++) {
+            const int o = o_begin + threadIdx.x + j * VNE_THREADS;
+            if (o >= o_end) break;
+            const int pr = o / KS, c = o % KS;
+            const T* X = sv + (size_t)s_x[pr - p_begin] * kGramRows * KS + c;
+            const T* Y = sv + (size_t)s_y[pr - p_begin] * kGramRows * KS + c;
+            T t = (T)0;
+#pragma unroll
+            for (int rr = 0; rr < kGramRows; rr++) t += X[rr * KS] * Y[rr * KS];
+            acc[j] += (double)t;
+        }
+    }
+    const size_t gbase = (((size_t)panel * g.groups + grp) * g.chunks + chunk) * kGramOut;
+#pragma unroll
+    for (int j = 0; j < kGramPer; j++) {
+        const int o = o_begin + threadIdx.x + j * VNE_THREADS;
+        if (o < o_end) g.part[gbase + (o - o_begin)] = acc[j];
+    }
+}
+
+// out[pair][panel * KS + c] = fixed-order sum over the row ranges
+__global__ void k_multi_gram_reduce(const double* part, int panels, int groups, int chunks, int ks, int npair,
+                                    double* out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = panels * ks;
+    if (idx >= npair * K) return;
+    const int pr = idx / K, col = idx % K, panel = col / ks, c = col % ks;
+    const int o = pr * ks + c, grp = o / kGramOut, oo = o % kGramOut;
+    double s = 0.0;
+    for (int ch = 0; ch < chunks; ch++) s += part[(((size_t)panel * groups + grp) * chunks + ch) * kGramOut + oo];
+    out[(size_t)pr * K + col] = s;
+}
+
 // Lanczos tridiagonal of A from the seed CG's scalars (the CG-Lanczos
 // relation): with step lengths a_i and direction coefficients b_i of CG on
 // A + s0 I, T_{i+1,i+1} = 1/a_i + b_{i-1}/a_{i-1} - s0 (no second term at
@@ -553,30 +588,6 @@ cudaError_t launch_cg_direction(const CgVectors<T>& v, const CgState& st, int ks
     VNE_KS_SWITCH(T, ks, (k_cg_direction<T, KS><<<panels * v.tiles_per_panel, VNE_THREADS, 0, s>>>(v, st)));
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_pair_dots(const PairDots<T>& pd, int npairs, double* out, cudaStream_t s) {
-    if (npairs <= 0) return cudaSuccess;
-    PairDots<T> q = pd;
-    const int ntile = pd.panels * pd.tiles_per_panel;
-    q.tile_in_y = ntile <= 65535 ? 1 : 0;
-    const dim3 grid = q.tile_in_y ? dim3(npairs, ntile) : dim3(ntile, npairs);
-    VNE_KS_SWITCH(T, pd.ks, (k_pair_dots<T, KS><<<grid, VNE_THREADS, 0, s>>>(q)));
-    const int K = pd.panels * pd.ks;
-    k_pair_reduce<<<(npairs * K + 255) / 256, 256, 0, s>>>(pd.part, npairs, pd.panels, pd.tiles_per_panel, pd.ks, out);
-    return cudaGetLastError();
-}
-cudaError_t launch_cg_tridiag(const double* ah, const double* bh, int K, int k, double s0, double tau, double* diag,
-                              double* off, cudaStream_t s) {
-    if (k <= 0) return cudaSuccess;
-    k_cg_tridiag<<<(K + 63) / 64, 64, 0, s>>>(ah, bh, K, k, s0, tau, diag, off);
-    return cudaGetLastError();
-}
-cudaError_t launch_gram_mirror(const double* uniq, int nb, int K, double* full, cudaStream_t s) {
-    const size_t total = (size_t)nb * nb * K;
-    if (total == 0) return cudaSuccess;
-    k_gram_mirror<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(uniq, nb, K, full);
-    return cudaGetLastError();
-}
 cudaError_t launch_rational_pass1(const double* M, int nb, int K, double drop, double* X, cudaStream_t s) {
     if (nb > kMaxBasis) return cudaErrorInvalidValue;
     k_rational_pass1<<<(K + 31) / 32, 32, 0, s>>>(M, nb, K, drop, X);
@@ -614,8 +625,6 @@ template cudaError_t launch_cg_update<float>(const CgVectors<float>&, const CgSt
 template cudaError_t launch_cg_update<double>(const CgVectors<double>&, const CgState&, int, int, cudaStream_t);
 template cudaError_t launch_cg_direction<float>(const CgVectors<float>&, const CgState&, int, int, cudaStream_t);
 template cudaError_t launch_cg_direction<double>(const CgVectors<double>&, const CgState&, int, int, cudaStream_t);
-template cudaError_t launch_pair_dots<float>(const PairDots<float>&, int, double*, cudaStream_t);
-template cudaError_t launch_pair_dots<double>(const PairDots<double>&, int, double*, cudaStream_t);
 template cudaError_t launch_block_transform<float>(const BlockTransform<float>&, int, int, cudaStream_t);
 template cudaError_t launch_block_transform<double>(const BlockTransform<double>&, int, int, cudaStream_t);
 

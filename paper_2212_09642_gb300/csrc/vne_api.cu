@@ -1102,25 +1102,24 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
     // Both are symmetric (W^T A W since A is): the pairs a <= b are formed
     // and mirrored.
     auto gram_pairs = [&](const std::vector<const T*>& Wv, const std::vector<const T*>& AWv, double* out) {
-        std::vector<const T*> px, py;
-        for (int half = 0; half < 2; half++)
-            for (int a = 0; a < nb; a++)
-                for (int b = a; b < nb; b++) {
-                    px.push_back(Wv[a]);
-                    py.push_back(half == 0 ? Wv[b] : AWv[b]);
-                }
-        const int npairs = (int)px.size(), nu = nb * (nb + 1) / 2;
-        PairDots<T> pd{};
-        pd.n = n;
-        pd.panels = panels;
-        pd.ks = ks;
-        pd.tiles_per_panel = tiles;
-        pd.tiles = P.d_tiles;
-        pd.x = upload(ctx, "rat.px", px);
-        pd.y = upload(ctx, "rat.py", py);
-        pd.part = ws_get_t<double>(ctx, "rat.ppart", (size_t)npairs * panels * tiles * ks);
+        // one pass over the 2 nb vectors (k_multi_gram); the pairs a <= b of
+        // W.W then W.AW, mirrored into the full [nb][nb] layouts
+        const int nu = nb * (nb + 1) / 2, npairs = 2 * nu;
+        MultiGram<T> mg{};
+        mg.n = n;
+        mg.panels = panels;
+        mg.ks = ks;
+        mg.nb = nb;
+        for (int a = 0; a < nb; a++) {
+            mg.w[a] = Wv[a];
+            mg.aw[a] = AWv[a];
+        }
+        const int groups = (npairs * ks + VNE_THREADS * 16 - 1) / (VNE_THREADS * 16);
+        const int want = std::max(1, 4 * std::max(ctx->sm_count, 1) / std::max(1, panels * groups));
+        mg.chunks = std::max(1, std::min(want, (n + 15) / 16));
+        mg.part = ws_get_t<double>(ctx, "rat.mgpart", (size_t)panels * groups * mg.chunks * VNE_THREADS * 16);
         double* uniq = ws_get_t<double>(ctx, "rat.uniq", (size_t)npairs * Kp);
-        VNE_TRY_CUDA(ctx, launch_pair_dots<T>(pd, npairs, uniq, st));
+        VNE_TRY_CUDA(ctx, launch_multi_gram<T>(mg, uniq, st));
         VNE_TRY_CUDA(ctx, launch_gram_mirror(uniq, nb, Kp, out, st));
         VNE_TRY_CUDA(ctx, launch_gram_mirror(uniq + (size_t)nu * Kp, nb, Kp, out + (size_t)nb * nb * Kp, st));
         ctx->launches += 4;
