@@ -588,6 +588,47 @@ cudaError_t launch_cg_direction(const CgVectors<T>& v, const CgState& st, int ks
     VNE_KS_SWITCH(T, ks, (k_cg_direction<T, KS><<<panels * v.tiles_per_panel, VNE_THREADS, 0, s>>>(v, st)));
     return cudaGetLastError();
 }
+template <typename T, int KS>
+cudaError_t multi_gram_ks(const MultiGram<T>& g, cudaStream_t s) {
+    const size_t smem = (size_t)2 * g.nb * kGramRows * KS * sizeof(T);
+    // the static pair tables (about 2 KB) count against the 48 KB default too
+    if (smem + 4096 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_multi_gram<T, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_multi_gram<T, KS><<<dim3(g.chunks, g.groups, g.panels), VNE_THREADS, smem, s>>>(g);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_multi_gram(MultiGram<T> g, double* out, cudaStream_t s) {
+    if (g.nb < 1 || g.nb > 24) return cudaErrorInvalidValue;
+    const int npair = g.nb * (g.nb + 1);
+    g.groups = (npair * g.ks + kGramOut - 1) / kGramOut;
+    cudaError_t e = cudaSuccess;
+    VNE_KS_SWITCH(T, g.ks, (e = multi_gram_ks<T, KS>(g, s)));
+    if (e != cudaSuccess) return e;
+    const int K = g.panels * g.ks;
+    k_multi_gram_reduce<<<(npair * K + 255) / 256, 256, 0, s>>>(g.part, g.panels, g.groups, g.chunks, g.ks, npair,
+                                                                 out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_multi_gram<float>(MultiGram<float>, double*, cudaStream_t);
+template cudaError_t launch_multi_gram<double>(MultiGram<double>, double*, cudaStream_t);
+
+cudaError_t launch_cg_tridiag(const double* ah, const double* bh, int K, int k, double s0, double tau, double* diag,
+                              double* off, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_cg_tridiag<<<(K + 63) / 64, 64, 0, s>>>(ah, bh, K, k, s0, tau, diag, off);
+    return cudaGetLastError();
+}
+cudaError_t launch_gram_mirror(const double* uniq, int nb, int K, double* full, cudaStream_t s) {
+    const size_t total = (size_t)nb * nb * K;
+    if (total == 0) return cudaSuccess;
+    k_gram_mirror<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(uniq, nb, K, full);
+    return cudaGetLastError();
+}
 cudaError_t launch_rational_pass1(const double* M, int nb, int K, double drop, double* X, cudaStream_t s) {
     if (nb > kMaxBasis) return cudaErrorInvalidValue;
     k_rational_pass1<<<(K + 31) / 32, 32, 0, s>>>(M, nb, K, drop, X);
