@@ -465,7 +465,12 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;
     constexpr int RPI = VNE_THREADS / LPR;  // rows per iteration
-    const int panel = p.panel_base + blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    // panels in reverse order: the step kernel walked them forwards, so the
+    // first panels updated are the ones it touched last (still partly in L2),
+    // and the next step starts on the panel updated last
+    const int np = gridDim.x / p.tiles_per_panel;
+    const int panel = p.panel_base + (np - 1 - (int)(blockIdx.x / p.tiles_per_panel)),
+              tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
     const int cofs = sub * CPL;
