@@ -155,7 +155,10 @@ struct RowSum {
     __device__ __forceinline__ double total() const { return acc + (double)part; }
 };
 
-// Pass 1: column sums per segment -> mean (only when desingularising).
+// Pass 1: column sums per segment -> mean (only when desingularising); the
+// source values are stored in w_1 on the way, so pass 2 reads them instead of
+// generating them again (the counter-based probes cost more integer work
+// than a read and a write of the block).
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
@@ -164,6 +167,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
     constexpr int RPI = VNE_THREADS / KS;
     const int gc = panel * KS + c;
+    T* out = p.w1 + (size_t)panel * p.n_total * KS;
     RowSum<T> rs;
     // four rows per pass, their node ids loaded first (same row order as a
     // plain loop, so the sums are unchanged)
@@ -177,7 +181,11 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int r = r0 + u * RPI;
-            if (r < t.row_end) rs.add(source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg));
+            if (r < t.row_end) {
+                const T v = source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg);
+                out[(size_t)r * KS + c] = v;
+                rs.add(v);
+            }
         }
     }
     __shared__ double red[VNE_THREADS];
@@ -197,7 +205,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
 }
 
 // Pass 2: w_1 = b - mean (stored in T), ||w_1||^2 (FP64 across partial sums),
-// sigma_1 = 1/||w_1||.
+// sigma_1 = 1/||w_1||.  With desingularisation b is read back from w_1, where
+// pass 1 stored it.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
@@ -213,17 +222,25 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
     for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPI) {
         int ids[4];
         T vals[4];
+        if (p.desing) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int r = r0 + u * RPI;
-            ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
-        }
+            for (int u = 0; u < 4; u++) {
+                const int r = r0 + u * RPI;
+                vals[u] = (live && r < t.row_end) ? out[(size_t)r * KS + c] - mu : (T)0;
+            }
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int r = r0 + u * RPI;
-            vals[u] = (live && r < t.row_end)
-                          ? source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg) - mu
-                          : (T)0;
+            for (int u = 0; u < 4; u++) {
+                const int r = r0 + u * RPI;
+                ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int r = r0 + u * RPI;
+                vals[u] = (live && r < t.row_end)
+                              ? source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg)
+                              : (T)0;
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
