@@ -1,0 +1,52 @@
+"""Parity at the headline's full size: the BA graph with n = 10^6, m = 4
+(seed 3), FP32, the schedule the autotuner picks (as the benchmark times it),
+60 Lanczos steps.  The oracle evaluates a few sampled quadratic forms one by
+one (FP64 Lanczos with the same breakdown rule and no reorthogonalisation,
+as the FP32 path), and the FP32 Hutch++ estimate is compared with the FP64
+device run on identical vectors (the accuracy the headline is quoted at)."""
+import numpy as np
+import pytest
+
+from oracle import density, krylov, rng
+from paper_2212_09642_gb300 import graphs, vne
+
+pytestmark = pytest.mark.gpu
+
+N, M_BA, SEED, STEPS = 1_000_000, 4, 3, 60
+
+
+@pytest.fixture(scope="module")
+def headline_graph():
+    return graphs.barabasi_albert(N, M_BA, SEED)
+
+
+def test_sampled_quadforms_at_full_size(vctx, headline_graph):
+    g = headline_graph
+    mat = vne.matrix_from_graph(vctx, g, fp64=False, reorder=True)
+    try:
+        vne.vne_autotune(vctx, mat, 112, 8)
+        # probes 100..111: the first Hutchinson columns of the headline's Hutch++
+        opt = vne.options(reorth=0, probe_offset=100)
+        _, _, psi = vne.vne_entropy_hutchinson(vctx, mat, 12, STEPS, 7, opt=opt, want_psi=True)
+    finally:
+        vne.vne_matrix_destroy(mat)
+    A, _ = density.density_matrix(g)
+    nA = density.gershgorin_norm(A)
+    X = rng.rademacher(7, g.n, 100, 3)
+    for j in range(3):
+        ref = krylov.lanczos_quadform(A, X[:, j], STEPS, reorth="none", norm_A=nA)[0]
+        assert abs(psi[j] - ref) <= 1e-5 * abs(ref), (j, psi[j], ref)
+
+
+def test_hutchpp_fp32_against_fp64_at_full_size(vctx, headline_graph):
+    """The headline's metric is quoted at a relative error of 1e-4 of the
+    mixed-precision estimate against the FP64 run on identical vectors."""
+    g = headline_graph
+    ests = {}
+    for fp64 in (False, True):
+        mat = vne.matrix_from_graph(vctx, g, fp64=fp64, reorder=True)
+        try:
+            ests[fp64] = vne.vne_entropy_hutchpp(vctx, mat, 100, 100, STEPS, 11, opt=vne.options(reorth=0))[0]
+        finally:
+            vne.vne_matrix_destroy(mat)
+    assert abs(ests[False] - ests[True]) <= 1e-4 * abs(ests[True]), ests
