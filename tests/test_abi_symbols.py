@@ -56,3 +56,23 @@ def test_host_greedy_coloring_matches_oracle(lib, d):
         want = coloring.greedy_distance_coloring(g, d)
         assert np.array_equal(got, want)
         assert s == want.max() + 1
+
+
+def test_null_handles_are_rejected_without_a_gpu(lib):
+    """Every entry point checks its handle before touching the device."""
+    from paper_2212_09642_gb300 import vne
+    k = __import__("ctypes").c_int32()
+    assert lib.vne_matrix_coloring(None, 2, None, None, None) == vne.VNE_EINVAL
+    assert lib.vne_entropy_probing_auto(None, 1e-3, 30, 8, vne._COLORING_FN(), None, None, None, None) == vne.VNE_EINVAL
+    assert lib.vne_ctx_last_poly_dim(None, __import__("ctypes").byref(k)) == vne.VNE_EINVAL
+    assert lib.vne_ctx_last_steps(None, __import__("ctypes").byref(k)) == vne.VNE_EINVAL
+    assert lib.vne_entropy_probing(None, None, 2, 30, None, 0, None, None, None) == vne.VNE_EINVAL
+
+
+def test_options_layout_matches_the_header(lib):
+    """The binding's vne_options has the C struct's size (defaults written by
+    the library land in the right fields)."""
+    from paper_2212_09642_gb300 import vne
+    o = vne.options()
+    assert o.quad_tol == 0.0 and o.check_every == 0 and o.spectrum_min == 0.0 and o.probe_offset == 0
+    assert vne.vne_probing_report.eps_abs.offset == 24 and __import__("ctypes").sizeof(vne.vne_probing_report) == 80
