@@ -101,6 +101,10 @@ struct vne_ctx {
     // kept for repeated estimates over the same batch; key = the matrices'
     // creation ids and the plan parameters
     Problem* batch_prob = nullptr;
+    // device colourings: streams of the jobs after the first, pinned counters
+    std::vector<cudaStream_t> color_streams;
+    std::vector<cudaEvent_t> color_events;
+    int32_t* pinned_ctr = nullptr;
     std::vector<uint64_t> batch_key;
     int batch_ks = 0;
 };
@@ -1303,6 +1307,9 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaStream_t sx : ctx->color_streams) cudaStreamDestroy(sx);
+    for (cudaEvent_t e : ctx->color_events) cudaEventDestroy(e);
+    if (ctx->pinned_ctr) cudaFreeHost(ctx->pinned_ctr);
     delete ctx->batch_prob;
     delete ctx;
     return VNE_OK;
@@ -1761,95 +1768,170 @@ extern "C" vne_status vne_entropy_hutchpp(vne_matrix* M, int32_t sketch_cols, in
 namespace {
 
 // Greedy distance-d colouring (Algorithm 1) of M's graph on the device, in
-// rounds of k_color_round (and k_color_big for balls too large for a warp);
-// the colours land in workspace `name` in the caller's node numbering.
-// Returns the number of rounds, or 0 when a ball (d >= 3) did not fit even a
-// CTA's table; then nothing is written.
-int device_coloring(vne_matrix* M, int d, const std::string& name, int32_t** out, int32_t* s) {
-    vne_ctx* ctx = M->ctx;
-    cudaStream_t st = ctx->stream;
-    const int64_t n = M->n;
-    uint64_t* key = ws_get_t<uint64_t>(ctx, "col.key", n);
-    int32_t* color = ws_get_t<int32_t>(ctx, "col.color", n);
-    int32_t* blk = ws_get_t<int32_t>(ctx, "col.blk", n);
-    int32_t* l0 = ws_get_t<int32_t>(ctx, "col.l0", n);
-    int32_t* l1 = ws_get_t<int32_t>(ctx, "col.l1", n);
-    int32_t* ctr = ws_get_t<int32_t>(ctx, "col.ctr", 8, true);  // cnt[3], ncolors, overflow, bigcnt[2]
-    int32_t* inv = M->d_node_id ? ws_get_t<int32_t>(ctx, "col.inv", n) : nullptr;
-    int32_t* tries = ws_get_t<int32_t>(ctx, "col.tries", n);
-    VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, inv, tries, color, blk, l0, st));
-    const int32_t n32 = (int32_t)n;
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(ctr, &n32, sizeof(n32), cudaMemcpyHostToDevice, st));
+// rounds of k_color_round (and k_color_big for balls too large for a warp).
+// Several colourings (one per distance) run at once, each on its own stream
+// with its own workspace: their rounds are latency-bound, so they overlap.
+// The colours land in workspace `name` of each job in the caller's node
+// numbering; job.rounds = the rounds it took, 0 when a ball (d >= 3) did not
+// fit even a CTA's table (then nothing is written).
+struct ColorJob {
+    int d = 1;
+    std::string name;
+    int32_t* out = nullptr;  // caller numbering
+    int32_t s = 0;           // colours
+    int rounds = 0;
+    // internal
+    cudaStream_t st = nullptr;
     ColorRound p{};
-    p.rowptr = M->d_rowptr;
-    p.col = M->d_col;
-    p.key = key;
-    p.inv = inv;
-    p.color = color;
-    p.blk = blk;
-    p.tries = tries;
-    p.list[0] = l0;
-    p.list[1] = l1;
-    p.cnt = ctr;
-    p.ncolors = ctr + 3;
-    p.overflow = ctr + 4;
-    p.d = d;
-    if (d >= 3) {
-        // balls too large for a warp's shared-memory table go to one CTA
-        // each (k_color_big); the tables start empty (epoch 0 everywhere)
-        const size_t ctas = (size_t)color_big_ctas();
-        p.biglist = ws_get_t<int32_t>(ctx, "col.big", n);
-        p.bigcnt = ctr + 5;
-        p.bigtab = ws_get_t<uint64_t>(ctx, "col.bigtab", ctas * color_big_table_entries(), true);
-        p.bigball = ws_get_t<int32_t>(ctx, "col.bigball", ctas * color_big_ball_entries());
-        p.epoch = ws_get_t<uint32_t>(ctx, "col.epoch", ctas, true);
-    }
+    int32_t* ctr = nullptr;
+    int32_t* h = nullptr;  // pinned host copy of the counters
     int r = 0;
-    int64_t prev = n;
-    int32_t h[8];
-    for (;;) {
-        // every round colours at least the first uncoloured node in the
-        // greedy order, so a batch of rounds always makes progress
-        const int batch = prev > 4096 ? 4 : 16;
-        for (int b = 0; b < batch; b++, r++) {
-            p.round = r;
-            VNE_TRY_CUDA(ctx, launch_color_round(p, st));
-            ctx->launches++;
-            if (p.biglist) {
-                VNE_TRY_CUDA(ctx, launch_color_big(p, st));
-                ctx->launches++;
-            }
+    int64_t prev = 0;
+    bool done = false, overflow = false;
+};
+
+void device_colorings(vne_matrix* M, std::vector<ColorJob>& jobs) {
+    vne_ctx* ctx = M->ctx;
+    const int64_t n = M->n;
+    const int nj = (int)jobs.size();
+    if (!ctx->pinned_ctr) VNE_TRY_CUDA(ctx, cudaMallocHost(&ctx->pinned_ctr, 8 * 8 * sizeof(int32_t)));
+    VNE_REQUIRE(ctx, nj >= 1 && nj <= 8, VNE_EINVAL, "1..8 colourings at once");
+    while ((int)ctx->color_streams.size() < nj - 1) {
+        cudaStream_t sx = nullptr;
+        VNE_TRY_CUDA(ctx, cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
+        ctx->color_streams.push_back(sx);
+        for (int k = 0; k < 2; k++) {  // fork and join events of that stream
+            cudaEvent_t e = nullptr;
+            VNE_TRY_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            ctx->color_events.push_back(e);
         }
-        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
-        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
-        if (h[4]) return 0;
-        const int64_t left = h[r % 3];
-        if (left == 0) break;
-        VNE_REQUIRE(ctx, left < prev, VNE_EDEVICE, "device colouring made no progress (%lld nodes left)",
-                    (long long)left);
-        prev = left;
     }
-    int32_t* dout = ws_get_t<int32_t>(ctx, name, n);
-    VNE_TRY_CUDA(ctx, launch_color_scatter(color, M->d_node_id, n, dout, st));
-    ctx->launches++;
-    *out = dout;
-    *s = h[3];
-    return r;
+    const int32_t n32 = (int32_t)n;
+    for (int i = 0; i < nj; i++) {
+        ColorJob& J = jobs[i];
+        J.st = i == 0 ? ctx->stream : ctx->color_streams[i - 1];
+        if (i > 0) {  // the job's stream follows the work enqueued on the context's stream
+            cudaEvent_t ev = ctx->color_events[2 * (i - 1)];
+            VNE_TRY_CUDA(ctx, cudaEventRecord(ev, ctx->stream));
+            VNE_TRY_CUDA(ctx, cudaStreamWaitEvent(J.st, ev, 0));
+        }
+        const std::string w = "col" + std::to_string(i) + ".";
+        uint64_t* key = ws_get_t<uint64_t>(ctx, w + "key", n);
+        int32_t* color = ws_get_t<int32_t>(ctx, w + "color", n);
+        int32_t* blk = ws_get_t<int32_t>(ctx, w + "blk", n);
+        int32_t* l0 = ws_get_t<int32_t>(ctx, w + "l0", n);
+        int32_t* l1 = ws_get_t<int32_t>(ctx, w + "l1", n);
+        J.ctr = ws_get_t<int32_t>(ctx, w + "ctr", 8, true);  // cnt[3], ncolors, overflow, bigcnt[2]
+        int32_t* inv = M->d_node_id ? ws_get_t<int32_t>(ctx, w + "inv", n) : nullptr;
+        int32_t* tries = ws_get_t<int32_t>(ctx, w + "tries", n);
+        VNE_TRY_CUDA(ctx, launch_color_init(M->d_rowptr, M->d_node_id, n, key, inv, tries, color, blk, l0, J.st));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(J.ctr, &n32, sizeof(n32), cudaMemcpyHostToDevice, J.st));
+        ColorRound& p = J.p;
+        p = ColorRound{};
+        p.rowptr = M->d_rowptr;
+        p.col = M->d_col;
+        p.key = key;
+        p.inv = inv;
+        p.color = color;
+        p.blk = blk;
+        p.tries = tries;
+        p.list[0] = l0;
+        p.list[1] = l1;
+        p.cnt = J.ctr;
+        p.ncolors = J.ctr + 3;
+        p.overflow = J.ctr + 4;
+        p.d = J.d;
+        if (J.d >= 3) {
+            // balls too large for a warp's shared-memory table go to one CTA
+            // each (k_color_big); the tables start empty (epoch 0 everywhere)
+            const size_t ctas = (size_t)color_big_ctas();
+            p.biglist = ws_get_t<int32_t>(ctx, w + "big", n);
+            p.bigcnt = J.ctr + 5;
+            p.bigtab = ws_get_t<uint64_t>(ctx, w + "bigtab", ctas * color_big_table_entries(), true);
+            p.bigball = ws_get_t<int32_t>(ctx, w + "bigball", ctas * color_big_ball_entries());
+            p.epoch = ws_get_t<uint32_t>(ctx, w + "epoch", ctas, true);
+        }
+        J.h = ctx->pinned_ctr + 8 * i;
+        J.r = 0;
+        J.prev = n;
+        J.done = J.overflow = false;
+    }
+    for (;;) {
+        bool any = false;
+        for (ColorJob& J : jobs) {
+            if (J.done) continue;
+            any = true;
+            // every round colours at least the first uncoloured node in the
+            // greedy order, so a batch of rounds always makes progress
+            const int batch = J.prev > 4096 ? 4 : 16;
+            for (int b = 0; b < batch; b++, J.r++) {
+                J.p.round = J.r;
+                VNE_TRY_CUDA(ctx, launch_color_round(J.p, J.st));
+                ctx->launches++;
+                if (J.p.biglist) {
+                    VNE_TRY_CUDA(ctx, launch_color_big(J.p, J.st));
+                    ctx->launches++;
+                }
+            }
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(J.h, J.ctr, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, J.st));
+        }
+        if (!any) break;
+        for (ColorJob& J : jobs) {
+            if (J.done) continue;
+            VNE_TRY_CUDA(ctx, cudaStreamSynchronize(J.st));
+            if (J.h[4]) {
+                J.done = J.overflow = true;
+                continue;
+            }
+            const int64_t left = J.h[J.r % 3];
+            if (left == 0) {
+                J.done = true;
+                continue;
+            }
+            VNE_REQUIRE(ctx, left < J.prev, VNE_EDEVICE, "device colouring made no progress (%lld nodes left)",
+                        (long long)left);
+            J.prev = left;
+        }
+    }
+    for (ColorJob& J : jobs) {
+        if (J.overflow) {
+            J.rounds = 0;
+            continue;
+        }
+        J.out = ws_get_t<int32_t>(ctx, J.name, n);
+        VNE_TRY_CUDA(ctx, launch_color_scatter(J.p.color, M->d_node_id, n, J.out, J.st));
+        ctx->launches++;
+        J.s = J.h[3];
+        J.rounds = J.r;
+    }
+    // the context's stream continues after every job
+    for (int i = 1; i < nj; i++) {
+        cudaEvent_t ev = ctx->color_events[2 * (i - 1) + 1];
+        VNE_TRY_CUDA(ctx, cudaEventRecord(ev, jobs[i].st));
+        VNE_TRY_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ev, 0));
+    }
 }
 
 // Colours of M's graph in the caller's numbering, on the device; *rounds =
 // device rounds.  A distance-(d - 1) ball beyond the CTA table (about 196,000
 // nodes) is refused: the sequential sweep over such balls would take
 // n x 196,000 steps or more.
+void matrix_colorings(vne_matrix* M, std::vector<ColorJob>& jobs) {
+    device_colorings(M, jobs);
+    for (const ColorJob& J : jobs)
+        VNE_REQUIRE(M->ctx, J.rounds > 0, VNE_EUNSUPPORTED,
+                    "distance-%d colouring: a ball of radius %d holds more than %zu nodes; pass a colouring", J.d,
+                    J.d - 1, color_big_table_entries() / 4 * 3);
+}
+
 int32_t* matrix_coloring(vne_matrix* M, int d, const std::string& name, int32_t* s, int* rounds) {
-    vne_ctx* ctx = M->ctx;
-    int32_t* dcol = nullptr;
-    int r = device_coloring(M, d, name, &dcol, s);
-    VNE_REQUIRE(ctx, r > 0, VNE_EUNSUPPORTED,
-                "distance-%d colouring: a ball of radius %d holds more than %zu nodes; pass a colouring", d, d - 1,
-                color_big_table_entries() / 4 * 3);
-    if (rounds) *rounds = r;
-    return dcol;
+    std::vector<ColorJob> jobs(1);
+    jobs[0].d = d;
+    jobs[0].name = name;
+    matrix_colorings(M, jobs);
+    *s = jobs[0].s;
+    if (rounds) *rounds = jobs[0].rounds;
+    return jobs[0].out;
 }
 
 }  // namespace
@@ -1967,12 +2049,16 @@ int probing_heuristic_d(double t1, double t2, double t3, double eps_abs, int d_m
 // relative (tol_rel x psi) or per colour eps_abs |V_l| / n.
 template <typename T>
 double probing_at(vne_matrix* M, const vne_options* o, int d, int m, double tol_rel, double eps_abs,
-                  vne_coloring_fn fn, void* user, int* colors, int* steps) {
+                  vne_coloring_fn fn, void* user, int* colors, int* steps, int32_t* pre_col = nullptr,
+                  int32_t pre_s = 0) {
     vne_ctx* ctx = M->ctx;
     int32_t s = 0;
     int32_t* dcol = nullptr;
     std::vector<int32_t> host_sizes;
-    if (fn) {
+    if (pre_col) {  // a device colouring computed beforehand
+        dcol = pre_col;
+        s = pre_s;
+    } else if (fn) {
         // the caller's colouring (e.g. an optimal one for a structured graph)
         std::vector<int32_t> col(M->n);
         s = fn(user, d, M->n, col.data());
@@ -2037,10 +2123,25 @@ extern "C" vne_status vne_entropy_probing_auto(vne_matrix* M, double eps, int32_
     vne_probing_report r{};
     std::vector<double> T;
     std::vector<int> cols, steps;
+    // the device colourings at d = 1, 2, 3 do not depend on the T values:
+    // computed first, at once (their rounds overlap on three streams)
+    std::vector<ColorJob> pre;
+    if (!coloring_fn) {
+        pre.resize(3);
+        for (int i = 0; i < 3; i++) {
+            pre[i].d = i + 1;
+            pre[i].name = "colors.d" + std::to_string(i + 1);
+        }
+        matrix_colorings(M, pre);
+    }
     auto run = [&](int d, double tol_rel, double eps_abs) {
         int c = 0, st = 0;
-        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st)
-                           : probing_at<float>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st);
+        int32_t* pc = (d <= (int)pre.size()) ? pre[d - 1].out : nullptr;
+        const int32_t ps = (d <= (int)pre.size()) ? pre[d - 1].s : 0;
+        double t = M->fp64 ? probing_at<double>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st,
+                                                pc, ps)
+                           : probing_at<float>(M, &o, d, krylov_steps, tol_rel, eps_abs, coloring_fn, user, &c, &st,
+                                               pc, ps);
         T.push_back(t);
         cols.push_back(c);
         steps.push_back(st);
