@@ -18,7 +18,7 @@ import numpy as np
 from .density import gershgorin_norm
 from .entropy import f_entropy
 from .krylov import lanczos_quadform, lanczos_fmatvec
-from .rng import rademacher
+from .rng import probes, rademacher
 
 
 def quadforms(A, X, m, reorth="full", desing=True, f=f_entropy):
@@ -28,9 +28,9 @@ def quadforms(A, X, m, reorth="full", desing=True, f=f_entropy):
                      for j in range(X.shape[1])])
 
 
-def hutchinson(A, num_vectors, m, seed, reorth="full", col_begin=0, rows=None):
-    """Returns (estimate, psi) for Rademacher probes of columns col_begin.."""
-    X = rademacher(seed, A.shape[0], col_begin, num_vectors, rows=rows)
+def hutchinson(A, num_vectors, m, seed, reorth="full", col_begin=0, rows=None, dist="rademacher"):
+    """Returns (estimate, psi) for Rademacher (or Gaussian) probes of columns col_begin.."""
+    X = probes(seed, A.shape[0], col_begin, num_vectors, rows=rows, dist=dist)
     psi = quadforms(A, X, m, reorth=reorth)
     return float(np.mean(psi)) if num_vectors else 0.0, psi
 
@@ -48,17 +48,17 @@ def orthonormal_range(Y, rtol=None):
     return U[:, s > rtol * s[0]]
 
 
-def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_parts=False):
+def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_parts=False, dist="rademacher"):
     """Hutch++ estimate of tr f(A) (eq. Hutch++_formula)."""
     n = A.shape[0]
     nA = gershgorin_norm(A)
-    Omega = rademacher(seed, n, 0, n_sketch, rows=rows)
+    Omega = probes(seed, n, 0, n_sketch, rows=rows, dist=dist)
     Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], m, reorth=reorth, norm_A=nA)
                          for j in range(n_sketch)]) if n_sketch else np.zeros((n, 0))
     Q = orthonormal_range(Y)
     psi_q = np.array([lanczos_quadform(A, Q[:, i], m, reorth=reorth, norm_A=nA)[0]
                       for i in range(Q.shape[1])])
-    G = rademacher(seed, n, n_sketch, n_hutch, rows=rows)
+    G = probes(seed, n, n_sketch, n_hutch, rows=rows, dist=dist)
     Gp = G - Q @ (Q.T @ G)
     psi_g = np.array([lanczos_quadform(A, Gp[:, j], m, reorth=reorth, norm_A=nA)[0]
                       for j in range(n_hutch)])

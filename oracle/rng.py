@@ -58,3 +58,31 @@ def rademacher(seed: int, n: int, col_begin: int, col_count: int, rows=None) -> 
     c = np.arange(col_begin, col_begin + col_count, dtype=np.uint64)
     h = hash_entries(seed, c[None, :], r[:, None])
     return np.where((h >> np.uint64(63)) == 0, 1.0, -1.0)
+
+
+# ---- Gaussian probes (the paper's distribution, Section 3.2) ----
+#
+# Box-Muller on the same counters (Box & Muller, "A note on the generation of
+# random normal deviates", Ann. Math. Statist. 1958):
+#   h1 = h(j, i),  h2 = mix64(h1 + gamma)
+#   u1 = ((h1 >> 11) + 1/2) 2^-53  in (0, 1),   u2 = (h2 >> 11) 2^-53  in [0, 1)
+#   x_i^{(j)} = sqrt(-2 log u1) cos(2 pi u2)
+# in FP64 on both sides (the two sides' log and cos may differ in the last
+# bits, so the vectors agree to rounding, not bit for bit).
+
+def gaussian(seed: int, n: int, col_begin: int, col_count: int, rows=None) -> np.ndarray:
+    """n x col_count standard normal entries, columns col_begin.. (see above)."""
+    r = np.arange(n, dtype=np.uint64) if rows is None else np.asarray(rows, dtype=np.uint64)
+    c = np.arange(col_begin, col_begin + col_count, dtype=np.uint64)
+    h1 = hash_entries(seed, c[None, :], r[:, None])
+    with np.errstate(over="ignore"):
+        h2 = mix64(h1 + GAMMA)
+    u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    u2 = (h2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def probes(seed: int, n: int, col_begin: int, col_count: int, rows=None, dist: str = "rademacher") -> np.ndarray:
+    if dist == "gaussian":
+        return gaussian(seed, n, col_begin, col_count, rows)
+    return rademacher(seed, n, col_begin, col_count, rows)
