@@ -109,7 +109,12 @@ typedef struct vne_options {
                              of A for the bounds; 0 = half the smallest
                              positive Ritz value of each column (the upper end
                              is the Gershgorin bound of A) */
-    int32_t reserved[2];
+    int32_t gaussian_probes; /* 1: Hutchinson / Hutch++ / batched / served
+                                probes are standard normal (the paper's
+                                choice, Section 3.2): Box-Muller on the same
+                                counters as the Rademacher entries, see
+                                vne_gaussian_probes; 0 (default): Rademacher */
+    int32_t reserved;
 } vne_options;
 
 /* Fill *opt with the defaults described above. */
@@ -357,6 +362,14 @@ vne_status vne_quadrature_bounds(vne_ctx *ctx, const double *alpha, const double
  * Rademacher columns col_begin..col_begin+k-1 for node ids 0..n-1. */
 vne_status vne_rademacher(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,
                           int32_t fp64, void *out_device);
+/* The Gaussian probes of the same counters (vne_options.gaussian_probes):
+ * with h1 = h(j, i) the Rademacher hash of column j and node i and
+ * h2 = mix64(h1 + 0x9E3779B97F4A7C15), u1 = ((h1 >> 11) + 1/2) 2^-53,
+ * u2 = (h2 >> 11) 2^-53, x = sqrt(-2 log u1) cos(2 pi u2) (Box-Muller), FP64.
+ * out_device: device double[n][k] row-major, columns col_begin.. .  EINVAL
+ * for bad sizes or a NULL buffer. */
+vne_status vne_gaussian_probes(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,
+                               double *out_device);
 
 /* ---- schedule autotuner --------------------------------------------------
  * Time the Lanczos step and update kernels of `mat` on one block of k

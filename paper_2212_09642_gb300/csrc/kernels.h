@@ -19,6 +19,7 @@ struct StartSource {
     const double* dense;    // SRC_DENSE64: [n][ld] in caller numbering
     const uint64_t* seg_seed;  // SRC_RADEMACHER, optional: per-segment mixed seed
     const int32_t* seg_col0;   //   and per-segment first probe column
+    int32_t gaussian;          // SRC_RADEMACHER: 1 = standard normal entries (Box-Muller on the counters)
 };
 
 template <typename T>
@@ -113,6 +114,8 @@ cudaError_t launch_spmm_plain(const int32_t* rowptr, const int32_t* col, const T
                               const int32_t* node_id, double scale, const T* X, T* Y, cudaStream_t);
 cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, int fp64, void* out,
                                    cudaStream_t);
+// FP64 standard normal probes from the same counters (Box-Muller).
+cudaError_t launch_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, double* out, cudaStream_t st);
 
 // ---- multi-shift CG and rational projection (rational.cu) ----
 struct CgState {

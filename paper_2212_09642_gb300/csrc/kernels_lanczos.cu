@@ -77,15 +77,27 @@ __device__ __forceinline__ double rademacher_entry(uint64_t s, uint64_t col, uin
     return (h >> 63) ? -1.0 : 1.0;
 }
 
+// Standard normal entries from the same counters (Box & Muller 1958): with
+// h1 = h(col, node) and h2 = mix64(h1 + gamma), u1 = ((h1 >> 11) + 1/2) 2^-53
+// and u2 = (h2 >> 11) 2^-53, x = sqrt(-2 log u1) cos(2 pi u2) in FP64.
+__device__ __forceinline__ double gaussian_entry(uint64_t s, uint64_t col, uint64_t node) {
+    const uint64_t h1 = mix64((((col << 32) | node) ^ s) + 0x9E3779B97F4A7C15ULL);
+    const uint64_t h2 = mix64(h1 + 0x9E3779B97F4A7C15ULL);
+    const double u1 = ((double)(h1 >> 11) + 0.5) * 0x1.0p-53;
+    const double u2 = (double)(h2 >> 11) * 0x1.0p-53;
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
 // Start-vector source value for packed row r (local node id `id`, segment
 // seg) and block column gc (global within the block).
 __device__ __forceinline__ double source_value(const StartSource& S, int r, int id, int gc, int seg) {
     if (gc >= S.ncols) return 0.0;
     switch (S.kind) {
-        case SRC_RADEMACHER:
-            if (S.seg_seed)
-                return rademacher_entry(S.seg_seed[seg], (uint64_t)(S.seg_col0[seg] + gc), (uint64_t)id);
-            return rademacher_entry(S.seed_mixed, (uint64_t)(S.col_begin + gc), (uint64_t)id);
+        case SRC_RADEMACHER: {
+            const uint64_t sd = S.seg_seed ? S.seg_seed[seg] : S.seed_mixed;
+            const uint64_t col = S.seg_seed ? (uint64_t)(S.seg_col0[seg] + gc) : (uint64_t)(S.col_begin + gc);
+            return S.gaussian ? gaussian_entry(sd, col, (uint64_t)id) : rademacher_entry(sd, col, (uint64_t)id);
+        }
         case SRC_INDICATOR:
             return (S.colors[id] == S.col_begin + gc) ? 1.0 : 0.0;
         case SRC_DENSE64:
@@ -118,6 +130,7 @@ __device__ __forceinline__ T source_value_t(const StartSource& S, const T* panel
         case SRC_RADEMACHER: {
             const uint64_t s = S.seg_seed ? S.seg_seed[seg] : S.seed_mixed;
             const uint64_t col = S.seg_seed ? (uint64_t)(S.seg_col0[seg] + gc) : (uint64_t)(S.col_begin + gc);
+            if (S.gaussian) return (T)gaussian_entry(s, col, (uint64_t)id);
             const uint64_t h = mix64((((col << 32) | (uint64_t)id) ^ s) + 0x9E3779B97F4A7C15ULL);
             return (h >> 63) ? (T)-1 : (T)1;
         }
@@ -686,6 +699,12 @@ __global__ void k_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin,
     else ((float*)out)[idx] = (float)v;
 }
 
+__global__ void k_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, double* out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    out[idx] = gaussian_entry(seed_mixed, (uint64_t)(col_begin + (int)(idx % k)), (uint64_t)(idx / k));
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 
@@ -779,6 +798,13 @@ cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin
     int64_t total = n * (int64_t)k;
     if (total == 0) return cudaSuccess;
     k_rademacher_fill<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(seed_mixed, n, col_begin, k, fp64, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, double* out, cudaStream_t st) {
+    const int64_t total = n * (int64_t)k;
+    if (total == 0) return cudaSuccess;
+    k_gaussian_fill<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(seed_mixed, n, col_begin, k, out);
     return cudaGetLastError();
 }
 

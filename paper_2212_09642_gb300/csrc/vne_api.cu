@@ -1598,6 +1598,7 @@ extern "C" vne_status vne_entropy_hutchinson(vne_matrix* M, int32_t num_vectors,
     VNE_REQUIRE(ctx, krylov_steps >= 1 && krylov_steps <= 128, VNE_EINVAL, "krylov_steps must be in [1, 128]");
     StartSource s{};
     s.kind = SRC_RADEMACHER;
+    s.gaussian = o.gaussian_probes != 0;
     s.seed_mixed = seed_mix(seed);
     VNE_REQUIRE(ctx, o.probe_offset >= 0, VNE_EINVAL, "probe_offset must be >= 0");
     s.col_begin = o.probe_offset;
@@ -1639,6 +1640,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     // 1. sketch: Y = f(A) Omega by the Lanczos matvec approximation, basis kept
     StartSource s{};
     s.kind = SRC_RADEMACHER;
+    s.gaussian = o && o->gaussian_probes != 0;
     s.seed_mixed = sm;
     s.col_begin = 0;
     s.ncols = Nr;
@@ -1696,6 +1698,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
         T* Gp = QG + (size_t)Kp * n;
         StartSource sg{};
         sg.kind = SRC_RADEMACHER;
+        sg.gaussian = o && o->gaussian_probes != 0;
         sg.seed_mixed = sm;
         sg.col_begin = Nr;
         sg.ncols = NH;
@@ -2282,6 +2285,18 @@ extern "C" vne_status vne_rademacher(vne_ctx* ctx, uint64_t seed, int64_t n, int
     VNE_API_END(ctx)
 }
 
+extern "C" vne_status vne_gaussian_probes(vne_ctx* ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,
+                                          double* out_device) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, out_device && n >= 1 && k >= 1 && col_begin >= 0, VNE_EINVAL,
+                "bad arguments to vne_gaussian_probes");
+    VNE_TRY_CUDA(ctx, launch_gaussian_fill(seed_mix(seed), n, col_begin, k, out_device, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_API_END(ctx)
+}
+
 // ---------------------------------------------------------------------------
 // batched uneven graphs: block-diagonal packing, one schedule, one launch per
 // kernel per step for all graphs
@@ -2380,6 +2395,7 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
     const int variant = fp64 ? 0 : (o.step_variant >= 0 ? o.step_variant : 4);
     StartSource s{};
     s.kind = SRC_RADEMACHER;
+    s.gaussian = o.gaussian_probes != 0;
     s.seed_mixed = seed_mix(seed);
     s.col_begin = 0;
     s.ncols = num_vectors;
@@ -2811,6 +2827,7 @@ extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t
     P.d_tiles = upload(ctx, "srv.tiles", P.tiles);
     StartSource src{};
     src.kind = SRC_RADEMACHER;
+    src.gaussian = S->opt.gaussian_probes != 0;
     src.ncols = S->block;
     src.seg_seed = upload(ctx, "srv.seeds", seeds);
     src.seg_col0 = upload(ctx, "srv.col0", col0);

@@ -52,7 +52,8 @@ class vne_options(ctypes.Structure):
                 ("cg_tol", ctypes.c_double), ("breakdown_tol", ctypes.c_double),
                 ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("probe_offset", ctypes.c_int32), ("check_every", ctypes.c_int32), ("quad_tol", ctypes.c_double),
-                ("spectrum_min", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
+                ("spectrum_min", ctypes.c_double), ("gaussian_probes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +89,7 @@ def _declare(lib):
                                      ctypes.POINTER(vne_options), _PD, _PI32]),
         "vne_greedy_coloring": (st, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _PI32]),
         "vne_matrix_coloring": (st, [_P, ctypes.c_int32, _P, _PI32, _PI32]),
+        "vne_gaussian_probes": (st, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_entropy_probing_auto": (st, [_P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _COLORING_FN, _P,
                                           ctypes.POINTER(vne_options), _PD, ctypes.POINTER(vne_probing_report)]),
         "vne_spmm": (st, [_P, _P, _P, ctypes.c_int32]),
@@ -143,7 +145,7 @@ def exported_symbols():
 _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
-               "vne_greedy_coloring", "vne_matrix_coloring", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
+               "vne_greedy_coloring", "vne_matrix_coloring", "vne_gaussian_probes", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_ctx_last_poly_dim", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
@@ -340,6 +342,11 @@ def vne_matrix_coloring(ctx, mat, n, distance):
     s, rounds = ctypes.c_int32(), ctypes.c_int32()
     _check(load().vne_matrix_coloring(mat, int(distance), _ptr(colors), ctypes.byref(s), ctypes.byref(rounds)), ctx)
     return colors, s.value, rounds.value
+
+
+def vne_gaussian_probes(ctx, seed, n, col_begin, k, out):
+    """Fill the device tensor out (float64, [n, k]) with the Gaussian probes."""
+    _check(load().vne_gaussian_probes(ctx, int(seed) & (2**64 - 1), int(n), int(col_begin), int(k), _ptr(out)), ctx)
 
 
 def vne_spmm(ctx, mat, X, Y, k):
