@@ -334,6 +334,17 @@ vne_status vne_matrix_coloring(vne_matrix *mat, int32_t distance, int32_t *color
  * numbering.  A is the normalised density matrix. */
 vne_status vne_spmm(vne_matrix *mat, const void *X, void *Y, int32_t k);
 
+/* C = X^T Y (the Gram of the Hutch++ sketch, Section 3.2: Y^T Y for the
+ * Cholesky-QR and Q^T G for the projection) on the tcgen05 tensor cores.
+ * X, Y: device float blocks in panel-major layout [k / ks][n][ks] (ks = 8,
+ * 16 or 32 columns per panel), kx, ky <= 128 columns, multiples of ks;
+ * C: host double[kx][ky] row-major.  TF32 three-product split (FP32
+ * accuracy), FP32 accumulation within a CTA, FP64 across CTAs.  EINVAL for
+ * bad sizes or NULL buffers; EDEVICE if a bounded wait of the kernel ran
+ * out. */
+vne_status vne_block_gram(vne_ctx *ctx, const float *X, int32_t kx, const float *Y, int32_t ky, int32_t ks,
+                          int64_t n, double *C);
+
 /* Gauss quadrature of given tridiagonals (Section 4): for each of `count`
  * columns, T = tridiag(beta[0..m-2], alpha[0..m-1]), psi = norm2 *
  * sum_j u_{1j}^2 f(scale * theta_j).  alpha, beta: double[count][m] host;

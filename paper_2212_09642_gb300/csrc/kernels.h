@@ -247,9 +247,15 @@ cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const d
                                 int count, int m, int ld, double* zvec, cudaStream_t);
 
 // Gram C = X^T Y of two panel-major blocks (FP32/FP64 data, FP64 result [Kx][Ky]).
+// FP32 blocks of at most 128 columns run on the tcgen05 tensor cores; err
+// (device int) is set to 1 if one of that kernel's bounded waits ran out.
 template <typename T>
 cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks,
-                        double* C, cudaStream_t);
+                        double* C, int* err, cudaStream_t);
+// Per-CTA partial Grams of the tcgen05 kernel: part [chunks][kx][ky], at
+// most max_chunks (one CTA per SM); *chunks_out = the CTAs launched.
+cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int ks, int n, double* part,
+                            int max_chunks, int* err, int* chunks_out, cudaStream_t st);
 // Out = (In2 ? In2 : 0) + coef * In * M, M double [kin][kout] row-major; panel-major blocks.
 template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,

@@ -1232,14 +1232,9 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, c
         }
 }
 
-// Tensor-core Gram C = X^T Y for FP32 blocks (kx, ky <= 128): warp-level
-// MMA m16n8k8 on TF32 operands with a three-product split (x = x_hi + x_lo,
-// both TF32; x^T y ~ hi.hi + hi.lo + lo.hi), which keeps the products at
-// FP32 accuracy.  The contraction reads each row of X and Y once (about 50
-// flops per byte for 112 columns), so it is bound by HBM, not by the tensor
-// pipe.  CTA: 8 warps in a 4 x 2 grid, each owning a 32 x 64 block of the
-// 128 x 128 output; rows are streamed in 32-row slabs through padded shared
-// memory; accumulation in FP32 over the CTA's rows, FP64 across CTAs.
+// TF32 split helpers for the warp-level MMA block product below
+// (x = x_hi + x_lo, both TF32; x^T y ~ hi.hi + hi.lo + lo.hi keeps FP32
+// accuracy).
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -1254,121 +1249,6 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int KS>
-__global__ void __launch_bounds__(256, 2) k_gram_tc(const float* __restrict__ X, int kx, const float* __restrict__ Y,
-                                                    int ky, int n, int rows_per_chunk, double* __restrict__ part) {
-    constexpr int LD = 136;  // padded row (128 + 8 floats): conflict-free fragment loads
-    constexpr int SLAB = 32;
-    constexpr int V_PER_ROW = KS / 4;  // float4 per row of one panel
-    // dynamic shared memory: [2 buffers][X, Y][SLAB][LD]; a Gram of a block
-    // with itself (X == Y) loads one slab per buffer
-    extern __shared__ __align__(16) float gsm[];
-    const bool same = (X == Y) && (kx == ky);
-    float* xbuf[2] = {gsm, gsm + 2 * SLAB * LD};
-    float* ybuf[2] = {same ? xbuf[0] : gsm + SLAB * LD, same ? xbuf[1] : gsm + 3 * SLAB * LD};
-    const int chunk = blockIdx.x;
-    const int r_begin = chunk * rows_per_chunk;
-    const int r_end = min(n, r_begin + rows_per_chunk);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp >> 1, wn = warp & 1;  // warp block: rows wm*32.., cols wn*64..
-    const int g = lane >> 2, tq = lane & 3;
-    const int px = kx / KS, py = ky / KS;     // panels of X and Y
-    float acc[2][8][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
-    // zero the columns no panel covers (they stay zero for the whole kernel)
-    for (int idx = threadIdx.x; idx < SLAB * 128; idx += 256) {
-        const int rl = idx >> 7, cl = idx & 127;
-        for (int bb = 0; bb < 2; bb++) {
-            if (cl >= kx) xbuf[bb][rl * LD + cl] = 0.f;
-            if (cl >= ky) ybuf[bb][rl * LD + cl] = 0.f;
-        }
-    }
-    // slab of SLAB rows into buffer bb by asynchronous 16-byte copies (rows
-    // past the chunk zero-filled): panel p of a block holds these rows
-    // contiguously, so consecutive threads copy consecutive pieces; the copy
-    // of the next slab runs while the current one is multiplied
-    const int nx = px * SLAB * V_PER_ROW, ny = same ? 0 : py * SLAB * V_PER_ROW;
-    auto issue_slab = [&](int rt, int bb) {
-        for (int idx = threadIdx.x; idx < nx + ny; idx += 256) {
-            const bool isx = idx < nx;
-            const int e = isx ? idx : idx - nx;
-            const int p = e / (SLAB * V_PER_ROW), rem = e % (SLAB * V_PER_ROW);
-            const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
-            const int r = rt + rl;
-            const float* src = (isx ? X : Y) + (size_t)p * n * KS + (size_t)(r < r_end ? r : r_begin) * KS + c;
-            float* dst = (isx ? xbuf[bb] : ybuf[bb]) + rl * LD + p * KS + c;
-            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
-                         "r"(r < r_end ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    __syncthreads();
-    if (r_begin < r_end) issue_slab(r_begin, 0);
-    for (int rt = r_begin, it = 0; rt < r_end; rt += SLAB, it++) {
-        const int bb = it & 1;
-        if (rt + SLAB < r_end) {
-            issue_slab(rt + SLAB, bb ^ 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();
-        const float(*Xs)[LD] = reinterpret_cast<const float(*)[LD]>(xbuf[bb]);
-        const float(*Ys)[LD] = reinterpret_cast<const float(*)[LD]>(ybuf[bb]);
-#pragma unroll 1
-        for (int k0 = 0; k0 < SLAB; k0 += 8) {
-            // A = X^T (M = output rows, K = slab rows), two 16-row tiles per warp
-            uint32_t ahi[2][4], alo[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int m0 = wm * 32 + i * 16;
-                const float vv[4] = {Xs[k0 + tq][m0 + g], Xs[k0 + tq][m0 + g + 8], Xs[k0 + tq + 4][m0 + g],
-                                     Xs[k0 + tq + 4][m0 + g + 8]};
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    ahi[i][q] = to_tf32(vv[q]);
-                    alo[i][q] = to_tf32(vv[q] - __uint_as_float(ahi[i][q]));
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int n0 = wn * 64 + j * 8;
-                const float w0 = Ys[k0 + tq][n0 + g], w1 = Ys[k0 + tq + 4][n0 + g];
-                uint32_t bhi[2], blo[2];
-                bhi[0] = to_tf32(w0);
-                bhi[1] = to_tf32(w1);
-                blo[0] = to_tf32(w0 - __uint_as_float(bhi[0]));
-                blo[1] = to_tf32(w1 - __uint_as_float(bhi[1]));
-#pragma unroll
-                for (int i = 0; i < 2; i++) {
-                    mma_tf32(acc[i][j], alo[i], bhi);
-                    mma_tf32(acc[i][j], ahi[i], blo);
-                    mma_tf32(acc[i][j], ahi[i], bhi);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // fragment (row g / g+8, col 2tq / 2tq+1) -> partial Gram of this chunk
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int row = wm * 32 + i * 16 + g + ((q & 2) ? 8 : 0);
-                const int col = wn * 64 + j * 8 + 2 * tq + (q & 1);
-                if (row < kx && col < ky) part[(size_t)chunk * kx * ky + (size_t)row * ky + col] = (double)acc[i][j][q];
-            }
-}
-
 __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int total, double* __restrict__ C) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -1379,29 +1259,14 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int 
 
 template <typename T>
 cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks, double* C,
-                        cudaStream_t st) {
+                        int* err, cudaStream_t st) {
     if (kx <= 0 || ky <= 0) return cudaSuccess;
-    if (sizeof(T) == 4 && kx <= 128 && ky <= 128) {
-        // tensor-core path (FP32 data)
-        int rpc = (n + nchunks - 1) / nchunks;
-        rpc = ((rpc + 31) / 32) * 32;
-        int chunks = rpc > 0 ? (n + rpc - 1) / rpc : 1;
-        if (chunks < 1) chunks = 1;
-        const float* Xf = reinterpret_cast<const float*>(X);
-        const float* Yf = reinterpret_cast<const float*>(Y);
-        const int smem = 4 * 32 * 136 * (int)sizeof(float);  // [2][X, Y][32][136]
-#define VNE_GRAM_TC(KSV)                                                                                     \
-        if (ks == KSV) {                                                                                     \
-            cudaError_t e = cudaFuncSetAttribute(k_gram_tc<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
-            if (e != cudaSuccess) return e;                                                                  \
-            k_gram_tc<KSV><<<chunks, 256, smem, st>>>(Xf, kx, Yf, ky, n, rpc, part);                        \
-        }
-        VNE_GRAM_TC(8)
-        else VNE_GRAM_TC(16)
-        else VNE_GRAM_TC(32)
-        else return cudaErrorInvalidValue;
-#undef VNE_GRAM_TC
-        int total = kx * ky;
+    if (sizeof(T) == 4 && err && kx <= 128 && ky <= 128 && (ks == 8 || ks == 16 || ks == 32)) {
+        int chunks = 0;
+        cudaError_t e = launch_gram_tc5(reinterpret_cast<const float*>(X), kx, reinterpret_cast<const float*>(Y), ky,
+                                        ks, n, part, nchunks, err, &chunks, st);
+        if (e != cudaSuccess) return e;
+        const int total = kx * ky;
         k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
         return cudaGetLastError();
     }
@@ -1484,7 +1349,7 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ In, int kin
 }
 
 // Tensor-core block product Out = coef * In M (+ In2) for FP32 blocks
-// (kin, kout <= 128), same TF32 three-product split as k_gram_tc.  M (FP64,
+// (kin, kout <= 128), the TF32 three-product split above.  M (FP64,
 // kin x kout) is converted once per CTA into hi/lo TF32 halves in shared
 // memory; each CTA then streams 64-row tiles of In through shared memory
 // (persistent grid).  Warps: 4 x 2, each owning 16 rows x 64 output columns.
@@ -1770,8 +1635,10 @@ cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Mi
     return cudaGetLastError();
 }
 
-template cudaError_t launch_gram<float>(const float*, int, const float*, int, int, int, double*, int, double*, cudaStream_t);
-template cudaError_t launch_gram<double>(const double*, int, const double*, int, int, int, double*, int, double*, cudaStream_t);
+template cudaError_t launch_gram<float>(const float*, int, const float*, int, int, int, double*, int, double*, int*,
+                                       cudaStream_t);
+template cudaError_t launch_gram<double>(const double*, int, const double*, int, int, int, double*, int, double*, int*,
+                                        cudaStream_t);
 template cudaError_t launch_apply<float>(const float*, int, const double*, int, const float*, float*, int, int, double, cudaStream_t);
 template cudaError_t launch_apply<double>(const double*, int, const double*, int, const double*, double*, int, int, double, cudaStream_t);
 

@@ -1,0 +1,319 @@
+// Gram C = X^T Y of two FP32 panel-major blocks on the fifth-generation
+// tensor cores (tcgen05), for the Hutch++ sketch (Section 3.2: the
+// Cholesky-QR of Y = f(A) Omega, and Q^T G for the projection G - Q Q^T G).
+//
+// The contraction runs over the n rows of the blocks; the output is at most
+// 128 x 128.  Each CTA owns a contiguous range of rows and accumulates its
+// partial Gram in tensor memory (TMEM, FP32, one column per output column);
+// the partials are summed in FP64 across CTAs by the caller's reduction.
+//
+// Pipeline per CTA (one CTA per SM, 256 threads):
+//   * raw slabs of 32 rows are copied into shared memory with cp.async,
+//     several slabs ahead (zero-filled past the CTA's last row);
+//   * all threads split each raw value x into TF32 parts x = hi + lo
+//     (hi = rna(x), lo = rna(x - hi)) and store them transposed into the
+//     K-major operand layout without swizzling: 8-row x 16-byte core
+//     matrices, 128 contiguous bytes each, core matrices 128 B apart along
+//     K (the slab's rows) and 1024 B apart along M / N (the block columns);
+//     the operand buffers are double-buffered, so the conversion of a slab
+//     overlaps the tensor-core work on the previous one;
+//   * one thread issues, per 8-row step of the slab, three kind::tf32 MMAs
+//     (hi.hi + hi.lo + lo.hi: products at FP32 accuracy) of shape
+//     M = 128 (columns of X, zero-padded) x N = ky rounded up to 16, and
+//     commits them to the buffer's mbarrier; the threads wait on that
+//     mbarrier before they overwrite the buffer two slabs later.
+// Every wait is bounded: a wait that runs out sets *err, and the CTA stops,
+// waits (bounded) for its copies and MMAs, frees its TMEM and returns.
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace vne {
+namespace {
+
+constexpr int kSlab = 32;                       // rows per slab (the contraction dimension)
+constexpr int kRawLd = 136;                     // padded raw row in floats (conflict-free column reads)
+constexpr int kRawFloats = kSlab * kRawLd;      // one raw slab of one block
+constexpr int kOpBytes = 128 * kSlab * 4;       // one TF32 operand slab: 128 rows x 32 K x 4 B
+constexpr uint32_t kLbo = 128;                  // byte step between core matrices along K
+constexpr uint32_t kSbo = (kSlab / 4) * 128;    // byte step between 8-row groups (1024)
+constexpr uint32_t kWaitPolls = 1u << 20;       // mbarrier polls before a wait is abandoned
+constexpr int kTmemCols = 128;                  // accumulator columns (N <= 128, FP32)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling:
+// start address, leading (K) and stride (M/N) byte offsets, all >> 4;
+// bits 46-47 hold the descriptor version (1), swizzle mode 0 (none).
+__device__ __forceinline__ uint64_t op_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((kLbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((kSbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::tf32: D = F32 (bits 4-5), A = B = TF32
+// (bits 7-9, 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitPolls; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <bool SAME>
+struct GramSmem {
+    static constexpr int kOps = SAME ? 2 : 4;     // per buffer: A hi, A lo (, B hi, B lo)
+    static constexpr int kStages = SAME ? 4 : 2;  // raw slabs in flight
+    static constexpr int kRawBlocks = SAME ? 1 : 2;
+    static constexpr int kOpRegion = 2 * kOps * kOpBytes;
+    static constexpr int kRawRegion = kStages * kRawBlocks * kRawFloats * 4;
+    static constexpr int kBytes = kOpRegion + kRawRegion + 32;  // + 2 mbarriers + TMEM address slot
+};
+
+// Split and transpose one raw slab (rows x columns, kRawLd stride) into the
+// K-major TF32 hi / lo operand buffers; columns >= k are written as zeros.
+__device__ __forceinline__ void convert_slab(const float* raw, int k, unsigned char* hi, unsigned char* lo) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int q = threadIdx.x + 256 * i;  // 128 rows of the operand x 8 groups of 4 slab rows
+        const int m = q & 127, kg = q >> 7;
+        uint4 h = make_uint4(0u, 0u, 0u, 0u), l = make_uint4(0u, 0u, 0u, 0u);
+        if (m < k) {
+            const float x0 = raw[(4 * kg + 0) * kRawLd + m], x1 = raw[(4 * kg + 1) * kRawLd + m];
+            const float x2 = raw[(4 * kg + 2) * kRawLd + m], x3 = raw[(4 * kg + 3) * kRawLd + m];
+            h.x = tf32_rna(x0);
+            h.y = tf32_rna(x1);
+            h.z = tf32_rna(x2);
+            h.w = tf32_rna(x3);
+            l.x = tf32_rna(x0 - __uint_as_float(h.x));
+            l.y = tf32_rna(x1 - __uint_as_float(h.y));
+            l.z = tf32_rna(x2 - __uint_as_float(h.z));
+            l.w = tf32_rna(x3 - __uint_as_float(h.w));
+        }
+        const uint32_t off = (uint32_t)(m >> 3) * kSbo + (uint32_t)kg * kLbo + (uint32_t)(m & 7) * 16;
+        *reinterpret_cast<uint4*>(hi + off) = h;
+        *reinterpret_cast<uint4*>(lo + off) = l;
+    }
+}
+
+template <int KS, bool SAME>
+__global__ void __launch_bounds__(256, 1)
+    k_gram_tc5(const float* __restrict__ X, int kx, const float* __restrict__ Y, int ky, int n, int rows_per_chunk,
+               double* __restrict__ part, int* __restrict__ err) {
+    using L = GramSmem<SAME>;
+    constexpr int V = KS / 4;  // 16-byte pieces per row of one panel
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* ops = smem;  // [buffer][A hi, A lo, B hi, B lo]
+    float* raw = reinterpret_cast<float*>(smem + L::kOpRegion);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::kOpRegion + L::kRawRegion);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chunk = blockIdx.x;
+    const int r_begin = chunk * rows_per_chunk;
+    const int r_end = min(n, r_begin + rows_per_chunk);
+    const int nslab = r_end > r_begin ? (r_end - r_begin + kSlab - 1) / kSlab : 0;
+    const int ky16 = (ky + 15) & ~15;
+    const int px = kx / KS, py = ky / KS;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    auto issue = [&](int s) {
+        if (s < nslab) {
+            const int rt = r_begin + s * kSlab;
+            float* rx = raw + (s % L::kStages) * L::kRawBlocks * kRawFloats;
+            const int nx = px * kSlab * V, ny = SAME ? 0 : py * kSlab * V;
+            for (int idx = tid; idx < nx + ny; idx += 256) {
+                const bool isx = idx < nx;
+                const int e = isx ? idx : idx - nx;
+                const int p = e / (kSlab * V), rem = e % (kSlab * V);
+                const int rl = rem / V, c = (rem % V) * 4;
+                const int r = rt + rl;
+                const bool in = r < r_end;
+                const float* src = (isx ? X : Y) + (size_t)p * n * KS + (size_t)(in ? r : r_begin) * KS + c;
+                float* dst = rx + (isx ? 0 : kRawFloats) + rl * kRawLd + p * KS + c;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                             "r"(in ? 16 : 0)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    const uint32_t idesc = idesc_tf32(128, ky16);
+    bool failed = false;
+    for (int s = 0; s < L::kStages - 1; s++) issue(s);
+    for (int s = 0; s < nslab; s++) {
+        issue(s + L::kStages - 1);  // into the stage converted in the previous iteration
+        asm volatile("cp.async.wait_group %0;" ::"n"(L::kStages - 1) : "memory");
+        const int b = s & 1;
+        // the MMAs of slab s - 2 read operand buffer b
+        const bool ready = s < 2 || mbar_wait(mbar + b, (uint32_t)((s - 2) >> 1) & 1u);
+        if (__syncthreads_or(!ready)) {  // also: slab s has landed for every thread's copies
+            failed = true;
+            break;
+        }
+        unsigned char* buf = ops + b * L::kOps * kOpBytes;
+        convert_slab(raw + (s % L::kStages) * L::kRawBlocks * kRawFloats, kx, buf, buf + kOpBytes);
+        if (!SAME) convert_slab(raw + (s % L::kStages) * L::kRawBlocks * kRawFloats + kRawFloats, ky,
+                                buf + 2 * kOpBytes, buf + 3 * kOpBytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(buf), a_lo = a_hi + kOpBytes;
+            const uint32_t b_hi = SAME ? a_hi : a_hi + 2 * kOpBytes, b_lo = b_hi + kOpBytes;
+#pragma unroll
+            for (int t = 0; t < kSlab / 8; t++) {
+                const uint32_t o = (uint32_t)t * 2 * kLbo;  // two core matrices of K per MMA
+                mma_tf32(tmem, op_desc(a_hi + o), op_desc(b_hi + o), idesc, (s > 0 || t > 0) ? 1u : 0u);
+                mma_tf32(tmem, op_desc(a_hi + o), op_desc(b_lo + o), idesc, 1u);
+                mma_tf32(tmem, op_desc(a_lo + o), op_desc(b_hi + o), idesc, 1u);
+            }
+            mma_commit(mbar + b);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (nslab > 0 && !failed) {
+        const int sl = nslab - 1;
+        const bool done = mbar_wait(mbar + (sl & 1), (uint32_t)(sl >> 1) & 1u);
+        failed = __syncthreads_or(!done);
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(err, 1);
+        // let the MMAs already issued finish before the TMEM is released
+        if (nslab > 0) {
+            mbar_wait(mbar, 0u);  // bounded; the outcome is already an error
+            mbar_wait(mbar + 1, 0u);
+        }
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quarter = warp & 3;           // TMEM lanes 32 * quarter .. + 31
+        const int row = quarter * 32 + lane;    // output row = column of X
+        double* dst = part + (size_t)chunk * kx * ky + (size_t)row * ky;
+#pragma unroll 1
+        for (int i = 0; i < 2; i++) {
+            const int c0 = ((warp >> 2) + 2 * i) * 32;
+            if (c0 >= ky16) continue;  // warp-uniform
+            uint32_t v[32];
+            if (nslab > 0) {
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] = 0u;
+            }
+            if (row < kx) {
+#pragma unroll
+                for (int j = 0; j < 32; j++)
+                    if (c0 + j < ky) dst[c0 + j] = (double)__uint_as_float(v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+template <int KS, bool SAME>
+cudaError_t gram_tc5_launch(const float* X, int kx, const float* Y, int ky, int n, int rpc, int chunks, double* part,
+                            int* err, cudaStream_t st) {
+    const int smem = GramSmem<SAME>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc5<KS, SAME>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc5<KS, SAME><<<chunks, 256, smem, st>>>(X, kx, Y, ky, n, rpc, part, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int ks, int n, double* part, int max_chunks,
+                            int* err, int* chunks_out, cudaStream_t st) {
+    if (kx < 1 || ky < 1 || kx > 128 || ky > 128 || n < 1 || max_chunks < 1 || !err || !chunks_out)
+        return cudaErrorInvalidValue;
+    if ((ks != 8 && ks != 16 && ks != 32) || kx % ks || ky % ks) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM, each over an equal share of the rows (a multiple of the slab)
+    const int want = std::max(1, std::min(max_chunks, sms));
+    int rpc = (n + want - 1) / want;
+    rpc = ((rpc + kSlab - 1) / kSlab) * kSlab;
+    const int chunks = (n + rpc - 1) / rpc;
+    *chunks_out = chunks;
+    const bool same = (X == Y) && (kx == ky);
+#define VNE_TC5(KSV)                                                                                      \
+    if (ks == KSV)                                                                                        \
+        return same ? gram_tc5_launch<KSV, true>(X, kx, Y, ky, n, rpc, chunks, part, err, st)             \
+                    : gram_tc5_launch<KSV, false>(X, kx, Y, ky, n, rpc, chunks, part, err, st);
+    VNE_TC5(8)
+    VNE_TC5(16)
+    VNE_TC5(32)
+#undef VNE_TC5
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace vne

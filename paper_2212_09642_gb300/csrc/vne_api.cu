@@ -1674,7 +1674,9 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     double* gpart = ws_get_t<double>(ctx, "gram.part", (size_t)nch * Kp * std::max(Kp, 128));
     double* G1 = ws_get_t<double>(ctx, "G1", (size_t)Kp * Kp);
     double* Minv = ws_get_t<double>(ctx, "Minv", (size_t)Kp * Kp);
-    int* drank = ws_get_t<int>(ctx, "rank", 2);
+    int* drank = ws_get_t<int>(ctx, "rank", 3);  // two ranks + the tensor-core Gram's wait flag
+    int* gerr = drank + 2;
+    VNE_TRY_CUDA(ctx, cudaMemsetAsync(gerr, 0, sizeof(int), st));
     T* Q1 = ws_get_t<T>(ctx, "Q1", blk);
     // Q and (I - Q Q^T) G share one buffer: Q in block columns [0, Kp), the
     // projected Hutchinson vectors in [Kp, Kp + Kg), so one Lanczos block
@@ -1684,10 +1686,10 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     T* QG = ws_get_t<T>(ctx, "QG", (size_t)(Kp + Kg) * n);
     T* Q = QG;
     const double tol = M->fp64 ? 1e-13 : 1e-5;
-    VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, st));
+    VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, gerr, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Y, Kp, Minv, Kp, nullptr, Q1, ks, n, 1.0, st));
-    VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, st));
+    VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, gerr, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, st));
     ctx->launches += 10;  // 2 x (gram + reduce + factor + apply)
@@ -1721,13 +1723,14 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
         VNE_TRY_CUDA(ctx, launch_start<T>(spp, ks, Kg / ks, st));
         double* C = ws_get_t<double>(ctx, "QtG", (size_t)Kp * Kg);
         double* gpart2 = ws_get_t<double>(ctx, "gram.part2", (size_t)nch * Kp * Kg);
-        VNE_TRY_CUDA(ctx, launch_gram<T>(Q, Kp, Gr, Kg, ks, n, gpart2, nch, C, st));
+        VNE_TRY_CUDA(ctx, launch_gram<T>(Q, Kp, Gr, Kg, ks, n, gpart2, nch, C, gerr, st));
         VNE_TRY_CUDA(ctx, launch_apply<T>(Q, Kp, C, Kg, Gr, Gp, ks, n, -1.0, st));
         ctx->launches += 4;
     }
-    int hr[2] = {0, 0};
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hr[3] = {0, 0, 0};
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    VNE_REQUIRE(ctx, hr[2] == 0, VNE_EDEVICE, "tensor-core Gram: a bounded wait ran out");
     const int r = std::min(hr[0], hr[1]);
     // 3. all N_r + N_H quadratic forms in one Lanczos block
     double low = 0.0, resid = 0.0;
@@ -2213,6 +2216,27 @@ extern "C" vne_status vne_spmm(vne_matrix* M, const void* X, void* Y, int32_t k)
         VNE_TRY_CUDA(ctx, launch_spmm_plain<float>(M->d_rowptr, M->d_col, (const float*)M->d_vals, (int)M->n, k,
                                                    M->d_node_id, M->scale, (const float*)X, (float*)Y, ctx->stream));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_block_gram(vne_ctx* ctx, const float* X, int32_t kx, const float* Y, int32_t ky, int32_t ks,
+                                     int64_t n, double* C) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, X && Y && C && n >= 1 && n < INT32_MAX && kx >= 1 && ky >= 1 && kx <= 128 && ky <= 128 &&
+                         (ks == 8 || ks == 16 || ks == 32) && kx % ks == 0 && ky % ks == 0,
+                VNE_EINVAL, "bad arguments to vne_block_gram");
+    const int nch = std::max(1, std::min(4 * ctx->sm_count, (int)((n + 63) / 64)));
+    double* part = ws_get_t<double>(ctx, "bg.part", (size_t)nch * kx * ky);
+    double* dC = ws_get_t<double>(ctx, "bg.C", (size_t)kx * ky);
+    int* err = ws_get_t<int>(ctx, "bg.err", 1, true);
+    VNE_TRY_CUDA(ctx, launch_gram<float>(X, kx, Y, ky, ks, (int)n, part, nch, dC, err, ctx->stream));
+    int herr = 0;
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(C, dC, (size_t)kx * ky * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_REQUIRE(ctx, herr == 0, VNE_EDEVICE, "tensor-core Gram: a bounded wait ran out");
     VNE_API_END(ctx)
 }
 

@@ -1,0 +1,47 @@
+"""The tcgen05 Gram C = X^T Y of the Hutch++ sketch (Section 3.2) against
+the FP64 product of the same FP32 blocks, elementwise: the TF32 three-product
+split and FP32 accumulation within a CTA keep each entry within a small
+multiple of the FP32 unit roundoff of sum_i |x_i| |y_i|."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2212_09642_gb300 import vne
+
+pytestmark = pytest.mark.gpu
+
+
+def panel_major(M, ks):
+    """[n, k] -> device float32 [k / ks][n][ks]."""
+    n, k = M.shape
+    P = np.ascontiguousarray(M.reshape(n, k // ks, ks).transpose(1, 0, 2)).astype(np.float32)
+    return torch.from_numpy(P).cuda()
+
+
+@pytest.mark.parametrize("n,kx,ky,ks,same", [
+    (100_003, 112, 112, 16, True),   # the sketch's Y^T Y shape, ragged tail
+    (5_000, 128, 128, 32, True),     # full 128 x 128 tile
+    (77_777, 112, 112, 16, False),   # Q^T G
+    (40_000, 16, 48, 8, False),      # narrow, N not a multiple of the output tile
+    (33, 32, 16, 16, False),         # fewer rows than one slab per CTA
+    (1, 8, 8, 8, True),              # a single row
+])
+def test_block_gram_tcgen05(vctx, n, kx, ky, ks, same):
+    rs = np.random.default_rng(n + kx + ky)
+    X = rs.standard_normal((n, kx)).astype(np.float32)
+    Y = X if same else rs.standard_normal((n, ky)).astype(np.float32)
+    dX = panel_major(X, ks)
+    dY = dX if same else panel_major(Y, ks)
+    C = vne.vne_block_gram(vctx, dX, kx, dY, ky, ks, n)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    ref = X64.T @ Y64
+    scale = np.abs(X64).T @ np.abs(Y64)
+    err = np.abs(C - ref)
+    assert np.all(err <= 2e-5 * scale + 1e-30), float(np.max(err / (scale + 1e-300)))
+
+
+def test_block_gram_rejects_bad_sizes(vctx):
+    d = torch.zeros((2, 10, 16), dtype=torch.float32, device="cuda")
+    for kx, ky, ks in [(0, 16, 16), (144, 16, 16), (16, 12, 16), (16, 16, 4)]:
+        with pytest.raises(vne.VneError):
+            vne.vne_block_gram(vctx, d, kx, d, ky, ks, 10)
