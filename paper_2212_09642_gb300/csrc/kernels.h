@@ -253,15 +253,18 @@ template <typename T>
 cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks,
                         double* C, int* err, cudaStream_t);
 // Per-CTA partial Grams of the tcgen05 kernel: part [chunks][kx][ky], at
-// most max_chunks (one CTA per SM); *chunks_out = the CTAs launched.
+// most max_chunks (one CTA per SM); *chunks_out = the CTAs launched;
+// *sym_out = 1 when the partials hold E with X^T X = E + E^T (X == Y).
 cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int ks, int n, double* part,
-                            int max_chunks, int* err, int* chunks_out, cudaStream_t st);
+                            int max_chunks, int* err, int* chunks_out, int* sym_out, cudaStream_t st);
 // Out = (In2 ? In2 : 0) + coef * In * M, M double [kin][kout] row-major; panel-major blocks.
 template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
                          double coef, cudaStream_t);
 // Pivoted Cholesky of a k x k SPD matrix G (FP64) with rank cut-off tol * max diag.
 // Writes Minv [k][k] (rows permuted: Q = Y Minv spans range(Y)) and rank.
-cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, cudaStream_t);
+// work: k * k + k doubles (R and 1 / R_jj), piv: k ints (device).
+cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, double* work,
+                                  int* piv, cudaStream_t);
 
 }  // namespace vne

@@ -1257,17 +1257,28 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int 
     C[idx] = s;
 }
 
+// C = sum over chunks of E + E^T (k x k partials of a symmetric Gram).
+__global__ void k_gram_reduce_sym(const double* __restrict__ part, int nchunks, int k, double* __restrict__ C) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= k * k) return;
+    const int a = idx / k, b = idx % k, t = b * k + a;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += part[(size_t)c * k * k + idx] + part[(size_t)c * k * k + t];
+    C[idx] = s;
+}
+
 template <typename T>
 cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, double* part, int nchunks, double* C,
                         int* err, cudaStream_t st) {
     if (kx <= 0 || ky <= 0) return cudaSuccess;
     if (sizeof(T) == 4 && err && kx <= 128 && ky <= 128 && (ks == 8 || ks == 16 || ks == 32)) {
-        int chunks = 0;
+        int chunks = 0, sym = 0;
         cudaError_t e = launch_gram_tc5(reinterpret_cast<const float*>(X), kx, reinterpret_cast<const float*>(Y), ky,
-                                        ks, n, part, nchunks, err, &chunks, st);
+                                        ks, n, part, nchunks, err, &chunks, &sym, st);
         if (e != cudaSuccess) return e;
         const int total = kx * ky;
-        k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
+        if (sym) k_gram_reduce_sym<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, kx, C);
+        else k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
         return cudaGetLastError();
     }
     int tiles_x = (kx + 63) / 64, tiles_y = (ky + 63) / 64;
@@ -1508,17 +1519,25 @@ cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const 
 }
 
 // ---------------------------------------------------------------------------
-// Pivoted Cholesky G = P R^T R P^T (one CTA, FP64).  Stops when the largest
-// remaining pivot is <= tol * max diag(G); rank r = pivots taken.  Writes
-// Minv with Minv[piv[i]][c] = (R^{-1})[i][c] for i, c < r, zero elsewhere, so
-// that Y Minv has orthonormal columns in exact arithmetic.
-__global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, double* __restrict__ Minv,
-                          int* __restrict__ rank_out) {
+// Pivoted Cholesky G = P R^T R P^T (FP64), in two kernels: the factor (one
+// CTA) and the triangular inverse (a warp per column).  Stops when the
+// largest remaining pivot is <= tol * max diag(G); rank r = pivots taken.
+// Writes Minv with Minv[piv[i]][c] = (R^{-1})[i][c] for i, c < r, zero
+// elsewhere, so that Y Minv has orthonormal columns in exact arithmetic.
+// Pivoted Cholesky factor of the FP64 Gram (one CTA): R upper triangular
+// with P^T G P = R^T R, the pivots, 1 / R_jj and the numerical rank (the
+// first pivot below tol * max diag stops the factorisation).  FP64 runs at a
+// small fraction of the FP32 rate on this part, so a step costs one square
+// root and one reciprocal (thread 0) and the row is scaled by multiplication.
+// Output R: work[0 .. k*k) row-major (upper triangle), 1 / R_jj:
+// work[k*k .. k*k + k), pivots: piv[0 .. k).
+__global__ void k_chol_factor(const double* __restrict__ G, int k, double tol, double* __restrict__ work,
+                              int* __restrict__ piv_out, int* __restrict__ rank_out) {
     extern __shared__ double A[];  // k x (k + 1): odd row stride against bank conflicts
     const int ld = k + 1;
     __shared__ int piv[128];
     __shared__ int s_p, s_rank;
-    __shared__ double s_max0;
+    __shared__ double s_max0, s_rinv;
     // symmetric part of G (the Gram partial sums of (a, b) and (b, a) may
     // round differently)
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
@@ -1580,10 +1599,15 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
             }
             __syncthreads();
         }
-        const double rjj = sqrt(A[j * ld + j]);
+        if (threadIdx.x == 0) {
+            const double rjj = sqrt(A[j * ld + j]);
+            A[j * ld + j] = rjj;
+            s_rinv = 1.0 / rjj;
+        }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[j * ld + i] /= rjj;
-        if (threadIdx.x == 0) A[j * ld + j] = rjj;
+        const double rinv = s_rinv;
+        for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[j * ld + i] *= rinv;
+        if (threadIdx.x == 0) work[(size_t)k * k + j] = rinv;
         __syncthreads();
         // rank-1 update of the trailing block: the upper triangle (a warp per
         // row), mirrored into the lower one for later pivot swaps
@@ -1593,7 +1617,7 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
             const int ga = j + 1 + a;
             const double la = A[j * ld + ga];
             for (int gb = ga + lane; gb < k; gb += 32) {
-                const double v = A[ga * ld + gb] - la * A[j * ld + gb];
+                const double v = fma(-la, A[j * ld + gb], A[ga * ld + gb]);
                 A[ga * ld + gb] = v;
                 A[gb * ld + ga] = v;
             }
@@ -1602,36 +1626,61 @@ __global__ void k_chol_qr(const double* __restrict__ G, int k, double tol, doubl
     }
     __syncthreads();
     const int r = s_rank;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) Minv[idx] = 0.0;
-    __syncthreads();
-    // R^{-1} column by column (back substitution), one thread per column; the
-    // inner products use four partial sums to shorten the dependent chain
-    for (int c = threadIdx.x; c < r; c += blockDim.x) {
-        double x[128];
-        x[c] = 1.0 / A[c * ld + c];
-        for (int i = c - 1; i >= 0; i--) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int l = i + 1;
-            for (; l + 3 <= c; l += 4) {
-                s0 = fma(A[i * ld + l], x[l], s0);
-                s1 = fma(A[i * ld + l + 1], x[l + 1], s1);
-                s2 = fma(A[i * ld + l + 2], x[l + 2], s2);
-                s3 = fma(A[i * ld + l + 3], x[l + 3], s3);
-            }
-            for (; l <= c; l++) s0 = fma(A[i * ld + l], x[l], s0);
-            x[i] = -((s0 + s1) + (s2 + s3)) / A[i * ld + i];
-        }
-        for (int i = 0; i <= c; i++) Minv[(size_t)piv[i] * k + c] = x[i];
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+        const int a = idx / k, b = idx % k;
+        work[idx] = (a < r && b >= a) ? A[a * ld + b] : 0.0;
     }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) piv_out[i] = piv[i];
     if (threadIdx.x == 0) *rank_out = r;
 }
 
-cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, cudaStream_t st) {
+// Minv = P R^{-1} (rows permuted back), zero beyond the rank: column c of
+// R^{-1} by back substitution, x_c = 1 / R_cc and, for i = c - 1 .. 0,
+// x_i = -(sum_{l = i+1..c} R_il x_l) / R_ii.  One warp per column, R staged
+// in shared memory, the inner products lane-parallel with a butterfly sum;
+// the columns are spread over the SMs (a column's chain is serial).
+__global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ work, int k, const int* __restrict__ piv,
+                                                 const int* __restrict__ rank, double* __restrict__ Minv) {
+    extern __shared__ double R[];  // rows 0 .. c_hi of R, row stride k + 1
+    __shared__ double xs[8][128];
+    const int ld = k + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = *rank;
+    const int c_hi = min(k - 1, (int)blockIdx.x * 8 + 7);  // last column of this CTA
+    for (int idx = threadIdx.x; idx < (c_hi + 1) * k; idx += blockDim.x) {
+        const int a = idx / k, b = idx % k;
+        R[a * ld + b] = work[idx];
+    }
+    __syncthreads();
+    const int c = blockIdx.x * 8 + warp;
+    if (c >= k) return;
+    const double* rinv = work + (size_t)k * k;
+    double* x = xs[warp];
+    if (c < r) {
+        if (lane == 0) x[c] = rinv[c];
+        __syncwarp();
+        for (int i = c - 1; i >= 0; i--) {
+            double s = 0.0;
+            for (int l = i + 1 + lane; l <= c; l += 32) s = fma(R[i * ld + l], x[l], s);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) x[i] = -s * rinv[i];
+            __syncwarp();
+        }
+    }
+    for (int i = lane; i < k; i += 32) Minv[(size_t)piv[i] * k + c] = (c < r && i <= c) ? x[i] : 0.0;
+}
+
+cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, double* work,
+                                  int* piv, cudaStream_t st) {
     if (k > 128 || k <= 0) return cudaErrorInvalidValue;
-    size_t smem = (size_t)k * (k + 1) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_chol_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)k * (k + 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_chol_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chol_qr<<<1, 256, smem, st>>>(G, k, tol, Minv, rank);
+    e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_chol_factor<<<1, 256, smem, st>>>(G, k, tol, work, piv, rank);
+    k_tri_inv<<<(k + 7) / 8, 256, smem, st>>>(work, k, piv, rank, Minv);
     return cudaGetLastError();
 }
 

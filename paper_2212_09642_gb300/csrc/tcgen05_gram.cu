@@ -18,10 +18,17 @@
 //     the operand buffers are double-buffered, so the conversion of a slab
 //     overlaps the tensor-core work on the previous one;
 //   * one thread issues, per 8-row step of the slab, three kind::tf32 MMAs
-//     (hi.hi + hi.lo + lo.hi: products at FP32 accuracy) of shape
+//     (hi.hi + hi.lo + lo.hi: products at FP32 accuracy; for the Gram of a
+//     block with itself two, E = (hi / 2) hi^T + hi lo^T, and the caller's
+//     reduction forms E + E^T) of shape
 //     M = 128 (columns of X, zero-padded) x N = ky rounded up to 16, and
 //     commits them to the buffer's mbarrier; the threads wait on that
-//     mbarrier before they overwrite the buffer two slabs later.
+//     mbarrier before they overwrite the buffer two slabs later;
+//   * the tensor core's FP32 accumulation drifts over long chains (about
+//     7e-5 of sum |x_i y_i| after 2,500 accumulations), so the MMAs of 8
+//     slabs go into one of two TMEM accumulators, and once they are done the
+//     threads add that accumulator into FP32 registers (tcgen05.ld) while
+//     the next group runs into the other one.
 // Every wait is bounded: a wait that runs out sets *err, and the CTA stops,
 // waits (bounded) for its copies and MMAs, frees its TMEM and returns.
 #include <algorithm>
@@ -33,13 +40,14 @@ namespace vne {
 namespace {
 
 constexpr int kSlab = 32;                       // rows per slab (the contraction dimension)
-constexpr int kRawLd = 136;                     // padded raw row in floats (conflict-free column reads)
+constexpr int kRawLd = 128;                     // raw row in floats (a warp reads 32 consecutive columns of a row)
 constexpr int kRawFloats = kSlab * kRawLd;      // one raw slab of one block
 constexpr int kOpBytes = 128 * kSlab * 4;       // one TF32 operand slab: 128 rows x 32 K x 4 B
 constexpr uint32_t kLbo = 128;                  // byte step between core matrices along K
 constexpr uint32_t kSbo = (kSlab / 4) * 128;    // byte step between 8-row groups (1024)
 constexpr uint32_t kWaitPolls = 1u << 20;       // mbarrier polls before a wait is abandoned
-constexpr int kTmemCols = 128;                  // accumulator columns (N <= 128, FP32)
+constexpr int kTmemCols = 256;                  // two accumulators of 128 FP32 columns (N <= 128)
+constexpr int kGroup = 8;                       // slabs accumulated in TMEM before a flush to registers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -108,8 +116,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 template <bool SAME>
 struct GramSmem {
-    static constexpr int kOps = SAME ? 2 : 4;     // per buffer: A hi, A lo (, B hi, B lo)
-    static constexpr int kStages = SAME ? 4 : 2;  // raw slabs in flight
+    static constexpr int kOps = SAME ? 3 : 4;     // per buffer: A hi, A lo, then hi / 2 or B hi, B lo
+    static constexpr int kStages = SAME ? 6 : 3;  // raw slab buffers (kStages - 1 slabs in flight)
     static constexpr int kRawBlocks = SAME ? 1 : 2;
     static constexpr int kOpRegion = 2 * kOps * kOpBytes;
     static constexpr int kRawRegion = kStages * kRawBlocks * kRawFloats * 4;
@@ -117,8 +125,10 @@ struct GramSmem {
 };
 
 // Split and transpose one raw slab (rows x columns, kRawLd stride) into the
-// K-major TF32 hi / lo operand buffers; columns >= k are written as zeros.
-__device__ __forceinline__ void convert_slab(const float* raw, int k, unsigned char* hi, unsigned char* lo) {
+// K-major TF32 hi / lo operand buffers (and hi / 2, exact, when half is
+// given); columns >= k are written as zeros.
+__device__ __forceinline__ void convert_slab(const float* raw, int k, unsigned char* hi, unsigned char* lo,
+                                             unsigned char* half) {
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int q = threadIdx.x + 256 * i;  // 128 rows of the operand x 8 groups of 4 slab rows
@@ -139,6 +149,10 @@ __device__ __forceinline__ void convert_slab(const float* raw, int k, unsigned c
         const uint32_t off = (uint32_t)(m >> 3) * kSbo + (uint32_t)kg * kLbo + (uint32_t)(m & 7) * 16;
         *reinterpret_cast<uint4*>(hi + off) = h;
         *reinterpret_cast<uint4*>(lo + off) = l;
+        if (half)
+            *reinterpret_cast<float4*>(half + off) =
+                make_float4(0.5f * __uint_as_float(h.x), 0.5f * __uint_as_float(h.y), 0.5f * __uint_as_float(h.z),
+                            0.5f * __uint_as_float(h.w));
     }
 }
 
@@ -201,11 +215,34 @@ __global__ void __launch_bounds__(256, 1)
     };
 
     const uint32_t idesc = idesc_tf32(128, ky16);
+    // this warp's share of the output: TMEM lanes 32 * quarter .. + 31 (one
+    // output row per lane), column blocks c0 = 32 * ((warp >> 2) + 2 i)
+    const int quarter = warp & 3;
+    float acc[2][32];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 32; j++) acc[i][j] = 0.f;
+    auto flush = [&](int g) {  // add accumulator g & 1 (all its MMAs done) into acc
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int c0 = ((warp >> 2) + 2 * i) * 32;
+            if (c0 < ky16) {  // warp-uniform
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((g & 1) * 128 + c0), v);
+#pragma unroll
+                for (int j = 0; j < 32; j++) acc[i][j] += __uint_as_float(v[j]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+    int next_flush = 0;  // first group not yet added into acc
     bool failed = false;
     for (int s = 0; s < L::kStages - 1; s++) issue(s);
     for (int s = 0; s < nslab; s++) {
-        issue(s + L::kStages - 1);  // into the stage converted in the previous iteration
-        asm volatile("cp.async.wait_group %0;" ::"n"(L::kStages - 1) : "memory");
+        // slabs s .. s + kStages - 2 are in flight: wait for slab s
+        asm volatile("cp.async.wait_group %0;" ::"n"(L::kStages - 2) : "memory");
         const int b = s & 1;
         // the MMAs of slab s - 2 read operand buffer b
         const bool ready = s < 2 || mbar_wait(mbar + b, (uint32_t)((s - 2) >> 1) & 1u);
@@ -213,25 +250,41 @@ __global__ void __launch_bounds__(256, 1)
             failed = true;
             break;
         }
+        // the groups whose last slab is <= s - 2 are complete
+        while (next_flush < (s - 1) / kGroup) flush(next_flush++);
         unsigned char* buf = ops + b * L::kOps * kOpBytes;
-        convert_slab(raw + (s % L::kStages) * L::kRawBlocks * kRawFloats, kx, buf, buf + kOpBytes);
+        convert_slab(raw + (s % L::kStages) * L::kRawBlocks * kRawFloats, kx, buf, buf + kOpBytes,
+                     SAME ? buf + 2 * kOpBytes : nullptr);
         if (!SAME) convert_slab(raw + (s % L::kStages) * L::kRawBlocks * kRawFloats + kRawFloats, ky,
-                                buf + 2 * kOpBytes, buf + 3 * kOpBytes);
+                                buf + 2 * kOpBytes, buf + 3 * kOpBytes, nullptr);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(buf), a_lo = a_hi + kOpBytes;
-            const uint32_t b_hi = SAME ? a_hi : a_hi + 2 * kOpBytes, b_lo = b_hi + kOpBytes;
+            const uint32_t d = tmem + (uint32_t)(((s / kGroup) & 1) * 128);
+            const bool first = (s % kGroup) == 0;
 #pragma unroll
             for (int t = 0; t < kSlab / 8; t++) {
                 const uint32_t o = (uint32_t)t * 2 * kLbo;  // two core matrices of K per MMA
-                mma_tf32(tmem, op_desc(a_hi + o), op_desc(b_hi + o), idesc, (s > 0 || t > 0) ? 1u : 0u);
-                mma_tf32(tmem, op_desc(a_hi + o), op_desc(b_lo + o), idesc, 1u);
-                mma_tf32(tmem, op_desc(a_lo + o), op_desc(b_hi + o), idesc, 1u);
+                if (SAME) {
+                    // E = (H / 2) H^T + H L^T, so that E + E^T = H H^T + H L^T + L H^T
+                    const uint32_t a_half = a_hi + 2 * kOpBytes;
+                    mma_tf32(d, op_desc(a_half + o), op_desc(a_hi + o), idesc, (!first || t > 0) ? 1u : 0u);
+                    mma_tf32(d, op_desc(a_hi + o), op_desc(a_lo + o), idesc, 1u);
+                } else {
+                    const uint32_t b_hi = a_hi + 2 * kOpBytes, b_lo = b_hi + kOpBytes;
+                    mma_tf32(d, op_desc(a_hi + o), op_desc(b_hi + o), idesc, (!first || t > 0) ? 1u : 0u);
+                    mma_tf32(d, op_desc(a_hi + o), op_desc(b_lo + o), idesc, 1u);
+                    mma_tf32(d, op_desc(a_lo + o), op_desc(b_hi + o), idesc, 1u);
+                }
             }
             mma_commit(mbar + b);
         }
+        // the next prefetch goes into the stage converted in the previous
+        // iteration; it is issued after the proxy fence above, so that the
+        // fence does not wait for it
+        issue(s + L::kStages - 1);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (nslab > 0 && !failed) {
@@ -247,25 +300,17 @@ __global__ void __launch_bounds__(256, 1)
             mbar_wait(mbar + 1, 0u);
         }
     } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int quarter = warp & 3;           // TMEM lanes 32 * quarter .. + 31
-        const int row = quarter * 32 + lane;    // output row = column of X
+        const int ngroups = (nslab + kGroup - 1) / kGroup;
+        while (next_flush < ngroups) flush(next_flush++);
+        const int row = quarter * 32 + lane;  // output row = column of X
         double* dst = part + (size_t)chunk * kx * ky + (size_t)row * ky;
-#pragma unroll 1
+#pragma unroll
         for (int i = 0; i < 2; i++) {
             const int c0 = ((warp >> 2) + 2 * i) * 32;
-            if (c0 >= ky16) continue;  // warp-uniform
-            uint32_t v[32];
-            if (nslab > 0) {
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; j++) v[j] = 0u;
-            }
-            if (row < kx) {
+            if (row < kx && c0 < ky16) {
 #pragma unroll
                 for (int j = 0; j < 32; j++)
-                    if (c0 + j < ky) dst[c0 + j] = (double)__uint_as_float(v[j]);
+                    if (c0 + j < ky) dst[c0 + j] = (double)acc[i][j];
             }
         }
     }
@@ -290,8 +335,8 @@ cudaError_t gram_tc5_launch(const float* X, int kx, const float* Y, int ky, int 
 }  // namespace
 
 cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int ks, int n, double* part, int max_chunks,
-                            int* err, int* chunks_out, cudaStream_t st) {
-    if (kx < 1 || ky < 1 || kx > 128 || ky > 128 || n < 1 || max_chunks < 1 || !err || !chunks_out)
+                            int* err, int* chunks_out, int* sym_out, cudaStream_t st) {
+    if (kx < 1 || ky < 1 || kx > 128 || ky > 128 || n < 1 || max_chunks < 1 || !err || !chunks_out || !sym_out)
         return cudaErrorInvalidValue;
     if ((ks != 8 && ks != 16 && ks != 32) || kx % ks || ky % ks) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
@@ -305,6 +350,7 @@ cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int 
     const int chunks = (n + rpc - 1) / rpc;
     *chunks_out = chunks;
     const bool same = (X == Y) && (kx == ky);
+    *sym_out = same ? 1 : 0;  // the partials of a block with itself hold E, the Gram is E + E^T
 #define VNE_TC5(KSV)                                                                                      \
     if (ks == KSV)                                                                                        \
         return same ? gram_tc5_launch<KSV, true>(X, kx, Y, ky, n, rpc, chunks, part, err, st)             \

@@ -1676,6 +1676,8 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     double* Minv = ws_get_t<double>(ctx, "Minv", (size_t)Kp * Kp);
     int* drank = ws_get_t<int>(ctx, "rank", 3);  // two ranks + the tensor-core Gram's wait flag
     int* gerr = drank + 2;
+    double* cwork = ws_get_t<double>(ctx, "chol.work", (size_t)Kp * Kp + Kp);
+    int* cpiv = ws_get_t<int>(ctx, "chol.piv", Kp);
     VNE_TRY_CUDA(ctx, cudaMemsetAsync(gerr, 0, sizeof(int), st));
     T* Q1 = ws_get_t<T>(ctx, "Q1", blk);
     // Q and (I - Q Q^T) G share one buffer: Q in block columns [0, Kp), the
@@ -1687,12 +1689,12 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     T* Q = QG;
     const double tol = M->fp64 ? 1e-13 : 1e-5;
     VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, gerr, st));
-    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, st));
+    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, cwork, cpiv, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Y, Kp, Minv, Kp, nullptr, Q1, ks, n, 1.0, st));
     VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, gerr, st));
-    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, st));
+    VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, cwork, cpiv, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, st));
-    ctx->launches += 10;  // 2 x (gram + reduce + factor + apply)
+    ctx->launches += 12;  // 2 x (gram + reduce + factor + inverse + apply)
     if (Kg > 0) {
         // G (Rademacher columns N_r..N_r+N_H-1), then G' = G - Q (Q^T G)
         const size_t gblk = (size_t)Kg * n;

@@ -19,7 +19,8 @@ def panel_major(M, ks):
 
 
 @pytest.mark.parametrize("n,kx,ky,ks,same", [
-    (100_003, 112, 112, 16, True),   # the sketch's Y^T Y shape, ragged tail
+    (1_000_000, 112, 112, 16, True), # the headline sketch's Y^T Y (n = 10^6, N_r = 100 in 7 panels)
+    (100_003, 112, 112, 16, True),   # the same shape, ragged tail
     (5_000, 128, 128, 32, True),     # full 128 x 128 tile
     (77_777, 112, 112, 16, False),   # Q^T G
     (40_000, 16, 48, 8, False),      # narrow, N not a multiple of the output tile
