@@ -168,47 +168,117 @@ struct RowSum {
     __device__ __forceinline__ double total() const { return acc + (double)part; }
 };
 
+// Four consecutive entries of one row of a panel (16-byte aligned: the
+// column offset is a multiple of 4 and a panel row holds KS >= 4 entries).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+    } else {
+        const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+        v[0] = x.x, v[1] = x.y, v[2] = y.x, v[3] = y.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// Rademacher entries of four block columns for one tile: key_j = (probe
+// column << 32) ^ seed, so that the hash input ((col << 32) | node) ^ seed
+// is key_j ^ node (the node id occupies the low 32 bits).
+struct RadQuad {
+    uint64_t key[4];
+    bool live[4];
+    __device__ __forceinline__ RadQuad(const StartSource& S, int seg, int gc0) {
+        const uint64_t sd = S.seg_seed ? S.seg_seed[seg] : S.seed_mixed;
+        const int cb = S.seg_seed ? S.seg_col0[seg] : S.col_begin;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            live[j] = gc0 + j < S.ncols;
+            key[j] = ((uint64_t)(cb + gc0 + j) << 32) ^ sd;
+        }
+    }
+    // the four entries of node id; neg[j] counts the -1 entries of live columns
+    template <typename T>
+    __device__ __forceinline__ void row(uint32_t id, T (&v)[4], int (&neg)[4]) const {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint64_t h = mix64((key[j] ^ (uint64_t)id) + 0x9E3779B97F4A7C15ULL);
+            const int sgn = (int)(h >> 63);
+            neg[j] += live[j] ? sgn : 0;
+            v[j] = live[j] ? (sgn ? (T)-1 : (T)1) : (T)0;
+        }
+    }
+};
+
+// Per-column totals of a CTA: each thread holds four columns' partial sums;
+// sum them over the threads of the same columns in a fixed order and write
+// the CTA's partial for the segment reduction.
+template <int KS>
+__device__ __forceinline__ void cta_column_partials(const double (&sum)[4], int rsub, int c0, double* part_out) {
+    constexpr int RPP = VNE_THREADS / (KS / 4);
+    __shared__ double red[RPP][KS];
+#pragma unroll
+    for (int j = 0; j < 4; j++) red[rsub][c0 + j] = sum[j];
+    __syncthreads();
+    if (threadIdx.x < KS) {
+        double s = 0.0;
+        for (int q = 0; q < RPP; q++) s += red[q][threadIdx.x];
+        part_out[threadIdx.x] = s;
+    }
+}
+
 // Pass 1: column sums per segment -> mean (only when desingularising); the
 // source values are stored in w_1 on the way, so pass 2 reads them instead of
-// generating them again (the counter-based probes cost more integer work
-// than a read and a write of the block).
+// generating them again.  A thread covers four consecutive columns of a row
+// (16-byte stores).  Rademacher sources take a dedicated path: four hashes
+// per row and integer counts of the -1 entries, so the column sums are exact
+// (as the FP32 partial sums of +-1 entries are).
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const SegInfo sg = p.seg[t.seg];
-    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
-    constexpr int RPI = VNE_THREADS / KS;
-    const int gc = panel * KS + c;
+    constexpr int QPR = KS / 4, RPP = VNE_THREADS / QPR;
+    const int c0 = (threadIdx.x % QPR) * 4, rsub = threadIdx.x / QPR;
+    const int gc0 = panel * KS + c0;
     T* out = p.w1 + (size_t)panel * p.n_total * KS;
-    RowSum<T> rs;
-    // four rows per pass, their node ids loaded first (same row order as a
-    // plain loop, so the sums are unchanged)
-    for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPI) {
-        int ids[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int r = r0 + u * RPI;
-            ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
+    double sum[4];
+    if (p.src.kind == SRC_RADEMACHER && !p.src.gaussian) {
+        const RadQuad rq(p.src, t.seg, gc0);
+        int neg[4] = {0, 0, 0, 0}, rows = 0;
+        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
+            const uint32_t id = p.node_id ? (uint32_t)__ldg(p.node_id + r) : (uint32_t)(r - sg.row_begin);
+            T v[4];
+            rq.row(id, v, neg);
+            st4(out + (size_t)r * KS + c0, v);
+            rows++;
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int r = r0 + u * RPI;
-            if (r < t.row_end) {
-                const T v = source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg);
-                out[(size_t)r * KS + c] = v;
-                rs.add(v);
+        for (int j = 0; j < 4; j++) sum[j] = rq.live[j] ? (double)(rows - 2 * neg[j]) : 0.0;
+    } else {
+        RowSum<T> rs[4];
+        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
+            const int id = p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin;
+            T v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                v[j] = source_value_t<T, KS>(p.src, p.panel_src, r, id, gc0 + j, p.n_total, t.seg);
+                rs[j].add(v[j]);
             }
+            st4(out + (size_t)r * KS + c0, v);
         }
+#pragma unroll
+        for (int j = 0; j < 4; j++) sum[j] = rs[j].total();
     }
-    __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = rs.total();
-    __syncthreads();
-    if (threadIdx.x < KS) {
-        double s = 0.0;
-        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
-        p.part[((size_t)panel * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
-    }
+    cta_column_partials<KS>(sum, rsub, c0, p.part + ((size_t)panel * p.tiles_per_panel + tile) * KS);
     __shared__ double tot[KS];
     if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + t.seg, panel, p.tiles_per_panel,
                             sg.tile_begin, sg.tile_count, tot)) {
@@ -219,59 +289,78 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
 
 // Pass 2: w_1 = b - mean (stored in T), ||w_1||^2 (FP64 across partial sums),
 // sigma_1 = 1/||w_1||.  With desingularisation b is read back from w_1, where
-// pass 1 stored it.
+// pass 1 stored it (16-byte loads, four rows in flight per thread); without,
+// Rademacher sources are generated as in pass 1 and their squared norms are
+// row counts (exact).
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const SegInfo sg = p.seg[t.seg];
-    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
-    constexpr int RPI = VNE_THREADS / KS;
-    const int gc = panel * KS + c;
-    const T mu = p.desing ? (T)p.mean[(size_t)t.seg * p.K + gc] : (T)0;
-    const bool live = gc < p.src.ncols;
+    constexpr int QPR = KS / 4, RPP = VNE_THREADS / QPR;
+    const int c0 = (threadIdx.x % QPR) * 4, rsub = threadIdx.x / QPR;
+    const int gc0 = panel * KS + c0;
     T* out = p.w1 + (size_t)panel * p.n_total * KS;
-    RowSum<T> rs;
-    for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPI) {
-        int ids[4];
-        T vals[4];
-        if (p.desing) {
+    double sum[4];
+    if (p.desing) {
+        T mu[4];
+        bool live[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            live[j] = gc0 + j < p.src.ncols;
+            mu[j] = (T)p.mean[(size_t)t.seg * p.K + gc0 + j];
+        }
+        RowSum<T> rs[4];
+        for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPP) {
+            T v[4][4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int r = r0 + u * RPI;
-                vals[u] = (live && r < t.row_end) ? out[(size_t)r * KS + c] - mu : (T)0;
+                const int r = r0 + u * RPP;
+                if (r < t.row_end) ld4(out + (size_t)r * KS + c0, v[u]);
             }
-        } else {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int r = r0 + u * RPI;
-                ids[u] = r < t.row_end ? (p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin) : 0;
-            }
+                const int r = r0 + u * RPP;
+                if (r < t.row_end) {
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int r = r0 + u * RPI;
-                vals[u] = (live && r < t.row_end)
-                              ? source_value_t<T, KS>(p.src, p.panel_src, r, ids[u], gc, p.n_total, t.seg)
-                              : (T)0;
+                    for (int j = 0; j < 4; j++) {
+                        v[u][j] = live[j] ? v[u][j] - mu[j] : (T)0;
+                        rs[j].add(v[u][j] * v[u][j]);
+                    }
+                    st4(out + (size_t)r * KS + c0, v[u]);
+                }
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int r = r0 + u * RPI;
-            if (r < t.row_end) {
-                out[(size_t)r * KS + c] = vals[u];
-                rs.add(vals[u] * vals[u]);
-            }
+        for (int j = 0; j < 4; j++) sum[j] = rs[j].total();
+    } else if (p.src.kind == SRC_RADEMACHER && !p.src.gaussian) {
+        const RadQuad rq(p.src, t.seg, gc0);
+        int neg[4] = {0, 0, 0, 0}, rows = 0;
+        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
+            const uint32_t id = p.node_id ? (uint32_t)__ldg(p.node_id + r) : (uint32_t)(r - sg.row_begin);
+            T v[4];
+            rq.row(id, v, neg);
+            st4(out + (size_t)r * KS + c0, v);
+            rows++;
         }
+#pragma unroll
+        for (int j = 0; j < 4; j++) sum[j] = rq.live[j] ? (double)rows : 0.0;
+    } else {
+        RowSum<T> rs[4];
+        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
+            const int id = p.node_id ? __ldg(p.node_id + r) : r - sg.row_begin;
+            T v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                v[j] = source_value_t<T, KS>(p.src, p.panel_src, r, id, gc0 + j, p.n_total, t.seg);
+                rs[j].add(v[j] * v[j]);
+            }
+            st4(out + (size_t)r * KS + c0, v);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) sum[j] = rs[j].total();
     }
-    __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = rs.total();
-    __syncthreads();
-    if (threadIdx.x < KS) {
-        double s = 0.0;
-        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
-        p.part[((size_t)panel * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
-    }
+    cta_column_partials<KS>(sum, rsub, c0, p.part + ((size_t)panel * p.tiles_per_panel + tile) * KS);
     __shared__ double tot[KS];
     if (last_cta_reduce<KS>(p.part, p.counter + (size_t)panel * p.nseg + t.seg, panel, p.tiles_per_panel,
                             sg.tile_begin, sg.tile_count, tot)) {
