@@ -54,6 +54,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_relabel(const int32_t* __restri
     }
 }
 
+// inv[order[i]] = i
+__global__ void k_invert_perm(const int32_t* __restrict__ order, int64_t n, int32_t* __restrict__ inv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        inv[order[i]] = (int32_t)i;
+}
+
 template <typename V>
 __global__ void k_convert(const double* __restrict__ in, int64_t count, V* __restrict__ out) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
@@ -89,6 +95,12 @@ cudaError_t launch_relabel(const int32_t* rp_old, const int32_t* col_old, const 
     else
         k_relabel<float><<<grid_for(n), kWarps * 32, 0, st>>>(rp_old, col_old, val_old, rp_new, order, inv, n,
                                                                col_new, (float*)val_new);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invert_perm(const int32_t* order, int64_t n, int32_t* inv, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_invert_perm<<<grid_for((n + 31) / 32), kWarps * 32, 0, st>>>(order, n, inv);
     return cudaGetLastError();
 }
 

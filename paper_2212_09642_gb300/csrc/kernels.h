@@ -227,6 +227,8 @@ cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int64_t n
                             unsigned long long* bad, cudaStream_t st);
 // New row i = old row order[i], columns renamed by inv; values (optional,
 // FP64 in) converted to the path precision.
+// inv[order[i]] = i for a permutation of 0 .. n-1 (device arrays).
+cudaError_t launch_invert_perm(const int32_t* order, int64_t n, int32_t* inv, cudaStream_t st);
 cudaError_t launch_relabel(const int32_t* rp_old, const int32_t* col_old, const double* val_old,
                            const int32_t* rp_new, const int32_t* order, const int32_t* inv, int64_t n,
                            int32_t* col_new, void* val_new, int fp64, cudaStream_t st);

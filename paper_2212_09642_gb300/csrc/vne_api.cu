@@ -105,6 +105,9 @@ struct vne_ctx {
     std::vector<cudaStream_t> color_streams;
     std::vector<cudaEvent_t> color_events;
     int32_t* pinned_ctr = nullptr;
+    // pinned host staging of the matrix assembly (reused; every assembly
+    // ends with a stream synchronisation, so no copy from it is in flight)
+    std::map<std::string, std::pair<void*, size_t>> pinned;
     std::vector<uint64_t> batch_key;
     int batch_ks = 0;
 };
@@ -185,6 +188,24 @@ void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero = fa
 template <typename T>
 T* ws_get_t(vne_ctx* ctx, const std::string& name, size_t count, bool zero = false) {
     return (T*)ws_get(ctx, name, count * sizeof(T), zero);
+}
+
+// Pinned host buffer `name` of at least `count` elements (grown on demand).
+template <typename T>
+T* pinned_get(vne_ctx* ctx, const std::string& name, size_t count) {
+    auto& b = ctx->pinned[name];
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 64);
+    if (b.second < bytes) {
+        if (b.first) cudaFreeHost(b.first);
+        b.first = nullptr;
+        b.second = 0;
+        if (cudaMallocHost(&b.first, bytes) != cudaSuccess) {
+            b.first = nullptr;
+            return nullptr;
+        }
+        b.second = bytes;
+    }
+    return (T*)b.first;
 }
 
 template <typename T>
@@ -1310,6 +1331,8 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
     for (cudaStream_t sx : ctx->color_streams) cudaStreamDestroy(sx);
     for (cudaEvent_t e : ctx->color_events) cudaEventDestroy(e);
     if (ctx->pinned_ctr) cudaFreeHost(ctx->pinned_ctr);
+    for (auto& kv : ctx->pinned)
+        if (kv.second.first) cudaFreeHost(kv.second.first);
     delete ctx->batch_prob;
     delete ctx;
     return VNE_OK;
@@ -1345,21 +1368,32 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     M->pattern = (vals == nullptr);
     const bool dev = flags & VNE_INPUT_DEVICE;
     // Row pointers on the host (O(n)): monotonicity, degrees, the relabelling
-    // and the work plan need them there.
-    std::vector<int64_t> rp(n + 1);
-    if (dev) VNE_TRY_CUDA(ctx, cudaMemcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-    else memcpy(rp.data(), row_ptr, (n + 1) * sizeof(int64_t));
-    VNE_REQUIRE(ctx, rp[0] == 0, VNE_EINVAL, "row_ptr[0] must be 0");
-    int64_t maxdeg = 0;
-    for (int64_t i = 0; i < n; i++) {
-        VNE_REQUIRE(ctx, rp[i + 1] >= rp[i], VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
-        maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
+    // and the work plan need them there.  One pass checks them, finds the
+    // largest degree and writes the int32 copy for the device into pinned
+    // staging; the uploads and the device validation of the columns then run
+    // while the host builds the relabelling.
+    std::vector<int64_t> rp_dev;
+    const int64_t* rph = row_ptr;
+    if (dev) {
+        rp_dev.resize(n + 1);
+        VNE_TRY_CUDA(ctx, cudaMemcpy(rp_dev.data(), row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        rph = rp_dev.data();
     }
-    const int64_t nnz = rp[n];
-    VNE_REQUIRE(ctx, nnz < (int64_t)INT32_MAX, VNE_EINVAL, "nnz = %lld exceeds int32", (long long)nnz);
+    VNE_REQUIRE(ctx, rph[0] == 0, VNE_EINVAL, "row_ptr[0] must be 0");
+    int32_t* rp32 = pinned_get<int32_t>(ctx, "asm.rp32", n + 1);
+    VNE_REQUIRE(ctx, rp32, VNE_ENOMEM, "pinned staging of %lld row pointers", (long long)(n + 1));
+    int64_t maxdeg = 0;
+    rp32[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t d = rph[i + 1] - rph[i];
+        VNE_REQUIRE(ctx, d >= 0, VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
+        VNE_REQUIRE(ctx, rph[i + 1] < (int64_t)INT32_MAX, VNE_EINVAL, "nnz = %lld exceeds int32",
+                    (long long)rph[i + 1]);
+        maxdeg = std::max(maxdeg, d);
+        rp32[i + 1] = (int32_t)rph[i + 1];
+    }
+    const int64_t nnz = rph[n];
     M->nnz = nnz;
-    std::vector<int32_t> rp32(n + 1);
-    for (int64_t i = 0; i <= n; i++) rp32[i] = (int32_t)rp[i];
     // Columns (and values) on the device: the caller's device arrays, or one
     // copy of the host arrays into staging buffers.
     const int32_t* d_ci = col_idx;
@@ -1374,17 +1408,45 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         if (nnz) VNE_TRY_CUDA(ctx, cudaMemcpyAsync(stage, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
         d_va = stage;
     }
-    int32_t* d_rp_in = upload(ctx, "asm.rowptr", rp32);
+    int32_t* d_rp_in = ws_get_t<int32_t>(ctx, "asm.rowptr", n + 1);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d_rp_in, rp32, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // column range and (pattern) self-loops, checked on the device
     unsigned long long* d_bad = ws_get_t<unsigned long long>(ctx, "asm.bad", 2);
     VNE_TRY_CUDA(ctx, launch_validate(d_rp_in, d_ci, n, vals ? 0 : 1, d_bad, st));
-    unsigned long long bad[2];
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
-    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
+    unsigned long long* bad = pinned_get<unsigned long long>(ctx, "asm.bad", 2);
+    VNE_REQUIRE(ctx, bad, VNE_ENOMEM, "pinned staging");
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(bad, d_bad, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     ctx->launches += 1;
+    // degree-descending relabelling (stable in the node id), built while the
+    // device validates: a counting sort over the degree classes; the packed
+    // row pointers follow from the class sizes alone
+    const bool by_degree = (flags & VNE_REORDER) && !(flags & VNE_REORDER_RCM);
+    int32_t* order_pin = nullptr;
+    int32_t* rp2_pin = nullptr;
+    std::vector<int64_t> rp2;
+    if (by_degree) {
+        order_pin = pinned_get<int32_t>(ctx, "asm.order", n);
+        rp2_pin = pinned_get<int32_t>(ctx, "asm.rp2", n + 1);
+        VNE_REQUIRE(ctx, order_pin && rp2_pin, VNE_ENOMEM, "pinned staging of the relabelling");
+        std::vector<int64_t> start(maxdeg + 2, 0);  // class c = maxdeg - degree
+        for (int64_t i = 0; i < n; i++) start[maxdeg - (rp32[i + 1] - rp32[i]) + 1]++;
+        for (int64_t c = 0; c <= maxdeg; c++) start[c + 1] += start[c];
+        rp2.resize(n + 1);
+        rp2[0] = 0;
+        rp2_pin[0] = 0;
+        for (int64_t c = 0; c <= maxdeg; c++) {
+            const int64_t d = maxdeg - c;
+            for (int64_t i = start[c]; i < start[c + 1]; i++) {
+                rp2[i + 1] = rp2[i] + d;
+                rp2_pin[i + 1] = (int32_t)rp2[i + 1];
+            }
+        }
+        for (int64_t i = 0; i < n; i++) order_pin[start[maxdeg - (rp32[i + 1] - rp32[i])]++] = (int32_t)i;
+    }
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
     if (bad[0] != ~0ull || bad[1] != ~0ull) {
         const unsigned long long k = std::min(bad[0], bad[1]);
-        const int64_t row = (int64_t)(std::upper_bound(rp.begin(), rp.end(), (int64_t)k) - rp.begin()) - 1;
+        const int64_t row = (int64_t)(std::upper_bound(rph, rph + n + 1, (int64_t)k) - rph) - 1;
         int32_t c = 0;
         VNE_TRY_CUDA(ctx, cudaMemcpy(&c, d_ci + k, sizeof(int32_t), cudaMemcpyDeviceToHost));
         if (k == bad[0]) VNE_REQUIRE(ctx, false, VNE_EINVAL, "column index %d out of range in row %lld", c, (long long)row);
@@ -1406,11 +1468,11 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         }
     }
     if (flags & VNE_CHECK_SYMMETRY) {
-        for (int64_t i = 0; i < n; i++) std::sort(hci.begin() + rp[i], hci.begin() + rp[i + 1]);
+        for (int64_t i = 0; i < n; i++) std::sort(hci.begin() + rph[i], hci.begin() + rph[i + 1]);
         for (int64_t i = 0; i < n; i++)
-            for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            for (int64_t k = rph[i]; k < rph[i + 1]; k++) {
                 int32_t j = hci[k];
-                bool found = std::binary_search(hci.begin() + rp[j], hci.begin() + rp[j + 1], (int32_t)i);
+                bool found = std::binary_search(hci.begin() + rph[j], hci.begin() + rph[j + 1], (int32_t)i);
                 VNE_REQUIRE(ctx, found, VNE_ENOTSYM, "pattern not symmetric: (%lld,%d)", (long long)i, j);
             }
     }
@@ -1423,7 +1485,7 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         double tr = 0.0, nm = 0.0;
         for (int64_t i = 0; i < n; i++) {
             double rs = 0.0;
-            for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            for (int64_t k = rph[i]; k < rph[i + 1]; k++) {
                 if (hci[k] == i) tr += hva[k];
                 rs += fabs(hva[k]);
             }
@@ -1444,15 +1506,27 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
     VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
     if (vals) VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
-    if (flags & (VNE_REORDER | VNE_REORDER_RCM)) {
-        // relabelling (host): reverse Cuthill-McKee, else degree-descending
-        // stable in the node id; the nonzeros are moved on the device
-        std::vector<int32_t> order = (flags & VNE_REORDER_RCM) ? rcm_order(n, rp.data(), hci.data())
-                                                               : degree_order(n, rp.data());  // new -> old
+    if (by_degree) {
+        // degree order built above; inverse permutation and the moved
+        // nonzeros on the device
+        int32_t* d_inv = ws_get_t<int32_t>(ctx, "asm.inv", n);
+        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_node_id, n * sizeof(int32_t)));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, order_pin, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp2_pin, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        VNE_TRY_CUDA(ctx, launch_invert_perm(M->d_node_id, n, d_inv, st));
+        VNE_TRY_CUDA(ctx, launch_relabel(d_rp_in, d_ci, d_va, M->d_rowptr, M->d_node_id, d_inv, n, M->d_col,
+                                         M->d_vals, fp64 ? 1 : 0, st));
+        ctx->launches += 2;
+        M->perm.assign(order_pin, order_pin + n);
+        VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));  // the pinned staging is reused by the next assembly
+    } else if (flags & VNE_REORDER_RCM) {
+        // relabelling (host): reverse Cuthill-McKee; the nonzeros are moved
+        // on the device
+        std::vector<int32_t> order = rcm_order(n, rph, hci.data());  // new -> old
         std::vector<int32_t> inv(n);
         for (int64_t i = 0; i < n; i++) inv[order[i]] = (int32_t)i;
-        std::vector<int64_t> rp2(n + 1, 0);
-        for (int64_t i = 0; i < n; i++) rp2[i + 1] = rp2[i] + (rp[order[i] + 1] - rp[order[i]]);
+        rp2.assign(n + 1, 0);
+        for (int64_t i = 0; i < n; i++) rp2[i + 1] = rp2[i] + (rph[order[i] + 1] - rph[order[i]]);
         std::vector<int32_t> rp2_32(n + 1);
         for (int64_t i = 0; i <= n; i++) rp2_32[i] = (int32_t)rp2[i];
         int32_t* d_inv = upload(ctx, "asm.inv", inv);
@@ -1464,7 +1538,6 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
                                          M->d_vals, fp64 ? 1 : 0, st));
         ctx->launches += 1;
         VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));  // host vectors above are sources of async copies
-        rp.swap(rp2);
         M->perm = std::move(order);
     } else {
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, d_rp_in, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
@@ -1473,9 +1546,10 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
             VNE_TRY_CUDA(ctx, launch_convert_values(d_va, nnz, M->d_vals, fp64 ? 1 : 0, st));
             ctx->launches += 1;
         }
+        rp2.assign(rph, rph + n + 1);
         VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
     }
-    M->h_rowptr.swap(rp);
+    M->h_rowptr.swap(rp2);
     M->maxdeg = maxdeg;
     {
         auto it = ctx->tune_cache.find(vne_ctx::TuneKey{M->n, M->nnz, maxdeg, (int)M->fp64, (int)M->pattern});
