@@ -345,6 +345,16 @@ vne_status vne_spmm(vne_matrix *mat, const void *X, void *Y, int32_t k);
 vne_status vne_block_gram(vne_ctx *ctx, const float *X, int32_t kx, const float *Y, int32_t ky, int32_t ks,
                           int64_t n, double *C);
 
+/* Out = In2 + coef In M (the block products of the Hutch++ sketch, Section
+ * 3.2: Q = Y R^{-1} and G - Q (Q^T G)) on the tcgen05 tensor cores.  In,
+ * In2 (nullable: no addend), Out: device float blocks in panel-major layout
+ * [k / ks][n][ks] with kin and kout columns (<= 128, multiples of ks = 8, 16
+ * or 32); M: host double[kin][kout] row-major.  TF32 three-product split
+ * (FP32 accuracy).  Out must not overlap In or In2.  EINVAL for bad sizes or
+ * NULL buffers; EDEVICE if a bounded wait of the kernel ran out. */
+vne_status vne_block_apply(vne_ctx *ctx, const float *In, int32_t kin, const double *M, int32_t kout,
+                           const float *In2, float *Out, int32_t ks, int64_t n, double coef);
+
 /* Gauss quadrature of given tridiagonals (Section 4): for each of `count`
  * columns, T = tridiag(beta[0..m-2], alpha[0..m-1]), psi = norm2 *
  * sum_j u_{1j}^2 f(scale * theta_j).  alpha, beta: double[count][m] host;

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvne.so")
 SOURCES = ["kernels_lanczos.cu", "kernels_dense.cu", "vne_api.cu", "host_graph.cpp", "noalloc.cu", "rational.cu",
-           "assemble.cu", "measure.cu", "coloring.cu", "tcgen05_gram.cu"]
+           "assemble.cu", "measure.cu", "coloring.cu", "tcgen05_sketch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

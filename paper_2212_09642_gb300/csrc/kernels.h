@@ -260,9 +260,13 @@ cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, d
 cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int ks, int n, double* part,
                             int max_chunks, int* err, int* chunks_out, int* sym_out, cudaStream_t st);
 // Out = (In2 ? In2 : 0) + coef * In * M, M double [kin][kout] row-major; panel-major blocks.
+// FP32 blocks with err given run on the tcgen05 tensor cores (err as for
+// launch_gram).
 template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
-                         double coef, cudaStream_t);
+                         double coef, int* err, cudaStream_t);
+cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout, const float* In2, float* Out, int ks,
+                             int n, double coef, int* err, cudaStream_t st);
 // Pivoted Cholesky of a k x k SPD matrix G (FP64) with rank cut-off tol * max diag.
 // Writes Minv [k][k] (rows permuted: Q = Y Minv spans range(Y)) and rank.
 // work: k * k + k doubles (R and 1 / R_jj), piv: k ints (device).

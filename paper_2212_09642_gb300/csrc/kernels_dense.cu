@@ -1232,23 +1232,6 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ X, int kx, c
         }
 }
 
-// TF32 split helpers for the warp-level MMA block product below
-// (x = x_hi + x_lo, both TF32; x^T y ~ hi.hi + hi.lo + lo.hi keeps FP32
-// accuracy).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int total, double* __restrict__ C) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -1359,146 +1342,17 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ In, int kin
     }
 }
 
-// Tensor-core block product Out = coef * In M (+ In2) for FP32 blocks
-// (kin, kout <= 128), the TF32 three-product split above.  M (FP64,
-// kin x kout) is converted once per CTA into hi/lo TF32 halves in shared
-// memory; each CTA then streams 64-row tiles of In through shared memory
-// (persistent grid).  Warps: 4 x 2, each owning 16 rows x 64 output columns.
-template <int KS>
-__global__ void __launch_bounds__(256) k_apply_tc(const float* __restrict__ In, int kin, const double* __restrict__ M,
-                                                  int kout, const float* __restrict__ In2, float* __restrict__ Out,
-                                                  int n, double coef) {
-    constexpr int LDB = 136;  // 136 = 8 (mod 32): conflict-free B fragments
-    constexpr int V_PER_ROW = KS / 4;
-    extern __shared__ __align__(16) uint32_t smu[];
-    const int kp = (kin + 7) & ~7;
-    const int lda = kp + 4;  // = 4 (mod 8): conflict-free A fragments
-    uint32_t* Bh = smu;
-    uint32_t* Bl = Bh + (size_t)kp * LDB;
-    float* As0 = reinterpret_cast<float*>(Bl + (size_t)kp * LDB);  // [2][64][lda]: double-buffered row tiles
-    for (int idx = threadIdx.x; idx < kp * 128; idx += 256) {
-        const int k = idx >> 7, c = idx & 127;
-        const float x = (k < kin && c < kout) ? (float)(coef * M[(size_t)k * kout + c]) : 0.f;
-        const uint32_t hi = to_tf32(x);
-        Bh[k * LDB + c] = hi;
-        Bl[k * LDB + c] = to_tf32(x - __uint_as_float(hi));
-    }
-    // columns kin..kp of both row-tile buffers stay zero
-    for (int idx = threadIdx.x; idx < 2 * 64 * (kp - kin); idx += 256) {
-        const int rl = idx / (kp - kin), c = kin + idx % (kp - kin);
-        As0[rl * lda + c] = 0.f;
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int g = lane >> 2, tq = lane & 3;
-    const int pin = kin / KS;
-    const int ntiles = (n + 63) / 64;
-    // Row tile `tile` into buffer `buf` by asynchronous 16-byte copies (rows
-    // past n are zero-filled): panel p holds rows r0.. contiguously, so
-    // consecutive threads copy consecutive 16-byte pieces.  The copy of the
-    // next tile runs while the current one is multiplied.
-    auto issue_tile = [&](int tile, int buf) {
-        const int r0 = tile * 64;
-        float* As = As0 + (size_t)buf * 64 * lda;
-        for (int idx = threadIdx.x; idx < pin * 64 * V_PER_ROW; idx += 256) {
-            const int p = idx / (64 * V_PER_ROW), rem = idx % (64 * V_PER_ROW);
-            const int rl = rem / V_PER_ROW, c = (rem % V_PER_ROW) * 4;
-            const int r = r0 + rl;
-            const float* src = In + (size_t)p * n * KS + (size_t)(r < n ? r : 0) * KS + c;
-            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(As + rl * lda + p * KS + c);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(r < n ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    if (blockIdx.x < ntiles) issue_tile(blockIdx.x, 0);
-    for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, it++) {
-        const int r0 = tile * 64;
-        const float* As = As0 + (size_t)(it & 1) * 64 * lda;
-        if (tile + (int)gridDim.x < ntiles) {
-            issue_tile(tile + gridDim.x, (it + 1) & 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
-        const int c0w = wn * 64;
-        if (c0w < kout) {
-            for (int k0 = 0; k0 < kp; k0 += 8) {
-                const float* ar = As + (wm * 16 + g) * lda + k0 + tq;
-                const float vv[4] = {ar[0], ar[8 * lda], ar[4], ar[8 * lda + 4]};
-                uint32_t ahi[4], alo[4];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    ahi[q] = to_tf32(vv[q]);
-                    alo[q] = to_tf32(vv[q] - __uint_as_float(ahi[q]));
-                }
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const int cb = c0w + j * 8;
-                    if (cb < kout) {
-                        const int bi = (k0 + tq) * LDB + cb + g;
-                        const uint32_t bhi[2] = {Bh[bi], Bh[bi + 4 * LDB]};
-                        const uint32_t blo[2] = {Bl[bi], Bl[bi + 4 * LDB]};
-                        mma_tf32(acc[j], alo, bhi);
-                        mma_tf32(acc[j], ahi, blo);
-                        mma_tf32(acc[j], ahi, bhi);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 8; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int r = r0 + wm * 16 + g + ((q & 2) ? 8 : 0);
-                const int c = c0w + j * 8 + 2 * tq + (q & 1);
-                if (r < n && c < kout) {
-                    const size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
-                    float v = acc[j][q];
-                    if (In2) v += In2[o];
-                    Out[o] = v;
-                }
-            }
-        __syncthreads();  // the buffer just read is the target of the next copy but one
-    }
-}
-
 template <typename T>
 cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const T* In2, T* Out, int ks, int n,
-                         double coef, cudaStream_t st) {
+                         double coef, int* err, cudaStream_t st) {
     if (kout > 128 || kin > 128) return cudaErrorInvalidValue;
+    if (sizeof(T) == 4 && err && kin > 0 && kout > 0 && (ks == 8 || ks == 16 || ks == 32))
+        return launch_apply_tc5(reinterpret_cast<const float*>(In), kin, M, kout, reinterpret_cast<const float*>(In2),
+                                reinterpret_cast<float*>(Out), ks, n, coef, err, st);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int ntiles = (n + 63) / 64;
-    if (sizeof(T) == 4 && kin > 0 && kout > 0 && kin % ks == 0) {
-        // tensor-core path (FP32 data)
-        const int kp = (kin + 7) & ~7;
-        const size_t smem_tc = (2 * (size_t)kp * 136 + 2 * 64 * (size_t)(kp + 4)) * 4;
-        dim3 g1(ntiles < sms ? ntiles : sms);
-        const float* Inf = reinterpret_cast<const float*>(In);
-        const float* In2f = reinterpret_cast<const float*>(In2);
-        float* Outf = reinterpret_cast<float*>(Out);
-#define VNE_APPLY_TC(KSV)                                                                                      \
-        if (ks == KSV) {                                                                                      \
-            cudaError_t e = cudaFuncSetAttribute(k_apply_tc<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                 (int)smem_tc);                                               \
-            if (e != cudaSuccess) return e;                                                                   \
-            k_apply_tc<KSV><<<g1, 256, smem_tc, st>>>(Inf, kin, M, kout, In2f, Outf, n, coef);                 \
-            return cudaGetLastError();                                                                        \
-        }
-        VNE_APPLY_TC(8)
-        VNE_APPLY_TC(16)
-        VNE_APPLY_TC(32)
-#undef VNE_APPLY_TC
-        return cudaErrorInvalidValue;
-    }
     size_t smem = ((size_t)kin * 128 + 64 * (size_t)kin) * sizeof(T);
     int per_sm = sizeof(T) == 4 ? 2 : 1;
     dim3 grid(ntiles < sms * per_sm ? ntiles : sms * per_sm);
@@ -1688,7 +1542,7 @@ template cudaError_t launch_gram<float>(const float*, int, const float*, int, in
                                        cudaStream_t);
 template cudaError_t launch_gram<double>(const double*, int, const double*, int, int, int, double*, int, double*, int*,
                                         cudaStream_t);
-template cudaError_t launch_apply<float>(const float*, int, const double*, int, const float*, float*, int, int, double, cudaStream_t);
-template cudaError_t launch_apply<double>(const double*, int, const double*, int, const double*, double*, int, int, double, cudaStream_t);
+template cudaError_t launch_apply<float>(const float*, int, const double*, int, const float*, float*, int, int, double, int*, cudaStream_t);
+template cudaError_t launch_apply<double>(const double*, int, const double*, int, const double*, double*, int, int, double, int*, cudaStream_t);
 
 }  // namespace vne

@@ -1,6 +1,9 @@
-// Gram C = X^T Y of two FP32 panel-major blocks on the fifth-generation
-// tensor cores (tcgen05), for the Hutch++ sketch (Section 3.2: the
-// Cholesky-QR of Y = f(A) Omega, and Q^T G for the projection G - Q Q^T G).
+// The dense contractions of the Hutch++ sketch (Section 3.2) on the
+// fifth-generation tensor cores (tcgen05): the Grams C = X^T Y of FP32
+// panel-major blocks (the Cholesky-QR of Y = f(A) Omega, and Q^T G for the
+// projection G - Q Q^T G) and the block products Out = In2 + coef In M
+// (Q = Y R^{-1}, G' = G - Q (Q^T G)).  The block product is described
+// above its kernel below; the Gram first.
 //
 // The contraction runs over the n rows of the blocks; the output is at most
 // 128 x 128.  Each CTA owns a contiguous range of rows and accumulates its
@@ -361,5 +364,223 @@ cudaError_t launch_gram_tc5(const float* X, int kx, const float* Y, int ky, int 
 #undef VNE_TC5
     return cudaErrorInvalidValue;
 }
+
+// ---------------------------------------------------------------------------
+// Block product Out = (In2 ? In2 : 0) + coef In M for FP32 panel-major blocks
+// In [n x kin], Out [n x kout] (kin, kout <= 128) and M FP64 [kin x kout].
+// The MMA's M dimension is a tile of 128 rows of In, N = kout rounded up to
+// 16 and K = kin, taken in chunks of 32 columns.  B = coef M^T is split
+// into TF32 hi / lo once per CTA and stays in shared memory (K-major, one
+// 32-column region per chunk).  For each (tile, chunk) unit the threads load
+// the chunk from HBM into registers one unit ahead (16-byte loads, rows in
+// order) and store its hi / lo parts into one of two A buffers; one thread
+// issues hi.hi + hi.lo + lo.hi per 8 columns of K into the tile's TMEM
+// accumulator (two, alternating between tiles) and commits to the buffer's
+// mbarrier.  Once a tile's last unit is done, the threads read its
+// accumulator (tcgen05.ld, one row per lane), add In2 and store Out, while
+// the next tile accumulates into the other one.  Persistent grid, one CTA
+// per SM; bounded waits as in the Gram.
+namespace {
+
+constexpr int kApplyChunk = 32;  // K columns per unit
+
+template <int KS>
+__global__ void __launch_bounds__(256, 1)
+    k_apply_tc5(const float* __restrict__ In, int kin, const double* __restrict__ Mat, int kout,
+                const float* __restrict__ In2, float* __restrict__ Out, int n, double coef, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nk = (kin + kApplyChunk - 1) / kApplyChunk;  // K chunks
+    const int kout16 = (kout + 15) & ~15;
+    const int bchunk = (kout16 / 8) * (int)kSbo;            // bytes of one B chunk (N rows x 32 K)
+    unsigned char* b_hi = smem;
+    unsigned char* b_lo = smem + nk * bchunk;
+    unsigned char* a_ops = smem + 2 * nk * bchunk;          // [2 buffers][hi, lo] x 16 KB
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(a_ops + 4 * kOpBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (n + 127) / 128;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nunits = my_tiles * nk;
+
+    // B = coef M^T, TF32 hi / lo, K-major per 32-column chunk
+    for (int idx = tid; idx < nk * kApplyChunk * kout16; idx += 256) {
+        const int k = idx / kout16, c = idx % kout16;
+        const float x = (k < kin && c < kout) ? (float)(coef * Mat[(size_t)k * kout + c]) : 0.f;
+        const uint32_t h = tf32_rna(x), l = tf32_rna(x - __uint_as_float(h));
+        const uint32_t off = (uint32_t)(k / kApplyChunk) * bchunk + (uint32_t)(c >> 3) * kSbo +
+                             (uint32_t)((k % kApplyChunk) >> 2) * kLbo + (uint32_t)(c & 7) * 16 + (uint32_t)(k & 3) * 4;
+        *reinterpret_cast<uint32_t*>(b_hi + off) = h;
+        *reinterpret_cast<uint32_t*>(b_lo + off) = l;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, written by the generic proxy
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_tf32(128, kout16);
+
+    // unit u = (local tile u / nk, chunk u % nk); this thread's four
+    // 16-byte pieces: operand row m, 4-column group kg of the chunk
+    auto load_unit = [&](int u, float4 (&v)[4]) {
+        const int tile = (int)blockIdx.x + (u / nk) * (int)gridDim.x, kc = u % nk;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = tid + 256 * i;
+            const int m = (q & 7) + 8 * (q >> 6), kg = (q >> 3) & 7;
+            const int r = tile * 128 + m, col = kc * kApplyChunk + 4 * kg;
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < n && col < kin)
+                v[i] = __ldcs(reinterpret_cast<const float4*>(In + (size_t)(col / KS) * n * KS + (size_t)r * KS +
+                                                              (col % KS)));
+        }
+    };
+    auto store_unit = [&](const float4 (&v)[4], unsigned char* hi, unsigned char* lo) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = tid + 256 * i;
+            const int m = (q & 7) + 8 * (q >> 6), kg = (q >> 3) & 7;
+            uint4 h, l;
+            h.x = tf32_rna(v[i].x);
+            h.y = tf32_rna(v[i].y);
+            h.z = tf32_rna(v[i].z);
+            h.w = tf32_rna(v[i].w);
+            l.x = tf32_rna(v[i].x - __uint_as_float(h.x));
+            l.y = tf32_rna(v[i].y - __uint_as_float(h.y));
+            l.z = tf32_rna(v[i].z - __uint_as_float(h.z));
+            l.w = tf32_rna(v[i].w - __uint_as_float(h.w));
+            const uint32_t off = (uint32_t)(m >> 3) * kSbo + (uint32_t)kg * kLbo + (uint32_t)(m & 7) * 16;
+            *reinterpret_cast<uint4*>(hi + off) = h;
+            *reinterpret_cast<uint4*>(lo + off) = l;
+        }
+    };
+    const int quarter = warp & 3;
+    auto epilogue = [&](int i) {  // local tile i: accumulator i & 1 holds coef In M for its 128 rows
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        const int r = tile * 128 + quarter * 32 + lane;
+#pragma unroll 1
+        for (int j = 0; j < 2; j++) {
+            const int c0 = ((warp >> 2) + 2 * j) * 32;
+            if (c0 >= kout16) continue;  // warp-uniform
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((i & 1) * 128 + c0), v);
+            if (r < n) {
+#pragma unroll
+                for (int g = 0; g < 8; g++) {
+                    const int c = c0 + 4 * g;
+                    if (c < kout) {
+                        const size_t o = (size_t)(c / KS) * n * KS + (size_t)r * KS + (c % KS);
+                        float4 y = make_float4(__uint_as_float(v[4 * g]), __uint_as_float(v[4 * g + 1]),
+                                               __uint_as_float(v[4 * g + 2]), __uint_as_float(v[4 * g + 3]));
+                        if (In2) {
+                            const float4 z = __ldcs(reinterpret_cast<const float4*>(In2 + o));
+                            y.x += z.x, y.y += z.y, y.z += z.z, y.w += z.w;
+                        }
+                        __stcs(reinterpret_cast<float4*>(Out + o), y);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+
+    bool failed = false;
+    int next_epi = 0;
+    float4 cur[4], nxt[4];
+    if (nunits > 0) load_unit(0, cur);
+    for (int u = 0; u < nunits; u++) {
+        if (u + 1 < nunits) load_unit(u + 1, nxt);
+        const int b = u & 1;
+        const bool ready = u < 2 || mbar_wait(mbar + b, (uint32_t)((u - 2) >> 1) & 1u);
+        if (__syncthreads_or(!ready)) {
+            failed = true;
+            break;
+        }
+        // tiles whose last unit is <= u - 2 are complete
+        while (next_epi < my_tiles && (next_epi + 1) * nk - 1 <= u - 2) epilogue(next_epi++);
+        unsigned char* hi = a_ops + b * 2 * kOpBytes;
+        store_unit(cur, hi, hi + kOpBytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int i = u / nk, kc = u % nk;
+            const uint32_t d = tmem + (uint32_t)((i & 1) * 128);
+            const uint32_t ah = smem_u32(hi), al = ah + kOpBytes;
+            const uint32_t bh = smem_u32(b_hi) + (uint32_t)(kc * bchunk), bl = smem_u32(b_lo) + (uint32_t)(kc * bchunk);
+            const int steps = min(kApplyChunk / 8, (kin - kc * kApplyChunk + 7) / 8);
+            for (int t = 0; t < steps; t++) {
+                const uint32_t o = (uint32_t)t * 2 * kLbo;
+                mma_tf32(d, op_desc(ah + o), op_desc(bh + o), idesc, (kc > 0 || t > 0) ? 1u : 0u);
+                mma_tf32(d, op_desc(ah + o), op_desc(bl + o), idesc, 1u);
+                mma_tf32(d, op_desc(al + o), op_desc(bh + o), idesc, 1u);
+            }
+            mma_commit(mbar + b);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) cur[i] = nxt[i];
+    }
+    if (nunits > 0 && !failed) {
+        const int ul = nunits - 1;
+        const bool done = mbar_wait(mbar + (ul & 1), (uint32_t)(ul >> 1) & 1u);
+        failed = __syncthreads_or(!done);
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(err, 1);
+        if (nunits > 0) {
+            mbar_wait(mbar, 0u);  // bounded; the outcome is already an error
+            mbar_wait(mbar + 1, 0u);
+        }
+    } else {
+        while (next_epi < my_tiles) epilogue(next_epi++);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout, const float* In2, float* Out, int ks,
+                             int n, double coef, int* err, cudaStream_t st) {
+    if (kin < 1 || kout < 1 || kin > 128 || kout > 128 || n < 1 || !err) return cudaErrorInvalidValue;
+    if ((ks != 8 && ks != 16 && ks != 32) || kin % ks || kout % ks) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int nk = (kin + kApplyChunk - 1) / kApplyChunk;
+    const int kout16 = (kout + 15) & ~15;
+    const int smem = 2 * nk * (kout16 / 8) * (int)kSbo + 4 * kOpBytes + 32;
+    const int ntiles = (n + 127) / 128;
+    const int grid = std::max(1, std::min(ntiles, sms));
+#define VNE_APPLY5(KSV)                                                                                       \
+    if (ks == KSV) {                                                                                          \
+        e = cudaFuncSetAttribute(k_apply_tc5<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);         \
+        if (e != cudaSuccess) return e;                                                                       \
+        k_apply_tc5<KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef, err);                   \
+        return cudaGetLastError();                                                                            \
+    }
+    VNE_APPLY5(8)
+    VNE_APPLY5(16)
+    VNE_APPLY5(32)
+#undef VNE_APPLY5
+    return cudaErrorInvalidValue;
+}
+
 
 }  // namespace vne

@@ -1764,10 +1764,10 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     const double tol = M->fp64 ? 1e-13 : 1e-5;
     VNE_TRY_CUDA(ctx, launch_gram<T>(Y, Kp, Y, Kp, ks, n, gpart, nch, G1, gerr, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank, cwork, cpiv, st));
-    VNE_TRY_CUDA(ctx, launch_apply<T>(Y, Kp, Minv, Kp, nullptr, Q1, ks, n, 1.0, st));
+    VNE_TRY_CUDA(ctx, launch_apply<T>(Y, Kp, Minv, Kp, nullptr, Q1, ks, n, 1.0, gerr, st));
     VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, gerr, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, cwork, cpiv, st));
-    VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, st));
+    VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, gerr, st));
     ctx->launches += 12;  // 2 x (gram + reduce + factor + inverse + apply)
     if (Kg > 0) {
         // G (Rademacher columns N_r..N_r+N_H-1), then G' = G - Q (Q^T G)
@@ -1800,13 +1800,13 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
         double* C = ws_get_t<double>(ctx, "QtG", (size_t)Kp * Kg);
         double* gpart2 = ws_get_t<double>(ctx, "gram.part2", (size_t)nch * Kp * Kg);
         VNE_TRY_CUDA(ctx, launch_gram<T>(Q, Kp, Gr, Kg, ks, n, gpart2, nch, C, gerr, st));
-        VNE_TRY_CUDA(ctx, launch_apply<T>(Q, Kp, C, Kg, Gr, Gp, ks, n, -1.0, st));
+        VNE_TRY_CUDA(ctx, launch_apply<T>(Q, Kp, C, Kg, Gr, Gp, ks, n, -1.0, gerr, st));
         ctx->launches += 4;
     }
     int hr[3] = {0, 0, 0};
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(hr, drank, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
-    VNE_REQUIRE(ctx, hr[2] == 0, VNE_EDEVICE, "tensor-core Gram: a bounded wait ran out");
+    VNE_REQUIRE(ctx, hr[2] == 0, VNE_EDEVICE, "tensor-core sketch kernel: a bounded wait ran out");
     const int r = std::min(hr[0], hr[1]);
     // 3. all N_r + N_H quadratic forms in one Lanczos block
     double low = 0.0, resid = 0.0;
@@ -2313,6 +2313,25 @@ extern "C" vne_status vne_block_gram(vne_ctx* ctx, const float* X, int32_t kx, c
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     VNE_REQUIRE(ctx, herr == 0, VNE_EDEVICE, "tensor-core Gram: a bounded wait ran out");
+    VNE_API_END(ctx)
+}
+
+extern "C" vne_status vne_block_apply(vne_ctx* ctx, const float* In, int32_t kin, const double* M, int32_t kout,
+                                      const float* In2, float* Out, int32_t ks, int64_t n, double coef) {
+    if (!ctx) return VNE_EINVAL;
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, In && M && Out && n >= 1 && n < INT32_MAX && kin >= 1 && kout >= 1 && kin <= 128 &&
+                         kout <= 128 && (ks == 8 || ks == 16 || ks == 32) && kin % ks == 0 && kout % ks == 0,
+                VNE_EINVAL, "bad arguments to vne_block_apply");
+    std::vector<double> hm(M, M + (size_t)kin * kout);
+    double* dM = upload(ctx, "ba.M", hm);
+    int* err = ws_get_t<int>(ctx, "ba.err", 1, true);
+    VNE_TRY_CUDA(ctx, launch_apply<float>(In, kin, dM, kout, In2, Out, ks, (int)n, coef, err, ctx->stream));
+    int herr = 0;
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    VNE_REQUIRE(ctx, herr == 0, VNE_EDEVICE, "tensor-core block product: a bounded wait ran out");
     VNE_API_END(ctx)
 }
 

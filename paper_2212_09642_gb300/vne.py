@@ -91,6 +91,8 @@ def _declare(lib):
         "vne_matrix_coloring": (st, [_P, ctypes.c_int32, _P, _PI32, _PI32]),
         "vne_gaussian_probes": (st, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
         "vne_block_gram": (st, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P]),
+        "vne_block_apply": (st, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int64,
+                                 ctypes.c_double]),
         "vne_entropy_probing_auto": (st, [_P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _COLORING_FN, _P,
                                           ctypes.POINTER(vne_options), _PD, ctypes.POINTER(vne_probing_report)]),
         "vne_spmm": (st, [_P, _P, _P, ctypes.c_int32]),
@@ -146,7 +148,7 @@ def exported_symbols():
 _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
                "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
-               "vne_greedy_coloring", "vne_matrix_coloring", "vne_gaussian_probes", "vne_block_gram", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
+               "vne_greedy_coloring", "vne_matrix_coloring", "vne_gaussian_probes", "vne_block_gram", "vne_block_apply", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_ctx_last_poly_dim", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
@@ -350,6 +352,13 @@ def vne_block_gram(ctx, X, kx, Y, ky, ks, n):
     C = np.zeros((kx, ky), dtype=np.float64)
     _check(load().vne_block_gram(ctx, _ptr(X), int(kx), _ptr(Y), int(ky), int(ks), int(n), _ptr(C)), ctx)
     return C
+
+
+def vne_block_apply(ctx, In, kin, M, kout, In2, Out, ks, n, coef=1.0):
+    """Out = In2 + coef In M on device float32 panel-major blocks (M: host float64 [kin, kout])."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    _check(load().vne_block_apply(ctx, _ptr(In), int(kin), _ptr(M), int(kout), _ptr(In2), _ptr(Out), int(ks), int(n),
+                                  float(coef)), ctx)
 
 
 def vne_gaussian_probes(ctx, seed, n, col_begin, k, out):
