@@ -1240,14 +1240,16 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nchunks, int 
     C[idx] = s;
 }
 
-// C = sum over chunks of E + E^T (k x k partials of a symmetric Gram).
-__global__ void k_gram_reduce_sym(const double* __restrict__ part, int nchunks, int k, double* __restrict__ C) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// C <- C + C^T in place (C = the summed partials E of a symmetric Gram): one
+// thread per pair a <= b.
+__global__ void k_gram_symmetrize(double* __restrict__ C, int k) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= k * k) return;
-    const int a = idx / k, b = idx % k, t = b * k + a;
-    double s = 0.0;
-    for (int c = 0; c < nchunks; c++) s += part[(size_t)c * k * k + idx] + part[(size_t)c * k * k + t];
-    C[idx] = s;
+    const int a = idx / k, b = idx % k;
+    if (a > b) return;
+    const double s = C[a * k + b] + C[b * k + a];
+    C[a * k + b] = s;
+    C[b * k + a] = s;
 }
 
 template <typename T>
@@ -1260,8 +1262,8 @@ cudaError_t launch_gram(const T* X, int kx, const T* Y, int ky, int ks, int n, d
                                         ks, n, part, nchunks, err, &chunks, &sym, st);
         if (e != cudaSuccess) return e;
         const int total = kx * ky;
-        if (sym) k_gram_reduce_sym<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, kx, C);
-        else k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
+        k_gram_reduce<<<(total + 255) / 256, 256, 0, st>>>(part, chunks, total, C);
+        if (sym) k_gram_symmetrize<<<(total + 255) / 256, 256, 0, st>>>(C, kx);
         return cudaGetLastError();
     }
     int tiles_x = (kx + 63) / 64, tiles_y = (ky + 63) / 64;

@@ -1768,7 +1768,7 @@ void hutchpp_impl(vne_matrix* M, const vne_options* o, int Nr, int NH, int m, ui
     VNE_TRY_CUDA(ctx, launch_gram<T>(Q1, Kp, Q1, Kp, ks, n, gpart, nch, G1, gerr, st));
     VNE_TRY_CUDA(ctx, launch_chol_qr_factor(G1, Kp, tol, Minv, drank + 1, cwork, cpiv, st));
     VNE_TRY_CUDA(ctx, launch_apply<T>(Q1, Kp, Minv, Kp, nullptr, Q, ks, n, 1.0, gerr, st));
-    ctx->launches += 12;  // 2 x (gram + reduce + factor + inverse + apply)
+    ctx->launches += 12;  // 2 x (gram + reduce + symmetrise + factor + inverse + apply)
     if (Kg > 0) {
         // G (Rademacher columns N_r..N_r+N_H-1), then G' = G - Q (Q^T G)
         const size_t gblk = (size_t)Kg * n;
