@@ -235,14 +235,45 @@ __device__ __forceinline__ void cta_column_partials(const double (&sum)[4], int 
     }
 }
 
-// Pass 1: column sums per segment -> mean (only when desingularising); the
-// source values are stored in w_1 on the way, so pass 2 reads them instead of
-// generating them again.  A thread covers four consecutive columns of a row
-// (16-byte stores).  Rademacher sources take a dedicated path: four hashes
-// per row and integer counts of the -1 entries, so the column sums are exact
-// (as the FP32 partial sums of +-1 entries are).
+// The Rademacher entries of this thread's four columns for the rows of a
+// tile (stored as they are generated if STORE); the node ids of four rows
+// are loaded before their hashes.  Returns the rows taken, counts the -1
+// entries.
+template <typename T, int KS, bool STORE>
+__device__ __forceinline__ int rad_rows(const StartParams<T>& p, const RowTile& t, const SegInfo& sg,
+                                        const RadQuad& rq, int rsub, int c0, T* out, int (&neg)[4]) {
+    constexpr int RPP = VNE_THREADS / (KS / 4);
+    int rows = 0;
+    for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPP) {
+        uint32_t ids[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPP;
+            ids[u] = r < t.row_end ? (p.node_id ? (uint32_t)__ldg(p.node_id + r) : (uint32_t)(r - sg.row_begin)) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = r0 + u * RPP;
+            if (r < t.row_end) {
+                T v[4];
+                rq.row(ids[u], v, neg);
+                if (STORE) st4(out + (size_t)r * KS + c0, v);
+                rows++;
+            }
+        }
+    }
+    return rows;
+}
+
+// Pass 1: column sums per segment -> mean (only when desingularising).  A
+// thread covers four consecutive columns of a row.  Rademacher sources take
+// a dedicated path: four hashes per row and integer counts of the -1
+// entries, so the column sums are exact (as the FP32 partial sums of +-1
+// entries are); pass 2 generates them again (cheaper than a store and a
+// read of the block).  Other sources are stored in w_1 on the way (16-byte
+// stores) and pass 2 reads them back.
 template <typename T, int KS>
-__global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
+__global__ void __launch_bounds__(VNE_THREADS, 4) k_start_mean(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const SegInfo sg = p.seg[t.seg];
@@ -253,14 +284,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
     double sum[4];
     if (p.src.kind == SRC_RADEMACHER && !p.src.gaussian) {
         const RadQuad rq(p.src, t.seg, gc0);
-        int neg[4] = {0, 0, 0, 0}, rows = 0;
-        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
-            const uint32_t id = p.node_id ? (uint32_t)__ldg(p.node_id + r) : (uint32_t)(r - sg.row_begin);
-            T v[4];
-            rq.row(id, v, neg);
-            st4(out + (size_t)r * KS + c0, v);
-            rows++;
-        }
+        int neg[4] = {0, 0, 0, 0};
+        const int rows = rad_rows<T, KS, false>(p, t, sg, rq, rsub, c0, out, neg);
 #pragma unroll
         for (int j = 0; j < 4; j++) sum[j] = rq.live[j] ? (double)(rows - 2 * neg[j]) : 0.0;
     } else {
@@ -288,12 +313,13 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_mean(StartParams<T> p) {
 }
 
 // Pass 2: w_1 = b - mean (stored in T), ||w_1||^2 (FP64 across partial sums),
-// sigma_1 = 1/||w_1||.  With desingularisation b is read back from w_1, where
-// pass 1 stored it (16-byte loads, four rows in flight per thread); without,
-// Rademacher sources are generated as in pass 1 and their squared norms are
-// row counts (exact).
+// sigma_1 = 1/||w_1||.  Rademacher entries are generated as in pass 1 and
+// their squared norms follow in closed form (rows, or rows (1 - mean^2) for
+// b - mean); other sources are read back from w_1, where pass 1 stored them
+// (16-byte loads, four rows in flight per thread), or, without
+// desingularisation, taken from the source.
 template <typename T, int KS>
-__global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) {
+__global__ void __launch_bounds__(VNE_THREADS, 3) k_start_center(StartParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     const RowTile t = p.tiles[tile];
     const SegInfo sg = p.seg[t.seg];
@@ -310,39 +336,68 @@ __global__ void __launch_bounds__(VNE_THREADS) k_start_center(StartParams<T> p) 
             live[j] = gc0 + j < p.src.ncols;
             mu[j] = (T)p.mean[(size_t)t.seg * p.K + gc0 + j];
         }
-        RowSum<T> rs[4];
-        for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPP) {
-            T v[4][4];
+        if (p.src.kind == SRC_RADEMACHER && !p.src.gaussian) {
+            // generated again (pass 1 did not store them); with b_i^2 = 1 and
+            // sum_i b_i = rows * mean, the squared norm of b - mean is
+            // rows (1 - mean^2), so no per-entry accumulation is needed
+            const RadQuad rq(p.src, t.seg, gc0);
+            int neg[4] = {0, 0, 0, 0}, rows = 0;
+            for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPP) {
+                uint32_t ids[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int r = r0 + u * RPP;
-                if (r < t.row_end) ld4(out + (size_t)r * KS + c0, v[u]);
-            }
+                for (int u = 0; u < 4; u++) {
+                    const int r = r0 + u * RPP;
+                    ids[u] = r < t.row_end ? (p.node_id ? (uint32_t)__ldg(p.node_id + r)
+                                                         : (uint32_t)(r - sg.row_begin))
+                                           : 0u;
+                }
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int r = r0 + u * RPP;
-                if (r < t.row_end) {
+                for (int u = 0; u < 4; u++) {
+                    const int r = r0 + u * RPP;
+                    if (r < t.row_end) {
+                        T v[4];
+                        rq.row(ids[u], v, neg);
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        v[u][j] = live[j] ? v[u][j] - mu[j] : (T)0;
-                        rs[j].add(v[u][j] * v[u][j]);
+                        for (int j = 0; j < 4; j++) v[j] = live[j] ? v[j] - mu[j] : (T)0;
+                        st4(out + (size_t)r * KS + c0, v);
+                        rows++;
                     }
-                    st4(out + (size_t)r * KS + c0, v[u]);
                 }
             }
-        }
 #pragma unroll
-        for (int j = 0; j < 4; j++) sum[j] = rs[j].total();
+            for (int j = 0; j < 4; j++) {
+                const double m = p.mean[(size_t)t.seg * p.K + gc0 + j];
+                sum[j] = live[j] ? (double)rows * (1.0 - m * m) : 0.0;
+            }
+        } else {
+            RowSum<T> rs[4];
+            for (int r0 = t.row_begin + rsub; r0 < t.row_end; r0 += 4 * RPP) {
+                T v[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int r = r0 + u * RPP;
+                    if (r < t.row_end) ld4(out + (size_t)r * KS + c0, v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int r = r0 + u * RPP;
+                    if (r < t.row_end) {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            v[u][j] = live[j] ? v[u][j] - mu[j] : (T)0;
+                            rs[j].add(v[u][j] * v[u][j]);
+                        }
+                        st4(out + (size_t)r * KS + c0, v[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) sum[j] = rs[j].total();
+        }
     } else if (p.src.kind == SRC_RADEMACHER && !p.src.gaussian) {
         const RadQuad rq(p.src, t.seg, gc0);
-        int neg[4] = {0, 0, 0, 0}, rows = 0;
-        for (int r = t.row_begin + rsub; r < t.row_end; r += RPP) {
-            const uint32_t id = p.node_id ? (uint32_t)__ldg(p.node_id + r) : (uint32_t)(r - sg.row_begin);
-            T v[4];
-            rq.row(id, v, neg);
-            st4(out + (size_t)r * KS + c0, v);
-            rows++;
-        }
+        int neg[4] = {0, 0, 0, 0};
+        const int rows = rad_rows<T, KS, true>(p, t, sg, rq, rsub, c0, out, neg);
 #pragma unroll
         for (int j = 0; j < 4; j++) sum[j] = rq.live[j] ? (double)rows : 0.0;
     } else {
