@@ -1434,11 +1434,13 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         rp2.resize(n + 1);
         rp2[0] = 0;
         rp2_pin[0] = 0;
+        int64_t acc = 0;  // running offset kept in a register (no store-to-load chain)
         for (int64_t c = 0; c <= maxdeg; c++) {
             const int64_t d = maxdeg - c;
             for (int64_t i = start[c]; i < start[c + 1]; i++) {
-                rp2[i + 1] = rp2[i] + d;
-                rp2_pin[i + 1] = (int32_t)rp2[i + 1];
+                acc += d;
+                rp2[i + 1] = acc;
+                rp2_pin[i + 1] = (int32_t)acc;
             }
         }
         for (int64_t i = 0; i < n; i++) order_pin[start[maxdeg - (rp32[i + 1] - rp32[i])]++] = (int32_t)i;
