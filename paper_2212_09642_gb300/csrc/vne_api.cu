@@ -783,10 +783,6 @@ vne_options defaults() {
     return o;
 }
 
-void check_mat(vne_matrix* M) {
-    if (!M) throw Error{VNE_EINVAL};
-}
-
 template <typename T>
 void check_ks(vne_ctx* ctx, int ks) {
     bool ok = sizeof(T) == 4 ? (ks == 8 || ks == 16 || ks == 32) : (ks == 4 || ks == 8 || ks == 16);
