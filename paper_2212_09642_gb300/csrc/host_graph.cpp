@@ -1,14 +1,112 @@
 // Host-side graph utilities of libvne: greedy distance-d colouring
-// (Algorithm 1 of Section 3.1) and the degree-descending and reverse
-// Cuthill-McKee relabellings.
+// (Algorithm 1 of Section 3.1), the degree-descending and reverse
+// Cuthill-McKee relabellings, and the O(n) passes of the matrix assembly
+// (threads over row ranges).
 #include <stdint.h>
 
 #include <algorithm>
 #include <vector>
+#include <thread>
+#include <climits>
 
 #include "host_graph.h"
 
 namespace vne {
+
+namespace {
+// Threads for an O(n) host pass: one per 2^17 rows, at most 8.
+int pass_threads(int64_t n) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t by_n = n >> 17;
+    int t = (int)std::min<int64_t>(std::min<int64_t>(8, hw ? (int64_t)hw : 1), std::max<int64_t>(1, by_n));
+    return std::max(1, t);
+}
+// Runs f(t, lo, hi) on T contiguous ranges of [0, n).
+template <typename F>
+void run_ranges(int64_t n, int T, F f) {
+    if (T <= 1) {
+        f(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int t = 0; t < T; t++) th.emplace_back(f, t, n * t / T, n * (t + 1) / T);
+    for (auto& x : th) x.join();
+}
+}  // namespace
+
+int64_t check_row_offsets(int64_t n, const int64_t* rph, int32_t* rp32, int64_t* maxdeg_out) {
+    const int T = pass_threads(n);
+    std::vector<int64_t> mx(T, 0), bad(T, -1);
+    rp32[0] = (int32_t)rph[0];
+    run_ranges(n, T, [&](int t, int64_t lo, int64_t hi) {
+        int64_t m = 0;
+        for (int64_t i = lo; i < hi; i++) {
+            const int64_t d = rph[i + 1] - rph[i];
+            if (d < 0 || rph[i + 1] >= (int64_t)INT32_MAX) {
+                bad[t] = i;
+                return;
+            }
+            m = std::max(m, d);
+            rp32[i + 1] = (int32_t)rph[i + 1];
+        }
+        mx[t] = m;
+    });
+    int64_t m = 0;
+    for (int t = 0; t < T; t++) {
+        if (bad[t] >= 0) return bad[t];  // ranges are in row order: the first bad row
+        m = std::max(m, mx[t]);
+    }
+    *maxdeg_out = m;
+    return -1;
+}
+
+void degree_relabel(int64_t n, const int32_t* rp32, int64_t maxdeg, int32_t* order, int64_t* rp2, int32_t* rp2_32) {
+    const int64_t C = maxdeg + 1;  // class c = maxdeg - degree
+    int T = pass_threads(n);
+    if (C * T > 4 * n) T = 1;  // per-thread class counts would outweigh the pass
+    // class counts per thread range, then the offset of each (class, thread):
+    // classes in order, threads in row order within a class (stable in the id)
+    std::vector<int64_t> cnt((size_t)T * C, 0);
+    run_ranges(n, T, [&](int t, int64_t lo, int64_t hi) {
+        int64_t* c = cnt.data() + (size_t)t * C;
+        for (int64_t i = lo; i < hi; i++) c[maxdeg - (rp32[i + 1] - rp32[i])]++;
+    });
+    std::vector<int64_t> cls_start(C + 1, 0), cls_base(C + 1, 0);  // first position, first packed offset
+    {
+        int64_t pos = 0, off = 0;
+        for (int64_t c = 0; c < C; c++) {
+            cls_start[c] = pos;
+            cls_base[c] = off;
+            int64_t k = 0;
+            for (int t = 0; t < T; t++) {
+                const int64_t v = cnt[(size_t)t * C + c];
+                cnt[(size_t)t * C + c] = pos + k;  // becomes the thread's cursor in class c
+                k += v;
+            }
+            pos += k;
+            off += k * (maxdeg - c);
+        }
+        cls_start[C] = pos;
+        cls_base[C] = off;
+    }
+    run_ranges(n, T, [&](int t, int64_t lo, int64_t hi) {
+        int64_t* cur = cnt.data() + (size_t)t * C;
+        for (int64_t i = lo; i < hi; i++) order[cur[maxdeg - (rp32[i + 1] - rp32[i])]++] = (int32_t)i;
+    });
+    // packed offsets: position p of class c starts at cls_base[c] + (p - cls_start[c]) * degree
+    rp2[0] = 0;
+    rp2_32[0] = 0;
+    run_ranges(n, T, [&](int, int64_t lo, int64_t hi) {
+        int64_t c = std::upper_bound(cls_start.begin(), cls_start.end(), lo) - cls_start.begin() - 1;
+        for (int64_t p = lo; p < hi; p++) {
+            while (p >= cls_start[c + 1]) c++;
+            const int64_t v = cls_base[c] + (p + 1 - cls_start[c]) * (maxdeg - c);
+            rp2[p + 1] = v;
+            rp2_32[p + 1] = (int32_t)v;
+        }
+    });
+}
 
 // Order of Algorithm 1: nodes by descending degree, ties by ascending id.
 std::vector<int32_t> degree_order(int64_t n, const int64_t* rowptr) {

@@ -1379,14 +1379,11 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
     int32_t* rp32 = pinned_get<int32_t>(ctx, "asm.rp32", n + 1);
     VNE_REQUIRE(ctx, rp32, VNE_ENOMEM, "pinned staging of %lld row pointers", (long long)(n + 1));
     int64_t maxdeg = 0;
-    rp32[0] = 0;
-    for (int64_t i = 0; i < n; i++) {
-        const int64_t d = rph[i + 1] - rph[i];
-        VNE_REQUIRE(ctx, d >= 0, VNE_EINVAL, "row_ptr not monotone at %lld", (long long)i);
-        VNE_REQUIRE(ctx, rph[i + 1] < (int64_t)INT32_MAX, VNE_EINVAL, "nnz = %lld exceeds int32",
-                    (long long)rph[i + 1]);
-        maxdeg = std::max(maxdeg, d);
-        rp32[i + 1] = (int32_t)rph[i + 1];
+    const int64_t bad_row = check_row_offsets(n, rph, rp32, &maxdeg);
+    if (bad_row >= 0) {
+        VNE_REQUIRE(ctx, rph[bad_row + 1] >= rph[bad_row], VNE_EINVAL, "row_ptr not monotone at %lld",
+                    (long long)bad_row);
+        VNE_REQUIRE(ctx, false, VNE_EINVAL, "nnz = %lld exceeds int32", (long long)rph[bad_row + 1]);
     }
     const int64_t nnz = rph[n];
     M->nnz = nnz;
@@ -1424,22 +1421,8 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         order_pin = pinned_get<int32_t>(ctx, "asm.order", n);
         rp2_pin = pinned_get<int32_t>(ctx, "asm.rp2", n + 1);
         VNE_REQUIRE(ctx, order_pin && rp2_pin, VNE_ENOMEM, "pinned staging of the relabelling");
-        std::vector<int64_t> start(maxdeg + 2, 0);  // class c = maxdeg - degree
-        for (int64_t i = 0; i < n; i++) start[maxdeg - (rp32[i + 1] - rp32[i]) + 1]++;
-        for (int64_t c = 0; c <= maxdeg; c++) start[c + 1] += start[c];
         rp2.resize(n + 1);
-        rp2[0] = 0;
-        rp2_pin[0] = 0;
-        int64_t acc = 0;  // running offset kept in a register (no store-to-load chain)
-        for (int64_t c = 0; c <= maxdeg; c++) {
-            const int64_t d = maxdeg - c;
-            for (int64_t i = start[c]; i < start[c + 1]; i++) {
-                acc += d;
-                rp2[i + 1] = acc;
-                rp2_pin[i + 1] = (int32_t)acc;
-            }
-        }
-        for (int64_t i = 0; i < n; i++) order_pin[start[maxdeg - (rp32[i + 1] - rp32[i])]++] = (int32_t)i;
+        degree_relabel(n, rp32, maxdeg, order_pin, rp2.data(), rp2_pin);
     }
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(st));
     if (bad[0] != ~0ull || bad[1] != ~0ull) {
