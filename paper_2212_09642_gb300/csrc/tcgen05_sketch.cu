@@ -7,8 +7,9 @@
 //
 // The contraction runs over the n rows of the blocks; the output is at most
 // 128 x 128.  Each CTA owns a contiguous range of rows and accumulates its
-// partial Gram in tensor memory (TMEM, FP32, one column per output column);
-// the partials are summed in FP64 across CTAs by the caller's reduction.
+// partial Gram in tensor memory (TMEM, FP32, one column per output column)
+// over groups of slabs, and the groups in FP32 registers; the partials are
+// summed in FP64 across CTAs by the caller's reduction.
 //
 // Pipeline per CTA (one CTA per SM, 256 threads):
 //   * raw slabs of 32 rows are copied into shared memory with cp.async,
