@@ -39,6 +39,11 @@ UNIT = "estimates/s"
 WORKLOAD = "BA n=1e6 m=4 (seed 3), rho=L/tr(L) FP32 implicit Laplacian, Hutch++ 300 matvec-equivalents, block 100, m=60"
 
 
+def workload_name(n):
+    """The headline workload's name, with the graph size when --n changes it."""
+    return WORKLOAD if n == N_NODES else WORKLOAD.replace("BA n=1e6", f"BA n={n}")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,7 +235,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz},
+        "config": {"workload": workload_name(g.n), "n": g.n, "nnz": g.nnz},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                          "sample": "per step: 1 sketch matvec + 1 quadratic form (FP64 scipy Lanczos, 60 steps) "
                                    "+ one n x 100 orthonormalisation/projection, scaled to 100 + 200 Krylov runs"},
@@ -396,7 +401,7 @@ def run_native(args):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.estimator == "hutchpp" else
+        "config": {"workload": workload_name(g.n) if args.estimator == "hutchpp" else
                    f"Hutchinson {args.vectors} vectors x {M_STEPS} steps on BA n={args.n} m=4 (profiling case)",
                    "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
                    "hutch_vectors": N_HUTCH, "krylov_steps": M_STEPS, "scalars": "f64",
