@@ -331,7 +331,8 @@ vne_status vne_matrix_coloring(vne_matrix *mat, int32_t distance, int32_t *color
 /* ---- kernel-level entry points (device pointers; used by the tests) ---
  * Y = A X for a block of k columns, X and Y device arrays [n][k] row-major
  * in the matrix's precision (float or double), rows in the caller's node
- * numbering.  A is the normalised density matrix. */
+ * numbering.  A is the normalised density matrix rho = L / tr(L) (Section
+ * 2). */
 vne_status vne_spmm(vne_matrix *mat, const void *X, void *Y, int32_t k);
 
 /* C = X^T Y (the Gram of the Hutch++ sketch, Section 3.2: Y^T Y for the
@@ -379,11 +380,14 @@ vne_status vne_quadrature_bounds(vne_ctx *ctx, const double *alpha, const double
                                  double scale, int32_t count, int32_t m, double lam_min, double lam_max,
                                  int32_t grid, double *lower, double *upper, double *estimate);
 
-/* Fill a device array [n][k] (row-major, float or double per `fp64`) with
- * Rademacher columns col_begin..col_begin+k-1 for node ids 0..n-1. */
+/* The probe vectors of the trace estimators (Section 3.2; Rademacher
+ * entries, E[x x^T] = I): fill a device array [n][k] (row-major, float or
+ * double per `fp64`) with columns col_begin..col_begin+k-1 for node ids
+ * 0..n-1.  EINVAL for bad sizes or a NULL buffer. */
 vne_status vne_rademacher(vne_ctx *ctx, uint64_t seed, int64_t n, int32_t col_begin, int32_t k,
                           int32_t fp64, void *out_device);
-/* The Gaussian probes of the same counters (vne_options.gaussian_probes):
+/* The Gaussian probes of Section 3.2 on the same counters
+ * (vne_options.gaussian_probes):
  * with h1 = h(j, i) the Rademacher hash of column j and node i and
  * h2 = mix64(h1 + 0x9E3779B97F4A7C15), u1 = ((h1 >> 11) + 1/2) 2^-53,
  * u2 = (h2 >> 11) 2^-53, x = sqrt(-2 log u1) cos(2 pi u2) (Box-Muller), FP64.
@@ -405,8 +409,8 @@ vne_status vne_autotune(vne_matrix *mat, int32_t k, int32_t steps, vne_options *
 
 /* ---- batched uneven graphs (one launch per step over all graphs) ------
  * Packs `count` matrices (same precision) block-diagonally and runs
- * Hutchinson with N Rademacher vectors and m Lanczos steps on each, all
- * graphs advancing together.  estimates double[count]; std_errors may be
+ * Hutchinson's estimator (Section 3.2) with N Rademacher vectors and m
+ * Lanczos steps (Section 4) on each, all graphs advancing together.  estimates double[count]; std_errors may be
  * NULL.  Each graph's result is independent of the others. */
 vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t num_vectors,
                                 int32_t krylov_steps, uint64_t seed, const vne_options *opt,
