@@ -12,6 +12,16 @@
 B = f(A) is applied through Lanczos (module krylov).  Probes are Rademacher
 (module rng).  Hutch++ takes its sketch from probe columns 0..N_r-1 and its
 Hutchinson vectors from columns N_r..N_r+N_H-1.
+
+orth() in eq. Hutch++_formula is any orthonormal basis of range(B Omega).
+With exact quadratic forms the estimate does not depend on the choice, but
+tr(Q^T B Q) is evaluated here as a sum of Lanczos quadratures psi_m(q_i),
+which is not invariant under rotations of Q.  The oracle therefore fixes
+orth() as the column-pivoted QR factorisation Y P = Q R (Businger and Golub
+1965: at every step the column with the largest norm after projecting out
+the chosen ones is taken), R with a positive diagonal, truncated at the
+numerical rank; this is a unique Q, and it is the factorisation a pivoted
+Cholesky of Y^T Y computes.
 """
 import numpy as np
 
@@ -35,17 +45,23 @@ def hutchinson(A, num_vectors, m, seed, reorth="full", col_begin=0, rows=None, d
     return float(np.mean(psi)) if num_vectors else 0.0, psi
 
 
-def orthonormal_range(Y, rtol=None):
-    """Orthonormal basis of range(Y): left singular vectors whose singular
-    value exceeds rtol * sigma_max (default: max(n, k) * eps)."""
-    if Y.shape[1] == 0:
-        return Y
-    U, s, _ = np.linalg.svd(Y, full_matrices=False)
+def orthonormal_range(Y, rtol=None, return_pivots=False):
+    """Q of the column-pivoted QR factorisation Y P = Q R (Householder, via
+    LAPACK geqp3), columns in pivot order, signs chosen so that diag(R) > 0,
+    truncated at the numerical rank: the pivots with |R_jj| > rtol |R_11|
+    (default rtol = max(n, k) * eps)."""
+    import scipy.linalg as sla
+    k = Y.shape[1]
+    if k == 0:
+        return (Y, np.zeros(0, dtype=np.int64)) if return_pivots else Y
+    Q, R, piv = sla.qr(np.asarray(Y, dtype=np.float64), mode="economic", pivoting=True)
     if rtol is None:
         rtol = max(Y.shape) * np.finfo(np.float64).eps
-    if s.size == 0 or s[0] == 0.0:
-        return U[:, :0]
-    return U[:, s > rtol * s[0]]
+    d = np.abs(np.diag(R))
+    r = 0 if d.size == 0 or d[0] == 0.0 else int(np.sum(d > rtol * d[0]))
+    sgn = np.where(np.diag(R)[:r] < 0.0, -1.0, 1.0)
+    Q = Q[:, :r] * sgn
+    return (Q, piv[:r].astype(np.int64)) if return_pivots else Q
 
 
 def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_parts=False, dist="rademacher"):
@@ -55,7 +71,7 @@ def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_part
     Omega = probes(seed, n, 0, n_sketch, rows=rows, dist=dist)
     Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], m, reorth=reorth, norm_A=nA)
                          for j in range(n_sketch)]) if n_sketch else np.zeros((n, 0))
-    Q = orthonormal_range(Y)
+    Q, piv = orthonormal_range(Y, return_pivots=True)
     psi_q = np.array([lanczos_quadform(A, Q[:, i], m, reorth=reorth, norm_A=nA)[0]
                       for i in range(Q.shape[1])])
     G = probes(seed, n, n_sketch, n_hutch, rows=rows, dist=dist)
@@ -66,7 +82,7 @@ def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_part
     resid = float(np.mean(psi_g)) if n_hutch else 0.0
     est = low_rank + resid
     if return_parts:
-        return est, dict(Y=Y, Q=Q, psi_q=psi_q, psi_g=psi_g, low_rank=low_rank, resid=resid)
+        return est, dict(Y=Y, Q=Q, pivots=piv, psi_q=psi_q, psi_g=psi_g, low_rank=low_rank, resid=resid)
     return est
 
 

@@ -12,11 +12,12 @@ A_m = V_m^T A V_m and V_m an orthonormal basis whose first column is
 c / ||c|| (eq. rational-krylov-approximation-quadform).  The paper builds V_m
 by rational Arnoldi with full orthogonalisation (Remark rational-lanczos); the
 oracle orthonormalises the spanning set above with modified Gram-Schmidt
-applied twice, in the order listed, dropping a vector whose remainder falls
-below 1e-6 of its norm (reading: the paper's rational Arnoldi needs no drop
-rule in exact arithmetic; a pole direction that is dependent on the earlier
-ones to six digits carries no usable information once the shifted systems
-are solved iteratively, so both implementations treat it as dependent).
+applied twice, in the order listed.  In exact arithmetic rational Arnoldi
+drops nothing (the spanning vectors of distinct poles are independent while
+m does not exceed the number of distinct eigenvalues); in floating point a
+vector whose remainder after the two passes is at the rounding level of its
+norm (below 1e-12 of it) is numerically in the span of the earlier ones and
+is dropped, which is the exact-arithmetic space up to rounding.
 
 The shifted solves use dense LU (small n) or, for large n, one conjugate
 gradient run per shift with relative residual 1e-10 -- the definition
@@ -73,8 +74,9 @@ def rational_basis(A, c, shifts, n_inf=2, method="auto"):
     return np.column_stack(cols)
 
 
-def orthonormalize(W, drop=1e-6):
-    """Modified Gram-Schmidt, two passes per vector, in column order."""
+def orthonormalize(W, drop=1e-12):
+    """Modified Gram-Schmidt, two passes per vector, in column order; a vector
+    whose remainder is at most drop times its norm is dependent (dropped)."""
     basis = []
     for j in range(W.shape[1]):
         w = W[:, j].astype(np.float64).copy()

@@ -120,3 +120,61 @@ def test_grid_colors_at_least_the_optimum():
     for d in (1, 2, 3):
         col = coloring.greedy_distance_coloring(g, d)
         assert col.max() + 1 >= math.ceil((d + 1) ** 2 / 2)
+
+
+# ---- orth() of eq. Hutch++_formula: column-pivoted QR ----
+
+def _brute_force_pivots(Y, r):
+    """Greedy column choice by explicit least squares: at every step the
+    column with the largest residual after fitting it by the chosen ones."""
+    chosen = []
+    for _ in range(r):
+        best, bi = -1.0, -1
+        for c in range(Y.shape[1]):
+            if c in chosen:
+                continue
+            y = Y[:, c]
+            if chosen:
+                B = Y[:, chosen]
+                coef = np.linalg.lstsq(B, y, rcond=None)[0]
+                res = np.linalg.norm(y - B @ coef)
+            else:
+                res = np.linalg.norm(y)
+            if res > best:
+                best, bi = res, c
+        chosen.append(bi)
+    return np.array(chosen)
+
+
+def test_orth_is_column_pivoted_qr():
+    rs = np.random.default_rng(11)
+    Y = rs.standard_normal((60, 9)) * np.array([3.0, 0.2, 5.0, 1.0, 0.7, 2.5, 0.1, 4.0, 1.5])
+    Q, piv = estimators.orthonormal_range(Y, return_pivots=True)
+    assert Q.shape == (60, 9)
+    assert np.array_equal(piv, _brute_force_pivots(Y, 9))
+    assert np.allclose(Q.T @ Q, np.eye(9), atol=1e-14)
+    R = Q.T @ Y[:, piv]
+    assert np.allclose(np.tril(R, -1), 0.0, atol=1e-13)
+    assert np.all(np.diag(R) > 0.0)
+    assert np.all(np.diff(np.abs(np.diag(R))) <= 1e-12)
+    assert np.allclose(Q @ R, Y[:, piv], atol=1e-13)
+
+
+def test_orth_rank_of_low_rank_sketch():
+    rs = np.random.default_rng(12)
+    Y = rs.standard_normal((50, 3)) @ rs.standard_normal((3, 7))
+    Q = estimators.orthonormal_range(Y)
+    assert Q.shape[1] == 3
+    U = np.linalg.svd(Y, full_matrices=False)[0][:, :3]
+    assert np.allclose(Q @ Q.T, U @ U.T, atol=1e-13)
+
+
+def test_hutchpp_parts_consistent():
+    # the low-rank part is the sum of the quadratures of the pivoted Q's
+    # columns; G' is orthogonal to Q
+    g = G.barabasi_albert(200, 3, 4)
+    A = _rho(g)
+    est, p = estimators.hutchpp(A, 6, 5, 20, seed=5, return_parts=True)
+    assert p["Q"].shape[1] == 6 and len(p["pivots"]) == 6
+    assert math.isclose(p["low_rank"], float(np.sum(p["psi_q"])), rel_tol=1e-15)
+    assert math.isclose(est, p["low_rank"] + p["resid"], rel_tol=1e-15)

@@ -113,3 +113,22 @@ def test_mixed_matches_dense_on_small_graph():
     c = krylov.desingularize(b)
     psi, k = rational.mixed_quadform(A, b, rational.default_shifts(A))
     assert abs(psi - float(c @ F @ c)) <= 1e-9 * float(c @ F @ c)
+
+
+def test_drop_rule_is_rounding_level():
+    # exact rational Arnoldi drops nothing: a direction independent to 1e-9
+    # is kept (its normalised remainder is the new basis vector), an exact
+    # repeat is dropped
+    e = np.eye(6)
+    W = np.column_stack([e[:, 0], e[:, 0] + 1e-9 * e[:, 1], 2.0 * e[:, 0], e[:, 2]])
+    V = rational.orthonormalize(W)
+    assert V.shape[1] == 3
+    assert np.allclose(np.abs(V[:, 1]), e[:, 1], atol=1e-6)
+    assert np.allclose(V.T @ V, np.eye(3), atol=1e-14)
+
+
+def test_repeated_pole_adds_no_direction():
+    A, s, b, c = _setup()
+    W1 = rational.rational_basis(A, c, s[:3], n_inf=2, method="dense")
+    W2 = rational.rational_basis(A, c, np.concatenate([s[:3], s[1:2]]), n_inf=2, method="dense")
+    assert rational.orthonormalize(W1).shape[1] == rational.orthonormalize(W2).shape[1] == 6
