@@ -19,7 +19,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvne.so")
-SOURCES = ["kernels_lanczos.cu", "kernels_dense.cu", "vne_api.cu", "host_graph.cpp", "noalloc.cu", "rational.cu",
+SOURCES = ["kernels_lanczos.cu", "kernels_dense.cu", "engine.cu", "abi.cu", "hutchpp.cu", "rational_driver.cu",
+           "probing.cu", "batch.cu", "autotune.cu", "serve.cu", "host_graph.cpp", "noalloc.cu", "rational.cu",
            "assemble.cu", "measure.cu", "coloring.cu", "tcgen05_sketch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

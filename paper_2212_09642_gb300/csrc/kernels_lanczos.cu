@@ -66,7 +66,7 @@ __device__ bool last_cta_reduce(const double* part, uint32_t* counter, int panel
 
 // ---------------------------------------------------------------------------
 // counter-based Rademacher entries (SplitMix64 mixer; see the header of
-// vne_api.cu for the definition)
+// abi.cu for the definition)
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
