@@ -241,13 +241,53 @@ vne_status vne_entropy_hutchinson(vne_matrix *mat, int32_t num_vectors, int32_t 
 /* ---- Hutch++ (Section 3.2, eq. Hutch++_formula)
  * Omega = Rademacher columns 0..N_r-1, G = columns N_r..N_r+N_H-1.
  * Y = f(A) Omega by the Lanczos matvec approximation
- * (eq. rational-krylov-approximation-matvec), Q = orthonormal basis of Y
- * (pivoted Cholesky-QR, twice), estimate = sum_i psi(q_i) +
- * (1/N_H) sum_j psi((I - Q Q^T) g_j).  parts (NULL ok) receives
- * {low-rank part, residual part, rank of Q}. */
+ * (eq. rational-krylov-approximation-matvec), Q = orth(Y) = the
+ * column-pivoted QR factor of Y (a pivoted Cholesky-QR pass, then an
+ * unpivoted one), estimate = sum_i psi(q_i) + (1/N_H) sum_j psi((I - Q Q^T)
+ * g_j).  parts (NULL ok) receives {low-rank part, residual part, rank of Q}.
+ * N_r in [1, 128], N_H in [0, 128].  ETIMEOUT if a bounded wait of the
+ * tensor-core sketch kernels ran out. */
 vne_status vne_entropy_hutchpp(vne_matrix *mat, int32_t sketch_cols, int32_t hutch_vectors,
                                int32_t krylov_steps, uint64_t seed, const vne_options *opt,
                                double *estimate, double *parts);
+
+/* ---- Hutch++ in two stages (Section 3.2, eq. Hutch++_formula), for
+ * callers that split one estimate over several GPUs (the quadratic forms are
+ * independent: remark after eq. rational-krylov-approximation-matvec) or
+ * inspect its parts.  vne_entropy_hutchpp is stage 1 over all N_r columns
+ * followed by stage 2 over all N_r + N_H quadratic forms, with the same
+ * results column for column.
+ *
+ * Stage 1: columns [col_begin, col_begin + ncols) of the sketch Y = f(A)
+ * Omega (eq. rational-krylov-approximation-matvec), Omega the probe columns
+ * 0..N_r-1 of `seed` (Rademacher, or Gaussian with opt->gaussian_probes).
+ * Every column is its own Lanczos recurrence: a column's value does not
+ * depend on the range it is computed in.
+ *   Y      [n][ncols] row-major, rows in the caller's node numbering, in the
+ *          matrix's precision (float for VNE_FP32, double for VNE_FP64); a
+ *          device pointer with VNE_VECTORS_DEVICE in flags, else host.
+ * ncols in [1, 256].  The call synchronises the context stream. */
+vne_status vne_hutchpp_sketch(vne_matrix *mat, int32_t col_begin, int32_t ncols, int32_t krylov_steps,
+                              uint64_t seed, const vne_options *opt, uint32_t flags, void *Y);
+
+/* Stage 2: from the whole sketch Y ([n][N_r], layout and flags as in stage
+ * 1), Q = orth(Y) as in vne_entropy_hutchpp, G' = (I - Q Q^T) G with G the
+ * probe columns N_r..N_r+N_H-1, and the quadratic forms psi_m of the columns
+ * [q_1 .. q_{N_r} | g'_1 .. g'_{N_H}] with index in
+ * [col_begin, col_begin + ncols): index i < N_r is q_{i+1} (psi = 0 for
+ * i >= rank), index N_r + j is g'_{j+1}.
+ *   psi     host double[ncols]
+ *   pivots  host int32[N_r] or NULL: the sketch column chosen as the i-th
+ *           pivot of Q (q_{i+1}), -1 beyond the rank
+ *   rank    host int32 or NULL: the numerical rank of Y (pivots above
+ *           1e-13 (FP64) / 1e-5 (FP32) of the largest diagonal of Y^T Y)
+ * The estimate is sum_{i < rank} psi[i] + (1/N_H) sum_j psi[N_r + j].
+ * EINVAL for a column range outside [0, N_r + N_H), N_r outside [1, 128] or
+ * N_H outside [0, 128]; ETIMEOUT as for vne_entropy_hutchpp. */
+vne_status vne_hutchpp_project(vne_matrix *mat, const void *Y, uint32_t flags, int32_t sketch_cols,
+                               int32_t hutch_vectors, int32_t krylov_steps, uint64_t seed, int32_t col_begin,
+                               int32_t ncols, const vne_options *opt, double *psi, int32_t *pivots,
+                               int32_t *rank);
 
 /* ---- probing (Section 3.1, eqs. probing_vectors, trace_probing)
  * T_d = sum_l psi(v_l), v_l the indicator of colour class l.
@@ -341,7 +381,7 @@ vne_status vne_spmm(vne_matrix *mat, const void *X, void *Y, int32_t k);
  * 16 or 32 columns per panel), kx, ky <= 128 columns, multiples of ks;
  * C: host double[kx][ky] row-major.  TF32 three-product split (FP32
  * accuracy), FP32 accumulation within a CTA, FP64 across CTAs.  EINVAL for
- * bad sizes or NULL buffers; EDEVICE if a bounded wait of the kernel ran
+ * bad sizes or NULL buffers; ETIMEOUT if a bounded wait of the kernel ran
  * out. */
 vne_status vne_block_gram(vne_ctx *ctx, const float *X, int32_t kx, const float *Y, int32_t ky, int32_t ks,
                           int64_t n, double *C);
@@ -352,7 +392,7 @@ vne_status vne_block_gram(vne_ctx *ctx, const float *X, int32_t kx, const float 
  * [k / ks][n][ks] with kin and kout columns (<= 128, multiples of ks = 8, 16
  * or 32); M: host double[kin][kout] row-major.  TF32 three-product split
  * (FP32 accuracy).  Out must not overlap In or In2.  EINVAL for bad sizes or
- * NULL buffers; EDEVICE if a bounded wait of the kernel ran out. */
+ * NULL buffers; ETIMEOUT if a bounded wait of the kernel ran out. */
 vne_status vne_block_apply(vne_ctx *ctx, const float *In, int32_t kin, const double *M, int32_t kout,
                            const float *In2, float *Out, int32_t ks, int64_t n, double coef);
 
@@ -457,11 +497,19 @@ vne_status vne_server_info(const vne_server *srv, int32_t *queued, int32_t *acti
  * three-term recurrence (reorth = 0): psi[j] ~ b_j^T f(rho) b_j for the graph
  * Laplacian density rho = L / tr(L) of a CSR pattern, with implicit
  * desingularisation.  Everything is caller-owned device memory:
- *   row_ptr  int32[n+1], col_idx int32[nnz] -- symmetric pattern, no self-loops
+ *   row_ptr  int32[n+1], nondecreasing, row_ptr[n] = nnz > 0
+ *   col_idx  int32[nnz] with 0 <= col < n -- a symmetric pattern without
+ *            self-loops
  *   vectors  double[n][k] row-major
  *   psi      double[k] output
  * Work goes on `stream` (a cudaStream_t, NULL for the legacy stream) on the
- * current device; the call returns without synchronising.
+ * current device; the call returns without synchronising.  The kernels check
+ * the CSR as they read it: a negative or decreasing row offset, nnz = 0 or a
+ * column outside [0, n) is never dereferenced and makes every psi NaN (the
+ * call cannot report it, since it does not wait for the GPU).  Symmetry is
+ * not checked.  If the calling thread already has a pending CUDA error, the
+ * call launches nothing, leaves that error in place and returns
+ * VNE_EDEVICE; a failing launch of its own also gives VNE_EDEVICE.
  *
  * Nothing is allocated: all intermediates live in one static device array of
  * VNE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until

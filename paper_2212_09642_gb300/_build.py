@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvne.so")
 SOURCES = ["kernels_lanczos.cu", "kernels_dense.cu", "engine.cu", "abi.cu", "hutchpp.cu", "rational_driver.cu",
            "probing.cu", "batch.cu", "autotune.cu", "serve.cu", "host_graph.cpp", "noalloc.cu", "rational.cu",
-           "assemble.cu", "measure.cu", "coloring.cu", "tcgen05_sketch.cu"]
+           "assemble.cu", "measure.cu", "coloring.cu", "tcgen05_sketch.cu", "layout.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

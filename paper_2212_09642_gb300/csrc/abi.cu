@@ -431,7 +431,7 @@ extern "C" vne_status vne_block_gram(vne_ctx* ctx, const float* X, int32_t kx, c
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(C, dC, (size_t)kx * ky * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    VNE_REQUIRE(ctx, herr == 0, VNE_EDEVICE, "tensor-core Gram: a bounded wait ran out");
+    VNE_REQUIRE(ctx, herr == 0, VNE_ETIMEOUT, "tensor-core Gram: a bounded wait ran out");
     VNE_API_END(ctx)
 }
 
@@ -450,7 +450,7 @@ extern "C" vne_status vne_block_apply(vne_ctx* ctx, const float* In, int32_t kin
     int herr = 0;
     VNE_TRY_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     VNE_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    VNE_REQUIRE(ctx, herr == 0, VNE_EDEVICE, "tensor-core block product: a bounded wait ran out");
+    VNE_REQUIRE(ctx, herr == 0, VNE_ETIMEOUT, "tensor-core block product: a bounded wait ran out");
     VNE_API_END(ctx)
 }
 

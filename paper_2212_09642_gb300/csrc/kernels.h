@@ -108,6 +108,9 @@ cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, i
 constexpr int kStepVariants = 8;
 template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
+// The first two passes of launch_reorth only: coef[i][col] = sig_i^2
+// (basis_i . w) for i < j (fixed-order sums, deterministic).
+template <typename T> cudaError_t launch_col_dots(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
 template <typename T> cudaError_t launch_recover(const RecoverParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T>
 cudaError_t launch_spmm_plain(const int32_t* rowptr, const int32_t* col, const T* vals, int n, int k,
@@ -117,7 +120,31 @@ cudaError_t launch_rademacher_fill(uint64_t seed_mixed, int64_t n, int col_begin
 // FP64 standard normal probes from the same counters (Box-Muller).
 cudaError_t launch_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, int k, double* out, cudaStream_t st);
 
+// ---- block layouts (layout.cu) ----
+// Columns col0 .. col0 + k - 1 of a panel-major block (n rows, panel width
+// ks) to row-major [n][k] in the caller's numbering (node_id: packed row ->
+// caller id, NULL for the identity).
+template <typename T>
+cudaError_t launch_panel_to_rows(const T* in, int n, int ks, int col0, int k, const int32_t* node_id, T* out,
+                                 cudaStream_t st);
+// Row-major [n][k] (caller numbering) to a panel-major block of Kp >= k
+// columns, the columns beyond k zero.
+template <typename T>
+cudaError_t launch_rows_to_panel(const T* in, int n, int ks, int k, int Kp, const int32_t* node_id, T* out,
+                                 cudaStream_t st);
+// Panel-major block of Kp >= k columns whose column c < k is column
+// src_cols[c] (device int32) of the panel-major `in`; columns beyond k zero.
+template <typename T>
+cudaError_t launch_select_columns(const T* in, int n, int ks, const int32_t* src_cols, int k, int Kp, T* out,
+                                  cudaStream_t st);
+
 // ---- multi-shift CG and rational projection (rational.cu) ----
+// v *= 1 / sqrt(rem2[col]) where rem2 > drop^2 orig2 (a kept direction),
+// else v = 0 (a dependent one): the last step of one Gram-Schmidt
+// orthonormalisation, for a panel-major block of K columns.
+template <typename T>
+cudaError_t launch_cgs_scale(T* v, const double* orig2, const double* rem2, double drop, int n, int K, int ks,
+                             int tiles_per_panel, const RowTile* tiles, cudaStream_t st);
 struct CgState {
     int32_t K, nshift;
     double scale, shift0, tol;
@@ -269,8 +296,9 @@ cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout
                              int n, double coef, int* err, cudaStream_t st);
 // Pivoted Cholesky of a k x k SPD matrix G (FP64) with rank cut-off tol * max diag.
 // Writes Minv [k][k] (rows permuted: Q = Y Minv spans range(Y)) and rank.
-// work: k * k + k doubles (R and 1 / R_jj), piv: k ints (device).
+// work: k * k + k doubles (R and 1 / R_jj), piv: k ints (device).  pivot =
+// false takes the columns in order (piv the identity).
 cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, double* work,
-                                  int* piv, cudaStream_t);
+                                  int* piv, cudaStream_t, bool pivot = true);
 
 }  // namespace vne

@@ -1386,9 +1386,11 @@ cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const 
 // small fraction of the FP32 rate on this part, so a step costs one square
 // root and one reciprocal (thread 0) and the row is scaled by multiplication.
 // Output R: work[0 .. k*k) row-major (upper triangle), 1 / R_jj:
-// work[k*k .. k*k + k), pivots: piv[0 .. k).
+// work[k*k .. k*k + k), pivots: piv[0 .. k).  With pivot = 0 the columns are
+// taken in their order (plain Cholesky; the first pivot below the cut-off
+// stops it).
 __global__ void k_chol_factor(const double* __restrict__ G, int k, double tol, double* __restrict__ work,
-                              int* __restrict__ piv_out, int* __restrict__ rank_out) {
+                              int* __restrict__ piv_out, int* __restrict__ rank_out, int pivot) {
     extern __shared__ double A[];  // k x (k + 1): odd row stride against bank conflicts
     const int ld = k + 1;
     __shared__ int piv[128];
@@ -1414,11 +1416,15 @@ __global__ void k_chol_factor(const double* __restrict__ G, int k, double tol, d
             // largest remaining diagonal entry (warp argmax, ties to the lower index)
             double best = -INFINITY;
             int p = j;
-            for (int i = j + (int)threadIdx.x; i < k; i += 32)
-                if (A[i * ld + i] > best) {
-                    best = A[i * ld + i];
-                    p = i;
-                }
+            if (pivot) {
+                for (int i = j + (int)threadIdx.x; i < k; i += 32)
+                    if (A[i * ld + i] > best) {
+                        best = A[i * ld + i];
+                        p = i;
+                    }
+            } else if (threadIdx.x == 0) {
+                best = A[j * ld + j];
+            }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const double ob = __shfl_xor_sync(0xffffffffu, best, off);
@@ -1528,14 +1534,14 @@ __global__ void __launch_bounds__(256) k_tri_inv(const double* __restrict__ work
 }
 
 cudaError_t launch_chol_qr_factor(const double* G, int k, double tol, double* Minv, int* rank, double* work,
-                                  int* piv, cudaStream_t st) {
+                                  int* piv, cudaStream_t st, bool pivot) {
     if (k > 128 || k <= 0) return cudaErrorInvalidValue;
     const size_t smem = (size_t)k * (k + 1) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_chol_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_chol_factor<<<1, 256, smem, st>>>(G, k, tol, work, piv, rank);
+    k_chol_factor<<<1, 256, smem, st>>>(G, k, tol, work, piv, rank, pivot ? 1 : 0);
     k_tri_inv<<<(k + 7) / 8, 256, smem, st>>>(work, k, piv, rank, Minv);
     return cudaGetLastError();
 }

@@ -920,6 +920,16 @@ cudaError_t launch_reorth(const ReorthParams<T>& p, const ReorthCoefParams& c, i
     return cudaGetLastError();
 }
 
+// coef[i][col] = sig_i^2 (basis_i . w) per column, without the update pass
+template <typename T>
+cudaError_t launch_col_dots(const ReorthParams<T>& p, const ReorthCoefParams& c, int ks, cudaStream_t st) {
+    if (p.j <= 0) return cudaSuccess;
+    VNE_DISPATCH_KS(T, ks, (k_reorth_dots<T, KS><<<dim3(p.panels * p.tiles_per_panel * p.j), VNE_THREADS, 0, st>>>(p)));
+    int total = c.panels * c.j * ks;
+    VNE_DISPATCH_KS(T, ks, (k_reorth_coef<KS><<<dim3((total + 255) / 256), 256, 0, st>>>(c)));
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_recover(const RecoverParams<T>& p, int ks, int panels, cudaStream_t st) {
     size_t smem = (size_t)p.m * ks * sizeof(T);
@@ -957,6 +967,7 @@ cudaError_t launch_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, 
     template cudaError_t launch_step<T>(const StepParams<T>&, int, int, bool, int, cudaStream_t);          \
     template cudaError_t launch_update<T>(const StepParams<T>&, int, int, cudaStream_t);                   \
     template cudaError_t launch_reorth<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
+    template cudaError_t launch_col_dots<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
     template cudaError_t launch_recover<T>(const RecoverParams<T>&, int, int, cudaStream_t);               \
     template cudaError_t launch_spmm_plain<T>(const int32_t*, const int32_t*, const T*, int, int,          \
                                               const int32_t*, double, const T*, T*, cudaStream_t);

@@ -60,6 +60,7 @@ struct Layout {
     double* part;     // [P][max(ctas, tiles)][KS]
     uint32_t* counter;  // [P]  (zeroed per call)
     int32_t* maxdeg;    // [1]  (zeroed per call)
+    int32_t* bad;       // [1]  (zeroed per call): set when the CSR input is invalid
     size_t bytes;       // total bytes used
     size_t zero_offset; // byte offset of the region that must start at zero
     size_t zero_bytes;
@@ -86,6 +87,7 @@ inline Layout make_layout(unsigned char* base, int n, int Kp, int m, int P, int 
     L.zero_offset = o;
     L.counter = (uint32_t*)take((size_t)P * sizeof(uint32_t));
     L.maxdeg = (int32_t*)take(sizeof(int32_t));
+    L.bad = (int32_t*)take(sizeof(int32_t));
     L.zero_bytes = o - L.zero_offset;
     L.bytes = o;
     return L;
@@ -129,10 +131,25 @@ __device__ void cta_partial(double v, int panel, int idx, int nparts, double* pa
     }
 }
 
+// Largest degree and the trace scale; rows that are not a CSR (a negative
+// offset, a decreasing pair of offsets, no stored entry at all) mark the
+// input invalid instead.
 __global__ void k_init(const int32_t* rowptr, int n, int Kp, Layout L) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(L.maxdeg, rowptr[i + 1] - rowptr[i]);
-    if (i < Kp) L.scale[i] = 1.0 / (double)rowptr[n];
+    if (i < n) {
+        const int32_t a = rowptr[i], b = rowptr[i + 1];
+        if (a < 0 || b < a) atomicExch(L.bad, 1);
+        else atomicMax(L.maxdeg, b - a);
+    }
+    const int32_t nnz = rowptr[n];
+    if (i == 0 && nnz <= 0) atomicExch(L.bad, 1);
+    if (i < Kp) L.scale[i] = nnz > 0 ? 1.0 / (double)nnz : 0.0;
+}
+
+// psi = NaN for every column when the input was found invalid.
+__global__ void k_mark_invalid(const Layout L, int k, double* psi) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < k && *L.bad) psi[c] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
 // pass 1: column means; pass 2 (center = 1): w_1 = b - mean, ||c||^2, sigma_1
@@ -188,11 +205,21 @@ __global__ void __launch_bounds__(VNE_THREADS) k_step_rows(const int32_t* __rest
     }
     const int r0 = cta * ROWS_PER_CTA + warp * ROWS_PER_WARP;
     const int r1 = min(n, r0 + ROWS_PER_WARP);
+    const int nnz = rowptr[n];
     for (int r = r0 + g; r < r1; r += G) {
-        const int kb = rowptr[r], ke = rowptr[r + 1];
+        int kb = rowptr[r], ke = rowptr[r + 1];
+        if (kb < 0 || ke < kb || ke > nnz) {  // not a CSR row: no entry is read
+            atomicExch(L.bad, 1);
+            kb = ke = 0;
+        }
         double acc[CPL] = {0.0, 0.0};
         for (int e = kb; e < ke; e++) {
-            const double2 x = *reinterpret_cast<const double2*>(W + (size_t)col[e] * KS + cofs);
+            const int cc = col[e];
+            if (cc < 0 || cc >= n) {  // outside the matrix: skipped, the input is marked invalid
+                atomicExch(L.bad, 1);
+                continue;
+            }
+            const double2 x = *reinterpret_cast<const double2*>(W + (size_t)cc * KS + cofs);
             acc[0] += x.x;
             acc[1] += x.y;
         }
@@ -281,6 +308,9 @@ extern "C" vne_status vne_quadform_noalloc(void* stream, int32_t n, const int32_
         g_addr[dev] = p;
         g_ready[dev] = true;
     }
+    // an error already pending on this thread belongs to earlier work: leave
+    // it for its owner and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return VNE_EDEVICE;
     cudaStream_t st = (cudaStream_t)stream;
     const int m = krylov_steps;
     const int P = (k + KS - 1) / KS, Kp = P * KS;
@@ -294,18 +324,26 @@ extern "C" vne_status vne_quadform_noalloc(void* stream, int32_t n, const int32_
     if (cudaMemsetAsync(L.alpha, 0, (size_t)m * Kp * sizeof(double), st) != cudaSuccess) return VNE_EDEVICE;
     if (cudaMemsetAsync(L.beta, 0, (size_t)m * Kp * sizeof(double), st) != cudaSuccess) return VNE_EDEVICE;
     if (cudaMemsetAsync(L.sigma, 0, (size_t)(m + 1) * Kp * sizeof(double), st) != cudaSuccess) return VNE_EDEVICE;
+    // every launch is checked right after it is made (the pending-error
+    // check above makes the status this call's own)
     const int nb = (n > Kp ? n : Kp);
     k_init<<<(nb + 255) / 256, 256, 0, st>>>(row_ptr, n, Kp, L);
+    if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
     k_start<<<P * tiles, VNE_THREADS, 0, st>>>(vectors, n, k, Kp, tiles, 0, L);
+    if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
     k_start<<<P * tiles, VNE_THREADS, 0, st>>>(vectors, n, k, Kp, tiles, 1, L);
+    if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
     // slots: w_j in slot (j-1) % 2, u in slot 2
     for (int j = 1; j <= m; j++) {
         const int s_cur = (j - 1) & 1, s_other = j & 1;
         k_step_rows<<<P * ctas, VNE_THREADS, 0, st>>>(row_ptr, col_idx, n, Kp, ctas, j, s_cur, s_other, 2, L);
+        if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
         k_update_rows<<<P * tiles, VNE_THREADS, 0, st>>>(n, Kp, tiles, j, s_cur, 2, s_other, L);
+        if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
     }
-    cudaError_t e = vne::launch_tridiag_quad(L.alpha, L.beta, L.norm2, L.scale, k, m, Kp, psi, st);
-    if (e != cudaSuccess) return VNE_EDEVICE;
+    if (vne::launch_tridiag_quad(L.alpha, L.beta, L.norm2, L.scale, k, m, Kp, psi, st) != cudaSuccess)
+        return VNE_EDEVICE;
+    k_mark_invalid<<<(k + 127) / 128, 128, 0, st>>>(L, k, psi);
     if (cudaGetLastError() != cudaSuccess) return VNE_EDEVICE;
     return VNE_OK;
 }

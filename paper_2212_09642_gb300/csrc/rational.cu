@@ -413,6 +413,38 @@ __global__ void k_rational_pass2(const double* Mg, const double* Kg, const doubl
     rank_out[c] = r;
 }
 
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_cgs_scale(T* v, const double* orig2, const double* rem2,
+                                                           double drop2, int n, int K, int tiles_per_panel,
+                                                           const RowTile* tiles) {
+    const int panel = blockIdx.x / tiles_per_panel, tile = blockIdx.x % tiles_per_panel;
+    const RowTile t = tiles[tile];
+    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
+    constexpr int RPI = VNE_THREADS / KS;
+    const int col = panel * KS + c;
+    const double r2 = rem2[col];
+    const double s = (r2 > 0.0 && r2 > drop2 * orig2[col]) ? 1.0 / sqrt(r2) : 0.0;
+    T* V = v + (size_t)panel * n * KS;
+    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) V[(size_t)r * KS + c] = (T)(s * (double)V[(size_t)r * KS + c]);
+}
+
+template <typename T>
+cudaError_t launch_cgs_scale(T* v, const double* orig2, const double* rem2, double drop, int n, int K, int ks,
+                             int tiles_per_panel, const RowTile* tiles, cudaStream_t st) {
+    dim3 grid((K / ks) * tiles_per_panel);
+    const double d2 = drop * drop;
+    if (ks == 4) k_cgs_scale<T, 4><<<grid, VNE_THREADS, 0, st>>>(v, orig2, rem2, d2, n, K, tiles_per_panel, tiles);
+    else if (ks == 8) k_cgs_scale<T, 8><<<grid, VNE_THREADS, 0, st>>>(v, orig2, rem2, d2, n, K, tiles_per_panel, tiles);
+    else if (ks == 16) k_cgs_scale<T, 16><<<grid, VNE_THREADS, 0, st>>>(v, orig2, rem2, d2, n, K, tiles_per_panel, tiles);
+    else if (ks == 32) k_cgs_scale<T, 32><<<grid, VNE_THREADS, 0, st>>>(v, orig2, rem2, d2, n, K, tiles_per_panel, tiles);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+template cudaError_t launch_cgs_scale<float>(float*, const double*, const double*, double, int, int, int, int,
+                                             const RowTile*, cudaStream_t);
+template cudaError_t launch_cgs_scale<double>(double*, const double*, const double*, double, int, int, int, int,
+                                              const RowTile*, cudaStream_t);
+
 // Per-column basis change: out_j = sum_i in_i X[i][j] (X per column, FP64,
 // staged in shared memory in the data precision).
 template <typename T, int KS>

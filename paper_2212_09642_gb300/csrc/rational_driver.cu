@@ -207,9 +207,12 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
     T* apow = ws_get_t<T>(ctx, "rat.apow", blk * kpoly);
     std::vector<const T*> W(nb), AW(nb);
     W[0] = C;
+    // the FP64 path orthonormalises W itself and applies A to the orthonormal
+    // basis afterwards, so it needs no A W
+    const bool need_aw = sizeof(T) != 8;
     if (mixed) {
         for (int j = 1; j < kpoly; j++) W[j] = rh + (size_t)(j - 1) * blk;
-        for (int j = 0; j < kpoly; j++) {
+        for (int j = 0; j < kpoly && need_aw; j++) {
             apply_operator<T>(ctx, P, ks, Kp, W[j], apow + (size_t)j * blk, 0.0, dq, variant, "rat.op0");
             AW[j] = apow + (size_t)j * blk;
         }
@@ -223,7 +226,7 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         for (int j = 1; j < kpoly; j++) W[j] = apow + (size_t)(j - 1) * blk;
         for (int j = 0; j < kpoly; j++) AW[j] = apow + (size_t)j * blk;
     }
-    for (int i = 0; i < nshift; i++)  // A x_s into the (now free) direction buffers
+    for (int i = 0; i < nshift && need_aw; i++)  // A x_s into the (now free) direction buffers
         apply_operator<T>(ctx, P, ks, Kp, v.x[i], v.ps[i], 0.0, dq, variant, "rat.op0");
     for (int i = 0; i < nshift; i++) {
         W[kpoly + i] = v.x[i];
@@ -257,36 +260,105 @@ void rational_block(vne_ctx* ctx, Problem& P, const StartSource& src, int K, int
         ctx->launches += 4;
     };
     const size_t gsz = (size_t)2 * nb * nb * Kp;
-    double* gram = ws_get_t<double>(ctx, "rat.gram", gsz);
     double* gram2 = ws_get_t<double>(ctx, "rat.gram2", gsz);
-    double* X1 = ws_get_t<double>(ctx, "rat.X1", (size_t)nb * nb * Kp);
-    gram_pairs(W, AW, gram);
-    VNE_TRY_CUDA(ctx, launch_rational_pass1(gram, nb, Kp, drop, X1, st));
-    T* tw = ws_get_t<T>(ctx, "rat.tw", blk * nb);
-    T* taw = ws_get_t<T>(ctx, "rat.taw", blk * nb);
-    std::vector<const T*> W1(nb), AW1(nb);
-    for (int dir = 0; dir < 2; dir++) {
-        BlockTransform<T> bt{};
-        bt.n = n;
-        bt.K = Kp;
-        bt.nb = nb;
-        bt.tiles_per_panel = tiles;
-        bt.tiles = P.d_tiles;
-        bt.X = X1;
-        T* base = dir == 0 ? tw : taw;
-        for (int i = 0; i < nb; i++) {
-            bt.in[i] = dir == 0 ? W[i] : AW[i];
-            bt.out[i] = base + (size_t)i * blk;
-            (dir == 0 ? W1 : AW1)[i] = bt.out[i];
-        }
-        VNE_TRY_CUDA(ctx, launch_block_transform<T>(bt, ks, panels, st));
-    }
-    gram_pairs(W1, AW1, gram2);
     double* dpsi = ws_get_t<double>(ctx, "rat.psi", Kp);
     int* drank = ws_get_t<int>(ctx, "rat.rank", Kp);
-    // ||c||^2 is the (0,0) entry of the first Gram matrix
-    VNE_TRY_CUDA(ctx, launch_rational_pass2(gram2, gram2 + (size_t)nb * nb * Kp, gram, nb, Kp, drop2, dpsi, drank, st));
-    ctx->launches += 4;
+    if (sizeof(T) == 8) {
+        // FP64: classical Gram-Schmidt applied twice to the vectors, in basis
+        // order, each column on its own.  A direction is dropped only when its
+        // remainder is at the rounding level of its norm (drop), which a
+        // factorisation of the Gram matrix could not resolve; then A V by the
+        // SpMM and the projection from the Gram matrices of (V, A V), whose
+        // first matrix is the identity up to rounding.
+        T* V = ws_get_t<T>(ctx, "rat.V", blk * nb);
+        T* AV = ws_get_t<T>(ctx, "rat.AV", blk * nb);
+        double* ones = upload(ctx, "rat.cgs.ones", std::vector<double>((size_t)nb * Kp, 1.0));
+        double* coef = ws_get_t<double>(ctx, "rat.cgs.coef", (size_t)nb * Kp);
+        double* cpart = ws_get_t<double>(ctx, "rat.cgs.part", (size_t)panels * nb * tiles * ks);
+        double* orig2 = ws_get_t<double>(ctx, "rat.cgs.orig2", Kp);
+        double* rem2 = ws_get_t<double>(ctx, "rat.cgs.rem2", Kp);
+        ReorthParams<T> rp{};
+        rp.basis = V;
+        rp.slot_stride = blk;
+        rp.K = Kp;
+        rp.n_total = n;
+        rp.panels = panels;
+        rp.tiles_per_panel = tiles;
+        rp.tiles = P.d_tiles;
+        rp.part = cpart;
+        rp.coef = coef;
+        ReorthCoefParams cp{};
+        cp.part = cpart;
+        cp.sig = ones;
+        cp.coef = coef;
+        cp.K = Kp;
+        cp.panels = panels;
+        cp.tiles_per_panel = tiles;
+        auto col_norm2 = [&](T* v, double* out) {  // out[col] = ||v[:, col]||^2
+            ReorthParams<T> q = rp;
+            q.basis = v;
+            q.w = v;
+            q.j = 1;
+            ReorthCoefParams qc = cp;
+            qc.j = 1;
+            qc.coef = out;
+            VNE_TRY_CUDA(ctx, launch_col_dots<T>(q, qc, ks, st));
+        };
+        for (int a = 0; a < nb; a++) {
+            T* va = V + (size_t)a * blk;
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(va, W[a], blk * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            col_norm2(va, orig2);
+            if (a > 0) {
+                rp.w = va;
+                rp.j = a;
+                cp.j = a;
+                for (int pass = 0; pass < 2; pass++) VNE_TRY_CUDA(ctx, launch_reorth<T>(rp, cp, ks, st));
+            }
+            col_norm2(va, rem2);
+            VNE_TRY_CUDA(ctx, launch_cgs_scale<T>(va, orig2, rem2, drop, n, Kp, ks, tiles, P.d_tiles, st));
+            ctx->launches += 5 + (a > 0 ? 6 : 0);
+        }
+        std::vector<const T*> Vv(nb), AVv(nb);
+        for (int a = 0; a < nb; a++) {
+            apply_operator<T>(ctx, P, ks, Kp, V + (size_t)a * blk, AV + (size_t)a * blk, 0.0, dq, variant, "rat.op0");
+            Vv[a] = V + (size_t)a * blk;
+            AVv[a] = AV + (size_t)a * blk;
+        }
+        gram_pairs(Vv, AVv, gram2);
+        // ||c||^2 of every column from the start pass
+        VNE_TRY_CUDA(ctx, launch_rational_pass2(gram2, gram2 + (size_t)nb * nb * Kp, norm2, nb, Kp, drop2, dpsi, drank,
+                                                st));
+        ctx->launches += 1;
+    } else {
+        double* gram = ws_get_t<double>(ctx, "rat.gram", gsz);
+        double* X1 = ws_get_t<double>(ctx, "rat.X1", (size_t)nb * nb * Kp);
+        gram_pairs(W, AW, gram);
+        VNE_TRY_CUDA(ctx, launch_rational_pass1(gram, nb, Kp, drop, X1, st));
+        T* tw = ws_get_t<T>(ctx, "rat.tw", blk * nb);
+        T* taw = ws_get_t<T>(ctx, "rat.taw", blk * nb);
+        std::vector<const T*> W1(nb), AW1(nb);
+        for (int dir = 0; dir < 2; dir++) {
+            BlockTransform<T> bt{};
+            bt.n = n;
+            bt.K = Kp;
+            bt.nb = nb;
+            bt.tiles_per_panel = tiles;
+            bt.tiles = P.d_tiles;
+            bt.X = X1;
+            T* base = dir == 0 ? tw : taw;
+            for (int i = 0; i < nb; i++) {
+                bt.in[i] = dir == 0 ? W[i] : AW[i];
+                bt.out[i] = base + (size_t)i * blk;
+                (dir == 0 ? W1 : AW1)[i] = bt.out[i];
+            }
+            VNE_TRY_CUDA(ctx, launch_block_transform<T>(bt, ks, panels, st));
+        }
+        gram_pairs(W1, AW1, gram2);
+        // ||c||^2 is the (0,0) entry of the first Gram matrix
+        VNE_TRY_CUDA(ctx, launch_rational_pass2(gram2, gram2 + (size_t)nb * nb * Kp, gram, nb, Kp, drop2, dpsi, drank,
+                                                st));
+        ctx->launches += 4;
+    }
     psi = download(ctx, dpsi, K);
     std::vector<int> hr(Kp), hit((size_t)nshift * Kp);
     std::vector<double> hres((size_t)nshift * Kp);
@@ -330,14 +402,18 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
     const double tol = (o && o->cg_tol > 0) ? o->cg_tol : 1e-8;
     const int maxit = (o && o->cg_max_iter > 0) ? o->cg_max_iter : 10000;
     const int n_inf = o ? o->n_inf_poles : 2;
-    // a pole direction whose squared relative remainder after orthogonalising
-    // against the earlier ones is below the threshold is dependent: FP64 uses
-    // the oracle's rule (remainder 1e-6 of the norm); FP32 vectors stop at a
-    // remainder of 1e-3, because a kept direction's A-image carries the
-    // vectors' rounding amplified by 1 / remainder.  Both Cholesky-QR passes
-    // apply the rule.
+    // a direction whose remainder after orthogonalising against the earlier
+    // ones is below the threshold is treated as dependent.  Exact rational
+    // Arnoldi drops nothing.  FP64 orthonormalises the vectors themselves and
+    // drops only at the rounding level (remainder 1e-12 of the norm).  FP32
+    // orthonormalises through the Gram matrices (Cholesky-QR2), which cannot
+    // resolve remainders below the square root of the rounding unit, and drops
+    // below a remainder of 1e-3 of the norm, because a kept direction's
+    // A-image carries the vectors' rounding amplified by 1 / remainder.
+    // FP64: relative remainder (Gram-Schmidt on the vectors); FP32: squared
+    // relative remainder (pivot of the Cholesky factor of the Gram matrix)
     const double drop = M->fp64 ? 1e-12 : 1e-6;
-    const double drop2 = drop;
+    const double drop2 = M->fp64 ? 1e-12 : drop;
     psi.assign(ncols, 0.0);
     iters.assign((size_t)nshift * ncols, 0);
     resid.assign((size_t)nshift * ncols, 0.0);

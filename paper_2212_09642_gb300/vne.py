@@ -85,6 +85,11 @@ def _declare(lib):
                                         ctypes.POINTER(vne_options), _PD, _PD, _PD]),
         "vne_entropy_hutchpp": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                      ctypes.POINTER(vne_options), _PD, _PD]),
+        "vne_hutchpp_sketch": (st, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                    ctypes.POINTER(vne_options), ctypes.c_uint32, _P]),
+        "vne_hutchpp_project": (st, [_P, _P, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vne_options),
+                                     _PD, _PI32, _PI32]),
         "vne_entropy_probing": (st, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                      ctypes.POINTER(vne_options), _PD, _PI32]),
         "vne_greedy_coloring": (st, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _PI32]),
@@ -147,7 +152,8 @@ def exported_symbols():
 
 _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_destroy", "vne_ctx_set_stream",
                "vne_last_error", "vne_create_density_matrix", "vne_matrix_destroy", "vne_matrix_info",
-               "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_entropy_probing",
+               "vne_quadform_batch", "vne_entropy_hutchinson", "vne_entropy_hutchpp", "vne_hutchpp_sketch",
+               "vne_hutchpp_project", "vne_entropy_probing",
                "vne_greedy_coloring", "vne_matrix_coloring", "vne_gaussian_probes", "vne_block_gram", "vne_block_apply", "vne_entropy_probing_auto", "vne_spmm", "vne_tridiag_quadrature", "vne_quadrature_bounds", "vne_rademacher",
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_ctx_last_poly_dim", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
@@ -275,6 +281,59 @@ def vne_entropy_hutchpp(ctx, mat, sketch_cols, hutch_vectors, krylov_steps, seed
                                       int(seed) & (2**64 - 1), ctypes.byref(o), ctypes.byref(est),
                                       parts.ctypes.data_as(_PD)), ctx)
     return est.value, parts
+
+
+def vne_hutchpp_sketch(ctx, mat, col_begin, ncols, krylov_steps, seed, fp64, opt=None, out=None):
+    """Columns [col_begin, col_begin + ncols) of the Hutch++ sketch f(A) Omega,
+    shape [n, ncols] in the caller's node order (float64 for an FP64 matrix,
+    float32 for FP32).  ``out``: a contiguous CUDA tensor of that shape and
+    dtype (the sketch stays on the device), else a new NumPy array."""
+    n = vne_matrix_info(mat)[0]
+    dt = np.float64 if fp64 else np.float32
+    o = opt if opt is not None else options()
+    if out is not None:
+        _require_device_block(out, (n, ncols), dt)
+        flags, dst = VNE_VECTORS_DEVICE, out
+    else:
+        flags, dst = 0, np.zeros((n, ncols), dtype=dt)
+    _check(load().vne_hutchpp_sketch(mat, int(col_begin), int(ncols), int(krylov_steps), int(seed) & (2**64 - 1),
+                                     ctypes.byref(o), flags, _ptr(dst)), ctx)
+    return dst
+
+
+def vne_hutchpp_project(ctx, mat, Y, sketch_cols, hutch_vectors, krylov_steps, seed, col_begin=0, ncols=None,
+                        opt=None):
+    """(psi [ncols], pivots [N_r], rank) of the Hutch++ quadratic forms with index
+    in [col_begin, col_begin + ncols) of [q_1..q_Nr | g'_1..g'_NH], from the
+    whole sketch Y ([n, N_r], a NumPy array or a contiguous CUDA tensor)."""
+    total = int(sketch_cols) + int(hutch_vectors)
+    ncols = total - int(col_begin) if ncols is None else int(ncols)
+    if hasattr(Y, "data_ptr"):
+        if not Y.is_cuda or not Y.is_contiguous() or Y.dim() != 2 or Y.shape[1] != sketch_cols:
+            raise VneError(VNE_EINVAL, "Y must be a contiguous CUDA tensor of shape [n, N_r]")
+        flags = VNE_VECTORS_DEVICE
+    else:
+        Y = np.ascontiguousarray(Y)
+        if Y.ndim != 2 or Y.shape[1] != sketch_cols or Y.dtype not in (np.float32, np.float64):
+            raise VneError(VNE_EINVAL, "Y must be a float32/float64 array of shape [n, N_r]")
+        flags = 0
+    psi = np.zeros(max(ncols, 0))
+    piv = np.zeros(int(sketch_cols), dtype=np.int32)
+    r = ctypes.c_int32()
+    o = opt if opt is not None else options()
+    _check(load().vne_hutchpp_project(mat, _ptr(Y), flags, int(sketch_cols), int(hutch_vectors), int(krylov_steps),
+                                      int(seed) & (2**64 - 1), int(col_begin), ncols, ctypes.byref(o),
+                                      psi.ctypes.data_as(_PD), piv.ctypes.data_as(_PI32), ctypes.byref(r)), ctx)
+    return psi, piv, r.value
+
+
+def _require_device_block(t, shape, dtype):
+    """A contiguous CUDA tensor of the given shape and NumPy dtype, else VneError."""
+    names = {np.float64: "torch.float64", np.float32: "torch.float32", np.int32: "torch.int32"}
+    ok = (hasattr(t, "data_ptr") and t.is_cuda and t.is_contiguous() and tuple(t.shape) == tuple(shape)
+          and str(t.dtype) == names[dtype])
+    if not ok:
+        raise VneError(VNE_EINVAL, f"expected a contiguous CUDA tensor {tuple(shape)} of {names[dtype]}")
 
 
 def vne_entropy_probing(ctx, mat, coloring=None, distance=1, krylov_steps=30, opt=None, shifts=None,
@@ -458,7 +517,16 @@ def vne_measure_gather(ctx, table_bytes, row_bytes, gathers, stream_bytes=0, rep
 
 def vne_quadform_noalloc(stream, n, row_ptr_dev, col_idx_dev, vectors_dev, k, krylov_steps, psi_dev):
     """Allocation-free FP64 Lanczos quadrature; every array is caller-owned device memory
-    (see include/vne.h).  Returns without synchronising the stream."""
+    (see include/vne.h): row_ptr int32 [n + 1], col_idx int32 [nnz], vectors float64
+    [n, k] contiguous, psi float64 [k].  Returns without synchronising the stream."""
+    if not (hasattr(row_ptr_dev, "data_ptr") and row_ptr_dev.is_cuda and row_ptr_dev.is_contiguous()
+            and str(row_ptr_dev.dtype) == "torch.int32" and row_ptr_dev.numel() == int(n) + 1):
+        raise VneError(VNE_EINVAL, "row_ptr must be a contiguous CUDA int32 tensor of n + 1 entries")
+    if not (hasattr(col_idx_dev, "data_ptr") and col_idx_dev.is_cuda and col_idx_dev.is_contiguous()
+            and str(col_idx_dev.dtype) == "torch.int32"):
+        raise VneError(VNE_EINVAL, "col_idx must be a contiguous CUDA int32 tensor")
+    _require_device_block(vectors_dev, (int(n), int(k)), np.float64)
+    _require_device_block(psi_dev, (int(k),), np.float64)
     s = getattr(stream, "cuda_stream", stream)
     st = load().vne_quadform_noalloc(s, int(n), _ptr(row_ptr_dev), _ptr(col_idx_dev), _ptr(vectors_dev), int(k),
                                      int(krylov_steps), _ptr(psi_dev))

@@ -50,3 +50,31 @@ def test_hutchpp_fp32_against_fp64_at_full_size(vctx, headline_graph):
         finally:
             vne.vne_matrix_destroy(mat)
     assert abs(ests[False] - ests[True]) <= 1e-4 * abs(ests[True]), ests
+
+
+def test_hutchpp_parts_against_oracle_at_full_size(vctx, headline_graph):
+    """The headline's Hutch++ path (FP32, degree relabelling, the tuned
+    schedule, 60 steps) at n = 10^6 on a sketch small enough for the oracle:
+    N_r = 6 sketch columns and N_H = 4 projected vectors.  Sketch columns
+    (relative to their norm), the pivot order, psi(q_i) and psi(g'_j) against
+    the FP64 oracle (no reorthogonalisation on either side), 1e-5."""
+    from oracle import estimators
+    g = headline_graph
+    Nr, NH, seed = 6, 4, 13
+    mat = vne.matrix_from_graph(vctx, g, fp64=False, reorder=True)
+    try:
+        vne.vne_autotune(vctx, mat, 112, 8)
+        opt = vne.options(reorth=0)
+        Y = vne.vne_hutchpp_sketch(vctx, mat, 0, Nr, STEPS, seed, False, opt=opt)
+        psi, piv, r = vne.vne_hutchpp_project(vctx, mat, Y, Nr, NH, STEPS, seed, opt=opt)
+    finally:
+        vne.vne_matrix_destroy(mat)
+    A, _ = density.density_matrix(g)
+    _, rp = estimators.hutchpp(A, Nr, NH, STEPS, seed=seed, reorth="none", return_parts=True)
+    Yr = rp["Y"]
+    for j in range(Nr):
+        assert np.linalg.norm(Y[:, j] - Yr[:, j]) <= 1e-5 * np.linalg.norm(Yr[:, j]), j
+    assert r == rp["Q"].shape[1] == Nr
+    assert np.array_equal(piv, rp["pivots"])
+    assert np.max(np.abs(psi[:Nr] - rp["psi_q"]) / np.abs(rp["psi_q"])) <= 1e-5
+    assert np.max(np.abs(psi[Nr:] - rp["psi_g"]) / np.abs(rp["psi_g"])) <= 1e-5

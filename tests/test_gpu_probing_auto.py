@@ -42,7 +42,7 @@ def test_probing_auto_matches_oracle(vctx, name, make, fp64, eps):
         est, rep = vne.vne_entropy_probing_auto(vctx, mat, eps, m, 16, opt=vne.options(check_every=check))
     finally:
         vne.vne_matrix_destroy(mat)
-    tol = 1e-10 if fp64 else 2e-5
+    tol = 1e-10 if fp64 else 1e-5
     for d in (1, 2, 3):
         col = coloring.greedy_distance_coloring(g, d)
         V = estimators.probing_vectors(col)

@@ -2,11 +2,14 @@
 (C ABI) vs the oracle's dense-solve rational quadrature on identical
 vectors and poles.
 
-Tolerances.  FP64 path with the CG driven to 1e-13: 1e-9 relative -- the GPU
-orthonormalises the basis through its Gram matrices (Cholesky-QR2) where the
-oracle applies Gram-Schmidt to the vectors; both drop a pole direction whose
-remainder is below 1e-6 of its norm.  Mixed path (FP32 vectors,
-CG to the default 1e-8 recursive residual): 2e-5 relative."""
+Tolerances: 1e-10 relative in the FP64 path (CG driven to 1e-13) and 1e-5
+in the mixed path (FP32 vectors, CG to the default 1e-8 recursive residual).
+The oracle solves the shifted systems directly and drops a spanning vector
+only at the rounding level of its norm (1e-12); the GPU orthonormalises
+through Gram matrices (Cholesky-QR2), which cannot resolve remainders below
+the square root of the rounding unit, so it drops a pole direction whose
+remainder is below 1e-6 (FP64) or 1e-3 (FP32) of its norm.  Both readings
+give the same psi within these tolerances on every case here."""
 import math
 
 import numpy as np
@@ -39,7 +42,7 @@ def test_rational_quadform_parity(vctx, name, g, fp64):
         vne.vne_matrix_destroy(mat)
     ref = np.array([rational.rational_quadform(A, X[:, j], sh) for j in range(X.shape[1])])
     rel = np.abs(psi - ref) / np.abs(ref)
-    assert rel.max() <= (1e-9 if fp64 else 2e-5), rel.max()
+    assert rel.max() <= (1e-10 if fp64 else 1e-5), rel.max()
     assert np.all(res <= tol_cg * 1.0000001)
     # larger shifts converge in fewer iterations (they are retired first)
     order = np.argsort(sh)
@@ -77,7 +80,7 @@ def test_rational_probing(vctx, fp64):
     V[np.arange(g.n), col] = 1.0
     ref = sum(rational.rational_quadform(A, V[:, l], sh) for l in range(V.shape[1]))
     assert s == V.shape[1]
-    assert abs(est - ref) <= (1e-9 if fp64 else 2e-5) * ref
+    assert abs(est - ref) <= (1e-10 if fp64 else 1e-5) * ref
     assert est <= entropy.dense_entropy(A) * (1 + 1e-7)
 
 
@@ -116,7 +119,7 @@ def test_mixed_switching_parity(vctx, name, g, fp64):
         assert k == _oracle_rule_k(A, X), (name, k)
     ref = np.array([rational.mixed_quadform(A, X[:, j], sh, k_poly=k, k_max=16)[0] for j in range(X.shape[1])])
     rel = np.abs(psi - ref) / np.abs(ref)
-    assert rel.max() <= (1e-9 if fp64 else 2e-5), (k, rel.max())
+    assert rel.max() <= (1e-10 if fp64 else 1e-5), (k, rel.max())
     assert np.all(res <= tol_cg * 1.0000001)
 
 
