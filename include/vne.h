@@ -487,6 +487,28 @@ vne_status vne_server_result(const vne_server *srv, int32_t ticket, int32_t *sta
                              double *std_error, int64_t *vectors_used, int64_t *ticks);
 vne_status vne_server_info(const vne_server *srv, int32_t *queued, int32_t *active, uint64_t *used_bytes);
 
+/* ---- failure injection (test hooks) -----------------------------------
+ * Host-side fault injection for the library's own error paths; nothing here
+ * touches a kernel.  Every device and pinned host buffer the library
+ * allocates goes through one pair of counted wrappers.
+ * vne_debug_fail_allocation(k): the k-th allocation from now on (k >= 1)
+ * fails as if the memory were exhausted, so the call that makes it returns
+ * VNE_ENOMEM; k = 0 switches the injection off.  Process-wide, not thread
+ * safe with concurrent calls.  EINVAL for k < 0.
+ * vne_debug_live_allocations: the number of device buffers and of pinned
+ * host buffers the library currently holds (across all contexts and
+ * matrices), to check that a failed call leaks nothing. */
+vne_status vne_debug_fail_allocation(int64_t k);
+vne_status vne_debug_live_allocations(int64_t *device_buffers, int64_t *pinned_buffers);
+/* Poll limit of the main-loop mbarrier waits of the tcgen05 sketch kernels
+ * (vne_block_gram, vne_block_apply and the Hutch++ orthonormalisation):
+ * polls >= 0 makes those waits give up after that many polls (0: at once),
+ * so that the kernels take their time-out path -- set the error flag, wait
+ * with the full limit for the MMAs already issued, free the tensor memory
+ * and return -- and the call reports VNE_ETIMEOUT; polls < 0 restores the
+ * built-in limit (2^20 polls).  Process-wide. */
+vne_status vne_debug_tensor_wait_limit(int64_t polls);
+
 /* ---- allocation-free quadratic forms ---------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they need the result (code bound

@@ -44,8 +44,7 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    for (auto& kv : ctx->ws)
-        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    for (auto& kv : ctx->ws) dev_free(kv.second.ptr);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->loop_ev)
         if (e) cudaEventDestroy(e);
@@ -53,9 +52,8 @@ extern "C" vne_status vne_ctx_destroy(vne_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (cudaStream_t sx : ctx->color_streams) cudaStreamDestroy(sx);
     for (cudaEvent_t e : ctx->color_events) cudaEventDestroy(e);
-    if (ctx->pinned_ctr) cudaFreeHost(ctx->pinned_ctr);
-    for (auto& kv : ctx->pinned)
-        if (kv.second.first) cudaFreeHost(kv.second.first);
+    pinned_free(ctx->pinned_ctr);
+    for (auto& kv : ctx->pinned) pinned_free(kv.second.first);
     delete ctx->batch_prob;
     delete ctx;
     return VNE_OK;
@@ -211,14 +209,14 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         M->scale = 1.0;
     }
     const size_t es = fp64 ? 8 : 4;
-    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_rowptr, (n + 1) * sizeof(int32_t)));
-    VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
-    if (vals) VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
+    VNE_TRY_CUDA(ctx, dev_malloc((void**)&M->d_rowptr, (n + 1) * sizeof(int32_t)));
+    VNE_TRY_CUDA(ctx, dev_malloc((void**)&M->d_col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    if (vals) VNE_TRY_CUDA(ctx, dev_malloc(&M->d_vals, std::max<int64_t>(nnz, 1) * es));
     if (by_degree) {
         // degree order built above; inverse permutation and the moved
         // nonzeros on the device
         int32_t* d_inv = ws_get_t<int32_t>(ctx, "asm.inv", n);
-        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_node_id, n * sizeof(int32_t)));
+        VNE_TRY_CUDA(ctx, dev_malloc((void**)&M->d_node_id, n * sizeof(int32_t)));
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, order_pin, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp2_pin, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         VNE_TRY_CUDA(ctx, launch_invert_perm(M->d_node_id, n, d_inv, st));
@@ -238,7 +236,7 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
         std::vector<int32_t> rp2_32(n + 1);
         for (int64_t i = 0; i <= n; i++) rp2_32[i] = (int32_t)rp2[i];
         int32_t* d_inv = upload(ctx, "asm.inv", inv);
-        VNE_TRY_CUDA(ctx, cudaMalloc(&M->d_node_id, n * sizeof(int32_t)));
+        VNE_TRY_CUDA(ctx, dev_malloc((void**)&M->d_node_id, n * sizeof(int32_t)));
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_node_id, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(M->d_rowptr, rp2_32.data(), (n + 1) * sizeof(int32_t),
                                           cudaMemcpyHostToDevice, st));
@@ -277,11 +275,6 @@ extern "C" vne_status vne_matrix_destroy(vne_matrix* M) {
     if (!M) return VNE_EINVAL;
     cudaSetDevice(M->ctx->device);
     if (M->ctx->stream) cudaStreamSynchronize(M->ctx->stream);
-    delete M->prob;
-    cudaFree(M->d_rowptr);
-    cudaFree(M->d_col);
-    cudaFree(M->d_vals);
-    cudaFree(M->d_node_id);
     delete M;
     return VNE_OK;
 }
@@ -606,3 +599,19 @@ extern "C" vne_status vne_ctx_stats(const vne_ctx* ctx, int64_t* launches, doubl
     return VNE_OK;
 }
 
+extern "C" vne_status vne_debug_fail_allocation(int64_t k) {
+    if (k < 0) return VNE_EINVAL;
+    fail_allocation_after(k);
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_debug_live_allocations(int64_t* device_buffers, int64_t* pinned_buffers) {
+    if (device_buffers) *device_buffers = live_device_buffers();
+    if (pinned_buffers) *pinned_buffers = live_pinned_buffers();
+    return VNE_OK;
+}
+
+extern "C" vne_status vne_debug_tensor_wait_limit(int64_t polls) {
+    set_tensor_wait_polls(polls);
+    return VNE_OK;
+}

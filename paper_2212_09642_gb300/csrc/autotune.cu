@@ -60,7 +60,7 @@ extern "C" vne_status vne_autotune(vne_matrix* M, int32_t k, int32_t steps, vne_
     // release the tuning block's workspace
     for (auto it = ctx->ws.begin(); it != ctx->ws.end();) {
         if (it->first.compare(0, 5, "tune.") == 0) {
-            cudaFree(it->second.ptr);
+            dev_free(it->second.ptr);
             it = ctx->ws.erase(it);
         } else {
             ++it;

@@ -75,8 +75,8 @@ extern "C" vne_status vne_batch_hutchinson(vne_matrix* const* mats, int32_t coun
         std::vector<int32_t> rp32(ntot + 1);
         for (int64_t i = 0; i <= ntot; i++) rp32[i] = (int32_t)rp[i];
         int32_t* drp = dev_copy(ctx, rp32);
-        int32_t* dci = dev_copy(ctx, ci);
         P->owned.push_back(drp);
+        int32_t* dci = dev_copy(ctx, ci);
         P->owned.push_back(dci);
         P->rowptr = drp;
         P->col = dci;

@@ -12,6 +12,52 @@
 
 namespace vne_engine {
 
+namespace {
+std::atomic<int64_t> g_live_dev{0}, g_live_pinned{0};
+std::atomic<int64_t> g_fail_countdown{0};  // > 0: the allocation that brings it to 0 fails
+
+bool inject_failure() {
+    int64_t v = g_fail_countdown.load();
+    while (v > 0) {
+        if (g_fail_countdown.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_dev++;
+    else *p = nullptr;
+    return e;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_dev--;
+}
+
+cudaError_t pinned_malloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) g_live_pinned++;
+    else *p = nullptr;
+    return e;
+}
+
+void pinned_free(void* p) {
+    if (!p) return;
+    cudaFreeHost(p);
+    g_live_pinned--;
+}
+
+int64_t live_device_buffers() { return g_live_dev.load(); }
+int64_t live_pinned_buffers() { return g_live_pinned.load(); }
+void fail_allocation_after(int64_t k) { g_fail_countdown.store(k); }
 
 void set_err(vne_ctx* ctx, const char* fmt, ...) {
     if (!ctx) return;
@@ -26,11 +72,11 @@ void set_err(vne_ctx* ctx, const char* fmt, ...) {
 void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero) {
     WsBuf& b = ctx->ws[name];
     if (b.bytes < bytes) {
-        if (b.ptr) cudaFree(b.ptr);
+        dev_free(b.ptr);
         b.ptr = nullptr;
         b.bytes = 0;
         size_t alloc = std::max<size_t>(bytes, 256);
-        VNE_TRY_CUDA(ctx, cudaMalloc(&b.ptr, alloc));
+        VNE_TRY_CUDA(ctx, dev_malloc(&b.ptr, alloc));
         VNE_TRY_CUDA(ctx, cudaMemsetAsync(b.ptr, 0, alloc, ctx->stream));
         b.bytes = alloc;
     }
@@ -41,10 +87,10 @@ void* ws_get(vne_ctx* ctx, const std::string& name, size_t bytes, bool zero) {
 void* pinned_bytes(vne_ctx* ctx, const std::string& name, size_t bytes) {
     auto& b = ctx->pinned[name];
     if (b.second < bytes) {
-        if (b.first) cudaFreeHost(b.first);
+        pinned_free(b.first);
         b.first = nullptr;
         b.second = 0;
-        if (cudaMallocHost(&b.first, bytes) != cudaSuccess) {
+        if (pinned_malloc(&b.first, bytes) != cudaSuccess) {
             b.first = nullptr;
             return nullptr;
         }
@@ -648,3 +694,11 @@ VNE_ENGINE_INSTANTIATE(float)
 VNE_ENGINE_INSTANTIATE(double)
 
 }  // namespace vne_engine
+
+vne_matrix::~vne_matrix() {
+    delete prob;
+    vne_engine::dev_free(d_rowptr);
+    vne_engine::dev_free(d_col);
+    vne_engine::dev_free(d_vals);
+    vne_engine::dev_free(d_node_id);
+}

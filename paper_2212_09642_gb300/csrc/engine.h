@@ -136,7 +136,12 @@ struct vne_matrix {
     int tuned_panel = 0, tuned_item_nnz = 0, tuned_variant = 0;
     bool tuned_interleave = false;
     int64_t maxdeg = 0;
+    ~vne_matrix();  // frees the device arrays and the cached schedule (engine.cu)
 };
+
+namespace vne_engine {
+void dev_free(void* p);
+}
 
 // ---------------------------------------------------------------------------
 // schedule ("plan") of a packed operator
@@ -169,19 +174,31 @@ struct Problem {
     bool owns_tables = true;   // false: the tables live in context workspace
     ~Problem() {
         if (owns_tables) {
-            cudaFree(d_segs);
-            cudaFree(d_items);
-            cudaFree(d_hubs);
-            cudaFree(d_cta_seg);
-            cudaFree(d_tiles);
+            vne_engine::dev_free(d_segs);
+            vne_engine::dev_free(d_items);
+            vne_engine::dev_free(d_hubs);
+            vne_engine::dev_free(d_cta_seg);
+            vne_engine::dev_free(d_tiles);
         }
-        for (void* p : owned) cudaFree(p);
+        for (void* p : owned) vne_engine::dev_free(p);
     }
     int ctas_per_panel() const { return (int)(items.size() / VNE_WARPS); }
     int tiles_per_panel() const { return (int)tiles.size(); }
 };
 
 namespace vne_engine {
+
+// Every device and pinned host allocation of the library goes through these
+// wrappers: they count live allocations (vne_debug_live_allocations) and,
+// for failure-injection tests, make the k-th next allocation fail as if the
+// memory were exhausted (vne_debug_fail_allocation).
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t pinned_malloc(void** p, size_t bytes);
+void pinned_free(void* p);
+int64_t live_device_buffers();
+int64_t live_pinned_buffers();
+void fail_allocation_after(int64_t k);  // 0: off
 
 struct Error {
     vne_status code;
@@ -245,12 +262,12 @@ extern const int kTileRows;
 // Work items and row tiles of one segment of a packed CSR.
 void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_t seg, int target, Problem& P);
 
-// Device copy of a host vector, owned by the caller (cudaFree).
+// Device copy of a host vector, owned by the caller (dev_free).
 template <typename T>
 T* dev_copy(vne_ctx* ctx, const std::vector<T>& v) {
     T* d = nullptr;
     size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
-    VNE_TRY_CUDA(ctx, cudaMalloc(&d, bytes));
+    VNE_TRY_CUDA(ctx, dev_malloc((void**)&d, bytes));
     if (!v.empty())
         VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     return d;

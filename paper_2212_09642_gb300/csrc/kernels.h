@@ -294,6 +294,9 @@ cudaError_t launch_apply(const T* In, int kin, const double* M, int kout, const 
                          double coef, int* err, cudaStream_t);
 cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout, const float* In2, float* Out, int ks,
                              int n, double coef, int* err, cudaStream_t st);
+// Poll limit of the main-loop mbarrier waits of the tcgen05 kernels (< 0:
+// the built-in limit); for failure-injection tests only.
+void set_tensor_wait_polls(int64_t polls);
 // Pivoted Cholesky of a k x k SPD matrix G (FP64) with rank cut-off tol * max diag.
 // Writes Minv [k][k] (rows permuted: Q = Y Minv spans range(Y)) and rank.
 // work: k * k + k doubles (R and 1 / R_jj), piv: k ints (device).  pivot =

@@ -32,7 +32,7 @@ void device_colorings(vne_matrix* M, std::vector<ColorJob>& jobs) {
     vne_ctx* ctx = M->ctx;
     const int64_t n = M->n;
     const int nj = (int)jobs.size();
-    if (!ctx->pinned_ctr) VNE_TRY_CUDA(ctx, cudaMallocHost(&ctx->pinned_ctr, 8 * 8 * sizeof(int32_t)));
+    if (!ctx->pinned_ctr) VNE_TRY_CUDA(ctx, pinned_malloc((void**)&ctx->pinned_ctr, 8 * 8 * sizeof(int32_t)));
     VNE_REQUIRE(ctx, nj >= 1 && nj <= 8, VNE_EINVAL, "1..8 colourings at once");
     while ((int)ctx->color_streams.size() < nj - 1) {
         cudaStream_t sx = nullptr;

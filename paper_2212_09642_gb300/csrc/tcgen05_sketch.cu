@@ -34,7 +34,8 @@
 //     threads add that accumulator into FP32 registers (tcgen05.ld) while
 //     the next group runs into the other one.
 // Every wait is bounded: a wait that runs out sets *err, and the CTA stops,
-// waits (bounded) for its copies and MMAs, frees its TMEM and returns.
+// waits for its copies and (bounded) for the last MMA commit on each
+// mbarrier, frees its TMEM and returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -89,9 +90,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // Bounded wait for the completion of the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls = kWaitPolls) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitPolls; it++) {
+    for (uint32_t it = 0; it < polls; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -102,6 +103,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+// After a wait gave up: let every MMA already issued finish before the TMEM
+// is released.  Work unit t commits to mbarrier t & 1 (phase t >> 1), and a
+// unit is committed only after the previous commit to the same barrier has
+// completed, so each barrier has at most one phase outstanding: that of the
+// last unit committed to it.  The waits use the full poll limit.
+__device__ __forceinline__ void drain_commits(uint64_t* mbar, int committed) {
+    for (int b = 0; b < 2; b++) {
+        const int t = ((committed - 1) & 1) == b ? committed - 1 : committed - 2;
+        if (t >= 0) mbar_wait(mbar + b, (uint32_t)(t >> 1) & 1u);
+    }
 }
 
 // 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
@@ -163,7 +176,7 @@ __device__ __forceinline__ void convert_slab(const float* raw, int k, unsigned c
 template <int KS, bool SAME>
 __global__ void __launch_bounds__(256, 1)
     k_gram_tc5(const float* __restrict__ X, int kx, const float* __restrict__ Y, int ky, int n, int rows_per_chunk,
-               double* __restrict__ part, int* __restrict__ err) {
+               double* __restrict__ part, int* __restrict__ err, uint32_t polls) {
     using L = GramSmem<SAME>;
     constexpr int V = KS / 4;  // 16-byte pieces per row of one panel
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -243,15 +256,17 @@ __global__ void __launch_bounds__(256, 1)
     };
     int next_flush = 0;  // first group not yet added into acc
     bool failed = false;
+    int committed = nslab;  // slabs whose MMAs were issued
     for (int s = 0; s < L::kStages - 1; s++) issue(s);
     for (int s = 0; s < nslab; s++) {
         // slabs s .. s + kStages - 2 are in flight: wait for slab s
         asm volatile("cp.async.wait_group %0;" ::"n"(L::kStages - 2) : "memory");
         const int b = s & 1;
         // the MMAs of slab s - 2 read operand buffer b
-        const bool ready = s < 2 || mbar_wait(mbar + b, (uint32_t)((s - 2) >> 1) & 1u);
+        const bool ready = s < 2 || mbar_wait(mbar + b, (uint32_t)((s - 2) >> 1) & 1u, polls);
         if (__syncthreads_or(!ready)) {  // also: slab s has landed for every thread's copies
             failed = true;
+            committed = s;
             break;
         }
         // the groups whose last slab is <= s - 2 are complete
@@ -293,16 +308,12 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (nslab > 0 && !failed) {
         const int sl = nslab - 1;
-        const bool done = mbar_wait(mbar + (sl & 1), (uint32_t)(sl >> 1) & 1u);
+        const bool done = mbar_wait(mbar + (sl & 1), (uint32_t)(sl >> 1) & 1u, polls);
         failed = __syncthreads_or(!done);
     }
     if (failed) {
         if (tid == 0) atomicExch(err, 1);
-        // let the MMAs already issued finish before the TMEM is released
-        if (nslab > 0) {
-            mbar_wait(mbar, 0u);  // bounded; the outcome is already an error
-            mbar_wait(mbar + 1, 0u);
-        }
+        drain_commits(mbar, committed);  // bounded; the outcome is already an error
     } else {
         const int ngroups = (nslab + kGroup - 1) / kGroup;
         while (next_flush < ngroups) flush(next_flush++);
@@ -326,13 +337,18 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
+// Poll limit of the main-loop waits of both kernels (kWaitPolls unless a
+// failure-injection test lowered it); the drain after a failure always uses
+// kWaitPolls.
+uint32_t g_main_polls = kWaitPolls;
+
 template <int KS, bool SAME>
 cudaError_t gram_tc5_launch(const float* X, int kx, const float* Y, int ky, int n, int rpc, int chunks, double* part,
                             int* err, cudaStream_t st) {
     const int smem = GramSmem<SAME>::kBytes;
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc5<KS, SAME>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc5<KS, SAME><<<chunks, 256, smem, st>>>(X, kx, Y, ky, n, rpc, part, err);
+    k_gram_tc5<KS, SAME><<<chunks, 256, smem, st>>>(X, kx, Y, ky, n, rpc, part, err, g_main_polls);
     return cudaGetLastError();
 }
 
@@ -388,7 +404,8 @@ constexpr int kApplyChunk = 32;  // K columns per unit
 template <int KS>
 __global__ void __launch_bounds__(256, 1)
     k_apply_tc5(const float* __restrict__ In, int kin, const double* __restrict__ Mat, int kout,
-                const float* __restrict__ In2, float* __restrict__ Out, int n, double coef, int* __restrict__ err) {
+                const float* __restrict__ In2, float* __restrict__ Out, int n, double coef, int* __restrict__ err,
+                uint32_t polls) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nk = (kin + kApplyChunk - 1) / kApplyChunk;  // K chunks
     const int kout16 = (kout + 15) & ~15;
@@ -497,15 +514,17 @@ __global__ void __launch_bounds__(256, 1)
     };
 
     bool failed = false;
+    int committed = nunits;  // units whose MMAs were issued
     int next_epi = 0;
     float4 cur[4], nxt[4];
     if (nunits > 0) load_unit(0, cur);
     for (int u = 0; u < nunits; u++) {
         if (u + 1 < nunits) load_unit(u + 1, nxt);
         const int b = u & 1;
-        const bool ready = u < 2 || mbar_wait(mbar + b, (uint32_t)((u - 2) >> 1) & 1u);
+        const bool ready = u < 2 || mbar_wait(mbar + b, (uint32_t)((u - 2) >> 1) & 1u, polls);
         if (__syncthreads_or(!ready)) {
             failed = true;
+            committed = u;
             break;
         }
         // tiles whose last unit is <= u - 2 are complete
@@ -534,15 +553,12 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (nunits > 0 && !failed) {
         const int ul = nunits - 1;
-        const bool done = mbar_wait(mbar + (ul & 1), (uint32_t)(ul >> 1) & 1u);
+        const bool done = mbar_wait(mbar + (ul & 1), (uint32_t)(ul >> 1) & 1u, polls);
         failed = __syncthreads_or(!done);
     }
     if (failed) {
         if (tid == 0) atomicExch(err, 1);
-        if (nunits > 0) {
-            mbar_wait(mbar, 0u);  // bounded; the outcome is already an error
-            mbar_wait(mbar + 1, 0u);
-        }
+        drain_commits(mbar, committed);  // bounded; the outcome is already an error
     } else {
         while (next_epi < my_tiles) epilogue(next_epi++);
     }
@@ -573,7 +589,7 @@ cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout
     if (ks == KSV) {                                                                                          \
         e = cudaFuncSetAttribute(k_apply_tc5<KSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);         \
         if (e != cudaSuccess) return e;                                                                       \
-        k_apply_tc5<KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef, err);                   \
+        k_apply_tc5<KSV><<<grid, 256, smem, st>>>(In, kin, M, kout, In2, Out, n, coef, err, g_main_polls);     \
         return cudaGetLastError();                                                                            \
     }
     VNE_APPLY5(8)
@@ -583,5 +599,8 @@ cudaError_t launch_apply_tc5(const float* In, int kin, const double* M, int kout
     return cudaErrorInvalidValue;
 }
 
+void set_tensor_wait_polls(int64_t polls) {
+    g_main_polls = polls < 0 ? kWaitPolls : (uint32_t)std::min<int64_t>(polls, kWaitPolls);
+}
 
 }  // namespace vne

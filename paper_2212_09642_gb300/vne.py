@@ -123,6 +123,9 @@ def _declare(lib):
         "vne_ctx_last_poly_dim": (st, [_P, _PI32]),
         "vne_quadrature_bounds": (st, [_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P, _P, _P]),
+        "vne_debug_fail_allocation": (st, [ctypes.c_int64]),
+        "vne_debug_live_allocations": (st, [_PI64, _PI64]),
+        "vne_debug_tensor_wait_limit": (st, [ctypes.c_int64]),
         "vne_measure_gather": (st, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_int32, _PD]),
     }
@@ -158,7 +161,8 @@ _SIGNATURES = ["vne_options_default", "vne_version", "vne_ctx_create", "vne_ctx_
                "vne_batch_hutchinson", "vne_ctx_profile", "vne_ctx_stats",
                "vne_ctx_graph_stats", "vne_ctx_last_steps", "vne_ctx_last_poly_dim", "vne_measure_gather", "vne_quadform_noalloc", "vne_autotune", "vne_quadform_rational",
                "vne_server_create", "vne_server_destroy", "vne_server_submit", "vne_server_step",
-               "vne_server_result", "vne_server_info"]
+               "vne_server_result", "vne_server_info", "vne_debug_fail_allocation", "vne_debug_live_allocations",
+               "vne_debug_tensor_wait_limit"]
 
 
 def _check(status, ctx=None):
@@ -505,6 +509,23 @@ def vne_ctx_last_poly_dim(ctx):
     k = ctypes.c_int32()
     _check(load().vne_ctx_last_poly_dim(ctx, ctypes.byref(k)), ctx)
     return k.value
+
+
+def vne_debug_fail_allocation(k):
+    """Make the k-th allocation from now on fail (VNE_ENOMEM); 0 switches it off."""
+    _check(load().vne_debug_fail_allocation(int(k)))
+
+
+def vne_debug_live_allocations():
+    """(device buffers, pinned host buffers) the library currently holds."""
+    d, h = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().vne_debug_live_allocations(ctypes.byref(d), ctypes.byref(h)))
+    return d.value, h.value
+
+
+def vne_debug_tensor_wait_limit(polls):
+    """Poll limit of the tcgen05 kernels' main-loop waits (< 0: the built-in one)."""
+    _check(load().vne_debug_tensor_wait_limit(int(polls)))
 
 
 def vne_measure_gather(ctx, table_bytes, row_bytes, gathers, stream_bytes=0, reps=3):

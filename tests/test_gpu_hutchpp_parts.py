@@ -9,7 +9,9 @@ FP64 oracle on the same probes and step counts.
 * psi(g'_j) per projected Hutchinson vector (these depend only on span(Q));
 * the estimate.
 Tolerances: 1e-10 (FP64 path, full reorthogonalisation on both sides) and
-1e-5 (mixed path: FP32 vectors, no reorthogonalisation on both sides).
+1e-5 (mixed path: FP32 vectors, no reorthogonalisation on both sides) for
+every quadratic form and the estimate; the sketch columns, vectors recovered
+from m + 1 Lanczos slots, to 1e-10 (FP64) and 5e-5 (FP32) of their norm.
 Also: the staged entry points split over column ranges reproduce the
 one-call estimate column for column."""
 import numpy as np
@@ -44,8 +46,9 @@ def test_hutchpp_parts_match_oracle(vctx, name, make, Nr, NH, m, fp64, tol):
     finally:
         vne.vne_matrix_destroy(mat)
     Yr = rp["Y"]
+    tol_vec = 1e-10 if fp64 else 5e-5
     for j in range(Nr):
-        assert np.linalg.norm(Y[:, j] - Yr[:, j]) <= tol * np.linalg.norm(Yr[:, j]), j
+        assert np.linalg.norm(Y[:, j] - Yr[:, j]) <= tol_vec * np.linalg.norm(Yr[:, j]), j
     assert r == rp["Q"].shape[1] == int(parts[2])
     assert np.array_equal(piv[:r], rp["pivots"])
     assert np.all(piv[r:] == -1)
