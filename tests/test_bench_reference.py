@@ -24,3 +24,8 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["n"] == 3000
+    # the record says how the number was made: a sample scaled to the estimate
+    cb = d["cpu_baseline"]
+    assert cb["extrapolated"] is True and cb["sampled_krylov_runs"] == 2
+    assert cb["krylov_runs_per_estimate"] == 300 and cb["scale_factor"] > 1
+    assert cb["threads"]["krylov"] == 1 and cb["measured_seconds"] > 0
