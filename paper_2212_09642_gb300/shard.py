@@ -1,4 +1,5 @@
-"""Probe-column sharding of one Hutchinson estimate over a process group.
+"""Probe-column sharding of one Hutchinson or Hutch++ estimate over a process
+group.
 
 The quadratic forms v_l^T f(A) v_l of a trace estimate are independent of one
 another (each probe builds its own Krylov space; Section 4, remark after the
@@ -10,6 +11,13 @@ sum of their psi values, then the sum of squared deviations from the common
 mean).  The union of the ranges is exactly the probe set of a single run
 with the same seed, so the sharded estimate is the single-run estimate up to
 the order of the final additions.
+
+Hutch++ (eq. Hutch++_formula) has one exchange step in the middle: every
+rank computes its range of the sketch columns f(A) omega_j (stage 1), the
+ranks all-gather the sketch, every rank forms the same Q = orth(Y) and
+G' = (I - Q Q^T) G from the whole sketch (deterministic kernels, identical
+inputs) and evaluates its range of the N_r + N_H quadratic forms of
+[Q | G'] (stage 2); two scalars are all-reduced at the end.
 """
 from __future__ import annotations
 
@@ -83,3 +91,71 @@ def hutchinson(ctx, mat, num_vectors: int, krylov_steps: int, seed: int, opt=Non
         _, _, psi = vne.vne_entropy_hutchinson(ctx, mat, count, krylov_steps, seed, opt=o, want_psi=True)
     mean, se, _ = combine(psi, group)
     return mean, se, count
+
+
+def _all_gather_columns(Y, total_cols, group):
+    """Concatenate the ranks' column blocks [n, k_r] (in rank order) into the
+    whole [n, total_cols] block on every rank.  Blocks are padded to the
+    largest k_r so that every rank sends the same shape."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    kmax = max(probe_range(total_cols, world, r)[1] for r in range(world))
+    nccl = dist.get_backend(group) == "nccl"
+    dev = f"cuda:{torch.cuda.current_device()}" if nccl else "cpu"
+    t = torch.as_tensor(Y, device=dev)
+    n = t.shape[0]
+    pad = torch.zeros((n, kmax), dtype=t.dtype, device=dev)
+    if t.shape[1]:
+        pad[:, :t.shape[1]] = t
+    outs = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(outs, pad, group=group)
+    cols = [outs[r][:, :probe_range(total_cols, world, r)[1]] for r in range(world)]
+    return torch.cat(cols, dim=1).contiguous()
+
+
+def hutchpp(ctx, mat, sketch_cols: int, hutch_vectors: int, krylov_steps: int, seed: int, fp64: bool, opt=None,
+            group=None, sketch_fn=None, project_fn=None):
+    """Hutch++ estimate of S(rho) split over the ranks of `group` (the default
+    group when torch.distributed is initialised, else one rank).
+
+    Stage 1: this rank's range of the N_r sketch columns; all-gather; stage 2:
+    this rank's range of the N_r + N_H quadratic forms; all-reduce of the
+    low-rank and residual sums.  ``sketch_fn(c0, k)`` and
+    ``project_fn(Y, c0, k)`` default to the library's stages
+    (vne_hutchpp_sketch, vne_hutchpp_project); they can be replaced by another
+    evaluator with the same contract.  Returns (estimate, rank of Q, the
+    quadratic forms this rank evaluated)."""
+    import torch.distributed as dist
+
+    from . import vne
+    if dist.is_available() and dist.is_initialized():
+        world, rank = dist.get_world_size(group), dist.get_rank(group)
+    else:
+        world, rank = 1, 0
+    Nr, NH = int(sketch_cols), int(hutch_vectors)
+    if sketch_fn is None:
+        def sketch_fn(c0, k):
+            if k == 0:
+                return np.zeros((vne.vne_matrix_info(mat)[0], 0), dtype=np.float64 if fp64 else np.float32)
+            return vne.vne_hutchpp_sketch(ctx, mat, c0, k, krylov_steps, seed, fp64, opt=opt)
+    if project_fn is None:
+        def project_fn(Y, c0, k):
+            return vne.vne_hutchpp_project(ctx, mat, Y, Nr, NH, krylov_steps, seed, col_begin=c0, ncols=k, opt=opt)
+    c0, k = probe_range(Nr, world, rank)
+    Y = sketch_fn(c0, k)  # [n, k]
+    if world > 1:
+        Yall = _all_gather_columns(Y, Nr, group)
+        Yall = Yall if Yall.is_cuda else Yall.numpy()
+    else:
+        Yall = Y
+    q0, qk = probe_range(Nr + NH, world, rank)
+    psi, piv, r = project_fn(Yall, q0, qk)
+    psi = np.asarray(psi, dtype=np.float64)
+    idx = np.arange(q0, q0 + qk)
+    low = math.fsum(psi[idx < r])
+    res = math.fsum(psi[idx >= Nr])
+    if world > 1:
+        low, res = _allreduce_sum([low, res], group)
+    est = low + (res / NH if NH > 0 else 0.0)
+    return est, int(r), psi

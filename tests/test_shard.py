@@ -79,3 +79,75 @@ def test_gloo_two_ranks_match_single_run(total):
         assert abs(se - ref_se) <= 1e-10 * max(ref_se, 1e-300)
     assert res[0][2] == res[1][2] and res[0][0] == res[1][0]  # same result on every rank
     assert res[0][4] + res[1][4] == total
+
+
+# ---- Hutch++ split over ranks: the host logic with the oracle as evaluator ----
+
+def _oracle_stages(A, Nr, NH, m, seed):
+    """Stage functions with the contract of the library's two stages, written
+    with the oracle: the sketch columns f(A) omega_j, and from the whole
+    sketch Q = orth(Y), G' and the quadratic forms of a column range."""
+    from oracle import density, estimators, krylov, rng
+    nA = density.gershgorin_norm(A)
+    n = A.shape[0]
+
+    def sketch(c0, k):
+        X = rng.rademacher(seed, n, c0, k)
+        cols = [krylov.lanczos_fmatvec(A, X[:, j], m, reorth="full", norm_A=nA) for j in range(k)]
+        return np.column_stack(cols) if k else np.zeros((n, 0))
+
+    def project(Y, c0, k):
+        Y = np.asarray(Y, dtype=np.float64)
+        Q, piv = estimators.orthonormal_range(Y, return_pivots=True)
+        r = Q.shape[1]
+        G = rng.rademacher(seed, n, Nr, NH)
+        Gp = G - Q @ (Q.T @ G)
+        psi = []
+        for i in range(c0, c0 + k):
+            if i < Nr:
+                psi.append(krylov.lanczos_quadform(A, Q[:, i], m, reorth="full", norm_A=nA)[0] if i < r else 0.0)
+            else:
+                psi.append(krylov.lanczos_quadform(A, Gp[:, i - Nr], m, reorth="full", norm_A=nA)[0])
+        pv = np.full(Nr, -1, dtype=np.int32)
+        pv[:r] = piv
+        return np.array(psi), pv, r
+
+    return sketch, project
+
+
+def _hpp_worker(rank, world, port, Nr, NH, seed, m, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import density
+        g = graphs.barabasi_albert(400, 3, 8)
+        A, _ = density.density_matrix(g)
+        sk, pr = _oracle_stages(A, Nr, NH, m, seed)
+        est, r, psi = shard.hutchpp(None, None, Nr, NH, m, seed, True, sketch_fn=sk, project_fn=pr)
+        out[rank] = (est, r, len(psi))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,Nr,NH", [(2, 8, 6), (3, 2, 4)])
+def test_gloo_hutchpp_matches_single_run(world, Nr, NH):
+    """world-size 2 and 3 gloo groups (with 3 ranks and N_r = 2 one rank has
+    no sketch column): the sketch gathered from the ranks' column ranges, the
+    quadratic forms split over the ranks and the two sums all-reduced give the
+    oracle's one-process Hutch++ estimate."""
+    from oracle import density, estimators
+    seed, m = 17, 14
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_hpp_worker, args=(world, _free_port(), Nr, NH, seed, m, out), nprocs=world,
+                       start_method="spawn", join=True)
+    g = graphs.barabasi_albert(400, 3, 8)
+    A, _ = density.density_matrix(g)
+    ref, rp = estimators.hutchpp(A, Nr, NH, m, seed=seed, reorth="full", return_parts=True)
+    res = [out[r] for r in range(world)]
+    for est, r, _ in res:
+        assert r == rp["Q"].shape[1]
+        assert abs(est - ref) <= 1e-13 * abs(ref)
+    assert sum(c for _, _, c in res) == Nr + NH
+    assert len({e for e, _, _ in res}) == 1  # the same estimate on every rank
