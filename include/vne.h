@@ -82,7 +82,7 @@ typedef struct vne_options {
     double cg_tol;        /* rational mode: relative residual (default 1e-8) */
     double breakdown_tol; /* Lanczos stops when beta_j <= tol * ||A||_G;
                              0 = default (1e-13 FP64, 1e-10 FP32) */
-    int32_t step_variant; /* SpMM step-kernel variant 0..7 (occupancy,
+    int32_t step_variant; /* SpMM step-kernel variant 0..13 (occupancy,
                              gathers in flight, shared-memory staging, L2
                              cache policy of the gathers), -1 = auto */
     int32_t interleave;   /* 1: launch step and update panel by panel so the
@@ -114,7 +114,10 @@ typedef struct vne_options {
                                 choice, Section 3.2): Box-Muller on the same
                                 counters as the Rademacher entries, see
                                 vne_gaussian_probes; 0 (default): Rademacher */
-    int32_t reserved;
+    int32_t items_per_warp; /* SpMM step kernel: work items a warp takes in
+                               turn (1, 2 or 4; a CTA covers 8 x this many
+                               items, so its reduction tail is amortised over
+                               more rows), 0 = auto */
 } vne_options;
 
 /* Fill *opt with the defaults described above. */

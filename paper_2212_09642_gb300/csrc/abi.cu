@@ -265,6 +265,7 @@ extern "C" vne_status vne_create_density_matrix(vne_ctx* ctx, int64_t n, const i
             M->tuned_item_nnz = it->second[1];
             M->tuned_variant = it->second[2];
             M->tuned_interleave = it->second[3] != 0;
+            M->tuned_ipw = it->second[4];
         }
     }
     *out = M.release();

@@ -152,7 +152,9 @@ void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_
     // every item holds at most `target` nonzeros: short rows are packed into
     // runs (at most 64 rows), rows longer than `target` are split into chunks
     const int64_t chunk = std::max(target, 32);
-    const int max_rows = 64;
+    // at most 64 rows per item, 128 for items of 1024 nonzeros or more (fewer
+    // CTAs, so less of the per-CTA reduction tail per row)
+    const int max_rows = target >= 1024 ? kItemMaxRows : 64;
     const size_t first_item = P.items.size();
     SegInfo& sg0 = P.segs[seg];
     sg0.hub_begin = (int32_t)P.hubs.size();
@@ -186,13 +188,13 @@ void plan_segment(const int64_t* rowptr, int32_t row_begin, int32_t rows, int32_
         blk_nnz += deg;
     }
     flush();
-    while ((P.items.size() - first_item) % VNE_WARPS) P.items.push_back(WorkItem{0, 0, 0, 0});
+    while ((P.items.size() - first_item) % ((size_t)VNE_WARPS * P.ipw)) P.items.push_back(WorkItem{0, 0, 0, 0});
     for (size_t i = first_item; i < P.items.size(); i++)
         P.stage_nnz = std::max<int32_t>(P.stage_nnz, P.items[i].nnz_end - P.items[i].nnz_begin);
     SegInfo& sg = P.segs[seg];
     sg.hub_count = (int32_t)P.hubs.size() - sg.hub_begin;
-    sg.cta_begin = (int32_t)(first_item / VNE_WARPS);
-    sg.cta_count = (int32_t)((P.items.size() - first_item) / VNE_WARPS);
+    sg.cta_begin = (int32_t)(first_item / ((size_t)VNE_WARPS * P.ipw));
+    sg.cta_count = (int32_t)((P.items.size() - first_item) / ((size_t)VNE_WARPS * P.ipw));
     for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
     sg.tile_begin = (int32_t)P.tiles.size();
     // row tiles of the streaming kernels: 4096 rows, fewer for small
@@ -224,15 +226,18 @@ Sched resolve_sched(const vne_matrix* M, const vne_options* o) {
     s.item_nnz = (o && o->item_nnz > 0) ? o->item_nnz : (M->tuned ? M->tuned_item_nnz : 256);
     s.variant = (o && o->step_variant >= 0) ? o->step_variant : (M->tuned ? M->tuned_variant : 4);
     if (M->fp64) s.variant = 0;
+    s.ipw = (o && o->items_per_warp > 0) ? o->items_per_warp : (M->tuned ? M->tuned_ipw : 1);
     s.interleave = (o && o->interleave >= 0) ? (o->interleave != 0) : (M->tuned ? M->tuned_interleave : false);
     s.graph = !(o && o->graphs == 0);
     return s;
 }
 
 Problem* matrix_problem(vne_matrix* M, const vne_options* opt) {
-    int target = resolve_sched(M, opt).item_nnz;
+    const Sched sc = resolve_sched(M, opt);
+    int target = sc.item_nnz;
     double taurel = (opt && opt->breakdown_tol > 0) ? opt->breakdown_tol : default_tau(M->fp64);
-    if (M->prob && M->prob_item_nnz == target && M->prob->segs[0].tau == taurel * M->normM) return M->prob;
+    if (M->prob && M->prob_item_nnz == target && M->prob->ipw == sc.ipw && M->prob->segs[0].tau == taurel * M->normM)
+        return M->prob;
     delete M->prob;
     M->prob = nullptr;
     std::unique_ptr<Problem> P(new Problem());
@@ -245,6 +250,7 @@ Problem* matrix_problem(vne_matrix* M, const vne_options* opt) {
     P->col = M->d_col;
     P->vals = M->d_vals;
     P->node_id = M->d_node_id;
+    P->ipw = sc.ipw;
     SegInfo s{};
     s.row_begin = 0;
     s.rows = (int32_t)M->n;
@@ -350,6 +356,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     p.hub_cnt = hub_cnt;
     p.hub_dot = hub_dot;
     p.stage_nnz = std::max(P.stage_nnz, 1);
+    p.ipw = P.ipw;
     p.tiles = P.d_tiles;
     p.tiles_per_panel = tiles;
     p.u = u;
@@ -652,6 +659,7 @@ void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* ou
     p.hub_cnt = ws_get_t<uint32_t>(ctx, "op.hub_cnt", (size_t)panels * std::max(nh, 1));
     p.hub_dot = ws_get_t<double>(ctx, "hub_dot", (size_t)panels * std::max(nh, 1) * ks);
     p.stage_nnz = std::max(P.stage_nnz, 1);
+    p.ipw = P.ipw;
     p.tiles = P.d_tiles;
     p.tiles_per_panel = tiles;
     p.first = (shift == 0.0) ? 1 : 0;

@@ -89,7 +89,7 @@ struct vne_ctx {
             return std::tie(n, nnz, maxdeg, fp64, pattern) < std::tie(o.n, o.nnz, o.maxdeg, o.fp64, o.pattern);
         }
     };
-    std::map<TuneKey, std::array<int, 4>> tune_cache;
+    std::map<TuneKey, std::array<int, 5>> tune_cache;
     // CUDA graphs of step loops, keyed by the launch parameters of the loop;
     // a loop is captured the second time its key is seen
     struct LoopGraph {
@@ -133,7 +133,7 @@ struct vne_matrix {
     Problem* prob = nullptr;        // cached schedule
     int prob_item_nnz = -1;
     bool tuned = false;             // autotuned schedule (vne_autotune)
-    int tuned_panel = 0, tuned_item_nnz = 0, tuned_variant = 0;
+    int tuned_panel = 0, tuned_item_nnz = 0, tuned_variant = 0, tuned_ipw = 1;
     bool tuned_interleave = false;
     int64_t maxdeg = 0;
     ~vne_matrix();  // frees the device arrays and the cached schedule (engine.cu)
@@ -164,6 +164,7 @@ struct Problem {
     std::vector<RowTile> tiles;
     int32_t hub_slots = 0;
     int32_t stage_nnz = 0;   // largest item (nonzeros)
+    int32_t ipw = 1;         // work items per warp (CTA = VNE_WARPS * ipw items)
     // device copies (owned)
     SegInfo* d_segs = nullptr;
     WorkItem* d_items = nullptr;
@@ -182,7 +183,7 @@ struct Problem {
         }
         for (void* p : owned) vne_engine::dev_free(p);
     }
-    int ctas_per_panel() const { return (int)(items.size() / VNE_WARPS); }
+    int ctas_per_panel() const { return (int)(items.size() / ((size_t)VNE_WARPS * ipw)); }
     int tiles_per_panel() const { return (int)tiles.size(); }
 };
 
@@ -278,7 +279,7 @@ double default_tau(bool fp64);
 int default_item_nnz(const vne_options* o);
 
 struct Sched {
-    int ks, item_nnz, variant;
+    int ks, item_nnz, variant, ipw;
     bool interleave;
     bool graph;
 };

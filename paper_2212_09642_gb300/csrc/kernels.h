@@ -57,6 +57,7 @@ struct StepParams {
     const RowTile* tiles;
     int32_t tiles_per_panel;
     int32_t stage_nnz;  // largest work item in nonzeros (staged variants)
+    int32_t ipw;        // work items per warp (a CTA covers VNE_WARPS * ipw consecutive items)
     int32_t panel_base; // first panel of this launch (per-panel launches)
     int32_t first;   // j == 1: no previous vector
     int32_t renorm;  // update kernel: only recompute the norm of w_next in place
@@ -105,7 +106,12 @@ struct RecoverParams {
 template <typename T> cudaError_t launch_start(const StartParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T>
 cudaError_t launch_step(const StepParams<T>&, int ks, int panels, bool valued, int variant, cudaStream_t);
-constexpr int kStepVariants = 8;
+constexpr int kStepVariants = 14;
+// A work item spans at most kItemMaxRows rows (64 for items of fewer than
+// 1024 nonzeros); the staged variants keep its row offsets in kStageRp ints
+// of shared memory per warp.
+constexpr int kItemMaxRows = 128;
+constexpr int kStageRp = kItemMaxRows + 4;
 template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
 // The first two passes of launch_reorth only: coef[i][col] = sig_i^2

@@ -48,11 +48,21 @@ __device__ bool last_cta_reduce(const double* part, uint32_t* counter, int panel
     __threadfence();
     constexpr int NS = VNE_THREADS / W;
     const int c = threadIdx.x % W, s = threadIdx.x / W;
-    double acc = 0.0;
-    if (s < NS)
-        for (int i = s; i < count; i += NS)
-            acc += ld_cg(&part[((size_t)panel * nparts + begin + i) * W + c]);
-    red[threadIdx.x] = acc;
+    // four independent accumulators, so that four loads are in flight at
+    // once (the order of the additions is still fixed)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (s < NS) {
+        const double* src = part + ((size_t)panel * nparts + begin) * W + c;
+        int i = s;
+        for (; i + 3 * NS < count; i += 4 * NS) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc[u] += ld_cg(src + (size_t)(i + u * NS) * W);
+        }
+#pragma unroll
+        for (int u = 0; u < 3; u++)
+            if (i + u * NS < count) acc[u] += ld_cg(src + (size_t)(i + u * NS) * W);
+    }
+    red[threadIdx.x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
     if (threadIdx.x < W) {
         double t = 0.0;
@@ -437,8 +447,13 @@ __global__ void __launch_bounds__(VNE_THREADS, 3) k_start_center(StartParams<T> 
 // copy the work item's column indices and row offsets into shared memory
 // with coalesced loads first, so each gather waits on a shared-memory read
 // instead of a dependent global index load (dynamic smem: item_nnz ints per
-// warp + 65 row offsets per warp).
-template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE, int HINT = 0>
+// warp + kStageRp row offsets per warp; a warp takes p.ipw items in turn, so
+// a CTA covers VNE_WARPS * ipw items and its reduction tail is amortised over
+// them), PTAIL = issue a row's last (fewer than
+// UNR) gathers at once under predicates instead of one per latency round,
+// and load the row's own entries of w_j and w_{j-1} before its gathers.
+template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE, int HINT = 0,
+          bool PTAIL = false>
 __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;  // lanes per row
@@ -466,10 +481,9 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     for (int q = 0; q < CPL; q++) dot[q] = (T)0;
     const uint64_t pol = HINT ? policy_evict_last() : 0ull;
 
-    auto epilogue = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL]) {
-        T x[CPL], xp[CPL], uu[CPL];
-        load_lane(W + (size_t)r * KS + cofs, x);
-        if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+    auto epilogue_x = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL], const T (&x)[CPL],
+                          const T (&xp)[CPL]) {
+        T uu[CPL];
 #pragma unroll
         for (int q = 0; q < CPL; q++) {
             T ax = VALUED ? acc[q] : ((T)deg * x[q] - acc[q]);
@@ -481,12 +495,20 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
         if (STREAM) store_lane_stream(U + (size_t)r * KS + cofs, uu);
         else store_lane(U + (size_t)r * KS + cofs, uu);
     };
+    auto epilogue = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL]) {
+        T x[CPL], xp[CPL];
+        load_lane(W + (size_t)r * KS + cofs, x);
+        if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+        epilogue_x(r, acc, deg, dt, x, xp);
+    };
 
-    const WorkItem it = p.items[(size_t)cta * VNE_WARPS + warp];
     extern __shared__ int32_t s_stage[];
-    int32_t* s_col = s_stage + warp * (p.stage_nnz + 68);
+    int32_t* s_col = s_stage + warp * (p.stage_nnz + kStageRp);
     int32_t* s_rp = s_col + p.stage_nnz;
+    for (int ii = 0; ii < p.ipw; ii++) {
+    const WorkItem it = p.items[((size_t)cta * p.ipw + ii) * VNE_WARPS + warp];
     int nb_item = it.nnz_begin;
+    if (STAGE && ii > 0) __syncwarp();  // the previous item's reads of the staging are done
     if (STAGE && it.rows != 0) {
         const int cnt = it.nnz_end - it.nnz_begin;
         for (int i = lane; i < cnt; i += 32) s_col[i] = __ldcs(p.col + nb_item + i);
@@ -499,6 +521,11 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
         for (int r = it.row + g; r < it.row + it.rows; r += G) {
             const int kb = STAGE ? s_rp[r - it.row] : p.rowptr[r];
             const int ke = STAGE ? s_rp[r - it.row + 1] : p.rowptr[r + 1];
+            T x[CPL], xp[CPL];
+            if (PTAIL) {  // the row's own entries, in flight while it gathers
+                load_lane(W + (size_t)r * KS + cofs, x);
+                if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+            }
             T acc[CPL];
 #pragma unroll
             for (int q = 0; q < CPL; q++) acc[q] = (T)0;
@@ -525,15 +552,44 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
                         for (int q = 0; q < CPL; q++) acc[q] += a[u][q] + a[u + 1][q];
                 }
             }
-            for (; k < ke; k++) {
-                int c0 = colidx(k);
-                T a0[CPL];
-                load_lane_hint<HINT>(W + (size_t)c0 * KS + cofs, a0, pol);
-                T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
+            if (PTAIL) {
+                if (k < ke) {  // the last ke - k < UNR gathers, all in flight at once
+                    T a[UNR][CPL];
 #pragma unroll
-                for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
+                    for (int u = 0; u < UNR; u++) {
+                        if (k + u < ke) {
+                            load_lane_hint<HINT>(W + (size_t)colidx(k + u) * KS + cofs, a[u], pol);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < CPL; q++) a[u][q] = (T)0;
+                        }
+                    }
+                    if (VALUED) {
+#pragma unroll
+                        for (int u = 0; u < UNR; u++) {
+                            const T v = (k + u < ke) ? __ldg(p.vals + k + u) : (T)0;
+#pragma unroll
+                            for (int q = 0; q < CPL; q++) acc[q] += v * a[u][q];
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < UNR; u += 2)
+#pragma unroll
+                            for (int q = 0; q < CPL; q++) acc[q] += a[u][q] + a[u + 1][q];
+                    }
+                }
+                epilogue_x(r, acc, ke - kb, dot, x, xp);
+            } else {
+                for (; k < ke; k++) {
+                    int c0 = colidx(k);
+                    T a0[CPL];
+                    load_lane_hint<HINT>(W + (size_t)c0 * KS + cofs, a0, pol);
+                    T v0 = VALUED ? __ldg(p.vals + k) : (T)1;
+#pragma unroll
+                    for (int q = 0; q < CPL; q++) acc[q] += VALUED ? v0 * a0[q] : a0[q];
+                }
+                epilogue(r, acc, ke - kb, dot);
             }
-            epilogue(r, acc, ke - kb, dot);
         }
     } else if (it.rows < 0) {
         // one chunk of a long row, all groups of the warp share it
@@ -588,6 +644,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
             if (lane == 0) p.hub_cnt[(size_t)panel * p.nhubs + it.row] = 0u;
         }
     }
+    }  // work items of this warp
 
     // CTA partial of w_j . u per column: FP64 across groups, warps, CTAs
     __shared__ double sred[VNE_WARPS][KS];
@@ -881,7 +938,7 @@ cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream
     return cudaGetLastError();
 }
 
-// Step-kernel variants: {MINB, UNR, STREAM, STAGE, HINT}.  FP64 uses variant 0 only.
+// Step-kernel variants: {MINB, UNR, STREAM, STAGE, HINT, PTAIL}.  FP64 uses variant 0 only.
 #define VNE_STEP_VARIANTS(T, KS, VALUED, v, st, grid, p, smem)                                                   \
     switch (sizeof(T) == 8 ? 0 : (v)) {                                                                          \
         case 1: k_step<T, KS, VALUED, 6, 4, true, false><<<grid, VNE_THREADS, 0, st>>>(p); break;               \
@@ -891,13 +948,20 @@ cudaError_t launch_start(const StartParams<T>& p, int ks, int panels, cudaStream
         case 5: k_step<T, KS, VALUED, 4, 8, true, true><<<grid, VNE_THREADS, smem, st>>>(p); break;             \
         case 6: k_step<T, KS, VALUED, 6, 4, true, true, 1><<<grid, VNE_THREADS, smem, st>>>(p); break;          \
         case 7: k_step<T, KS, VALUED, 6, 4, true, true, 2><<<grid, VNE_THREADS, smem, st>>>(p); break;          \
+        case 8: k_step<T, KS, VALUED, 6, 8, true, true, 0, true><<<grid, VNE_THREADS, smem, st>>>(p); break;    \
+        case 9: k_step<T, KS, VALUED, 6, 4, true, true, 0, true><<<grid, VNE_THREADS, smem, st>>>(p); break;    \
+        case 10: k_step<T, KS, VALUED, 4, 8, true, true, 0, true><<<grid, VNE_THREADS, smem, st>>>(p); break;   \
+        case 11: k_step<T, KS, VALUED, 6, 8, true, false, 0, true><<<grid, VNE_THREADS, 0, st>>>(p); break;     \
+        case 12: k_step<T, KS, VALUED, 5, 4, true, true, 0, true><<<grid, VNE_THREADS, smem, st>>>(p); break;   \
+        case 13: k_step<T, KS, VALUED, 5, 8, true, true, 0, true><<<grid, VNE_THREADS, smem, st>>>(p); break;   \
         default: k_step<T, KS, VALUED, 4, 4, false, false><<<grid, VNE_THREADS, 0, st>>>(p); break;             \
     }
 
 template <typename T>
 cudaError_t launch_step(const StepParams<T>& p, int ks, int panels, bool valued, int variant, cudaStream_t st) {
     dim3 grid(panels * p.ctas_per_panel);
-    const size_t smem = (size_t)VNE_WARPS * (p.stage_nnz + 68) * sizeof(int32_t);
+    const size_t smem = (size_t)VNE_WARPS * (p.stage_nnz + kStageRp) * sizeof(int32_t);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;  // items above 1024 nonzeros are not staged
     if (valued) VNE_DISPATCH_KS(T, ks, VNE_STEP_VARIANTS(T, KS, true, variant, st, grid, p, smem));
     else VNE_DISPATCH_KS(T, ks, VNE_STEP_VARIANTS(T, KS, false, variant, st, grid, p, smem));
     return cudaGetLastError();

@@ -167,7 +167,8 @@ extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t
         const int32_t seg = (int32_t)sidx;
         const int32_t hub_base = (int32_t)P.hubs.size(), slot_base = P.hub_slots;
         sg.row_begin = (int32_t)r0;
-        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);
+        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);  // the packed problem takes one item per warp
+        sg.cta_count = (int32_t)(MP->items.size() / VNE_WARPS);
         sg.tile_begin = (int32_t)P.tiles.size();
         sg.hub_begin = hub_base;
         for (WorkItem it : MP->items) {

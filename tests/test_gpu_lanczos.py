@@ -217,7 +217,7 @@ def test_autotuned_schedule_keeps_parity(vctx):
     try:
         chosen, ms = vne.vne_autotune(vctx, mat, 16, 4)
         assert chosen.panel in (8, 16, 32) and chosen.item_nnz in (128, 256, 512, 1024)
-        assert 0 <= chosen.step_variant < 8 and ms > 0
+        assert 0 <= chosen.step_variant < 14 and ms > 0
         psi = vne.vne_quadform_batch(vctx, mat, X, 30, opt=vne.options(reorth=0))
         # a second matrix of the same shape inherits the tuned schedule
         mat2 = vne.matrix_from_graph(vctx, g, fp64=False, reorder=True)
@@ -232,7 +232,7 @@ def test_autotuned_schedule_keeps_parity(vctx):
     assert np.max(np.abs(psi - ref) / np.abs(ref)) <= TOL32
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", list(range(14)))
 def test_every_step_variant_matches_oracle_and_is_deterministic(vctx, variant):
     # item_nnz = 64 splits every row longer than 64 into chunks (many long rows)
     g = graphs.barabasi_albert(20000, 4, 3)
@@ -247,5 +247,23 @@ def test_every_step_variant_matches_oracle_and_is_deterministic(vctx, variant):
         vne.vne_matrix_destroy(mat)
     for a in again:
         assert np.array_equal(a, psi)  # bit-reproducible run to run
+    ref = np.array([r[0] for r in _oracle_psi(A, X, 30, "none")])
+    assert np.max(np.abs(psi - ref) / np.abs(ref)) <= TOL32
+
+
+@pytest.mark.parametrize("variant,ipw", [(4, 2), (10, 2), (12, 4), (0, 4)])
+def test_items_per_warp_match_oracle_and_are_deterministic(vctx, variant, ipw):
+    # a warp takes ipw work items in turn (long rows split at item_nnz = 64)
+    g = graphs.barabasi_albert(20000, 4, 3)
+    A, _ = density.density_matrix(g)
+    X = rng.rademacher(8, g.n, 0, 12)
+    mat = vne.matrix_from_graph(vctx, g, fp64=False, reorder=True)
+    try:
+        opt = vne.options(reorth=0, step_variant=variant, item_nnz=64, items_per_warp=ipw)
+        psi = vne.vne_quadform_batch(vctx, mat, X, 30, opt=opt)
+        again = vne.vne_quadform_batch(vctx, mat, X, 30, opt=opt)
+    finally:
+        vne.vne_matrix_destroy(mat)
+    assert np.array_equal(again, psi)
     ref = np.array([r[0] for r in _oracle_psi(A, X, 30, "none")])
     assert np.max(np.abs(psi - ref) / np.abs(ref)) <= TOL32
