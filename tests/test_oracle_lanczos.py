@@ -134,3 +134,55 @@ def test_posterior_bounds_bracket_the_error():
         assert lo <= err * (1 + 1e-6) + 1e-300
         assert err <= hi * (1 + 1e-6)
         assert lo <= est <= hi
+
+
+# ---- partial reorthogonalisation (Simon's omega recurrence) ----
+
+def _pro_case():
+    A = _rho(G.erdos_renyi(400, 0.05, 3))
+    c = krylov.desingularize(rng.rademacher(1, 400, 0, 1)[:, 0])
+    return A, c
+
+
+@pytest.mark.parametrize("eps", [2.0 ** -53, 2.0 ** -24])
+def test_partial_reorth_keeps_semi_orthogonality(eps):
+    # plain Lanczos loses orthogonality completely within 150 steps here;
+    # partial reorthogonalisation keeps |v_i . v_k| at the sqrt(eps) level it
+    # promises, reorthogonalising in pairs of steps and far less often than
+    # every step
+    A, c = _pro_case()
+    _, _, Vn = krylov.lanczos(A, c, 150, reorth="none", keep_basis=True)
+    assert np.max(np.abs(Vn.T @ Vn - np.eye(Vn.shape[1]))) > 0.1
+    st = {}
+    _, _, V = krylov.lanczos(A, c, 150, reorth="partial", keep_basis=True, eps=eps, stats=st)
+    off = np.abs(V.T @ V - np.eye(V.shape[1]))
+    assert np.max(off) <= 10 * math.sqrt(eps)
+    steps = st["reorth_steps"]
+    assert 2 <= len(steps) < 150 / 2
+    assert all(b == a + 1 for a, b in zip(steps[0::2], steps[1::2]))  # each trigger is followed by its pair
+
+
+def test_partial_reorth_estimates_track_the_loss():
+    # omega_{j+1,k} estimates v_{j+1} . v_k: the measured inner products stay
+    # within a modest factor of the estimates at every step
+    A, c = _pro_case()
+    st = {}
+    _, _, V = krylov.lanczos(A, c, 150, reorth="partial", keep_basis=True, stats=st)
+    for j, om in enumerate(st["omega"]):
+        if j + 1 >= V.shape[1]:
+            break
+        actual = np.abs(V[:, : j + 1].T @ V[:, j + 1])
+        assert np.all(actual <= 100.0 * np.abs(om[: j + 1]) + 1e-15), j
+
+
+@pytest.mark.parametrize("m", [2, 5, 8])
+def test_partial_reorth_polynomial_exactness(m):
+    # Lemma exactness-rational-krylov-quadform holds with the partial policy too
+    A = _rho(G.erdos_renyi(150, 0.06, 3))
+    b = rng.rademacher(5, 150, 0, 1)[:, 0]
+    c = krylov.desingularize(b)
+    Ad = A.toarray()
+    for p in range(0, 2 * m):
+        exact = float(c @ np.linalg.matrix_power(Ad, p) @ c)
+        got = krylov.lanczos_quadform(A, b, m, reorth="partial", eps=2.0 ** -24, f=lambda x, p=p: x ** p)[0]
+        assert math.isclose(got, exact, rel_tol=1e-9, abs_tol=1e-14 * abs(exact) + 1e-300)
