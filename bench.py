@@ -59,7 +59,10 @@ def parse():
     ap.add_argument("--vectors", type=int, default=112)
     ap.add_argument("--reorder", choices=["degree", "rcm", "none"], default="degree",
                     help="node relabelling of the headline matrix (default: descending degree)")
-    ap.add_argument("--schedule", default="", help="panel,item_nnz,step_variant[,interleave] (skips the autotuner)")
+    ap.add_argument("--schedule", default="",
+                    help="panel,item_nnz,step_variant[,interleave[,items_per_warp]] (skips the autotuner)")
+    ap.add_argument("--reorth", choices=["none", "partial"], default="none",
+                    help="Lanczos reorthogonalisation of the FP32 estimate (partial: Simon's omega recurrence)")
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c6", "c7"], default="c2",
                     help="c2 = the headline workload; c1/c3/c4/c5/c6/c7 print measurement lines of the other configs")
     ap.add_argument("--requests", type=int, default=400, help="c5: number of queries")
@@ -329,19 +332,22 @@ def run_native(args):
     vne.vne_ctx_set_stream(ctx, stream)
     flags = vne.VNE_FP32 | {"degree": vne.VNE_REORDER, "rcm": vne.VNE_REORDER_RCM, "none": 0}[args.reorder]
     mat = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
-    opt = vne.options(reorth=0)
+    reorth = {"none": 0, "partial": 2}[args.reorth]
+    opt = vne.options(reorth=reorth)
     seed0 = 1000 * (rank + 1)
     if args.schedule:
-        vals = [int(x) for x in args.schedule.split(",")] + [0]
-        pnl, itm, var, il = vals[:4]
-        opt = vne.options(reorth=0, panel=pnl, item_nnz=itm, step_variant=var, interleave=il)
-        tuned_cfg = {"panel": pnl, "item_nnz": itm, "step_variant": var, "interleave": il, "source": "--schedule"}
+        vals = [int(x) for x in args.schedule.split(",")] + [0, 0]
+        pnl, itm, var, il, ipw = vals[:5]
+        opt = vne.options(reorth=reorth, panel=pnl, item_nnz=itm, step_variant=var, interleave=il,
+                          items_per_warp=ipw)
+        tuned_cfg = {"panel": pnl, "item_nnz": itm, "step_variant": var, "interleave": il,
+                     "items_per_warp": ipw, "source": "--schedule"}
     else:
         # schedule autotuner (once per matrix shape; cached in the context)
         tuned, tune_ms = vne.vne_autotune(ctx, mat, 112 if args.estimator == "hutchpp" else args.vectors, 8)
         tuned_cfg = {"panel": tuned.panel, "item_nnz": tuned.item_nnz, "step_variant": tuned.step_variant,
-                     "interleave": tuned.interleave, "ms_per_lanczos_step_112_cols": tune_ms,
-                     "source": "vne_autotune"}
+                     "interleave": tuned.interleave, "items_per_warp": tuned.items_per_warp,
+                     "ms_per_lanczos_step_112_cols": tune_ms, "source": "vne_autotune"}
 
     def one(seed):
         if args.estimator == "hutchinson":
@@ -474,7 +480,8 @@ def run_native(args):
                    "n": int(n_), "nnz": int(nnz_), "sketch_cols": N_SKETCH,
                    "hutch_vectors": N_HUTCH, "krylov_steps": M_STEPS, "scalars": "f64",
                    "l2": "inputs larger than L2 (each 100-column block is 400 MB; L2 129 MB)",
-                   "parallelism": f"replicas x{world} (independent estimates)", "reorder": args.reorder},
+                   "parallelism": f"replicas x{world} (independent estimates)", "reorder": args.reorder,
+                   "reorth": args.reorth},
         "roofline": roof, "update_kernel": update, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": sampler.summary() if sampler else None,
         "schedule": tuned_cfg,

@@ -65,8 +65,17 @@ typedef struct vne_matrix vne_matrix;
 typedef struct vne_options {
     int32_t reorth;       /* 0: plain three-term Lanczos; 1: full
                              reorthogonalisation (classical Gram-Schmidt
-                             twice) against the stored basis.  -1: default
-                             (full for FP64 matrices, none for FP32). */
+                             twice) against the stored basis; 2: partial
+                             reorthogonalisation (Simon's omega recurrence
+                             estimates the loss of orthogonality from alpha
+                             and beta, in FP64, with the rounding unit of the
+                             vector precision; once it reaches sqrt(eps) the
+                             new vector and the next one are orthogonalised,
+                             twice, against the basis vectors whose estimate
+                             is at least eps^(3/4)).  Reorthogonalisation
+                             keeps all m + 1 Lanczos vectors of a block.
+                             -1: default (full for FP64 matrices, none for
+                             FP32). */
     int32_t block;        /* probe columns per device block, 0 = auto (<= 256) */
     int32_t panel;        /* columns per panel of the panel-major vector
                              layout (FP32: 8, 16, 32; FP64: 4, 8, 16), 0 = auto */

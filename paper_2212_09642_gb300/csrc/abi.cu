@@ -329,7 +329,7 @@ extern "C" vne_status vne_quadform_batch(vne_matrix* M, const double* vectors, i
     Problem* P = matrix_problem(M, &o);
     Sched sc = resolve_sched(M, &o);
     int ks = sc.ks;
-    bool reorth = want_reorth(M, &o);
+    const int reorth = want_reorth(M, &o);
     int lim = block_limit(&o);
     for (int b0 = 0; b0 < k; b0 += lim) {
         int K = std::min(lim, k - b0);

@@ -251,6 +251,7 @@ Problem* matrix_problem(vne_matrix* M, const vne_options* opt) {
     P->vals = M->d_vals;
     P->node_id = M->d_node_id;
     P->ipw = sc.ipw;
+    P->norm_m = M->normM;
     SegInfo s{};
     s.row_begin = 0;
     s.rows = (int32_t)M->n;
@@ -279,7 +280,7 @@ int choose_panel(bool fp64, const vne_options* opt, int64_t n) {
 
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
-               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant,
+               int reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant,
                bool interleave, bool graph, bool want_psi, const Adaptive* ad) {
     cudaStream_t st = ctx->stream;
     const int panels = (K + ks - 1) / ks;
@@ -287,9 +288,9 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
     const int S = P.nseg;
     const int SK = S * Kp;
     const size_t slot_elems = (size_t)Kp * P.n_total;
-    const bool store_all = keep_basis || reorth;
+    const bool store_all = keep_basis || reorth != 0;
     const int nslots = store_all ? m + 1 : 2;
-    VNE_REQUIRE(ctx, reorth == false || S == 1, VNE_EUNSUPPORTED, "full reorthogonalisation needs a single matrix");
+    VNE_REQUIRE(ctx, reorth == 0 || S == 1, VNE_EUNSUPPORTED, "reorthogonalisation needs a single matrix");
     T* slots = ws_get_t<T>(ctx, tag + ".slots", slot_elems * nslots);
     T* u = ws_get_t<T>(ctx, "u", slot_elems);
     double* alpha = ws_get_t<double>(ctx, tag + ".alpha", (size_t)m * SK, true);
@@ -368,6 +369,24 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
         rcoef = ws_get_t<double>(ctx, "reorth.coef", (size_t)m * Kp);
         rpart = ws_get_t<double>(ctx, "reorth.part", (size_t)panels * m * tiles * ks);
     }
+    // partial reorthogonalisation state (Simon's omega recurrence)
+    ProParams pro{};
+    if (reorth == 2) {
+        pro.alpha = alpha;
+        pro.beta = beta;
+        pro.sig = sigma;
+        pro.omega = ws_get_t<double>(ctx, tag + ".pro.omega", (size_t)2 * (m + 2) * SK);
+        pro.sel = ws_get_t<uint8_t>(ctx, tag + ".pro.sel", (size_t)(m + 1) * SK);
+        pro.pend_sel = ws_get_t<uint8_t>(ctx, tag + ".pro.psel", (size_t)(m + 2) * SK);
+        pro.pend = ws_get_t<int32_t>(ctx, tag + ".pro.pend", SK);
+        pro.panel_active = ws_get_t<int32_t>(ctx, tag + ".pro.active", panels);
+        pro.SK = SK;
+        pro.ks = ks;
+        pro.K = Kp;
+        pro.m = m;
+        pro.eps = sizeof(T) == 4 ? 0x1.0p-24 : 0x1.0p-53;
+        pro.normM = P.norm_m;
+    }
     // The step loop, enqueued on stream `s`; `prof` brackets the launches
     // with events (never while capturing).
     auto enqueue_loop = [&](cudaStream_t s, bool prof, int j_begin, int j_end) {
@@ -432,7 +451,44 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
                     ctx->pending.push_back({1, e1, e2, upd_bytes});
                 }
             }
-            if (reorth && j < m + 1) {
+            if (reorth == 2) {
+                // estimate the loss of orthogonality of w_{j+1}; orthogonalise
+                // the columns that need it (twice) against their selected
+                // basis vectors and renormalise; panels with nothing to do
+                // skip every pass
+                pro.j = j;
+                VNE_TRY_CUDA(ctx, cudaMemsetAsync(pro.panel_active, 0, panels * sizeof(int32_t), s));
+                VNE_TRY_CUDA(ctx, launch_pro_omega(pro, s));
+                ReorthParams<T> rp{};
+                rp.basis = slots;
+                rp.slot_stride = slot_elems;
+                rp.w = slot(j + 1);
+                rp.j = j;
+                rp.K = Kp;
+                rp.n_total = P.n_total;
+                rp.panels = panels;
+                rp.tiles_per_panel = tiles;
+                rp.tiles = P.d_tiles;
+                rp.part = rpart;
+                rp.coef = rcoef;
+                rp.panel_active = pro.panel_active;
+                ReorthCoefParams cp{};
+                cp.part = rpart;
+                cp.sig = sigma;
+                cp.coef = rcoef;
+                cp.j = j;
+                cp.K = Kp;
+                cp.panels = panels;
+                cp.tiles_per_panel = tiles;
+                cp.sel = pro.sel;
+                cp.panel_active = pro.panel_active;
+                for (int pass = 0; pass < 2; pass++) VNE_TRY_CUDA(ctx, launch_reorth<T>(rp, cp, ks, s));
+                p.renorm = 1;
+                p.panel_active = pro.panel_active;
+                VNE_TRY_CUDA(ctx, launch_update<T>(p, ks, panels, s));
+                p.panel_active = nullptr;
+                ctx->launches += 8;
+            } else if (reorth && j < m + 1) {
                 ReorthParams<T> rp{};
                 rp.basis = slots;
                 rp.slot_stride = slot_elems;
@@ -570,10 +626,10 @@ std::vector<double> download(vne_ctx* ctx, const double* d, size_t count) {
     return h;
 }
 
-bool want_reorth(const vne_matrix* M, const vne_options* o) {
+int want_reorth(const vne_matrix* M, const vne_options* o) {
     int r = o ? o->reorth : -1;
-    if (r < 0) return M->fp64;
-    return r != 0;
+    if (r < 0) return M->fp64 ? 1 : 0;
+    return r == 2 ? 2 : (r != 0 ? 1 : 0);
 }
 
 int block_limit(const vne_options* o) { return (o && o->block > 0) ? o->block : 256; }
@@ -594,7 +650,7 @@ std::vector<double> quadforms(vne_matrix* M, const vne_options* o, StartSource s
     int ks = sc.ks;
     check_ks<T>(ctx, ks);
     int lim = block_limit(o);
-    bool reorth = want_reorth(M, o);
+    const int reorth = want_reorth(M, o);
     std::vector<double> psi(ncols);
     ctx->last_steps = 0;
     Adaptive ad;
@@ -692,7 +748,7 @@ void apply_operator(vne_ctx* ctx, Problem& P, int ks, int Kp, const T* in, T* ou
 }
 
 #define VNE_ENGINE_INSTANTIATE(T)                                                                                \
-    template void run_block<T>(vne_ctx*, Problem&, const StartSource&, const T*, int, int, int, bool, bool, bool, \
+    template void run_block<T>(vne_ctx*, Problem&, const StartSource&, const T*, int, int, int, int, bool, bool,  \
                                const std::string&, BlockOut&, int, bool, bool, bool, const Adaptive*);          \
     template std::vector<double> quadforms<T>(vne_matrix*, const vne_options*, StartSource, int, int,             \
                                               const double*);                                                    \

@@ -165,6 +165,7 @@ struct Problem {
     int32_t hub_slots = 0;
     int32_t stage_nnz = 0;   // largest item (nonzeros)
     int32_t ipw = 1;         // work items per warp (CTA = VNE_WARPS * ipw items)
+    double norm_m = 0.0;     // Gershgorin bound of the stored operator (single matrix)
     // device copies (owned)
     SegInfo* d_segs = nullptr;
     WorkItem* d_items = nullptr;
@@ -321,10 +322,11 @@ struct Adaptive {
 // m Lanczos steps of a block of K columns (see engine.cu).
 template <typename T>
 void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_src, int K, int ks, int m,
-               bool reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
+               int reorth, bool keep_basis, bool desing, const std::string& tag, BlockOut& out, int variant = 0,
                bool interleave = false, bool graph = true, bool want_psi = true, const Adaptive* ad = nullptr);
 
-bool want_reorth(const vne_matrix* M, const vne_options* o);
+// Reorthogonalisation policy of a call: 0 none, 1 full, 2 partial.
+int want_reorth(const vne_matrix* M, const vne_options* o);
 int block_limit(const vne_options* o);
 vne_options defaults();
 

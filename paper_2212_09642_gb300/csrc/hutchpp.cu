@@ -31,7 +31,8 @@ struct HppPlan {
     Sched sc;
     int ks, n, m;
     uint64_t seed_mixed;
-    bool gaussian, reorth;
+    bool gaussian;
+    int reorth;  // 0 none, 1 full, 2 partial
 };
 
 template <typename T>

@@ -58,6 +58,7 @@ struct StepParams {
     int32_t tiles_per_panel;
     int32_t stage_nnz;  // largest work item in nonzeros (staged variants)
     int32_t ipw;        // work items per warp (a CTA covers VNE_WARPS * ipw consecutive items)
+    const int32_t* panel_active;  // update kernel with renorm: nullable, inactive panels are skipped
     int32_t panel_base; // first panel of this launch (per-panel launches)
     int32_t first;   // j == 1: no previous vector
     int32_t renorm;  // update kernel: only recompute the norm of w_next in place
@@ -84,6 +85,7 @@ struct ReorthParams {
     const RowTile* tiles;
     double* part;         // [panels][j][tiles][KS]
     const double* coef;   // [j][K]
+    const int32_t* panel_active;  // nullable: panels with no column to orthogonalise are skipped
 };
 
 struct ReorthCoefParams {
@@ -91,7 +93,25 @@ struct ReorthCoefParams {
     const double* sig;    // [j][K] sigma_i of each basis vector
     double* coef;
     int32_t j, K, panels, tiles_per_panel;
+    const uint8_t* sel;           // nullable [j][K]: orthogonalise column c against basis vector i
+    const int32_t* panel_active;  // nullable, as in ReorthParams
 };
+
+// Partial reorthogonalisation (Simon's omega recurrence), one thread per
+// column, after the update of step j (1-based) has formed w_{j+1} and beta_j.
+struct ProParams {
+    const double* alpha;  // [m][SK], M units
+    const double* beta;   // [m][SK]
+    const double* sig;    // [m+1][SK]: sigma_{j+1} = 0 marks a finished column
+    double* omega;        // [2][m+2][SK]: omega_{j-1,.} and omega_{j,.}, rolled in place
+    uint8_t* sel;         // [m+1][SK]: this step's set (row i: basis vector i+1)
+    uint8_t* pend_sel;    // [m+1][SK]: the set the next step repeats
+    int32_t* pend;        // [SK]
+    int32_t* panel_active;  // [panels], zeroed before the kernel
+    int32_t j, SK, ks, K, m;
+    double eps, normM;
+};
+cudaError_t launch_pro_omega(const ProParams& p, cudaStream_t st);
 
 template <typename T>
 struct RecoverParams {

@@ -702,6 +702,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
     const int np = gridDim.x / p.tiles_per_panel;
     const int panel = p.panel_base + (np - 1 - (int)(blockIdx.x / p.tiles_per_panel)),
               tile = blockIdx.x % p.tiles_per_panel;
+    if (p.renorm && p.panel_active && !p.panel_active[panel]) return;  // nothing changed in this panel
     const RowTile t = p.tiles[tile];
     const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
     const int cofs = sub * CPL;
@@ -767,6 +768,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) 
     const int i = blockIdx.x % p.j;
     const int pt = blockIdx.x / p.j;
     const int panel = pt / p.tiles_per_panel, tile = pt % p.tiles_per_panel;
+    if (p.panel_active && !p.panel_active[panel]) return;
     const RowTile t = p.tiles[tile];
     const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
     constexpr int RPI = VNE_THREADS / KS;
@@ -794,10 +796,14 @@ __global__ void k_reorth_coef(ReorthCoefParams p) {
     int total = p.panels * p.j * KS;
     if (idx >= total) return;
     int c = idx % KS, i = (idx / KS) % p.j, panel = idx / (KS * p.j);
+    int col = panel * KS + c;
+    if ((p.panel_active && !p.panel_active[panel]) || (p.sel && !p.sel[(size_t)i * p.K + col])) {
+        p.coef[(size_t)i * p.K + col] = 0.0;
+        return;
+    }
     double s = 0.0;
     for (int t = 0; t < p.tiles_per_panel; t++)
         s += p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + t) * KS + c];
-    int col = panel * KS + c;
     double sig = p.sig[(size_t)i * p.K + col];
     p.coef[(size_t)i * p.K + col] = sig * sig * s;
 }
@@ -806,6 +812,7 @@ __global__ void k_reorth_coef(ReorthCoefParams p) {
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p) {
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
+    if (p.panel_active && !p.panel_active[panel]) return;
     const RowTile t = p.tiles[tile];
     const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
     constexpr int RPI = VNE_THREADS / KS;
@@ -814,10 +821,96 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p)
     const int col = panel * KS + c;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         double v = (double)Wn[(size_t)r * KS + c];
-        for (int i = 0; i < p.j; i++)
-            v -= p.coef[(size_t)i * p.K + col] * (double)p.basis[(size_t)i * p.slot_stride + pofs + (size_t)r * KS + c];
+        for (int i = 0; i < p.j; i++) {
+            const double cf = p.coef[(size_t)i * p.K + col];
+            if (cf != 0.0) v -= cf * (double)p.basis[(size_t)i * p.slot_stride + pofs + (size_t)r * KS + c];
+        }
         Wn[(size_t)r * KS + c] = (T)v;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Partial reorthogonalisation (Simon 1984): the loss of orthogonality
+// omega_{j+1,k} ~ v_{j+1} . v_k, k = 1..j, follows from the alpha's and
+// beta's alone,
+//   beta_j omega_{j+1,k} = beta_k omega_{j,k+1} + (alpha_k - alpha_j) omega_{j,k}
+//                          + beta_{k-1} omega_{j,k-1} - beta_{j-1} omega_{j-1,k} +- 2 eps ||M||,
+// with omega_{j,j} = 1 and omega_{j+1,j} = eps.  Once max_{k<j} |omega_{j+1,k}|
+// reaches sqrt(eps), w_{j+1} is orthogonalised against the v_k with
+// |omega_{j+1,k}| >= eps^(3/4) (those estimates are reset to eps), and the
+// next vector against the same set.  One thread per column; the rows
+// omega_{j-1,.} and omega_{j,.} are rolled in place.
+__device__ __forceinline__ int m2_row(int j) { return j & 1; }  // rolling buffer of omega_{j,.}
+
+__global__ void k_pro_omega(ProParams p) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.SK) return;
+    const int j = p.j, SK = p.SK;
+    double* om_old = p.omega + (size_t)m2_row(j + 1) * (p.m + 2) * SK;  // omega_{j-1,.}, becomes omega_{j+1,.}
+    const double* om = p.omega + (size_t)m2_row(j) * (p.m + 2) * SK;     // omega_{j,.}
+    for (int k = 0; k <= j; k++) p.sel[(size_t)k * SK + c] = 0;
+    const double bj = p.beta[(size_t)(j - 1) * SK + c];
+    if (j == 1) {  // a new block: omega_{0,.} = 0, omega_{1,.} = e_1, no pending set
+        double* om1 = p.omega + (size_t)(m2_row(1)) * (p.m + 2) * SK;
+        for (int k = 0; k < p.m + 2; k++) {
+            om_old[(size_t)k * SK + c] = 0.0;
+            om1[(size_t)k * SK + c] = k == 1 ? 1.0 : 0.0;
+        }
+        p.pend[c] = 0;
+    }
+    if (!(bj > 0.0) || p.sig[(size_t)j * SK + c] == 0.0) {  // finished column: nothing to estimate
+        p.pend[c] = 0;
+        return;
+    }
+    const double aj = p.alpha[(size_t)(j - 1) * SK + c];
+    const double bjm1 = j > 1 ? p.beta[(size_t)(j - 2) * SK + c] : 0.0;
+    const double noise = 2.0 * p.eps * p.normM;
+    // omega_{j+1,k} for k = 1..j-1 (1-based), written over omega_{j-1,k}
+    // after it is read
+    double om_jm1_prev = 0.0;  // omega_{j,k-1}
+    double mx = 0.0;
+    for (int k = 1; k <= j - 1; k++) {
+        const double ok = (k == j) ? 1.0 : om[(size_t)k * SK + c];
+        const double okp1 = (k + 1 == j) ? 1.0 : om[(size_t)(k + 1) * SK + c];
+        double t = p.beta[(size_t)(k - 1) * SK + c] * okp1 + (p.alpha[(size_t)(k - 1) * SK + c] - aj) * ok -
+                   bjm1 * om_old[(size_t)k * SK + c];
+        if (k > 1) t += p.beta[(size_t)(k - 2) * SK + c] * om_jm1_prev;
+        t += copysign(noise, t);
+        const double v = t / bj;
+        om_jm1_prev = ok;
+        om_old[(size_t)k * SK + c] = v;
+        mx = fmax(mx, fabs(v));
+    }
+    om_old[(size_t)j * SK + c] = p.eps;
+    om_old[(size_t)(j + 1) * SK + c] = 1.0;
+    const double sq = sqrt(p.eps), eta = pow(p.eps, 0.75);
+    int any = 0;
+    if (p.pend[c]) {  // the second vector of a pair: the previous step's set (k <= j - 1)
+        p.pend[c] = 0;
+        for (int k = 1; k <= j - 1; k++)
+            if (p.pend_sel[(size_t)k * SK + c]) {
+                p.sel[(size_t)(k - 1) * SK + c] = 1;
+                om_old[(size_t)k * SK + c] = p.eps;
+                any = 1;
+            }
+    } else if (j > 1 && mx >= sq) {
+        for (int k = 1; k <= j; k++) {
+            const int s = fabs(om_old[(size_t)k * SK + c]) >= eta;
+            p.pend_sel[(size_t)k * SK + c] = (uint8_t)s;
+            if (s) {
+                p.sel[(size_t)(k - 1) * SK + c] = 1;
+                om_old[(size_t)k * SK + c] = p.eps;
+                any = 1;
+            }
+        }
+        p.pend[c] = 1;
+    }
+    if (any) atomicOr(p.panel_active + (c % p.K) / p.ks, 1);
+}
+
+cudaError_t launch_pro_omega(const ProParams& p, cudaStream_t st) {
+    k_pro_omega<<<(p.SK + 127) / 128, 128, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
