@@ -353,6 +353,14 @@ void rational_quadforms(vne_matrix* M, const vne_options* o, StartSource src, in
                         int nshift, std::vector<double>& psi, std::vector<int>& iters, std::vector<double>& resid);
 std::vector<double> resolve_shifts(const vne_matrix* M, const double* poles, int num_poles);
 
+// Hutch++ deflation basis of one query (hutchpp.cu): the sketch of probe
+// columns 0..Nr-1, Q = orth(f(A) Omega) copied to q_rows ([n][Nr] row-major
+// in M's packed row order, zero columns beyond the rank), psi(q_i) for
+// i < Nr (0 beyond the rank) and the rank.
+template <typename T>
+void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, uint64_t seed, T* q_rows,
+                       std::vector<double>& psi_q, int& rank);
+
 }  // namespace vne_engine
 
 using namespace vne_engine;

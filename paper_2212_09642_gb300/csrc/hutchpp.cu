@@ -285,6 +285,31 @@ void hutchpp_project_impl(vne_matrix* M, const vne_options* o, const void* Yin, 
 
 }  // namespace
 
+namespace vne_engine {
+
+template <typename T>
+void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, uint64_t seed, T* q_rows,
+                       std::vector<double>& psi_q, int& rank) {
+    vne_ctx* ctx = M->ctx;
+    HppPlan h = hpp_plan<T>(M, o, m, seed);
+    int Kp = 0;
+    T* Y = sketch_block<T>(M, h, 0, Nr, "Y", &Kp);
+    ProjectOut po;
+    project_block<T>(M, h, Y, Kp, Nr, 0, 0, -1, po);
+    T* QG = ws_get_t<T>(ctx, "QG", (size_t)Kp * h.n);  // Q in its first Kp columns, zero beyond the rank
+    VNE_TRY_CUDA(ctx, launch_panel_to_rows<T>(QG, h.n, h.ks, 0, Nr, nullptr, q_rows, ctx->stream));
+    ctx->launches += 1;
+    psi_q = po.psi;
+    rank = po.rank;
+}
+
+template void hutchpp_deflation<float>(vne_matrix*, const vne_options*, int, int, uint64_t, float*,
+                                       std::vector<double>&, int&);
+template void hutchpp_deflation<double>(vne_matrix*, const vne_options*, int, int, uint64_t, double*,
+                                        std::vector<double>&, int&);
+
+}  // namespace vne_engine
+
 extern "C" vne_status vne_entropy_hutchpp(vne_matrix* M, int32_t sketch_cols, int32_t hutch_vectors,
                                           int32_t krylov_steps, uint64_t seed, const vne_options* opt,
                                           double* estimate, double* parts) {

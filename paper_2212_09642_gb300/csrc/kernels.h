@@ -58,6 +58,15 @@ struct StepParams {
     int32_t tiles_per_panel;
     int32_t stage_nnz;  // largest work item in nonzeros (staged variants)
     int32_t ipw;        // work items per warp (a CTA covers VNE_WARPS * ipw consecutive items)
+    // per-segment step counters (serving): with segj set, segment s runs its
+    // own step segj[s] (0: idle this launch); w_j lives in slot (j - 1) & 1,
+    // the scalars in row j - 1 of [m][nseg * K] arrays (sigma: [m + 1][...])
+    const int32_t* segj;
+    T* slot0;
+    T* slot1;
+    double* alpha0;
+    double* beta0;
+    double* sigma0;
     const int32_t* panel_active;  // update kernel with renorm: nullable, inactive panels are skipped
     int32_t panel_base; // first panel of this launch (per-panel launches)
     int32_t first;   // j == 1: no previous vector
@@ -133,6 +142,35 @@ constexpr int kStepVariants = 14;
 constexpr int kItemMaxRows = 128;
 constexpr int kStageRp = kItemMaxRows + 4;
 template <typename T> cudaError_t launch_update(const StepParams<T>&, int ks, int panels, cudaStream_t);
+// Start vectors of a served block (Hutch++ with a deflation basis Q per
+// segment): for the segments listed, g = probe columns col0[s] ..
+// col0[s] + K - 1 (Rademacher, or Gaussian), g' = g - Q_s (Q_s^T g),
+// c = g' - mean(g') 1 written to w1 (panel-major, K columns), with
+// ||c||^2 and sigma_1 = 1 / ||c||.  Three passes with fixed-order
+// per-segment reductions.
+template <typename T>
+struct SrvStartParams {
+    const int32_t* tile_list;  // [ntiles] tiles of the starting segments, grouped by segment
+    const RowTile* tiles;
+    const SegInfo* seg;        // rows of each segment
+    const int32_t* seg_tb;     // [nseg] first entry of the segment in tile_list
+    const int32_t* seg_tc;     // [nseg] its number of tiles
+    const int32_t* node_id;    // packed row -> node id in the query's own numbering
+    const uint64_t* seg_seed;  // [nseg] mixed seed
+    const int32_t* seg_col0;   // [nseg] first probe column of the block
+    const T* q;                // [n_total][4] deflation basis, zero columns beyond the rank
+    double* coef;              // [nseg][4][K]
+    double* mean;              // [nseg][K]
+    double* norm2;             // [nseg][K]
+    double* sig1;              // [nseg][K]: row 0 of the sigma array
+    T* w1;                     // panel-major [K / KS][n_total][KS]
+    double* part;              // [ntiles][4 * K]
+    uint32_t* counter;         // [nseg], zero between launches
+    int32_t ntiles, K, n_total, gaussian;
+};
+template <typename T> cudaError_t launch_srv_start(const SrvStartParams<T>& p, int ks, cudaStream_t st);
+// Step and update kernels for per-segment step counters (p.segj, pattern operators only).
+template <typename T> cudaError_t launch_step_update_segj(const StepParams<T>&, int ks, int panels, cudaStream_t);
 template <typename T> cudaError_t launch_reorth(const ReorthParams<T>&, const ReorthCoefParams&, int ks, cudaStream_t);
 // The first two passes of launch_reorth only: coef[i][col] = sig_i^2
 // (basis_i . w) for i < j (fixed-order sums, deterministic).

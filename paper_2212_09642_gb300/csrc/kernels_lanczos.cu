@@ -439,6 +439,167 @@ __global__ void __launch_bounds__(VNE_THREADS, 3) k_start_center(StartParams<T> 
 }
 
 // ---------------------------------------------------------------------------
+// Served blocks: deflated start vectors (see kernels.h).  One CTA per listed
+// tile; thread t handles block column t % 64 (and t % 64 + 64, ..) of the
+// tile's rows t / 64, t / 64 + 4, ...; partials of the CTA are summed over
+// its four row groups, and the last CTA of a segment adds the segment's
+// tile partials in list order.
+
+// The last-arriving CTA of segment s sums the W-value partials of its tiles
+// (list entries tb .. tb + tc - 1) in order; true in that CTA, with the
+// totals in out[0 .. W).
+__device__ bool srv_last_reduce(const double* part, uint32_t* counter, int tb, int tc, int W, double* out) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == (unsigned)(tc - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < tc; i++) acc += ld_cg(&part[(size_t)(tb + i) * W + w]);
+        out[w] = acc;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T srv_probe(const SrvStartParams<T>& p, int s, int c, int r) {
+    const uint64_t sd = p.seg_seed[s];
+    const uint64_t col = (uint64_t)(p.seg_col0[s] + c);
+    const uint64_t id = (uint64_t)p.node_id[r];
+    return (T)(p.gaussian ? gaussian_entry(sd, col, id) : rademacher_entry(sd, col, id));
+}
+
+// pass 1: coef[s][i][c] = q_i . g_c over the segment's rows
+template <typename T>
+__global__ void __launch_bounds__(VNE_THREADS) k_srv_coef(SrvStartParams<T> p) {
+    const RowTile t = p.tiles[p.tile_list[blockIdx.x]];
+    const int s = t.seg, c0 = threadIdx.x % 64, rs = threadIdx.x / 64;
+    __shared__ double red[VNE_THREADS / 64][4 * 256];
+    for (int c = c0; c < p.K; c += 64) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int r = t.row_begin + rs; r < t.row_end; r += VNE_THREADS / 64) {
+            const double g = (double)srv_probe(p, s, c, r);
+#pragma unroll
+            for (int i = 0; i < 4; i++) acc[i] += (double)p.q[(size_t)r * 4 + i] * g;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) red[rs][i * p.K + c] = acc[i];
+    }
+    __syncthreads();
+    const int W = 4 * p.K;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < VNE_THREADS / 64; q++) v += red[q][w];
+        p.part[(size_t)blockIdx.x * W + w] = v;
+    }
+    __shared__ double tot[4 * 256];
+    if (srv_last_reduce(p.part, p.counter + s, p.seg_tb[s], p.seg_tc[s], W, tot))
+        for (int w = threadIdx.x; w < W; w += blockDim.x) p.coef[(size_t)s * W + w] = tot[w];
+}
+
+// pass 2 (center = 0): column sums of g' = g - Q coef -> mean; pass 3
+// (center = 1): c = g' - mean written to w1, ||c||^2 -> norm2, sigma_1
+template <typename T, int KS>
+__global__ void __launch_bounds__(VNE_THREADS) k_srv_pass(SrvStartParams<T> p, int center) {
+    const RowTile t = p.tiles[p.tile_list[blockIdx.x]];
+    const int s = t.seg, c0 = threadIdx.x % 64, rs = threadIdx.x / 64;
+    __shared__ double red[VNE_THREADS / 64][256];
+    for (int c = c0; c < p.K; c += 64) {
+        T cf[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) cf[i] = (T)p.coef[((size_t)s * 4 + i) * p.K + c];
+        const T mu = center ? (T)p.mean[(size_t)s * p.K + c] : (T)0;
+        T* out = p.w1 + (size_t)(c / KS) * p.n_total * KS + (c % KS);
+        RowSum<T> acc;
+        for (int r = t.row_begin + rs; r < t.row_end; r += VNE_THREADS / 64) {
+            T v = srv_probe(p, s, c, r);
+#pragma unroll
+            for (int i = 0; i < 4; i++) v -= p.q[(size_t)r * 4 + i] * cf[i];
+            if (center) {
+                v -= mu;
+                out[(size_t)r * KS] = v;
+                acc.add(v * v);
+            } else {
+                acc.add(v);
+            }
+        }
+        red[rs][c] = acc.total();
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < p.K; w += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < VNE_THREADS / 64; q++) v += red[q][w];
+        p.part[(size_t)blockIdx.x * p.K + w] = v;
+    }
+    __shared__ double tot[256];
+    if (srv_last_reduce(p.part, p.counter + s, p.seg_tb[s], p.seg_tc[s], p.K, tot)) {
+        for (int w = threadIdx.x; w < p.K; w += blockDim.x) {
+            const size_t o = (size_t)s * p.K + w;
+            if (center) {
+                p.norm2[o] = tot[w];
+                p.sig1[o] = tot[w] > 0.0 ? 1.0 / sqrt(tot[w]) : 0.0;
+            } else {
+                p.mean[o] = tot[w] / (double)p.seg[s].rows;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The per-step pointers of one segment: the launch's own (one step j for
+// every segment), or, with per-segment step counters, those of the
+// segment's step j_s (false: the segment is idle in this launch).
+template <typename T>
+struct StepView {
+    const T* w_cur;
+    const T* w_prev;
+    T* w_next;
+    const double* sig_cur;
+    const double* sig_prev;
+    const double* beta_prev;
+    double* alpha;
+    double* beta;
+    double* sig_next;
+    int first;
+};
+
+template <bool SEGJ, typename T>
+__device__ __forceinline__ bool step_view(const StepParams<T>& p, int seg, StepView<T>& v) {
+    if (!SEGJ) {
+        v.w_cur = p.w_cur;
+        v.w_prev = p.w_prev;
+        v.w_next = p.w_next;
+        v.sig_cur = p.sig_cur;
+        v.sig_prev = p.sig_prev;
+        v.beta_prev = p.beta_prev;
+        v.alpha = p.alpha;
+        v.beta = p.beta;
+        v.sig_next = p.sig_next;
+        v.first = p.first;
+        return true;
+    }
+    const int j = p.segj[seg];
+    if (j <= 0) return false;
+    const size_t SK = (size_t)p.nseg * p.K;
+    v.w_cur = ((j - 1) & 1) ? p.slot1 : p.slot0;
+    v.w_prev = (j & 1) ? p.slot1 : p.slot0;
+    v.w_next = (j & 1) ? p.slot1 : p.slot0;
+    v.sig_cur = p.sigma0 + (size_t)(j - 1) * SK;
+    v.sig_prev = j > 1 ? p.sigma0 + (size_t)(j - 2) * SK : p.sigma0;
+    v.beta_prev = j > 1 ? p.beta0 + (size_t)(j - 2) * SK : p.beta0;
+    v.alpha = p.alpha0 + (size_t)(j - 1) * SK;
+    v.beta = p.beta0 + (size_t)(j - 1) * SK;
+    v.sig_next = p.sigma0 + (size_t)j * SK;
+    v.first = j == 1;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Step kernel: u = sigma_j M w_j - beta_{j-1} sigma_{j-1} w_{j-1},
 // alpha_j = sigma_j (w_j . u).  One warp per work item.
 // Variants (selected by the schedule autotuner): MINB = CTAs per SM the
@@ -453,7 +614,7 @@ __global__ void __launch_bounds__(VNE_THREADS, 3) k_start_center(StartParams<T> 
 // UNR) gathers at once under predicates instead of one per latency round,
 // and load the row's own entries of w_j and w_{j-1} before its gathers.
 template <typename T, int KS, bool VALUED, int MINB, int UNR, bool STREAM, bool STAGE, int HINT = 0,
-          bool PTAIL = false>
+          bool PTAIL = false, bool SEGJ = false>
 __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;  // lanes per row
@@ -462,9 +623,11 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     const int g = lane / LPR, sub = lane % LPR;
     const int panel = p.panel_base + blockIdx.x / p.ctas_per_panel, cta = blockIdx.x % p.ctas_per_panel;
     const int seg = p.cta_seg[cta];
+    StepView<T> sv;
+    if (!step_view<SEGJ>(p, seg, sv)) return;  // idle segment: every CTA of it returns here
     const size_t pofs = (size_t)panel * p.n_total * KS;
-    const T* __restrict__ W = p.w_cur + pofs;
-    const T* __restrict__ Wp = p.w_prev + pofs;
+    const T* __restrict__ W = sv.w_cur + pofs;
+    const T* __restrict__ Wp = sv.w_prev + pofs;
     T* __restrict__ U = p.u + pofs;
     const int cofs = sub * CPL;
 
@@ -472,8 +635,8 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     __shared__ T s_sig[KS], s_cp[KS];
     if (threadIdx.x < KS) {
         const size_t o = (size_t)seg * p.K + panel * KS + threadIdx.x;
-        s_sig[threadIdx.x] = (T)p.sig_cur[o];
-        s_cp[threadIdx.x] = p.first ? (T)0 : (T)(p.beta_prev[o] * p.sig_prev[o]);
+        s_sig[threadIdx.x] = (T)sv.sig_cur[o];
+        s_cp[threadIdx.x] = sv.first ? (T)0 : (T)(sv.beta_prev[o] * sv.sig_prev[o]);
     }
     __syncthreads();
     T dot[CPL];
@@ -488,7 +651,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
         for (int q = 0; q < CPL; q++) {
             T ax = VALUED ? acc[q] : ((T)deg * x[q] - acc[q]);
             T v = s_sig[cofs + q] * ax;
-            if (!p.first) v -= s_cp[cofs + q] * xp[q];
+            if (!sv.first) v -= s_cp[cofs + q] * xp[q];
             uu[q] = v;
             dt[q] += x[q] * v;
         }
@@ -498,7 +661,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
     auto epilogue = [&](int r, const T (&acc)[CPL], int deg, T (&dt)[CPL]) {
         T x[CPL], xp[CPL];
         load_lane(W + (size_t)r * KS + cofs, x);
-        if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+        if (!sv.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
         epilogue_x(r, acc, deg, dt, x, xp);
     };
 
@@ -524,7 +687,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
             T x[CPL], xp[CPL];
             if (PTAIL) {  // the row's own entries, in flight while it gathers
                 load_lane(W + (size_t)r * KS + cofs, x);
-                if (!p.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
+                if (!sv.first) load_lane_stream(Wp + (size_t)r * KS + cofs, xp);
             }
             T acc[CPL];
 #pragma unroll
@@ -682,7 +845,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
             double t = tot[threadIdx.x];
             for (int q = 0; q < NS; q++) t += hred[q * KS + threadIdx.x];
             size_t o = (size_t)seg * p.K + panel * KS + threadIdx.x;
-            p.alpha[o] = p.sig_cur[o] * t;
+            sv.alpha[o] = sv.sig_cur[o] * t;
         }
     }
 }
@@ -691,7 +854,7 @@ __global__ void __launch_bounds__(VNE_THREADS, MINB) k_step(StepParams<T> p) {
 // Update kernel: w_{j+1} = u - alpha_j sigma_j w_j (or, with `renorm`, just
 // the norm of w_{j+1} in place), beta_j = ||w_{j+1}||, sigma_{j+1} = 1/beta_j
 // unless beta_j <= tau (breakdown: beta_j = sigma_{j+1} = 0, column done).
-template <typename T, int KS>
+template <typename T, int KS, bool SEGJ = false>
 __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
     constexpr int CPL = LaneVec<T>::CPL;
     constexpr int LPR = KS / CPL;
@@ -704,6 +867,8 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
               tile = blockIdx.x % p.tiles_per_panel;
     if (p.renorm && p.panel_active && !p.panel_active[panel]) return;  // nothing changed in this panel
     const RowTile t = p.tiles[tile];
+    StepView<T> sv;
+    if (!step_view<SEGJ>(p, t.seg, sv)) return;  // idle segment: every CTA of it returns here
     const int sub = threadIdx.x % LPR, rsub = threadIdx.x / LPR;
     const int cofs = sub * CPL;
     const size_t pofs = (size_t)panel * p.n_total * KS;
@@ -711,12 +876,12 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
     T a[CPL], nrm[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; q++) {
-        a[q] = p.renorm ? (T)0 : (T)(p.alpha[so + q] * p.sig_cur[so + q]);
+        a[q] = p.renorm ? (T)0 : (T)(sv.alpha[so + q] * sv.sig_cur[so + q]);
         nrm[q] = (T)0;
     }
     const T* __restrict__ Uu = p.u + pofs;
-    const T* __restrict__ W = p.w_cur + pofs;
-    T* __restrict__ Wn = p.w_next + pofs;
+    const T* __restrict__ W = sv.w_cur + pofs;
+    T* __restrict__ Wn = sv.w_next + pofs;
     for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
         T uu[CPL], x[CPL], wn[CPL];
         if (p.renorm) {
@@ -747,12 +912,12 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
         if (threadIdx.x < KS) {
             size_t o = (size_t)t.seg * p.K + panel * KS + threadIdx.x;
             double b = sqrt(tot[threadIdx.x]);
-            if (!(b > sg.tau) || p.sig_cur[o] == 0.0) {
-                p.beta[o] = 0.0;
-                p.sig_next[o] = 0.0;
+            if (!(b > sg.tau) || sv.sig_cur[o] == 0.0) {
+                sv.beta[o] = 0.0;
+                sv.sig_next[o] = 0.0;
             } else {
-                p.beta[o] = b;
-                p.sig_next[o] = 1.0 / b;
+                sv.beta[o] = b;
+                sv.sig_next[o] = 1.0 / b;
             }
         }
     }
@@ -1067,6 +1232,31 @@ cudaError_t launch_update(const StepParams<T>& p, int ks, int panels, cudaStream
     return cudaGetLastError();
 }
 
+// One Lanczos step (step kernel, then update kernel) of a pattern operator
+// with per-segment step counters (p.segj): segment s runs its step
+// p.segj[s], idle segments (0) are skipped.  The step kernel is the
+// predicated-tail staged variant with four CTAs per SM.
+template <typename T>
+cudaError_t launch_srv_start(const SrvStartParams<T>& p, int ks, cudaStream_t st) {
+    if (p.ntiles == 0) return cudaSuccess;
+    if (p.K < 1 || p.K > 64 || p.K % ks) return cudaErrorInvalidValue;
+    k_srv_coef<T><<<p.ntiles, VNE_THREADS, 0, st>>>(p);
+    VNE_DISPATCH_KS(T, ks, (k_srv_pass<T, KS><<<p.ntiles, VNE_THREADS, 0, st>>>(p, 0)));
+    VNE_DISPATCH_KS(T, ks, (k_srv_pass<T, KS><<<p.ntiles, VNE_THREADS, 0, st>>>(p, 1)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step_update_segj(const StepParams<T>& p, int ks, int panels, cudaStream_t st) {
+    if (!p.segj) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)VNE_WARPS * (p.stage_nnz + kStageRp) * sizeof(int32_t);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    dim3 gs(panels * p.ctas_per_panel), gu(panels * p.tiles_per_panel);
+    VNE_DISPATCH_KS(T, ks, (k_step<T, KS, false, 4, 8, true, true, 0, true, true><<<gs, VNE_THREADS, smem, st>>>(p)));
+    VNE_DISPATCH_KS(T, ks, (k_update<T, KS, true><<<gu, VNE_THREADS, 0, st>>>(p)));
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_reorth(const ReorthParams<T>& p, const ReorthCoefParams& c, int ks, cudaStream_t st) {
     if (p.j <= 0) return cudaSuccess;
@@ -1123,6 +1313,8 @@ cudaError_t launch_gaussian_fill(uint64_t seed_mixed, int64_t n, int col_begin, 
     template cudaError_t launch_start<T>(const StartParams<T>&, int, int, cudaStream_t);                   \
     template cudaError_t launch_step<T>(const StepParams<T>&, int, int, bool, int, cudaStream_t);          \
     template cudaError_t launch_update<T>(const StepParams<T>&, int, int, cudaStream_t);                   \
+    template cudaError_t launch_step_update_segj<T>(const StepParams<T>&, int, int, cudaStream_t);         \
+    template cudaError_t launch_srv_start<T>(const SrvStartParams<T>&, int, cudaStream_t);                 \
     template cudaError_t launch_reorth<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
     template cudaError_t launch_col_dots<T>(const ReorthParams<T>&, const ReorthCoefParams&, int, cudaStream_t); \
     template cudaError_t launch_recover<T>(const RecoverParams<T>&, int, int, cudaStream_t);               \

@@ -1,24 +1,37 @@
 // Serving loop of libvne: continuous batching of entropy queries.
-#include "engine.h"
-
-// ---------------------------------------------------------------------------
-// serving: continuous batching of entropy queries
 //
-// Each tick admits queued requests (FIFO) while the active set fits the HBM
-// budget and the slot limit, packs the active graphs block-diagonally on the
-// device (their CSR stays resident from vne_create_density_matrix), and runs
-// one Lanczos block of `block` Rademacher probes per request in one batched
-// launch sequence.  A request's probes for tick t are its columns
-// t*block .. (t+1)*block-1, so its numbers do not depend on its neighbours.
-// After the block each request updates its running mean and variance and
-// retires once 2.576 * stderr <= (eps / 2) * |mean| (at least two blocks) or
-// its vector cap is reached.
+// A query asks for S(rho) of one graph to a relative accuracy eps.  The
+// server answers with Hutch++ (Section 3.2, eq. Hutch++_formula) in an
+// adaptive form: a fixed sketch of N_r = 4 columns when the query is
+// admitted (Q = orth(f(A) Omega) and psi(q_i), computed for the query alone),
+// then blocks of K deflated Hutchinson probes g' = (I - Q Q^T) g until
+// 2.576 * stderr <= (eps / 2) * |estimate| (at least two blocks) or the
+// probe cap; estimate = sum_i psi(q_i) + mean psi(g').  The adaptive
+// algorithm the paper cites is not printed in it; this is the stated proxy.
+//
+// Device layout: an arena of fixed capacity (rows, nonzeros) holds the
+// packed CSR of every admitted query and the Lanczos vectors of its current
+// block (two slots and u, panel-major, K columns) at a row range that the
+// query keeps from admission to completion; its CSR is copied there once.
+// Per-query scalars live in segment slot s (0 .. max_active - 1) of
+// [m][max_active * K] arrays.  The work tables of the packed operator are
+// rebuilt on the host only when the active set changes.
+//
+// A tick (vne_server_step) is one Lanczos step of every active query, each
+// at its own step j: queries whose block starts get their deflated start
+// vectors, one step and one update kernel run over all active segments with
+// per-segment step counters, and the queries whose block ends get their
+// Gauss quadratures and update their statistics.  Admission happens at every
+// tick, FIFO, while a segment slot and arena space are free.  A query's
+// numbers depend only on its own graph, seed and schedule, so they are the
+// same whatever runs beside it.
+#include "engine.h"
 
 namespace {
 
 __global__ void k_pack_rowptr(const int32_t* src, int n, int32_t e0, int32_t* dst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i] + e0;
+    if (i <= n) dst[i] = src[i] + e0;
 }
 __global__ void k_pack_col(const int32_t* src, int64_t nnz, int32_t r0, int32_t* dst) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,38 +42,416 @@ __global__ void k_pack_ids(const int32_t* perm, int n, int32_t* dst) {
     if (i < n) dst[i] = perm ? perm[i] : i;
 }
 
+// First-fit allocator of [begin, end) ranges of a fixed capacity.
+struct Ranges {
+    std::vector<std::pair<int64_t, int64_t>> free;  // sorted, disjoint
+    void reset(int64_t cap) {
+        free.clear();
+        if (cap > 0) free.push_back({0, cap});
+    }
+    int64_t take(int64_t size) {
+        for (size_t i = 0; i < free.size(); i++) {
+            const int64_t b = free[i].first, e = free[i].second;
+            if (e - b >= size) {
+                if (e - b == size) free.erase(free.begin() + i);
+                else free[i].first = b + size;
+                return b;
+            }
+        }
+        return -1;
+    }
+    void give(int64_t b, int64_t size) {
+        auto it = std::lower_bound(free.begin(), free.end(), std::make_pair(b, (int64_t)0));
+        it = free.insert(it, {b, b + size});
+        const size_t i = it - free.begin();
+        if (i + 1 < free.size() && free[i].second == free[i + 1].first) {
+            free[i].second = free[i + 1].second;
+            free.erase(free.begin() + i + 1);
+        }
+        if (i > 0 && free[i - 1].second == free[i].first) {
+            free[i - 1].second = free[i].second;
+            free.erase(free.begin() + i);
+        }
+    }
+};
+
+constexpr int kSketchCols = 4;  // N_r of the served Hutch++
+
 }  // namespace
 
 struct vne_server {
     vne_ctx* ctx = nullptr;
-    size_t budget = 0, used = 0;
-    int max_active = 64, m = 40, block = 64, max_vectors = 8192;
     vne_options opt;
+    size_t budget = 0, used = 0;
+    int max_active = 64, m = 40, K = 64, ks = 16, max_vectors = 8192;
+    int precision = -1;  // -1 not yet known, 0 FP32, 1 FP64 (all queries share it)
+    // arena
+    int64_t rows_cap = 0, nnz_cap = 0;
+    Ranges rows, nnz;
+    int32_t *a_rowptr = nullptr, *a_col = nullptr, *a_nid = nullptr;
+    void *slot0 = nullptr, *slot1 = nullptr, *u = nullptr, *q = nullptr;
+    double *alpha = nullptr, *beta = nullptr, *sigma = nullptr, *norm2 = nullptr, *mean = nullptr, *psi = nullptr,
+           *coef = nullptr, *scale = nullptr;
+    std::vector<void*> owned;
+    // segment slots
+    std::vector<int> slot_req;  // request index, -1 free
+    Problem P;                  // packed operator of the active set (tables in context workspace)
+    bool dirty = true;
     struct Req {
         vne_matrix* M;
         double eps;
-        uint64_t seed_mixed;
+        uint64_t seed, seed_mixed;
         int max_vectors;
         int state;  // 0 queued, 1 active, 2 done
-        int64_t nvec;
-        double mean, m2, est, se;
-        size_t footprint;
-        int64_t submit_tick, admit_tick, done_tick;
-        int blocks;
+        int slot = -1;
+        int64_t r0 = -1, e0 = -1;
+        int j = 0;  // Lanczos step of the current block, 0 = the block has not started
+        int blocks = 0;
+        int64_t nvec = 0;
+        double mean = 0.0, m2 = 0.0, low = 0.0, est = 0.0, se = 0.0;
+        int rank = 0;
+        size_t footprint = 0;
+        int64_t submit_tick = 0, admit_tick = -1, done_tick = -1;
     };
     std::vector<Req> reqs;
-    std::vector<int> pending;  // FIFO (front = index pend_head)
+    std::vector<int> pending;  // FIFO (front = pend_head)
     size_t pend_head = 0;
     std::vector<int> active;
     int64_t tick = 0;
+    ~vne_server() {
+        for (void* p : owned) dev_free(p);
+    }
 };
+
+namespace {
+
+size_t row_bytes(const vne_server* S, size_t es) {
+    // CSR offsets and node ids, two vector slots and u, the deflation basis
+    return 8 + 3 * (size_t)S->K * es + kSketchCols * es;
+}
+
+// Allocate the arena for the precision of the first query.
+void arena_alloc(vne_server* S, bool fp64) {
+    vne_ctx* ctx = S->ctx;
+    const size_t es = fp64 ? 8 : 4;
+    const int SK = S->max_active * S->K;
+    const size_t fixed = (size_t)(3 * S->m + 8 + 4) * SK * 8 + ((size_t)1 << 20);
+    VNE_REQUIRE(ctx, S->budget > fixed, VNE_ENOMEM, "HBM budget %zu too small for the server's scalars", S->budget);
+    // rows and nonzeros share the budget: up to 12 nonzeros per row
+    const size_t per_row = row_bytes(S, es) + 12 * 4;
+    S->rows_cap = (int64_t)std::min<size_t>((S->budget - fixed) / per_row, (size_t)INT32_MAX - 1);
+    S->nnz_cap = std::min<int64_t>(12 * S->rows_cap, INT32_MAX - 1);
+    auto take = [&](size_t bytes) {
+        void* p = nullptr;
+        VNE_TRY_CUDA(ctx, dev_malloc(&p, std::max<size_t>(bytes, 256)));
+        S->owned.push_back(p);
+        return p;
+    };
+    S->a_rowptr = (int32_t*)take((S->rows_cap + 1) * 4);
+    S->a_col = (int32_t*)take(std::max<int64_t>(S->nnz_cap, 1) * 4);
+    S->a_nid = (int32_t*)take(S->rows_cap * 4);
+    S->slot0 = take((size_t)S->rows_cap * S->K * es);
+    S->slot1 = take((size_t)S->rows_cap * S->K * es);
+    S->u = take((size_t)S->rows_cap * S->K * es);
+    S->q = take((size_t)S->rows_cap * kSketchCols * es);
+    S->alpha = (double*)take((size_t)S->m * SK * 8);
+    S->beta = (double*)take((size_t)S->m * SK * 8);
+    S->sigma = (double*)take((size_t)(S->m + 1) * SK * 8);
+    S->norm2 = (double*)take((size_t)SK * 8);
+    S->mean = (double*)take((size_t)SK * 8);
+    S->psi = (double*)take((size_t)SK * 8);
+    S->scale = (double*)take((size_t)SK * 8);
+    S->coef = (double*)take((size_t)kSketchCols * SK * 8);
+    if (fp64 && S->ks > 16) {  // FP64 panels hold 4, 8 or 16 columns
+        S->ks = 16;
+        S->K = ((S->K + 15) / 16) * 16;
+    }
+    S->rows.reset(S->rows_cap);
+    S->nnz.reset(S->nnz_cap);
+    S->slot_req.assign(S->max_active, -1);
+    S->precision = fp64 ? 1 : 0;
+}
+
+// Rebuild the work tables of the packed operator from the active set: every
+// slot is a segment (an empty one when free), each active query's own
+// schedule shifted to its arena rows and nonzeros.
+void rebuild_layout(vne_server* S) {
+    vne_ctx* ctx = S->ctx;
+    Problem& P = S->P;
+    P.owns_tables = false;
+    P.fp64 = S->precision == 1;
+    P.valued = false;
+    P.ipw = 1;
+    P.segs.assign(S->max_active, SegInfo{});
+    P.items.clear();
+    P.hubs.clear();
+    P.cta_seg.clear();
+    P.tiles.clear();
+    P.hub_slots = 0;
+    P.stage_nnz = 1;
+    std::vector<double> hscale((size_t)S->max_active * S->K, 0.0);
+    for (int s = 0; s < S->max_active; s++) {
+        const int ri = S->slot_req[s];
+        if (ri < 0) continue;
+        const vne_server::Req& rq = S->reqs[ri];
+        Problem* MP = matrix_problem(rq.M, &S->opt);
+        SegInfo sg = MP->segs[0];
+        const int32_t r0 = (int32_t)rq.r0, e0 = (int32_t)rq.e0, hub_base = (int32_t)P.hubs.size();
+        sg.row_begin = r0;
+        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);
+        sg.cta_count = (int32_t)(MP->items.size() / VNE_WARPS);
+        sg.tile_begin = (int32_t)P.tiles.size();
+        sg.hub_begin = hub_base;
+        for (WorkItem it : MP->items) {
+            if (it.rows > 0) it.row += r0;
+            else if (it.rows < 0) it.row += hub_base;
+            if (it.rows != 0) {
+                it.nnz_begin += e0;
+                it.nnz_end += e0;
+            }
+            P.items.push_back(it);
+        }
+        for (HubRow h : MP->hubs) {
+            h.row += r0;
+            h.slot += P.hub_slots;
+            h.seg = s;
+            P.hubs.push_back(h);
+        }
+        P.hub_slots += MP->hub_slots;
+        for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(s);
+        for (RowTile t : MP->tiles) {
+            t.row_begin += r0;
+            t.row_end += r0;
+            t.seg = s;
+            P.tiles.push_back(t);
+        }
+        P.stage_nnz = std::max(P.stage_nnz, MP->stage_nnz);
+        P.segs[s] = sg;
+        for (int c = 0; c < S->K; c++) hscale[(size_t)s * S->K + c] = sg.scale;
+    }
+    P.n_total = (int32_t)S->rows_cap;
+    P.nnz_total = S->nnz_cap;
+    P.nseg = S->max_active;
+    P.rowptr = S->a_rowptr;
+    P.col = S->a_col;
+    P.node_id = S->a_nid;
+    P.vals = nullptr;
+    P.d_segs = upload(ctx, "srv.segs", P.segs);
+    P.d_items = upload(ctx, "srv.items", P.items);
+    P.d_hubs = upload(ctx, "srv.hubs", P.hubs);
+    P.d_cta_seg = upload(ctx, "srv.ctaseg", P.cta_seg);
+    P.d_tiles = upload(ctx, "srv.tiles", P.tiles);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->scale, hscale.data(), hscale.size() * 8, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+    S->dirty = false;
+}
+
+// Admit the query at the head of the queue if a slot and arena space are
+// free: copy its CSR into the arena and compute its deflation basis.
+template <typename T>
+bool admit_one(vne_server* S, int ri) {
+    vne_ctx* ctx = S->ctx;
+    cudaStream_t st = ctx->stream;
+    vne_server::Req& rq = S->reqs[ri];
+    vne_matrix* M = rq.M;
+    int s = -1;
+    for (int i = 0; i < S->max_active && s < 0; i++)
+        if (S->slot_req[i] < 0) s = i;
+    if (s < 0) return false;
+    const int64_t r0 = S->rows.take(M->n + 1);  // one spare row holds the end offset
+    if (r0 < 0) return false;
+    const int64_t e0 = S->nnz.take(std::max<int64_t>(M->nnz, 1));
+    if (e0 < 0) {
+        S->rows.give(r0, M->n + 1);
+        return false;
+    }
+    const int n = (int)M->n;
+    k_pack_rowptr<<<(n + 256) / 256, 256, 0, st>>>(M->d_rowptr, n, (int32_t)e0, S->a_rowptr + r0);
+    if (M->nnz) k_pack_col<<<(unsigned)((M->nnz + 255) / 256), 256, 0, st>>>(M->d_col, M->nnz, (int32_t)r0, S->a_col + e0);
+    k_pack_ids<<<(n + 255) / 256, 256, 0, st>>>(M->d_node_id, n, S->a_nid + r0);
+    VNE_TRY_CUDA(ctx, cudaGetLastError());
+    ctx->launches += 3;
+    std::vector<double> psi_q;
+    int rank = 0;
+    vne_options o = S->opt;
+    o.probe_offset = 0;
+    hutchpp_deflation<T>(M, &o, kSketchCols, S->m, rq.seed, (T*)S->q + r0 * kSketchCols, psi_q, rank);
+    rq.low = 0.0;
+    for (int i = 0; i < rank; i++) rq.low += psi_q[i];
+    rq.rank = rank;
+    rq.slot = s;
+    rq.r0 = r0;
+    rq.e0 = e0;
+    rq.j = 0;
+    rq.state = 1;
+    rq.admit_tick = S->tick;
+    S->slot_req[s] = ri;
+    S->used += rq.footprint;
+    S->active.push_back(ri);
+    S->dirty = true;
+    return true;
+}
+
+void release(vne_server* S, vne_server::Req& rq) {
+    S->rows.give(rq.r0, rq.M->n + 1);
+    S->nnz.give(rq.e0, std::max<int64_t>(rq.M->nnz, 1));
+    S->slot_req[rq.slot] = -1;
+    S->used -= rq.footprint;
+    S->dirty = true;
+}
+
+template <typename T>
+int tick_impl(vne_server* S) {
+    vne_ctx* ctx = S->ctx;
+    cudaStream_t st = ctx->stream;
+    // admission, FIFO
+    while (S->pend_head < S->pending.size() && (int)S->active.size() < S->max_active) {
+        const int ri = S->pending[S->pend_head];
+        if (S->used + S->reqs[ri].footprint > S->budget) break;
+        if (!admit_one<T>(S, ri)) break;
+        S->pend_head++;
+    }
+    S->tick++;
+    if (S->active.empty()) return 0;
+    if (S->dirty) rebuild_layout(S);
+    Problem& P = S->P;
+    const int K = S->K, SK = S->max_active * K, ks = S->ks, panels = K / ks;
+    // blocks that start now: deflated start vectors
+    std::vector<int32_t> tlist, tb(S->max_active, 0), tc(S->max_active, 0), col0(S->max_active, 0);
+    std::vector<uint64_t> seeds(S->max_active, 0);
+    for (int ri : S->active) {
+        vne_server::Req& rq = S->reqs[ri];
+        const SegInfo& sg = P.segs[rq.slot];
+        seeds[rq.slot] = rq.seed_mixed;
+        if (rq.j != 0) continue;
+        tb[rq.slot] = (int32_t)tlist.size();
+        tc[rq.slot] = sg.tile_count;
+        col0[rq.slot] = kSketchCols + rq.blocks * K;
+        for (int t = 0; t < sg.tile_count; t++) tlist.push_back(sg.tile_begin + t);
+        rq.j = 1;
+    }
+    if (!tlist.empty()) {
+        SrvStartParams<T> sp{};
+        sp.tile_list = upload(ctx, "srv.tlist", tlist);
+        sp.tiles = P.d_tiles;
+        sp.seg = P.d_segs;
+        sp.seg_tb = upload(ctx, "srv.tb", tb);
+        sp.seg_tc = upload(ctx, "srv.tc", tc);
+        sp.node_id = P.node_id;
+        sp.seg_seed = upload(ctx, "srv.seeds", seeds);
+        sp.seg_col0 = upload(ctx, "srv.col0", col0);
+        sp.q = (const T*)S->q;
+        sp.coef = S->coef;
+        sp.mean = S->mean;
+        sp.norm2 = S->norm2;
+        sp.sig1 = S->sigma;
+        sp.w1 = (T*)S->slot0;
+        sp.part = ws_get_t<double>(ctx, "srv.part", tlist.size() * kSketchCols * K);
+        sp.counter = ws_get_t<uint32_t>(ctx, "srv.counter", S->max_active);
+        sp.ntiles = (int32_t)tlist.size();
+        sp.K = K;
+        sp.n_total = P.n_total;
+        sp.gaussian = S->opt.gaussian_probes != 0;
+        VNE_TRY_CUDA(ctx, launch_srv_start<T>(sp, ks, st));
+        ctx->launches += 3;
+    }
+    // one Lanczos step of every active segment, each at its own step
+    std::vector<int32_t> segj(S->max_active, 0);
+    for (int ri : S->active) segj[S->reqs[ri].slot] = S->reqs[ri].j;
+    StepParams<T> p;
+    memset(&p, 0, sizeof(p));
+    p.rowptr = P.rowptr;
+    p.col = P.col;
+    p.n_total = P.n_total;
+    p.K = K;
+    p.nseg = P.nseg;
+    p.seg = P.d_segs;
+    p.items = P.d_items;
+    p.ctas_per_panel = P.ctas_per_panel();
+    p.cta_seg = P.d_cta_seg;
+    p.hubs = P.d_hubs;
+    p.nhubs = std::max<int>((int)P.hubs.size(), 1);
+    p.hub_slots = std::max(P.hub_slots, 1);
+    p.hub_part = ws_get_t<T>(ctx, "srv.hub_part", (size_t)panels * p.hub_slots * ks);
+    p.hub_cnt = ws_get_t<uint32_t>(ctx, "srv.hub_cnt", (size_t)panels * p.nhubs);
+    p.hub_dot = ws_get_t<double>(ctx, "srv.hub_dot", (size_t)panels * p.nhubs * ks);
+    p.stage_nnz = std::max(P.stage_nnz, 1);
+    p.ipw = 1;
+    p.tiles = P.d_tiles;
+    p.tiles_per_panel = P.tiles_per_panel();
+    p.u = (T*)S->u;
+    p.part = ws_get_t<double>(ctx, "srv.step_part",
+                              (size_t)panels * std::max(P.ctas_per_panel(), P.tiles_per_panel()) * ks);
+    p.counter = ws_get_t<uint32_t>(ctx, "srv.step_counter", (size_t)panels * P.nseg);
+    p.segj = upload(ctx, "srv.segj", segj);
+    p.slot0 = (T*)S->slot0;
+    p.slot1 = (T*)S->slot1;
+    p.alpha0 = S->alpha;
+    p.beta0 = S->beta;
+    p.sigma0 = S->sigma;
+    if (P.ctas_per_panel() > 0) {
+        VNE_TRY_CUDA(ctx, launch_step_update_segj<T>(p, ks, panels, st));
+        ctx->launches += 2;
+    }
+    // blocks that end now: quadratures and statistics
+    std::vector<int> ending;
+    for (int ri : S->active)
+        if (S->reqs[ri].j == S->m) ending.push_back(ri);
+    for (int ri : ending) {
+        const int s = S->reqs[ri].slot;
+        const size_t o = (size_t)s * K;
+        VNE_TRY_CUDA(ctx, launch_tridiag_quad(S->alpha + o, S->beta + o, S->norm2 + o, S->scale + o, K, S->m, SK,
+                                              S->psi + o, st));
+        ctx->launches += 1;
+    }
+    int completed = 0;
+    if (!ending.empty()) {
+        std::vector<double> hp = download(ctx, S->psi, SK);
+        std::vector<int> still;
+        for (int ri : S->active) {
+            vne_server::Req& rq = S->reqs[ri];
+            if (rq.j != S->m) {
+                rq.j++;
+                still.push_back(ri);
+                continue;
+            }
+            for (int c = 0; c < K; c++) {  // Welford update
+                const double x = hp[(size_t)rq.slot * K + c];
+                rq.nvec++;
+                const double d = x - rq.mean;
+                rq.mean += d / (double)rq.nvec;
+                rq.m2 += d * (x - rq.mean);
+            }
+            rq.blocks++;
+            rq.est = rq.low + rq.mean;
+            rq.se = rq.nvec > 1 ? sqrt(rq.m2 / (double)(rq.nvec - 1) / (double)rq.nvec) : 0.0;
+            const bool converged = rq.blocks >= 2 && 2.576 * rq.se <= 0.5 * rq.eps * fabs(rq.est);
+            if (converged || rq.nvec >= rq.max_vectors) {
+                rq.state = 2;
+                rq.done_tick = S->tick;
+                release(S, rq);
+                completed++;
+            } else {
+                rq.j = 0;  // the next block starts at the next tick
+                still.push_back(ri);
+            }
+        }
+        S->active.swap(still);
+    } else {
+        for (int ri : S->active) S->reqs[ri].j++;
+    }
+    return completed;
+}
+
+}  // namespace
 
 extern "C" vne_status vne_server_create(vne_ctx* ctx, uint64_t hbm_budget_bytes, int32_t max_active,
                                         int32_t krylov_steps, int32_t block_vectors, const vne_options* opt,
                                         vne_server** out) {
     if (!ctx || !out) return VNE_EINVAL;
     *out = nullptr;
-    if (max_active < 1 || krylov_steps < 1 || krylov_steps > 128 || block_vectors < 2 || block_vectors > 256)
+    if (max_active < 1 || max_active > 1024 || krylov_steps < 1 || krylov_steps > 128 || block_vectors < 8 ||
+        block_vectors > 64)
         return VNE_EINVAL;
     vne_server* S = new (std::nothrow) vne_server();
     if (!S) return VNE_ENOMEM;
@@ -68,15 +459,25 @@ extern "C" vne_status vne_server_create(vne_ctx* ctx, uint64_t hbm_budget_bytes,
     S->budget = hbm_budget_bytes;
     S->max_active = max_active;
     S->m = krylov_steps;
-    S->block = block_vectors;
     if (opt) S->opt = *opt;
     else vne_options_default(&S->opt);
+    S->opt.reorth = 0;
+    S->ks = S->opt.panel > 0 ? S->opt.panel : 16;
+    if (S->ks != 8 && S->ks != 16 && S->ks != 32) S->ks = 16;
+    S->K = ((block_vectors + S->ks - 1) / S->ks) * S->ks;
+    if (S->K > 64) {
+        delete S;
+        return VNE_EINVAL;
+    }
     *out = S;
     return VNE_OK;
 }
 
 extern "C" vne_status vne_server_destroy(vne_server* S) {
     if (!S) return VNE_EINVAL;
+    cudaSetDevice(S->ctx->device);
+    if (S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
+    else cudaDeviceSynchronize();
     delete S;
     return VNE_OK;
 }
@@ -85,28 +486,29 @@ extern "C" vne_status vne_server_submit(vne_server* S, vne_matrix* M, double rel
                                         int32_t max_vectors, int32_t* ticket) {
     if (!S || !M || !ticket || !(rel_eps > 0.0) || max_vectors < 2) return VNE_EINVAL;
     vne_ctx* ctx = S->ctx;
-    if (M->ctx != ctx || M->fp64 || !M->pattern) {
-        set_err(ctx, "serving takes FP32 graph (pattern) matrices of the server's context");
-        return VNE_EINVAL;
-    }
+    VNE_API_BEGIN
+    cudaSetDevice(ctx->device);
+    VNE_REQUIRE(ctx, M->ctx == ctx && M->pattern && M->desing, VNE_EINVAL,
+                "serving takes graph (pattern) matrices of the server's context");
+    VNE_REQUIRE(ctx, S->precision < 0 || S->precision == (M->fp64 ? 1 : 0), VNE_EINVAL,
+                "all queries of a server share one precision");
+    if (S->precision < 0) arena_alloc(S, M->fp64);
+    const size_t es = M->fp64 ? 8 : 4;
     vne_server::Req r{};
     r.M = M;
     r.eps = rel_eps;
+    r.seed = seed;
     r.seed_mixed = seed_mix(seed);
     r.max_vectors = max_vectors;
-    const int ks = resolve_sched(M, &S->opt).ks;
-    const int Kp = ((S->block + ks - 1) / ks) * ks;
-    // resident CSR + the block's Lanczos vectors (2 slots + u) + scalars
-    r.footprint = (size_t)4 * (M->n + 1 + M->nnz) + (size_t)3 * M->n * Kp * 4 + (size_t)(3 * S->m + 8) * Kp * 8;
-    if (r.footprint > S->budget) {
-        set_err(ctx, "request footprint %zu exceeds the HBM budget %zu", r.footprint, S->budget);
-        return VNE_ENOMEM;
-    }
+    r.footprint = (size_t)(M->n + 1) * row_bytes(S, es) + (size_t)4 * M->nnz;
+    VNE_REQUIRE(ctx, M->n + 1 <= S->rows_cap && M->nnz <= S->nnz_cap && r.footprint <= S->budget, VNE_ENOMEM,
+                "query of %lld rows and %lld nonzeros exceeds the server's capacity", (long long)M->n,
+                (long long)M->nnz);
     r.submit_tick = S->tick;
     *ticket = (int32_t)S->reqs.size();
     S->reqs.push_back(r);
     S->pending.push_back(*ticket);
-    return VNE_OK;
+    VNE_API_END(ctx)
 }
 
 extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t* active_count) {
@@ -114,145 +516,11 @@ extern "C" vne_status vne_server_step(vne_server* S, int32_t* completed, int32_t
     vne_ctx* ctx = S->ctx;
     VNE_API_BEGIN
     cudaSetDevice(ctx->device);
-    if (completed) *completed = 0;
-    // admission
-    while (S->pend_head < S->pending.size() && (int)S->active.size() < S->max_active) {
-        vne_server::Req& r = S->reqs[S->pending[S->pend_head]];
-        if (S->used + r.footprint > S->budget) break;
-        S->used += r.footprint;
-        r.state = 1;
-        r.admit_tick = S->tick;
-        S->active.push_back(S->pending[S->pend_head]);
-        S->pend_head++;
-    }
+    int done = 0;
+    if (S->precision == 1) done = tick_impl<double>(S);
+    else if (S->precision == 0) done = tick_impl<float>(S);
+    if (completed) *completed = done;
     if (active_count) *active_count = (int32_t)S->active.size();
-    S->tick++;
-    if (S->active.empty()) return VNE_OK;
-    const vne_options& o = S->opt;
-    // all active matrices share the schedule knobs of the server options
-    const int target = default_item_nnz(&o);
-    int ks = 0, variant = 0;
-    Problem P;
-    P.owns_tables = false;
-    P.fp64 = false;
-    P.valued = false;
-    int64_t ntot = 0, nnztot = 0;
-    for (int idx : S->active) {
-        ntot += S->reqs[idx].M->n;
-        nnztot += S->reqs[idx].M->nnz;
-    }
-    VNE_REQUIRE(ctx, ntot < INT32_MAX && nnztot < INT32_MAX, VNE_EINVAL, "active set too large");
-    int32_t* prp = ws_get_t<int32_t>(ctx, "srv.rowptr", ntot + 1);
-    int32_t* pci = ws_get_t<int32_t>(ctx, "srv.col", std::max<int64_t>(nnztot, 1));
-    int32_t* pid = ws_get_t<int32_t>(ctx, "srv.ids", ntot);
-    std::vector<uint64_t> seeds;
-    std::vector<int32_t> col0;
-    int64_t r0 = 0, e0 = 0;
-    cudaStream_t st = ctx->stream;
-    for (size_t sidx = 0; sidx < S->active.size(); sidx++) {
-        vne_server::Req& rq = S->reqs[S->active[sidx]];
-        vne_matrix* M = rq.M;
-        Sched sc = resolve_sched(M, &o);
-        if (sidx == 0) {
-            ks = sc.ks;
-            variant = sc.variant;
-        }
-        Problem* MP = matrix_problem(M, &o);  // the matrix's own (cached) schedule
-        const int n = (int)M->n;
-        k_pack_rowptr<<<(n + 255) / 256, 256, 0, st>>>(M->d_rowptr, n, (int32_t)e0, prp + r0);
-        if (M->nnz) k_pack_col<<<(unsigned)((M->nnz + 255) / 256), 256, 0, st>>>(M->d_col, M->nnz, (int32_t)r0, pci + e0);
-        k_pack_ids<<<(n + 255) / 256, 256, 0, st>>>(M->d_node_id, n, pid + r0);
-        ctx->launches += 3;
-        SegInfo sg = MP->segs[0];
-        const int32_t seg = (int32_t)sidx;
-        const int32_t hub_base = (int32_t)P.hubs.size(), slot_base = P.hub_slots;
-        sg.row_begin = (int32_t)r0;
-        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);  // the packed problem takes one item per warp
-        sg.cta_count = (int32_t)(MP->items.size() / VNE_WARPS);
-        sg.tile_begin = (int32_t)P.tiles.size();
-        sg.hub_begin = hub_base;
-        for (WorkItem it : MP->items) {
-            if (it.rows > 0) it.row += (int32_t)r0;
-            else if (it.rows < 0) it.row += hub_base;
-            if (it.rows != 0) {
-                it.nnz_begin += (int32_t)e0;
-                it.nnz_end += (int32_t)e0;
-            }
-            P.items.push_back(it);
-        }
-        for (HubRow h : MP->hubs) {
-            h.row += (int32_t)r0;
-            h.slot += slot_base;
-            h.seg = seg;
-            P.hubs.push_back(h);
-        }
-        P.hub_slots += MP->hub_slots;
-        for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(seg);
-        for (RowTile t : MP->tiles) {
-            t.row_begin += (int32_t)r0;
-            t.row_end += (int32_t)r0;
-            t.seg = seg;
-            P.tiles.push_back(t);
-        }
-        P.stage_nnz = std::max(P.stage_nnz, MP->stage_nnz);
-        P.segs.push_back(sg);
-        seeds.push_back(rq.seed_mixed);
-        col0.push_back(rq.blocks * S->block);
-        r0 += M->n;
-        e0 += M->nnz;
-    }
-    const int32_t last = (int32_t)nnztot;
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(prp + ntot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    VNE_TRY_CUDA(ctx, cudaGetLastError());
-    P.n_total = (int32_t)ntot;
-    P.nnz_total = nnztot;
-    P.nseg = (int32_t)S->active.size();
-    P.rowptr = prp;
-    P.col = pci;
-    P.node_id = pid;
-    P.d_segs = upload(ctx, "srv.segs", P.segs);
-    P.d_items = upload(ctx, "srv.items", P.items);
-    P.d_hubs = upload(ctx, "srv.hubs", P.hubs);
-    P.d_cta_seg = upload(ctx, "srv.ctaseg", P.cta_seg);
-    P.d_tiles = upload(ctx, "srv.tiles", P.tiles);
-    StartSource src{};
-    src.kind = SRC_RADEMACHER;
-    src.gaussian = S->opt.gaussian_probes != 0;
-    src.ncols = S->block;
-    src.seg_seed = upload(ctx, "srv.seeds", seeds);
-    src.seg_col0 = upload(ctx, "srv.col0", col0);
-    BlockOut out;
-    check_ks<float>(ctx, ks);
-    ctx->last_steps = 0;
-    run_block<float>(ctx, P, src, nullptr, S->block, ks, S->m, false, false, true, "srv", out, variant, false,
-                     S->opt.graphs != 0);
-    std::vector<double> psi = download(ctx, out.psi, out.SK);
-    // statistics and retirement
-    std::vector<int> still;
-    for (size_t sidx = 0; sidx < S->active.size(); sidx++) {
-        const int idx = S->active[sidx];
-        vne_server::Req& rq = S->reqs[idx];
-        for (int c = 0; c < S->block; c++) {  // Welford update
-            const double x = psi[sidx * out.Kp + c];
-            rq.nvec++;
-            const double d = x - rq.mean;
-            rq.mean += d / (double)rq.nvec;
-            rq.m2 += d * (x - rq.mean);
-        }
-        rq.blocks++;
-        rq.est = rq.mean;
-        rq.se = rq.nvec > 1 ? sqrt(rq.m2 / (double)(rq.nvec - 1) / (double)rq.nvec) : 0.0;
-        const bool converged = rq.blocks >= 2 && 2.576 * rq.se <= 0.5 * rq.eps * fabs(rq.mean);
-        if (converged || rq.nvec >= rq.max_vectors) {
-            rq.state = 2;
-            rq.done_tick = S->tick;
-            S->used -= rq.footprint;
-            if (completed) (*completed)++;
-        } else {
-            still.push_back(idx);
-        }
-    }
-    S->active.swap(still);
     VNE_API_END(ctx)
 }
 
