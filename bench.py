@@ -61,8 +61,9 @@ def parse():
                     help="node relabelling of the headline matrix (default: descending degree)")
     ap.add_argument("--schedule", default="",
                     help="panel,item_nnz,step_variant[,interleave[,items_per_warp]] (skips the autotuner)")
-    ap.add_argument("--reorth", choices=["none", "partial"], default="none",
-                    help="Lanczos reorthogonalisation of the FP32 estimate (partial: Simon's omega recurrence)")
+    ap.add_argument("--reorth", choices=["none", "partial", "full"], default="none",
+                    help="Lanczos reorthogonalisation of the FP32 estimate (partial: Simon's omega recurrence; "
+                         "full: classical Gram-Schmidt twice at every step)")
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c6", "c7"], default="c2",
                     help="c2 = the headline workload; c1/c3/c4/c5/c6/c7 print measurement lines of the other configs")
     ap.add_argument("--requests", type=int, default=2000, help="c5: number of queries")
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--fp64-limit-s", type=float, default=600.0,
                     help="c5: wall-time limit of the FP64 one-at-a-time arm (it serves a prefix of the queries)")
     ap.add_argument("--scaling-exponents", default="10,12,14,16,18,20", help="c7: n = 2^e for these e")
+    ap.add_argument("--scaling-runs", type=int, default=10, help="c7: seeds averaged for the stochastic estimator")
+    ap.add_argument("--ba-max-colors", type=int, default=10000,
+                    help="c7: BA probing is not run above a size whose colouring needed more colours")
     return ap.parse_args()
 
 
@@ -334,7 +338,7 @@ def run_native(args):
     vne.vne_ctx_set_stream(ctx, stream)
     flags = vne.VNE_FP32 | {"degree": vne.VNE_REORDER, "rcm": vne.VNE_REORDER_RCM, "none": 0}[args.reorder]
     mat = vne.vne_create_density_matrix(ctx, g.n, g.rowptr, g.col, None, flags)
-    reorth = {"none": 0, "partial": 2}[args.reorth]
+    reorth = {"none": 0, "partial": 2, "full": 1}[args.reorth]
     opt = vne.options(reorth=reorth)
     seed0 = 1000 * (rank + 1)
     if args.schedule:
@@ -438,7 +442,9 @@ def run_native(args):
     per_launch_bytes = byts / cnt if cnt else None
     roof = {"kernel": "k_step (fused SpMM + Lanczos partial inner products)", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
-            "peak_kind": peak_kind, "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
+            "peak_kind": peak_kind, "nominal_peak": 7900.0,
+            "frac_of_nominal": achieved / 7900.0 if achieved else None,
+            "traffic": recorded_traffic(), "algorithmic_bytes_per_launch": per_launch_bytes,
             "avg_launch_ms": ms / cnt if cnt else None, "launches_timed": int(cnt),
             "share_of_step_time": (ms / elapsed_ms) if elapsed_ms else None}
     # the same launches counted by what they move through L2: every nonzero
@@ -680,10 +686,16 @@ def run_scaling(args, ctx, stream):
     """Scaling study of Section 6 (Figure 6): seconds per estimate against n =
     2^10 .. 2^20 for the 2D square grid and BA graphs, probing with the
     heuristic choice of d at eps = 1e-4 (grid: the optimal lattice colouring,
-    BA: Algorithm 1 on the device) and the stochastic estimator at eps = 1e-2
-    (the serving proxy: Hutchinson blocks of 64 probes until 2.576 stderr <=
-    eps/2 |S|, one query at a time).  Each point: one warm-up call, then the
-    best of `steps` timed calls (CUDA events on the library stream)."""
+    BA: Algorithm 1 on the device) and the adaptive stochastic estimator at
+    eps = 1e-2 (the served Hutch++ proxy: N_r = 4 sketch columns, then blocks
+    of 64 deflated probes until 2.576 stderr <= eps/2 |S|, one query at a time
+    on a server made for the graph), averaged over `--scaling-runs` seeds as
+    the paper averages its adaptive Hutch++ over many runs.  Probing: one
+    warm-up call, then the best of `steps` timed calls (CUDA events on the
+    library stream).  BA probing stops growing n once the previous size took
+    longer than 10 s or needed more than `--ba-max-colors` colours: the
+    colour count of a distance-d colouring of a BA graph grows with n, and
+    the probing cost with colours x n."""
     import numpy as np
     import torch
     from paper_2212_09642_gb300 import graphs, grid_coloring, vne
@@ -701,15 +713,30 @@ def run_scaling(args, ctx, stream):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         return best, out
 
-    def stochastic(mat, seed):
-        srv = vne.vne_server_create(ctx, 64 << 30, max_active=1, krylov_steps=40, block_vectors=64,
+    def stochastic(mat, n, seeds):
+        """Seconds per served query (wall clock from submission to the
+        result, device synchronised at both ends) for each seed, after one
+        warm-up query; the server is created once per graph."""
+        srv = vne.vne_server_create(ctx, (1 << 30) + 1200 * n, max_active=1, krylov_steps=40, block_vectors=64,
                                     opt=vne.options(reorth=0))
-        t = vne.vne_server_submit(ctx, srv, mat, 1e-2, seed, 1 << 16)
-        while vne.vne_server_result(srv, t)["state"] != 2:
-            vne.vne_server_step(ctx, srv)
-        r = vne.vne_server_result(srv, t)
-        vne.vne_server_destroy(srv)
-        return r
+        try:
+            def one(seed):
+                t = vne.vne_server_submit(ctx, srv, mat, 1e-2, seed, 1 << 16)
+                while vne.vne_server_result(srv, t)["state"] != 2:
+                    vne.vne_server_step(ctx, srv)
+                return vne.vne_server_result(srv, t)
+            one(seeds[0] + 7919)
+            times, res = [], []
+            for sd in seeds:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = one(sd)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+                res.append(r)
+        finally:
+            vne.vne_server_destroy(srv)
+        return times, res
 
     reps = max(1, min(args.steps, 3))
     exps = [int(e) for e in args.scaling_exponents.split(",")]
@@ -717,6 +744,7 @@ def run_scaling(args, ctx, stream):
     sampler = ClockSampler(0)
     sampler.__enter__()
     ba_budget_s = 10.0  # BA probing stops growing n once one estimate takes longer
+    ba_colors_ok = True  # ... or once it needs more than --ba-max-colors colours
     for kind in ("grid", "ba"):
         for e in exps:
             n = 1 << e
@@ -729,7 +757,7 @@ def run_scaling(args, ctx, stream):
                 colfn = None
             mat = vne.matrix_from_graph(ctx, g, fp64=False, reorder=True)
             pt = {"graph": kind, "n": g.n, "nnz": g.nnz}
-            if kind == "grid" or ba_budget_s > 0:
+            if kind == "grid" or (ba_budget_s > 0 and ba_colors_ok):
                 t_p, (est, rep) = timed(lambda: vne.vne_entropy_probing_auto(
                     ctx, mat, 1e-4, 128, 32, opt=vne.options(check_every=2), coloring=colfn), reps)
                 pt["probing"] = {"s_per_estimate": t_p, "estimate": est, "d": rep["d"], "colors": rep["colors"],
@@ -737,11 +765,20 @@ def run_scaling(args, ctx, stream):
                                  "lanczos_steps": rep["steps_d"] + [rep["steps"]]}
                 if kind == "ba" and t_p > ba_budget_s:
                     ba_budget_s = 0.0
+                if kind == "ba" and rep["colors"] > args.ba_max_colors:
+                    ba_colors_ok = False
             else:
-                pt["probing"] = "not run: the previous BA size took longer than 10 s per estimate"
-            t_s, r = timed(lambda: stochastic(mat, 77 + e), reps)
-            pt["stochastic"] = {"s_per_estimate": t_s, "estimate": r["estimate"], "std_error": r["std_error"],
-                                "vectors": r["vectors"]}
+                pt["probing"] = (f"not run: the previous BA size took longer than 10 s per estimate or needed "
+                                 f"more than {args.ba_max_colors} colours")
+            times, rs = stochastic(mat, g.n, [1000 * e + r for r in range(args.scaling_runs)])
+            ests = np.array([r["estimate"] for r in rs])
+            pt["stochastic"] = {"s_per_estimate_mean": float(np.mean(times)), "s_per_estimate_min": float(min(times)),
+                                "s_per_estimate_max": float(max(times)), "runs": len(times),
+                                "estimate_mean": float(np.mean(ests)),
+                                "estimate_spread": float(np.std(ests) / abs(np.mean(ests))) if len(ests) > 1 else 0.0,
+                                "vectors_mean": float(np.mean([r["vectors"] for r in rs])),
+                                "vectors_min": int(min(r["vectors"] for r in rs)),
+                                "vectors_max": int(max(r["vectors"] for r in rs))}
             curve.append(pt)
             vne.vne_matrix_destroy(mat)
             print(json.dumps(pt), file=sys.stderr, flush=True)
@@ -753,9 +790,11 @@ def run_scaling(args, ctx, stream):
             "config": {"workload": "scaling study: 2D square grids and BA m=2 graphs, n = 2^" + ",".join(map(str, exps))
                                    + "; probing with the heuristic choice of d at eps 1e-4 (grid: lattice "
                                    "colouring with ceil((d+1)^2/2) colours; BA: device greedy colouring), Lanczos "
-                                   "stopped by Theorem 4.4 (checks every 2 steps, at most 128); stochastic proxy at "
-                                   "eps 1e-2 (Hutchinson blocks of 64 x 40 steps)",
-                       "timing": f"best of {reps} after one warm-up, CUDA events",
+                                   "stopped by Theorem 4.4 (checks every 2 steps, at most 128); adaptive Hutch++ "
+                                   "proxy at eps 1e-2 (N_r = 4 sketch columns, blocks of 64 deflated probes x 40 "
+                                   f"steps), mean over {args.scaling_runs} seeds",
+                       "timing": f"probing: best of {reps} after one warm-up, CUDA events; stochastic: wall clock "
+                                 "per served query, device synchronised, after one warm-up query",
                        "l2": "small sizes are L2-resident (the curve spans both regimes)"},
             "curve": curve, "clocks": sampler.summary()}
 

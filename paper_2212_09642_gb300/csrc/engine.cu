@@ -472,6 +472,7 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
                 rp.part = rpart;
                 rp.coef = rcoef;
                 rp.panel_active = pro.panel_active;
+                rp.sel = pro.sel;
                 ReorthCoefParams cp{};
                 cp.part = rpart;
                 cp.sig = sigma;
@@ -553,7 +554,8 @@ void run_block(vne_ctx* ctx, Problem& P, const StartSource& src, const T* panel_
         const int ints[] = {(int)sizeof(T), ks, panels, m, variant, (int)interleave, (int)reorth, (int)store_all,
                             (int)P.valued, SK};
         put(ints, sizeof(ints));
-        const void* ptrs[] = {slots, alpha, beta, sigma, rcoef, rpart};
+        const void* ptrs[] = {slots,     alpha,    beta,         sigma,    rcoef,          rpart,
+                              pro.omega, pro.sel,     pro.pend_sel, pro.pend, pro.panel_active};
         put(ptrs, sizeof(ptrs));
         put(&slot_elems, sizeof(slot_elems));
         put(&p, sizeof(p));

@@ -95,6 +95,7 @@ struct ReorthParams {
     double* part;         // [panels][j][tiles][KS]
     const double* coef;   // [j][K]
     const int32_t* panel_active;  // nullable: panels with no column to orthogonalise are skipped
+    const uint8_t* sel;   // nullable [j][K]: a (panel, i) with no selected column is skipped
 };
 
 struct ReorthCoefParams {

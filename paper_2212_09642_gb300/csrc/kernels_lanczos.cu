@@ -926,29 +926,94 @@ __global__ void __launch_bounds__(VNE_THREADS) k_update(StepParams<T> p) {
 // ---------------------------------------------------------------------------
 // Full reorthogonalisation (classical Gram-Schmidt pass) of w_{j+1} against
 // v_i = sigma_i w_i, i = 1..j, all stored in consecutive slots.
-// Pass A: coef_i = sigma_i^2 (w_i . w_{j+1}) for every (i, column).
+// The passes stream a row tile of one panel, which is a contiguous run of
+// (rows x KS) elements, in 16-byte chunks: thread t takes chunks t, t + 256,
+// ..., all of them in the same column group (t mod KS/V, V elements a chunk).
+// Pass A: coef_i = sigma_i^2 (w_i . w_{j+1}) for every (i, column).  Products
+// are formed in the vector precision and summed in runs of 16 chunks before
+// the FP64 sum (GB300 retires FP64 at a small fraction of the FP32 rate; a
+// run keeps the FP32 error near 16 units of the run's magnitude).  With a
+// selection, a (panel, i) whose columns all skip basis vector i does nothing:
+// pass B sets its coefficients to zero without its partials.
+constexpr int kReorthMaxJ = 136;  // basis vectors per pass (m <= 128 Lanczos steps)
+
+template <typename T>
+struct Chunk16 {
+    static constexpr int V = 16 / (int)sizeof(T);
+    T x[V];
+};
+
+template <typename T>
+__device__ __forceinline__ Chunk16<T> load_chunk(const T* p) {
+    Chunk16<T> c;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        c.x[0] = v.x; c.x[1] = v.y; c.x[2] = v.z; c.x[3] = v.w;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        c.x[0] = v.x; c.x[1] = v.y;
+    }
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_chunk(T* p, const Chunk16<T>& c) {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(c.x[0], c.x[1], c.x[2], c.x[3]);
+    else *reinterpret_cast<double2*>(p) = make_double2(c.x[0], c.x[1]);
+}
+
+template <typename T, int KS>
+__device__ __forceinline__ bool reorth_panel_uses(const ReorthParams<T>& p, int panel, int i) {
+    if (!p.sel) return true;
+    const uint8_t* s = p.sel + (size_t)i * p.K + (size_t)panel * KS;
+    int any = 0;
+#pragma unroll
+    for (int c = 0; c < KS; c++) any |= s[c];
+    return any != 0;
+}
+
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) {
+    constexpr int V = Chunk16<T>::V, G = KS / V;
+    static_assert(KS % V == 0 && VNE_THREADS % G == 0, "chunk layout");
     // grid: panel * tiles * j ; each CTA: one tile, one i
     const int i = blockIdx.x % p.j;
     const int pt = blockIdx.x / p.j;
     const int panel = pt / p.tiles_per_panel, tile = pt % p.tiles_per_panel;
     if (p.panel_active && !p.panel_active[panel]) return;
+    if (!reorth_panel_uses<T, KS>(p, panel, i)) return;
     const RowTile t = p.tiles[tile];
-    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
-    constexpr int RPI = VNE_THREADS / KS;
-    const size_t pofs = (size_t)panel * p.n_total * KS;
-    const T* Wi = p.basis + (size_t)i * p.slot_stride + pofs;
-    const T* Wn = p.w + pofs;
-    double acc = 0.0;
-    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI)
-        acc += (double)Wi[(size_t)r * KS + c] * (double)Wn[(size_t)r * KS + c];
-    __shared__ double red[VNE_THREADS];
-    red[threadIdx.x] = acc;
+    const size_t base = (size_t)panel * p.n_total * KS + (size_t)t.row_begin * KS;
+    const T* Wi = p.basis + (size_t)i * p.slot_stride + base;
+    const T* Wn = p.w + base;
+    const int nchunks = (t.row_end - t.row_begin) * G;
+    double acc[V];
+#pragma unroll
+    for (int e = 0; e < V; e++) acc[e] = 0.0;
+    for (int q0 = threadIdx.x; q0 < nchunks; q0 += 16 * VNE_THREADS) {
+        T run[V];
+#pragma unroll
+        for (int e = 0; e < V; e++) run[e] = (T)0;
+#pragma unroll 4
+        for (int u = 0; u < 16; u++) {
+            const int q = q0 + u * VNE_THREADS;
+            if (q < nchunks) {
+                const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
+#pragma unroll
+                for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < V; e++) acc[e] += (double)run[e];
+    }
+    __shared__ double red[VNE_THREADS][V];
+#pragma unroll
+    for (int e = 0; e < V; e++) red[threadIdx.x][e] = acc[e];
     __syncthreads();
     if (threadIdx.x < KS) {
+        const int g = threadIdx.x / V, e = threadIdx.x % V;
         double s = 0.0;
-        for (int q = 0; q < RPI; q++) s += red[q * KS + threadIdx.x];
+        for (int q = g; q < VNE_THREADS; q += G) s += red[q][e];
         p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
     }
 }
@@ -973,24 +1038,54 @@ __global__ void k_reorth_coef(ReorthCoefParams p) {
     p.coef[(size_t)i * p.K + col] = sig * sig * s;
 }
 
-// Pass C: w_{j+1} -= sum_i coef_i w_i.
+// Pass C: w_{j+1} -= sum_i coef_i w_i in the vector precision.  Each CTA first
+// lists the basis vectors with a nonzero coefficient in its panel (in index
+// order) and stages their coefficients, rounded to the vector precision, in
+// shared memory; only those vectors are read.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p) {
+    constexpr int V = Chunk16<T>::V, G = KS / V;
+    static_assert(KS % V == 0 && VNE_THREADS % G == 0, "chunk layout");
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     if (p.panel_active && !p.panel_active[panel]) return;
+    __shared__ uint8_t used[kReorthMaxJ];
+    __shared__ int16_t act[kReorthMaxJ];
+    __shared__ T cf[kReorthMaxJ * KS];
+    __shared__ int nact;
+    const double* cp = p.coef + (size_t)panel * KS;
+    for (int i = threadIdx.x; i < p.j; i += VNE_THREADS) {
+        int u = 0;
+        for (int c = 0; c < KS; c++) u |= cp[(size_t)i * p.K + c] != 0.0;
+        used[i] = (uint8_t)u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int i = 0; i < p.j; i++)
+            if (used[i]) act[k++] = (int16_t)i;
+        nact = k;
+    }
+    __syncthreads();
+    const int na = nact;
+    for (int x = threadIdx.x; x < na * KS; x += VNE_THREADS) cf[x] = (T)cp[(size_t)act[x / KS] * p.K + x % KS];
+    __syncthreads();
+    if (na == 0) return;
     const RowTile t = p.tiles[tile];
-    const int c = threadIdx.x % KS, rsub = threadIdx.x / KS;
-    constexpr int RPI = VNE_THREADS / KS;
-    const size_t pofs = (size_t)panel * p.n_total * KS;
-    T* Wn = p.w + pofs;
-    const int col = panel * KS + c;
-    for (int r = t.row_begin + rsub; r < t.row_end; r += RPI) {
-        double v = (double)Wn[(size_t)r * KS + c];
-        for (int i = 0; i < p.j; i++) {
-            const double cf = p.coef[(size_t)i * p.K + col];
-            if (cf != 0.0) v -= cf * (double)p.basis[(size_t)i * p.slot_stride + pofs + (size_t)r * KS + c];
+    const size_t base = (size_t)panel * p.n_total * KS + (size_t)t.row_begin * KS;
+    T* Wn = p.w + base;
+    const T* B = p.basis + base;
+    const int nchunks = (t.row_end - t.row_begin) * G;
+    const int g = threadIdx.x % G;
+    for (int q = threadIdx.x; q < nchunks; q += VNE_THREADS) {
+        Chunk16<T> v = load_chunk(Wn + (size_t)q * V);
+#pragma unroll 4
+        for (int k = 0; k < na; k++) {
+            const Chunk16<T> b = load_chunk(B + (size_t)act[k] * p.slot_stride + (size_t)q * V);
+            const T* c = cf + k * KS + g * V;
+#pragma unroll
+            for (int e = 0; e < V; e++) v.x[e] -= c[e] * b.x[e];
         }
-        Wn[(size_t)r * KS + c] = (T)v;
+        store_chunk(Wn + (size_t)q * V, v);
     }
 }
 
@@ -1260,6 +1355,7 @@ cudaError_t launch_step_update_segj(const StepParams<T>& p, int ks, int panels, 
 template <typename T>
 cudaError_t launch_reorth(const ReorthParams<T>& p, const ReorthCoefParams& c, int ks, cudaStream_t st) {
     if (p.j <= 0) return cudaSuccess;
+    if (p.j > kReorthMaxJ) return cudaErrorInvalidValue;
     VNE_DISPATCH_KS(T, ks, (k_reorth_dots<T, KS><<<dim3(p.panels * p.tiles_per_panel * p.j), VNE_THREADS, 0, st>>>(p)));
     int total = c.panels * c.j * ks;
     VNE_DISPATCH_KS(T, ks, (k_reorth_coef<KS><<<dim3((total + 255) / 256), 256, 0, st>>>(c)));
