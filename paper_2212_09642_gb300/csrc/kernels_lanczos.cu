@@ -1006,14 +1006,23 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) 
 #pragma unroll
         for (int e = 0; e < V; e++) acc[e] += (double)run[e];
     }
-    __shared__ double red[VNE_THREADS][V];
+    // lanes of one column group (lane mod G) combine by a fixed shuffle tree,
+    // then the warps' sums are added in warp order
 #pragma unroll
-    for (int e = 0; e < V; e++) red[threadIdx.x][e] = acc[e];
+    for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+        for (int e = 0; e < V; e++) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+    constexpr int NW = VNE_THREADS / 32;
+    __shared__ double red[NW][KS];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (lane < G)
+#pragma unroll
+        for (int e = 0; e < V; e++) red[warp][lane * V + e] = acc[e];
     __syncthreads();
     if (threadIdx.x < KS) {
-        const int g = threadIdx.x / V, e = threadIdx.x % V;
         double s = 0.0;
-        for (int q = g; q < VNE_THREADS; q += G) s += red[q][e];
+#pragma unroll
+        for (int w = 0; w < NW; w++) s += red[w][threadIdx.x];
         p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
     }
 }
@@ -1038,32 +1047,35 @@ __global__ void k_reorth_coef(ReorthCoefParams p) {
     p.coef[(size_t)i * p.K + col] = sig * sig * s;
 }
 
-// Pass C: w_{j+1} -= sum_i coef_i w_i in the vector precision.  Each CTA first
-// lists the basis vectors with a nonzero coefficient in its panel (in index
-// order) and stages their coefficients, rounded to the vector precision, in
-// shared memory; only those vectors are read.
+// Pass C: w_{j+1} -= sum_i coef_i w_i in the vector precision.  Warp 0 of each
+// CTA lists the basis vectors with a nonzero coefficient in its panel (in
+// index order, by ballots), their coefficients are staged in shared memory
+// rounded to the vector precision, and only those vectors are read; a thread
+// keeps four chunks in flight.
 template <typename T, int KS>
 __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p) {
-    constexpr int V = Chunk16<T>::V, G = KS / V;
+    constexpr int V = Chunk16<T>::V, G = KS / V, U = 4;
     static_assert(KS % V == 0 && VNE_THREADS % G == 0, "chunk layout");
     const int panel = blockIdx.x / p.tiles_per_panel, tile = blockIdx.x % p.tiles_per_panel;
     if (p.panel_active && !p.panel_active[panel]) return;
-    __shared__ uint8_t used[kReorthMaxJ];
     __shared__ int16_t act[kReorthMaxJ];
     __shared__ T cf[kReorthMaxJ * KS];
     __shared__ int nact;
     const double* cp = p.coef + (size_t)panel * KS;
-    for (int i = threadIdx.x; i < p.j; i += VNE_THREADS) {
-        int u = 0;
-        for (int c = 0; c < KS; c++) u |= cp[(size_t)i * p.K + c] != 0.0;
-        used[i] = (uint8_t)u;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int i = 0; i < p.j; i++)
-            if (used[i]) act[k++] = (int16_t)i;
-        nact = k;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int count = 0;
+        for (int b0 = 0; b0 < p.j; b0 += 32) {
+            const int i = b0 + lane;
+            int u = 0;
+            if (i < p.j)
+#pragma unroll
+                for (int c = 0; c < KS; c++) u |= cp[(size_t)i * p.K + c] != 0.0;
+            const unsigned m = __ballot_sync(0xffffffffu, u);
+            if (u) act[count + __popc(m & ((1u << lane) - 1u))] = (int16_t)i;
+            count += __popc(m);
+        }
+        if (lane == 0) nact = count;
     }
     __syncthreads();
     const int na = nact;
@@ -1076,16 +1088,32 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p)
     const T* B = p.basis + base;
     const int nchunks = (t.row_end - t.row_begin) * G;
     const int g = threadIdx.x % G;
-    for (int q = threadIdx.x; q < nchunks; q += VNE_THREADS) {
-        Chunk16<T> v = load_chunk(Wn + (size_t)q * V);
-#pragma unroll 4
+    for (int q0 = threadIdx.x; q0 < nchunks; q0 += U * VNE_THREADS) {
+        Chunk16<T> v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int q = q0 + u * VNE_THREADS;
+            if (q < nchunks) v[u] = load_chunk(Wn + (size_t)q * V);
+        }
+#pragma unroll 2
         for (int k = 0; k < na; k++) {
-            const Chunk16<T> b = load_chunk(B + (size_t)act[k] * p.slot_stride + (size_t)q * V);
+            const T* bk = B + (size_t)act[k] * p.slot_stride;
             const T* c = cf + k * KS + g * V;
 #pragma unroll
-            for (int e = 0; e < V; e++) v.x[e] -= c[e] * b.x[e];
+            for (int u = 0; u < U; u++) {
+                const int q = q0 + u * VNE_THREADS;
+                if (q < nchunks) {
+                    const Chunk16<T> b = load_chunk(bk + (size_t)q * V);
+#pragma unroll
+                    for (int e = 0; e < V; e++) v[u].x[e] -= c[e] * b.x[e];
+                }
+            }
         }
-        store_chunk(Wn + (size_t)q * V, v);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int q = q0 + u * VNE_THREADS;
+            if (q < nchunks) store_chunk(Wn + (size_t)q * V, v[u]);
+        }
     }
 }
 
