@@ -469,20 +469,36 @@ vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t 
                                 double *estimates, double *std_errors);
 
 /* ---- serving: continuous batching of entropy queries -------------------
- * A server admits queued queries (FIFO) while the active set fits
- * `hbm_budget_bytes` (each query counts its resident CSR plus one block of
- * Lanczos vectors) and `max_active` slots.  Each vne_server_step is one
- * tick: it packs the active graphs block-diagonally on the device and runs
- * one Lanczos block (`block_vectors` Rademacher probes x `krylov_steps`
- * steps) for all of them in one batched launch sequence, then updates every
- * query's running mean and standard error and retires those with
- * 2.576 * stderr <= (eps / 2) * |estimate| (after at least two blocks) or
- * with max_vectors probes.  A query's probes in its t-th block are columns
- * t*block .. (t+1)*block-1 of its own seed, so its result is bit-identical
- * alone and in any mix.  This is the stated proxy for the adaptive
- * stopping of Section 5.2 (Hutchinson part only; no low-rank sketch).
- * Matrices must be FP32 graph patterns of the server's context and stay
- * alive until their queries are done. */
+ * A query asks for S(rho) of one graph to a relative accuracy eps.  It is
+ * answered by Hutch++ (Section 3.2, eq. Hutch++_formula) in an adaptive
+ * form, the stated proxy for the adaptive Hutch++ of Section 5.2 (whose
+ * steps the paper does not print): at admission a sketch of N_r = 4 columns
+ * (probe columns 0..3 of the query's seed) gives Q = orth(f(A) Omega) and
+ * psi(q_i) for the query alone; then blocks of `block_vectors` deflated
+ * probes g' = (I - Q Q^T) g (probe columns 4, 5, ... in block order) run
+ * `krylov_steps` Lanczos steps each, until 2.576 * stderr(psi(g')) <=
+ * (eps / 2) * |sum psi(q_i) + mean psi(g')| after at least two blocks, or
+ * max_vectors probes.  The estimate is sum psi(q_i) + mean psi(g').
+ *
+ * Device memory: on the first submission the server takes an arena sized
+ * from `hbm_budget_bytes` (the server's scalars, then rows and nonzeros,
+ * up to 12 nonzeros per row); a query keeps its packed CSR (copied once, at
+ * admission), its block's two Lanczos slots and u, and its Q at a row range
+ * of the arena from admission to completion.  A query counts (n + 1) rows
+ * of (8 + (3 K + 4) * element size) bytes plus 4 bytes per nonzero against
+ * the budget; queries are admitted FIFO while that fits and a slot of the
+ * `max_active` is free.  All queries of a server share one precision (that
+ * of the first one); FP32 and FP64 graph patterns are accepted.
+ *
+ * Each vne_server_step is one tick: admission, then ONE Lanczos step of
+ * every active query, each at its own step j of its own block (one step
+ * kernel and one update kernel over all active queries, with per-query step
+ * counters; queries whose block starts get their deflated start vectors
+ * first, queries whose block ends get their Gauss quadratures and update
+ * their statistics after).  A query's numbers depend only on its graph,
+ * seed and the server's block_vectors and krylov_steps, so its result is
+ * bit-identical alone and in any mix.  Matrices must be graph patterns of
+ * the server's context and stay alive until their queries are done. */
 typedef struct vne_server vne_server;
 vne_status vne_server_create(vne_ctx *ctx, uint64_t hbm_budget_bytes, int32_t max_active, int32_t krylov_steps,
                              int32_t block_vectors, const vne_options *opt, vne_server **out);
@@ -491,8 +507,8 @@ vne_status vne_server_destroy(vne_server *srv);
  * ENOMEM if the query alone exceeds the budget. */
 vne_status vne_server_submit(vne_server *srv, vne_matrix *mat, double rel_eps, uint64_t seed, int32_t max_vectors,
                              int32_t *ticket);
-/* One tick (admission + one batched block); completed = queries retired in it,
- * active = queries that ran in it. */
+/* One tick (admission + one Lanczos step of every active query); completed =
+ * queries retired in it, active = queries that ran in it. */
 vne_status vne_server_step(vne_server *srv, int32_t *completed, int32_t *active);
 /* state 0 queued / 1 active / 2 done; ticks[3] = {submit, admit, done} tick. */
 vne_status vne_server_result(const vne_server *srv, int32_t ticket, int32_t *state, double *estimate,
