@@ -218,13 +218,21 @@ def oracle_sample(g, columns=1, seed=7):
     G = rng.rademacher(seed, g.n, N_SKETCH, N_HUTCH)
     G - Q @ (Q.T @ G)
     t_o = time.perf_counter() - t0
+    # context: one scipy sparse product with a 16-column block (one thread)
+    X16 = rng.rademacher(seed, g.n, 0, 16)
+    t0 = time.perf_counter()
+    A @ X16
+    t_s = time.perf_counter() - t0
+    spmm_bytes = 4.0 * (g.n + 1) + 12.0 * A.nnz + 2.0 * g.n * 16 * 8
     measured = time.perf_counter() - t_all
     runs = N_SKETCH + N_SKETCH + N_HUTCH
     total = N_SKETCH * t_f + (N_SKETCH + N_HUTCH) * t_q + t_o
     rec = dict(extrapolated=True, sampled_krylov_runs=2 * columns, krylov_runs_per_estimate=runs,
                scale_factor=total / measured if measured > 0 else None, measured_seconds=measured,
                t_fmatvec_s=t_f, t_quadform_s=t_q, t_orth_s=t_o,
-               threads={"krylov": 1, "orthonormalisation": blas_threads()})
+               threads={"krylov": 1, "orthonormalisation": blas_threads()},
+               scipy_spmm_16_columns={"seconds": t_s, "algorithmic_gbs": spmm_bytes / t_s / 1e9 if t_s > 0 else None,
+                                      "threads": 1, "counted_in_value": False})
     return total, rec
 
 
@@ -317,6 +325,46 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+
+def oracle_c1_baseline(g):
+    """The whole C1 estimate by the oracle on the host (no extrapolation):
+    FP64 scipy Lanczos with full reorthogonalisation, 100 probes x 50 steps."""
+    from oracle import density, estimators
+    A, _ = density.density_matrix(g)
+    estimators.hutchinson(A, 2, 50, 2, reorth="full")  # warm-up
+    t0 = time.perf_counter()
+    est, _ = estimators.hutchinson(A, 100, 50, 2, reorth="full")
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": "the whole estimate: 100 Rademacher probes x 50 FP64 Lanczos steps with full "
+                      "reorthogonalisation (scipy sparse products on one thread, Gram-Schmidt by BLAS)",
+            "extrapolated": False, "measured_seconds": t, "estimate": est,
+            "threads": {"sparse_products": 1, "reorthogonalisation": blas_threads()}}
+
+
+def oracle_c4_baseline(gs, sample=8, probes=16):
+    """C4 by the oracle on a seeded sample of the 512 graphs (every 64th),
+    `probes` of the 64 probes x 40 plain FP64 Lanczos steps each, scaled to
+    the batch by the probes and by the work per graph, proportional to
+    (n + nnz)."""
+    from oracle import density, estimators
+    pick = list(range(0, len(gs), max(1, len(gs) // sample)))[:sample]
+    t = 0.0
+    for i in pick:
+        A, _ = density.density_matrix(gs[i])
+        t0 = time.perf_counter()
+        estimators.hutchinson(A, probes, 40, 1000 + i, reorth="none")
+        t += time.perf_counter() - t0
+    w_all = float(sum(gg.n + gg.nnz for gg in gs))
+    w_s = float(sum(gs[i].n + gs[i].nnz for i in pick))
+    scale = (w_all / w_s) * (64.0 / probes)
+    return {"value": len(gs) / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(pick)} of the {len(gs)} graphs (every {max(1, len(gs) // sample)}th), {probes} of the "
+                      "64 probes x 40 plain FP64 Lanczos steps each (scipy, one thread), scaled to the batch by "
+                      "sum(n + nnz) and to 64 probes",
+            "extrapolated": True, "scale_factor": scale, "measured_seconds": t, "sampled_graphs": len(pick),
+            "sampled_probes_per_graph": probes}
+
 
 def run_native(args):
     import numpy as np
@@ -587,6 +635,8 @@ def run_other(args):
                                           "estimate": outs2[0][0],
                                           "rel_diff_vs_fixed_steps": abs(outs2[0][0] - outs[0][0]) / abs(outs[0][0])}
         vne.vne_matrix_destroy(mat)
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_c1_baseline(g)
     elif args.workload == "c3":
         n = args.n if args.n != N_NODES else 4_000_000
         g = graphs.random_geometric(n, graphs.rgg_radius_for_degree(n, 6.0), 4)
@@ -676,6 +726,8 @@ def run_other(args):
                     update_kernel=_roof(kst, "update", ms, "k_update"), gpu_launches=int(launches), clocks=clk)
         for m in mats:
             vne.vne_matrix_destroy(m)
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_c4_baseline(gs)
     else:
         line.update(run_serving(args, ctx, stream))
     vne.vne_ctx_destroy(ctx)
