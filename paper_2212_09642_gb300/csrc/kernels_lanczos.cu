@@ -990,18 +990,31 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) 
     double acc[V];
 #pragma unroll
     for (int e = 0; e < V; e++) acc[e] = 0.0;
-    // exact trip counts (predicated-off iterations would still take FP64
-    // issue slots, the bound of FP64 inner products on this part)
     for (int q0 = threadIdx.x; q0 < nchunks; q0 += 16 * VNE_THREADS) {
-        const int q1 = min(nchunks, q0 + 16 * VNE_THREADS);
         T run[V];
 #pragma unroll
         for (int e = 0; e < V; e++) run[e] = (T)0;
+        if constexpr (sizeof(T) == 8) {
+            // exact trip counts: a predicated-off iteration would still take
+            // FP64 issue slots, the bound of FP64 inner products on this part
+            const int q1 = min(nchunks, q0 + 16 * VNE_THREADS);
 #pragma unroll 4
-        for (int q = q0; q < q1; q += VNE_THREADS) {
-            const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
+            for (int q = q0; q < q1; q += VNE_THREADS) {
+                const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
 #pragma unroll
-            for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
+                for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
+            }
+        } else {
+            // a fixed run of 16 with predicated tails (measured faster for FP32)
+#pragma unroll 4
+            for (int u = 0; u < 16; u++) {
+                const int q = q0 + u * VNE_THREADS;
+                if (q < nchunks) {
+                    const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
+#pragma unroll
+                    for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
+                }
+            }
         }
 #pragma unroll
         for (int e = 0; e < V; e++) acc[e] += (double)run[e];
@@ -1069,7 +1082,7 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p)
             const int i = b0 + lane;
             int u = 0;
             if (i < p.j)
-#pragma unroll
+#pragma unroll 8
                 for (int c = 0; c < KS; c++) u |= cp[(size_t)i * p.K + c] != 0.0;
             const unsigned m = __ballot_sync(0xffffffffu, u);
             if (u) act[count + __popc(m & ((1u << lane) - 1u))] = (int16_t)i;
@@ -1088,37 +1101,68 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_apply(ReorthParams<T> p)
     const T* B = p.basis + base;
     const int nchunks = (t.row_end - t.row_begin) * G;
     const int g = threadIdx.x % G;
-    // full groups of U chunks, then the remaining chunks one at a time (a
-    // predicated-off FMA would still take an issue slot of the FP64 pipe)
-    int q0 = threadIdx.x;
-    for (; q0 + (U - 1) * VNE_THREADS < nchunks; q0 += U * VNE_THREADS) {
-        Chunk16<T> v[U];
+    if constexpr (sizeof(T) == 8) {
+        // full groups of U chunks, then the remaining chunks one at a time (a
+        // predicated-off FMA would still take an issue slot of the FP64 pipe)
+        int q0 = threadIdx.x;
+        for (; q0 + (U - 1) * VNE_THREADS < nchunks; q0 += U * VNE_THREADS) {
+            Chunk16<T> v[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) v[u] = load_chunk(Wn + (size_t)(q0 + u * VNE_THREADS) * V);
+            for (int u = 0; u < U; u++) v[u] = load_chunk(Wn + (size_t)(q0 + u * VNE_THREADS) * V);
 #pragma unroll 2
-        for (int k = 0; k < na; k++) {
-            const T* bk = B + (size_t)act[k] * p.slot_stride;
-            const T* c = cf + k * KS + g * V;
+            for (int k = 0; k < na; k++) {
+                const T* bk = B + (size_t)act[k] * p.slot_stride;
+                const T* c = cf + k * KS + g * V;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const Chunk16<T> b = load_chunk(bk + (size_t)(q0 + u * VNE_THREADS) * V);
+#pragma unroll
+                    for (int e = 0; e < V; e++) v[u].x[e] -= c[e] * b.x[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) store_chunk(Wn + (size_t)(q0 + u * VNE_THREADS) * V, v[u]);
+        }
+        for (; q0 < nchunks; q0 += VNE_THREADS) {
+            Chunk16<T> v = load_chunk(Wn + (size_t)q0 * V);
+#pragma unroll 2
+            for (int k = 0; k < na; k++) {
+                const Chunk16<T> b = load_chunk(B + (size_t)act[k] * p.slot_stride + (size_t)q0 * V);
+                const T* c = cf + k * KS + g * V;
+#pragma unroll
+                for (int e = 0; e < V; e++) v.x[e] -= c[e] * b.x[e];
+            }
+            store_chunk(Wn + (size_t)q0 * V, v);
+        }
+    } else {
+        // groups of U chunks with predicated tails (measured faster for FP32)
+        for (int q0 = threadIdx.x; q0 < nchunks; q0 += U * VNE_THREADS) {
+            Chunk16<T> v[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const Chunk16<T> b = load_chunk(bk + (size_t)(q0 + u * VNE_THREADS) * V);
+                const int q = q0 + u * VNE_THREADS;
+                if (q < nchunks) v[u] = load_chunk(Wn + (size_t)q * V);
+            }
+#pragma unroll 2
+            for (int k = 0; k < na; k++) {
+                const T* bk = B + (size_t)act[k] * p.slot_stride;
+                const T* c = cf + k * KS + g * V;
 #pragma unroll
-                for (int e = 0; e < V; e++) v[u].x[e] -= c[e] * b.x[e];
+                for (int u = 0; u < U; u++) {
+                    const int q = q0 + u * VNE_THREADS;
+                    if (q < nchunks) {
+                        const Chunk16<T> b = load_chunk(bk + (size_t)q * V);
+#pragma unroll
+                        for (int e = 0; e < V; e++) v[u].x[e] -= c[e] * b.x[e];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int q = q0 + u * VNE_THREADS;
+                if (q < nchunks) store_chunk(Wn + (size_t)q * V, v[u]);
             }
         }
-#pragma unroll
-        for (int u = 0; u < U; u++) store_chunk(Wn + (size_t)(q0 + u * VNE_THREADS) * V, v[u]);
-    }
-    for (; q0 < nchunks; q0 += VNE_THREADS) {
-        Chunk16<T> v = load_chunk(Wn + (size_t)q0 * V);
-#pragma unroll 4
-        for (int k = 0; k < na; k++) {
-            const Chunk16<T> b = load_chunk(B + (size_t)act[k] * p.slot_stride + (size_t)q0 * V);
-            const T* c = cf + k * KS + g * V;
-#pragma unroll
-            for (int e = 0; e < V; e++) v.x[e] -= c[e] * b.x[e];
-        }
-        store_chunk(Wn + (size_t)q0 * V, v);
     }
 }
 
