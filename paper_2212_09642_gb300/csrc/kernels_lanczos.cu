@@ -987,24 +987,50 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) 
     const T* Wi = p.basis + (size_t)i * p.slot_stride + base;
     const T* Wn = p.w + base;
     const int nchunks = (t.row_end - t.row_begin) * G;
-    double acc[V];
+    const size_t opart = (((size_t)panel * p.j + i) * p.tiles_per_panel + tile) * KS;
+    if constexpr (sizeof(T) == 8) {
+        // FP64 inner products are bound by the FP64 pipe, so the partial sums
+        // take as few FP64 additions as possible: each thread accumulates its
+        // chunks directly (exact trip count: a predicated-off iteration would
+        // still take FP64 issue slots), then 8 partials per (column,
+        // sub-sum) and the 8 sub-sums per column are added in index order
+        double acc[V];
 #pragma unroll
-    for (int e = 0; e < V; e++) acc[e] = 0.0;
-    for (int q0 = threadIdx.x; q0 < nchunks; q0 += 16 * VNE_THREADS) {
-        T run[V];
-#pragma unroll
-        for (int e = 0; e < V; e++) run[e] = (T)0;
-        if constexpr (sizeof(T) == 8) {
-            // exact trip counts: a predicated-off iteration would still take
-            // FP64 issue slots, the bound of FP64 inner products on this part
-            const int q1 = min(nchunks, q0 + 16 * VNE_THREADS);
+        for (int e = 0; e < V; e++) acc[e] = 0.0;
 #pragma unroll 4
-            for (int q = q0; q < q1; q += VNE_THREADS) {
-                const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
+        for (int q = threadIdx.x; q < nchunks; q += VNE_THREADS) {
+            const Chunk16<T> a = load_chunk(Wi + (size_t)q * V), b = load_chunk(Wn + (size_t)q * V);
 #pragma unroll
-                for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
-            }
-        } else {
+            for (int e = 0; e < V; e++) acc[e] += a.x[e] * b.x[e];
+        }
+        constexpr int PER = VNE_THREADS / G;  // partials per column
+        constexpr int SUB = PER >= 8 ? 8 : PER;
+        __shared__ double red[VNE_THREADS * V];
+        __shared__ double sub[KS * SUB];
+#pragma unroll
+        for (int e = 0; e < V; e++) red[threadIdx.x * V + e] = acc[e];
+        __syncthreads();
+        if (threadIdx.x < KS * SUB) {
+            const int c = threadIdx.x % KS, sidx = threadIdx.x / KS, g = c / V, e = c % V;
+            double x = 0.0;
+            for (int k = sidx; k < PER; k += SUB) x += red[(g + k * G) * V + e];
+            sub[sidx * KS + c] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < KS) {
+            double x = 0.0;
+#pragma unroll
+            for (int k = 0; k < SUB; k++) x += sub[k * KS + threadIdx.x];
+            p.part[opart + threadIdx.x] = x;
+        }
+    } else {
+        double acc[V];
+#pragma unroll
+        for (int e = 0; e < V; e++) acc[e] = 0.0;
+        for (int q0 = threadIdx.x; q0 < nchunks; q0 += 16 * VNE_THREADS) {
+            T run[V];
+#pragma unroll
+            for (int e = 0; e < V; e++) run[e] = (T)0;
             // a fixed run of 16 with predicated tails (measured faster for FP32)
 #pragma unroll 4
             for (int u = 0; u < 16; u++) {
@@ -1015,28 +1041,28 @@ __global__ void __launch_bounds__(VNE_THREADS) k_reorth_dots(ReorthParams<T> p) 
                     for (int e = 0; e < V; e++) run[e] += a.x[e] * b.x[e];
                 }
             }
+#pragma unroll
+            for (int e = 0; e < V; e++) acc[e] += (double)run[e];
         }
+        // lanes of one column group (lane mod G) combine by a fixed shuffle
+        // tree, then the warps' sums are added in warp order
 #pragma unroll
-        for (int e = 0; e < V; e++) acc[e] += (double)run[e];
-    }
-    // lanes of one column group (lane mod G) combine by a fixed shuffle tree,
-    // then the warps' sums are added in warp order
+        for (int off = G; off < 32; off <<= 1)
 #pragma unroll
-    for (int off = G; off < 32; off <<= 1)
+            for (int e = 0; e < V; e++) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+        constexpr int NW = VNE_THREADS / 32;
+        __shared__ double red[NW][KS];
+        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+        if (lane < G)
 #pragma unroll
-        for (int e = 0; e < V; e++) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
-    constexpr int NW = VNE_THREADS / 32;
-    __shared__ double red[NW][KS];
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    if (lane < G)
+            for (int e = 0; e < V; e++) red[warp][lane * V + e] = acc[e];
+        __syncthreads();
+        if (threadIdx.x < KS) {
+            double x = 0.0;
 #pragma unroll
-        for (int e = 0; e < V; e++) red[warp][lane * V + e] = acc[e];
-    __syncthreads();
-    if (threadIdx.x < KS) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) s += red[w][threadIdx.x];
-        p.part[(((size_t)panel * p.j + i) * p.tiles_per_panel + tile) * KS + threadIdx.x] = s;
+            for (int w = 0; w < NW; w++) x += red[w][threadIdx.x];
+            p.part[opart + threadIdx.x] = x;
+        }
     }
 }
 
