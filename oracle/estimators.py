@@ -86,6 +86,78 @@ def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_part
     return est
 
 
+def served_hutchpp(A, eps, block, m, seed, n_sketch=4, max_vectors=8192, quad_tol=None, check_every=5,
+                   grid=1000, reorth="none"):
+    """The adaptive Hutch++ proxy of a served query (readings R31, R33): the
+    Hutch++ estimate of eq. Hutch++_formula with a sketch of `n_sketch`
+    columns (probe columns 0..n_sketch-1, Lanczos f(A) omega and psi(q_i) with
+    m steps), then blocks of `block` deflated probes g' = (I - Q Q^T) g (probe
+    columns n_sketch + b * block ...) until, after at least two blocks,
+    2.576 stderr(psi(g')) <= (eps / 2) |sum psi(q_i) + mean psi(g')|, or
+    max_vectors probes.
+
+    quad_tol (R33): the Lanczos runs of a block stop together at the first
+    multiple j of check_every below m at which every column's a-posteriori
+    estimate of Theorem 4.4 (eq. error-bound-a-posteriori--estimate: the
+    geometric mean of the bounds, with lam_min half the column's smallest
+    positive Ritz value and lam_max the Gershgorin bound of A) is at most
+    quad_tol |psi_j|; else after m steps.  None: always m steps.
+
+    Returns (estimate, std_error, vectors, block_steps)."""
+    from .bounds import posterior_bounds
+    from .krylov import desingularize, gauss_quadrature, lanczos, tridiagonal_eig
+    n = A.shape[0]
+    nA = gershgorin_norm(A)
+    Omega = probes(seed, n, 0, n_sketch)
+    Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], m, reorth=reorth, norm_A=nA) for j in range(n_sketch)])
+    Q = orthonormal_range(Y)
+    low = float(sum(lanczos_quadform(A, Q[:, i], m, reorth=reorth, norm_A=nA)[0] for i in range(Q.shape[1])))
+
+    def block_psi(Gp):
+        runs = []
+        for j in range(Gp.shape[1]):
+            c = desingularize(Gp[:, j])
+            alpha, beta, _ = lanczos(A, c, m, reorth=reorth, norm_A=nA)
+            runs.append((alpha, beta, float(c @ c)))
+
+        def psi_at(run, k):
+            alpha, beta, nb = run
+            k = min(k, len(alpha))
+            return gauss_quadrature(alpha[:k], beta[:k - 1], nb) if k else 0.0
+
+        def estimate_at(run, k):
+            alpha, beta, nb = run
+            if len(alpha) < k or beta[k - 1] == 0.0:
+                return 0.0  # the Krylov space is invariant: exact
+            theta, _ = tridiagonal_eig(alpha[:k], beta[:k - 1])
+            pos = theta[theta > 0.0]
+            if pos.size == 0:
+                return np.inf
+            return posterior_bounds(alpha[:k], beta[:k], nb, 0.5 * float(pos.min()), nA, grid=grid)[2]
+
+        steps = m
+        if quad_tol is not None:
+            for k in range(check_every, m, check_every):
+                if all(estimate_at(r, k) <= quad_tol * abs(psi_at(r, k)) for r in runs):
+                    steps = k
+                    break
+        return np.array([psi_at(r, steps) for r in runs]), steps
+
+    psi_all, steps_all = [], []
+    b = 0
+    while True:
+        G = probes(seed, n, n_sketch + b * block, block)
+        psi, steps = block_psi(G - Q @ (Q.T @ G))
+        psi_all.extend(psi.tolist())
+        steps_all.append(steps)
+        b += 1
+        x = np.array(psi_all)
+        est = low + float(np.mean(x))
+        se = float(np.std(x, ddof=1) / np.sqrt(len(x))) if len(x) > 1 else 0.0
+        if (b >= 2 and 2.576 * se <= 0.5 * eps * abs(est)) or len(x) >= max_vectors:
+            return est, se, len(x), steps_all
+
+
 def probing_vectors(colors, n_colors=None):
     """n x s 0/1 matrix with column l the indicator of colour class l (eq. probing_vectors)."""
     colors = np.asarray(colors, dtype=np.int64)
