@@ -87,31 +87,35 @@ def hutchpp(A, n_sketch, n_hutch, m, seed, reorth="full", rows=None, return_part
 
 
 def served_hutchpp(A, eps, block, m, seed, n_sketch=4, max_vectors=8192, quad_tol=None, check_every=5,
-                   grid=1000, reorth="none"):
+                   grid=256, reorth="none", sketch_steps=None):
     """The adaptive Hutch++ proxy of a served query (readings R31, R33): the
     Hutch++ estimate of eq. Hutch++_formula with a sketch of `n_sketch`
-    columns (probe columns 0..n_sketch-1, Lanczos f(A) omega and psi(q_i) with
-    m steps), then blocks of `block` deflated probes g' = (I - Q Q^T) g (probe
-    columns n_sketch + b * block ...) until, after at least two blocks,
+    columns (probe columns 0..n_sketch-1, Y = f(A) Omega by Lanczos with
+    `sketch_steps` steps (default m), Q = orth(Y) and the quadratic forms
+    psi(q_i)), then blocks of `block` deflated probes g' = (I - Q Q^T) g
+    (probe columns n_sketch + b * block ...) until, after at least two blocks,
     2.576 stderr(psi(g')) <= (eps / 2) |sum psi(q_i) + mean psi(g')|, or
     max_vectors probes.
 
-    quad_tol (R33): the Lanczos runs of a block stop together at the first
-    multiple j of check_every below m at which every column's a-posteriori
-    estimate of Theorem 4.4 (eq. error-bound-a-posteriori--estimate: the
-    geometric mean of the bounds, with lam_min half the column's smallest
-    positive Ritz value and lam_max the Gershgorin bound of A) is at most
-    quad_tol |psi_j|; else after m steps.  None: always m steps.
+    quad_tol (R33): the Lanczos runs of a block of quadratic forms (the
+    psi(q_i) as one block, then each block of deflated probes) stop together
+    at the first multiple j of check_every below m at which every column's
+    a-posteriori estimate of Theorem 4.4 (eq.
+    error-bound-a-posteriori--estimate: the geometric mean of the bounds, with
+    lam_min half the column's smallest positive Ritz value and lam_max the
+    Gershgorin bound of A; the min and max of |g_m| over `grid` geometric and
+    `grid` linear points of that interval and the Ritz values in it) is at
+    most quad_tol |psi_j|; else after m steps.  None: always m steps.
 
-    Returns (estimate, std_error, vectors, block_steps)."""
+    Returns (estimate, std_error, vectors, block_steps, sketch_form_steps)."""
     from .bounds import posterior_bounds
     from .krylov import desingularize, gauss_quadrature, lanczos, tridiagonal_eig
     n = A.shape[0]
     nA = gershgorin_norm(A)
+    ms = m if sketch_steps is None else sketch_steps
     Omega = probes(seed, n, 0, n_sketch)
-    Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], m, reorth=reorth, norm_A=nA) for j in range(n_sketch)])
+    Y = np.column_stack([lanczos_fmatvec(A, Omega[:, j], ms, reorth=reorth, norm_A=nA) for j in range(n_sketch)])
     Q = orthonormal_range(Y)
-    low = float(sum(lanczos_quadform(A, Q[:, i], m, reorth=reorth, norm_A=nA)[0] for i in range(Q.shape[1])))
 
     def block_psi(Gp):
         runs = []
@@ -143,6 +147,9 @@ def served_hutchpp(A, eps, block, m, seed, n_sketch=4, max_vectors=8192, quad_to
                     break
         return np.array([psi_at(r, steps) for r in runs]), steps
 
+    # the quadratic forms of the basis vectors, as one block
+    psi_q, q_steps = block_psi(Q) if Q.shape[1] else (np.zeros(0), 0)
+    low = float(np.sum(psi_q))
     psi_all, steps_all = [], []
     b = 0
     while True:
@@ -155,7 +162,7 @@ def served_hutchpp(A, eps, block, m, seed, n_sketch=4, max_vectors=8192, quad_to
         est = low + float(np.mean(x))
         se = float(np.std(x, ddof=1) / np.sqrt(len(x))) if len(x) > 1 else 0.0
         if (b >= 2 and 2.576 * se <= 0.5 * eps * abs(est)) or len(x) >= max_vectors:
-            return est, se, len(x), steps_all
+            return est, se, len(x), steps_all, q_steps
 
 
 def probing_vectors(colors, n_colors=None):
