@@ -72,6 +72,12 @@ def parse():
                     help="c5: wall-time limit of the FP64 one-at-a-time arm (it serves a prefix of the queries)")
     ap.add_argument("--scaling-exponents", default="10,12,14,16,18,20", help="c7: n = 2^e for these e")
     ap.add_argument("--scaling-runs", type=int, default=10, help="c7: seeds averaged for the stochastic estimator")
+    ap.add_argument("--serve-krylov-tol", type=float, default=-1.0,
+                    help="c5: Krylov tolerance of the served blocks (< 0: half the query's accuracy, Section 5.2; "
+                         "0: fixed 40 steps)")
+    ap.add_argument("--serve-check", type=int, default=3, help="c5: Lanczos steps between Krylov-error checks")
+    ap.add_argument("--serve-sketch", type=int, default=10,
+                    help="c5/c7: Lanczos steps of each query's 4-column sketch f(A) Omega (0: 40)")
     ap.add_argument("--ba-max-colors", type=int, default=10000,
                     help="c7: BA probing is not run above a size whose colouring needed more colours")
     return ap.parse_args()
@@ -635,7 +641,7 @@ def run_other(args):
                                           "estimate": outs2[0][0],
                                           "rel_diff_vs_fixed_steps": abs(outs2[0][0] - outs[0][0]) / abs(outs[0][0])}
         vne.vne_matrix_destroy(mat)
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_c1_baseline(g)
     elif args.workload == "c3":
         n = args.n if args.n != N_NODES else 4_000_000
@@ -726,7 +732,7 @@ def run_other(args):
                     update_kernel=_roof(kst, "update", ms, "k_update"), gpu_launches=int(launches), clocks=clk)
         for m in mats:
             vne.vne_matrix_destroy(m)
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_c4_baseline(gs)
     else:
         line.update(run_serving(args, ctx, stream))
@@ -770,7 +776,8 @@ def run_scaling(args, ctx, stream):
         result, device synchronised at both ends) for each seed, after one
         warm-up query; the server is created once per graph."""
         srv = vne.vne_server_create(ctx, (1 << 30) + 1200 * n, max_active=1, krylov_steps=40, block_vectors=64,
-                                    opt=vne.options(reorth=0))
+                                    opt=vne.options(reorth=0, quad_tol=args.serve_krylov_tol,
+                                                    check_every=args.serve_check, sketch_steps=args.serve_sketch))
         try:
             def one(seed):
                 t = vne.vne_server_submit(ctx, srv, mat, 1e-2, seed, 1 << 16)
@@ -843,8 +850,10 @@ def run_scaling(args, ctx, stream):
                                    + "; probing with the heuristic choice of d at eps 1e-4 (grid: lattice "
                                    "colouring with ceil((d+1)^2/2) colours; BA: device greedy colouring), Lanczos "
                                    "stopped by Theorem 4.4 (checks every 2 steps, at most 128); adaptive Hutch++ "
-                                   "proxy at eps 1e-2 (N_r = 4 sketch columns, blocks of 64 deflated probes x 40 "
-                                   f"steps), mean over {args.scaling_runs} seeds",
+                                   "proxy at eps 1e-2 (N_r = 4 sketch columns, blocks of 64 deflated probes, at "
+                                   "most 40 Lanczos steps"
+                                   + (", stopped by the Theorem 4.4 estimate" if args.serve_krylov_tol != 0 else "")
+                                   + f"), mean over {args.scaling_runs} seeds",
                        "timing": f"probing: best of {reps} after one warm-up, CUDA events; stochastic: wall clock "
                                  "per served query, device synchronised, after one warm-up query",
                        "l2": "small sizes are L2-resident (the curve spans both regimes)"},
@@ -881,8 +890,10 @@ def run_serving(args, ctx, stream):
         service time.  Returns completion latencies, vectors, estimates."""
         mats = [vne.matrix_from_graph(ctx, g, fp64=fp64, reorder=True) for g in pool]
         srv = vne.vne_server_create(ctx, budget, max_active=slots, krylov_steps=m, block_vectors=block,
-                                    opt=vne.options(reorth=0))
+                                    opt=vne.options(reorth=0, quad_tol=args.serve_krylov_tol,
+                                                    check_every=args.serve_check, sketch_steps=args.serve_sketch))
         lat, vecs, ests, served = {}, {}, {}, 0
+        steps = {}  # Lanczos steps per block of each query (ticks from admission to completion / blocks)
         try:
             t0 = time.perf_counter()
             if realtime:
@@ -906,6 +917,7 @@ def run_serving(args, ctx, stream):
                             if r["state"] == 2:
                                 lat[i] = t_now - arrivals[i]
                                 vecs[i], ests[i] = r["vectors"], r["estimate"]
+                                steps[i] = (r["done_tick"] - r["admit_tick"]) / (r["vectors"] / block)
                                 live.discard(i)
                 served = R
             else:
@@ -923,22 +935,23 @@ def run_serving(args, ctx, stream):
                     free_at = start + service
                     lat[i] = free_at - arrivals[i]
                     vecs[i], ests[i] = r["vectors"], r["estimate"]
+                    steps[i] = (r["done_tick"] - r["admit_tick"]) / (r["vectors"] / block)
                     served = i + 1
             total = time.perf_counter() - t0
         finally:
             vne.vne_server_destroy(srv)
             for mt in mats:
                 vne.vne_matrix_destroy(mt)
-        return lat, vecs, ests, served, total
+        return lat, vecs, ests, served, total, steps
 
     sampler = ClockSampler(0)
     sampler.__enter__()
     vne.vne_ctx_profile(ctx, True)
-    lat, vecs, ests, _, total = serve(False, 128, 120 << 30, True, None)
+    lat, vecs, ests, _, total, steps = serve(False, 128, 120 << 30, True, None)
     launches, kst = vne.vne_ctx_stats(ctx)
     vne.vne_ctx_profile(ctx, False)
     sampler.__exit__()
-    lat64, vecs64, ests64, served64, total64 = serve(True, 1, 60 << 30, False, args.fp64_limit_s)
+    lat64, vecs64, ests64, served64, total64, steps64 = serve(True, 1, 60 << 30, False, args.fp64_limit_s)
     idx = np.arange(R)
     L = np.array([lat[i] for i in idx])
     L64 = np.array([lat64[i] for i in range(served64)])
@@ -948,9 +961,16 @@ def run_serving(args, ctx, stream):
             "value": R / total, "ms_per_step": 1e3 * total / R, "dtype": "f32",
             "config": {"workload": f"C5: {R} queries, Poisson {args.rate}/s (seed 5), graphs from a pool of 24 "
                                    "(n log-uniform [1e3, 1e6], ER/BA/WS), eps 1e-3, Hutch++ proxy: 4 sketch columns "
-                                   "+ blocks of 64 deflated probes x 40 steps until 2.576 se <= eps/2 |S|, cap 8192 "
-                                   "probes, 128 slots, one Lanczos step per tick",
+                                   "+ blocks of 64 deflated probes until 2.576 se <= eps/2 |S|, cap 8192 probes, "
+                                   + f"sketch of {args.serve_sketch or 40} Lanczos steps, "
+                                   + ("Lanczos blocks of at most 40 steps stopped by the Theorem 4.4 estimate at "
+                                      + ("eps/2" if args.serve_krylov_tol < 0 else f"{args.serve_krylov_tol}")
+                                      + f" relative (checks every {args.serve_check} steps)"
+                                      if args.serve_krylov_tol != 0 else "40 Lanczos steps per block")
+                                   + ", 128 slots, one Lanczos step per tick",
                        "pool_n": [int(x) for x in pool_n]},
+            "lanczos_steps_per_block": {"served_mean": float(np.mean(list(steps.values()))),
+                                        "fp64_mean": float(np.mean(list(steps64.values()))) if steps64 else None},
             "latency_s": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
                           "mean": float(L.mean())},
             "fp64_one_at_a_time": {"queries": int(served64), "estimates_per_s": served64 / total64,

@@ -113,7 +113,9 @@ typedef struct vne_options {
                              of a block has the error estimate of Theorem 4.4
                              (geometric mean of its bounds) below quad_tol x
                              |psi|, or at krylov_steps; checks after at least
-                             check_every steps.  0 = fixed krylov_steps. */
+                             check_every steps.  0 = fixed krylov_steps.
+                             Servers: < 0 takes half of each query's
+                             rel_eps (see the serving section). */
     double spectrum_min;  /* adaptive mode: lower end of the spectral interval
                              of A for the bounds; 0 = half the smallest
                              positive Ritz value of each column (the upper end
@@ -127,6 +129,10 @@ typedef struct vne_options {
                                turn (1, 2 or 4; a CTA covers 8 x this many
                                items, so its reduction tail is amortised over
                                more rows), 0 = auto */
+    int32_t sketch_steps;   /* servers: Lanczos steps of a query's sketch
+                               f(A) Omega (any sketch keeps Hutch++ unbiased,
+                               so this sets only how much variance it
+                               removes), 0 = krylov_steps */
 } vne_options;
 
 /* Fill *opt with the defaults described above. */
@@ -479,6 +485,15 @@ vne_status vne_batch_hutchinson(vne_matrix *const *mats, int32_t count, int32_t 
  * `krylov_steps` Lanczos steps each, until 2.576 * stderr(psi(g')) <=
  * (eps / 2) * |sum psi(q_i) + mean psi(g')| after at least two blocks, or
  * max_vectors probes.  The estimate is sum psi(q_i) + mean psi(g').
+ * With opt->quad_tol != 0 at creation the Lanczos runs of a block stop
+ * together at the first multiple of opt->check_every (default 5) below
+ * krylov_steps at which every column's Theorem 4.4 estimate is at most
+ * tau |psi| (lam_min half the column's smallest positive Ritz value, lam_max
+ * the Gershgorin bound of A, |g_m| over 256 geometric and 256 linear points
+ * and the Ritz values in between); tau = quad_tol, or for quad_tol < 0 half the
+ * query's rel_eps, the Krylov share of the error budget of Section 5.2.
+ * quad_tol = 0: every block runs krylov_steps steps.  The sketch columns
+ * always run krylov_steps steps.
  *
  * Device memory: on the first submission the server takes an arena sized
  * from `hbm_budget_bytes` (the server's scalars, then rows and nonzeros,

@@ -357,9 +357,11 @@ std::vector<double> resolve_shifts(const vne_matrix* M, const double* poles, int
 // columns 0..Nr-1, Q = orth(f(A) Omega) copied to q_rows ([n][Nr] row-major
 // in M's packed row order, zero columns beyond the rank), psi(q_i) for
 // i < Nr (0 beyond the rank) and the rank.
+// The sketch takes sketch_steps Lanczos steps, the quadratic forms m, or
+// fewer with `ad` (stopped by the Theorem 4.4 estimate).
 template <typename T>
-void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, uint64_t seed, T* q_rows,
-                       std::vector<double>& psi_q, int& rank);
+void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, int sketch_steps, uint64_t seed,
+                       T* q_rows, std::vector<double>& psi_q, int& rank, const Adaptive* ad = nullptr);
 
 }  // namespace vne_engine
 

@@ -101,7 +101,7 @@ struct ProjectOut {
 // [c0, c0 + k) of [q_1 .. q_Nr | g'_1 .. g'_NH] (all of them for k < 0).
 template <typename T>
 void project_block(vne_matrix* M, const HppPlan& h, const T* Y, int Kp, int Nr, int NH, int c0, int k,
-                   ProjectOut& out) {
+                   ProjectOut& out, const Adaptive* ad = nullptr) {
     vne_ctx* ctx = M->ctx;
     cudaStream_t st = ctx->stream;
     Problem& P = *h.P;
@@ -195,7 +195,7 @@ void project_block(vne_matrix* M, const HppPlan& h, const T* Y, int Kp, int Nr, 
     if (all) {
         sq.ncols = Kp + Kg;
         run_block<T>(ctx, P, sq, QG, Kp + Kg, ks, m, h.reorth, false, M->desing, "q", qo, h.sc.variant,
-                     h.sc.interleave, h.sc.graph);
+                     h.sc.interleave, h.sc.graph, true, ad);
         std::vector<double> hq = download(ctx, qo.psi, Kp + Kg);
         for (int c = 0; c < Nr; c++) out.psi[c] = c < r ? hq[c] : 0.0;
         for (int j = 0; j < NH; j++) out.psi[Nr + j] = hq[Kp + j];
@@ -288,14 +288,16 @@ void hutchpp_project_impl(vne_matrix* M, const vne_options* o, const void* Yin, 
 namespace vne_engine {
 
 template <typename T>
-void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, uint64_t seed, T* q_rows,
-                       std::vector<double>& psi_q, int& rank) {
+void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, int sketch_steps, uint64_t seed,
+                       T* q_rows, std::vector<double>& psi_q, int& rank, const Adaptive* ad) {
     vne_ctx* ctx = M->ctx;
     HppPlan h = hpp_plan<T>(M, o, m, seed);
+    HppPlan hs = h;  // the sketch f(A) Omega with its own step count
+    hs.m = sketch_steps;
     int Kp = 0;
-    T* Y = sketch_block<T>(M, h, 0, Nr, "Y", &Kp);
+    T* Y = sketch_block<T>(M, hs, 0, Nr, "Y", &Kp);
     ProjectOut po;
-    project_block<T>(M, h, Y, Kp, Nr, 0, 0, -1, po);
+    project_block<T>(M, h, Y, Kp, Nr, 0, 0, -1, po, ad);
     T* QG = ws_get_t<T>(ctx, "QG", (size_t)Kp * h.n);  // Q in its first Kp columns, zero beyond the rank
     VNE_TRY_CUDA(ctx, launch_panel_to_rows<T>(QG, h.n, h.ks, 0, Nr, nullptr, q_rows, ctx->stream));
     ctx->launches += 1;
@@ -303,10 +305,10 @@ void hutchpp_deflation(vne_matrix* M, const vne_options* o, int Nr, int m, uint6
     rank = po.rank;
 }
 
-template void hutchpp_deflation<float>(vne_matrix*, const vne_options*, int, int, uint64_t, float*,
-                                       std::vector<double>&, int&);
-template void hutchpp_deflation<double>(vne_matrix*, const vne_options*, int, int, uint64_t, double*,
-                                        std::vector<double>&, int&);
+template void hutchpp_deflation<float>(vne_matrix*, const vne_options*, int, int, int, uint64_t, float*,
+                                       std::vector<double>&, int&, const Adaptive*);
+template void hutchpp_deflation<double>(vne_matrix*, const vne_options*, int, int, int, uint64_t, double*,
+                                        std::vector<double>&, int&, const Adaptive*);
 
 }  // namespace vne_engine
 

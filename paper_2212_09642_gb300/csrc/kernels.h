@@ -337,6 +337,16 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
 cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const double* norm2, const double* scale,
                                   int count, int m, int ld, double lam_min, double lam_max, int grid, double* lower,
                                   double* upper, double* estimate, cudaStream_t st);
+// The same for a list of columns: entry k is column cols[k] of the ld-strided
+// arrays after mcol[k] <= m steps (outputs at that column); the bounds take
+// lam_max_col[k] as the upper end of the interval when lam_max_col is given.
+cudaError_t launch_tridiag_quad_list(const double* alpha, const double* beta, const double* norm2,
+                                     const double* scale_per_col, int count, const int32_t* cols,
+                                     const int32_t* mcol, int m, int ld, double* psi, cudaStream_t);
+cudaError_t launch_tridiag_bounds_list(const double* alpha, const double* beta, const double* norm2,
+                                       const double* scale, int count, const int32_t* cols, const int32_t* mcol,
+                                       const double* lam_max_col, int m, int ld, double lam_min, double lam_max,
+                                       int grid, double* lower, double* upper, double* estimate, cudaStream_t st);
 cudaError_t launch_tridiag_fvec(const double* alpha, const double* beta, const double* scale_per_col,
                                 int count, int m, int ld, double* zvec, cudaStream_t);
 

@@ -674,11 +674,16 @@ __device__ bool tq_spectrum(const double* __restrict__ alpha, const double* __re
 template <int MAXM>
 __global__ void __launch_bounds__(32) k_tridiag_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
                                                      const double* __restrict__ norm2, const double* __restrict__ scale,
-                                                     int count, int m, int ld, double* __restrict__ psi) {
+                                                     int count, int m_all, int ld, double* __restrict__ psi,
+                                                     const int32_t* __restrict__ cols,
+                                                     const int32_t* __restrict__ mcol) {
     __shared__ TqShared<MAXM> S;
     extern __shared__ double piv[];  // [2][MAXM][32]: twisted pivots, transposed per lane
-    const int c = blockIdx.x, lane = threadIdx.x;
-    if (c >= count) return;
+    const int lane = threadIdx.x;
+    if ((int)blockIdx.x >= count) return;
+    // entry blockIdx.x: column c (of the ld-strided arrays) after m steps
+    const int c = cols ? cols[blockIdx.x] : (int)blockIdx.x;
+    const int m = mcol ? mcol[blockIdx.x] : m_all;
     if (!tq_spectrum<MAXM>(alpha, beta, c, m, ld, lane, S)) {
         if (lane == 0) psi[c] = nan("");
         return;
@@ -981,15 +986,23 @@ template <int MAXM>
 __global__ void __launch_bounds__(32) k_tridiag_bounds(const double* __restrict__ alpha,
                                                        const double* __restrict__ beta,
                                                        const double* __restrict__ norm2,
-                                                       const double* __restrict__ scale, int count, int m, int ld,
+                                                       const double* __restrict__ scale, int count, int m_all, int ld,
                                                        double lam_min, double lam_max, int grid,
                                                        double* __restrict__ lower, double* __restrict__ upper,
-                                                       double* __restrict__ estimate) {
+                                                       double* __restrict__ estimate,
+                                                       const int32_t* __restrict__ cols,
+                                                       const int32_t* __restrict__ mcol,
+                                                       const double* __restrict__ lam_max_col) {
     __shared__ TqShared<MAXM> S;
     __shared__ double s_th[MAXM], s_ab[MAXM], s_gam[MAXM], s_lt[MAXM];
     extern __shared__ double piv[];  // [2][MAXM][32] twisted pivots
-    const int c = blockIdx.x, lane = threadIdx.x;
-    if (c >= count) return;
+    const int lane = threadIdx.x;
+    if ((int)blockIdx.x >= count) return;
+    // entry blockIdx.x: column c (of the ld-strided arrays) after m steps,
+    // with its own upper end of the spectral interval if given
+    const int c = cols ? cols[blockIdx.x] : (int)blockIdx.x;
+    const int m = mcol ? mcol[blockIdx.x] : m_all;
+    if (lam_max_col) lam_max = lam_max_col[blockIdx.x];
     if (!tq_spectrum<MAXM>(alpha, beta, c, m, ld, lane, S)) {
         if (lane == 0) lower[c] = upper[c] = estimate[c] = nan("");
         return;
@@ -1099,9 +1112,17 @@ __global__ void __launch_bounds__(32) k_tridiag_bounds(const double* __restrict_
 cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const double* norm2, const double* scale,
                                   int count, int m, int ld, double lam_min, double lam_max, int grid, double* lower,
                                   double* upper, double* estimate, cudaStream_t st) {
+    return launch_tridiag_bounds_list(alpha, beta, norm2, scale, count, nullptr, nullptr, nullptr, m, ld, lam_min,
+                                      lam_max, grid, lower, upper, estimate, st);
+}
+
+cudaError_t launch_tridiag_bounds_list(const double* alpha, const double* beta, const double* norm2,
+                                       const double* scale, int count, const int32_t* cols, const int32_t* mcol,
+                                       const double* lam_max_col, int m, int ld, double lam_min, double lam_max,
+                                       int grid, double* lower, double* upper, double* estimate, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     // lam_min <= 0: half the smallest positive Ritz value of each column
-    if (!(lam_max > 0.0 && lam_max > lam_min) || grid < 1) return cudaErrorInvalidValue;
+    if ((!lam_max_col && !(lam_max > 0.0 && lam_max > lam_min)) || grid < 1) return cudaErrorInvalidValue;
 #define VNE_BOUND_CASE(MM)                                                                                   \
     if (m <= MM) {                                                                                          \
         const int smem = 2 * MM * 32 * (int)sizeof(double);                                                 \
@@ -1109,7 +1130,7 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);            \
         if (e != cudaSuccess) return e;                                                                     \
         k_tridiag_bounds<MM><<<count, 32, smem, st>>>(alpha, beta, norm2, scale, count, m, ld, lam_min, lam_max, \
-                                                       grid, lower, upper, estimate);                       \
+                                                       grid, lower, upper, estimate, cols, mcol, lam_max_col); \
         return cudaGetLastError();                                                                          \
     }
     VNE_BOUND_CASE(32)
@@ -1122,6 +1143,12 @@ cudaError_t launch_tridiag_bounds(const double* alpha, const double* beta, const
 cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const double* norm2,
                                 const double* scale_per_col, int count, int m, int ld, double* psi,
                                 cudaStream_t st) {
+    return launch_tridiag_quad_list(alpha, beta, norm2, scale_per_col, count, nullptr, nullptr, m, ld, psi, st);
+}
+
+cudaError_t launch_tridiag_quad_list(const double* alpha, const double* beta, const double* norm2,
+                                     const double* scale_per_col, int count, const int32_t* cols,
+                                     const int32_t* mcol, int m, int ld, double* psi, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     // one warp (CTA) per tridiagonal; dynamic shared memory holds the
     // twisted-factorisation pivots of the 32 lanes
@@ -1131,7 +1158,8 @@ cudaError_t launch_tridiag_quad(const double* alpha, const double* beta, const d
         cudaError_t e = cudaFuncSetAttribute(k_tridiag_quad<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              smem);                                                         \
         if (e != cudaSuccess) return e;                                                                     \
-        k_tridiag_quad<MM><<<count, 32, smem, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi);   \
+        k_tridiag_quad<MM><<<count, 32, smem, st>>>(alpha, beta, norm2, scale_per_col, count, m, ld, psi,    \
+                                                     cols, mcol);                                           \
         return cudaGetLastError();                                                                          \
     }
     VNE_QUAD_CASE(32)

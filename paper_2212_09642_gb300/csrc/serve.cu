@@ -8,14 +8,26 @@
 // 2.576 * stderr <= (eps / 2) * |estimate| (at least two blocks) or the
 // probe cap; estimate = sum_i psi(q_i) + mean psi(g').  The adaptive
 // algorithm the paper cites is not printed in it; this is the stated proxy.
+// With a Krylov tolerance tau (Section 5.2 keeps the Krylov error of the
+// adaptive estimator within half the requested accuracy), the Lanczos runs of
+// a block -- the basis vectors' quadratic forms at admission, then each
+// block of deflated probes -- stop together at the first multiple of
+// check_every below m at which every column's Theorem 4.4 estimate is at most
+// tau |psi| (lam_min half the column's smallest positive Ritz value, lam_max
+// the Gershgorin bound).  The sketch f(A) Omega takes opt.sketch_steps steps
+// (any sketch keeps Hutch++ unbiased; it sets only the variance removed).
 //
 // Device layout: an arena of fixed capacity (rows, nonzeros) holds the
 // packed CSR of every admitted query and the Lanczos vectors of its current
 // block (two slots and u, panel-major, K columns) at a row range that the
 // query keeps from admission to completion; its CSR is copied there once.
 // Per-query scalars live in segment slot s (0 .. max_active - 1) of
-// [m][max_active * K] arrays.  The work tables of the packed operator are
-// rebuilt on the host only when the active set changes.
+// [m][(max_active + 1) * K] arrays; segment max_active is never active.  The
+// work tables of the packed operator (work items and their CTA-to-segment
+// map, long-row chunks, row tiles) are device tables whose ranges a query
+// takes at admission, first fit, its own schedule shifted to its arena rows
+// and nonzeros; at completion its CTAs and tiles are handed to the idle
+// segment and the ranges are freed.  No tick rebuilds the tables.
 //
 // A tick (vne_server_step) is one Lanczos step of every active query, each
 // at its own step j: queries whose block starts get their deflated start
@@ -77,6 +89,52 @@ struct Ranges {
 
 constexpr int kSketchCols = 4;  // N_r of the served Hutch++
 
+// Device records with first-fit ranges; a table grows (keeping its
+// contents, the new part filled with `fill`) when a range does not fit.
+// `per` records per range unit.
+template <typename R>
+struct DevTable {
+    R* d = nullptr;
+    int64_t cap = 0;  // range units
+    int per = 1;
+    R fill{};
+    Ranges free;
+    int64_t take(vne_ctx* ctx, int64_t n) {
+        if (n <= 0) return 0;
+        int64_t b = free.take(n);
+        if (b >= 0) return b;
+        const int64_t ncap = std::max<int64_t>({2 * cap, cap + n, 1024});
+        R* nd = nullptr;
+        VNE_TRY_CUDA(ctx, dev_malloc((void**)&nd, (size_t)ncap * per * sizeof(R)));
+        cudaError_t e = cap ? cudaMemcpyAsync(nd, d, (size_t)cap * per * sizeof(R), cudaMemcpyDeviceToDevice,
+                                              ctx->stream)
+                            : cudaSuccess;
+        if (e == cudaSuccess) {
+            const std::vector<R> tail((size_t)(ncap - cap) * per, fill);
+            e = cudaMemcpyAsync(nd + (size_t)cap * per, tail.data(), tail.size() * sizeof(R),
+                                cudaMemcpyHostToDevice, ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            dev_free(nd);
+            VNE_TRY_CUDA(ctx, e);
+        }
+        dev_free(d);
+        d = nd;
+        free.give(cap, ncap - cap);
+        cap = ncap;
+        return free.take(n);
+    }
+    void give(int64_t b, int64_t n) {
+        if (n > 0) free.give(b, n);
+    }
+    void put(vne_ctx* ctx, int64_t b, const std::vector<R>& v) {
+        if (!v.empty())
+            VNE_TRY_CUDA(ctx, cudaMemcpyAsync(d + (size_t)b * per, v.data(), v.size() * sizeof(R),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+    }
+};
+
 }  // namespace
 
 struct vne_server {
@@ -84,6 +142,8 @@ struct vne_server {
     vne_options opt;
     size_t budget = 0, used = 0;
     int max_active = 64, m = 40, K = 64, ks = 16, max_vectors = 8192;
+    double quad_tol = 0.0;  // > 0: Krylov tolerance; < 0: half of each query's accuracy; 0: m steps
+    int check = 5, grid = 256;  // Theorem 4.4 estimate over 256 geometric + 256 linear points
     int precision = -1;  // -1 not yet known, 0 FP32, 1 FP64 (all queries share it)
     // arena
     int64_t rows_cap = 0, nnz_cap = 0;
@@ -91,12 +151,19 @@ struct vne_server {
     int32_t *a_rowptr = nullptr, *a_col = nullptr, *a_nid = nullptr;
     void *slot0 = nullptr, *slot1 = nullptr, *u = nullptr, *q = nullptr;
     double *alpha = nullptr, *beta = nullptr, *sigma = nullptr, *norm2 = nullptr, *mean = nullptr, *psi = nullptr,
-           *coef = nullptr, *scale = nullptr;
+           *coef = nullptr, *scale = nullptr, *est = nullptr;
     std::vector<void*> owned;
-    // segment slots
+    // segment slots (segment max_active: the idle one)
+    int nseg = 65;
     std::vector<int> slot_req;  // request index, -1 free
-    Problem P;                  // packed operator of the active set (tables in context workspace)
-    bool dirty = true;
+    Problem P;                  // packed operator of the active set (tables below, not owned by P)
+    DevTable<WorkItem> items;   // range unit: one CTA (VNE_WARPS items)
+    DevTable<int32_t> cta_seg;  // range unit: one CTA
+    DevTable<HubRow> hubs;
+    DevTable<RowTile> tiles;
+    Ranges hub_slots;           // partial-sum slots of the long-row chunks
+    int64_t hub_slot_cap = 0;
+    SegInfo* d_segs = nullptr;
     struct Req {
         vne_matrix* M;
         double eps;
@@ -109,8 +176,11 @@ struct vne_server {
         int blocks = 0;
         int64_t nvec = 0;
         double mean = 0.0, m2 = 0.0, low = 0.0, est = 0.0, se = 0.0;
+        double tau = 0.0, lam_max = 0.0;  // Krylov tolerance (0: m steps), Gershgorin bound of A
         int rank = 0;
         size_t footprint = 0;
+        // ranges of the work tables: CTAs, long rows, their slots, tiles
+        int64_t cta_b = 0, cta_n = 0, hub_b = 0, hub_n = 0, hs_b = 0, hs_n = 0, tile_b = 0, tile_n = 0;
         int64_t submit_tick = 0, admit_tick = -1, done_tick = -1;
     };
     std::vector<Req> reqs;
@@ -120,6 +190,11 @@ struct vne_server {
     int64_t tick = 0;
     ~vne_server() {
         for (void* p : owned) dev_free(p);
+        dev_free(items.d);
+        dev_free(cta_seg.d);
+        dev_free(hubs.d);
+        dev_free(tiles.d);
+        dev_free(d_segs);
     }
 };
 
@@ -134,8 +209,9 @@ size_t row_bytes(const vne_server* S, size_t es) {
 void arena_alloc(vne_server* S, bool fp64) {
     vne_ctx* ctx = S->ctx;
     const size_t es = fp64 ? 8 : 4;
-    const int SK = S->max_active * S->K;
-    const size_t fixed = (size_t)(3 * S->m + 8 + 4) * SK * 8 + ((size_t)1 << 20);
+    S->nseg = S->max_active + 1;
+    const int SK = S->nseg * S->K;
+    const size_t fixed = (size_t)(3 * S->m + 8 + 4 + 3) * SK * 8 + ((size_t)1 << 20);
     VNE_REQUIRE(ctx, S->budget > fixed, VNE_ENOMEM, "HBM budget %zu too small for the server's scalars", S->budget);
     // rows and nonzeros share the budget: up to 12 nonzeros per row
     const size_t per_row = row_bytes(S, es) + 12 * 4;
@@ -160,6 +236,7 @@ void arena_alloc(vne_server* S, bool fp64) {
     S->norm2 = (double*)take((size_t)SK * 8);
     S->mean = (double*)take((size_t)SK * 8);
     S->psi = (double*)take((size_t)SK * 8);
+    S->est = (double*)take((size_t)3 * SK * 8);
     S->scale = (double*)take((size_t)SK * 8);
     S->coef = (double*)take((size_t)kSketchCols * SK * 8);
     if (fp64 && S->ks > 16) {  // FP64 panels hold 4, 8 or 16 columns
@@ -170,80 +247,115 @@ void arena_alloc(vne_server* S, bool fp64) {
     S->nnz.reset(S->nnz_cap);
     S->slot_req.assign(S->max_active, -1);
     S->precision = fp64 ? 1 : 0;
-}
-
-// Rebuild the work tables of the packed operator from the active set: every
-// slot is a segment (an empty one when free), each active query's own
-// schedule shifted to its arena rows and nonzeros.
-void rebuild_layout(vne_server* S) {
-    vne_ctx* ctx = S->ctx;
+    // the packed operator: the arena, and tables filled per query
     Problem& P = S->P;
     P.owns_tables = false;
-    P.fp64 = S->precision == 1;
+    P.fp64 = fp64;
     P.valued = false;
     P.ipw = 1;
-    P.segs.assign(S->max_active, SegInfo{});
-    P.items.clear();
-    P.hubs.clear();
-    P.cta_seg.clear();
-    P.tiles.clear();
-    P.hub_slots = 0;
-    P.stage_nnz = 1;
-    std::vector<double> hscale((size_t)S->max_active * S->K, 0.0);
-    for (int s = 0; s < S->max_active; s++) {
-        const int ri = S->slot_req[s];
-        if (ri < 0) continue;
-        const vne_server::Req& rq = S->reqs[ri];
-        Problem* MP = matrix_problem(rq.M, &S->opt);
-        SegInfo sg = MP->segs[0];
-        const int32_t r0 = (int32_t)rq.r0, e0 = (int32_t)rq.e0, hub_base = (int32_t)P.hubs.size();
-        sg.row_begin = r0;
-        sg.cta_begin = (int32_t)(P.items.size() / VNE_WARPS);
-        sg.cta_count = (int32_t)(MP->items.size() / VNE_WARPS);
-        sg.tile_begin = (int32_t)P.tiles.size();
-        sg.hub_begin = hub_base;
-        for (WorkItem it : MP->items) {
-            if (it.rows > 0) it.row += r0;
-            else if (it.rows < 0) it.row += hub_base;
-            if (it.rows != 0) {
-                it.nnz_begin += e0;
-                it.nnz_end += e0;
-            }
-            P.items.push_back(it);
-        }
-        for (HubRow h : MP->hubs) {
-            h.row += r0;
-            h.slot += P.hub_slots;
-            h.seg = s;
-            P.hubs.push_back(h);
-        }
-        P.hub_slots += MP->hub_slots;
-        for (int32_t c = 0; c < sg.cta_count; c++) P.cta_seg.push_back(s);
-        for (RowTile t : MP->tiles) {
-            t.row_begin += r0;
-            t.row_end += r0;
-            t.seg = s;
-            P.tiles.push_back(t);
-        }
-        P.stage_nnz = std::max(P.stage_nnz, MP->stage_nnz);
-        P.segs[s] = sg;
-        for (int c = 0; c < S->K; c++) hscale[(size_t)s * S->K + c] = sg.scale;
-    }
     P.n_total = (int32_t)S->rows_cap;
     P.nnz_total = S->nnz_cap;
-    P.nseg = S->max_active;
+    P.nseg = S->nseg;
     P.rowptr = S->a_rowptr;
     P.col = S->a_col;
     P.node_id = S->a_nid;
     P.vals = nullptr;
-    P.d_segs = upload(ctx, "srv.segs", P.segs);
-    P.d_items = upload(ctx, "srv.items", P.items);
-    P.d_hubs = upload(ctx, "srv.hubs", P.hubs);
-    P.d_cta_seg = upload(ctx, "srv.ctaseg", P.cta_seg);
-    P.d_tiles = upload(ctx, "srv.tiles", P.tiles);
-    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->scale, hscale.data(), hscale.size() * 8, cudaMemcpyHostToDevice,
+    P.stage_nnz = 1;
+    P.segs.assign(S->nseg, SegInfo{});
+    S->items.per = VNE_WARPS;
+    // never-used parts of the tables: empty items, CTAs and tiles of the idle segment
+    S->items.fill = WorkItem{0, 0, 0, 0};
+    S->cta_seg.fill = S->max_active;
+    S->tiles.fill = RowTile{0, 0, S->max_active, 0};
+    S->hubs.fill = HubRow{0, 0, 0, S->max_active};
+    VNE_TRY_CUDA(ctx, dev_malloc((void**)&S->d_segs, (size_t)S->nseg * sizeof(SegInfo)));
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->d_segs, P.segs.data(), (size_t)S->nseg * sizeof(SegInfo),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+}
+
+// Place a query's schedule in the work tables: its CTAs, long rows, their
+// partial-sum slots and row tiles get ranges of their own (first fit), its
+// items and tiles shifted to its arena rows and nonzeros and mapped to its
+// segment slot s.
+void place_tables(vne_server* S, vne_server::Req& rq, int s) {
+    vne_ctx* ctx = S->ctx;
+    Problem& P = S->P;
+    Problem* MP = matrix_problem(rq.M, &S->opt);
+    rq.cta_n = (int64_t)(MP->items.size() / VNE_WARPS);
+    rq.hub_n = (int64_t)MP->hubs.size();
+    rq.hs_n = MP->hub_slots;
+    rq.tile_n = (int64_t)MP->tiles.size();
+    rq.cta_b = S->items.take(ctx, rq.cta_n);
+    if (S->cta_seg.take(ctx, rq.cta_n) != rq.cta_b)  // the two CTA tables share their ranges
+        VNE_REQUIRE(ctx, false, VNE_EDEVICE, "server CTA tables out of step");
+    rq.hub_b = S->hubs.take(ctx, rq.hub_n);
+    rq.tile_b = S->tiles.take(ctx, rq.tile_n);
+    rq.hs_b = 0;
+    if (rq.hs_n > 0) {
+        rq.hs_b = S->hub_slots.take(rq.hs_n);
+        if (rq.hs_b < 0) {  // grow the slot space
+            const int64_t grow = std::max<int64_t>(rq.hs_n, S->hub_slot_cap + 1024);
+            S->hub_slots.give(S->hub_slot_cap, grow);
+            S->hub_slot_cap += grow;
+            rq.hs_b = S->hub_slots.take(rq.hs_n);
+        }
+    }
+    const int32_t r0 = (int32_t)rq.r0, e0 = (int32_t)rq.e0, hb = (int32_t)rq.hub_b;
+    std::vector<WorkItem> it = MP->items;
+    for (WorkItem& w : it) {
+        if (w.rows > 0) w.row += r0;
+        else if (w.rows < 0) w.row += hb;
+        if (w.rows != 0) {
+            w.nnz_begin += e0;
+            w.nnz_end += e0;
+        }
+    }
+    std::vector<HubRow> hubs = MP->hubs;
+    for (HubRow& h : hubs) {
+        h.row += r0;
+        h.slot += (int32_t)rq.hs_b;
+        h.seg = s;
+    }
+    std::vector<RowTile> tiles = MP->tiles;
+    for (RowTile& t : tiles) {
+        t.row_begin += r0;
+        t.row_end += r0;
+        t.seg = s;
+    }
+    S->items.put(ctx, rq.cta_b, it);
+    S->cta_seg.put(ctx, rq.cta_b, std::vector<int32_t>((size_t)rq.cta_n, s));
+    S->hubs.put(ctx, rq.hub_b, hubs);
+    S->tiles.put(ctx, rq.tile_b, tiles);
+    SegInfo sg = MP->segs[0];
+    sg.row_begin = r0;
+    sg.cta_begin = (int32_t)rq.cta_b;
+    sg.cta_count = (int32_t)rq.cta_n;
+    sg.tile_begin = (int32_t)rq.tile_b;
+    sg.hub_begin = hb;
+    P.segs[s] = sg;
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->d_segs + s, &P.segs[s], sizeof(SegInfo), cudaMemcpyHostToDevice,
                                       ctx->stream));
-    S->dirty = false;
+    std::vector<double> hscale((size_t)S->K, sg.scale);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->scale + (size_t)s * S->K, hscale.data(), hscale.size() * 8,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    P.stage_nnz = std::max(P.stage_nnz, MP->stage_nnz);
+}
+
+// Hand a finished query's CTAs and tiles to the idle segment and free its
+// ranges (its items and long rows are no longer reachable).
+void clear_tables(vne_server* S, vne_server::Req& rq) {
+    vne_ctx* ctx = S->ctx;
+    const int32_t idle = S->max_active;
+    S->cta_seg.put(ctx, rq.cta_b, std::vector<int32_t>((size_t)rq.cta_n, idle));
+    S->tiles.put(ctx, rq.tile_b, std::vector<RowTile>((size_t)rq.tile_n, RowTile{0, 0, idle, 0}));
+    S->P.segs[rq.slot] = SegInfo{};
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(S->d_segs + rq.slot, &S->P.segs[rq.slot], sizeof(SegInfo),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    S->items.give(rq.cta_b, rq.cta_n);
+    S->cta_seg.give(rq.cta_b, rq.cta_n);
+    S->hubs.give(rq.hub_b, rq.hub_n);
+    S->tiles.give(rq.tile_b, rq.tile_n);
+    if (rq.hs_n > 0) S->hub_slots.give(rq.hs_b, rq.hs_n);
 }
 
 // Admit the query at the head of the queue if a slot and arena space are
@@ -275,29 +387,37 @@ bool admit_one(vne_server* S, int ri) {
     int rank = 0;
     vne_options o = S->opt;
     o.probe_offset = 0;
-    hutchpp_deflation<T>(M, &o, kSketchCols, S->m, rq.seed, (T*)S->q + r0 * kSketchCols, psi_q, rank);
+    Adaptive ad;  // the Krylov rule of the blocks, on the basis vectors' quadratic forms
+    ad.tol = rq.tau;
+    ad.check = S->check;
+    ad.lam_min = 0.0;
+    ad.lam_max = rq.lam_max;
+    ad.grid = S->grid;
+    const int ms = S->opt.sketch_steps > 0 ? std::min(S->opt.sketch_steps, S->m) : S->m;
+    hutchpp_deflation<T>(M, &o, kSketchCols, S->m, ms, rq.seed, (T*)S->q + r0 * kSketchCols, psi_q, rank,
+                         rq.tau > 0.0 ? &ad : nullptr);
     rq.low = 0.0;
     for (int i = 0; i < rank; i++) rq.low += psi_q[i];
     rq.rank = rank;
     rq.slot = s;
     rq.r0 = r0;
     rq.e0 = e0;
+    place_tables(S, rq, s);
     rq.j = 0;
     rq.state = 1;
     rq.admit_tick = S->tick;
     S->slot_req[s] = ri;
     S->used += rq.footprint;
     S->active.push_back(ri);
-    S->dirty = true;
     return true;
 }
 
 void release(vne_server* S, vne_server::Req& rq) {
+    clear_tables(S, rq);
     S->rows.give(rq.r0, rq.M->n + 1);
     S->nnz.give(rq.e0, std::max<int64_t>(rq.M->nnz, 1));
     S->slot_req[rq.slot] = -1;
     S->used -= rq.footprint;
-    S->dirty = true;
 }
 
 template <typename T>
@@ -313,12 +433,25 @@ int tick_impl(vne_server* S) {
     }
     S->tick++;
     if (S->active.empty()) return 0;
-    if (S->dirty) rebuild_layout(S);
     Problem& P = S->P;
-    const int K = S->K, SK = S->max_active * K, ks = S->ks, panels = K / ks;
+    P.d_segs = S->d_segs;
+    P.d_items = S->items.d;
+    P.d_cta_seg = S->cta_seg.d;
+    P.d_hubs = S->hubs.d;
+    P.d_tiles = S->tiles.d;
+    // the tables' extent: the ends of the ranges in use
+    int64_t cta_high = 0, tile_high = 0, hub_high = 0, slot_high = 0;
+    for (int ri : S->active) {
+        const vne_server::Req& rq = S->reqs[ri];
+        cta_high = std::max(cta_high, rq.cta_b + rq.cta_n);
+        tile_high = std::max(tile_high, rq.tile_b + rq.tile_n);
+        hub_high = std::max(hub_high, rq.hub_b + rq.hub_n);
+        slot_high = std::max(slot_high, rq.hs_b + rq.hs_n);
+    }
+    const int K = S->K, SK = S->nseg * K, ks = S->ks, panels = K / ks;
     // blocks that start now: deflated start vectors
-    std::vector<int32_t> tlist, tb(S->max_active, 0), tc(S->max_active, 0), col0(S->max_active, 0);
-    std::vector<uint64_t> seeds(S->max_active, 0);
+    std::vector<int32_t> tlist, tb(S->nseg, 0), tc(S->nseg, 0), col0(S->nseg, 0);
+    std::vector<uint64_t> seeds(S->nseg, 0);
     for (int ri : S->active) {
         vne_server::Req& rq = S->reqs[ri];
         const SegInfo& sg = P.segs[rq.slot];
@@ -347,7 +480,7 @@ int tick_impl(vne_server* S) {
         sp.sig1 = S->sigma;
         sp.w1 = (T*)S->slot0;
         sp.part = ws_get_t<double>(ctx, "srv.part", tlist.size() * kSketchCols * K);
-        sp.counter = ws_get_t<uint32_t>(ctx, "srv.counter", S->max_active);
+        sp.counter = ws_get_t<uint32_t>(ctx, "srv.counter", S->nseg);
         sp.ntiles = (int32_t)tlist.size();
         sp.K = K;
         sp.n_total = P.n_total;
@@ -356,7 +489,7 @@ int tick_impl(vne_server* S) {
         ctx->launches += 3;
     }
     // one Lanczos step of every active segment, each at its own step
-    std::vector<int32_t> segj(S->max_active, 0);
+    std::vector<int32_t> segj(S->nseg, 0);  // the idle segment max_active stays 0
     for (int ri : S->active) segj[S->reqs[ri].slot] = S->reqs[ri].j;
     StepParams<T> p;
     memset(&p, 0, sizeof(p));
@@ -367,21 +500,20 @@ int tick_impl(vne_server* S) {
     p.nseg = P.nseg;
     p.seg = P.d_segs;
     p.items = P.d_items;
-    p.ctas_per_panel = P.ctas_per_panel();
+    p.ctas_per_panel = (int32_t)cta_high;
     p.cta_seg = P.d_cta_seg;
     p.hubs = P.d_hubs;
-    p.nhubs = std::max<int>((int)P.hubs.size(), 1);
-    p.hub_slots = std::max(P.hub_slots, 1);
+    p.nhubs = (int32_t)std::max<int64_t>(hub_high, 1);
+    p.hub_slots = (int32_t)std::max<int64_t>(slot_high, 1);
     p.hub_part = ws_get_t<T>(ctx, "srv.hub_part", (size_t)panels * p.hub_slots * ks);
     p.hub_cnt = ws_get_t<uint32_t>(ctx, "srv.hub_cnt", (size_t)panels * p.nhubs);
     p.hub_dot = ws_get_t<double>(ctx, "srv.hub_dot", (size_t)panels * p.nhubs * ks);
     p.stage_nnz = std::max(P.stage_nnz, 1);
     p.ipw = 1;
     p.tiles = P.d_tiles;
-    p.tiles_per_panel = P.tiles_per_panel();
+    p.tiles_per_panel = (int32_t)tile_high;
     p.u = (T*)S->u;
-    p.part = ws_get_t<double>(ctx, "srv.step_part",
-                              (size_t)panels * std::max(P.ctas_per_panel(), P.tiles_per_panel()) * ks);
+    p.part = ws_get_t<double>(ctx, "srv.step_part", (size_t)panels * std::max(cta_high, tile_high) * ks);
     p.counter = ws_get_t<uint32_t>(ctx, "srv.step_counter", (size_t)panels * P.nseg);
     p.segj = upload(ctx, "srv.segj", segj);
     p.slot0 = (T*)S->slot0;
@@ -389,57 +521,110 @@ int tick_impl(vne_server* S) {
     p.alpha0 = S->alpha;
     p.beta0 = S->beta;
     p.sigma0 = S->sigma;
-    if (P.ctas_per_panel() > 0) {
+    if (cta_high > 0) {
         VNE_TRY_CUDA(ctx, launch_step_update_segj<T>(p, ks, panels, st));
         ctx->launches += 2;
     }
-    // blocks that end now: quadratures and statistics
-    std::vector<int> ending;
-    for (int ri : S->active)
-        if (S->reqs[ri].j == S->m) ending.push_back(ri);
-    for (int ri : ending) {
-        const int s = S->reqs[ri].slot;
-        const size_t o = (size_t)s * K;
-        VNE_TRY_CUDA(ctx, launch_tridiag_quad(S->alpha + o, S->beta + o, S->norm2 + o, S->scale + o, K, S->m, SK,
-                                              S->psi + o, st));
-        ctx->launches += 1;
+    // blocks that end now (step m) or check their Krylov error (a multiple of
+    // check_every below m, with a tolerance).  A check needs every column's
+    // Theorem 4.4 estimate within tau |psi|; it is evaluated on the first
+    // kFirst columns of each checking query, and on the others only for the
+    // queries whose first columns all pass (the same decision, without the
+    // FP64 work of estimates that cannot change it)
+    std::vector<int> ending, checking;
+    for (int ri : S->active) {
+        const vne_server::Req& rq = S->reqs[ri];
+        if (rq.j == S->m) ending.push_back(ri);
+        else if (rq.tau > 0.0 && rq.j % S->check == 0) checking.push_back(ri);
     }
-    int completed = 0;
-    if (!ending.empty()) {
-        std::vector<double> hp = download(ctx, S->psi, SK);
-        std::vector<int> still;
-        for (int ri : S->active) {
-            vne_server::Req& rq = S->reqs[ri];
-            if (rq.j != S->m) {
-                rq.j++;
-                still.push_back(ri);
-                continue;
-            }
-            for (int c = 0; c < K; c++) {  // Welford update
-                const double x = hp[(size_t)rq.slot * K + c];
-                rq.nvec++;
-                const double d = x - rq.mean;
-                rq.mean += d / (double)rq.nvec;
-                rq.m2 += d * (x - rq.mean);
-            }
-            rq.blocks++;
-            rq.est = rq.low + rq.mean;
-            rq.se = rq.nvec > 1 ? sqrt(rq.m2 / (double)(rq.nvec - 1) / (double)rq.nvec) : 0.0;
-            const bool converged = rq.blocks >= 2 && 2.576 * rq.se <= 0.5 * rq.eps * fabs(rq.est);
-            if (converged || rq.nvec >= rq.max_vectors) {
-                rq.state = 2;
-                rq.done_tick = S->tick;
-                release(S, rq);
-                completed++;
-            } else {
-                rq.j = 0;  // the next block starts at the next tick
-                still.push_back(ri);
+    const int kFirst = std::min(K, 8);
+    std::vector<double> hp, he;
+    auto evaluate = [&](const std::vector<int>& quad_all, const std::vector<int>& est_q, int c_begin, int c_end) {
+        // quadratures of all columns of quad_all, quadratures and estimates of
+        // columns [c_begin, c_end) of est_q; then psi and the estimates to the host
+        std::vector<int32_t> qcols, qm, bcols, bm;
+        std::vector<double> blam;
+        for (int ri : quad_all) {
+            const vne_server::Req& rq = S->reqs[ri];
+            for (int c = 0; c < K; c++) {
+                qcols.push_back(rq.slot * K + c);
+                qm.push_back(rq.j);
             }
         }
-        S->active.swap(still);
-    } else {
-        for (int ri : S->active) S->reqs[ri].j++;
+        for (int ri : est_q) {
+            const vne_server::Req& rq = S->reqs[ri];
+            for (int c = c_begin; c < c_end; c++) {
+                qcols.push_back(rq.slot * K + c);
+                qm.push_back(rq.j);
+                bcols.push_back(rq.slot * K + c);
+                bm.push_back(rq.j);
+                blam.push_back(rq.lam_max);
+            }
+        }
+        if (qcols.empty()) return;
+        VNE_TRY_CUDA(ctx, launch_tridiag_quad_list(S->alpha, S->beta, S->norm2, S->scale, (int)qcols.size(),
+                                                   upload(ctx, "srv.qcols", qcols), upload(ctx, "srv.qm", qm), S->m,
+                                                   SK, S->psi, st));
+        ctx->launches += 1;
+        if (!bcols.empty()) {
+            VNE_TRY_CUDA(ctx, launch_tridiag_bounds_list(S->alpha, S->beta, S->norm2, S->scale, (int)bcols.size(),
+                                                         upload(ctx, "srv.bcols", bcols), upload(ctx, "srv.bm", bm),
+                                                         upload(ctx, "srv.blam", blam), S->m, SK, 0.0, 1.0, S->grid,
+                                                         S->est, S->est + SK, S->est + 2 * SK, st));
+            ctx->launches += 1;
+            he = download(ctx, S->est + 2 * SK, SK);
+        }
+        hp = download(ctx, S->psi, SK);
+    };
+    auto passes = [&](const vne_server::Req& rq, int c_begin, int c_end) {
+        for (int c = c_begin; c < c_end; c++) {
+            const size_t o = (size_t)rq.slot * K + c;
+            if (!(he[o] <= rq.tau * fabs(hp[o]))) return false;
+        }
+        return true;
+    };
+    evaluate(ending, checking, 0, kFirst);
+    std::vector<int> candidates;
+    for (int ri : checking)
+        if (passes(S->reqs[ri], 0, kFirst)) candidates.push_back(ri);
+    std::vector<char> block_done(S->reqs.size(), 0);
+    for (int ri : ending) block_done[ri] = 1;
+    // the rest of the candidates' columns (the device arrays keep the values
+    // of the first evaluation for every other column)
+    if (!candidates.empty() && kFirst < K) evaluate({}, candidates, kFirst, K);
+    for (int ri : candidates)
+        if (passes(S->reqs[ri], kFirst, K)) block_done[ri] = 1;
+    int completed = 0;
+    std::vector<int> still;
+    for (int ri : S->active) {
+        vne_server::Req& rq = S->reqs[ri];
+        if (!block_done[ri]) {
+            rq.j++;
+            still.push_back(ri);
+            continue;
+        }
+        for (int c = 0; c < K; c++) {  // Welford update
+            const double x = hp[(size_t)rq.slot * K + c];
+            rq.nvec++;
+            const double d = x - rq.mean;
+            rq.mean += d / (double)rq.nvec;
+            rq.m2 += d * (x - rq.mean);
+        }
+        rq.blocks++;
+        rq.est = rq.low + rq.mean;
+        rq.se = rq.nvec > 1 ? sqrt(rq.m2 / (double)(rq.nvec - 1) / (double)rq.nvec) : 0.0;
+        const bool converged = rq.blocks >= 2 && 2.576 * rq.se <= 0.5 * rq.eps * fabs(rq.est);
+        if (converged || rq.nvec >= rq.max_vectors) {
+            rq.state = 2;
+            rq.done_tick = S->tick;
+            release(S, rq);
+            completed++;
+        } else {
+            rq.j = 0;  // the next block starts at the next tick
+            still.push_back(ri);
+        }
     }
+    S->active.swap(still);
     return completed;
 }
 
@@ -462,6 +647,8 @@ extern "C" vne_status vne_server_create(vne_ctx* ctx, uint64_t hbm_budget_bytes,
     if (opt) S->opt = *opt;
     else vne_options_default(&S->opt);
     S->opt.reorth = 0;
+    S->quad_tol = S->opt.quad_tol;
+    S->check = S->opt.check_every > 0 ? S->opt.check_every : 5;
     S->ks = S->opt.panel > 0 ? S->opt.panel : 16;
     if (S->ks != 8 && S->ks != 16 && S->ks != 32) S->ks = 16;
     S->K = ((block_vectors + S->ks - 1) / S->ks) * S->ks;
@@ -500,6 +687,8 @@ extern "C" vne_status vne_server_submit(vne_server* S, vne_matrix* M, double rel
     r.seed = seed;
     r.seed_mixed = seed_mix(seed);
     r.max_vectors = max_vectors;
+    r.tau = S->quad_tol > 0.0 ? S->quad_tol : (S->quad_tol < 0.0 ? 0.5 * rel_eps : 0.0);
+    r.lam_max = M->normM * M->scale;
     r.footprint = (size_t)(M->n + 1) * row_bytes(S, es) + (size_t)4 * M->nnz;
     VNE_REQUIRE(ctx, M->n + 1 <= S->rows_cap && M->nnz <= S->nnz_cap && r.footprint <= S->budget, VNE_ENOMEM,
                 "query of %lld rows and %lld nonzeros exceeds the server's capacity", (long long)M->n,

@@ -53,7 +53,7 @@ class vne_options(ctypes.Structure):
                 ("step_variant", ctypes.c_int32), ("interleave", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("probe_offset", ctypes.c_int32), ("check_every", ctypes.c_int32), ("quad_tol", ctypes.c_double),
                 ("spectrum_min", ctypes.c_double), ("gaussian_probes", ctypes.c_int32),
-                ("items_per_warp", ctypes.c_int32)]
+                ("items_per_warp", ctypes.c_int32), ("sketch_steps", ctypes.c_int32)]
 
 
 _lib = None

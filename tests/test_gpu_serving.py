@@ -21,12 +21,12 @@ def _graphs():
             graphs.erdos_renyi(7000, 8 / 6999, 35)]
 
 
-def _run(vctx, mats, schedule, budget, max_active, eps=2e-3, cap=1024):
+def _run(vctx, mats, schedule, budget, max_active, eps=2e-3, cap=1024, opt=None):
     """schedule: list of (tick, matrix index, seed); returns per-request results and
     the largest number of queries active in one tick.  Checks that the bytes
     held by admitted queries never exceed the budget."""
     srv = vne.vne_server_create(vctx, budget, max_active=max_active, krylov_steps=M_STEPS, block_vectors=64,
-                                opt=vne.options(reorth=0, panel=8))
+                                opt=opt if opt is not None else vne.options(reorth=0, panel=8))
     tickets = {}
     most = 0
     try:
@@ -116,6 +116,52 @@ def test_serving_fp64_one_at_a_time(vctx):
             A, _ = density.density_matrix(gs[mi])
             ref = estimators.hutchpp(A, 4, r["vectors"], M_STEPS, seed=seed, reorth="none")
             assert abs(r["estimate"] - ref) <= 1e-10 * ref
+    finally:
+        for m in mats:
+            vne.vne_matrix_destroy(m)
+
+
+CHECK = 3
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_serving_krylov_stopping(vctx, fp64):
+    """quad_tol < 0: every query's blocks (the basis vectors' quadratic forms
+    at admission, then the deflated probe blocks) stop their Lanczos runs at
+    the first multiple of check_every where every column's Theorem 4.4
+    estimate is within half the query's accuracy (Section 5.2); the FP32
+    server also takes a short sketch (sketch_steps).  Each result is
+    bit-identical alone and in the mix; it is the oracle's served estimator
+    with the same rule (1e-5 mixed, 1e-10 FP64): the same probes, the same
+    Lanczos steps (the ticks a query took are the oracle's block steps) and
+    the same estimate."""
+    gs = _graphs()[:4] if not fp64 else _graphs()[:2]
+    mats = [vne.matrix_from_graph(vctx, g, fp64=fp64) for g in gs]
+    eps = 2e-3
+    sketch = M_STEPS if fp64 else 8  # FP32: a short sketch (Hutch++ stays unbiased)
+    opt = vne.options(reorth=0, panel=8, quad_tol=-1.0, check_every=CHECK, sketch_steps=0 if fp64 else sketch)
+    try:
+        if fp64:
+            sched = [(0, i, 300 + i) for i in range(len(gs))]
+            res, most = _run(vctx, mats, sched, budget=1 << 34, max_active=1, eps=eps, opt=opt)
+        else:
+            sched = [(0, 0, 41), (0, 1, 42), (5, 2, 43), (17, 3, 44), (20, 0, 45)]
+            res, most = _run(vctx, mats, sched, budget=1 << 36, max_active=8, eps=eps, opt=opt)
+            assert most >= 3
+        for (mi, seed), r in res.items():
+            assert r["state"] == 2
+            if not fp64:
+                alone, _ = _run(vctx, mats, [(0, mi, seed)], budget=1 << 36, max_active=8, eps=eps, opt=opt)
+                assert alone[(mi, seed)]["estimate"] == r["estimate"]
+            A, _ = density.density_matrix(gs[mi])
+            ref, _, nv, steps, _ = estimators.served_hutchpp(A, eps, 64, M_STEPS, seed, max_vectors=1024,
+                                                             quad_tol=0.5 * eps, check_every=CHECK,
+                                                             sketch_steps=sketch)
+            assert r["vectors"] == nv
+            assert r["done_tick"] - r["admit_tick"] == sum(steps), (steps, r)
+            assert max(steps) < M_STEPS  # the blocks stopped early
+            tol = 1e-10 if fp64 else 1e-5
+            assert abs(r["estimate"] - ref) <= tol * ref
     finally:
         for m in mats:
             vne.vne_matrix_destroy(m)
