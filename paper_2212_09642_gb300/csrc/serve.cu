@@ -387,6 +387,7 @@ bool admit_one(vne_server* S, int ri) {
     int rank = 0;
     vne_options o = S->opt;
     o.probe_offset = 0;
+    o.panel = sizeof(T) == 4 ? 8 : 4;  // the narrowest panel holding the 4 sketch columns
     Adaptive ad;  // the Krylov rule of the blocks, on the basis vectors' quadratic forms
     ad.tol = rq.tau;
     ad.check = S->check;
