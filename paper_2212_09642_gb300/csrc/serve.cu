@@ -164,6 +164,9 @@ struct vne_server {
     Ranges hub_slots;           // partial-sum slots of the long-row chunks
     int64_t hub_slot_cap = 0;
     SegInfo* d_segs = nullptr;
+    cudaEvent_t stage_ev = nullptr;  // recorded after each tick's staging copy
+    char* pin = nullptr;             // pinned staging of a tick's host arrays
+    size_t pin_cap = 0;
     struct Req {
         vne_matrix* M;
         double eps;
@@ -195,6 +198,8 @@ struct vne_server {
         dev_free(hubs.d);
         dev_free(tiles.d);
         dev_free(d_segs);
+        if (stage_ev) cudaEventDestroy(stage_ev);
+        pinned_free(pin);
     }
 };
 
@@ -450,6 +455,9 @@ int tick_impl(vne_server* S) {
         slot_high = std::max(slot_high, rq.hs_b + rq.hs_n);
     }
     const int K = S->K, SK = S->nseg * K, ks = S->ks, panels = K / ks;
+    // Every host array of the tick's launches is known before the first of
+    // them; they go to the device in one asynchronous copy from one pinned
+    // buffer (a copy from pageable memory would synchronise the stream).
     // blocks that start now: deflated start vectors
     std::vector<int32_t> tlist, tb(S->nseg, 0), tc(S->nseg, 0), col0(S->nseg, 0);
     std::vector<uint64_t> seeds(S->nseg, 0);
@@ -464,16 +472,95 @@ int tick_impl(vne_server* S) {
         for (int t = 0; t < sg.tile_count; t++) tlist.push_back(sg.tile_begin + t);
         rq.j = 1;
     }
+    // one Lanczos step of every active segment, each at its own step
+    std::vector<int32_t> segj(S->nseg, 0);  // the idle segment max_active stays 0
+    for (int ri : S->active) segj[S->reqs[ri].slot] = S->reqs[ri].j;
+    // blocks that end after this step (step m) or check their Krylov error (a
+    // multiple of check_every below m, with a tolerance).  A check needs
+    // every column's Theorem 4.4 estimate within tau |psi|; it is evaluated
+    // on the first kFirst columns of each checking query, and on the others
+    // only for the queries whose first columns all pass (the same decision,
+    // without the FP64 work of estimates that cannot change it)
+    std::vector<int> ending, checking;
+    for (int ri : S->active) {
+        const vne_server::Req& rq = S->reqs[ri];
+        if (rq.j == S->m) ending.push_back(ri);
+        else if (rq.tau > 0.0 && rq.j % S->check == 0) checking.push_back(ri);
+    }
+    const int kFirst = std::min(K, 8);
+    struct Lists {
+        std::vector<int32_t> qcols, qm, bcols, bm;
+        std::vector<double> blam;
+    };
+    auto make_lists = [&](const std::vector<int>& quad_all, const std::vector<int>& est_q, int c_begin, int c_end) {
+        // quadratures of all columns of quad_all, quadratures and estimates
+        // of columns [c_begin, c_end) of est_q
+        Lists L;
+        for (int ri : quad_all) {
+            const vne_server::Req& rq = S->reqs[ri];
+            for (int c = 0; c < K; c++) {
+                L.qcols.push_back(rq.slot * K + c);
+                L.qm.push_back(rq.j);
+            }
+        }
+        for (int ri : est_q) {
+            const vne_server::Req& rq = S->reqs[ri];
+            for (int c = c_begin; c < c_end; c++) {
+                L.qcols.push_back(rq.slot * K + c);
+                L.qm.push_back(rq.j);
+                L.bcols.push_back(rq.slot * K + c);
+                L.bm.push_back(rq.j);
+                L.blam.push_back(rq.lam_max);
+            }
+        }
+        return L;
+    };
+    Lists LA = make_lists(ending, checking, 0, kFirst);
+    // the staging copy (after the previous tick's copy has read the buffer)
+    struct Part {
+        const void* src;
+        size_t bytes, off;
+    };
+    std::vector<Part> parts;
+    size_t total = 0;
+    auto add = [&](const void* src, size_t bytes) {
+        const size_t off = (total + 15) & ~(size_t)15;
+        parts.push_back({src, bytes, off});
+        total = off + std::max<size_t>(bytes, 16);
+        return parts.size() - 1;
+    };
+    const size_t i_tl = add(tlist.data(), tlist.size() * 4), i_tb = add(tb.data(), tb.size() * 4),
+                 i_tc = add(tc.data(), tc.size() * 4), i_sd = add(seeds.data(), seeds.size() * 8),
+                 i_c0 = add(col0.data(), col0.size() * 4), i_sj = add(segj.data(), segj.size() * 4),
+                 i_qc = add(LA.qcols.data(), LA.qcols.size() * 4), i_qm = add(LA.qm.data(), LA.qm.size() * 4),
+                 i_bc = add(LA.bcols.data(), LA.bcols.size() * 4), i_bm = add(LA.bm.data(), LA.bm.size() * 4),
+                 i_bl = add(LA.blam.data(), LA.blam.size() * 8);
+    if (S->stage_ev) VNE_TRY_CUDA(ctx, cudaEventSynchronize(S->stage_ev));
+    if (S->pin_cap < total) {
+        pinned_free(S->pin);
+        S->pin = nullptr;
+        S->pin_cap = 0;
+        VNE_TRY_CUDA(ctx, pinned_malloc((void**)&S->pin, 2 * total));
+        S->pin_cap = 2 * total;
+    }
+    char* pin = S->pin;
+    for (const Part& q : parts)
+        if (q.bytes) memcpy(pin + q.off, q.src, q.bytes);
+    char* dstage = (char*)ws_get(ctx, "srv.stage", total);
+    VNE_TRY_CUDA(ctx, cudaMemcpyAsync(dstage, pin, total, cudaMemcpyHostToDevice, st));
+    if (!S->stage_ev) VNE_TRY_CUDA(ctx, cudaEventCreateWithFlags(&S->stage_ev, cudaEventDisableTiming));
+    VNE_TRY_CUDA(ctx, cudaEventRecord(S->stage_ev, st));
+    auto dptr = [&](size_t i) { return (void*)(dstage + parts[i].off); };
     if (!tlist.empty()) {
         SrvStartParams<T> sp{};
-        sp.tile_list = upload(ctx, "srv.tlist", tlist);
+        sp.tile_list = (const int32_t*)dptr(i_tl);
         sp.tiles = P.d_tiles;
         sp.seg = P.d_segs;
-        sp.seg_tb = upload(ctx, "srv.tb", tb);
-        sp.seg_tc = upload(ctx, "srv.tc", tc);
+        sp.seg_tb = (const int32_t*)dptr(i_tb);
+        sp.seg_tc = (const int32_t*)dptr(i_tc);
         sp.node_id = P.node_id;
-        sp.seg_seed = upload(ctx, "srv.seeds", seeds);
-        sp.seg_col0 = upload(ctx, "srv.col0", col0);
+        sp.seg_seed = (const uint64_t*)dptr(i_sd);
+        sp.seg_col0 = (const int32_t*)dptr(i_c0);
         sp.q = (const T*)S->q;
         sp.coef = S->coef;
         sp.mean = S->mean;
@@ -489,9 +576,6 @@ int tick_impl(vne_server* S) {
         VNE_TRY_CUDA(ctx, launch_srv_start<T>(sp, ks, st));
         ctx->launches += 3;
     }
-    // one Lanczos step of every active segment, each at its own step
-    std::vector<int32_t> segj(S->nseg, 0);  // the idle segment max_active stays 0
-    for (int ri : S->active) segj[S->reqs[ri].slot] = S->reqs[ri].j;
     StepParams<T> p;
     memset(&p, 0, sizeof(p));
     p.rowptr = P.rowptr;
@@ -516,7 +600,7 @@ int tick_impl(vne_server* S) {
     p.u = (T*)S->u;
     p.part = ws_get_t<double>(ctx, "srv.step_part", (size_t)panels * std::max(cta_high, tile_high) * ks);
     p.counter = ws_get_t<uint32_t>(ctx, "srv.step_counter", (size_t)panels * P.nseg);
-    p.segj = upload(ctx, "srv.segj", segj);
+    p.segj = (const int32_t*)dptr(i_sj);
     p.slot0 = (T*)S->slot0;
     p.slot1 = (T*)S->slot1;
     p.alpha0 = S->alpha;
@@ -526,52 +610,17 @@ int tick_impl(vne_server* S) {
         VNE_TRY_CUDA(ctx, launch_step_update_segj<T>(p, ks, panels, st));
         ctx->launches += 2;
     }
-    // blocks that end now (step m) or check their Krylov error (a multiple of
-    // check_every below m, with a tolerance).  A check needs every column's
-    // Theorem 4.4 estimate within tau |psi|; it is evaluated on the first
-    // kFirst columns of each checking query, and on the others only for the
-    // queries whose first columns all pass (the same decision, without the
-    // FP64 work of estimates that cannot change it)
-    std::vector<int> ending, checking;
-    for (int ri : S->active) {
-        const vne_server::Req& rq = S->reqs[ri];
-        if (rq.j == S->m) ending.push_back(ri);
-        else if (rq.tau > 0.0 && rq.j % S->check == 0) checking.push_back(ri);
-    }
-    const int kFirst = std::min(K, 8);
     std::vector<double> hp, he;
-    auto evaluate = [&](const std::vector<int>& quad_all, const std::vector<int>& est_q, int c_begin, int c_end) {
-        // quadratures of all columns of quad_all, quadratures and estimates of
-        // columns [c_begin, c_end) of est_q; then psi and the estimates to the host
-        std::vector<int32_t> qcols, qm, bcols, bm;
-        std::vector<double> blam;
-        for (int ri : quad_all) {
-            const vne_server::Req& rq = S->reqs[ri];
-            for (int c = 0; c < K; c++) {
-                qcols.push_back(rq.slot * K + c);
-                qm.push_back(rq.j);
-            }
-        }
-        for (int ri : est_q) {
-            const vne_server::Req& rq = S->reqs[ri];
-            for (int c = c_begin; c < c_end; c++) {
-                qcols.push_back(rq.slot * K + c);
-                qm.push_back(rq.j);
-                bcols.push_back(rq.slot * K + c);
-                bm.push_back(rq.j);
-                blam.push_back(rq.lam_max);
-            }
-        }
-        if (qcols.empty()) return;
-        VNE_TRY_CUDA(ctx, launch_tridiag_quad_list(S->alpha, S->beta, S->norm2, S->scale, (int)qcols.size(),
-                                                   upload(ctx, "srv.qcols", qcols), upload(ctx, "srv.qm", qm), S->m,
-                                                   SK, S->psi, st));
+    auto evaluate = [&](const Lists& L, const int32_t* qc, const int32_t* qm, const int32_t* bc, const int32_t* bm,
+                        const double* bl) {
+        if (L.qcols.empty()) return;
+        VNE_TRY_CUDA(ctx, launch_tridiag_quad_list(S->alpha, S->beta, S->norm2, S->scale, (int)L.qcols.size(), qc,
+                                                   qm, S->m, SK, S->psi, st));
         ctx->launches += 1;
-        if (!bcols.empty()) {
-            VNE_TRY_CUDA(ctx, launch_tridiag_bounds_list(S->alpha, S->beta, S->norm2, S->scale, (int)bcols.size(),
-                                                         upload(ctx, "srv.bcols", bcols), upload(ctx, "srv.bm", bm),
-                                                         upload(ctx, "srv.blam", blam), S->m, SK, 0.0, 1.0, S->grid,
-                                                         S->est, S->est + SK, S->est + 2 * SK, st));
+        if (!L.bcols.empty()) {
+            VNE_TRY_CUDA(ctx, launch_tridiag_bounds_list(S->alpha, S->beta, S->norm2, S->scale, (int)L.bcols.size(),
+                                                         bc, bm, bl, S->m, SK, 0.0, 1.0, S->grid, S->est,
+                                                         S->est + SK, S->est + 2 * SK, st));
             ctx->launches += 1;
             he = download(ctx, S->est + 2 * SK, SK);
         }
@@ -584,7 +633,8 @@ int tick_impl(vne_server* S) {
         }
         return true;
     };
-    evaluate(ending, checking, 0, kFirst);
+    evaluate(LA, (const int32_t*)dptr(i_qc), (const int32_t*)dptr(i_qm), (const int32_t*)dptr(i_bc),
+             (const int32_t*)dptr(i_bm), (const double*)dptr(i_bl));
     std::vector<int> candidates;
     for (int ri : checking)
         if (passes(S->reqs[ri], 0, kFirst)) candidates.push_back(ri);
@@ -592,7 +642,11 @@ int tick_impl(vne_server* S) {
     for (int ri : ending) block_done[ri] = 1;
     // the rest of the candidates' columns (the device arrays keep the values
     // of the first evaluation for every other column)
-    if (!candidates.empty() && kFirst < K) evaluate({}, candidates, kFirst, K);
+    if (!candidates.empty() && kFirst < K) {
+        Lists LB = make_lists({}, candidates, kFirst, K);
+        evaluate(LB, upload(ctx, "srv.qcols", LB.qcols), upload(ctx, "srv.qm", LB.qm),
+                 upload(ctx, "srv.bcols", LB.bcols), upload(ctx, "srv.bm", LB.bm), upload(ctx, "srv.blam", LB.blam));
+    }
     for (int ri : candidates)
         if (passes(S->reqs[ri], kFirst, K)) block_done[ri] = 1;
     int completed = 0;
