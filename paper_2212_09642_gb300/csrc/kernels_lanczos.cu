@@ -481,14 +481,15 @@ __global__ void __launch_bounds__(VNE_THREADS) k_srv_coef(SrvStartParams<T> p) {
     const int s = t.seg, c0 = threadIdx.x % 64, rs = threadIdx.x / 64;
     __shared__ double red[VNE_THREADS / 64][4 * 256];
     for (int c = c0; c < p.K; c += 64) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        // products in the vector precision, runs of 16 rows summed in FP64
+        RowSum<T> acc[4];
         for (int r = t.row_begin + rs; r < t.row_end; r += VNE_THREADS / 64) {
-            const double g = (double)srv_probe(p, s, c, r);
+            const T g = srv_probe(p, s, c, r);
 #pragma unroll
-            for (int i = 0; i < 4; i++) acc[i] += (double)p.q[(size_t)r * 4 + i] * g;
+            for (int i = 0; i < 4; i++) acc[i].add(p.q[(size_t)r * 4 + i] * g);
         }
 #pragma unroll
-        for (int i = 0; i < 4; i++) red[rs][i * p.K + c] = acc[i];
+        for (int i = 0; i < 4; i++) red[rs][i * p.K + c] = acc[i].total();
     }
     __syncthreads();
     const int W = 4 * p.K;

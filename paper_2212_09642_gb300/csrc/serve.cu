@@ -614,12 +614,14 @@ int tick_impl(vne_server* S) {
     auto evaluate = [&](const Lists& L, const int32_t* qc, const int32_t* qm, const int32_t* bc, const int32_t* bm,
                         const double* bl) {
         if (L.qcols.empty()) return;
+        // the kernels' step bucket from the largest step count listed
+        const int mx = *std::max_element(L.qm.begin(), L.qm.end());
         VNE_TRY_CUDA(ctx, launch_tridiag_quad_list(S->alpha, S->beta, S->norm2, S->scale, (int)L.qcols.size(), qc,
-                                                   qm, S->m, SK, S->psi, st));
+                                                   qm, mx, SK, S->psi, st));
         ctx->launches += 1;
         if (!L.bcols.empty()) {
             VNE_TRY_CUDA(ctx, launch_tridiag_bounds_list(S->alpha, S->beta, S->norm2, S->scale, (int)L.bcols.size(),
-                                                         bc, bm, bl, S->m, SK, 0.0, 1.0, S->grid, S->est,
+                                                         bc, bm, bl, mx, SK, 0.0, 1.0, S->grid, S->est,
                                                          S->est + SK, S->est + 2 * SK, st));
             ctx->launches += 1;
             he = download(ctx, S->est + 2 * SK, SK);

@@ -165,3 +165,36 @@ def test_serving_krylov_stopping(vctx, fp64):
     finally:
         for m in mats:
             vne.vne_matrix_destroy(m)
+
+
+def test_serving_work_tables_reused_and_grown(vctx):
+    """The server's work tables (CTAs, long rows, tiles) are device tables in
+    which each admitted query takes first-fit ranges and frees them at
+    completion.  Queries of very different sizes through three slots make
+    the ranges fragment, get reused by other queries and the tables grow
+    mid-run; every result is still bit-identical to the query served alone,
+    and within the mixed-path tolerance of the oracle for two of them."""
+    # the large ones need more than the tables' first 1024 CTAs together
+    gs = [graphs.barabasi_albert(300_000, 3, 61), graphs.erdos_renyi(1500, 8 / 1499, 62),
+          graphs.watts_strogatz(150_000, 6, 0.1, 63), graphs.barabasi_albert(900, 3, 64),
+          graphs.erdos_renyi(250_000, 8 / 249_999, 65)]
+    mats = [vne.matrix_from_graph(vctx, g, fp64=False) for g in gs]
+    opt = vne.options(reorth=0, panel=8, quad_tol=-1.0, check_every=CHECK, sketch_steps=8)
+    eps = 4e-3
+    try:
+        sched = [(t, i % 5, 700 + i) for i, t in enumerate([0, 0, 0, 3, 9, 15, 22, 30, 41, 55, 60, 75])]
+        mixed, most = _run(vctx, mats, sched, budget=1 << 36, max_active=3, eps=eps, cap=512, opt=opt)
+        assert most == 3
+        for (mi, seed), r in mixed.items():
+            assert r["state"] == 2
+            alone, _ = _run(vctx, mats, [(0, mi, seed)], budget=1 << 36, max_active=3, eps=eps, cap=512, opt=opt)
+            assert alone[(mi, seed)]["estimate"] == r["estimate"], (mi, seed)
+        for mi, seed in [(1, 701), (3, 703)]:
+            A, _ = density.density_matrix(gs[mi])
+            ref, _, nv, steps, _ = estimators.served_hutchpp(A, eps, 64, M_STEPS, seed, max_vectors=512,
+                                                             quad_tol=0.5 * eps, check_every=CHECK, sketch_steps=8)
+            r = mixed[(mi, seed)]
+            assert r["vectors"] == nv and abs(r["estimate"] - ref) <= 1e-5 * ref
+    finally:
+        for m in mats:
+            vne.vne_matrix_destroy(m)
