@@ -68,6 +68,8 @@ def parse():
                     help="c2 = the headline workload; c1/c3/c4/c5/c6/c7 print measurement lines of the other configs")
     ap.add_argument("--requests", type=int, default=2000, help="c5: number of queries")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: Poisson arrival rate (queries/s)")
+    ap.add_argument("--at-once", action="store_true",
+                    help="c5: every query arrives at the start (a saturated server, for profiling)")
     ap.add_argument("--fp64-limit-s", type=float, default=600.0,
                     help="c5: wall-time limit of the FP64 one-at-a-time arm (it serves a prefix of the queries)")
     ap.add_argument("--scaling-exponents", default="10,12,14,16,18,20", help="c7: n = 2^e for these e")
@@ -880,6 +882,8 @@ def run_serving(args, ctx, stream):
             pool.append(graphs.watts_strogatz(int(nn), 6, 0.1, 500 + i))
     R = args.requests
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=R))
+    if args.at_once:
+        arrivals[:] = 0.0  # every query arrives at the start: a saturated server (profiling)
     which = rng.integers(0, len(pool), size=R)
     eps, cap, m, block = 1e-3, 8192, 40, 64
 
@@ -951,7 +955,10 @@ def run_serving(args, ctx, stream):
     launches, kst = vne.vne_ctx_stats(ctx)
     vne.vne_ctx_profile(ctx, False)
     sampler.__exit__()
-    lat64, vecs64, ests64, served64, total64, steps64 = serve(True, 1, 60 << 30, False, args.fp64_limit_s)
+    if args.fp64_limit_s > 0:
+        lat64, vecs64, ests64, served64, total64, steps64 = serve(True, 1, 60 << 30, False, args.fp64_limit_s)
+    else:  # the FP64 arm left out
+        lat64, vecs64, ests64, served64, total64, steps64 = {}, {}, {}, 0, 1.0, {}
     idx = np.arange(R)
     L = np.array([lat[i] for i in idx])
     L64 = np.array([lat64[i] for i in range(served64)])
@@ -979,7 +986,8 @@ def run_serving(args, ctx, stream):
                                    "served_p99_same_queries": float(np.percentile(Lsame, 99)),
                                    "max_rel_dev_mixed_vs_fp64": float(max(dev)) if dev else None,
                                    "how": "the same server code with FP64 matrices and one slot; each query runs "
-                                          "alone, latency = FIFO queueing on the same arrivals + its service time"},
+                                          "alone, latency = FIFO queueing on the same arrivals + its service time"}
+            if served64 else None,
             "mean_vectors_per_query": float(np.mean([vecs[i] for i in idx])),
             "roofline": None, "roofline_note": "the served ticks launch step and update together per tick; the "
                                                "kernels' rooflines are those of the headline workload",
